@@ -11,7 +11,7 @@ millions of SNPs):
 
 * kinship  Phi = Z Z^T / k + 1e-3 I, Z (n x k) genotypes drawn Binomial(2, f_l),
   f_l ~ U(0.05, 0.5), each column standardised with its sample mean and
-  population SD (a constant column is redrawn);
+  population SD (a constant column is redrawn, up to 64 times, then zeroed);
 * covariates X_L (n x (p-1)): an intercept column of ones, then N(0,1) columns;
 * SNP dosages x_j ~ Binomial(2, f_j), f_j ~ U(0.05, 0.5), stored int8
   (or float64 for the small FP64-dosage workload);
@@ -72,10 +72,12 @@ def kinship_genotypes(n: int, k: int, seed: int = DEFAULT_SEED, study: int = 0) 
         for j in range(block.shape[1]):
             col = block[:, j]
             redraw = 0
-            while col.std() == 0.0:  # constant column: redraw from the same chunk stream
+            while col.std() == 0.0 and redraw < 64:  # constant column: redraw from the chunk stream
                 redraw += 1
                 col = _binomial2(crng, freqs[c0 + j:c0 + j + 1], n)[:, 0].astype(np.float64)
-            block[:, j] = (col - col.mean()) / col.std()
+            sd = col.std()
+            # a column that stays constant (always so when n = 1) carries no kinship
+            block[:, j] = (col - col.mean()) / sd if sd > 0.0 else 0.0
         Z[:, c0:c1] = block
     return Z
 

@@ -1,0 +1,178 @@
+/*
+ * gwas_b300 — per-SNP generalized least squares (GLS) on one B300 GPU.
+ *
+ * C ABI of the library built from paper_1302_4332_b300/csrc (libgwas_b300.so).
+ * Plain pointers and sizes only.  Every step of the computation runs in the
+ * library's own CUDA kernels (sm_103a); there is no CPU fallback: without a
+ * usable CUDA device every call that computes returns GWAS_ERR_CUDA.
+ *
+ * The computation (Beyer & Bientinesi, "Streaming Data from HDD to GPUs for
+ * Sustained Peak Performance"):
+ *
+ *   Eq. 1    r_i = (X_i^T M^-1 X_i)^-1 X_i^T M^-1 y,   i = 1..m,
+ *            X_i = (X_L | X_R_i)  (Sec. 1.3): X_L holds the p-1 fixed
+ *            covariates, X_R_i is the i-th SNP column.
+ *   Eq. 2    L L^T = M,  X~ = L^-1 X,  y~ = L^-1 y,
+ *            r_i = (X~_i^T X~_i)^-1 X~_i^T y~.
+ *   Listing 1: X~_L, y~, r_T = X~_L^T y~, S_TL = X~_L^T X~_L once; per SNP the
+ *            triangular solve, S_BL = x~_i^T X~_L, S_BR = x~_i^T x~_i,
+ *            r_B = x~_i^T y~ and the p x p SPD solve.
+ *   Sec. 2.2 SNP columns are solved as blocks (trsv -> trsm).
+ *
+ * M = sigma2 (h Phi + (1 - h) I) with Phi the n x n kinship (the paper leaves
+ * M's parametrisation open).  Each SNP result is r (called b here) with p
+ * entries in the column order of X_i: entries 0..p-2 are the covariates, entry
+ * p-1 the SNP effect; se_j = sqrt((S^-1)_jj), S = X_i^T M^-1 X_i.
+ *
+ * Storage: column-major.  Element (i, j) of an n-row matrix with leading
+ * dimension ld is at [i + j * ld].
+ *
+ * Pointers: every array argument may be host memory (pageable or pinned) or
+ * device memory of the context's device; the library finds out which with
+ * cudaPointerGetAttributes.  When the SNP input and all outputs are device
+ * pointers the call is asynchronous on the context's stream and device-side
+ * errors surface at the next gwas_synchronize(); otherwise the call returns
+ * once the outputs are in host memory.  All pointers are borrowed for the
+ * duration of the call only; inputs to gwas_init are copied.
+ *
+ * Errors: every int-returning call returns GWAS_OK (0) or a negative
+ * GWAS_ERR_* code; gwas_strerror() names it and gwas_last_error_detail()
+ * gives the context's last message.  A SNP whose design is numerically
+ * collinear (last pivot d^2 <= 1e-7 * S_BR, e.g. a monomorphic SNP) is not a
+ * call error: its status is GWAS_SNP_SINGULAR and its b and se are NaN.
+ */
+#ifndef GWAS_B300_H
+#define GWAS_B300_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define GWAS_OK 0
+#define GWAS_ERR_ARG (-1)        /* bad n, p, h, sigma2, size, leading dimension, or NULL pointer */
+#define GWAS_ERR_NOT_SPD (-2)    /* Cholesky pivot <= 0 (index: gwas_not_spd_index) or S_TL singular */
+#define GWAS_ERR_CUDA (-3)       /* CUDA runtime/driver error, or no usable device */
+#define GWAS_ERR_TIMEOUT (-4)    /* a bounded device-side or host-side wait ran out */
+#define GWAS_ERR_IO (-5)         /* host-side input/output failure */
+#define GWAS_ERR_NOMEM (-6)      /* device or pinned-host allocation failed */
+#define GWAS_ERR_UNSUPPORTED (-7)/* configuration this build does not provide */
+
+#define GWAS_SNP_OK 0
+#define GWAS_SNP_SINGULAR 1
+
+/* Arithmetic of the blocked triangular solve X~ = L^-1 X_R (Sec. 2.2's trsm).
+ * The Cholesky of M, the diagonal-block inverses of L, X~_L / y~ and the
+ * p x p solves are FP64 in every mode.
+ *   GWAS_FP64   : all of the solve in FP64.
+ *   GWAS_TF32X3 : block products on the tensor cores, each FP32 operand split
+ *                 into TF32 hi + lo, three products (hi*hi + hi*lo + lo*hi),
+ *                 FP32 accumulation.
+ *   GWAS_BF16X3 : the same with BF16 hi + lo pieces. */
+typedef enum { GWAS_FP64 = 0, GWAS_TF32X3 = 1, GWAS_BF16X3 = 2 } gwas_precision;
+
+typedef struct {
+  int precision;   /* gwas_precision */
+  int bs;          /* SNP columns per block: the most columns one solve call takes (>= 1) */
+  int ring_depth;  /* device slots of the host->device block ring used by gwas_solve_stream (>= 2) */
+  int device;      /* CUDA device ordinal; -1 = the current device */
+  int reserved[4]; /* must be zero */
+} gwas_config;
+
+typedef struct gwas_ctx gwas_ctx; /* opaque; owned by the library */
+
+/* Fills *cfg with the defaults: GWAS_FP64, bs = 4096, ring_depth = 3, device -1. */
+void gwas_config_default(gwas_config *cfg);
+
+/* Sets up one study (Listing 1, loop-invariant part; Sec. 3: L stays on the GPU).
+ *   n       samples (>= 1); p columns of each X_i (1 <= p <= 16)
+ *   phi_or_L n x n, leading dimension n.  is_L = 0: the kinship Phi (symmetric;
+ *           only its lower triangle is read) and M = sigma2 (h Phi + (1-h) I)
+ *           is formed on the device; is_L = 1: the lower Cholesky factor L of M
+ *           (upper triangle ignored; h and sigma2 are then only recorded).
+ *   XL      n x (p-1) covariates, leading dimension n (may be NULL when p = 1)
+ *   y       n phenotypes
+ *   h       0 <= h <= 1;  sigma2 > 0
+ *   cfg     NULL for the defaults
+ *   stream  cudaStream_t the context issues its work on (NULL: the legacy default stream)
+ * On success *out owns device memory of about 8 n^2 bytes (FP64 L and the
+ * block operator) plus, for the split modes, 4 n^2 bytes of split copies,
+ * plus per-block scratch of about 8 n bs bytes.
+ * Errors: GWAS_ERR_ARG, GWAS_ERR_NOT_SPD (M or S_TL not positive definite),
+ * GWAS_ERR_NOMEM, GWAS_ERR_CUDA, GWAS_ERR_UNSUPPORTED. */
+int gwas_init(gwas_ctx **out, int n, int p, const double *phi_or_L, int is_L, const double *XL,
+              const double *y, double h, double sigma2, const gwas_config *cfg, void *stream);
+
+/* One block of SNPs (Listing 1 loop body, batched per Sec. 2.2).
+ *   XR      n x ncols int8 dosages, leading dimension ldx >= n (rows >= n ignored)
+ *   ncols   0 <= ncols <= cfg.bs
+ *   b, se   p x ncols FP64 outputs, leading dimension p (se may be NULL)
+ *   status  ncols ints, GWAS_SNP_OK / GWAS_SNP_SINGULAR (may be NULL)
+ * Errors: GWAS_ERR_ARG, GWAS_ERR_CUDA, GWAS_ERR_TIMEOUT. */
+int gwas_solve_block(gwas_ctx *ctx, const int8_t *XR, int64_t ldx, int ncols, double *b, double *se,
+                     int *status);
+
+/* As gwas_solve_block with FP64 SNP values (any real dosages). */
+int gwas_solve_block_f64(gwas_ctx *ctx, const double *XR, int64_t ldx, int ncols, double *b, double *se,
+                         int *status);
+
+/* Whole-study streaming (Sec. 3.1, re-designed): m SNP columns in HOST memory
+ * are cut into blocks of cfg.bs columns and copied into a ring of
+ * cfg.ring_depth device slots on a copy stream, overlapping the solve of the
+ * previous blocks on the compute stream; results are copied back per block.
+ *   XR_host n x m int8, leading dimension ldx >= n (pinned memory gives full
+ *           link speed; pageable memory works through the driver's staging)
+ *   b_host, se_host p x m;  status_host m (se_host / status_host may be NULL)
+ * Returns when all results are in host memory. */
+int gwas_solve_stream(gwas_ctx *ctx, const int8_t *XR_host, int64_t ldx, int64_t m, double *b_host,
+                      double *se_host, int *status_host);
+
+/* Waits for the context's queued work and reports device-side errors
+ * (GWAS_ERR_TIMEOUT when a bounded wait inside a kernel gave up). */
+int gwas_synchronize(gwas_ctx *ctx);
+
+/* Sets the stream later calls are issued on (cudaStream_t; NULL = legacy default). */
+int gwas_set_stream(gwas_ctx *ctx, void *stream);
+
+/* Study facts: n, p, the padded row count of the device layout, precision. */
+int gwas_get_info(const gwas_ctx *ctx, int *n, int *p, int *n_pad, int *precision, int *bs);
+
+/* Index of the first failing Cholesky pivot after GWAS_ERR_NOT_SPD, else -1. */
+int64_t gwas_not_spd_index(const gwas_ctx *ctx);
+
+/* Device copy of the lower factor L (n x n, leading dimension ld >= n) into
+ * caller memory (host or device); for checks of the factorization. */
+int gwas_copy_factor(gwas_ctx *ctx, double *L, int64_t ld);
+
+/* Stage timing with CUDA events recorded around each stage on the stream the
+ * stage runs on; for measurement only (a few microseconds per event pair).
+ * Stages: GWAS_STAGE_H2D (block copy in), GWAS_STAGE_TRSM (the blocked
+ * triangular solve), GWAS_STAGE_REDUCE (reductions + p x p solves),
+ * GWAS_STAGE_D2H (results out).  gwas_timing_enable(ctx, 1) clears and starts
+ * the accumulators, 0 stops them.  gwas_timing_read waits for the recorded
+ * events and writes the summed milliseconds and the number of timed launches
+ * per stage into ms[GWAS_NSTAGES] and count[GWAS_NSTAGES]. */
+#define GWAS_STAGE_H2D 0
+#define GWAS_STAGE_TRSM 1
+#define GWAS_STAGE_REDUCE 2
+#define GWAS_STAGE_D2H 3
+#define GWAS_NSTAGES 4
+int gwas_timing_enable(gwas_ctx *ctx, int enable);
+int gwas_timing_read(gwas_ctx *ctx, double *ms, int64_t *count);
+
+/* Kernel launches the context issued since it was created (all kinds). */
+int64_t gwas_kernel_launches(const gwas_ctx *ctx);
+
+const char *gwas_strerror(int code);
+const char *gwas_last_error_detail(const gwas_ctx *ctx);
+
+/* Frees everything the context owns.  NULL is accepted. */
+void gwas_destroy(gwas_ctx *ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* GWAS_B300_H */

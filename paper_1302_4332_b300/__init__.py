@@ -1,0 +1,295 @@
+"""gwas_b300: per-SNP generalized least squares on one B300 GPU.
+
+Thin Python binding of the C ABI in include/gwas_b300.h (libgwas_b300.so).
+It only marshals arguments: every step of the computation runs in the
+library's CUDA kernels.  There is no CPU fallback: if the library or a CUDA
+device is missing, calls raise.
+
+Array convention (the C ABI's column-major layout):
+  * a matrix with n rows is a numpy array in Fortran order, or a torch tensor
+    whose first dimension has stride 1 (e.g. ``t.T`` of a contiguous tensor);
+  * results b and se come back as (p, ncols) arrays in the same layout.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgwas_b300.so")
+
+GWAS_OK = 0
+ERRORS = {
+    -1: "GWAS_ERR_ARG", -2: "GWAS_ERR_NOT_SPD", -3: "GWAS_ERR_CUDA", -4: "GWAS_ERR_TIMEOUT",
+    -5: "GWAS_ERR_IO", -6: "GWAS_ERR_NOMEM", -7: "GWAS_ERR_UNSUPPORTED",
+}
+PRECISIONS = {"fp64": 0, "tf32x3": 1, "bf16x3": 2}
+SNP_OK, SNP_SINGULAR = 0, 1
+
+# Every symbol the header declares (checked by the CPU test suite).
+EXPORTS = (
+    "gwas_config_default", "gwas_init", "gwas_solve_block", "gwas_solve_block_f64", "gwas_solve_stream",
+    "gwas_synchronize", "gwas_set_stream", "gwas_get_info", "gwas_not_spd_index", "gwas_copy_factor",
+    "gwas_kernel_launches", "gwas_strerror", "gwas_last_error_detail", "gwas_destroy",
+    "gwas_timing_enable", "gwas_timing_read",
+)
+STAGES = ("h2d", "trsm", "reduce", "d2h")
+
+
+class GwasError(RuntimeError):
+    def __init__(self, code: int, detail: str = ""):
+        self.code = code
+        self.name = ERRORS.get(code, f"code {code}")
+        super().__init__(f"{self.name}: {detail}" if detail else self.name)
+
+
+class NotSPDError(GwasError):
+    def __init__(self, code, detail, index):
+        super().__init__(code, detail)
+        self.index = index
+
+
+class _Config(ctypes.Structure):
+    _fields_ = [("precision", ctypes.c_int), ("bs", ctypes.c_int), ("ring_depth", ctypes.c_int),
+                ("device", ctypes.c_int), ("reserved", ctypes.c_int * 4)]
+
+
+_lib = None
+
+
+def load(path: str | None = None):
+    """Loads libgwas_b300.so (built by paper_1302_4332_b300.build)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = path or LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError(f"{path} is missing: build it with `python -m paper_1302_4332_b300.build`")
+    lib = ctypes.CDLL(path)
+    vp, i64, c_int, dp = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int, ctypes.c_double
+    lib.gwas_config_default.argtypes = [ctypes.POINTER(_Config)]
+    lib.gwas_config_default.restype = None
+    lib.gwas_init.argtypes = [ctypes.POINTER(vp), c_int, c_int, vp, c_int, vp, vp, dp, dp,
+                              ctypes.POINTER(_Config), vp]
+    lib.gwas_init.restype = c_int
+    lib.gwas_solve_block.argtypes = [vp, vp, i64, c_int, vp, vp, vp]
+    lib.gwas_solve_block.restype = c_int
+    lib.gwas_solve_block_f64.argtypes = [vp, vp, i64, c_int, vp, vp, vp]
+    lib.gwas_solve_block_f64.restype = c_int
+    lib.gwas_solve_stream.argtypes = [vp, vp, i64, i64, vp, vp, vp]
+    lib.gwas_solve_stream.restype = c_int
+    lib.gwas_synchronize.argtypes = [vp]
+    lib.gwas_synchronize.restype = c_int
+    lib.gwas_set_stream.argtypes = [vp, vp]
+    lib.gwas_set_stream.restype = c_int
+    lib.gwas_get_info.argtypes = [vp] + [ctypes.POINTER(c_int)] * 5
+    lib.gwas_get_info.restype = c_int
+    lib.gwas_not_spd_index.argtypes = [vp]
+    lib.gwas_not_spd_index.restype = i64
+    lib.gwas_copy_factor.argtypes = [vp, vp, i64]
+    lib.gwas_copy_factor.restype = c_int
+    lib.gwas_kernel_launches.argtypes = [vp]
+    lib.gwas_kernel_launches.restype = i64
+    lib.gwas_strerror.argtypes = [c_int]
+    lib.gwas_strerror.restype = ctypes.c_char_p
+    lib.gwas_last_error_detail.argtypes = [vp]
+    lib.gwas_last_error_detail.restype = ctypes.c_char_p
+    lib.gwas_timing_enable.argtypes = [vp, c_int]
+    lib.gwas_timing_enable.restype = c_int
+    lib.gwas_timing_read.argtypes = [vp, ctypes.POINTER(dp), ctypes.POINTER(i64)]
+    lib.gwas_timing_read.restype = c_int
+    lib.gwas_destroy.argtypes = [vp]
+    lib.gwas_destroy.restype = None
+    _lib = lib
+    return lib
+
+
+def _torch():
+    import torch
+    return torch
+
+
+def _is_torch(a) -> bool:
+    return type(a).__module__.startswith("torch")
+
+
+def _colmajor(a, dtype, rows: int, name: str, allow_none=False):
+    """(pointer, leading dimension, keep-alive) of a column-major matrix argument."""
+    if a is None:
+        if allow_none:
+            return None, 0, None
+        raise ValueError(f"{name} is required")
+    if _is_torch(a):
+        torch = _torch()
+        tdt = {np.int8: torch.int8, np.float64: torch.float64, np.int32: torch.int32}[dtype]
+        if a.dtype != tdt:
+            raise TypeError(f"{name} must be {tdt}, got {a.dtype}")
+        if a.dim() == 1:
+            a = a.reshape(-1, 1)
+        if a.shape[0] != rows:
+            raise ValueError(f"{name} must have {rows} rows, got {tuple(a.shape)}")
+        if a.shape[1] > 1 and a.stride(0) != 1:
+            raise ValueError(f"{name} must be column-major (stride 1 along rows)")
+        ld = a.stride(1) if a.shape[1] > 1 else rows
+        return a.data_ptr(), ld, a
+    arr = np.asarray(a)
+    if arr.dtype != dtype:
+        arr = arr.astype(dtype)
+    if arr.ndim == 1:
+        arr = arr.reshape(-1, 1)
+    if arr.shape[0] != rows:
+        raise ValueError(f"{name} must have {rows} rows, got {arr.shape}")
+    arr = np.asfortranarray(arr)
+    return arr.ctypes.data, rows, arr
+
+
+class GLS:
+    """One study on the GPU: Listing 1's loop-invariant part at construction,
+    then per-block solves.
+
+    phi_or_L: n x n kinship Phi (or, with is_L=True, the lower factor L of M).
+    XL: n x (p-1) covariates; y: n phenotypes; M = sigma2 (h Phi + (1-h) I).
+    precision: "fp64", "tf32x3" or "bf16x3" for the blocked triangular solve.
+    """
+
+    def __init__(self, phi_or_L, XL, y, h: float, sigma2: float = 1.0, *, precision: str = "fp64",
+                 bs: int = 4096, ring_depth: int = 3, is_L: bool = False, device: int = -1, stream=None):
+        lib = load()
+        n = int(np.shape(y)[0]) if not _is_torch(y) else int(y.shape[0])
+        q = 0 if XL is None else (int(XL.shape[1]) if np.ndim(XL) == 2 or _is_torch(XL) else 1)
+        self.n, self.p = n, q + 1
+        phi_p, ldphi, self._k1 = _colmajor(phi_or_L, np.float64, n, "phi_or_L")
+        if ldphi != n:
+            raise ValueError("phi_or_L must be a contiguous n x n column-major matrix")
+        xl_p, ldxl, self._k2 = _colmajor(XL, np.float64, n, "XL", allow_none=True) if q else (None, n, None)
+        if q and ldxl != n:
+            raise ValueError("XL must be contiguous with leading dimension n")
+        y_p, _, self._k3 = _colmajor(y, np.float64, n, "y")
+        cfg = _Config()
+        lib.gwas_config_default(ctypes.byref(cfg))
+        cfg.precision = PRECISIONS[precision]
+        cfg.bs = int(bs)
+        cfg.ring_depth = int(ring_depth)
+        cfg.device = int(device)
+        self.precision, self.bs = precision, int(bs)
+        stream_p = None
+        if stream is not None:
+            stream_p = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        ctx = ctypes.c_void_p()
+        rc = lib.gwas_init(ctypes.byref(ctx), n, self.p, phi_p, int(bool(is_L)), xl_p, y_p, float(h),
+                           float(sigma2), ctypes.byref(cfg), stream_p)
+        self._k1 = self._k2 = self._k3 = None
+        if rc != GWAS_OK:
+            detail = (lib.gwas_last_error_detail(None) or b"").decode()
+            if rc == -2:
+                raise NotSPDError(rc, detail, int(lib.gwas_not_spd_index(None)))
+            raise GwasError(rc, detail)
+        self._ctx = ctx
+        info = [ctypes.c_int() for _ in range(5)]
+        lib.gwas_get_info(ctx, *[ctypes.byref(i) for i in info])
+        self.n_pad = info[2].value
+
+    # -- helpers ---------------------------------------------------------------
+    def _check(self, rc: int):
+        if rc != GWAS_OK:
+            detail = (load().gwas_last_error_detail(self._ctx) or b"").decode()
+            raise GwasError(rc, detail)
+
+    def _outputs(self, ncols: int, like, b, se, status):
+        p = self.p
+        if b is None:
+            if _is_torch(like) and like.is_cuda:
+                torch = _torch()
+                b = torch.empty((ncols, p), dtype=torch.float64, device=like.device).T
+                se = torch.empty((ncols, p), dtype=torch.float64, device=like.device).T
+                status = torch.empty(ncols, dtype=torch.int32, device=like.device)
+            else:
+                b = np.empty((p, ncols), order="F")
+                se = np.empty((p, ncols), order="F")
+                status = np.empty(ncols, dtype=np.int32)
+        bp, ldb, _ = _colmajor(b, np.float64, p, "b")
+        sp, lds, _ = _colmajor(se, np.float64, p, "se", allow_none=True)
+        if ldb != p or (sp is not None and lds != p):
+            raise ValueError("b and se must be contiguous p x ncols column-major")
+        if status is not None and not _is_torch(status):
+            status = np.ascontiguousarray(status, dtype=np.int32)
+        stp = None if status is None else (status.data_ptr() if _is_torch(status) else status.ctypes.data)
+        return (b, se, status), (bp, sp, stp)
+
+    # -- the path ----------------------------------------------------------------
+    def solve_block(self, XR, b=None, se=None, status=None):
+        """b, se, status for the SNP columns of XR (n x ncols int8 dosages)."""
+        xp, ldx, keep = _colmajor(XR, np.int8, self.n, "XR")
+        ncols = int(keep.shape[1])
+        outs, ptrs = self._outputs(ncols, keep, b, se, status)
+        self._check(load().gwas_solve_block(self._ctx, xp, ldx, ncols, *ptrs))
+        return outs
+
+    def solve_block_f64(self, XR, b=None, se=None, status=None):
+        """As solve_block with FP64 SNP values."""
+        xp, ldx, keep = _colmajor(XR, np.float64, self.n, "XR")
+        ncols = int(keep.shape[1])
+        outs, ptrs = self._outputs(ncols, keep, b, se, status)
+        self._check(load().gwas_solve_block_f64(self._ctx, xp, ldx, ncols, *ptrs))
+        return outs
+
+    def solve_stream(self, XR_host, b=None, se=None, status=None):
+        """All m SNP columns of a HOST array, streamed block by block through the device ring."""
+        xp, ldx, keep = _colmajor(XR_host, np.int8, self.n, "XR_host")
+        if _is_torch(keep) and keep.is_cuda:
+            raise ValueError("solve_stream takes host memory")
+        m = int(keep.shape[1])
+        if b is None:
+            b = np.empty((self.p, m), order="F")
+            se = np.empty((self.p, m), order="F")
+            status = np.empty(m, dtype=np.int32)
+        _, ptrs = self._outputs(m, keep, b, se, status)
+        self._check(load().gwas_solve_stream(self._ctx, xp, ldx, m, *ptrs))
+        return b, se, status
+
+    def synchronize(self):
+        self._check(load().gwas_synchronize(self._ctx))
+
+    def set_stream(self, stream):
+        sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+        self._check(load().gwas_set_stream(self._ctx, sp))
+
+    def factor(self) -> np.ndarray:
+        """The device factor L (n x n, lower) copied to the host."""
+        L = np.empty((self.n, self.n), order="F")
+        self._check(load().gwas_copy_factor(self._ctx, L.ctypes.data, self.n))
+        return L
+
+    def timing(self, enable: bool = True):
+        """Starts (clearing) or stops the per-stage CUDA-event timers."""
+        self._check(load().gwas_timing_enable(self._ctx, int(bool(enable))))
+
+    def timing_read(self) -> dict:
+        """{stage: (total ms, timed launches)} for h2d, trsm, reduce, d2h."""
+        ms = (ctypes.c_double * 4)()
+        cnt = (ctypes.c_int64 * 4)()
+        self._check(load().gwas_timing_read(self._ctx, ms, cnt))
+        return {name: (ms[i], int(cnt[i])) for i, name in enumerate(STAGES)}
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(load().gwas_kernel_launches(self._ctx))
+
+    def close(self):
+        if getattr(self, "_ctx", None):
+            load().gwas_destroy(self._ctx)
+            self._ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -1,0 +1,568 @@
+// The C ABI of gwas_b300 (include/gwas_b300.h): study set-up, block solves and
+// the host->device block stream.  Host code only orchestrates; every step of
+// the computation is one of the library's kernels.
+#include <cuda.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "gwas_internal.cuh"
+
+using namespace gwas;
+
+struct gwas_ctx {
+  int dev = 0;
+  int num_sms = 148;
+  cudaStream_t stream = nullptr;
+  cudaStream_t copy_stream = nullptr;
+  int n = 0, p = 0, q = 0, n_pad = 0, P = 0;
+  int prec = GWAS_FP64, bs = 0, ring_depth = 0;
+  double h = 0.0, sigma2 = 0.0;
+  // study data (device)
+  double* L = nullptr;     // n_pad x n_pad column-major
+  double* Dinv = nullptr;  // P x TB x TB
+  double* Aop = nullptr;   // n_pad x n_pad row-major block operator
+  double* W = nullptr;     // n_pad x (q+1): [X~_L | y~]
+  double* G = nullptr;     // (q+1)^2
+  SolveConsts* sc = nullptr;
+  DevStatus* st = nullptr;
+  // per-block scratch (device)
+  double* Xt = nullptr;    // n_pad x bs FP64 (FP64 mode; set-up in every mode)
+  Sched* sched = nullptr;  // scheduler counter + tile flags
+  size_t sched_bytes = 0;
+  // device staging for host arguments
+  std::vector<int8_t*> ring;      // ring_depth slots of n_pad x bs int8
+  std::vector<cudaEvent_t> ev_copied, ev_free, ev_out;
+  double* d_b = nullptr;  // ring_depth x p x bs
+  double* d_se = nullptr;
+  int* d_status = nullptr;
+  double* h_b = nullptr;  // pinned result staging, ring_depth slots
+  double* h_se = nullptr;
+  int* h_status = nullptr;
+  double* f64_in = nullptr;  // n x bs FP64 staging for gwas_solve_block_f64 with host input
+  int64_t launches = 0;
+  int64_t not_spd_index = -1;
+  std::string detail;
+  // stage timing (measurement only)
+  bool timing = false;
+  struct Mark { int stage; cudaEvent_t a, b; };
+  std::vector<Mark> marks;
+  std::vector<cudaEvent_t> event_pool;
+};
+
+namespace {
+
+thread_local int64_t tl_init_not_spd = -1;
+thread_local std::string tl_init_detail;
+
+int fail(gwas_ctx* c, int code, const char* fmt, ...) {
+  if (c) {
+    char buf[512];
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(buf, sizeof buf, fmt, ap);
+    va_end(ap);
+    c->detail = buf;
+  }
+  return code;
+}
+
+#define CK(call)                                                                                   \
+  do {                                                                                             \
+    cudaError_t e_ = (call);                                                                       \
+    if (e_ != cudaSuccess)                                                                         \
+      return fail(ctx, e_ == cudaErrorMemoryAllocation ? GWAS_ERR_NOMEM : GWAS_ERR_CUDA, "%s: %s (%s:%d)", \
+                  #call, cudaGetErrorString(e_), __FILE__, __LINE__);                              \
+  } while (0)
+
+bool is_device_ptr(const void* ptr) {
+  if (!ptr) return false;
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, ptr) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+template <typename T>
+cudaError_t dmalloc(T** p, size_t bytes) {
+  *p = nullptr;
+  if (bytes == 0) return cudaSuccess;
+  return cudaMalloc(reinterpret_cast<void**>(p), bytes);
+}
+
+cudaEvent_t pool_event(gwas_ctx* c) {
+  if (!c->event_pool.empty()) {
+    cudaEvent_t e = c->event_pool.back();
+    c->event_pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  cudaEventCreate(&e);
+  return e;
+}
+
+// Brackets one stage with events on stream s when timing is on.
+struct StageMark {
+  gwas_ctx* c;
+  int stage;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  StageMark(gwas_ctx* c_, int stage_, cudaStream_t s_) : c(c_), stage(stage_), s(s_) {
+    if (c->timing) {
+      a = pool_event(c);
+      cudaEventRecord(a, s);
+    }
+  }
+  ~StageMark() {
+    if (a) {
+      cudaEvent_t b = pool_event(c);
+      cudaEventRecord(b, s);
+      c->marks.push_back({stage, a, b});
+    }
+  }
+};
+
+// Reads the device status block; returns a GWAS code (TIMEOUT) and clears it.
+int check_device_status(gwas_ctx* ctx) {
+  DevStatus hs;
+  CK(cudaMemcpyAsync(&hs, ctx->st, sizeof hs, cudaMemcpyDeviceToHost, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  if (hs.err != DEV_OK || hs.abort) {
+    DevStatus clean{};
+    clean.not_spd = hs.not_spd;
+    clean.sc_err = hs.sc_err;
+    CK(cudaMemcpy(ctx->st, &clean, sizeof clean, cudaMemcpyHostToDevice));
+    return fail(ctx, GWAS_ERR_TIMEOUT, "a bounded device-side wait ran out (device code %d)", hs.err);
+  }
+  return GWAS_OK;
+}
+
+// X~ = L^-1 X for one block (FP64 or split precision), then reductions + solve.
+int run_block(gwas_ctx* ctx, const void* X, bool int8_input, int64_t ldx, int ncols, double* b, double* se,
+              int* status) {
+  const int C64 = (ncols + F64_TN - 1) / F64_TN;
+  if (ctx->prec == GWAS_FP64 || !int8_input) {
+    CK(cudaMemsetAsync(ctx->sched, 0, sizeof(Sched) + sizeof(int) * (size_t)ctx->P * C64, ctx->stream));
+    TrsmF64Args a{};
+    a.Aop = ctx->Aop; a.lda = ctx->n_pad;
+    a.X = X; a.ldx = ldx; a.n = ctx->n;
+    a.Xt = ctx->Xt; a.ldt = ctx->n_pad;
+    a.P = ctx->P; a.ncols = ncols; a.C = C64;
+    a.sched = ctx->sched; a.st = ctx->st;
+    {
+      StageMark m(ctx, GWAS_STAGE_TRSM, ctx->stream);
+      CK(launch_trsm_f64(a, int8_input, ctx->stream, ctx->num_sms));
+    }
+    ctx->launches += 1;
+    {
+      StageMark m(ctx, GWAS_STAGE_REDUCE, ctx->stream);
+      CK(launch_reduce_solve(ctx->Xt, XT_F64, ctx->n_pad, ctx->n_pad, ctx->W, ctx->n_pad, ctx->sc, ctx->q, ncols,
+                             b, se, status, ctx->stream));
+    }
+    ctx->launches += 1;
+    return GWAS_OK;
+  }
+  return fail(ctx, GWAS_ERR_UNSUPPORTED, "split-precision solve not built");
+}
+
+int solve_common(gwas_ctx* ctx, const void* XR, bool int8_input, int64_t ldx, int ncols, double* b, double* se,
+                 int* status) {
+  if (!ctx) return GWAS_ERR_ARG;
+  if (!XR || !b || ncols < 0 || ncols > ctx->bs || ldx < ctx->n)
+    return fail(ctx, GWAS_ERR_ARG, "bad arguments: XR=%p b=%p ncols=%d (bs %d) ldx=%lld (n %d)", XR, (void*)b,
+                ncols, ctx->bs, (long long)ldx, ctx->n);
+  if (ncols == 0) return GWAS_OK;
+  CK(cudaSetDevice(ctx->dev));
+  const bool dev_in = is_device_ptr(XR);
+  const bool dev_out = is_device_ptr(b) && (!se || is_device_ptr(se)) && (!status || is_device_ptr(status));
+  const void* xin = XR;
+  int64_t ld_in = ldx;
+  if (!dev_in) {
+    StageMark m(ctx, GWAS_STAGE_H2D, ctx->stream);
+    if (int8_input) {
+      CK(cudaMemcpy2DAsync(ctx->ring[0], (size_t)ctx->n_pad, XR, (size_t)ldx, (size_t)ctx->n, (size_t)ncols,
+                           cudaMemcpyHostToDevice, ctx->stream));
+      xin = ctx->ring[0];
+      ld_in = ctx->n_pad;
+    } else {
+      if (!ctx->f64_in) CK(dmalloc(&ctx->f64_in, sizeof(double) * (size_t)ctx->n * ctx->bs));
+      CK(cudaMemcpy2DAsync(ctx->f64_in, sizeof(double) * (size_t)ctx->n, XR, sizeof(double) * (size_t)ldx,
+                           sizeof(double) * (size_t)ctx->n, (size_t)ncols, cudaMemcpyHostToDevice, ctx->stream));
+      xin = ctx->f64_in;
+      ld_in = ctx->n;
+    }
+  }
+  double* ob = dev_out ? b : ctx->d_b;
+  double* ose = dev_out ? se : (se ? ctx->d_se : nullptr);
+  int* ost = dev_out ? status : (status ? ctx->d_status : nullptr);
+  int rc = run_block(ctx, xin, int8_input, ld_in, ncols, ob, ose, ost);
+  if (rc != GWAS_OK) return rc;
+  if (dev_in && dev_out) return GWAS_OK;  // asynchronous on the context's stream
+  if (!dev_out) {
+    StageMark m(ctx, GWAS_STAGE_D2H, ctx->stream);
+    CK(cudaMemcpyAsync(b, ctx->d_b, sizeof(double) * (size_t)ctx->p * ncols, cudaMemcpyDeviceToHost, ctx->stream));
+    if (se)
+      CK(cudaMemcpyAsync(se, ctx->d_se, sizeof(double) * (size_t)ctx->p * ncols, cudaMemcpyDeviceToHost,
+                         ctx->stream));
+    if (status)
+      CK(cudaMemcpyAsync(status, ctx->d_status, sizeof(int) * (size_t)ncols, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  return check_device_status(ctx);
+}
+
+void free_all(gwas_ctx* c) {
+  if (!c) return;
+  cudaSetDevice(c->dev);
+  cudaStreamSynchronize(c->stream);
+  if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+  for (auto* p : c->ring) cudaFree(p);
+  for (auto& v : {&c->ev_copied, &c->ev_free, &c->ev_out})
+    for (auto ev : *v) cudaEventDestroy(ev);
+  for (auto& mk : c->marks) { cudaEventDestroy(mk.a); cudaEventDestroy(mk.b); }
+  for (auto ev : c->event_pool) cudaEventDestroy(ev);
+  cudaFree(c->L); cudaFree(c->Dinv); cudaFree(c->Aop); cudaFree(c->W); cudaFree(c->G);
+  cudaFree(c->sc); cudaFree(c->st); cudaFree(c->Xt); cudaFree(c->sched);
+  cudaFree(c->d_b); cudaFree(c->d_se); cudaFree(c->d_status); cudaFree(c->f64_in);
+  cudaFreeHost(c->h_b); cudaFreeHost(c->h_se); cudaFreeHost(c->h_status);
+  if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+  delete c;
+}
+
+}  // namespace
+
+extern "C" {
+
+void gwas_config_default(gwas_config* cfg) {
+  if (!cfg) return;
+  std::memset(cfg, 0, sizeof *cfg);
+  cfg->precision = GWAS_FP64;
+  cfg->bs = 4096;
+  cfg->ring_depth = 3;
+  cfg->device = -1;
+}
+
+const char* gwas_strerror(int code) {
+  switch (code) {
+    case GWAS_OK: return "ok";
+    case GWAS_ERR_ARG: return "invalid argument";
+    case GWAS_ERR_NOT_SPD: return "matrix not positive definite";
+    case GWAS_ERR_CUDA: return "CUDA error";
+    case GWAS_ERR_TIMEOUT: return "bounded wait timed out";
+    case GWAS_ERR_IO: return "input/output error";
+    case GWAS_ERR_NOMEM: return "out of memory";
+    case GWAS_ERR_UNSUPPORTED: return "unsupported configuration";
+    default: return "unknown error";
+  }
+}
+
+const char* gwas_last_error_detail(const gwas_ctx* ctx) { return ctx ? ctx->detail.c_str() : tl_init_detail.c_str(); }
+
+int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, const double* XL, const double* y,
+              double h, double sigma2, const gwas_config* cfg_in, void* stream) {
+  if (!out) return GWAS_ERR_ARG;
+  *out = nullptr;
+  gwas_config cfg;
+  gwas_config_default(&cfg);
+  if (cfg_in) cfg = *cfg_in;
+  if (n < 1 || p < 1 || p > QMAX + 1 || !phi_or_L || !y || (p > 1 && !XL) || !(h >= 0.0 && h <= 1.0) ||
+      !(sigma2 > 0.0) || cfg.bs < 1 || cfg.ring_depth < 2 || cfg.precision < GWAS_FP64 ||
+      cfg.precision > GWAS_BF16X3)
+    return GWAS_ERR_ARG;
+  for (int r : cfg.reserved)
+    if (r != 0) return GWAS_ERR_ARG;
+
+  gwas_ctx* ctx = new gwas_ctx;
+  int dev = cfg.device;
+  if (dev < 0) {
+    if (cudaGetDevice(&dev) != cudaSuccess) {
+      cudaGetLastError();
+      free_all(ctx);
+      return GWAS_ERR_CUDA;
+    }
+  }
+  ctx->dev = dev;
+  {
+    cudaError_t e = cudaSetDevice(dev);
+    if (e != cudaSuccess) { cudaGetLastError(); free_all(ctx); return GWAS_ERR_CUDA; }
+  }
+  int rc = [&]() -> int {
+    cudaDeviceProp prop;
+    CK(cudaGetDeviceProperties(&prop, dev));
+    if (prop.major < 10) return fail(ctx, GWAS_ERR_UNSUPPORTED, "device %s (sm_%d%d) is not a Blackwell part",
+                                     prop.name, prop.major, prop.minor);
+    ctx->num_sms = prop.multiProcessorCount;
+    ctx->stream = static_cast<cudaStream_t>(stream);
+    CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+    ctx->n = n; ctx->p = p; ctx->q = p - 1;
+    ctx->n_pad = (n + TB - 1) / TB * TB;
+    ctx->P = ctx->n_pad / TB;
+    ctx->prec = cfg.precision; ctx->bs = cfg.bs; ctx->ring_depth = cfg.ring_depth;
+    ctx->h = h; ctx->sigma2 = sigma2;
+    const size_t np = (size_t)ctx->n_pad, n2 = np * np;
+    CK(dmalloc(&ctx->L, sizeof(double) * n2));
+    CK(dmalloc(&ctx->Dinv, sizeof(double) * (size_t)ctx->P * TB * TB));
+    CK(dmalloc(&ctx->Aop, sizeof(double) * n2));
+    CK(dmalloc(&ctx->W, sizeof(double) * np * (ctx->q + 1)));
+    CK(dmalloc(&ctx->G, sizeof(double) * (ctx->q + 1) * (ctx->q + 1)));
+    CK(dmalloc(&ctx->sc, sizeof(SolveConsts)));
+    CK(dmalloc(&ctx->st, sizeof(DevStatus)));
+    const int maxC = std::max((cfg.bs + F64_TN - 1) / F64_TN, 1);
+    ctx->sched_bytes = sizeof(Sched) + sizeof(int) * (size_t)ctx->P * maxC;
+    CK(dmalloc(&ctx->sched, ctx->sched_bytes));
+    const int xt_cols = std::max(cfg.bs, p);
+    CK(dmalloc(&ctx->Xt, sizeof(double) * np * xt_cols));
+    DevStatus st0{};
+    st0.not_spd = ~0ull;
+    CK(cudaMemcpyAsync(ctx->st, &st0, sizeof st0, cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemsetAsync(ctx->Aop, 0, sizeof(double) * n2, ctx->stream));
+
+    // a1: M (or the given L) into the padded device layout
+    const double* src = phi_or_L;
+    double* tmp = nullptr;
+    if (!is_device_ptr(phi_or_L)) {
+      CK(dmalloc(&tmp, sizeof(double) * (size_t)n * n));
+      CK(cudaMemcpyAsync(tmp, phi_or_L, sizeof(double) * (size_t)n * n, cudaMemcpyHostToDevice, ctx->stream));
+      src = tmp;
+    }
+    CK(launch_form_m(src, n, n, ctx->n_pad, h, sigma2, is_L, ctx->L, ctx->stream));
+    ctx->launches += 1;
+    CK(cudaStreamSynchronize(ctx->stream));
+    if (tmp) cudaFree(tmp);
+
+    // a2 + a4: Cholesky with the diagonal-block inverses (a given L is refactored
+    // from L L^T only in the sense that its diagonal blocks are inverted here)
+    double* panel = nullptr;
+    CK(dmalloc(&panel, sizeof(double) * np * TB));
+    if (!is_L) {
+      CK(launch_potrf(ctx->L, ctx->n_pad, ctx->Dinv, panel, ctx->st, ctx->stream, &ctx->launches));
+    } else {
+      CK(launch_invert_diag_blocks(ctx->L, ctx->n_pad, ctx->Dinv, ctx->st, ctx->stream));
+      ctx->launches += 1;
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    cudaFree(panel);
+    DevStatus hs;
+    CK(cudaMemcpy(&hs, ctx->st, sizeof hs, cudaMemcpyDeviceToHost));
+    if (hs.not_spd != ~0ull) {
+      ctx->not_spd_index = (int64_t)hs.not_spd;
+      return fail(ctx, GWAS_ERR_NOT_SPD, "M is not positive definite: pivot %lld", (long long)hs.not_spd);
+    }
+    CK(launch_build_aop(ctx->L, ctx->Dinv, ctx->n_pad, ctx->Aop, ctx->stream, &ctx->launches));
+
+    // a3: [X~_L | y~] = L^-1 [X_L | y] (FP64), G = W^T W, solve constants
+    double* XLy = nullptr;
+    CK(dmalloc(&XLy, sizeof(double) * (size_t)n * (ctx->q + 1)));
+    if (ctx->q) {
+      const bool d = is_device_ptr(XL);
+      CK(cudaMemcpyAsync(XLy, XL, sizeof(double) * (size_t)n * ctx->q,
+                         d ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+    }
+    CK(cudaMemcpyAsync(XLy + (size_t)n * ctx->q, y, sizeof(double) * (size_t)n,
+                       is_device_ptr(y) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
+    {
+      const int Cw = (ctx->q + 1 + F64_TN - 1) / F64_TN;
+      CK(cudaMemsetAsync(ctx->sched, 0, sizeof(Sched) + sizeof(int) * (size_t)ctx->P * Cw, ctx->stream));
+      TrsmF64Args a{};
+      a.Aop = ctx->Aop; a.lda = ctx->n_pad;
+      a.X = XLy; a.ldx = n; a.n = n;
+      a.Xt = ctx->W; a.ldt = ctx->n_pad;
+      a.P = ctx->P; a.ncols = ctx->q + 1; a.C = Cw;
+      a.sched = ctx->sched; a.st = ctx->st;
+      CK(launch_trsm_f64(a, false, ctx->stream, ctx->num_sms));
+      ctx->launches += 1;
+    }
+    CK(launch_gram(ctx->W, ctx->n_pad, ctx->n_pad, ctx->q + 1, ctx->G, ctx->stream));
+    CK(launch_solve_consts(ctx->G, ctx->q, ctx->sc, ctx->st, ctx->stream));
+    ctx->launches += 2;
+    CK(cudaStreamSynchronize(ctx->stream));
+    cudaFree(XLy);
+    CK(cudaMemcpy(&hs, ctx->st, sizeof hs, cudaMemcpyDeviceToHost));
+    if (hs.err != DEV_OK) return fail(ctx, GWAS_ERR_TIMEOUT, "set-up solve timed out");
+    if (hs.sc_err) return fail(ctx, GWAS_ERR_NOT_SPD, "S_TL = X~_L^T X~_L is singular (collinear covariates)");
+
+    if (ctx->prec != GWAS_FP64)
+      return fail(ctx, GWAS_ERR_UNSUPPORTED, "split-precision modes are not built");
+
+    // staging: device ring, outputs, pinned result slots, events
+    const int R = ctx->ring_depth;
+    ctx->ring.assign(R, nullptr);
+    for (int i = 0; i < R; ++i) {
+      CK(dmalloc(&ctx->ring[i], np * cfg.bs));
+      CK(cudaMemsetAsync(ctx->ring[i], 0, np * cfg.bs, ctx->stream));
+    }
+    CK(dmalloc(&ctx->d_b, sizeof(double) * (size_t)R * p * cfg.bs));
+    CK(dmalloc(&ctx->d_se, sizeof(double) * (size_t)R * p * cfg.bs));
+    CK(dmalloc(&ctx->d_status, sizeof(int) * (size_t)R * cfg.bs));
+    CK(cudaMallocHost(&ctx->h_b, sizeof(double) * (size_t)R * p * cfg.bs));
+    CK(cudaMallocHost(&ctx->h_se, sizeof(double) * (size_t)R * p * cfg.bs));
+    CK(cudaMallocHost(&ctx->h_status, sizeof(int) * (size_t)R * cfg.bs));
+    for (auto* v : {&ctx->ev_copied, &ctx->ev_free, &ctx->ev_out}) {
+      v->assign(R, nullptr);
+      for (auto& ev : *v) CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return GWAS_OK;
+  }();
+  if (rc != GWAS_OK) {
+    // a failed set-up leaves no context: its facts stay readable through a NULL context
+    tl_init_not_spd = ctx->not_spd_index;
+    tl_init_detail = ctx->detail;
+    free_all(ctx);
+    return rc;
+  }
+  tl_init_not_spd = -1;
+  tl_init_detail.clear();
+  *out = ctx;
+  return GWAS_OK;
+}
+
+int gwas_solve_block(gwas_ctx* ctx, const int8_t* XR, int64_t ldx, int ncols, double* b, double* se, int* status) {
+  return solve_common(ctx, XR, true, ldx, ncols, b, se, status);
+}
+
+int gwas_solve_block_f64(gwas_ctx* ctx, const double* XR, int64_t ldx, int ncols, double* b, double* se,
+                         int* status) {
+  return solve_common(ctx, XR, false, ldx, ncols, b, se, status);
+}
+
+int gwas_solve_stream(gwas_ctx* ctx, const int8_t* XR_host, int64_t ldx, int64_t m, double* b_host,
+                      double* se_host, int* status_host) {
+  if (!ctx) return GWAS_ERR_ARG;
+  if (!XR_host || !b_host || m < 0 || ldx < ctx->n)
+    return fail(ctx, GWAS_ERR_ARG, "bad arguments to gwas_solve_stream");
+  if (m == 0) return GWAS_OK;
+  CK(cudaSetDevice(ctx->dev));
+  const int R = ctx->ring_depth, bs = ctx->bs, p = ctx->p;
+  const int64_t nblk = (m + bs - 1) / bs;
+  auto cols_of = [&](int64_t blk) { return (int)std::min<int64_t>(bs, m - blk * bs); };
+  // Results of block blk are copied out of pinned slot blk % R once its event fired.
+  auto drain = [&](int64_t blk) -> int {
+    const int slot = (int)(blk % R), nc = cols_of(blk);
+    CK(cudaEventSynchronize(ctx->ev_out[slot]));
+    std::memcpy(b_host + blk * bs * p, ctx->h_b + (size_t)slot * p * bs, sizeof(double) * (size_t)p * nc);
+    if (se_host)
+      std::memcpy(se_host + blk * bs * p, ctx->h_se + (size_t)slot * p * bs, sizeof(double) * (size_t)p * nc);
+    if (status_host)
+      std::memcpy(status_host + blk * bs, ctx->h_status + (size_t)slot * bs, sizeof(int) * (size_t)nc);
+    return GWAS_OK;
+  };
+  auto enqueue_copy = [&](int64_t blk) -> int {
+    const int slot = (int)(blk % R);
+    CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_free[slot], 0));
+    StageMark mk(ctx, GWAS_STAGE_H2D, ctx->copy_stream);
+    CK(cudaMemcpy2DAsync(ctx->ring[slot], (size_t)ctx->n_pad, XR_host + blk * bs * ldx, (size_t)ldx,
+                         (size_t)ctx->n, (size_t)cols_of(blk), cudaMemcpyHostToDevice, ctx->copy_stream));
+    CK(cudaEventRecord(ctx->ev_copied[slot], ctx->copy_stream));
+    return GWAS_OK;
+  };
+  // the ring starts free
+  for (int s = 0; s < R; ++s) CK(cudaEventRecord(ctx->ev_free[s], ctx->stream));
+  int rc;
+  int64_t next_copy = 0;
+  for (; next_copy < std::min<int64_t>(R, nblk); ++next_copy)
+    if ((rc = enqueue_copy(next_copy)) != GWAS_OK) return rc;
+  for (int64_t blk = 0; blk < nblk; ++blk) {
+    const int slot = (int)(blk % R), nc = cols_of(blk);
+    CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_copied[slot], 0));
+    double* ob = ctx->d_b + (size_t)slot * p * bs;
+    double* ose = ctx->d_se + (size_t)slot * p * bs;
+    int* ost = ctx->d_status + (size_t)slot * bs;
+    if ((rc = run_block(ctx, ctx->ring[slot], true, ctx->n_pad, nc, ob, ose, ost)) != GWAS_OK) return rc;
+    CK(cudaEventRecord(ctx->ev_free[slot], ctx->stream));
+    {
+    StageMark mk(ctx, GWAS_STAGE_D2H, ctx->stream);
+    CK(cudaMemcpyAsync(ctx->h_b + (size_t)slot * p * bs, ob, sizeof(double) * (size_t)p * nc,
+                       cudaMemcpyDeviceToHost, ctx->stream));
+    if (se_host)
+      CK(cudaMemcpyAsync(ctx->h_se + (size_t)slot * p * bs, ose, sizeof(double) * (size_t)p * nc,
+                         cudaMemcpyDeviceToHost, ctx->stream));
+    if (status_host)
+      CK(cudaMemcpyAsync(ctx->h_status + (size_t)slot * bs, ost, sizeof(int) * (size_t)nc,
+                         cudaMemcpyDeviceToHost, ctx->stream));
+    }
+    CK(cudaEventRecord(ctx->ev_out[slot], ctx->stream));
+    if (next_copy < nblk) {
+      if ((rc = enqueue_copy(next_copy)) != GWAS_OK) return rc;
+      ++next_copy;
+    }
+    // results of the previous block: its copy-out overlaps this block's solve
+    if (blk >= 1 && (rc = drain(blk - 1)) != GWAS_OK) return rc;
+  }
+  if ((rc = drain(nblk - 1)) != GWAS_OK) return rc;
+  return check_device_status(ctx);
+}
+
+int gwas_synchronize(gwas_ctx* ctx) {
+  if (!ctx) return GWAS_ERR_ARG;
+  CK(cudaSetDevice(ctx->dev));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return check_device_status(ctx);
+}
+
+int gwas_set_stream(gwas_ctx* ctx, void* stream) {
+  if (!ctx) return GWAS_ERR_ARG;
+  ctx->stream = static_cast<cudaStream_t>(stream);
+  return GWAS_OK;
+}
+
+int gwas_get_info(const gwas_ctx* ctx, int* n, int* p, int* n_pad, int* precision, int* bs) {
+  if (!ctx) return GWAS_ERR_ARG;
+  if (n) *n = ctx->n;
+  if (p) *p = ctx->p;
+  if (n_pad) *n_pad = ctx->n_pad;
+  if (precision) *precision = ctx->prec;
+  if (bs) *bs = ctx->bs;
+  return GWAS_OK;
+}
+
+int64_t gwas_not_spd_index(const gwas_ctx* ctx) { return ctx ? ctx->not_spd_index : tl_init_not_spd; }
+
+int gwas_copy_factor(gwas_ctx* ctx, double* L, int64_t ld) {
+  if (!ctx || !L || ld < ctx->n) return GWAS_ERR_ARG;
+  CK(cudaSetDevice(ctx->dev));
+  CK(cudaMemcpy2DAsync(L, sizeof(double) * (size_t)ld, ctx->L, sizeof(double) * (size_t)ctx->n_pad,
+                       sizeof(double) * (size_t)ctx->n, (size_t)ctx->n, cudaMemcpyDefault, ctx->stream));
+  CK(cudaStreamSynchronize(ctx->stream));
+  return GWAS_OK;
+}
+
+int gwas_timing_enable(gwas_ctx* ctx, int enable) {
+  if (!ctx) return GWAS_ERR_ARG;
+  CK(cudaSetDevice(ctx->dev));
+  CK(cudaStreamSynchronize(ctx->stream));
+  CK(cudaStreamSynchronize(ctx->copy_stream));
+  for (auto& mk : ctx->marks) {
+    ctx->event_pool.push_back(mk.a);
+    ctx->event_pool.push_back(mk.b);
+  }
+  ctx->marks.clear();
+  ctx->timing = enable != 0;
+  return GWAS_OK;
+}
+
+int gwas_timing_read(gwas_ctx* ctx, double* ms, int64_t* count) {
+  if (!ctx || !ms || !count) return GWAS_ERR_ARG;
+  CK(cudaSetDevice(ctx->dev));
+  for (int i = 0; i < GWAS_NSTAGES; ++i) { ms[i] = 0.0; count[i] = 0; }
+  for (auto& mk : ctx->marks) {
+    CK(cudaEventSynchronize(mk.b));
+    float t = 0.f;
+    CK(cudaEventElapsedTime(&t, mk.a, mk.b));
+    ms[mk.stage] += t;
+    count[mk.stage] += 1;
+  }
+  return GWAS_OK;
+}
+
+int64_t gwas_kernel_launches(const gwas_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+void gwas_destroy(gwas_ctx* ctx) { free_all(ctx); }
+
+}  // extern "C"

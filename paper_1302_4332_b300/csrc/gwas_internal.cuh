@@ -1,0 +1,113 @@
+// Internal declarations of the gwas_b300 CUDA library (sm_103a).
+//
+// Device layout of one study (n samples, n_pad = n rounded up to TB):
+//   L     n_pad x n_pad FP64, column-major: the lower Cholesky factor of M
+//         (Sec. 2.1 "potrf M"); padded rows/columns hold the identity.
+//   Dinv  P = n_pad / TB diagonal-block inverses D_k^-1 = L_kk^-1, TB x TB each,
+//         column-major, FP64.
+//   Aop   n_pad x n_pad FP64, ROW-major: the block operator of the blocked
+//         triangular solve.  Row panel k holds
+//             [ -D_k^-1 L_k0 | ... | -D_k^-1 L_k,k-1 | D_k^-1 ]
+//         so that X~_k = D_k^-1 X_k + sum_{j<k} (-D_k^-1 L_kj) X~_j is one
+//         product per row panel (Sec. 2.2: the trsm over a block of SNPs).
+//         Row-major = the reduction index is contiguous for every row.
+//   W     n_pad x (q+1) FP64, column-major: [X~_L | y~] (Listing 1 precompute).
+//   Xt    n_pad x bs: X~_b = L^-1 X_b for the current block of SNPs.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+
+#include "../../include/gwas_b300.h"
+
+namespace gwas {
+
+constexpr int TB = 128;             // diagonal block (row panel) size of the blocked solve
+constexpr int F64_TN = 64;          // SNP columns per tile of the FP64 solve
+constexpr int QMAX = 15;            // most fixed covariates (p <= 16)
+constexpr double SINGULAR_TAU = 1e-7;
+constexpr long long WAIT_LIMIT_NS = 8000000000LL;  // bounded device-side waits: 8 s
+
+// Codes the kernels write into DevStatus::err.
+enum : int { DEV_OK = 0, DEV_ERR_TIMEOUT = 1 };
+
+// Device-resident status block of a context.
+struct DevStatus {
+  int err;                      // first device-side error (DEV_*)
+  int abort;                    // set when a persistent kernel gives up; others drain
+  unsigned long long not_spd;   // smallest failing Cholesky pivot, ~0ull if none
+  int sc_err;                   // S_TL not positive definite
+  int pad[3];
+};
+
+// Per-SNP solve constants from the loop-invariant part of Listing 1.
+// With S_TL = C C^T:  Cinv = C^-1, zT = C^-1 r_T, b0 = S_TL^-1 r_T,
+// dSTL_j = (S_TL^-1)_jj.
+struct SolveConsts {
+  int q;
+  int pad;
+  double Cinv[QMAX * QMAX];  // column-major q x q (leading dimension QMAX)
+  double zT[QMAX];
+  double b0[QMAX];
+  double dSTL[QMAX];
+};
+
+// Scheduler state of one persistent triangular-solve launch.
+struct Sched {
+  unsigned int counter;  // next tile to hand out
+  unsigned int pad[31];
+  // followed by int flags[P * C]: tile (k, c) finished
+};
+
+__host__ __device__ inline int* sched_flags(Sched* s) { return reinterpret_cast<int*>(s + 1); }
+
+// ---- launchers (each returns the cudaError_t of its launch) ----
+
+// a1: A = sigma2 (h Phi + (1-h) I) on the lower triangle (or a copy of a given L),
+// identity on the padding, zero strict upper triangle.
+cudaError_t launch_form_m(const double* phi, int64_t ldphi, int n, int n_pad, double h, double sigma2,
+                          int is_L, double* A, cudaStream_t s);
+
+// a2 + a4: blocked right-looking Cholesky of A (n_pad x n_pad) in place; writes
+// the diagonal-block inverses into Dinv.  panel is n_pad x TB scratch.
+// Counts its launches into *launches.
+cudaError_t launch_potrf(double* A, int n_pad, double* Dinv, double* panel, DevStatus* st, cudaStream_t s,
+                         int64_t* launches);
+
+// a4 for a caller-supplied L: checks its diagonal and inverts its diagonal blocks.
+cudaError_t launch_invert_diag_blocks(double* L, int n_pad, double* Dinv, DevStatus* st, cudaStream_t s);
+
+// a4: the block operator Aop (row-major) from L and Dinv.
+cudaError_t launch_build_aop(const double* L, const double* Dinv, int n_pad, double* Aop, cudaStream_t s,
+                             int64_t* launches);
+
+// a6 (FP64): Xt = L^-1 X for ncols columns of X (TIn = int8_t or double).
+struct TrsmF64Args {
+  const double* Aop;
+  int64_t lda;        // n_pad
+  const void* X;      // input columns
+  int64_t ldx;
+  int n;              // valid rows of X (rows >= n read as 0)
+  double* Xt;
+  int64_t ldt;        // n_pad
+  int P;              // row panels
+  int ncols;
+  int C;              // column tiles (of F64_TN)
+  Sched* sched;
+  DevStatus* st;
+};
+cudaError_t launch_trsm_f64(const TrsmF64Args& a, bool int8_input, cudaStream_t s, int num_sms);
+
+// a3: G = W^T W (nc x nc, column-major), W n_pad x nc.
+cudaError_t launch_gram(const double* W, int64_t ldw, int n_pad, int nc, double* G, cudaStream_t s);
+// a3: solve constants from G (q covariates), flags S_TL not SPD in st->sc_err.
+cudaError_t launch_solve_consts(const double* G, int q, SolveConsts* sc, DevStatus* st, cudaStream_t s);
+
+// a7 + a8: per-SNP reductions against W and the p x p solve.
+enum XtKind : int { XT_F64 = 0, XT_F32 = 1 };
+cudaError_t launch_reduce_solve(const void* Xt, XtKind kind, int64_t ldt, int rows, const double* W,
+                                int64_t ldw, const SolveConsts* sc, int q, int ncols, double* b, double* se,
+                                int* status, cudaStream_t s);
+
+}  // namespace gwas

@@ -1,0 +1,64 @@
+"""CPU checks of the C-ABI library: it loads, exports every symbol the header
+declares, and refuses to compute without a CUDA device (no CPU fallback)."""
+import ctypes
+import glob
+import os
+import re
+
+import numpy as np
+import pytest
+
+import paper_1302_4332_b300 as gw
+from paper_1302_4332_b300 import build as gbuild
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def _header_symbols():
+    syms = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        syms |= set(re.findall(r"\b(gwas_[a-z0-9_]+)\s*\(", text))
+    return syms
+
+
+@pytest.fixture(scope="module")
+def lib():
+    gbuild.build()
+    return gw.load()
+
+
+def test_library_exports_every_declared_symbol(lib):
+    syms = _header_symbols()
+    assert syms, "no declarations found"
+    assert set(gw.EXPORTS) <= syms
+    for s in sorted(syms):
+        assert hasattr(lib, s), f"{s} declared in include/ but not exported"
+
+
+def test_strerror_and_defaults(lib):
+    assert lib.gwas_strerror(0) == b"ok"
+    assert lib.gwas_strerror(-2) == b"matrix not positive definite"
+    cfg = gw._Config()
+    lib.gwas_config_default(ctypes.byref(cfg))
+    assert (cfg.precision, cfg.bs, cfg.ring_depth, cfg.device) == (0, 4096, 3, -1)
+
+
+def test_null_context_is_an_argument_error(lib):
+    assert lib.gwas_synchronize(None) == -1
+    assert lib.gwas_solve_block(None, None, 0, 0, None, None, None) == -1
+    lib.gwas_destroy(None)
+
+
+def _has_gpu():
+    import torch
+    return torch.cuda.is_available()
+
+
+@pytest.mark.skipif(_has_gpu(), reason="a GPU is present")
+def test_no_device_fails_loudly(lib):
+    n = 8
+    with pytest.raises(gw.GwasError) as e:
+        gw.GLS(np.eye(n), np.ones((n, 1)), np.ones(n), 0.5)
+    assert e.value.name in ("GWAS_ERR_CUDA", "GWAS_ERR_UNSUPPORTED")

@@ -1,0 +1,141 @@
+"""Parity of the CUDA path (through the C ABI) with the FP64 oracle.
+
+Tolerance of the FP64 path: per-SNP normwise relative error of b <= 1e-10 and
+component-wise relative error of se <= 1e-10; statuses identical."""
+import numpy as np
+import pytest
+
+import gwas_synth
+import oracle
+import paper_1302_4332_b300 as gw
+from metrics import compare
+
+pytestmark = pytest.mark.gpu
+
+TOL64 = 1e-10
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1302_4332_b300 import build
+    build.build()
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _case(n, p, k, h, sigma2=1.0, m=64, seed=11, c0=0):
+    s = gwas_synth.study(n, p, k, h, sigma2, seed=seed)
+    X = gwas_synth.dosages(n, c0, c0 + m, seed=seed)
+    L = oracle.potrf(oracle.form_m(s["Phi"], h, sigma2))
+    r, se, _, st = oracle.gls(L, s["XL"], s["y"], X)
+    return s, X, L, (r, se, st)
+
+
+@pytest.fixture(scope="module")
+def small_study():
+    """n = 1000, p = 4, h = 0.6: the small FP64-dosage workload (first 2000 SNPs here)."""
+    return _case(1000, 4, 2000, 0.6, m=2000)
+
+
+def test_fp64_dosages_full_parity(small_study):
+    s, X, L, (r, se, st) = small_study
+    with gw.GLS(s["Phi"], s["XL"], s["y"], s["h"], s["sigma2"], bs=4096) as g:
+        b, se_g, st_g = g.solve_block_f64(X.astype(np.float64))
+    e = compare(b, se_g, st_g, r, se, st)
+    assert e["b_norm"] <= TOL64 and e["se_rel"] <= TOL64, e
+
+
+def test_int8_dosages_parity_and_factor(small_study):
+    s, X, L, (r, se, st) = small_study
+    with gw.GLS(s["Phi"], s["XL"], s["y"], s["h"], s["sigma2"], bs=1024) as g:
+        Lg = g.factor()
+        outs = [g.solve_block(X[:, c0:c0 + 1024]) for c0 in range(0, X.shape[1], 1024)]
+    np.testing.assert_allclose(Lg, L, rtol=0, atol=1e-12 * np.abs(L).max())
+    b = np.concatenate([o[0] for o in outs], axis=1)
+    se_g = np.concatenate([o[1] for o in outs], axis=1)
+    st_g = np.concatenate([o[2] for o in outs])
+    e = compare(b, se_g, st_g, r, se, st)
+    assert e["b_norm"] <= TOL64 and e["se_rel"] <= TOL64, e
+
+
+@pytest.mark.parametrize("n,p,m", [(1, 1, 3), (5, 2, 1), (127, 4, 63), (129, 4, 65), (300, 7, 300),
+                                   (257, 1, 129), (640, 16, 70)])
+def test_ragged_shapes(n, p, m):
+    s, X, L, (r, se, st) = _case(n, p, max(2 * n, 4), 0.5, sigma2=1.3, m=m)
+    with gw.GLS(s["Phi"], s["XL"] if p > 1 else None, s["y"], 0.5, 1.3, bs=max(m, 1)) as g:
+        b, se_g, st_g = g.solve_block(X)
+    e = compare(b, se_g, st_g, r, se, st)
+    assert e["b_norm"] <= TOL64 and e["se_rel"] <= TOL64, e
+
+
+def test_given_factor_matches(small_study):
+    s, X, L, (r, se, st) = small_study
+    with gw.GLS(L, s["XL"], s["y"], s["h"], s["sigma2"], is_L=True, bs=512) as g:
+        b, se_g, st_g = g.solve_block(X[:, :512])
+    e = compare(b, se_g, st_g, r[:, :512], se[:, :512], st[:512])
+    assert e["b_norm"] <= TOL64 and e["se_rel"] <= TOL64, e
+
+
+def test_singular_and_degenerate_snps():
+    s, X, L, _ = _case(200, 4, 400, 0.6, m=6)
+    X[:, 1] = 2          # monomorphic: collinear with the intercept
+    X[:, 2] = 0          # all zero
+    X[:, 3] = 2
+    X[17, 3] = 1         # one sample differs: a valid design
+    r, se, _, st = oracle.gls(L, s["XL"], s["y"], X)
+    assert st.tolist() == [0, 1, 1, 0, 0, 0]
+    with gw.GLS(s["Phi"], s["XL"], s["y"], 0.6, 1.0, bs=16) as g:
+        b, se_g, st_g = g.solve_block(X)
+    e = compare(b, se_g, st_g, r, se, st)
+    assert e["b_norm"] <= TOL64, e
+
+
+def test_h0_and_h1_edges():
+    for h in (0.0, 1.0):
+        s, X, L, (r, se, st) = _case(300, 4, 600, h, m=50)
+        with gw.GLS(s["Phi"], s["XL"], s["y"], h, 1.0, bs=64) as g:
+            b, se_g, st_g = g.solve_block(X)
+        e = compare(b, se_g, st_g, r, se, st)
+        assert e["b_norm"] <= TOL64 and e["se_rel"] <= TOL64, (h, e)
+
+
+def test_not_spd_and_bad_arguments():
+    n = 200
+    Phi = np.eye(n)
+    Phi[150, 150] = -5.0   # M_150,150 = 0.5 * -5 + 0.5 < 0
+    with pytest.raises(gw.NotSPDError) as e:
+        gw.GLS(Phi, np.ones((n, 1)), np.ones(n), 0.5)
+    assert e.value.index == 150
+    XL = np.column_stack([np.ones(n), 2 * np.ones(n)])  # collinear covariates
+    with pytest.raises(gw.NotSPDError):
+        gw.GLS(np.eye(n), XL, np.ones(n), 0.5)
+    with pytest.raises(gw.GwasError) as e:
+        gw.GLS(np.eye(n), np.ones((n, 1)), np.ones(n), 1.5)
+    assert e.value.name == "GWAS_ERR_ARG"
+    with gw.GLS(np.eye(n), np.ones((n, 1)), np.ones(n), 0.5, bs=8) as g:
+        with pytest.raises(gw.GwasError) as e:
+            g.solve_block(np.zeros((n, 9), dtype=np.int8))  # more columns than bs
+        assert e.value.name == "GWAS_ERR_ARG"
+        b, se, st = g.solve_block(np.zeros((n, 0), dtype=np.int8))
+        assert b.shape == (2, 0)
+
+
+def test_device_tensors_async(small_study):
+    import torch
+    s, X, L, (r, se, st) = small_study
+    Xd = torch.from_numpy(np.ascontiguousarray(X.T)).cuda().T  # n x m, column-major on the device
+    with gw.GLS(s["Phi"], s["XL"], s["y"], s["h"], s["sigma2"], bs=2000) as g:
+        b, se_g, st_g = g.solve_block(Xd)
+        g.synchronize()
+        e = compare(b.cpu().numpy(), se_g.cpu().numpy(), st_g.cpu().numpy(), r, se, st)
+    assert e["b_norm"] <= TOL64 and e["se_rel"] <= TOL64, e
+
+
+def test_stream_matches_blocks(small_study):
+    s, X, L, (r, se, st) = small_study
+    Xh = np.asfortranarray(X[:, :1900])
+    with gw.GLS(s["Phi"], s["XL"], s["y"], s["h"], s["sigma2"], bs=256, ring_depth=3) as g:
+        b, se_g, st_g = g.solve_stream(Xh)
+    e = compare(b, se_g, st_g, r[:, :1900], se[:, :1900], st[:1900])
+    assert e["b_norm"] <= TOL64 and e["se_rel"] <= TOL64, e
