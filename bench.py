@@ -1,0 +1,474 @@
+#!/usr/bin/env python
+"""GLS solves per second (SNPs/s) at n = 10^4, p = 4 on one or more B300s.
+
+One step = the whole hot path over 8 blocks of bs = 4096 SNPs (32,768 SNPs)
+of the paper-scale workload (n = 10,000 samples, p = 4, int8 dosages;
+Sec. 1.4 of the paper): per block, the blocked triangular solve
+X~ = L^-1 X_b, the per-SNP reductions and the p x p solves with standard
+errors.  The study set-up (M, Cholesky,
+diagonal-block inverses, the X_L / y precompute) is done once before timing,
+as in the paper's measurements (Sec. 4).
+
+  value   device-resident throughput: the step's 8 int8 blocks already in
+          HBM (328 MB, larger than the 126 MB L2; every block also streams
+          the n x n operator), results written to HBM;
+  e2e     the same metric through gwas_solve_stream with HOST buffers: every
+          step copies its 8 blocks host->device from pinned memory and their
+          b / se / status back, overlapped by the library's block ring.
+
+Paths: "fp64" (all-FP64 solve, DFMA) and, when built, the split-precision
+tensor-core paths.  The headline `value` is the fastest split path when one is
+built, else fp64; every path's numbers are in "paths".
+
+python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
+Multi-GPU: launched by torchrun, one rank per GPU; SNP blocks are sharded
+across ranks with no collective on the data path ("scaling": "weak").
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "GLS solves/sec (SNPs/s) at n=10k,p=4: split-prec vs FP64 path, % roofline"
+UNIT = "SNPs/s"
+WORKLOAD = "n10k_p4_m1M_int8"
+SPLIT_PATHS = ("bf16x3", "tf32x3")
+N_RESIDENT_BLOCKS = 8
+
+
+def parse_args():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--paths", default="auto", help="comma list of fp64,bf16x3,tf32x3 (auto: all built)")
+    ap.add_argument("--n", type=int, default=None, help="override n (smaller smoke runs only)")
+    ap.add_argument("--bs", type=int, default=None, help="override bs (smaller smoke runs only)")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--fp64-steps", type=int, default=None,
+                    help="steps of the fp64 path when a split path is the headline (default 1)")
+    return ap.parse_args()
+
+
+def workload(args):
+    import gwas_synth
+    w = dict(gwas_synth.WORKLOADS[WORKLOAD])
+    if args.n:
+        w["n"] = args.n
+        w["k"] = max(2, args.n // 2)
+    if args.bs:
+        w["bs"] = args.bs
+    return w
+
+
+# ------------------------------------------------------------------ clocks
+class ClockSampler:
+    """SM clock and throttle reasons sampled through NVML while running."""
+
+    REASONS = {
+        0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
+        0x10: "sync_boost", 0x20: "sw_thermal_slowdown", 0x40: "hw_thermal_slowdown",
+        0x80: "hw_power_brake_slowdown", 0x100: "display_clock_setting",
+    }
+
+    def __init__(self, device_index: int, period_s: float = 0.005):
+        self.period = period_s
+        self.samples = []
+        self.reasons = 0
+        self._stop = threading.Event()
+        self._thread = None
+        self.max_mhz = None
+        try:
+            import pynvml
+            pynvml.nvmlInit()
+            self._nvml = pynvml
+            self._h = pynvml.nvmlDeviceGetHandleByIndex(device_index)
+            self.max_mhz = pynvml.nvmlDeviceGetMaxClockInfo(self._h, pynvml.NVML_CLOCK_SM)
+        except Exception as e:  # no NVML binding: sample with nvidia-smi instead
+            self._nvml = None
+            self.error = repr(e)
+        self._device_index = device_index
+        self._proc = None
+
+    def _run(self):
+        nv = self._nvml
+        while not self._stop.is_set():
+            try:
+                self.samples.append(nv.nvmlDeviceGetClockInfo(self._h, nv.NVML_CLOCK_SM))
+                self.reasons |= nv.nvmlDeviceGetCurrentClocksEventReasons(self._h)
+            except Exception:
+                pass
+            time.sleep(self.period)
+
+    def _run_smi(self):
+        import subprocess
+        cmd = ["nvidia-smi", "-i", str(self._device_index),
+               "--query-gpu=clocks.sm,clocks.max.sm,clocks_event_reasons.active",
+               "--format=csv,noheader,nounits", "-lms", "20"]
+        try:
+            self._proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception as e:
+            self.error = repr(e)
+            return
+        for line in self._proc.stdout:
+            parts = [x.strip() for x in line.split(",")]
+            try:
+                self.samples.append(float(parts[0]))
+                self.max_mhz = float(parts[1])
+                self.reasons |= int(parts[2], 16)
+            except Exception:
+                pass
+
+    def __enter__(self):
+        self._thread = threading.Thread(target=self._run if self._nvml else self._run_smi, daemon=True)
+        self._thread.start()
+        if not self._nvml:
+            time.sleep(0.3)  # let nvidia-smi start before the timed region
+        return self
+
+    def __exit__(self, *exc):
+        self._stop.set()
+        if self._proc is not None:
+            time.sleep(0.05)
+            self._proc.terminate()
+        if self._thread:
+            self._thread.join(timeout=5)
+
+    def summary(self):
+        if not self.samples:
+            return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": [], "samples": 0,
+                    "error": getattr(self, "error", "no samples")}
+        reasons = [name for bit, name in self.REASONS.items() if self.reasons & bit and bit != 0x1]
+        return {"sm_mhz": float(np.median(self.samples)), "sm_max_mhz": self.max_mhz, "reasons": reasons,
+                "samples": len(self.samples), "source": "nvml" if self._nvml else "nvidia-smi"}
+
+
+# ------------------------------------------------------------------ peaks
+def load_measured_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+def measure_extra_peaks(torch, dev):
+    """FP64 and TF32 GEMM rates (cuBLAS through torch) and pinned H2D GB/s,
+    which the measured-peaks file does not hold."""
+    out = {}
+
+    def best_gemm(dtype, n, reps):
+        a = torch.randn(n, n, device=dev, dtype=dtype)
+        b = torch.randn(n, n, device=dev, dtype=dtype)
+        torch.matmul(a, b)
+        torch.cuda.synchronize()
+        best = 1e9
+        for _ in range(reps):
+            s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            s.record()
+            torch.matmul(a, b)
+            e.record()
+            torch.cuda.synchronize()
+            best = min(best, s.elapsed_time(e) / 1e3)
+        return 2.0 * n ** 3 / best / 1e12
+
+    out["fp64_tflops_cublas"] = best_gemm(torch.float64, 4096, 3)
+    prev = torch.backends.cuda.matmul.allow_tf32
+    torch.backends.cuda.matmul.allow_tf32 = True
+    out["tf32_tflops_cublas"] = best_gemm(torch.float32, 8192, 5)
+    torch.backends.cuda.matmul.allow_tf32 = prev
+    src = torch.empty(1 << 30, dtype=torch.uint8, pin_memory=True)
+    dst = torch.empty(1 << 30, dtype=torch.uint8, device=dev)
+    dst.copy_(src, non_blocking=True)
+    torch.cuda.synchronize()
+    best = 1e9
+    for _ in range(5):
+        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        s.record()
+        dst.copy_(src, non_blocking=True)
+        e.record()
+        torch.cuda.synchronize()
+        best = min(best, s.elapsed_time(e) / 1e3)
+    out["h2d_gbs_pinned"] = (1 << 30) / best / 1e9
+    del src, dst
+    torch.cuda.empty_cache()
+    return out
+
+
+def kernel_traffic(path: str):
+    """DRAM bytes per launch of the path's triangular-solve kernel from the
+    committed ncu summary, if that summary was taken on the current source."""
+    try:
+        with open(os.path.join(ROOT, "profiles", "traffic_per_launch.json")) as f:
+            rec = json.load(f).get(path)
+        if not rec:
+            return None
+        src = os.path.join(ROOT, "paper_1302_4332_b300", "csrc", rec["source"])
+        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
+        return rec["dram_bytes"] if digest == rec["sha256_16"] else None
+    except Exception:
+        return None
+
+
+# ------------------------------------------------------------------ ours
+def run_ours(args, rank, world, local_rank, dist):
+    import torch
+    import gwas_synth
+    import paper_1302_4332_b300 as gw
+    from paper_1302_4332_b300 import build as gbuild
+
+    gbuild.build()
+    dev = torch.device("cuda", local_rank)
+    torch.cuda.set_device(dev)
+    w = workload(args)
+    n, p, bs = w["n"], w["p"], w["bs"]
+    t0 = time.time()
+    s = gwas_synth.study(n, p, w["k"], w["h"], w["sigma2"])
+    # this rank's blocks: columns [ (rank*NB + i) * bs, ... )
+    blocks_h = [gwas_synth.dosages(n, (rank * N_RESIDENT_BLOCKS + i) * bs, (rank * N_RESIDENT_BLOCKS + i + 1) * bs)
+                for i in range(N_RESIDENT_BLOCKS)]
+    gen_s = time.time() - t0
+    blocks_d = [torch.from_numpy(np.ascontiguousarray(b.T)).to(dev).T for b in blocks_h]
+
+    peaks = load_measured_peaks()
+    extra = measure_extra_peaks(torch, dev) if rank == 0 else {}
+
+    built = list(getattr(gw, "BUILT_PRECISIONS", ("fp64",)))
+    paths = built if args.paths == "auto" else [x for x in args.paths.split(",") if x]
+    has_split = any(pp in paths for pp in SPLIT_PATHS)
+    NB = N_RESIDENT_BLOCKS
+    step_snps = NB * bs
+    results = {}
+    for path in paths:
+        steps, warm_blocks = args.steps, args.warmup * NB
+        if path == "fp64" and has_split:
+            # the FP64 path is two orders of magnitude slower: one step, a few warm-up blocks
+            steps, warm_blocks = (args.fp64_steps or 1), args.warmup
+        t_init = time.time()
+        g = gw.GLS(s["Phi"], s["XL"], s["y"], w["h"], w["sigma2"], precision=path, bs=bs)
+        init_s = time.time() - t_init
+        b = torch.empty((bs, p), dtype=torch.float64, device=dev).T
+        se = torch.empty((bs, p), dtype=torch.float64, device=dev).T
+        st = torch.empty(bs, dtype=torch.int32, device=dev)
+        for i in range(warm_blocks):
+            g.solve_block(blocks_d[i % NB], b, se, st)
+        g.synchronize()
+        g.timing(True)
+        launches0 = g.kernel_launches
+        if dist:
+            dist.barrier()
+        torch.cuda.synchronize()
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        with ClockSampler(local_rank) as clk:
+            ev0.record()
+            for i in range(steps * NB):
+                g.solve_block(blocks_d[i % NB], b, se, st)
+            ev1.record()
+            torch.cuda.synchronize()
+        g.synchronize()
+        elapsed = ev0.elapsed_time(ev1) / 1e3
+        if dist:
+            t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            elapsed = float(t.item())
+            dist.barrier()
+        launches = g.kernel_launches - launches0
+        stages = g.timing_read()
+        g.timing(False)
+        res = dict(snps_per_s=world * steps * step_snps / elapsed, ms_per_step=1e3 * elapsed / steps, steps=steps,
+                   warmup_blocks=warm_blocks, snps_per_step=step_snps, init_s=init_s, gpu_launches=launches,
+                   clocks=clk.summary(),
+                   stage_ms_per_block={k: v[0] / max(v[1], 1) for k, v in stages.items() if v[1]})
+        trsm_ms = stages["trsm"][0] / max(stages["trsm"][1], 1)
+        alg_tflop = float(n) * n * bs / 1e12  # n^2 flops per SNP column (Sec. 2.2's trsm)
+        achieved = alg_tflop / (trsm_ms / 1e3)
+        if path == "fp64":
+            pk = extra.get("fp64_tflops_cublas")
+            roof = dict(bound="alu", achieved=achieved, peak=pk, unit="TFLOP/s",
+                        frac=achieved / pk if pk else None, traffic=kernel_traffic(path),
+                        peak_basis="FP64 dense GEMM rate measured with cuBLAS DGEMM on this GPU (of measured)")
+        else:
+            bf16 = peaks.get("bf16_tflops") or 1800.0
+            base = bf16 if path == "bf16x3" else (extra.get("tf32_tflops_cublas") or bf16 * 1.1 / 2.25)
+            pk = base / 3.0
+            roof = dict(bound="tensor", achieved=achieved, peak=pk, unit="TFLOP/s", frac=achieved / pk,
+                        traffic=kernel_traffic(path),
+                        peak_basis=(f"{'bf16' if path == 'bf16x3' else 'tf32'} dense tensor peak (of measured) / 3: "
+                                    "three split products per algorithmic product"))
+        res["roofline"] = roof
+        res["trsm_ms_per_launch"] = trsm_ms
+        # end to end: the 8 blocks in pinned host memory, streamed through the block ring every step
+        if not args.no_e2e:
+            Xh = torch.empty((step_snps, n), dtype=torch.int8, pin_memory=True)
+            Xh_np = Xh.numpy()
+            for i in range(NB):
+                Xh_np[i * bs:(i + 1) * bs] = blocks_h[i].T
+            bh = torch.empty((step_snps, p), dtype=torch.float64, pin_memory=True)
+            seh = torch.empty((step_snps, p), dtype=torch.float64, pin_memory=True)
+            sth = torch.empty(step_snps, dtype=torch.int32, pin_memory=True)
+            g.solve_stream(Xh_np[:bs].T, bh.numpy()[:bs].T, seh.numpy()[:bs].T, sth.numpy()[:bs])  # warm
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            for _ in range(steps):
+                g.solve_stream(Xh_np.T, bh.numpy().T, seh.numpy().T, sth.numpy())
+            e2e_s = time.perf_counter() - t1
+            if dist:
+                t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
+                dist.all_reduce(t, op=dist.ReduceOp.MAX)
+                e2e_s = float(t.item())
+            res["e2e"] = dict(value=world * steps * step_snps / e2e_s, unit=UNIT,
+                              h2d_bytes_per_step=n * step_snps, d2h_bytes_per_step=step_snps * (2 * p * 8 + 4))
+            del Xh, bh, seh, sth
+        # keep a few results for the error report against the oracle
+        res["_sample"] = (b[:, :64].cpu().numpy().copy(), se[:, :64].cpu().numpy().copy(),
+                          st[:64].cpu().numpy().copy(), (steps * NB - 1) % NB)
+        results[path] = res
+        g.close()
+        torch.cuda.empty_cache()
+
+    return dict(w=w, s=s, blocks_h=blocks_h, results=results, peaks=peaks, extra=extra, gen_s=gen_s)
+
+
+def cpu_baseline(w, s, X_sample, target_s=12.0):
+    """The oracle as it stands on the host cores: Cholesky first (not timed,
+    as the paper leaves set-up out), then per-SNP GLS on a bounded sample."""
+    import oracle
+    t0 = time.time()
+    L = oracle.potrf(oracle.form_m(s["Phi"], w["h"], w["sigma2"]))
+    chol_s = time.time() - t0
+    t1 = time.time()
+    oracle.gls(L, s["XL"], s["y"], X_sample[:, :16])
+    rate = 16 / max(time.time() - t1, 1e-9)
+    m = int(min(X_sample.shape[1], max(32, rate * target_s)))
+    m -= m % 16 if m > 16 else 0
+    t2 = time.time()
+    r, se, _, st = oracle.gls(L, s["XL"], s["y"], X_sample[:, :m])
+    dt = time.time() - t2
+    return dict(value=m / dt, unit=UNIT, cores=oracle.num_threads(), kind="oracle",
+                sample=f"first {m} SNPs of one bs block at n={w['n']}, p={w['p']}; Cholesky ({chol_s:.1f} s) excluded"), \
+        (L, r, se, st)
+
+
+def error_report(res_path, oracle_out, blocks_h, s, w):
+    """Max / median error of b and se against the FP64 oracle on 64 SNPs."""
+    import oracle
+    from oracle.metrics import compare
+    b, se, st, blk = res_path["_sample"]
+    L = oracle_out[0]
+    r, se_o, _, st_o = oracle.gls(L, s["XL"], s["y"], blocks_h[blk][:, :64])
+    return compare(b, se, st, r, se_o, st_o)
+
+
+def main():
+    args = parse_args()
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local_rank = int(os.environ.get("LOCAL_RANK", "0"))
+
+    if args.impl == "reference":
+        if rank != 0:
+            return 0
+        return run_reference(args, world)
+
+    dist = None
+    if world > 1:
+        import torch
+        import torch.distributed as tdist
+        torch.cuda.set_device(local_rank)
+        tdist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+        dist = tdist
+    out = run_ours(args, rank, world, local_rank, dist)
+    w, results = out["w"], out["results"]
+    if rank != 0:
+        if dist:
+            dist.destroy_process_group()
+        return 0
+
+    cpu = None
+    oracle_out = None
+    if world == 1 and not args.no_cpu_baseline:
+        cpu, oracle_out = cpu_baseline(w, out["s"], out["blocks_h"][0])
+    errors = {}
+    if oracle_out is not None:
+        for path, res in results.items():
+            try:
+                errors[path] = error_report(res, oracle_out, out["blocks_h"], out["s"], w)
+            except Exception as e:  # report, do not hide
+                errors[path] = {"error": repr(e)}
+
+    split = [pp for pp in SPLIT_PATHS if pp in results]
+    head = max(split, key=lambda pp: results[pp]["snps_per_s"]) if split else "fp64"
+    hr = results[head]
+    paths_out = {}
+    for path, res in results.items():
+        r = {k: v for k, v in res.items() if not k.startswith("_")}
+        if path in errors:
+            r["error_vs_oracle"] = errors[path]
+        paths_out[path] = r
+    line = {
+        "metric": METRIC, "value": hr["snps_per_s"], "unit": UNIT, "n_gpus": world, "steps": hr["steps"],
+        "warmup": args.warmup, "ms_per_step": hr["ms_per_step"], "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": {"fp64": "f64", "bf16x3": "bf16x3", "tf32x3": "tf32x3"}[head],
+        "data": "synthetic (seeded kinship, covariates, phenotype and int8 dosages shaped like the paper's n=1e4, p=4 workload)",
+        "config": {"workload": WORKLOAD, "n": w["n"], "p": w["p"], "bs": w["bs"],
+                   "snps_per_step": N_RESIDENT_BLOCKS * w["bs"],
+                   "headline_path": head, "parallelism": f"snp-shard x{world}",
+                   "l2": "inputs larger than L2: 8 resident int8 blocks (328 MB) per step plus the n x n block operator streamed every block"},
+        "roofline": hr["roofline"], "e2e": hr.get("e2e"), "gpu_launches": hr["gpu_launches"],
+        "clocks": hr["clocks"], "cpu_baseline": cpu, "paths": paths_out,
+        "peaks": {"measured_file": {k: out["peaks"].get(k) for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained")},
+                  "measured_here": out["extra"]},
+    }
+    print(json.dumps(line), flush=True)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+def run_reference(args, world):
+    """The oracle arm: the FP64 CPU oracle as it stands, on the host cores."""
+    import gwas_synth
+    import oracle
+    w = workload(args)
+    n, p, bs = w["n"], w["p"], w["bs"]
+    s = gwas_synth.study(n, p, w["k"], w["h"], w["sigma2"])
+    per_step = 64 if n >= 5000 else 512
+    X = gwas_synth.dosages(n, 0, per_step * (args.warmup + args.steps))
+    L = oracle.potrf(oracle.form_m(s["Phi"], w["h"], w["sigma2"]))
+    for i in range(args.warmup):
+        oracle.gls(L, s["XL"], s["y"], X[:, i * per_step:(i + 1) * per_step])
+    t0 = time.time()
+    for i in range(args.warmup, args.warmup + args.steps):
+        oracle.gls(L, s["XL"], s["y"], X[:, i * per_step:(i + 1) * per_step])
+    dt = time.time() - t0
+    v = args.steps * per_step / dt
+    sample = f"{per_step} SNPs per step at n={n}, p={p} (one bs={bs} block would take {bs / v:.0f} s); Cholesky excluded"
+    line = {
+        "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+        "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": WORKLOAD, "n": n, "p": p, "bs": bs, "snps_per_step": per_step,
+                   "headline_path": "oracle-fp64-cpu", "parallelism": "host cores"},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle", "sample": sample},
+        "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,4 +1,5 @@
-"""Error measures used by the parity tests (the readings are stated once here).
+"""Error measures of GPU results against the oracle (test infrastructure; the
+readings are stated once here).
 
 * b: per-SNP normwise relative error ||b - b_ref||_2 / ||b_ref||_2, max over
   SNPs, plus the SE-scaled error max_j |b_j - b_ref_j| / se_ref_j (a

@@ -26,6 +26,7 @@ ERRORS = {
     -5: "GWAS_ERR_IO", -6: "GWAS_ERR_NOMEM", -7: "GWAS_ERR_UNSUPPORTED",
 }
 PRECISIONS = {"fp64": 0, "tf32x3": 1, "bf16x3": 2}
+BUILT_PRECISIONS = ("fp64", "bf16x3", "tf32x3")
 SNP_OK, SNP_SINGULAR = 0, 1
 
 # Every symbol the header declares (checked by the CPU test suite).

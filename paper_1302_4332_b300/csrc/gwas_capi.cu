@@ -12,6 +12,7 @@
 #include <vector>
 
 #include "gwas_internal.cuh"
+#include "trsm_tc.cuh"
 
 using namespace gwas;
 
@@ -35,6 +36,7 @@ struct gwas_ctx {
   double* Xt = nullptr;    // n_pad x bs FP64 (FP64 mode; set-up in every mode)
   Sched* sched = nullptr;  // scheduler counter + tile flags
   size_t sched_bytes = 0;
+  tc::TcState* tcs = nullptr;  // split-precision state (TF32X3 / BF16X3)
   // device staging for host arguments
   std::vector<int8_t*> ring;      // ring_depth slots of n_pad x bs int8
   std::vector<cudaEvent_t> ev_copied, ev_free, ev_out;
@@ -169,7 +171,28 @@ int run_block(gwas_ctx* ctx, const void* X, bool int8_input, int64_t ldx, int nc
     ctx->launches += 1;
     return GWAS_OK;
   }
-  return fail(ctx, GWAS_ERR_UNSUPPORTED, "split-precision solve not built");
+  // split precision: the TMA map of X needs a 16-byte aligned base and leading dimension
+  const int8_t* X8 = static_cast<const int8_t*>(X);
+  if ((reinterpret_cast<uintptr_t>(X8) & 15) || (ldx & 15)) {
+    CK(cudaMemcpy2DAsync(ctx->ring[0], (size_t)ctx->n_pad, X8, (size_t)ldx, (size_t)ctx->n, (size_t)ncols,
+                         cudaMemcpyDeviceToDevice, ctx->stream));
+    X8 = ctx->ring[0];
+    ldx = ctx->n_pad;
+  }
+  {
+    StageMark m(ctx, GWAS_STAGE_TRSM, ctx->stream);
+    int64_t nl = 0;
+    cudaError_t e = tc::run_block(ctx->tcs, X8, ldx, ncols, ctx->stream, &nl);
+    ctx->launches += nl;
+    if (e != cudaSuccess) return fail(ctx, GWAS_ERR_CUDA, "split-precision solve: %s", cudaGetErrorString(e));
+  }
+  {
+    StageMark m(ctx, GWAS_STAGE_REDUCE, ctx->stream);
+    CK(launch_reduce_solve(tc::xt_f32(ctx->tcs), XT_F32, tc::xt_ld(ctx->tcs), ctx->n_pad, ctx->W, ctx->n_pad,
+                           ctx->sc, ctx->q, ncols, b, se, status, ctx->stream));
+  }
+  ctx->launches += 1;
+  return GWAS_OK;
 }
 
 int solve_common(gwas_ctx* ctx, const void* XR, bool int8_input, int64_t ldx, int ncols, double* b, double* se,
@@ -231,6 +254,7 @@ void free_all(gwas_ctx* c) {
   cudaFree(c->sc); cudaFree(c->st); cudaFree(c->Xt); cudaFree(c->sched);
   cudaFree(c->d_b); cudaFree(c->d_se); cudaFree(c->d_status); cudaFree(c->f64_in);
   cudaFreeHost(c->h_b); cudaFreeHost(c->h_se); cudaFreeHost(c->h_status);
+  if (c->tcs) tc::destroy(c->tcs);
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   delete c;
 }
@@ -387,8 +411,16 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
     if (hs.err != DEV_OK) return fail(ctx, GWAS_ERR_TIMEOUT, "set-up solve timed out");
     if (hs.sc_err) return fail(ctx, GWAS_ERR_NOT_SPD, "S_TL = X~_L^T X~_L is singular (collinear covariates)");
 
-    if (ctx->prec != GWAS_FP64)
-      return fail(ctx, GWAS_ERR_UNSUPPORTED, "split-precision modes are not built");
+    // split-precision operands: hi + lo copies of the block operator
+    if (ctx->prec != GWAS_FP64) {
+      int64_t nl = 0;
+      cudaError_t e = tc::create(&ctx->tcs, ctx->prec == GWAS_BF16X3 ? tc::SPLIT_BF16 : tc::SPLIT_TF32, ctx->Aop,
+                                 ctx->n, ctx->n_pad, cfg.bs, ctx->num_sms, ctx->st, ctx->stream, &nl);
+      ctx->launches += nl;
+      if (e != cudaSuccess)
+        return fail(ctx, e == cudaErrorMemoryAllocation ? GWAS_ERR_NOMEM : GWAS_ERR_CUDA, "split set-up: %s",
+                    cudaGetErrorString(e));
+    }
 
     // staging: device ring, outputs, pinned result slots, events
     const int R = ctx->ring_depth;

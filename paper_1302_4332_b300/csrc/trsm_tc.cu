@@ -1,0 +1,520 @@
+// a6, split-precision modes: the blocked triangular solve X~ = L^-1 X on the
+// 5th-generation tensor cores (tcgen05), operands brought in by TMA,
+// accumulators in tensor memory (TMEM).
+//
+// Same dataflow as the FP64 solve (Sec. 2.2's trsm over a block of SNP
+// columns): output tile (k, c) = rows k*TB.., SNP columns c*TN.. is
+//     X~_kc = D_k^-1 X_kc + sum_{j<k} (-D_k^-1 L_kj) X~_jc ,
+// one product chain with the row panel k of the block operator Aop.
+// Precision (the split forms):
+//   * Aop is split once at set-up into hi + lo pieces (BF16 or TF32);
+//   * the int8 dosages X_kc are exact in BF16/TF32: the diagonal step needs
+//     the two products Ahi*X + Alo*X; the cast from int8 happens in shared
+//     memory right after the TMA load (no converted copy in HBM);
+//   * X~_jc (j < k) are FP32 results of earlier tiles, kept in HBM as hi + lo
+//     pieces: three products Ahi*Bhi + Ahi*Blo + Alo*Bhi;
+//   * all products accumulate in FP32 in TMEM; the FP32 X~ goes to the
+//     FP64 reductions.
+//
+// One persistent CTA per SM, 8 warps:
+//   warp 0    tile scheduler + TMA producer (one thread)
+//   warp 1    MMA issuer (one thread)
+//   warps 2-3 int8 -> BF16/TF32 cast of the diagonal block (+ TMEM allocation)
+//   warps 4-7 epilogue: TMEM -> registers -> FP32 X~ and its hi/lo pieces in
+//             HBM, then the tile's finished-flag (release)
+// Tiles are handed out in (k, c) order by an atomic counter; a tile waits
+// (bounded) on the flag of tile (j, c) before loading X~_jc, so the launch
+// cannot deadlock.  Two TMEM accumulators (2 x TN columns) let the epilogue
+// of one tile overlap the products of the next.
+#include <cuda.h>
+#include <cuda_bf16.h>
+
+#include <cstdio>
+
+#include "tc_ptx.cuh"
+#include "trsm_tc.cuh"
+
+namespace gwas {
+namespace tc {
+
+constexpr int TN = 256;      // SNP columns per tile (MMA N)
+constexpr int STAGES = 2;    // operand stages in shared memory
+constexpr int TRING = 2;     // tile-id ring between the scheduler and the other roles
+constexpr int THREADS = 256;
+
+template <bool TF32>
+struct Cfg {
+  static constexpr int ESZ = TF32 ? 4 : 2;       // bytes per operand element
+  static constexpr int KCH = 128 / ESZ;          // K per stage: one 128-byte swizzle row
+  static constexpr int KMMA = TF32 ? 8 : 16;     // K per tcgen05.mma
+  static constexpr int CPB = TB / KCH;           // stages per TB-wide block
+  static constexpr int A_BYTES = TB * 128;       // one piece of A per stage: 16 KB
+  static constexpr int B_BYTES = TN * 128;       // one piece of B per stage: 32 KB
+  static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr int X8_BYTES = TN * TB;       // int8 diagonal block: 32 KB
+  static constexpr int BAR_OFF = STAGES * STAGE_BYTES + X8_BYTES;
+  static constexpr int NBARS = 2 * STAGES + 4 + 2 * TRING + 3;
+  static constexpr int SMEM = 1024 + BAR_OFF + NBARS * 8 + TRING * 4 + 16;
+};
+
+struct TcParams {
+  int P, C, ncols;
+  int* flags;
+  unsigned int* counter;
+  float* xt32;   // FP32 X~ (n_pad x bs); the B "hi" piece in TF32 mode
+  void* bhi;     // BF16 mode: hi piece of X~
+  void* blo;     // lo piece of X~ (BF16 or FP32)
+  int64_t ldt;
+  DevStatus* st;
+};
+
+__device__ __forceinline__ uint32_t tf32_trunc_bits(float x) { return __float_as_uint(x) & 0xFFFFE000u; }
+
+template <bool TF32>
+__global__ void __launch_bounds__(THREADS, 1)
+    trsm_tc_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
+                   const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
+                   const __grid_constant__ CUtensorMap mX8, const TcParams p) {
+  using K = Cfg<TF32>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* x8 = smem + STAGES * K::STAGE_BYTES;
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + K::BAR_OFF);
+  uint64_t* full = bars;
+  uint64_t* empty = full + STAGES;
+  uint64_t* acc_full = empty + STAGES;
+  uint64_t* acc_empty = acc_full + 2;
+  uint64_t* tile_full = acc_empty + 2;
+  uint64_t* tile_empty = tile_full + TRING;
+  uint64_t* x8_full = tile_empty + TRING;
+  uint64_t* x8_empty = x8_full + 1;
+  uint64_t* drain = x8_empty + 1;
+  int* tile_ring = reinterpret_cast<int*>(drain + 1);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tile_ring + TRING);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntiles = p.P * p.C;
+  DevStatus* st = p.st;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      ptx::mbar_init(&full[s], 2);   // producer (+tx) and producer-or-cast
+      ptx::mbar_init(&empty[s], 1);  // MMA commit
+    }
+    for (int a = 0; a < 2; ++a) {
+      ptx::mbar_init(&acc_full[a], 1);
+      ptx::mbar_init(&acc_empty[a], 4);  // one arrival per epilogue warp
+    }
+    for (int i = 0; i < TRING; ++i) {
+      ptx::mbar_init(&tile_full[i], 1);
+      ptx::mbar_init(&tile_empty[i], 7);  // MMA warp + 2 cast warps + 4 epilogue warps
+    }
+    ptx::mbar_init(x8_full, 1);
+    ptx::mbar_init(x8_empty, 1);
+    ptx::mbar_init(drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    ptx::prefetch_tensormap(&mAhi);
+    ptx::prefetch_tensormap(&mAlo);
+    ptx::prefetch_tensormap(&mBhi);
+    ptx::prefetch_tensormap(&mBlo);
+    ptx::prefetch_tensormap(&mX8);
+  }
+  if (warp == 2) {
+    ptx::tmem_alloc(tmem_slot, 2 * TN);
+    ptx::tmem_relinquish();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------ scheduler + TMA producer
+    if (lane == 0) {
+      uint32_t cnt = 0;
+      for (int it = 0;; ++it) {
+        const int slot = it % TRING;
+        const uint32_t use = it / TRING;
+        if (!ptx::mbar_wait(&tile_empty[slot], (use & 1) ^ 1, st)) break;
+        int t = ptx::aborting(st) ? ntiles : (int)atomicAdd(p.counter, 1u);
+        if (t > ntiles) t = ntiles;
+        tile_ring[slot] = t;
+        ptx::mbar_arrive(&tile_full[slot]);
+        if (t >= ntiles) break;
+        const int k = t / p.C, c = t % p.C;
+        if (!ptx::mbar_wait(x8_empty, (it & 1) ^ 1, st)) break;
+        ptx::mbar_arrive_expect_tx(x8_full, K::X8_BYTES);
+        ptx::tma_load_2d(x8, &mX8, x8_full, k * TB, c * TN);
+        bool ok = true;
+        for (int jj = 0; jj <= k && ok; ++jj) {
+          const int j = (jj == 0) ? k : jj - 1;
+          if (jj > 0) {
+            if (!ptx::wait_flag(&p.flags[j * p.C + c], st)) { ok = false; break; }
+            ptx::fence_proxy_async_global();
+          }
+          for (int h = 0; h < K::CPB; ++h, ++cnt) {
+            const int s = cnt % STAGES;
+            const uint32_t r = cnt / STAGES;
+            if (!ptx::mbar_wait(&empty[s], (r & 1) ^ 1, st)) { ok = false; break; }
+            uint8_t* sb = smem + s * K::STAGE_BYTES;
+            const int kx = j * TB + h * K::KCH;
+            if (jj == 0) {
+              ptx::mbar_arrive_expect_tx(&full[s], 2 * K::A_BYTES);
+              ptx::tma_load_2d(sb, &mAhi, &full[s], kx, k * TB);
+              ptx::tma_load_2d(sb + K::A_BYTES, &mAlo, &full[s], kx, k * TB);
+            } else {
+              ptx::mbar_arrive_expect_tx(&full[s], 2 * K::A_BYTES + 2 * K::B_BYTES);
+              ptx::tma_load_2d(sb, &mAhi, &full[s], kx, k * TB);
+              ptx::tma_load_2d(sb + K::A_BYTES, &mAlo, &full[s], kx, k * TB);
+              ptx::tma_load_2d(sb + 2 * K::A_BYTES, &mBhi, &full[s], kx, c * TN);
+              ptx::tma_load_2d(sb + 2 * K::A_BYTES + K::B_BYTES, &mBlo, &full[s], kx, c * TN);
+              ptx::mbar_arrive(&full[s]);
+            }
+          }
+        }
+        if (!ok) break;
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------------------ MMA issuer
+    if (lane == 0) {
+      constexpr uint32_t idesc = ptx::idesc_f32acc<TF32>(TB, TN);
+      uint32_t cnt = 0;
+      for (int it = 0;; ++it) {
+        const int slot = it % TRING;
+        const uint32_t use = it / TRING;
+        if (!ptx::mbar_wait(&tile_full[slot], use & 1, st)) break;
+        const int t = tile_ring[slot];
+        ptx::mbar_arrive(&tile_empty[slot]);
+        if (t >= ntiles) break;
+        const int k = t / p.C;
+        const int a = it & 1;
+        const uint32_t u = it >> 1;
+        if (!ptx::mbar_wait(&acc_empty[a], (u & 1) ^ 1, st)) break;
+        ptx::tc_fence_after();
+        const uint32_t d = tmem_base + a * TN;
+        uint32_t accumulate = 0;
+        bool ok = true;
+        for (int jj = 0; jj <= k && ok; ++jj) {
+          for (int h = 0; h < K::CPB; ++h, ++cnt) {
+            const int s = cnt % STAGES;
+            const uint32_t r = cnt / STAGES;
+            if (!ptx::mbar_wait(&full[s], r & 1, st)) { ok = false; break; }
+            ptx::tc_fence_after();
+            const uint32_t base = ptx::smem_u32(smem + s * K::STAGE_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < K::KCH / K::KMMA; ++kk) {
+              const uint32_t off = kk * K::KMMA * K::ESZ;
+              const uint64_t ahi = ptx::sdesc_k128(base + off);
+              const uint64_t alo = ptx::sdesc_k128(base + K::A_BYTES + off);
+              const uint64_t bhi = ptx::sdesc_k128(base + 2 * K::A_BYTES + off);
+              const uint64_t blo = ptx::sdesc_k128(base + 2 * K::A_BYTES + K::B_BYTES + off);
+              ptx::mma<TF32>(d, alo, bhi, idesc, accumulate);
+              accumulate = 1;
+              if (jj > 0) ptx::mma<TF32>(d, ahi, blo, idesc, 1);
+              ptx::mma<TF32>(d, ahi, bhi, idesc, 1);
+            }
+            ptx::mma_commit(&empty[s]);
+          }
+        }
+        if (!ok) break;
+        ptx::mma_commit(&acc_full[a]);
+      }
+    }
+  } else if (warp < 4) {
+    // ---------------------------------------- int8 -> BF16/TF32 cast (diagonal block)
+    // The 64 threads decide together (group_and) after every wait.
+    const int ct = threadIdx.x - 64;  // 0..63
+    constexpr int E = 16 / K::ESZ;    // elements per 16-byte chunk
+    uint32_t cnt = 0;
+    for (int it = 0;; ++it) {
+      const int slot = it % TRING;
+      const uint32_t use = it / TRING;
+      if (!ptx::group_and(2, 64, ptx::mbar_wait(&tile_full[slot], use & 1, st))) break;
+      const int t = tile_ring[slot];
+      ptx::named_bar(2, 64);
+      if (lane == 0) ptx::mbar_arrive(&tile_empty[slot]);
+      if (t >= ntiles) break;
+      const int k = t / p.C;
+      if (!ptx::group_and(2, 64, ptx::mbar_wait(x8_full, it & 1, st))) break;
+      bool ok = true;
+      for (int h = 0; h < K::CPB; ++h) {
+        const int s = (cnt + h) % STAGES;
+        const uint32_t r = (cnt + h) / STAGES;
+        if (!ptx::group_and(2, 64, ptx::mbar_wait(&empty[s], (r & 1) ^ 1, st))) { ok = false; break; }
+        uint8_t* bh = smem + s * K::STAGE_BYTES + 2 * K::A_BYTES;
+        for (int col = ct; col < TN; col += 64) {
+          const int8_t* src = reinterpret_cast<const int8_t*>(x8 + col * TB + h * K::KCH);
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            uint32_t w[4];
+            if constexpr (TF32) {
+              const char4 v = *reinterpret_cast<const char4*>(src + q * E);
+              w[0] = __float_as_uint((float)v.x);
+              w[1] = __float_as_uint((float)v.y);
+              w[2] = __float_as_uint((float)v.z);
+              w[3] = __float_as_uint((float)v.w);
+            } else {
+              const char4 v0 = *reinterpret_cast<const char4*>(src + q * E);
+              const char4 v1 = *reinterpret_cast<const char4*>(src + q * E + 4);
+              const signed char e8[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+              for (int i = 0; i < 4; ++i) {
+                const __nv_bfloat162 b2 = __floats2bfloat162_rn((float)e8[2 * i], (float)e8[2 * i + 1]);
+                w[i] = *reinterpret_cast<const uint32_t*>(&b2);
+              }
+            }
+            *reinterpret_cast<uint4*>(bh + col * 128 + ((q ^ (col & 7)) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
+          }
+        }
+        ptx::fence_proxy_async_shared();
+        ptx::named_bar(2, 64);
+        if (ct == 0) ptx::mbar_arrive(&full[s]);
+      }
+      if (!ok) break;
+      if (ct == 0) ptx::mbar_arrive(x8_empty);
+      cnt += K::CPB * (k + 1);
+    }
+  } else {
+    // ----------------------------------------------------------------- epilogue
+    // The 128 threads decide together (group_and) after every wait.
+    const int e = warp - 4;  // TMEM lanes 32e .. 32e + 31
+    for (int it = 0;; ++it) {
+      const int slot = it % TRING;
+      const uint32_t use = it / TRING;
+      if (!ptx::group_and(1, 128, ptx::mbar_wait(&tile_full[slot], use & 1, st))) break;
+      const int t = tile_ring[slot];
+      ptx::named_bar(1, 128);
+      if (lane == 0) ptx::mbar_arrive(&tile_empty[slot]);
+      if (t >= ntiles) break;
+      const int k = t / p.C, c = t % p.C;
+      const int a = it & 1;
+      const uint32_t u = it >> 1;
+      if (!ptx::group_and(1, 128, ptx::mbar_wait(&acc_full[a], u & 1, st))) break;
+      ptx::tc_fence_after();
+      const int64_t row = (int64_t)k * TB + 32 * e + lane;
+#pragma unroll 1
+      for (int ch = 0; ch < TN / 32; ++ch) {
+        uint32_t v[32];
+        ptx::tmem_ld_32x32b_x32(tmem_base + (static_cast<uint32_t>(32 * e) << 16) + a * TN + ch * 32, v);
+        ptx::tmem_ld_wait();
+#pragma unroll
+        for (int i = 0; i < 32; ++i) {
+          const int col = c * TN + ch * 32 + i;
+          if (col < p.ncols) {
+            const float x = __uint_as_float(v[i]);
+            const int64_t idx = (int64_t)col * p.ldt + row;
+            p.xt32[idx] = x;
+            if constexpr (TF32) {
+              static_cast<float*>(p.blo)[idx] = x - __uint_as_float(tf32_trunc_bits(x));
+            } else {
+              const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+              static_cast<__nv_bfloat16*>(p.bhi)[idx] = hi;
+              static_cast<__nv_bfloat16*>(p.blo)[idx] = __float2bfloat16_rn(x - __bfloat162float(hi));
+            }
+          }
+        }
+      }
+      ptx::tc_fence_before();
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&acc_empty[a]);
+      ptx::named_bar(1, 128);
+      if (e == 0 && lane == 0) {
+        ptx::fence_proxy_async_global();
+        __threadfence();
+        ptx::st_release(&p.flags[k * p.C + c], 1);
+      }
+    }
+  }
+
+  // ---------------------------------------------------------------- teardown
+  if (warp == 1 && lane == 0) {
+    // every MMA this CTA issued has completed before TMEM is released
+    ptx::mma_commit(drain);
+    const long long t0 = ptx::globaltimer();
+    while (!ptx::mbar_try_wait(drain, 0) && ptx::globaltimer() - t0 < 100000000LL) {
+    }
+  }
+  if (ptx::aborting(st)) {
+    // an aborted launch may still have TMA copies in flight into this CTA's
+    // shared memory: give them time to land before the CTA retires
+    const long long t0 = ptx::globaltimer();
+    while (ptx::globaltimer() - t0 < 2000000LL) {
+    }
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  if (warp == 2) ptx::tmem_dealloc(tmem_base, 2 * TN);
+}
+
+// ------------------------------------------------------------ set-up kernels
+template <bool TF32>
+__global__ void split_aop_kernel(const double* __restrict__ A, int64_t count, void* __restrict__ hi,
+                                 void* __restrict__ lo) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
+    const double a = A[e];
+    if constexpr (TF32) {
+      uint32_t hb;
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"((float)a));
+      const float h = __uint_as_float(hb);
+      static_cast<float*>(hi)[e] = h;
+      static_cast<float*>(lo)[e] = (float)(a - (double)h);
+    } else {
+      const __nv_bfloat16 h = __double2bfloat16(a);
+      static_cast<__nv_bfloat16*>(hi)[e] = h;
+      static_cast<__nv_bfloat16*>(lo)[e] = __double2bfloat16(a - (double)__bfloat162float(h));
+    }
+  }
+}
+
+// ------------------------------------------------------------------- host side
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+struct TcState {
+  bool tf32 = false;
+  int n = 0, n_pad = 0, bs = 0, P = 0, num_sms = 0;
+  void* ahi = nullptr;
+  void* alo = nullptr;
+  float* xt32 = nullptr;
+  void* bhi = nullptr;
+  void* blo = nullptr;
+  int64_t ldt = 0;
+  unsigned int* sched = nullptr;  // [0] counter, flags from +32
+  size_t sched_bytes = 0;
+  DevStatus* st = nullptr;
+  CUtensorMap mAhi, mAlo, mBhi, mBlo;
+  EncodeTiledFn encode = nullptr;
+};
+
+static cudaError_t get_encode(EncodeTiledFn* fn) {
+  void* f = nullptr;
+  cudaDriverEntryPointQueryResult q;
+  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q);
+  if (e != cudaSuccess) return e;
+  if (q != cudaDriverEntryPointSuccess || !f) return cudaErrorNotSupported;
+  *fn = reinterpret_cast<EncodeTiledFn>(f);
+  return cudaSuccess;
+}
+
+// 2D tiled map: dims {inner, outer}, outer stride in bytes, box {bi, bo}.
+static cudaError_t make_map(EncodeTiledFn enc, CUtensorMap* m, CUtensorMapDataType dt, const void* base,
+                            uint64_t inner, uint64_t outer, uint64_t stride_bytes, uint32_t bi, uint32_t bo,
+                            bool swizzle128) {
+  cuuint64_t dims[2] = {inner, outer};
+  cuuint64_t strides[1] = {stride_bytes};
+  cuuint32_t box[2] = {bi, bo};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = enc(m, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                   swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+template <bool TF32>
+static cudaError_t set_smem_attr() {
+  return cudaFuncSetAttribute(trsm_tc_kernel<TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<TF32>::SMEM);
+}
+
+cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_pad, int bs, int num_sms,
+                   DevStatus* st, cudaStream_t s, int64_t* launches) {
+  *out = nullptr;
+  TcState* t = new TcState;
+  t->tf32 = (split == SPLIT_TF32);
+  t->n = n;
+  t->n_pad = n_pad;
+  t->bs = bs;
+  t->P = n_pad / TB;
+  t->num_sms = num_sms;
+  t->st = st;
+  t->ldt = n_pad;
+  const size_t esz = t->tf32 ? 4 : 2;
+  const size_t n2 = (size_t)n_pad * n_pad;
+  const int Cmax = (bs + TN - 1) / TN;
+  cudaError_t e;
+#define TRY(x)              \
+  do {                      \
+    e = (x);                \
+    if (e != cudaSuccess) { \
+      destroy(t);           \
+      return e;             \
+    }                       \
+  } while (0)
+  TRY(get_encode(&t->encode));
+  TRY(cudaMalloc(&t->ahi, esz * n2));
+  TRY(cudaMalloc(&t->alo, esz * n2));
+  TRY(cudaMalloc(&t->xt32, sizeof(float) * (size_t)n_pad * bs));
+  if (!t->tf32) TRY(cudaMalloc(&t->bhi, 2 * (size_t)n_pad * bs));
+  TRY(cudaMalloc(&t->blo, esz * (size_t)n_pad * bs));
+  t->sched_bytes = 128 + sizeof(int) * (size_t)t->P * Cmax;
+  TRY(cudaMalloc(&t->sched, t->sched_bytes));
+  TRY(cudaMemsetAsync(t->sched, 0, t->sched_bytes, s));
+  if (t->tf32)
+    split_aop_kernel<true><<<1184, 256, 0, s>>>(Aop, (int64_t)n2, t->ahi, t->alo);
+  else
+    split_aop_kernel<false><<<1184, 256, 0, s>>>(Aop, (int64_t)n2, t->ahi, t->alo);
+  ++*launches;
+  TRY(cudaGetLastError());
+  const CUtensorMapDataType dt = t->tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const uint32_t kch = t->tf32 ? Cfg<true>::KCH : Cfg<false>::KCH;
+  TRY(make_map(t->encode, &t->mAhi, dt, t->ahi, n_pad, n_pad, esz * n_pad, kch, TB, true));
+  TRY(make_map(t->encode, &t->mAlo, dt, t->alo, n_pad, n_pad, esz * n_pad, kch, TB, true));
+  const void* bhi_base = t->tf32 ? static_cast<const void*>(t->xt32) : t->bhi;
+  TRY(make_map(t->encode, &t->mBhi, dt, bhi_base, n_pad, bs, esz * n_pad, kch, TN, true));
+  TRY(make_map(t->encode, &t->mBlo, dt, t->blo, n_pad, bs, esz * n_pad, kch, TN, true));
+  TRY(t->tf32 ? set_smem_attr<true>() : set_smem_attr<false>());
+#undef TRY
+  *out = t;
+  return cudaSuccess;
+}
+
+cudaError_t run_block(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaStream_t s, int64_t* launches) {
+  if (ncols <= 0) return cudaSuccess;
+  if (ncols > t->bs || (reinterpret_cast<uintptr_t>(X) & 15) || (ldx & 15) || ldx < t->n)
+    return cudaErrorInvalidValue;
+  CUtensorMap mX8;
+  cudaError_t e = make_map(t->encode, &mX8, CU_TENSOR_MAP_DATA_TYPE_UINT8, X, (uint64_t)t->n, (uint64_t)ncols,
+                           (uint64_t)ldx, TB, TN, false);
+  if (e != cudaSuccess) return e;
+  const int C = (ncols + TN - 1) / TN;
+  const int ntiles = t->P * C;
+  e = cudaMemsetAsync(t->sched, 0, 128 + sizeof(int) * (size_t)t->P * C, s);
+  if (e != cudaSuccess) return e;
+  TcParams p;
+  p.P = t->P;
+  p.C = C;
+  p.ncols = ncols;
+  p.counter = t->sched;
+  p.flags = reinterpret_cast<int*>(t->sched + 32);
+  p.xt32 = t->xt32;
+  p.bhi = t->bhi;
+  p.blo = t->blo;
+  p.ldt = t->ldt;
+  p.st = t->st;
+  const int grid = ntiles < t->num_sms ? ntiles : t->num_sms;
+  if (t->tf32)
+    trsm_tc_kernel<true><<<grid, THREADS, Cfg<true>::SMEM, s>>>(t->mAhi, t->mAlo, t->mBhi, t->mBlo, mX8, p);
+  else
+    trsm_tc_kernel<false><<<grid, THREADS, Cfg<false>::SMEM, s>>>(t->mAhi, t->mAlo, t->mBhi, t->mBlo, mX8, p);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+const float* xt_f32(const TcState* t) { return t->xt32; }
+int64_t xt_ld(const TcState* t) { return t->ldt; }
+
+void destroy(TcState* t) {
+  if (!t) return;
+  cudaFree(t->ahi);
+  cudaFree(t->alo);
+  cudaFree(t->xt32);
+  cudaFree(t->bhi);
+  cudaFree(t->blo);
+  cudaFree(t->sched);
+  delete t;
+}
+
+}  // namespace tc
+}  // namespace gwas

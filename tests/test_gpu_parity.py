@@ -8,7 +8,7 @@ import pytest
 import gwas_synth
 import oracle
 import paper_1302_4332_b300 as gw
-from metrics import compare
+from oracle.metrics import compare
 
 pytestmark = pytest.mark.gpu
 
@@ -139,3 +139,77 @@ def test_stream_matches_blocks(small_study):
         b, se_g, st_g = g.solve_stream(Xh)
     e = compare(b, se_g, st_g, r[:, :1900], se[:, :1900], st[:1900])
     assert e["b_norm"] <= TOL64 and e["se_rel"] <= TOL64, e
+
+
+# ---------------------------------------------------------------- split precision
+TOL_SPLIT = 1e-5
+SPLITS = ("bf16x3", "tf32x3")
+
+
+@pytest.mark.parametrize("prec", SPLITS)
+def test_split_precision_parity(small_study, prec):
+    s, X, L, (r, se, st) = small_study
+    with gw.GLS(s["Phi"], s["XL"], s["y"], s["h"], s["sigma2"], precision=prec, bs=1024) as g:
+        outs = [g.solve_block(X[:, c0:c0 + 1024]) for c0 in range(0, X.shape[1], 1024)]
+    b = np.concatenate([o[0] for o in outs], axis=1)
+    se_g = np.concatenate([o[1] for o in outs], axis=1)
+    st_g = np.concatenate([o[2] for o in outs])
+    e = compare(b, se_g, st_g, r, se, st)
+    print(prec, e)
+    assert e["b_norm"] <= TOL_SPLIT and e["se_rel"] <= TOL_SPLIT, e
+
+
+@pytest.mark.parametrize("prec", SPLITS)
+@pytest.mark.parametrize("n,p,m", [(1, 1, 3), (127, 4, 63), (129, 2, 257), (300, 7, 300), (1000, 4, 513)])
+def test_split_ragged_shapes(prec, n, p, m):
+    s, X, L, (r, se, st) = _case(n, p, max(2 * n, 4), 0.5, sigma2=1.3, m=m)
+    with gw.GLS(s["Phi"], s["XL"] if p > 1 else None, s["y"], 0.5, 1.3, precision=prec, bs=max(m, 1)) as g:
+        b, se_g, st_g = g.solve_block(X)
+    e = compare(b, se_g, st_g, r, se, st)
+    assert e["b_norm"] <= TOL_SPLIT and e["se_rel"] <= TOL_SPLIT, (prec, e)
+
+
+@pytest.mark.parametrize("prec", SPLITS)
+def test_split_unaligned_device_input(prec):
+    import torch
+    s, X, L, (r, se, st) = _case(200, 4, 400, 0.6, m=40)
+    # device input with a leading dimension that is not a multiple of 16
+    buf = torch.zeros((40, 203), dtype=torch.int8, device="cuda")
+    buf[:, :200] = torch.from_numpy(np.ascontiguousarray(X.T)).cuda()
+    Xd = buf.T[:200]
+    assert Xd.stride(1) == 203
+    with gw.GLS(s["Phi"], s["XL"], s["y"], 0.6, 1.0, precision=prec, bs=64) as g:
+        b, se_g, st_g = g.solve_block(Xd)
+        g.synchronize()
+    e = compare(b.cpu().numpy(), se_g.cpu().numpy(), st_g.cpu().numpy(), r, se, st)
+    assert e["b_norm"] <= TOL_SPLIT and e["se_rel"] <= TOL_SPLIT, e
+
+
+@pytest.mark.parametrize("prec", SPLITS)
+def test_split_singular_and_near_singular(prec):
+    """A monomorphic SNP is flagged; a SNP with one deviating sample is a valid
+    but ill-conditioned design (S_BR / d^2 ~ 4n): its b is checked against the
+    oracle in units of the oracle's standard error."""
+    s, X, L, _ = _case(200, 4, 400, 0.6, m=6)
+    X[:, 1] = 2
+    X[:, 3] = 2
+    X[17, 3] = 1
+    r, se, _, st = oracle.gls(L, s["XL"], s["y"], X)
+    with gw.GLS(s["Phi"], s["XL"], s["y"], 0.6, 1.0, precision=prec, bs=64) as g:
+        b, se_g, st_g = g.solve_block(X)
+    assert st_g.tolist() == st.tolist() == [0, 1, 0, 0, 0, 0]
+    assert np.isnan(b[:, 1]).all()
+    well = [0, 2, 4, 5]
+    e = compare(b[:, well], se_g[:, well], st_g[well], r[:, well], se[:, well], st[well])
+    assert e["b_norm"] <= TOL_SPLIT and e["se_rel"] <= TOL_SPLIT, e
+    e3 = compare(b[:, [3]], se_g[:, [3]], st_g[[3]], r[:, [3]], se[:, [3]], st[[3]])
+    assert e3["b_se_scaled"] <= 1e-3 and e3["se_rel"] <= 1e-3, e3
+
+
+@pytest.mark.parametrize("prec", SPLITS)
+def test_split_stream(small_study, prec):
+    s, X, L, (r, se, st) = small_study
+    with gw.GLS(s["Phi"], s["XL"], s["y"], s["h"], s["sigma2"], precision=prec, bs=512, ring_depth=3) as g:
+        b, se_g, st_g = g.solve_stream(np.asfortranarray(X[:, :1800]))
+    e = compare(b, se_g, st_g, r[:, :1800], se[:, :1800], st[:1800])
+    assert e["b_norm"] <= TOL_SPLIT and e["se_rel"] <= TOL_SPLIT, e
