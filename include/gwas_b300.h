@@ -129,6 +129,32 @@ int gwas_solve_block_f64(gwas_ctx *ctx, const double *XR, int64_t ldx, int ncols
 int gwas_solve_stream(gwas_ctx *ctx, const int8_t *XR_host, int64_t ldx, int64_t m, double *b_host,
                       double *se_host, int *status_host);
 
+/* gwas_solve_block without any allocation, FP64 solve only.  The paper has no
+ * counterpart: this entry point exists for callers that cannot allocate
+ * device memory when they solve -- e.g. a process whose device memory is
+ * held by another framework's caching allocator, or a service that must not
+ * call cudaMalloc once it is serving.  They run gwas_init once at start-up;
+ * this call then allocates nothing (no cudaMalloc, no cudaFree, no library
+ * routine that allocates).
+ *   XR, b, se, status: DEVICE pointers only (host pointers: GWAS_ERR_ARG);
+ *   layouts and outputs as gwas_solve_block; asynchronous on the context's
+ *   stream (device-side errors surface at gwas_synchronize).
+ * Scratch: one fixed device array of GWAS_STATIC_SCRATCH_BYTES inside the
+ * library (CUDA sets it aside when the library's device code is loaded on a
+ * device and keeps it until the process exits).  A call needs
+ *   256-byte-rounded (128 + 4 * ceil(n/128) * ceil(ncols/64)) + 8 * n_pad * ncols
+ * bytes, n_pad = n rounded up to 128 (at n = 10,000: up to 414 columns); a
+ * larger call returns GWAS_ERR_ARG.  Every call uses the same array and it
+ * keeps the previous call's contents (the call clears what must start at
+ * zero): calls whose GPU work overlaps -- two streams, or two contexts at
+ * once -- race on it and give wrong results.  The first call on a device looks
+ * the array's device address up (cudaGetSymbolAddress); make that first call
+ * before any stream capture.
+ * Errors: GWAS_ERR_ARG, GWAS_ERR_CUDA. */
+#define GWAS_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
+int gwas_solve_block_static(gwas_ctx *ctx, const int8_t *XR, int64_t ldx, int ncols, double *b, double *se,
+                            int *status);
+
 /* Waits for the context's queued work and reports device-side errors
  * (GWAS_ERR_TIMEOUT when a bounded wait inside a kernel gave up). */
 int gwas_synchronize(gwas_ctx *ctx);

@@ -34,7 +34,7 @@ EXPORTS = (
     "gwas_config_default", "gwas_init", "gwas_solve_block", "gwas_solve_block_f64", "gwas_solve_stream",
     "gwas_synchronize", "gwas_set_stream", "gwas_get_info", "gwas_not_spd_index", "gwas_copy_factor",
     "gwas_kernel_launches", "gwas_strerror", "gwas_last_error_detail", "gwas_destroy",
-    "gwas_timing_enable", "gwas_timing_read",
+    "gwas_timing_enable", "gwas_timing_read", "gwas_solve_block_static",
 )
 STAGES = ("h2d", "trsm", "reduce", "d2h")
 
@@ -101,6 +101,8 @@ def load(path: str | None = None):
     lib.gwas_timing_enable.restype = c_int
     lib.gwas_timing_read.argtypes = [vp, ctypes.POINTER(dp), ctypes.POINTER(i64)]
     lib.gwas_timing_read.restype = c_int
+    lib.gwas_solve_block_static.argtypes = [vp, vp, i64, c_int, vp, vp, vp]
+    lib.gwas_solve_block_static.restype = c_int
     lib.gwas_destroy.argtypes = [vp]
     lib.gwas_destroy.restype = None
     _lib = lib

@@ -598,3 +598,20 @@ int64_t gwas_kernel_launches(const gwas_ctx* ctx) { return ctx ? ctx->launches :
 void gwas_destroy(gwas_ctx* ctx) { free_all(ctx); }
 
 }  // extern "C"
+
+bool gwas::ctx_view(gwas_ctx* ctx, CtxView* v) {
+  if (!ctx || !v) return false;
+  v->dev = ctx->dev;
+  v->num_sms = ctx->num_sms;
+  v->n = ctx->n;
+  v->q = ctx->q;
+  v->n_pad = ctx->n_pad;
+  v->P = ctx->P;
+  v->stream = ctx->stream;
+  v->Aop = ctx->Aop;
+  v->W = ctx->W;
+  v->sc = ctx->sc;
+  v->st = ctx->st;
+  v->launches = &ctx->launches;
+  return true;
+}

@@ -110,4 +110,17 @@ cudaError_t launch_reduce_solve(const void* Xt, XtKind kind, int64_t ldt, int ro
                                 int64_t ldw, const SolveConsts* sc, int q, int ncols, double* b, double* se,
                                 int* status, cudaStream_t s);
 
+// Read-only view of a context's study data and stream, for entry points that
+// live outside the context's own file.
+struct CtxView {
+  int dev, num_sms, n, q, n_pad, P;
+  cudaStream_t stream;
+  const double* Aop;
+  const double* W;
+  const SolveConsts* sc;
+  DevStatus* st;
+  int64_t* launches;
+};
+bool ctx_view(gwas_ctx* ctx, CtxView* v);
+
 }  // namespace gwas
