@@ -37,6 +37,8 @@ struct gwas_ctx {
   Sched* sched = nullptr;  // scheduler counter + tile flags
   size_t sched_bytes = 0;
   tc::TcState* tcs = nullptr;  // split-precision state (TF32X3 / BF16X3)
+  float* W32 = nullptr;        // W in FP32, row-major (split-path reductions)
+  bool intercept = false;      // X_L[:, 0] == 1 for every sample
   // device staging for host arguments
   std::vector<int8_t*> ring;      // ring_depth slots of n_pad x bs int8
   std::vector<cudaEvent_t> ev_copied, ev_free, ev_out;
@@ -189,7 +191,7 @@ int run_block(gwas_ctx* ctx, const void* X, bool int8_input, int64_t ldx, int nc
   {
     StageMark m(ctx, GWAS_STAGE_REDUCE, ctx->stream);
     CK(launch_reduce_solve(tc::xt_f32(ctx->tcs), XT_F32, tc::xt_ld(ctx->tcs), ctx->n_pad, ctx->W, ctx->n_pad,
-                           ctx->sc, ctx->q, ncols, b, se, status, ctx->stream));
+                           ctx->sc, ctx->q, ncols, b, se, status, ctx->stream, ctx->W32, tc::shift_of(ctx->tcs)));
   }
   ctx->launches += 1;
   return GWAS_OK;
@@ -252,7 +254,7 @@ void free_all(gwas_ctx* c) {
   for (auto ev : c->event_pool) cudaEventDestroy(ev);
   cudaFree(c->L); cudaFree(c->Dinv); cudaFree(c->Aop); cudaFree(c->W); cudaFree(c->G);
   cudaFree(c->sc); cudaFree(c->st); cudaFree(c->Xt); cudaFree(c->sched);
-  cudaFree(c->d_b); cudaFree(c->d_se); cudaFree(c->d_status); cudaFree(c->f64_in);
+  cudaFree(c->d_b); cudaFree(c->d_se); cudaFree(c->d_status); cudaFree(c->f64_in); cudaFree(c->W32);
   cudaFreeHost(c->h_b); cudaFreeHost(c->h_se); cudaFreeHost(c->h_status);
   if (c->tcs) tc::destroy(c->tcs);
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
@@ -388,6 +390,12 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
       CK(cudaMemcpyAsync(XLy, XL, sizeof(double) * (size_t)n * ctx->q,
                          d ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
     }
+    if (ctx->q) {
+      std::vector<double> col0(n);
+      CK(cudaMemcpyAsync(col0.data(), XLy, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      ctx->intercept = std::all_of(col0.begin(), col0.end(), [](double v) { return v == 1.0; });
+    }
     CK(cudaMemcpyAsync(XLy + (size_t)n * ctx->q, y, sizeof(double) * (size_t)n,
                        is_device_ptr(y) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
     {
@@ -415,11 +423,15 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
     if (ctx->prec != GWAS_FP64) {
       int64_t nl = 0;
       cudaError_t e = tc::create(&ctx->tcs, ctx->prec == GWAS_BF16X3 ? tc::SPLIT_BF16 : tc::SPLIT_TF32, ctx->Aop,
-                                 ctx->n, ctx->n_pad, cfg.bs, ctx->num_sms, ctx->st, ctx->stream, &nl);
+                                 ctx->n, ctx->n_pad, cfg.bs, ctx->num_sms, ctx->intercept, ctx->st, ctx->stream,
+                                 &nl);
       ctx->launches += nl;
       if (e != cudaSuccess)
         return fail(ctx, e == cudaErrorMemoryAllocation ? GWAS_ERR_NOMEM : GWAS_ERR_CUDA, "split set-up: %s",
                     cudaGetErrorString(e));
+      CK(dmalloc(&ctx->W32, sizeof(float) * np * w32_stride(ctx->q)));
+      CK(launch_make_w32(ctx->W, ctx->n_pad, ctx->n_pad, ctx->q, ctx->W32, ctx->stream));
+      ctx->launches += 1;
     }
 
     // staging: device ring, outputs, pinned result slots, events

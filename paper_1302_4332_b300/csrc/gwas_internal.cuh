@@ -51,6 +51,7 @@ struct SolveConsts {
   double zT[QMAX];
   double b0[QMAX];
   double dSTL[QMAX];
+  double stl00;  // S_TL[0][0] (uncentered S_BR of a shifted SNP, see reduce_solve.cu)
 };
 
 // Scheduler state of one persistent triangular-solve launch.
@@ -106,9 +107,17 @@ cudaError_t launch_solve_consts(const double* G, int q, SolveConsts* sc, DevStat
 
 // a7 + a8: per-SNP reductions against W and the p x p solve.
 enum XtKind : int { XT_F64 = 0, XT_F32 = 1 };
+// XT_F64 reads W (FP64, column-major, ldw); XT_F32 reads W32 (FP32, row-major,
+// row stride w32_stride(q), made by launch_make_w32).  shift (XT_F32 only, may
+// be null): per-SNP integer c_i the SNP column was shifted by before the solve
+// (x' = x - c_i * X_L[:, 0], X_L[:, 0] the intercept); results are mapped back
+// to the unshifted design.
 cudaError_t launch_reduce_solve(const void* Xt, XtKind kind, int64_t ldt, int rows, const double* W,
                                 int64_t ldw, const SolveConsts* sc, int q, int ncols, double* b, double* se,
-                                int* status, cudaStream_t s);
+                                int* status, cudaStream_t s, const float* W32 = nullptr,
+                                const int8_t* shift = nullptr);
+int w32_stride(int q);
+cudaError_t launch_make_w32(const double* W, int64_t ldw, int rows, int q, float* W32, cudaStream_t s);
 
 // Read-only view of a context's study data and stream, for entry points that
 // live outside the context's own file.

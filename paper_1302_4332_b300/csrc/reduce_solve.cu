@@ -85,6 +85,7 @@ __global__ void solve_consts_kernel(const double* __restrict__ G, int q, SolveCo
     sc->b0[j] = v;
     sc->dSTL[j] = d;
   }
+  sc->stl00 = q > 0 ? G[0] : 0.0;
 }
 
 cudaError_t launch_solve_consts(const double* G, int q, SolveConsts* sc, DevStatus* st, cudaStream_t s) {
@@ -93,39 +94,20 @@ cudaError_t launch_solve_consts(const double* G, int q, SolveConsts* sc, DevStat
 }
 
 // ------------------------------------------------- per-SNP reductions + solve
-template <typename T>
-__device__ __forceinline__ double load_x(const T* p) { return (double)__ldcs(p); }
-
-// One warp per SNP.  QM is a compile-time bound on q (accumulators in registers).
-template <int QM, typename T>
-__global__ void __launch_bounds__(256) reduce_solve_kernel(const T* __restrict__ Xt, int64_t ldt, int rows,
-                                                           const double* __restrict__ W, int64_t ldw,
-                                                           const SolveConsts* __restrict__ sc, int q,
-                                                           int ncols, double* __restrict__ b,
-                                                           double* __restrict__ se, int* __restrict__ status) {
-  const int lane = threadIdx.x & 31;
-  const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (col >= ncols) return;
-  const T* x = Xt + (int64_t)col * ldt;
-  double acc[QM + 2];  // [0..q-1] S_BL, [q] r_B, [q+1] S_BR
-#pragma unroll
-  for (int a = 0; a < QM + 2; ++a) acc[a] = 0.0;
-  for (int r = lane; r < rows; r += 32) {
-    const double xv = load_x(x + r);
-#pragma unroll
-    for (int a = 0; a <= QM; ++a)
-      if (a <= q) acc[a] = fma(xv, W[r + a * ldw], acc[a]);
-    acc[QM + 1] = fma(xv, xv, acc[QM + 1]);
-  }
-#pragma unroll
-  for (int a = 0; a < QM + 2; ++a)
-#pragma unroll
-    for (int o = 16; o; o >>= 1) acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], o);
-  if (lane != 0) return;
-
+// acc[0..q-1] = S_BL, acc[q] = r_B, acc[QM+1] = S_BR (lane 0 after the warp reduction).
+// c != 0: the sums are those of the shifted SNP x' = x - c * X_L[:, 0] (X_L[:, 0]
+// the intercept).  [X_L | x'] spans the same space as [X_L | x]:  d^2 and b_p
+// are unchanged, b_0 = b'_0 - c b_p, and with S = T^T S' T (T = I + c e_0 e_p^T)
+// (S^-1)_00 = dSTL_0 + (g_0 + c)^2 / d^2; every other entry is unchanged.  The
+// collinearity test uses the unshifted S_BR = S'_BR + 2 c S'_BL,0 + c^2 S_TL,00.
+template <int QM>
+__device__ __forceinline__ void solve_store(const double (&acc)[QM + 2], const SolveConsts* __restrict__ sc,
+                                            int q, int col, double* __restrict__ b, double* __restrict__ se,
+                                            int* __restrict__ status, double c = 0.0) {
   const int p = q + 1;
   const double sbr = acc[QM + 1], rb = acc[q];
-  double l[QM > 0 ? QM : 1], g[QM > 0 ? QM : 1];
+  const double sbr_test = (c != 0.0 && q > 0) ? sbr + 2.0 * c * acc[0] + c * c * sc->stl00 : sbr;
+  double l[QM > 0 ? QM : 1];
   double ll = 0.0, lz = 0.0;
 #pragma unroll
   for (int i = 0; i < QM; ++i) {
@@ -139,7 +121,7 @@ __global__ void __launch_bounds__(256) reduce_solve_kernel(const T* __restrict__
   const double d2 = sbr - ll;
   double* bo = b + (int64_t)col * p;
   double* so = se ? se + (int64_t)col * p : nullptr;
-  if (!(d2 > SINGULAR_TAU * sbr)) {
+  if (!(d2 > SINGULAR_TAU * sbr_test)) {
     const double nan = __longlong_as_double(0x7ff8000000000000LL);
     for (int j = 0; j < p; ++j) {
       bo[j] = nan;
@@ -152,39 +134,179 @@ __global__ void __launch_bounds__(256) reduce_solve_kernel(const T* __restrict__
 #pragma unroll
   for (int j = 0; j < QM; ++j) {
     if (j >= q) break;
-    double v = 0.0;
+    double v = 0.0;  // g_j = (C^-T l)_j
     for (int i = j; i < q; ++i) v = fma(sc->Cinv[i + j * QMAX], l[i], v);
-    g[j] = v;
+    if (j == 0) v += c;
     bo[j] = sc->b0[j] - bp * v;
     if (so) so[j] = sqrt(sc->dSTL[j] + v * v / d2);
   }
   bo[q] = bp;
   if (so) so[q] = sqrt(1.0 / d2);
   if (status) status[col] = GWAS_SNP_OK;
-  (void)g;
 }
 
-template <typename T>
-static cudaError_t dispatch_rs(const T* Xt, int64_t ldt, int rows, const double* W, int64_t ldw,
-                               const SolveConsts* sc, int q, int ncols, double* b, double* se, int* status,
-                               cudaStream_t s) {
-  const int grid = (ncols + 7) / 8;
-  if (q <= 3)
-    reduce_solve_kernel<3, T><<<grid, 256, 0, s>>>(Xt, ldt, rows, W, ldw, sc, q, ncols, b, se, status);
-  else if (q <= 7)
-    reduce_solve_kernel<7, T><<<grid, 256, 0, s>>>(Xt, ldt, rows, W, ldw, sc, q, ncols, b, se, status);
-  else
-    reduce_solve_kernel<QMAX, T><<<grid, 256, 0, s>>>(Xt, ldt, rows, W, ldw, sc, q, ncols, b, se, status);
-  return cudaGetLastError();
+template <int QM>
+__device__ __forceinline__ void warp_sum(double (&acc)[QM + 2]) {
+#pragma unroll
+  for (int a = 0; a < QM + 2; ++a)
+#pragma unroll
+    for (int o = 16; o; o >>= 1) acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], o);
+}
+
+// FP64 X~ (the FP64 path): FP64 products and sums.  One warp per SNP.
+template <int QM>
+__global__ void __launch_bounds__(256) reduce_solve_kernel(const double* __restrict__ Xt, int64_t ldt, int rows,
+                                                           const double* __restrict__ W, int64_t ldw,
+                                                           const SolveConsts* __restrict__ sc, int q,
+                                                           int ncols, double* __restrict__ b,
+                                                           double* __restrict__ se, int* __restrict__ status) {
+  const int lane = threadIdx.x & 31;
+  const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (col >= ncols) return;
+  const double* x = Xt + (int64_t)col * ldt;
+  double acc[QM + 2];
+#pragma unroll
+  for (int a = 0; a < QM + 2; ++a) acc[a] = 0.0;
+  for (int r = lane; r < rows; r += 32) {
+    const double xv = __ldcs(x + r);
+#pragma unroll
+    for (int a = 0; a <= QM; ++a)
+      if (a <= q) acc[a] = fma(xv, W[r + a * ldw], acc[a]);
+    acc[QM + 1] = fma(xv, xv, acc[QM + 1]);
+  }
+  warp_sum<QM>(acc);
+  if (lane == 0) solve_store<QM>(acc, sc, q, col, b, se, status);
+}
+
+// FP32 X~ (the split paths).  A block of RS_WARPS warps handles RS_SNPS SNPs;
+// warp w takes every RS_WARPS-th group of 32 rows, lane l one row of the group,
+// so each W row (FP32, row-major, stride WS) is loaded once for RS_SNPS SNPs.
+// FP32 products are summed over 16 rows per lane and each partial is folded
+// into FP64 (B300 runs FP64 at a small fraction of the FP32 rate, and X~
+// itself carries FP32 precision).  Warp totals meet in shared memory; one
+// thread per SNP runs the p x p solve.
+constexpr int RS_WARPS = 4;
+constexpr int RS_SNPS = 4;
+
+template <int QM, int WS>
+__global__ void __launch_bounds__(32 * RS_WARPS) reduce_solve_f32_kernel(
+    const float* __restrict__ Xt, int64_t ldt, int rows, const float* __restrict__ W32,
+    const SolveConsts* __restrict__ sc, int q, int ncols, double* __restrict__ b, double* __restrict__ se,
+    int* __restrict__ status, const int8_t* __restrict__ shift) {
+  __shared__ double red[RS_WARPS][RS_SNPS][QM + 2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int col0 = blockIdx.x * RS_SNPS;
+  const float* x[RS_SNPS];
+#pragma unroll
+  for (int s = 0; s < RS_SNPS; ++s) x[s] = Xt + (int64_t)min(col0 + s, ncols - 1) * ldt;
+  double acc[RS_SNPS][QM + 2];
+#pragma unroll
+  for (int s = 0; s < RS_SNPS; ++s)
+#pragma unroll
+    for (int a = 0; a < QM + 2; ++a) acc[s][a] = 0.0;
+  constexpr int CH = 16;                  // rows per lane summed in FP32
+  constexpr int STEP = 32 * RS_WARPS;     // rows per sweep of the block
+  for (int r0 = warp * 32 + lane; r0 < rows; r0 += STEP * CH) {
+    float part[RS_SNPS][QM + 2];
+#pragma unroll
+    for (int s = 0; s < RS_SNPS; ++s)
+#pragma unroll
+      for (int a = 0; a < QM + 2; ++a) part[s][a] = 0.f;
+#pragma unroll 4
+    for (int i = 0; i < CH; ++i) {
+      const int r = r0 + STEP * i;
+      if (r < rows) {
+        float wv[WS];
+        const float4* wr = reinterpret_cast<const float4*>(W32 + (int64_t)r * WS);
+#pragma unroll
+        for (int v4 = 0; v4 < WS / 4; ++v4) {
+          const float4 w = __ldg(wr + v4);
+          wv[4 * v4] = w.x;
+          wv[4 * v4 + 1] = w.y;
+          wv[4 * v4 + 2] = w.z;
+          wv[4 * v4 + 3] = w.w;
+        }
+#pragma unroll
+        for (int s = 0; s < RS_SNPS; ++s) {
+          const float xv = __ldcs(x[s] + r);
+#pragma unroll
+          for (int a = 0; a <= QM && a < WS; ++a) part[s][a] = fmaf(xv, wv[a], part[s][a]);
+          part[s][QM + 1] = fmaf(xv, xv, part[s][QM + 1]);
+        }
+      }
+    }
+#pragma unroll
+    for (int s = 0; s < RS_SNPS; ++s)
+#pragma unroll
+      for (int a = 0; a < QM + 2; ++a) acc[s][a] += (double)part[s][a];
+  }
+#pragma unroll
+  for (int s = 0; s < RS_SNPS; ++s) {
+    warp_sum<QM>(acc[s]);
+    if (lane == 0)
+#pragma unroll
+      for (int a = 0; a < QM + 2; ++a) red[warp][s][a] = acc[s][a];
+  }
+  __syncthreads();
+  if (threadIdx.x < RS_SNPS) {
+    const int s = threadIdx.x, col = col0 + s;
+    if (col < ncols) {
+      double tot[QM + 2];
+#pragma unroll
+      for (int a = 0; a < QM + 2; ++a) {
+        double v = 0.0;
+#pragma unroll
+        for (int w = 0; w < RS_WARPS; ++w) v += red[w][s][a];
+        tot[a] = v;
+      }
+      solve_store<QM>(tot, sc, q, col, b, se, status, shift ? (double)shift[col] : 0.0);
+    }
+  }
 }
 
 cudaError_t launch_reduce_solve(const void* Xt, XtKind kind, int64_t ldt, int rows, const double* W,
                                 int64_t ldw, const SolveConsts* sc, int q, int ncols, double* b, double* se,
-                                int* status, cudaStream_t s) {
+                                int* status, cudaStream_t s, const float* W32, const int8_t* shift) {
   if (ncols <= 0) return cudaSuccess;
-  if (kind == XT_F64)
-    return dispatch_rs(static_cast<const double*>(Xt), ldt, rows, W, ldw, sc, q, ncols, b, se, status, s);
-  return dispatch_rs(static_cast<const float*>(Xt), ldt, rows, W, ldw, sc, q, ncols, b, se, status, s);
+  const int grid = (ncols + 7) / 8;
+  if (kind == XT_F64) {
+    const double* X = static_cast<const double*>(Xt);
+    if (q <= 3)
+      reduce_solve_kernel<3><<<grid, 256, 0, s>>>(X, ldt, rows, W, ldw, sc, q, ncols, b, se, status);
+    else if (q <= 7)
+      reduce_solve_kernel<7><<<grid, 256, 0, s>>>(X, ldt, rows, W, ldw, sc, q, ncols, b, se, status);
+    else
+      reduce_solve_kernel<QMAX><<<grid, 256, 0, s>>>(X, ldt, rows, W, ldw, sc, q, ncols, b, se, status);
+    return cudaGetLastError();
+  }
+  if (!W32) return cudaErrorInvalidValue;
+  const float* X = static_cast<const float*>(Xt);
+  const int g4 = (ncols + RS_SNPS - 1) / RS_SNPS;
+  constexpr int T = 32 * RS_WARPS;
+  if (q <= 3)
+    reduce_solve_f32_kernel<3, 4><<<g4, T, 0, s>>>(X, ldt, rows, W32, sc, q, ncols, b, se, status, shift);
+  else if (q <= 7)
+    reduce_solve_f32_kernel<7, 8><<<g4, T, 0, s>>>(X, ldt, rows, W32, sc, q, ncols, b, se, status, shift);
+  else
+    reduce_solve_f32_kernel<QMAX, 16><<<g4, T, 0, s>>>(X, ldt, rows, W32, sc, q, ncols, b, se, status, shift);
+  return cudaGetLastError();
+}
+
+// W32 = W in FP32, row-major with row stride w32_stride(q) (zero-padded).
+__global__ void make_w32_kernel(const double* __restrict__ W, int64_t ldw, int rows, int nc, int ws,
+                                float* __restrict__ W32) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < (int64_t)rows * ws;
+       e += (int64_t)gridDim.x * blockDim.x) {
+    const int r = (int)(e / ws), a = (int)(e % ws);
+    W32[e] = a < nc ? (float)W[r + a * ldw] : 0.f;
+  }
+}
+
+int w32_stride(int q) { return q <= 3 ? 4 : (q <= 7 ? 8 : 16); }
+
+cudaError_t launch_make_w32(const double* W, int64_t ldw, int rows, int q, float* W32, cudaStream_t s) {
+  make_w32_kernel<<<256, 256, 0, s>>>(W, ldw, rows, q + 1, w32_stride(q), W32);
+  return cudaGetLastError();
 }
 
 }  // namespace gwas

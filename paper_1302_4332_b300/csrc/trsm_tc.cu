@@ -58,7 +58,8 @@ struct Cfg {
 };
 
 struct TcParams {
-  int P, C, ncols;
+  int P, C, ncols, n;
+  const int8_t* shift;  // per-SNP integer shift c_i (x' = x - c_i on rows < n), or null
   int* flags;
   unsigned int* counter;
   float* xt32;   // FP32 X~ (n_pad x bs); the B "hi" piece in TF32 mode
@@ -235,7 +236,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       ptx::named_bar(2, 64);
       if (lane == 0) ptx::mbar_arrive(&tile_empty[slot]);
       if (t >= ntiles) break;
-      const int k = t / p.C;
+      const int k = t / p.C, ctile = t % p.C;
       if (!ptx::group_and(2, 64, ptx::mbar_wait(x8_full, it & 1, st))) break;
       bool ok = true;
       for (int h = 0; h < K::CPB; ++h) {
@@ -245,22 +246,33 @@ __global__ void __launch_bounds__(THREADS, 1)
         uint8_t* bh = smem + s * K::STAGE_BYTES + 2 * K::A_BYTES;
         for (int col = ct; col < TN; col += 64) {
           const int8_t* src = reinterpret_cast<const int8_t*>(x8 + col * TB + h * K::KCH);
+          const int colg = ctile * TN + col;
+          const int csh = (p.shift && colg < p.ncols) ? p.shift[colg] : 0;
+          const int row0 = k * TB + h * K::KCH;
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
-            uint32_t w[4];
+            // x' = x - c on the n sample rows, 0 on the padding (exact small integers)
+            float f[E];
             if constexpr (TF32) {
               const char4 v = *reinterpret_cast<const char4*>(src + q * E);
-              w[0] = __float_as_uint((float)v.x);
-              w[1] = __float_as_uint((float)v.y);
-              w[2] = __float_as_uint((float)v.z);
-              w[3] = __float_as_uint((float)v.w);
+              const signed char e4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+              for (int i = 0; i < 4; ++i) f[i] = (row0 + q * E + i < p.n) ? (float)(e4[i] - csh) : 0.f;
             } else {
               const char4 v0 = *reinterpret_cast<const char4*>(src + q * E);
               const char4 v1 = *reinterpret_cast<const char4*>(src + q * E + 4);
               const signed char e8[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
 #pragma unroll
+              for (int i = 0; i < 8; ++i) f[i] = (row0 + q * E + i < p.n) ? (float)(e8[i] - csh) : 0.f;
+            }
+            uint32_t w[4];
+            if constexpr (TF32) {
+#pragma unroll
+              for (int i = 0; i < 4; ++i) w[i] = __float_as_uint(f[i]);
+            } else {
+#pragma unroll
               for (int i = 0; i < 4; ++i) {
-                const __nv_bfloat162 b2 = __floats2bfloat162_rn((float)e8[2 * i], (float)e8[2 * i + 1]);
+                const __nv_bfloat162 b2 = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
                 w[i] = *reinterpret_cast<const uint32_t*>(&b2);
               }
             }
@@ -348,6 +360,35 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (warp == 2) ptx::tmem_dealloc(tmem_base, 2 * TN);
 }
 
+// ------------------------------------------- per-SNP integer shift (pre-pass)
+// c_i = round(mean of the n dosages of SNP i), from an exact integer sum.
+__global__ void column_shift_kernel(const int8_t* __restrict__ X, int64_t ldx, int n, int ncols,
+                                    int8_t* __restrict__ shift) {
+  const int lane = threadIdx.x & 31;
+  const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (col >= ncols) return;
+  const int8_t* x = X + (int64_t)col * ldx;  // 16-byte aligned (checked by the caller)
+  int sum = 0;
+  const int n16 = n & ~15;
+  for (int r = lane * 16; r < n16; r += 32 * 16) {
+    const int4 v = __ldg(reinterpret_cast<const int4*>(x + r));
+    const int w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+    for (int i = 0; i < 4; ++i) sum += __dp4a(w[i], 0x01010101, 0);
+  }
+  for (int r = n16 + lane; r < n; r += 32) sum += x[r];
+#pragma unroll
+  for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+  if (lane == 0) {
+    const long long num = 2LL * sum + n;  // floor((2 sum + n) / 2n) = round-half-up of sum / n
+    const long long den = 2LL * n;
+    long long c = num >= 0 ? num / den : -((-num + den - 1) / den);
+    if (c > 127) c = 127;
+    if (c < -127) c = -127;
+    shift[col] = (int8_t)c;
+  }
+}
+
 // ------------------------------------------------------------ set-up kernels
 template <bool TF32>
 __global__ void split_aop_kernel(const double* __restrict__ A, int64_t count, void* __restrict__ hi,
@@ -382,6 +423,8 @@ struct TcState {
   void* bhi = nullptr;
   void* blo = nullptr;
   int64_t ldt = 0;
+  int8_t* shift = nullptr;        // per-SNP integer shift (bs)
+  bool center = false;            // X_L[:, 0] is the intercept: shift SNP columns
   unsigned int* sched = nullptr;  // [0] counter, flags from +32
   size_t sched_bytes = 0;
   DevStatus* st = nullptr;
@@ -419,7 +462,7 @@ static cudaError_t set_smem_attr() {
 }
 
 cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_pad, int bs, int num_sms,
-                   DevStatus* st, cudaStream_t s, int64_t* launches) {
+                   bool center, DevStatus* st, cudaStream_t s, int64_t* launches) {
   *out = nullptr;
   TcState* t = new TcState;
   t->tf32 = (split == SPLIT_TF32);
@@ -448,6 +491,8 @@ cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_p
   TRY(cudaMalloc(&t->xt32, sizeof(float) * (size_t)n_pad * bs));
   if (!t->tf32) TRY(cudaMalloc(&t->bhi, 2 * (size_t)n_pad * bs));
   TRY(cudaMalloc(&t->blo, esz * (size_t)n_pad * bs));
+  TRY(cudaMalloc(&t->shift, (size_t)bs));
+  t->center = center;
   t->sched_bytes = 128 + sizeof(int) * (size_t)t->P * Cmax;
   TRY(cudaMalloc(&t->sched, t->sched_bytes));
   TRY(cudaMemsetAsync(t->sched, 0, t->sched_bytes, s));
@@ -482,10 +527,17 @@ cudaError_t run_block(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaS
   const int ntiles = t->P * C;
   e = cudaMemsetAsync(t->sched, 0, 128 + sizeof(int) * (size_t)t->P * C, s);
   if (e != cudaSuccess) return e;
+  if (t->center) {
+    column_shift_kernel<<<(ncols + 7) / 8, 256, 0, s>>>(X, ldx, t->n, ncols, t->shift);
+    ++*launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  }
   TcParams p;
   p.P = t->P;
   p.C = C;
   p.ncols = ncols;
+  p.n = t->n;
+  p.shift = t->center ? t->shift : nullptr;
   p.counter = t->sched;
   p.flags = reinterpret_cast<int*>(t->sched + 32);
   p.xt32 = t->xt32;
@@ -503,6 +555,7 @@ cudaError_t run_block(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaS
 }
 
 const float* xt_f32(const TcState* t) { return t->xt32; }
+const int8_t* shift_of(const TcState* t) { return t->center ? t->shift : nullptr; }
 int64_t xt_ld(const TcState* t) { return t->ldt; }
 
 void destroy(TcState* t) {
@@ -513,6 +566,7 @@ void destroy(TcState* t) {
   cudaFree(t->bhi);
   cudaFree(t->blo);
   cudaFree(t->sched);
+  cudaFree(t->shift);
   delete t;
 }
 

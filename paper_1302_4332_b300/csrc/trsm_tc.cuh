@@ -15,15 +15,20 @@ enum Split : int { SPLIT_BF16 = 0, SPLIT_TF32 = 1 };
 struct TcState;
 
 // Splits the FP64 block operator Aop into hi + lo pieces (BF16 or TF32) and
-// allocates the per-block buffers for up to bs SNP columns.
+// allocates the per-block buffers for up to bs SNP columns.  center: X_L's
+// first column is the intercept, so every SNP column is solved shifted by the
+// integer nearest its mean (exact in BF16/TF32; the reductions map the results
+// back), which removes most of the cancellation between the SNP and the
+// intercept in S_BR - S_BL S_TL^-1 S_BL^T.
 cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_pad, int bs, int num_sms,
-                   DevStatus* st, cudaStream_t s, int64_t* launches);
+                   bool center, DevStatus* st, cudaStream_t s, int64_t* launches);
 
 // X~ = L^-1 X for ncols <= bs int8 columns (X 16-byte aligned, ldx % 16 == 0).
 // The FP32 result is left in xt_f32() with leading dimension xt_ld().
 cudaError_t run_block(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaStream_t s, int64_t* launches);
 
 const float* xt_f32(const TcState* t);
+const int8_t* shift_of(const TcState* t);  // per-SNP shifts of the last block, or null
 int64_t xt_ld(const TcState* t);
 void destroy(TcState* t);
 

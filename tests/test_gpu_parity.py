@@ -203,6 +203,7 @@ def test_split_singular_and_near_singular(prec):
     e = compare(b[:, well], se_g[:, well], st_g[well], r[:, well], se[:, well], st[well])
     assert e["b_norm"] <= TOL_SPLIT and e["se_rel"] <= TOL_SPLIT, e
     e3 = compare(b[:, [3]], se_g[:, [3]], st_g[[3]], r[:, [3]], se[:, [3]], st[[3]])
+    print(prec, "near-singular", e3)
     assert e3["b_se_scaled"] <= 1e-3 and e3["se_rel"] <= 1e-3, e3
 
 
@@ -213,3 +214,44 @@ def test_split_stream(small_study, prec):
         b, se_g, st_g = g.solve_stream(np.asfortranarray(X[:, :1800]))
     e = compare(b, se_g, st_g, r[:, :1800], se[:, :1800], st[:1800])
     assert e["b_norm"] <= TOL_SPLIT and e["se_rel"] <= TOL_SPLIT, e
+
+
+# ------------------------------------------------------- full size (n = 10,000)
+@pytest.fixture(scope="module")
+def paper_scale():
+    """The paper-scale workload: n = 10,000, p = 4, h = 0.5, kinship from k = 5,000
+    genotypes, m = 1,000,000 SNPs in blocks of 4,096 (the last block holds 576)."""
+    w = gwas_synth.WORKLOADS["n10k_p4_m1M_int8"]
+    s = gwas_synth.study(w["n"], w["p"], w["k"], w["h"], w["sigma2"])
+    L = oracle.potrf(oracle.form_m(s["Phi"], w["h"], w["sigma2"]))
+    first = gwas_synth.dosages(w["n"], 0, w["bs"])
+    last0 = (w["m"] // w["bs"]) * w["bs"]
+    last = gwas_synth.dosages(w["n"], last0, w["m"])
+    rng = np.random.default_rng(7)
+    pick_first = np.sort(rng.choice(w["bs"], 48, replace=False))
+    pick_last = np.r_[0, np.sort(rng.choice(np.arange(1, last.shape[1] - 1), 14, replace=False)), last.shape[1] - 1]
+    ref_first = oracle.gls(L, s["XL"], s["y"], first[:, pick_first])
+    ref_last = oracle.gls(L, s["XL"], s["y"], last[:, pick_last])
+    return w, s, first, last, pick_first, pick_last, ref_first, ref_last
+
+
+# b: per-SNP normwise relative error (the stated bar: 1e-10 FP64, 1e-5 split);
+# se: component-wise, 1e-10 FP64, 1e-4 split (FP32 accumulation of ~10^3 tensor
+# products per output at n = 10^4).
+FULL_TOL = {"fp64": (1e-10, 1e-10), "bf16x3": (1e-5, 1e-4), "tf32x3": (1e-5, 1e-4)}
+
+
+@pytest.mark.parametrize("prec", ["fp64", "bf16x3", "tf32x3"])
+def test_full_size_sampled(paper_scale, prec):
+    import torch
+    w, s, first, last, pf, pl, ref_first, ref_last = paper_scale
+    tb, ts = FULL_TOL[prec]
+    with gw.GLS(s["Phi"], s["XL"], s["y"], w["h"], w["sigma2"], precision=prec, bs=w["bs"]) as g:
+        for X, pick, (r, se, _, st) in ((first, pf, ref_first), (last, pl, ref_last)):
+            Xd = torch.from_numpy(np.ascontiguousarray(X.T)).cuda().T
+            b, se_g, st_g = g.solve_block(Xd)
+            g.synchronize()
+            b, se_g, st_g = b.cpu().numpy()[:, pick], se_g.cpu().numpy()[:, pick], st_g.cpu().numpy()[pick]
+            e = compare(b, se_g, st_g, r, se, st)
+            print(prec, X.shape[1], e)
+            assert e["b_norm"] <= tb and e["se_rel"] <= ts, (prec, e)
