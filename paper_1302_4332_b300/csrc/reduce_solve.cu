@@ -178,90 +178,57 @@ __global__ void __launch_bounds__(256) reduce_solve_kernel(const double* __restr
   if (lane == 0) solve_store<QM>(acc, sc, q, col, b, se, status);
 }
 
-// FP32 X~ (the split paths).  A block of RS_WARPS warps handles RS_SNPS SNPs;
-// warp w takes every RS_WARPS-th group of 32 rows, lane l one row of the group,
-// so each W row (FP32, row-major, stride WS) is loaded once for RS_SNPS SNPs.
+// FP32 X~ (the split paths).  One warp per SNP; each lane takes 4 consecutive
+// rows per 16-byte load of X~ (rows is a multiple of 128, columns 16-byte
+// aligned) with the matching 4 rows of W32 (FP32, row-major, stride WS).
 // FP32 products are summed over 16 rows per lane and each partial is folded
 // into FP64 (B300 runs FP64 at a small fraction of the FP32 rate, and X~
-// itself carries FP32 precision).  Warp totals meet in shared memory; one
-// thread per SNP runs the p x p solve.
-constexpr int RS_WARPS = 4;
-constexpr int RS_SNPS = 4;
-
+// itself carries FP32 precision).
 template <int QM, int WS>
-__global__ void __launch_bounds__(32 * RS_WARPS) reduce_solve_f32_kernel(
-    const float* __restrict__ Xt, int64_t ldt, int rows, const float* __restrict__ W32,
-    const SolveConsts* __restrict__ sc, int q, int ncols, double* __restrict__ b, double* __restrict__ se,
-    int* __restrict__ status, const int8_t* __restrict__ shift) {
-  __shared__ double red[RS_WARPS][RS_SNPS][QM + 2];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int col0 = blockIdx.x * RS_SNPS;
-  const float* x[RS_SNPS];
+__global__ void __launch_bounds__(256) reduce_solve_f32_kernel(const float* __restrict__ Xt, int64_t ldt, int rows,
+                                                               const float* __restrict__ W32,
+                                                               const SolveConsts* __restrict__ sc, int q,
+                                                               int ncols, double* __restrict__ b,
+                                                               double* __restrict__ se, int* __restrict__ status,
+                                                               const int8_t* __restrict__ shift) {
+  const int lane = threadIdx.x & 31;
+  const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (col >= ncols) return;
+  const float4* x4 = reinterpret_cast<const float4*>(Xt + (int64_t)col * ldt);
+  double acc[QM + 2];
 #pragma unroll
-  for (int s = 0; s < RS_SNPS; ++s) x[s] = Xt + (int64_t)min(col0 + s, ncols - 1) * ldt;
-  double acc[RS_SNPS][QM + 2];
+  for (int a = 0; a < QM + 2; ++a) acc[a] = 0.0;
+  const int nv = rows >> 2;  // float4 groups of rows
+  for (int v0 = lane; v0 < nv; v0 += 32 * 4) {
+    float part[QM + 2];
 #pragma unroll
-  for (int s = 0; s < RS_SNPS; ++s)
+    for (int a = 0; a < QM + 2; ++a) part[a] = 0.f;
 #pragma unroll
-    for (int a = 0; a < QM + 2; ++a) acc[s][a] = 0.0;
-  constexpr int CH = 16;                  // rows per lane summed in FP32
-  constexpr int STEP = 32 * RS_WARPS;     // rows per sweep of the block
-  for (int r0 = warp * 32 + lane; r0 < rows; r0 += STEP * CH) {
-    float part[RS_SNPS][QM + 2];
+    for (int i = 0; i < 4; ++i) {
+      const int v = v0 + 32 * i;
+      if (v < nv) {
+        const float4 xv = __ldcs(x4 + v);
+        const float xs[4] = {xv.x, xv.y, xv.z, xv.w};
 #pragma unroll
-    for (int s = 0; s < RS_SNPS; ++s)
+        for (int e = 0; e < 4; ++e) {
+          const float4* wr = reinterpret_cast<const float4*>(W32 + (int64_t)(4 * v + e) * WS);
 #pragma unroll
-      for (int a = 0; a < QM + 2; ++a) part[s][a] = 0.f;
-#pragma unroll 4
-    for (int i = 0; i < CH; ++i) {
-      const int r = r0 + STEP * i;
-      if (r < rows) {
-        float wv[WS];
-        const float4* wr = reinterpret_cast<const float4*>(W32 + (int64_t)r * WS);
+          for (int v4 = 0; v4 < WS / 4; ++v4) {
+            const float4 w = __ldg(wr + v4);
+            const float wv[4] = {w.x, w.y, w.z, w.w};
 #pragma unroll
-        for (int v4 = 0; v4 < WS / 4; ++v4) {
-          const float4 w = __ldg(wr + v4);
-          wv[4 * v4] = w.x;
-          wv[4 * v4 + 1] = w.y;
-          wv[4 * v4 + 2] = w.z;
-          wv[4 * v4 + 3] = w.w;
-        }
-#pragma unroll
-        for (int s = 0; s < RS_SNPS; ++s) {
-          const float xv = __ldcs(x[s] + r);
-#pragma unroll
-          for (int a = 0; a <= QM && a < WS; ++a) part[s][a] = fmaf(xv, wv[a], part[s][a]);
-          part[s][QM + 1] = fmaf(xv, xv, part[s][QM + 1]);
+            for (int t = 0; t < 4; ++t)
+              if (4 * v4 + t <= QM) part[4 * v4 + t] = fmaf(xs[e], wv[t], part[4 * v4 + t]);
+          }
+          part[QM + 1] = fmaf(xs[e], xs[e], part[QM + 1]);
         }
       }
     }
 #pragma unroll
-    for (int s = 0; s < RS_SNPS; ++s)
-#pragma unroll
-      for (int a = 0; a < QM + 2; ++a) acc[s][a] += (double)part[s][a];
+    for (int a = 0; a < QM + 2; ++a) acc[a] += (double)part[a];
   }
-#pragma unroll
-  for (int s = 0; s < RS_SNPS; ++s) {
-    warp_sum<QM>(acc[s]);
-    if (lane == 0)
-#pragma unroll
-      for (int a = 0; a < QM + 2; ++a) red[warp][s][a] = acc[s][a];
-  }
-  __syncthreads();
-  if (threadIdx.x < RS_SNPS) {
-    const int s = threadIdx.x, col = col0 + s;
-    if (col < ncols) {
-      double tot[QM + 2];
-#pragma unroll
-      for (int a = 0; a < QM + 2; ++a) {
-        double v = 0.0;
-#pragma unroll
-        for (int w = 0; w < RS_WARPS; ++w) v += red[w][s][a];
-        tot[a] = v;
-      }
-      solve_store<QM>(tot, sc, q, col, b, se, status, shift ? (double)shift[col] : 0.0);
-    }
-  }
+  warp_sum<QM>(acc);
+  if (lane == 0) solve_store<QM>(acc, sc, q, col, b, se, status, shift ? (double)shift[col] : 0.0);
 }
 
 cudaError_t launch_reduce_solve(const void* Xt, XtKind kind, int64_t ldt, int rows, const double* W,
@@ -281,14 +248,13 @@ cudaError_t launch_reduce_solve(const void* Xt, XtKind kind, int64_t ldt, int ro
   }
   if (!W32) return cudaErrorInvalidValue;
   const float* X = static_cast<const float*>(Xt);
-  const int g4 = (ncols + RS_SNPS - 1) / RS_SNPS;
-  constexpr int T = 32 * RS_WARPS;
+  if ((rows & 3) || (ldt & 3)) return cudaErrorInvalidValue;  // 16-byte rows groups
   if (q <= 3)
-    reduce_solve_f32_kernel<3, 4><<<g4, T, 0, s>>>(X, ldt, rows, W32, sc, q, ncols, b, se, status, shift);
+    reduce_solve_f32_kernel<3, 4><<<grid, 256, 0, s>>>(X, ldt, rows, W32, sc, q, ncols, b, se, status, shift);
   else if (q <= 7)
-    reduce_solve_f32_kernel<7, 8><<<g4, T, 0, s>>>(X, ldt, rows, W32, sc, q, ncols, b, se, status, shift);
+    reduce_solve_f32_kernel<7, 8><<<grid, 256, 0, s>>>(X, ldt, rows, W32, sc, q, ncols, b, se, status, shift);
   else
-    reduce_solve_f32_kernel<QMAX, 16><<<g4, T, 0, s>>>(X, ldt, rows, W32, sc, q, ncols, b, se, status, shift);
+    reduce_solve_f32_kernel<QMAX, 16><<<grid, 256, 0, s>>>(X, ldt, rows, W32, sc, q, ncols, b, se, status, shift);
   return cudaGetLastError();
 }
 

@@ -16,16 +16,25 @@
 //   * all products accumulate in FP32 in TMEM; the FP32 X~ goes to the
 //     FP64 reductions.
 //
-// One persistent CTA per SM, 8 warps:
-//   warp 0    tile scheduler + TMA producer (one thread)
-//   warp 1    MMA issuer (one thread)
-//   warps 2-3 int8 -> BF16/TF32 cast of the diagonal block (+ TMEM allocation)
-//   warps 4-7 epilogue: TMEM -> registers -> FP32 X~ and its hi/lo pieces in
-//             HBM, then the tile's finished-flag (release)
+// Accumulation: the tensor core adds each K-step into its FP32 accumulator
+// with truncation, which biases long sums toward zero.  So every 128-wide
+// K-block (one j) accumulates into a fresh TMEM partial, and the epilogue
+// warps add that partial into an FP32 master held in registers with
+// round-to-nearest adds.  Two TMEM partials alternate so the MMAs of block
+// j+1 overlap the promotion of block j.
+//
+// One persistent CTA per SM, 12 warps:
+//   warp 0     tile scheduler + TMA producer (one thread)
+//   warp 1     MMA issuer (one thread)
+//   warps 2-3  int8 -> BF16/TF32 cast of the diagonal block (+ TMEM allocation)
+//   warps 4-11 epilogue: warp 4+e owns TMEM lanes 32*(e%4).. and SNP columns
+//              128*(e/4)..+127 of the tile; it promotes every partial into
+//              its master, then writes FP32 X~ and its hi/lo pieces to HBM
+//              and raises the tile's finished-flag (release)
+// Operands stream through STAGES shared-memory stages of 64-byte swizzled rows.
 // Tiles are handed out in (k, c) order by an atomic counter; a tile waits
 // (bounded) on the flag of tile (j, c) before loading X~_jc, so the launch
-// cannot deadlock.  Two TMEM accumulators (2 x TN columns) let the epilogue
-// of one tile overlap the products of the next.
+// cannot deadlock.
 #include <cuda.h>
 #include <cuda_bf16.h>
 
@@ -38,18 +47,20 @@ namespace gwas {
 namespace tc {
 
 constexpr int TN = 256;      // SNP columns per tile (MMA N)
-constexpr int STAGES = 2;    // operand stages in shared memory
+constexpr int STAGES = 4;    // operand stages in shared memory
 constexpr int TRING = 2;     // tile-id ring between the scheduler and the other roles
-constexpr int THREADS = 256;
+constexpr int EPI_WARPS = 8;
+constexpr int THREADS = 32 * (4 + EPI_WARPS);
+constexpr int EPI_COLS = TN / 2;  // SNP columns per epilogue warp
 
 template <bool TF32>
 struct Cfg {
   static constexpr int ESZ = TF32 ? 4 : 2;       // bytes per operand element
-  static constexpr int KCH = 128 / ESZ;          // K per stage: one 128-byte swizzle row
+  static constexpr int KCH = 64 / ESZ;           // K per stage: one 64-byte swizzle row
   static constexpr int KMMA = TF32 ? 8 : 16;     // K per tcgen05.mma
-  static constexpr int CPB = TB / KCH;           // stages per TB-wide block
-  static constexpr int A_BYTES = TB * 128;       // one piece of A per stage: 16 KB
-  static constexpr int B_BYTES = TN * 128;       // one piece of B per stage: 32 KB
+  static constexpr int CPB = TB / KCH;           // stages per TB-wide block (4 or 8)
+  static constexpr int A_BYTES = TB * 64;        // one piece of A per stage: 8 KB
+  static constexpr int B_BYTES = TN * 64;        // one piece of B per stage: 16 KB
   static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
   static constexpr int X8_BYTES = TN * TB;       // int8 diagonal block: 32 KB
   static constexpr int BAR_OFF = STAGES * STAGE_BYTES + X8_BYTES;
@@ -83,9 +94,9 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + K::BAR_OFF);
   uint64_t* full = bars;
   uint64_t* empty = full + STAGES;
-  uint64_t* acc_full = empty + STAGES;
-  uint64_t* acc_empty = acc_full + 2;
-  uint64_t* tile_full = acc_empty + 2;
+  uint64_t* part_full = empty + STAGES;
+  uint64_t* part_empty = part_full + 2;
+  uint64_t* tile_full = part_empty + 2;
   uint64_t* tile_empty = tile_full + TRING;
   uint64_t* x8_full = tile_empty + TRING;
   uint64_t* x8_empty = x8_full + 1;
@@ -103,12 +114,12 @@ __global__ void __launch_bounds__(THREADS, 1)
       ptx::mbar_init(&empty[s], 1);  // MMA commit
     }
     for (int a = 0; a < 2; ++a) {
-      ptx::mbar_init(&acc_full[a], 1);
-      ptx::mbar_init(&acc_empty[a], 4);  // one arrival per epilogue warp
+      ptx::mbar_init(&part_full[a], 1);           // MMA commit
+      ptx::mbar_init(&part_empty[a], EPI_WARPS);  // one arrival per epilogue warp
     }
     for (int i = 0; i < TRING; ++i) {
       ptx::mbar_init(&tile_full[i], 1);
-      ptx::mbar_init(&tile_empty[i], 7);  // MMA warp + 2 cast warps + 4 epilogue warps
+      ptx::mbar_init(&tile_empty[i], 1 + 2 + EPI_WARPS);  // MMA + cast warps + epilogue warps
     }
     ptx::mbar_init(x8_full, 1);
     ptx::mbar_init(x8_empty, 1);
@@ -180,7 +191,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     // ------------------------------------------------------------ MMA issuer
     if (lane == 0) {
       constexpr uint32_t idesc = ptx::idesc_f32acc<TF32>(TB, TN);
-      uint32_t cnt = 0;
+      uint32_t cnt = 0, kb = 0;
       for (int it = 0;; ++it) {
         const int slot = it % TRING;
         const uint32_t use = it / TRING;
@@ -189,14 +200,14 @@ __global__ void __launch_bounds__(THREADS, 1)
         ptx::mbar_arrive(&tile_empty[slot]);
         if (t >= ntiles) break;
         const int k = t / p.C;
-        const int a = it & 1;
-        const uint32_t u = it >> 1;
-        if (!ptx::mbar_wait(&acc_empty[a], (u & 1) ^ 1, st)) break;
-        ptx::tc_fence_after();
-        const uint32_t d = tmem_base + a * TN;
-        uint32_t accumulate = 0;
         bool ok = true;
-        for (int jj = 0; jj <= k && ok; ++jj) {
+        for (int jj = 0; jj <= k && ok; ++jj, ++kb) {
+          // a fresh partial per K-block, alternating between the two TMEM buffers
+          const int a = kb & 1;
+          if (!ptx::mbar_wait(&part_empty[a], ((kb >> 1) & 1) ^ 1, st)) { ok = false; break; }
+          ptx::tc_fence_after();
+          const uint32_t d = tmem_base + a * TN;
+          uint32_t accumulate = 0;
           for (int h = 0; h < K::CPB; ++h, ++cnt) {
             const int s = cnt % STAGES;
             const uint32_t r = cnt / STAGES;
@@ -206,10 +217,10 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
             for (int kk = 0; kk < K::KCH / K::KMMA; ++kk) {
               const uint32_t off = kk * K::KMMA * K::ESZ;
-              const uint64_t ahi = ptx::sdesc_k128(base + off);
-              const uint64_t alo = ptx::sdesc_k128(base + K::A_BYTES + off);
-              const uint64_t bhi = ptx::sdesc_k128(base + 2 * K::A_BYTES + off);
-              const uint64_t blo = ptx::sdesc_k128(base + 2 * K::A_BYTES + K::B_BYTES + off);
+              const uint64_t ahi = ptx::sdesc_k64(base + off);
+              const uint64_t alo = ptx::sdesc_k64(base + K::A_BYTES + off);
+              const uint64_t bhi = ptx::sdesc_k64(base + 2 * K::A_BYTES + off);
+              const uint64_t blo = ptx::sdesc_k64(base + 2 * K::A_BYTES + K::B_BYTES + off);
               ptx::mma<TF32>(d, alo, bhi, idesc, accumulate);
               accumulate = 1;
               if (jj > 0) ptx::mma<TF32>(d, ahi, blo, idesc, 1);
@@ -217,9 +228,10 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             ptx::mma_commit(&empty[s]);
           }
+          if (!ok) break;
+          ptx::mma_commit(&part_full[a]);
         }
         if (!ok) break;
-        ptx::mma_commit(&acc_full[a]);
       }
     }
   } else if (warp < 4) {
@@ -250,7 +262,7 @@ __global__ void __launch_bounds__(THREADS, 1)
           const int csh = (p.shift && colg < p.ncols) ? p.shift[colg] : 0;
           const int row0 = k * TB + h * K::KCH;
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
+          for (int q = 0; q < 4; ++q) {  // four 16-byte chunks per 64-byte row
             // x' = x - c on the n sample rows, 0 on the padding (exact small integers)
             float f[E];
             if constexpr (TF32) {
@@ -276,7 +288,9 @@ __global__ void __launch_bounds__(THREADS, 1)
                 w[i] = *reinterpret_cast<const uint32_t*>(&b2);
               }
             }
-            *reinterpret_cast<uint4*>(bh + col * 128 + ((q ^ (col & 7)) << 4)) = make_uint4(w[0], w[1], w[2], w[3]);
+            // 64-byte swizzle: 16-byte chunk q of row col sits at chunk q ^ ((col >> 1) & 3)
+            *reinterpret_cast<uint4*>(bh + col * 64 + ((q ^ ((col >> 1) & 3)) << 4)) =
+                make_uint4(w[0], w[1], w[2], w[3]);
           }
         }
         ptx::fence_proxy_async_shared();
@@ -289,48 +303,62 @@ __global__ void __launch_bounds__(THREADS, 1)
     }
   } else {
     // ----------------------------------------------------------------- epilogue
-    // The 128 threads decide together (group_and) after every wait.
-    const int e = warp - 4;  // TMEM lanes 32e .. 32e + 31
+    // The EPI_WARPS warps decide together (group_and) after every wait.
+    constexpr int NT = 32 * EPI_WARPS;
+    const int e = warp - 4;
+    const int lq = e & 3;           // TMEM lanes 32 lq .. 32 lq + 31
+    const int chalf = e >> 2;       // SNP columns chalf * EPI_COLS ..
+    uint32_t kb = 0;
+    float master[EPI_COLS];
     for (int it = 0;; ++it) {
       const int slot = it % TRING;
       const uint32_t use = it / TRING;
-      if (!ptx::group_and(1, 128, ptx::mbar_wait(&tile_full[slot], use & 1, st))) break;
+      if (!ptx::group_and(1, NT, ptx::mbar_wait(&tile_full[slot], use & 1, st))) break;
       const int t = tile_ring[slot];
-      ptx::named_bar(1, 128);
+      ptx::named_bar(1, NT);
       if (lane == 0) ptx::mbar_arrive(&tile_empty[slot]);
       if (t >= ntiles) break;
       const int k = t / p.C, c = t % p.C;
-      const int a = it & 1;
-      const uint32_t u = it >> 1;
-      if (!ptx::group_and(1, 128, ptx::mbar_wait(&acc_full[a], u & 1, st))) break;
-      ptx::tc_fence_after();
-      const int64_t row = (int64_t)k * TB + 32 * e + lane;
-#pragma unroll 1
-      for (int ch = 0; ch < TN / 32; ++ch) {
-        uint32_t v[32];
-        ptx::tmem_ld_32x32b_x32(tmem_base + (static_cast<uint32_t>(32 * e) << 16) + a * TN + ch * 32, v);
-        ptx::tmem_ld_wait();
 #pragma unroll
-        for (int i = 0; i < 32; ++i) {
-          const int col = c * TN + ch * 32 + i;
-          if (col < p.ncols) {
-            const float x = __uint_as_float(v[i]);
-            const int64_t idx = (int64_t)col * p.ldt + row;
-            p.xt32[idx] = x;
-            if constexpr (TF32) {
-              static_cast<float*>(p.blo)[idx] = x - __uint_as_float(tf32_trunc_bits(x));
-            } else {
-              const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-              static_cast<__nv_bfloat16*>(p.bhi)[idx] = hi;
-              static_cast<__nv_bfloat16*>(p.blo)[idx] = __float2bfloat16_rn(x - __bfloat162float(hi));
-            }
+      for (int i = 0; i < EPI_COLS; ++i) master[i] = 0.f;
+      bool ok = true;
+      for (int jj = 0; jj <= k; ++jj, ++kb) {
+        const int a = kb & 1;
+        if (!ptx::group_and(1, NT, ptx::mbar_wait(&part_full[a], (kb >> 1) & 1, st))) { ok = false; break; }
+        ptx::tc_fence_after();
+        const uint32_t tb = tmem_base + (static_cast<uint32_t>(32 * lq) << 16) + a * TN + chalf * EPI_COLS;
+#pragma unroll
+        for (int ch = 0; ch < EPI_COLS / 16; ++ch) {
+          uint32_t v[16];
+          ptx::tmem_ld_32x32b_x16(tb + ch * 16, v);
+          ptx::tmem_ld_wait();
+#pragma unroll
+          for (int i = 0; i < 16; ++i) master[ch * 16 + i] += __uint_as_float(v[i]);  // round to nearest
+        }
+        ptx::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) ptx::mbar_arrive(&part_empty[a]);
+      }
+      if (!ok) break;
+      const int64_t row = (int64_t)k * TB + 32 * lq + lane;
+      const int col0 = c * TN + chalf * EPI_COLS;
+#pragma unroll
+      for (int i = 0; i < EPI_COLS; ++i) {
+        const int col = col0 + i;
+        if (col < p.ncols) {
+          const float x = master[i];
+          const int64_t idx = (int64_t)col * p.ldt + row;
+          p.xt32[idx] = x;
+          if constexpr (TF32) {
+            static_cast<float*>(p.blo)[idx] = x - __uint_as_float(tf32_trunc_bits(x));
+          } else {
+            const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+            static_cast<__nv_bfloat16*>(p.bhi)[idx] = hi;
+            static_cast<__nv_bfloat16*>(p.blo)[idx] = __float2bfloat16_rn(x - __bfloat162float(hi));
           }
         }
       }
-      ptx::tc_fence_before();
-      __syncwarp();
-      if (lane == 0) ptx::mbar_arrive(&acc_empty[a]);
-      ptx::named_bar(1, 128);
+      ptx::named_bar(1, NT);
       if (e == 0 && lane == 0) {
         ptx::fence_proxy_async_global();
         __threadfence();
@@ -442,16 +470,17 @@ static cudaError_t get_encode(EncodeTiledFn* fn) {
   return cudaSuccess;
 }
 
-// 2D tiled map: dims {inner, outer}, outer stride in bytes, box {bi, bo}.
+// 2D tiled map: dims {inner, outer}, outer stride in bytes, box {bi, bo};
+// swz: the 64-byte swizzle of the operand stages (box inner extent 64 bytes).
 static cudaError_t make_map(EncodeTiledFn enc, CUtensorMap* m, CUtensorMapDataType dt, const void* base,
                             uint64_t inner, uint64_t outer, uint64_t stride_bytes, uint32_t bi, uint32_t bo,
-                            bool swizzle128) {
+                            bool swz) {
   cuuint64_t dims[2] = {inner, outer};
   cuuint64_t strides[1] = {stride_bytes};
   cuuint32_t box[2] = {bi, bo};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = enc(m, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   swizzle128 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_NONE,
+                   swz ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE,
                    CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
