@@ -222,6 +222,28 @@ def kernel_traffic(path: str):
         return None
 
 
+# ------------------------------------------------------------------ sharding
+def shard_block_starts(rank: int, world: int, nb: int, bs: int) -> list[int]:
+    """First SNP column of each of this rank's nb resident blocks: rank r owns
+    blocks r*nb .. r*nb + nb - 1 of the study, so ranks never share a SNP."""
+    return [(rank * nb + i) * bs for i in range(nb)]
+
+
+def max_over_ranks(x: float, dist, device=None) -> float:
+    """The slowest rank's time (the job's time); identity without a process group."""
+    if dist is None:
+        return float(x)
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_rate(world: int, units_per_rank: int, seconds: float) -> float:
+    """Whole-job throughput: the units all ranks processed over the slowest rank's time."""
+    return world * units_per_rank / seconds
+
+
 # ------------------------------------------------------------------ ours
 def run_ours(args, rank, world, local_rank, dist):
     import torch
@@ -237,8 +259,7 @@ def run_ours(args, rank, world, local_rank, dist):
     t0 = time.time()
     s = gwas_synth.study(n, p, w["k"], w["h"], w["sigma2"])
     # this rank's blocks: columns [ (rank*NB + i) * bs, ... )
-    blocks_h = [gwas_synth.dosages(n, (rank * N_RESIDENT_BLOCKS + i) * bs, (rank * N_RESIDENT_BLOCKS + i + 1) * bs)
-                for i in range(N_RESIDENT_BLOCKS)]
+    blocks_h = [gwas_synth.dosages(n, c0, c0 + bs) for c0 in shard_block_starts(rank, world, N_RESIDENT_BLOCKS, bs)]
     gen_s = time.time() - t0
     blocks_d = [torch.from_numpy(np.ascontiguousarray(b.T)).to(dev).T for b in blocks_h]
 
@@ -278,16 +299,13 @@ def run_ours(args, rank, world, local_rank, dist):
             ev1.record()
             torch.cuda.synchronize()
         g.synchronize()
-        elapsed = ev0.elapsed_time(ev1) / 1e3
+        elapsed = max_over_ranks(ev0.elapsed_time(ev1) / 1e3, dist, dev)
         if dist:
-            t = torch.tensor([elapsed], dtype=torch.float64, device=dev)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            elapsed = float(t.item())
             dist.barrier()
         launches = g.kernel_launches - launches0
         stages = g.timing_read()
         g.timing(False)
-        res = dict(snps_per_s=world * steps * step_snps / elapsed, ms_per_step=1e3 * elapsed / steps, steps=steps,
+        res = dict(snps_per_s=job_rate(world, steps * step_snps, elapsed), ms_per_step=1e3 * elapsed / steps, steps=steps,
                    warmup_blocks=warm_blocks, snps_per_step=step_snps, init_s=init_s, gpu_launches=launches,
                    clocks=clk.summary(),
                    stage_ms_per_block={k: v[0] / max(v[1], 1) for k, v in stages.items() if v[1]})
@@ -325,12 +343,8 @@ def run_ours(args, rank, world, local_rank, dist):
             t1 = time.perf_counter()
             for _ in range(steps):
                 g.solve_stream(Xh_np.T, bh.numpy().T, seh.numpy().T, sth.numpy())
-            e2e_s = time.perf_counter() - t1
-            if dist:
-                t = torch.tensor([e2e_s], dtype=torch.float64, device=dev)
-                dist.all_reduce(t, op=dist.ReduceOp.MAX)
-                e2e_s = float(t.item())
-            res["e2e"] = dict(value=world * steps * step_snps / e2e_s, unit=UNIT,
+            e2e_s = max_over_ranks(time.perf_counter() - t1, dist, dev)
+            res["e2e"] = dict(value=job_rate(world, steps * step_snps, e2e_s), unit=UNIT,
                               h2d_bytes_per_step=n * step_snps, d2h_bytes_per_step=step_snps * (2 * p * 8 + 4))
             del Xh, bh, seh, sth
         # keep a few results for the error report against the oracle
