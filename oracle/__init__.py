@@ -46,6 +46,11 @@ def _load():
         lib.oracle_trsm_lower.restype = None
         lib.oracle_gls.argtypes = [i64, ctypes.c_int, dp, dp, dp, i64, dp, dp, dp, dp, ip]
         lib.oracle_gls.restype = ctypes.c_int
+        lib.oracle_gls_grad.argtypes = [i64, ctypes.c_int, dp, dp, ctypes.c_double, ctypes.c_double, dp, dp, i64,
+                                         dp, dp, dp, dp]
+        lib.oracle_gls_grad.restype = ctypes.c_int
+        lib.oracle_reml.argtypes = [i64, ctypes.c_int, dp, dp, dp, ctypes.c_double, ctypes.c_int, dp]
+        lib.oracle_reml.restype = i64
         lib.oracle_num_threads.argtypes = []
         lib.oracle_num_threads.restype = ctypes.c_int
         lib.oracle_set_num_threads.argtypes = [ctypes.c_int]
@@ -129,6 +134,64 @@ def gls(L, XL, y, XR):
     if rc != 0:
         raise ValueError("oracle_gls: bad arguments")
     return r, se, chi2, status
+
+
+def gls_grad(L, phi, h: float, sigma2: float, XL, y, XR):
+    """Wald chi2 per SNP, d chi2 / dh per SNP, and sum over SNPs of d chi2 / dy.
+
+    Dense form with D = dM/dh = sigma2 (Phi - I) (not in the paper; the
+    differentiation form).  Returns (chi2, dchi2_dh, dy)."""
+    L, phi = _f64(L), _f64(phi)
+    n = L.shape[0]
+    XL = _f64(XL).reshape(n, -1, order="F") if np.size(XL) else np.zeros((n, 0), order="F")
+    y = _f64(y).reshape(n)
+    XR = _f64(XR).reshape(n, -1, order="F")
+    p, m = XL.shape[1] + 1, XR.shape[1]
+    chi2 = np.empty(m)
+    dh = np.empty(m)
+    dy = np.empty(n)
+    XLp = XL if XL.size else np.zeros((n, 1), order="F")
+    rc = _load().oracle_gls_grad(n, p, _p(L), _p(phi), float(h), float(sigma2), _p(XLp), _p(y), m, _p(XR),
+                                 _p(chi2), _p(dh), _p(dy))
+    if rc != 0:
+        raise ValueError("oracle_gls_grad: bad arguments")
+    return chi2, dh, dy
+
+
+def reml(phi, XL, y, h: float, grad: bool = True):
+    """REML log-likelihood of the null model y ~ N(X_L beta, s2 (h Phi + (1-h) I)),
+    s2 profiled out; returns (l, dl/dh or None, s2_hat).  Dense evaluation."""
+    phi = _f64(phi)
+    n = phi.shape[0]
+    XL = _f64(XL).reshape(n, -1, order="F")
+    y = _f64(y).reshape(n)
+    out = np.zeros(3)
+    rc = _load().oracle_reml(n, XL.shape[1], _p(phi), _p(XL), _p(y), float(h), int(bool(grad)), _p(out))
+    if rc != 0:
+        raise NotSPD(int(rc) - 1)
+    return out[0], (out[1] if grad else None), out[2]
+
+
+def reml_argmax(phi, XL, y, lo: float = 1e-4, hi: float = 1.0 - 1e-4, grid: int = 41, tol: float = 1e-7):
+    """argmax of the REML log-likelihood over h: a dense grid, then
+    golden-section search in the bracket around the best grid point."""
+    hs = np.linspace(lo, hi, grid)
+    vals = [reml(phi, XL, y, h, grad=False)[0] for h in hs]
+    i = int(np.argmax(vals))
+    a, b = hs[max(i - 1, 0)], hs[min(i + 1, grid - 1)]
+    g = (np.sqrt(5.0) - 1.0) / 2.0
+    c, d = b - g * (b - a), a + g * (b - a)
+    fc, fd = reml(phi, XL, y, c, grad=False)[0], reml(phi, XL, y, d, grad=False)[0]
+    while b - a > tol:
+        if fc > fd:
+            b, d, fd = d, c, fc
+            c = b - g * (b - a)
+            fc = reml(phi, XL, y, c, grad=False)[0]
+        else:
+            a, c, fc = c, d, fd
+            d = a + g * (b - a)
+            fd = reml(phi, XL, y, d, grad=False)[0]
+    return 0.5 * (a + b)
 
 
 def gls_from_phi(phi, XL, y, XR, h: float, sigma2: float):

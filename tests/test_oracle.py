@@ -235,3 +235,68 @@ def test_generator_columns_regenerate_independently():
     Phi = gwas_synth.kinship(gwas_synth.kinship_genotypes(80, 40, seed=5))
     np.testing.assert_allclose(Phi, Phi.T, rtol=0, atol=0)
     assert np.linalg.eigvalsh(Phi).min() >= gwas_synth.KINSHIP_RIDGE * 0.999
+
+
+# --- gradients and REML (the differentiation form) ---------------------------------
+
+def test_grad_matches_central_differences():
+    s, X = _study(70, 4, 140, 0.6, sigma2=1.3, m=6)
+    L = oracle.potrf(oracle.form_m(s["Phi"], 0.6, 1.3))
+    chi2, dh, dy = oracle.gls_grad(L, s["Phi"], 0.6, 1.3, s["XL"], s["y"], X)
+    c_ref = oracle.gls_from_phi(s["Phi"], s["XL"], s["y"], X, 0.6, 1.3)[2]
+    np.testing.assert_allclose(chi2, c_ref, rtol=1e-12)
+    d = 1e-6
+    fd_h = (oracle.gls_from_phi(s["Phi"], s["XL"], s["y"], X, 0.6 + d, 1.3)[2]
+            - oracle.gls_from_phi(s["Phi"], s["XL"], s["y"], X, 0.6 - d, 1.3)[2]) / (2 * d)
+    np.testing.assert_allclose(dh, fd_h, rtol=1e-6, atol=1e-8)
+    for j in (0, 13, 69):
+        yp, ym = s["y"].copy(), s["y"].copy()
+        yp[j] += d
+        ym[j] -= d
+        fd = (oracle.gls_from_phi(s["Phi"], s["XL"], yp, X, 0.6, 1.3)[2].sum()
+              - oracle.gls_from_phi(s["Phi"], s["XL"], ym, X, 0.6, 1.3)[2].sum()) / (2 * d)
+        assert abs(dy[j] - fd) <= 1e-6 * max(1.0, abs(fd)), (j, dy[j], fd)
+
+
+def test_grad_special_cases():
+    s, X = _study(50, 3, 100, 0.4, m=5)
+    # Phi = I: M = sigma2 I for every h, so chi2 does not depend on h
+    L = oracle.potrf(oracle.form_m(np.eye(50), 0.4, 1.0))
+    _, dh, _ = oracle.gls_grad(L, np.eye(50), 0.4, 1.0, s["XL"], s["y"], X)
+    np.testing.assert_array_equal(dh, 0.0)
+    # b does not depend on sigma2 and (S^-1)_pp scales with it, so chi2 and its gradients scale 1/sigma2
+    L2 = oracle.potrf(oracle.form_m(s["Phi"], 0.4, 2.0))
+    L1 = oracle.potrf(oracle.form_m(s["Phi"], 0.4, 1.0))
+    c2, dh2, dy2 = oracle.gls_grad(L2, s["Phi"], 0.4, 2.0, s["XL"], s["y"], X)
+    c1, dh1, dy1 = oracle.gls_grad(L1, s["Phi"], 0.4, 1.0, s["XL"], s["y"], X)
+    np.testing.assert_allclose(c2, c1 / 2.0, rtol=1e-11)
+    np.testing.assert_allclose(dh2, dh1 / 2.0, rtol=1e-9, atol=1e-12)
+    np.testing.assert_allclose(dy2, dy1 / 2.0, rtol=1e-9, atol=1e-12)
+
+
+def test_reml_gradient_and_closed_forms():
+    s, _ = _study(80, 3, 160, 0.5)
+    XL, y, Phi = s["XL"], s["y"], s["Phi"]
+    l, dl, s2 = oracle.reml(Phi, XL, y, 0.5)
+    d = 1e-6
+    fd = (oracle.reml(Phi, XL, y, 0.5 + d, grad=False)[0] - oracle.reml(Phi, XL, y, 0.5 - d, grad=False)[0]) / (2 * d)
+    assert abs(dl - fd) <= 1e-6 * max(1.0, abs(fd))
+    # h = 0: V = I, the REML likelihood of ordinary least squares
+    n, q = XL.shape
+    beta, *_ = np.linalg.lstsq(XL, y, rcond=None)
+    rss = float(np.sum((y - XL @ beta) ** 2))
+    l0 = -0.5 * ((n - q) * np.log(rss / (n - q)) + np.linalg.slogdet(XL.T @ XL)[1])
+    assert abs(oracle.reml(Phi, XL, y, 0.0, grad=False)[0] - l0) <= 1e-9 * abs(l0)
+    # Phi = I: the likelihood does not depend on h
+    g = oracle.reml(np.eye(n), XL, y, 0.3)[1]
+    assert abs(g) <= 1e-10
+
+
+def test_reml_argmax_is_a_stationary_maximum():
+    s = gwas_synth.study(120, 3, 240, 0.5, seed=9)
+    h_hat = oracle.reml_argmax(s["Phi"], s["XL"], s["y"])
+    assert 0.0 < h_hat < 1.0
+    l, dl, _ = oracle.reml(s["Phi"], s["XL"], s["y"], h_hat)
+    assert abs(dl) <= 1e-4
+    for dh in (-1e-3, 1e-3):
+        assert oracle.reml(s["Phi"], s["XL"], s["y"], h_hat + dh, grad=False)[0] <= l
