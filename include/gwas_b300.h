@@ -155,6 +155,37 @@ int gwas_solve_stream(gwas_ctx *ctx, const int8_t *XR_host, int64_t ldx, int64_t
 int gwas_solve_block_static(gwas_ctx *ctx, const int8_t *XR, int64_t ldx, int ncols, double *b, double *se,
                             int *status);
 
+/* The differentiation form (not in the paper): for one block of SNPs, the
+ * Wald statistic chi2_i = b_{p-1}^2 / (S^-1)_{p-1,p-1} of every SNP and the
+ * gradient of their sum with respect to h and y.  FP64 (forward solve
+ * X~ = L^-1 X and transpose solve X^ = L^-T X~ = M^-1 X, then per-SNP p x p
+ * adjoints); needs 0 < h <= 1 (it uses dM/dh = (M - sigma2 I) / h).
+ *   chi2, dchi2_dh  ncols each, may be NULL (a collinear SNP: NaN and 0)
+ *   dh_accum        one double; the block's sum of d chi2/dh is ADDED to it
+ *   dy_accum        n doubles; the block's d(sum chi2)/dy is ADDED to it
+ * Host or device pointers.  The first call builds the transpose operator
+ * (8 n^2 bytes).  Errors: GWAS_ERR_ARG, GWAS_ERR_CUDA, GWAS_ERR_TIMEOUT. */
+int gwas_adjoint_block(gwas_ctx *ctx, const int8_t *XR, int64_t ldx, int ncols, double *chi2, double *dchi2_dh,
+                       double *dh_accum, double *dy_accum);
+
+/* REML of the null model y ~ N(X_L beta, s2 (h Phi + (1 - h) I)) with s2
+ * profiled out (q = p - 1 covariates), evaluated on the GPU in FP64 at one h:
+ *   out[0] = l(h) = -1/2 [ (n - q) log s2 + log|V| + log|X_L^T V^-1 X_L| ]
+ *   out[1] = dl/dh = (tr(P) - ||P y||^2 / s2) / (2 h),   out[2] = s2,
+ * P = V^-1 - V^-1 X_L (X_L^T V^-1 X_L)^-1 X_L^T V^-1, s2 = y^T P y / (n - q).
+ * phi n x n, XL n x q, y n (host or device).  0 < h <= 1. */
+int gwas_reml_eval(int n, int q, const double *phi, const double *XL, const double *y, double h,
+                   const gwas_config *cfg, void *stream, double *out);
+
+/* Gradient-based REML fit of h from h0 (0 < h0 < 1): the sign change of
+ * dl/dh is bracketed by stepping uphill, then closed by modified regula
+ * falsi until the bracket is narrower than tol (or max_evals likelihood
+ * evaluations were spent).  *h_out, *loglik_out (may be NULL), *evals_out
+ * (may be NULL). */
+int gwas_reml_fit(int n, int q, const double *phi, const double *XL, const double *y, double h0, double tol,
+                  int max_evals, const gwas_config *cfg, void *stream, double *h_out, double *loglik_out,
+                  int *evals_out);
+
 /* Waits for the context's queued work and reports device-side errors
  * (GWAS_ERR_TIMEOUT when a bounded wait inside a kernel gave up). */
 int gwas_synchronize(gwas_ctx *ctx);

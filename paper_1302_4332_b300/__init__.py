@@ -34,7 +34,8 @@ EXPORTS = (
     "gwas_config_default", "gwas_init", "gwas_solve_block", "gwas_solve_block_f64", "gwas_solve_stream",
     "gwas_synchronize", "gwas_set_stream", "gwas_get_info", "gwas_not_spd_index", "gwas_copy_factor",
     "gwas_kernel_launches", "gwas_strerror", "gwas_last_error_detail", "gwas_destroy",
-    "gwas_timing_enable", "gwas_timing_read", "gwas_solve_block_static",
+    "gwas_timing_enable", "gwas_timing_read", "gwas_solve_block_static", "gwas_adjoint_block",
+    "gwas_reml_eval", "gwas_reml_fit",
 )
 STAGES = ("h2d", "trsm", "reduce", "d2h")
 
@@ -103,10 +104,59 @@ def load(path: str | None = None):
     lib.gwas_timing_read.restype = c_int
     lib.gwas_solve_block_static.argtypes = [vp, vp, i64, c_int, vp, vp, vp]
     lib.gwas_solve_block_static.restype = c_int
+    lib.gwas_adjoint_block.argtypes = [vp, vp, i64, c_int, vp, vp, vp, vp]
+    lib.gwas_adjoint_block.restype = c_int
+    lib.gwas_reml_eval.argtypes = [c_int, c_int, vp, vp, vp, dp, ctypes.POINTER(_Config), vp, ctypes.POINTER(dp)]
+    lib.gwas_reml_eval.restype = c_int
+    lib.gwas_reml_fit.argtypes = [c_int, c_int, vp, vp, vp, dp, dp, c_int, ctypes.POINTER(_Config), vp,
+                                  ctypes.POINTER(dp), ctypes.POINTER(dp), ctypes.POINTER(c_int)]
+    lib.gwas_reml_fit.restype = c_int
     lib.gwas_destroy.argtypes = [vp]
     lib.gwas_destroy.restype = None
     _lib = lib
     return lib
+
+
+def _host_f64(a, name):
+    arr = np.asfortranarray(np.asarray(a.detach().cpu() if _is_torch(a) else a, dtype=np.float64))
+    return arr
+
+
+def reml_eval(phi, XL, y, h: float, bs: int = 4096):
+    """REML log-likelihood of the null model, its derivative in h and s2 (GPU, FP64)."""
+    lib = load()
+    phi, y = _host_f64(phi, "phi"), _host_f64(y, "y")
+    n = y.shape[0]
+    XL = _host_f64(XL, "XL").reshape(n, -1, order="F") if XL is not None else np.zeros((n, 0), order="F")
+    cfg = _Config()
+    lib.gwas_config_default(ctypes.byref(cfg))
+    cfg.bs = int(bs)
+    out = (ctypes.c_double * 3)()
+    rc = lib.gwas_reml_eval(n, XL.shape[1], phi.ctypes.data, XL.ctypes.data if XL.size else None, y.ctypes.data,
+                            float(h), ctypes.byref(cfg), None, out)
+    if rc != GWAS_OK:
+        raise GwasError(rc, (lib.gwas_last_error_detail(None) or b"").decode())
+    return out[0], out[1], out[2]
+
+
+def reml_fit(phi, XL, y, h0: float = 0.2, tol: float = 1e-8, max_evals: int = 60, bs: int = 4096):
+    """Gradient-based REML fit of h (GPU, FP64).  Returns (h_hat, loglik, evaluations)."""
+    lib = load()
+    phi, y = _host_f64(phi, "phi"), _host_f64(y, "y")
+    n = y.shape[0]
+    XL = _host_f64(XL, "XL").reshape(n, -1, order="F") if XL is not None else np.zeros((n, 0), order="F")
+    cfg = _Config()
+    lib.gwas_config_default(ctypes.byref(cfg))
+    cfg.bs = int(bs)
+    h = ctypes.c_double()
+    ll = ctypes.c_double()
+    ev = ctypes.c_int()
+    rc = lib.gwas_reml_fit(n, XL.shape[1], phi.ctypes.data, XL.ctypes.data if XL.size else None, y.ctypes.data,
+                           float(h0), float(tol), int(max_evals), ctypes.byref(cfg), None, ctypes.byref(h),
+                           ctypes.byref(ll), ctypes.byref(ev))
+    if rc != GWAS_OK:
+        raise GwasError(rc, (lib.gwas_last_error_detail(None) or b"").decode())
+    return h.value, ll.value, ev.value
 
 
 def _torch():
@@ -251,6 +301,31 @@ class GLS:
         _, ptrs = self._outputs(m, keep, b, se, status)
         self._check(load().gwas_solve_stream(self._ctx, xp, ldx, m, *ptrs))
         return b, se, status
+
+    def adjoint_block(self, XR, dh_accum=None, dy_accum=None, chi2=None, dchi2_dh=None):
+        """Wald chi2 per SNP and the gradient of their sum w.r.t. h and y (FP64).
+
+        dh_accum (1 element) and dy_accum (n) are ADDED to; numpy arrays are
+        created when not given.  Returns (chi2, dchi2_dh, dh_accum, dy_accum)."""
+        xp, ldx, keep = _colmajor(XR, np.int8, self.n, "XR")
+        ncols = int(keep.shape[1])
+        on_dev = _is_torch(keep) and keep.is_cuda
+        if on_dev:
+            torch = _torch()
+            mk = lambda k: torch.zeros(k, dtype=torch.float64, device=keep.device)
+        else:
+            mk = lambda k: np.zeros(k)
+        chi2 = mk(ncols) if chi2 is None else chi2
+        dchi2_dh = mk(ncols) if dchi2_dh is None else dchi2_dh
+        dh_accum = mk(1) if dh_accum is None else dh_accum
+        dy_accum = mk(self.n) if dy_accum is None else dy_accum
+        ptr = lambda a: a.data_ptr() if _is_torch(a) else a.ctypes.data
+        for a in (chi2, dchi2_dh, dh_accum, dy_accum):
+            if (a.dtype != np.float64) if not _is_torch(a) else (str(a.dtype) != "torch.float64"):
+                raise TypeError("adjoint outputs must be float64")
+        self._check(load().gwas_adjoint_block(self._ctx, xp, ldx, ncols, ptr(chi2), ptr(dchi2_dh), ptr(dh_accum),
+                                              ptr(dy_accum)))
+        return chi2, dchi2_dh, dh_accum, dy_accum
 
     def synchronize(self):
         self._check(load().gwas_synchronize(self._ctx))

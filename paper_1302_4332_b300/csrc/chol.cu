@@ -260,4 +260,34 @@ cudaError_t launch_build_aop(const double* L, const double* Dinv, int n_pad, dou
   return cudaGetLastError();
 }
 
+// --------------------------------------------- the transpose block operator
+__global__ void put_diag_inverses_t_kernel(const double* __restrict__ Dinv, int P, int64_t n_pad,
+                                           double* __restrict__ AopT) {
+  const int k = blockIdx.x;
+  const double* D = Dinv + (int64_t)k * TB * TB;
+  for (int e = threadIdx.x; e < TB * TB; e += blockDim.x) {
+    const int i = e / TB, j = e % TB;  // AopT[k-panel row i][k-block col j] = D_k^-T(i, j) = D_k^-1(j, i)
+    AopT[((int64_t)k * TB + i) * n_pad + (int64_t)k * TB + j] = D[j + i * TB];
+  }
+}
+
+cudaError_t launch_build_aop_t(const double* L, const double* Dinv, int n_pad, double* AopT, cudaStream_t s,
+                               int64_t* launches) {
+  const int P = n_pad / TB;
+  cudaError_t e;
+  for (int k = 0; k + 1 < P; ++k) {
+    // AopT[k-panel rows, (k+1)TB :] = -D_k^-T L[(k+1)TB :, k-panel cols]^T
+    DgemmArgs g{};
+    g.M = TB; g.N = n_pad - (k + 1) * TB; g.K = TB;
+    g.A = Dinv + (int64_t)k * TB * TB; g.a_i = TB; g.a_t = 1;                // A(i, t) = D_k^-1(t, i)
+    g.B = L + (int64_t)k * TB * n_pad + (k + 1) * TB; g.b_j = 1; g.b_t = n_pad;  // B(j, t) = L((k+1)TB + j, kTB + t)
+    g.C = AopT + (int64_t)k * TB * n_pad + (k + 1) * TB; g.c_i = n_pad; g.c_j = 1;
+    g.alpha = -1.0; g.beta = 0.0; g.lower = 0;
+    if ((e = dgemm(g, s, launches)) != cudaSuccess) return e;
+  }
+  put_diag_inverses_t_kernel<<<P, 256, 0, s>>>(Dinv, P, n_pad, AopT);
+  ++*launches;
+  return cudaGetLastError();
+}
+
 }  // namespace gwas

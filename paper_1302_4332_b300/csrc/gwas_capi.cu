@@ -5,6 +5,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -39,6 +40,12 @@ struct gwas_ctx {
   tc::TcState* tcs = nullptr;  // split-precision state (TF32X3 / BF16X3)
   float* W32 = nullptr;        // W in FP32, row-major (split-path reductions)
   bool intercept = false;      // X_L[:, 0] == 1 for every sample
+  // adjoint form (built on first use)
+  double* AopT = nullptr;      // transpose block operator, row-major
+  double* Xhat = nullptr;      // n_pad x bs: X^ = L^-T X~
+  double* What = nullptr;      // n_pad x (q+1): [X^_L | y^]
+  double* GH = nullptr;        // (q+1)^2 Gram of What
+  double* adj = nullptr;       // per-SNP chi2 (bs), dh (bs), y-weights (bs x p), uT (q), dh/dy staging (1 + n)
   // device staging for host arguments
   std::vector<int8_t*> ring;      // ring_depth slots of n_pad x bs int8
   std::vector<cudaEvent_t> ev_copied, ev_free, ev_out;
@@ -145,6 +152,43 @@ int check_device_status(gwas_ctx* ctx) {
     CK(cudaMemcpy(ctx->st, &clean, sizeof clean, cudaMemcpyHostToDevice));
     return fail(ctx, GWAS_ERR_TIMEOUT, "a bounded device-side wait ran out (device code %d)", hs.err);
   }
+  return GWAS_OK;
+}
+
+// out = L^-1 X (upper = false) or L^-T X (upper = true) for FP64 columns, FP64 solve.
+int solve_f64_cols(gwas_ctx* ctx, const double* X, int64_t ldx, int rows, int ncols, double* out, bool upper) {
+  for (int c0 = 0; c0 < ncols; c0 += ctx->bs) {
+    const int nc = std::min(ctx->bs, ncols - c0);
+    const int C64 = (nc + F64_TN - 1) / F64_TN;
+    CK(cudaMemsetAsync(ctx->sched, 0, sizeof(Sched) + sizeof(int) * (size_t)ctx->P * C64, ctx->stream));
+    TrsmF64Args a{};
+    a.Aop = upper ? ctx->AopT : ctx->Aop; a.lda = ctx->n_pad;
+    a.X = X + (int64_t)c0 * ldx; a.ldx = ldx; a.n = rows;
+    a.Xt = out + (int64_t)c0 * ctx->n_pad; a.ldt = ctx->n_pad;
+    a.P = ctx->P; a.ncols = nc; a.C = C64;
+    a.sched = ctx->sched; a.st = ctx->st;
+    CK(launch_trsm_f64(a, false, ctx->stream, ctx->num_sms, upper));
+    ctx->launches += 1;
+  }
+  return GWAS_OK;
+}
+
+// The adjoint's loop-invariant part: the transpose operator, X^_L and y^, their Gram.
+int ensure_adjoint(gwas_ctx* ctx) {
+  if (ctx->AopT) return GWAS_OK;
+  const size_t np = (size_t)ctx->n_pad;
+  const int nc = ctx->q + 1;
+  CK(dmalloc(&ctx->AopT, sizeof(double) * np * np));
+  CK(cudaMemsetAsync(ctx->AopT, 0, sizeof(double) * np * np, ctx->stream));
+  CK(launch_build_aop_t(ctx->L, ctx->Dinv, ctx->n_pad, ctx->AopT, ctx->stream, &ctx->launches));
+  CK(dmalloc(&ctx->Xhat, sizeof(double) * np * std::max(ctx->bs, nc)));
+  CK(dmalloc(&ctx->What, sizeof(double) * np * nc));
+  CK(dmalloc(&ctx->GH, sizeof(double) * nc * nc));
+  CK(dmalloc(&ctx->adj, sizeof(double) * ((size_t)ctx->bs * (2 + ctx->p) + QMAX + 1 + ctx->n)));
+  int rc = solve_f64_cols(ctx, ctx->W, ctx->n_pad, ctx->n_pad, nc, ctx->What, true);
+  if (rc != GWAS_OK) return rc;
+  CK(launch_gram(ctx->What, ctx->n_pad, ctx->n_pad, nc, ctx->GH, ctx->stream));
+  ctx->launches += 1;
   return GWAS_OK;
 }
 
@@ -255,6 +299,7 @@ void free_all(gwas_ctx* c) {
   cudaFree(c->L); cudaFree(c->Dinv); cudaFree(c->Aop); cudaFree(c->W); cudaFree(c->G);
   cudaFree(c->sc); cudaFree(c->st); cudaFree(c->Xt); cudaFree(c->sched);
   cudaFree(c->d_b); cudaFree(c->d_se); cudaFree(c->d_status); cudaFree(c->f64_in); cudaFree(c->W32);
+  cudaFree(c->AopT); cudaFree(c->Xhat); cudaFree(c->What); cudaFree(c->GH); cudaFree(c->adj);
   cudaFreeHost(c->h_b); cudaFreeHost(c->h_se); cudaFreeHost(c->h_status);
   if (c->tcs) tc::destroy(c->tcs);
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
@@ -541,6 +586,213 @@ int gwas_solve_stream(gwas_ctx* ctx, const int8_t* XR_host, int64_t ldx, int64_t
   }
   if ((rc = drain(nblk - 1)) != GWAS_OK) return rc;
   return check_device_status(ctx);
+}
+
+int gwas_adjoint_block(gwas_ctx* ctx, const int8_t* XR, int64_t ldx, int ncols, double* chi2, double* dchi2_dh,
+                       double* dh_accum, double* dy_accum) {
+  if (!ctx) return GWAS_ERR_ARG;
+  if (!XR || !dh_accum || !dy_accum || ncols < 0 || ncols > ctx->bs || ldx < ctx->n)
+    return fail(ctx, GWAS_ERR_ARG, "bad arguments to gwas_adjoint_block");
+  if (!(ctx->h > 0.0)) return fail(ctx, GWAS_ERR_ARG, "the adjoint needs h > 0");
+  if (ncols == 0) return GWAS_OK;
+  CK(cudaSetDevice(ctx->dev));
+  int rc = ensure_adjoint(ctx);
+  if (rc != GWAS_OK) return rc;
+  const int p = ctx->p, bs = ctx->bs, n = ctx->n;
+  double* d_chi2 = ctx->adj;
+  double* d_dh = d_chi2 + bs;
+  double* d_w = d_dh + bs;
+  double* d_uT = d_w + (size_t)bs * p;
+  double* d_acc = d_uT + QMAX;  // [dh, dy...] staging for host accumulators
+  const bool dev_acc = is_device_ptr(dh_accum) && is_device_ptr(dy_accum);
+  double* acc_dh = dev_acc ? dh_accum : d_acc;
+  double* acc_dy = dev_acc ? dy_accum : d_acc + 1;
+  if (!dev_acc) {
+    CK(cudaMemcpyAsync(d_acc, dh_accum, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
+    CK(cudaMemcpyAsync(d_acc + 1, dy_accum, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
+  }
+  // forward solve X~ (FP64) of the int8 block
+  const void* xin = XR;
+  int64_t ld_in = ldx;
+  if (!is_device_ptr(XR)) {
+    CK(cudaMemcpy2DAsync(ctx->ring[0], (size_t)ctx->n_pad, XR, (size_t)ldx, (size_t)n, (size_t)ncols,
+                         cudaMemcpyHostToDevice, ctx->stream));
+    xin = ctx->ring[0];
+    ld_in = ctx->n_pad;
+  }
+  {
+    const int C64 = (ncols + F64_TN - 1) / F64_TN;
+    CK(cudaMemsetAsync(ctx->sched, 0, sizeof(Sched) + sizeof(int) * (size_t)ctx->P * C64, ctx->stream));
+    TrsmF64Args a{};
+    a.Aop = ctx->Aop; a.lda = ctx->n_pad;
+    a.X = xin; a.ldx = ld_in; a.n = n;
+    a.Xt = ctx->Xt; a.ldt = ctx->n_pad;
+    a.P = ctx->P; a.ncols = ncols; a.C = C64;
+    a.sched = ctx->sched; a.st = ctx->st;
+    StageMark m(ctx, GWAS_STAGE_TRSM, ctx->stream);
+    CK(launch_trsm_f64(a, true, ctx->stream, ctx->num_sms));
+    ctx->launches += 1;
+  }
+  // transpose solve X^ = L^-T X~
+  {
+    StageMark m(ctx, GWAS_STAGE_TRSM, ctx->stream);
+    if ((rc = solve_f64_cols(ctx, ctx->Xt, ctx->n_pad, ctx->n_pad, ncols, ctx->Xhat, true)) != GWAS_OK) return rc;
+  }
+  {
+    StageMark m(ctx, GWAS_STAGE_REDUCE, ctx->stream);
+    CK(launch_adjoint(ctx->Xt, ctx->Xhat, ctx->n_pad, ctx->n_pad, n, ctx->W, ctx->What, ctx->n_pad, ctx->sc, ctx->GH,
+                      ctx->q, ncols, ctx->h, ctx->sigma2, d_chi2, d_dh, d_w, d_uT, acc_dh, acc_dy, ctx->stream));
+    ctx->launches += 3;
+  }
+  if (chi2)
+    CK(cudaMemcpyAsync(chi2, d_chi2, sizeof(double) * ncols, cudaMemcpyDefault, ctx->stream));
+  if (dchi2_dh)
+    CK(cudaMemcpyAsync(dchi2_dh, d_dh, sizeof(double) * ncols, cudaMemcpyDefault, ctx->stream));
+  if (!dev_acc) {
+    CK(cudaMemcpyAsync(dh_accum, d_acc, sizeof(double), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(dy_accum, d_acc + 1, sizeof(double) * n, cudaMemcpyDeviceToHost, ctx->stream));
+  }
+  if (dev_acc && is_device_ptr(XR) && (!chi2 || is_device_ptr(chi2)) && (!dchi2_dh || is_device_ptr(dchi2_dh)))
+    return GWAS_OK;
+  return check_device_status(ctx);
+}
+
+// REML of the null model at one h (FP64 throughout); see gwas_b300.h.
+static int reml_eval_impl(const double* phi, int n, int q, const double* XL, const double* y, double h,
+                          const gwas_config* cfg, void* stream, double* out) {
+  gwas_ctx* ctx = nullptr;
+  gwas_config c;
+  gwas_config_default(&c);
+  if (cfg) c = *cfg;
+  c.precision = GWAS_FP64;
+  c.bs = std::max(c.bs, q + 1 + 64);  // room for [r~ | X~_L] plus identity chunks in the scratch
+  int rc = gwas_init(&ctx, n, q + 1, phi, 0, XL, y, h, 1.0, &c, stream);
+  if (rc != GWAS_OK) return rc;
+  rc = [&]() -> int {
+    rc = ensure_adjoint(ctx);
+    if (rc != GWAS_OK) return rc;
+    const int nc = q + 1, np = ctx->n_pad;
+    double* U = ctx->Xt;       // [r~ | X~_L]
+    double* Uh = ctx->Xhat;    // [P y | X^_L]  (P y = V^-1 (y - X_L beta) = L^-T r~)
+    double* d = ctx->adj;      // scalars
+    CK(launch_null_residual(ctx->W, np, np, q, ctx->sc, U, ctx->stream));
+    if (q) CK(cudaMemcpyAsync(U + np, ctx->W, sizeof(double) * (size_t)np * q, cudaMemcpyDeviceToDevice, ctx->stream));
+    if ((rc = solve_f64_cols(ctx, U, np, np, nc, Uh, true)) != GWAS_OK) return rc;
+    CK(launch_log_diag(ctx->L, np, n, d, ctx->stream));                  // d[0] = sum log L_ii
+    CK(launch_col_sumsq(U, np, n, 1, d + 1, ctx->stream));               // d[1] = y^T P y
+    CK(launch_col_sumsq(Uh, np, n, 1, d + 2, ctx->stream));              // d[2] = ||P y||^2
+    if (q) CK(launch_gram(Uh + np, np, np, q, d + 3, ctx->stream));     // d[3..] = X^_L^T X^_L (q x q)
+    ctx->launches += 5;
+    // tr(V^-1) = ||L^-1||_F^2, columns of the identity in chunks
+    double* E = ctx->Xhat + (size_t)np * nc;  // free space after Uh
+    const int chunk = std::max(1, std::min(ctx->bs - nc, n));
+    double trv = 0.0;
+    std::vector<double> part(chunk);
+    double* dpart = d + 3 + q * q;
+    for (int c0 = 0; c0 < n; c0 += chunk) {
+      const int ncc = std::min(chunk, n - c0);
+      CK(launch_identity_cols(E, n, c0, ncc, ctx->stream));
+      if ((rc = solve_f64_cols(ctx, E, n, n, ncc, ctx->Xt, false)) != GWAS_OK) return rc;
+      CK(launch_col_sumsq(ctx->Xt, np, np, ncc, dpart, ctx->stream));
+      ctx->launches += 2;
+      CK(cudaMemcpyAsync(part.data(), dpart, sizeof(double) * ncc, cudaMemcpyDeviceToHost, ctx->stream));
+      CK(cudaStreamSynchronize(ctx->stream));
+      for (int i = 0; i < ncc; ++i) trv += part[i];
+    }
+    std::vector<double> hd(3 + q * q);
+    SolveConsts hsc;
+    CK(cudaMemcpyAsync(hd.data(), d, sizeof(double) * hd.size(), cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(&hsc, ctx->sc, sizeof hsc, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaStreamSynchronize(ctx->stream));
+    if ((rc = check_device_status(ctx)) != GWAS_OK) return rc;
+    // A^-1 = Cinv^T Cinv;  log|A| = -2 sum log Cinv_ii;  tr(A^-1 T_LL)
+    double logdetA = 0.0, trAT = 0.0;
+    for (int i = 0; i < q; ++i) logdetA -= 2.0 * std::log(hsc.Cinv[i + i * QMAX]);
+    for (int i = 0; i < q; ++i)
+      for (int j = 0; j < q; ++j) {
+        double aij = 0.0;
+        for (int t = std::max(i, j); t < q; ++t) aij += hsc.Cinv[t + i * QMAX] * hsc.Cinv[t + j * QMAX];
+        trAT += aij * hd[3 + j + i * q];
+      }
+    const double logdetV = 2.0 * hd[0], yPy = hd[1], Py2 = hd[2];
+    const double s2 = yPy / (double)(n - q);
+    const double trP = trv - trAT;
+    out[0] = -0.5 * ((double)(n - q) * std::log(s2) + logdetV + logdetA);
+    out[1] = (h > 0.0) ? (trP - Py2 / s2) / (2.0 * h) : std::nan("");
+    out[2] = s2;
+    return GWAS_OK;
+  }();
+  if (rc != GWAS_OK) {
+    tl_init_detail = ctx->detail;
+  }
+  gwas_destroy(ctx);
+  return rc;
+}
+
+int gwas_reml_eval(int n, int q, const double* phi, const double* XL, const double* y, double h,
+                   const gwas_config* cfg, void* stream, double* out) {
+  if (n < 2 || q < 0 || q >= n || !phi || !y || (q && !XL) || !out || !(h > 0.0 && h <= 1.0)) return GWAS_ERR_ARG;
+  return reml_eval_impl(phi, n, q, XL, y, h, cfg, stream, out);
+}
+
+int gwas_reml_fit(int n, int q, const double* phi, const double* XL, const double* y, double h0, double tol,
+                  int max_evals, const gwas_config* cfg, void* stream, double* h_out, double* loglik_out,
+                  int* evals_out) {
+  if (n < 2 || q < 0 || q >= n || !phi || !y || (q && !XL) || !h_out || !(h0 > 0.0 && h0 < 1.0) || !(tol > 0.0) ||
+      max_evals < 3)
+    return GWAS_ERR_ARG;
+  const double lo_lim = 1e-6, hi_lim = 1.0 - 1e-6;
+  int evals = 0;
+  double out[3];
+  auto grad = [&](double h, double* g) -> int {
+    int rc = reml_eval_impl(phi, n, q, XL, y, h, cfg, stream, out);
+    ++evals;
+    *g = out[1];
+    return rc;
+  };
+  // bracket a sign change of dl/dh by stepping downhill-to-uphill from h0
+  double a = h0, ga;
+  int rc = grad(a, &ga);
+  if (rc != GWAS_OK) return rc;
+  double step = 0.05, b = a, gb = ga;
+  while (evals < max_evals) {
+    b = std::min(hi_lim, std::max(lo_lim, a + (ga > 0.0 ? step : -step)));
+    if ((rc = grad(b, &gb)) != GWAS_OK) return rc;
+    if ((ga > 0.0) != (gb > 0.0) || b == lo_lim || b == hi_lim) break;
+    a = b;
+    ga = gb;
+    step *= 2.0;
+  }
+  double h = b, gh = gb;
+  if ((ga > 0.0) == (gb > 0.0)) {
+    h = b;  // the maximum sits on the boundary of (0, 1)
+  } else {
+    // Illinois (modified regula falsi) on the gradient
+    int side = 0;
+    while (std::fabs(b - a) > tol && evals < max_evals) {
+      h = (a * gb - b * ga) / (gb - ga);
+      if (!(h > std::min(a, b) && h < std::max(a, b))) h = 0.5 * (a + b);
+      if ((rc = grad(h, &gh)) != GWAS_OK) return rc;
+      if (gh == 0.0) { a = b = h; break; }
+      if ((gh > 0.0) == (gb > 0.0)) {
+        b = h; gb = gh;
+        if (side == -1) ga *= 0.5;
+        side = -1;
+      } else {
+        a = h; ga = gh;
+        if (side == 1) gb *= 0.5;
+        side = 1;
+      }
+      if (std::fabs(gh) == 0.0) break;
+    }
+    h = (std::fabs(ga) < std::fabs(gb)) ? a : b;
+  }
+  if ((rc = reml_eval_impl(phi, n, q, XL, y, h, cfg, stream, out)) != GWAS_OK) return rc;
+  ++evals;
+  *h_out = h;
+  if (loglik_out) *loglik_out = out[0];
+  if (evals_out) *evals_out = evals;
+  return GWAS_OK;
 }
 
 int gwas_synchronize(gwas_ctx* ctx) {

@@ -98,7 +98,14 @@ struct TrsmF64Args {
   Sched* sched;
   DevStatus* st;
 };
-cudaError_t launch_trsm_f64(const TrsmF64Args& a, bool int8_input, cudaStream_t s, int num_sms);
+// upper = true: Xt = L^-T X with Aop the transpose block operator (FP64 input only).
+cudaError_t launch_trsm_f64(const TrsmF64Args& a, bool int8_input, cudaStream_t s, int num_sms,
+                            bool upper = false);
+
+// The transpose block operator (row-major): row panel k holds D_k^-T at
+// block k and -D_k^-T L_jk^T at blocks j > k.
+cudaError_t launch_build_aop_t(const double* L, const double* Dinv, int n_pad, double* AopT, cudaStream_t s,
+                               int64_t* launches);
 
 // a3: G = W^T W (nc x nc, column-major), W n_pad x nc.
 cudaError_t launch_gram(const double* W, int64_t ldw, int n_pad, int nc, double* G, cudaStream_t s);
@@ -118,6 +125,18 @@ cudaError_t launch_reduce_solve(const void* Xt, XtKind kind, int64_t ldt, int ro
                                 const int8_t* shift = nullptr);
 int w32_stride(int q);
 cudaError_t launch_make_w32(const double* W, int64_t ldw, int rows, int q, float* W32, cudaStream_t s);
+
+// a11: per-SNP adjoint (chi2, d chi2/dh, y-weights), their sums over SNPs and
+// the y-gradient; FP64.  GH = What^T What, What = [X^_L | y^] = L^-T W.
+cudaError_t launch_adjoint(const double* Xt, const double* Xh, int64_t ldt, int rows, int n, const double* W,
+                           const double* Wh, int64_t ldw, const SolveConsts* sc, const double* GH, int q,
+                           int ncols, double h, double sigma2, double* chi2, double* dh, double* wv, double* uT,
+                           double* dh_accum, double* dy_accum, cudaStream_t s);
+cudaError_t launch_log_diag(const double* L, int64_t ld, int n, double* out, cudaStream_t s);
+cudaError_t launch_col_sumsq(const double* X, int64_t ld, int n, int ncols, double* out, cudaStream_t s);
+cudaError_t launch_identity_cols(double* E, int n, int c0, int ncols, cudaStream_t s);
+cudaError_t launch_null_residual(const double* W, int64_t ldw, int rows, int q, const SolveConsts* sc, double* R,
+                                 cudaStream_t s);
 
 // Read-only view of a context's study data and stream, for entry points that
 // live outside the context's own file.

@@ -50,7 +50,10 @@ __device__ bool wait_flag(const int* flag, DevStatus* st) {
 
 constexpr int KC = 16;  // reduction chunk
 
-template <typename TIn>
+// UPPER: the transpose solve X^ = L^-T X with the transpose block operator
+// (row panel k = [D_k^-T at block k | -D_k^-T L_jk^T for j > k]); tiles are
+// handed out from the last row panel up and tile (k, c) walks j = P-1 .. k+1.
+template <typename TIn, bool UPPER>
 __global__ void __launch_bounds__(256, 2) trsm_f64_kernel(TrsmF64Args a) {
   __shared__ double As[KC][TB + 1];
   __shared__ double Bs[KC][F64_TN + 1];
@@ -70,8 +73,9 @@ __global__ void __launch_bounds__(256, 2) trsm_f64_kernel(TrsmF64Args a) {
     __syncthreads();
     const int tile = s_tile;
     if (tile >= ntiles) return;
-    const int k = tile / a.C, c = tile % a.C;
+    const int k = UPPER ? a.P - 1 - tile / a.C : tile / a.C, c = tile % a.C;
     const int col0 = c * F64_TN;
+    const int nsteps = UPPER ? a.P - k : k + 1;
 
     double acc[8][4];
 #pragma unroll
@@ -79,9 +83,10 @@ __global__ void __launch_bounds__(256, 2) trsm_f64_kernel(TrsmF64Args a) {
 #pragma unroll
       for (int q = 0; q < 4; ++q) acc[r][q] = 0.0;
 
-    // j = k first (the diagonal inverse on this tile's own input), then 0..k-1
-    for (int step = 0; step <= k; ++step) {
-      const int j = (step == 0) ? k : step - 1;
+    // j = k first (the diagonal inverse on this tile's own input), then the
+    // finished panels, oldest first: 0..k-1 (lower) or P-1..k+1 (upper)
+    for (int step = 0; step < nsteps; ++step) {
+      const int j = (step == 0) ? k : (UPPER ? a.P - step : step - 1);
       if (j != k) {
         if (tid == 0) s_ok = wait_flag(&flags[j * a.C + c], a.st) ? 1 : 0;
         __syncthreads();
@@ -147,23 +152,26 @@ __global__ void __launch_bounds__(256, 2) trsm_f64_kernel(TrsmF64Args a) {
   }
 }
 
-cudaError_t launch_trsm_f64(const TrsmF64Args& a, bool int8_input, cudaStream_t s, int num_sms) {
+cudaError_t launch_trsm_f64(const TrsmF64Args& a, bool int8_input, cudaStream_t s, int num_sms, bool upper) {
   if (a.ncols <= 0) return cudaSuccess;
   int per_sm = 0;
   cudaError_t e;
+  if (int8_input && upper) return cudaErrorInvalidValue;  // the transpose solve takes FP64 input
   if (int8_input)
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trsm_f64_kernel<int8_t>, 256, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trsm_f64_kernel<int8_t, false>, 256, 0);
   else
-    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trsm_f64_kernel<double>, 256, 0);
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trsm_f64_kernel<double, false>, 256, 0);
   if (e != cudaSuccess) return e;
   if (per_sm < 1) per_sm = 1;
   int grid = num_sms * per_sm;
   const int ntiles = a.P * a.C;
   if (grid > ntiles) grid = ntiles;
   if (int8_input)
-    trsm_f64_kernel<int8_t><<<grid, 256, 0, s>>>(a);
+    trsm_f64_kernel<int8_t, false><<<grid, 256, 0, s>>>(a);
+  else if (upper)
+    trsm_f64_kernel<double, true><<<grid, 256, 0, s>>>(a);
   else
-    trsm_f64_kernel<double><<<grid, 256, 0, s>>>(a);
+    trsm_f64_kernel<double, false><<<grid, 256, 0, s>>>(a);
   return cudaGetLastError();
 }
 

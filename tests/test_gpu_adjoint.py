@@ -1,0 +1,107 @@
+"""The differentiation form on the GPU (FP64) against the oracle's dense-form
+gradients, central differences, and the REML fit of h against the oracle."""
+import numpy as np
+import pytest
+
+import gwas_synth
+import oracle
+import paper_1302_4332_b300 as gw
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1302_4332_b300 import build
+    build.build()
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+def _rel(a, b):
+    a, b = np.asarray(a, float), np.asarray(b, float)
+    return float(np.linalg.norm(a - b) / np.linalg.norm(b))
+
+
+@pytest.mark.parametrize("n,p,m,h,sigma2", [(300, 4, 70, 0.5, 1.3), (129, 2, 65, 0.8, 1.0), (257, 6, 40, 0.3, 0.7)])
+def test_adjoint_matches_oracle(n, p, m, h, sigma2):
+    s = gwas_synth.study(n, p, 2 * n, h, sigma2, seed=5)
+    X = gwas_synth.dosages(n, 0, m, seed=5)
+    L = oracle.potrf(oracle.form_m(s["Phi"], h, sigma2))
+    c_ref, dh_ref, dy_ref = oracle.gls_grad(L, s["Phi"], h, sigma2, s["XL"], s["y"], X)
+    with gw.GLS(s["Phi"], s["XL"], s["y"], h, sigma2, bs=64) as g:
+        dh, dy = np.zeros(1), np.zeros(n)
+        chi2, dch = [], []
+        for c0 in range(0, m, 64):
+            c, d, dh, dy = g.adjoint_block(X[:, c0:c0 + 64], dh_accum=dh, dy_accum=dy)
+            chi2.append(c.copy())
+            dch.append(d.copy())
+    chi2, dch = np.concatenate(chi2), np.concatenate(dch)
+    assert _rel(chi2, c_ref) <= 1e-10
+    assert _rel(dch, dh_ref) <= 1e-9
+    assert abs(dh[0] - dh_ref.sum()) <= 1e-9 * np.abs(dh_ref).sum()
+    assert _rel(dy, dy_ref) <= 1e-9
+
+
+def test_autograd_matches_central_differences():
+    import torch
+    from paper_1302_4332_b300.autograd import wald_chi2_sum
+    n, p, m = 200, 4, 96
+    s = gwas_synth.study(n, p, 400, 0.6, 1.0, seed=8)
+    blocks = [gwas_synth.dosages(n, 0, 48, seed=8), gwas_synth.dosages(n, 48, m, seed=8)]
+    h = torch.tensor(0.6, dtype=torch.float64, requires_grad=True)
+    y = torch.tensor(s["y"], dtype=torch.float64, requires_grad=True)
+    loss = wald_chi2_sum(h, y, s["Phi"], s["XL"], blocks, bs=64)
+    loss.backward()
+    f = lambda hh, yy: float(wald_chi2_sum(torch.tensor(hh, dtype=torch.float64),
+                                           torch.tensor(yy, dtype=torch.float64), s["Phi"], s["XL"], blocks, bs=64))
+    d = 1e-6
+    fd_h = (f(0.6 + d, s["y"]) - f(0.6 - d, s["y"])) / (2 * d)
+    assert abs(h.grad.item() - fd_h) <= 1e-6 * abs(fd_h)
+    for j in (0, 57, 199):
+        yp, ym = s["y"].copy(), s["y"].copy()
+        yp[j] += d
+        ym[j] -= d
+        fd = (f(0.6, yp) - f(0.6, ym)) / (2 * d)
+        assert abs(y.grad[j].item() - fd) <= 1e-6 * max(1.0, abs(fd)), (j, y.grad[j].item(), fd)
+
+
+def test_adjoint_paper_scale_n5000():
+    """The differentiation workload: n = 5,000, p = 4, h = 0.5, one 512-SNP block."""
+    n, p, m = 5000, 4, 512
+    s = gwas_synth.study(n, p, 5000, 0.5, 1.0, seed=4)
+    X = gwas_synth.dosages(n, 0, m, seed=4)
+    L = oracle.potrf(oracle.form_m(s["Phi"], 0.5, 1.0))
+    c_ref, dh_ref, dy_ref = oracle.gls_grad(L, s["Phi"], 0.5, 1.0, s["XL"], s["y"], X)
+    with gw.GLS(s["Phi"], s["XL"], s["y"], 0.5, 1.0, bs=m) as g:
+        chi2, dch, dh, dy = g.adjoint_block(X)
+    assert _rel(chi2, c_ref) <= 1e-10
+    assert _rel(dch, dh_ref) <= 1e-6 and abs(dh[0] - dh_ref.sum()) <= 1e-6 * np.abs(dh_ref).sum()
+    assert _rel(dy, dy_ref) <= 1e-6
+
+
+@pytest.mark.parametrize("h", [0.2, 0.5, 0.9])
+def test_reml_eval_matches_oracle(h):
+    s = gwas_synth.study(400, 3, 800, 0.5, seed=6)
+    l, dl, s2 = gw.reml_eval(s["Phi"], s["XL"], s["y"], h)
+    lo, dlo, s2o = oracle.reml(s["Phi"], s["XL"], s["y"], h)
+    assert abs(l - lo) <= 1e-9 * abs(lo)
+    assert abs(dl - dlo) <= 1e-8 * max(1.0, abs(dlo))
+    assert abs(s2 - s2o) <= 1e-10 * s2o
+
+
+def test_reml_fit_matches_oracle_argmax():
+    s = gwas_synth.study(600, 3, 1200, 0.5, seed=10)
+    h_hat, ll, evals = gw.reml_fit(s["Phi"], s["XL"], s["y"], h0=0.2, tol=1e-9)
+    h_ref = oracle.reml_argmax(s["Phi"], s["XL"], s["y"], tol=1e-9)
+    assert abs(h_hat - h_ref) <= 1e-6, (h_hat, h_ref, evals)
+
+
+def test_reml_fit_n2000_oracle_gradient_changes_sign():
+    """A larger null model: the oracle's dense dl/dh changes sign across the GPU fit."""
+    s = gwas_synth.study(2000, 3, 2000, 0.5, seed=12)
+    h_hat, ll, evals = gw.reml_fit(s["Phi"], s["XL"], s["y"], h0=0.2, tol=1e-9)
+    g_lo = oracle.reml(s["Phi"], s["XL"], s["y"], h_hat - 1e-6)[1]
+    g_hi = oracle.reml(s["Phi"], s["XL"], s["y"], h_hat + 1e-6)[1]
+    assert g_lo > 0 > g_hi, (h_hat, g_lo, g_hi)
