@@ -186,6 +186,34 @@ int gwas_reml_fit(int n, int q, const double *phi, const double *XL, const doubl
                   int max_evals, const gwas_config *cfg, void *stream, double *h_out, double *loglik_out,
                   int *evals_out);
 
+/* The batching form (not in the paper): several studies -- each its own
+ * context (own n, factor and operator), all in the same split precision on
+ * the same device -- solved by ONE persistent tensor-core launch whose tiles
+ * come from all studies, row panel by row panel (or study after study), so
+ * small studies never leave SMs idle.  The whole step (shift pre-passes, the
+ * batched launch, every study's reductions) is captured into a CUDA graph on
+ * first use and replayed; a new ncols vector or tile order re-captures it.
+ * At most 8 studies. */
+typedef struct gwas_batch gwas_batch;
+int gwas_batch_create(gwas_batch **out, gwas_ctx *const *studies, int nstudies, void *stream);
+/* XR[i] n_i x ncols[i] int8 (leading dimension ldx[i], host or device), ncols[i] <= bs of
+ * study i (0 skips it); b[i], se[i] p x ncols[i]; status[i] ncols[i] (se, status and
+ * their entries may be NULL).  Inputs are copied into the batch's fixed device slots;
+ * asynchronous on the batch stream when every pointer is device memory. */
+int gwas_batch_solve(gwas_batch *B, const int8_t *const *XR, const int64_t *ldx, const int *ncols,
+                     double *const *b, double *const *se, int *const *status);
+int gwas_batch_synchronize(gwas_batch *B);
+/* 0: interleave the studies row panel by row panel (default); 1: one study after another. */
+int gwas_batch_set_order(gwas_batch *B, int order_mode);
+/* Autotuner: times the captured step (reps replays after one warm-up, CUDA
+ * events) for SNP columns per study per launch in 512, 1024, ... up to the
+ * smallest bs, and both tile orders; keeps the fastest order and reports its
+ * columns and rate (SNPs/s over all studies).  Overwrites the input slots. */
+int gwas_batch_autotune(gwas_batch *B, int reps, int *cols_out, int *order_out, double *snps_per_s_out);
+int64_t gwas_batch_kernel_launches(const gwas_batch *B);
+const char *gwas_batch_last_error_detail(const gwas_batch *B);
+void gwas_batch_destroy(gwas_batch *B);
+
 /* Waits for the context's queued work and reports device-side errors
  * (GWAS_ERR_TIMEOUT when a bounded wait inside a kernel gave up). */
 int gwas_synchronize(gwas_ctx *ctx);

@@ -35,7 +35,9 @@ EXPORTS = (
     "gwas_synchronize", "gwas_set_stream", "gwas_get_info", "gwas_not_spd_index", "gwas_copy_factor",
     "gwas_kernel_launches", "gwas_strerror", "gwas_last_error_detail", "gwas_destroy",
     "gwas_timing_enable", "gwas_timing_read", "gwas_solve_block_static", "gwas_adjoint_block",
-    "gwas_reml_eval", "gwas_reml_fit",
+    "gwas_reml_eval", "gwas_reml_fit", "gwas_batch_create", "gwas_batch_solve", "gwas_batch_synchronize",
+    "gwas_batch_set_order", "gwas_batch_autotune", "gwas_batch_kernel_launches", "gwas_batch_last_error_detail",
+    "gwas_batch_destroy",
 )
 STAGES = ("h2d", "trsm", "reduce", "d2h")
 
@@ -111,6 +113,23 @@ def load(path: str | None = None):
     lib.gwas_reml_fit.argtypes = [c_int, c_int, vp, vp, vp, dp, dp, c_int, ctypes.POINTER(_Config), vp,
                                   ctypes.POINTER(dp), ctypes.POINTER(dp), ctypes.POINTER(c_int)]
     lib.gwas_reml_fit.restype = c_int
+    P = ctypes.POINTER
+    lib.gwas_batch_create.argtypes = [P(vp), P(vp), c_int, vp]
+    lib.gwas_batch_create.restype = c_int
+    lib.gwas_batch_solve.argtypes = [vp, P(vp), P(i64), P(c_int), P(vp), P(vp), P(vp)]
+    lib.gwas_batch_solve.restype = c_int
+    lib.gwas_batch_synchronize.argtypes = [vp]
+    lib.gwas_batch_synchronize.restype = c_int
+    lib.gwas_batch_set_order.argtypes = [vp, c_int]
+    lib.gwas_batch_set_order.restype = c_int
+    lib.gwas_batch_autotune.argtypes = [vp, c_int, P(c_int), P(c_int), P(dp)]
+    lib.gwas_batch_autotune.restype = c_int
+    lib.gwas_batch_kernel_launches.argtypes = [vp]
+    lib.gwas_batch_kernel_launches.restype = i64
+    lib.gwas_batch_last_error_detail.argtypes = [vp]
+    lib.gwas_batch_last_error_detail.restype = ctypes.c_char_p
+    lib.gwas_batch_destroy.argtypes = [vp]
+    lib.gwas_batch_destroy.restype = None
     lib.gwas_destroy.argtypes = [vp]
     lib.gwas_destroy.restype = None
     _lib = lib
@@ -359,6 +378,90 @@ class GLS:
         if getattr(self, "_ctx", None):
             load().gwas_destroy(self._ctx)
             self._ctx = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class GLSBatch:
+    """The batching form: several split-precision studies (GLS objects) solved
+    by one persistent tensor-core launch, replayed from a captured CUDA graph.
+    The GLS objects must outlive the batch."""
+
+    def __init__(self, studies, stream=None):
+        lib = load()
+        self.studies = list(studies)
+        arr = (ctypes.c_void_p * len(self.studies))(*[g._ctx for g in self.studies])
+        B = ctypes.c_void_p()
+        sp = None if stream is None else (stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream))
+        rc = lib.gwas_batch_create(ctypes.byref(B), arr, len(self.studies), sp)
+        if rc != GWAS_OK:
+            raise GwasError(rc, (lib.gwas_last_error_detail(None) or b"").decode())
+        self._B = B
+
+    def _check(self, rc):
+        if rc != GWAS_OK:
+            raise GwasError(rc, (load().gwas_batch_last_error_detail(self._B) or b"").decode())
+
+    def solve(self, blocks):
+        """blocks[i]: n_i x ncols_i int8 (column-major; None or 0 columns skips study i).
+        Returns a list of (b, se, status) per study (None for skipped studies)."""
+        ns = len(self.studies)
+        xs, lds, ncs, outs, keep = [], [], [], [], []
+        for g, X in zip(self.studies, blocks):
+            if X is None or (hasattr(X, "shape") and X.shape[1] == 0):
+                xs.append(None); lds.append(g.n); ncs.append(0); outs.append(None)
+                continue
+            xp, ld, k = _colmajor(X, np.int8, g.n, "XR")
+            keep.append(k)
+            nc = int(k.shape[1])
+            if _is_torch(k) and k.is_cuda:
+                torch = _torch()
+                o = (torch.empty((nc, g.p), dtype=torch.float64, device=k.device).T,
+                     torch.empty((nc, g.p), dtype=torch.float64, device=k.device).T,
+                     torch.empty(nc, dtype=torch.int32, device=k.device))
+            else:
+                o = (np.empty((g.p, nc), order="F"), np.empty((g.p, nc), order="F"), np.empty(nc, dtype=np.int32))
+            xs.append(xp); lds.append(ld); ncs.append(nc); outs.append(o)
+        ptr = lambda a: None if a is None else (a.data_ptr() if _is_torch(a) else a.ctypes.data)
+        VP = ctypes.c_void_p * ns
+        rc = load().gwas_batch_solve(self._B, VP(*xs), (ctypes.c_int64 * ns)(*lds), (ctypes.c_int * ns)(*ncs),
+                                     VP(*[ptr(o[0]) if o else None for o in outs]),
+                                     VP(*[ptr(o[1]) if o else None for o in outs]),
+                                     VP(*[ptr(o[2]) if o else None for o in outs]))
+        self._check(rc)
+        return outs
+
+    def synchronize(self):
+        self._check(load().gwas_batch_synchronize(self._B))
+
+    def set_order(self, mode: int):
+        self._check(load().gwas_batch_set_order(self._B, int(mode)))
+
+    def autotune(self, reps: int = 3):
+        """(columns per study per launch, tile order, SNPs/s) of the fastest measured configuration."""
+        c, o, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        self._check(load().gwas_batch_autotune(self._B, int(reps), ctypes.byref(c), ctypes.byref(o),
+                                               ctypes.byref(r)))
+        return c.value, o.value, r.value
+
+    @property
+    def kernel_launches(self) -> int:
+        return int(load().gwas_batch_kernel_launches(self._B))
+
+    def close(self):
+        if getattr(self, "_B", None):
+            load().gwas_batch_destroy(self._B)
+            self._B = None
 
     def __enter__(self):
         return self

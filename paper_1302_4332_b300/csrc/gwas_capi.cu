@@ -795,6 +795,256 @@ int gwas_reml_fit(int n, int q, const double* phi, const double* XL, const doubl
   return GWAS_OK;
 }
 
+}  // extern "C"
+
+// ------------------------------------------------------------ batching form
+struct gwas_batch {
+  int ns = 0;
+  int dev = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<gwas_ctx*> ctx;
+  std::vector<tc::TcState*> ts;
+  tc::TcBatchState* tb = nullptr;
+  std::vector<int8_t*> slot;    // per study: n_pad x bs int8 input slot
+  std::vector<double*> d_b, d_se;
+  std::vector<int*> d_st;
+  cudaGraph_t graph = nullptr;
+  cudaGraphExec_t exec = nullptr;
+  std::vector<int> planned_cols;
+  int planned_order = -1;
+  int order_mode = 0;
+  int64_t launches = 0;
+  int64_t launches_per_step = 0;
+  std::string detail;
+};
+
+namespace {
+
+int bfail(gwas_batch* B, int code, const char* msg, cudaError_t e = cudaSuccess) {
+  if (B) B->detail = std::string(msg) + (e != cudaSuccess ? std::string(": ") + cudaGetErrorString(e) : "");
+  return code;
+}
+
+#define BCK(call, msg)                                                                                      \
+  do {                                                                                                     \
+    cudaError_t e_ = (call);                                                                               \
+    if (e_ != cudaSuccess) return bfail(B, e_ == cudaErrorMemoryAllocation ? GWAS_ERR_NOMEM : GWAS_ERR_CUDA, msg, e_); \
+  } while (0)
+
+void batch_free(gwas_batch* B) {
+  if (!B) return;
+  cudaSetDevice(B->dev);
+  if (B->stream) cudaStreamSynchronize(B->stream);
+  if (B->exec) cudaGraphExecDestroy(B->exec);
+  if (B->graph) cudaGraphDestroy(B->graph);
+  for (auto* p : B->slot) cudaFree(p);
+  for (auto* p : B->d_b) cudaFree(p);
+  for (auto* p : B->d_se) cudaFree(p);
+  for (auto* p : B->d_st) cudaFree(p);
+  if (B->tb) tc::batch_destroy(B->tb);
+  if (B->own_stream && B->stream) cudaStreamDestroy(B->stream);
+  delete B;
+}
+
+// Plans for cols[] and captures the whole step into a CUDA graph.
+int batch_capture(gwas_batch* B, const std::vector<int>& cols, int order) {
+  std::vector<const int8_t*> X(B->ns);
+  std::vector<int64_t> ld(B->ns);
+  for (int i = 0; i < B->ns; ++i) {
+    X[i] = B->slot[i];
+    ld[i] = B->ctx[i]->n_pad;
+  }
+  BCK(tc::batch_plan(B->tb, B->ts.data(), X.data(), ld.data(), cols.data(), order, B->stream), "batch plan");
+  if (B->exec) { cudaGraphExecDestroy(B->exec); B->exec = nullptr; }
+  if (B->graph) { cudaGraphDestroy(B->graph); B->graph = nullptr; }
+  BCK(cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
+  int64_t nl = 0;
+  cudaError_t e = tc::batch_launch(B->tb, B->ts.data(), B->stream, &nl);
+  for (int i = 0; i < B->ns && e == cudaSuccess; ++i) {
+    gwas_ctx* c = B->ctx[i];
+    if (cols[i] == 0) continue;
+    e = launch_reduce_solve(tc::xt_f32(c->tcs), XT_F32, tc::xt_ld(c->tcs), c->n_pad, c->W, c->n_pad, c->sc, c->q,
+                            cols[i], B->d_b[i], B->d_se[i], B->d_st[i], B->stream, c->W32, tc::shift_of(c->tcs));
+    ++nl;
+  }
+  cudaGraph_t g = nullptr;
+  cudaError_t e2 = cudaStreamEndCapture(B->stream, &g);
+  if (e != cudaSuccess) { if (g) cudaGraphDestroy(g); return bfail(B, GWAS_ERR_CUDA, "capture", e); }
+  BCK(e2, "end capture");
+  B->graph = g;
+  BCK(cudaGraphInstantiate(&B->exec, g, 0), "instantiate");
+  B->planned_cols = cols;
+  B->planned_order = order;
+  B->launches_per_step = nl;
+  return GWAS_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int gwas_batch_create(gwas_batch** out, gwas_ctx* const* studies, int nstudies, void* stream) {
+  if (!out || !studies || nstudies < 1 || nstudies > tc::kMaxBatchStudies) return GWAS_ERR_ARG;
+  *out = nullptr;
+  for (int i = 0; i < nstudies; ++i) {
+    if (!studies[i] || !studies[i]->tcs) return GWAS_ERR_ARG;  // split-precision contexts only
+    if (studies[i]->prec != studies[0]->prec || studies[i]->dev != studies[0]->dev) return GWAS_ERR_ARG;
+  }
+  gwas_batch* B = new gwas_batch;
+  B->ns = nstudies;
+  B->dev = studies[0]->dev;
+  int rc = [&]() -> int {
+    BCK(cudaSetDevice(B->dev), "set device");
+    if (stream) {
+      B->stream = static_cast<cudaStream_t>(stream);
+    } else {
+      BCK(cudaStreamCreateWithFlags(&B->stream, cudaStreamNonBlocking), "stream");
+      B->own_stream = true;
+    }
+    for (int i = 0; i < nstudies; ++i) {
+      gwas_ctx* c = studies[i];
+      B->ctx.push_back(c);
+      B->ts.push_back(c->tcs);
+      int8_t* sl = nullptr;
+      double *db = nullptr, *dse = nullptr;
+      int* dst = nullptr;
+      BCK(dmalloc(&sl, (size_t)c->n_pad * c->bs), "slot");
+      B->slot.push_back(sl);
+      BCK(cudaMemsetAsync(sl, 0, (size_t)c->n_pad * c->bs, B->stream), "slot clear");
+      BCK(dmalloc(&db, sizeof(double) * (size_t)c->p * c->bs), "b");
+      B->d_b.push_back(db);
+      BCK(dmalloc(&dse, sizeof(double) * (size_t)c->p * c->bs), "se");
+      B->d_se.push_back(dse);
+      BCK(dmalloc(&dst, sizeof(int) * (size_t)c->bs), "status");
+      B->d_st.push_back(dst);
+    }
+    BCK(tc::batch_create(&B->tb, B->ts.data(), nstudies), "batch state");
+    BCK(cudaStreamSynchronize(B->stream), "sync");
+    return GWAS_OK;
+  }();
+  if (rc != GWAS_OK) {
+    tl_init_detail = B->detail;
+    batch_free(B);
+    return rc;
+  }
+  *out = B;
+  return GWAS_OK;
+}
+
+int gwas_batch_set_order(gwas_batch* B, int order_mode) {
+  if (!B || order_mode < 0 || order_mode > 1) return GWAS_ERR_ARG;
+  B->order_mode = order_mode;
+  return GWAS_OK;
+}
+
+int gwas_batch_solve(gwas_batch* B, const int8_t* const* XR, const int64_t* ldx, const int* ncols, double* const* b,
+                     double* const* se, int* const* status) {
+  if (!B || !XR || !ldx || !ncols || !b) return GWAS_ERR_ARG;
+  std::vector<int> cols(B->ns);
+  bool any_host = false;
+  for (int i = 0; i < B->ns; ++i) {
+    gwas_ctx* c = B->ctx[i];
+    if (ncols[i] < 0 || ncols[i] > c->bs || (ncols[i] > 0 && (!XR[i] || !b[i] || ldx[i] < c->n)))
+      return bfail(B, GWAS_ERR_ARG, "bad arguments to gwas_batch_solve");
+    cols[i] = ncols[i];
+  }
+  BCK(cudaSetDevice(B->dev), "set device");
+  for (int i = 0; i < B->ns; ++i) {
+    if (cols[i] == 0) continue;
+    gwas_ctx* c = B->ctx[i];
+    const bool dev_in = is_device_ptr(XR[i]);
+    any_host |= !dev_in;
+    BCK(cudaMemcpy2DAsync(B->slot[i], (size_t)c->n_pad, XR[i], (size_t)ldx[i], (size_t)c->n, (size_t)cols[i],
+                          dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, B->stream),
+        "input copy");
+  }
+  if (!B->exec || cols != B->planned_cols || B->order_mode != B->planned_order) {
+    int rc = batch_capture(B, cols, B->order_mode);
+    if (rc != GWAS_OK) return rc;
+  }
+  BCK(cudaGraphLaunch(B->exec, B->stream), "graph launch");
+  B->launches += B->launches_per_step;
+  for (int i = 0; i < B->ns; ++i) {
+    if (cols[i] == 0) continue;
+    gwas_ctx* c = B->ctx[i];
+    any_host |= !is_device_ptr(b[i]) || (se && se[i] && !is_device_ptr(se[i])) ||
+                (status && status[i] && !is_device_ptr(status[i]));
+    BCK(cudaMemcpyAsync(b[i], B->d_b[i], sizeof(double) * (size_t)c->p * cols[i], cudaMemcpyDefault, B->stream),
+        "b out");
+    if (se && se[i])
+      BCK(cudaMemcpyAsync(se[i], B->d_se[i], sizeof(double) * (size_t)c->p * cols[i], cudaMemcpyDefault, B->stream),
+          "se out");
+    if (status && status[i])
+      BCK(cudaMemcpyAsync(status[i], B->d_st[i], sizeof(int) * (size_t)cols[i], cudaMemcpyDefault, B->stream),
+          "status out");
+  }
+  if (!any_host) return GWAS_OK;
+  BCK(cudaStreamSynchronize(B->stream), "sync");
+  for (int i = 0; i < B->ns; ++i) {
+    int rc = check_device_status(B->ctx[i]);
+    if (rc != GWAS_OK) return bfail(B, rc, "device-side wait ran out");
+  }
+  return GWAS_OK;
+}
+
+int gwas_batch_synchronize(gwas_batch* B) {
+  if (!B) return GWAS_ERR_ARG;
+  BCK(cudaSetDevice(B->dev), "set device");
+  BCK(cudaStreamSynchronize(B->stream), "sync");
+  for (int i = 0; i < B->ns; ++i) {
+    int rc = check_device_status(B->ctx[i]);
+    if (rc != GWAS_OK) return bfail(B, rc, "device-side wait ran out");
+  }
+  return GWAS_OK;
+}
+
+int gwas_batch_autotune(gwas_batch* B, int reps, int* cols_out, int* order_out, double* snps_per_s_out) {
+  if (!B || !cols_out || reps < 1) return GWAS_ERR_ARG;
+  BCK(cudaSetDevice(B->dev), "set device");
+  int maxc = 1 << 30;
+  for (auto* c : B->ctx) maxc = std::min(maxc, c->bs);
+  // synthetic dosages: any values cost the same; fill the slots with 1
+  for (int i = 0; i < B->ns; ++i)
+    BCK(cudaMemsetAsync(B->slot[i], 1, (size_t)B->ctx[i]->n_pad * B->ctx[i]->bs, B->stream), "fill");
+  cudaEvent_t e0, e1;
+  BCK(cudaEventCreate(&e0), "event");
+  BCK(cudaEventCreate(&e1), "event");
+  double best = -1.0;
+  int best_cols = 0, best_order = 0;
+  for (int cand = 512; cand <= maxc; cand *= 2) {
+    for (int order = 0; order <= 1; ++order) {
+      std::vector<int> cols(B->ns, cand);
+      int rc = batch_capture(B, cols, order);
+      if (rc != GWAS_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
+      BCK(cudaGraphLaunch(B->exec, B->stream), "warm-up");
+      BCK(cudaEventRecord(e0, B->stream), "event");
+      for (int r = 0; r < reps; ++r) BCK(cudaGraphLaunch(B->exec, B->stream), "timed");
+      BCK(cudaEventRecord(e1, B->stream), "event");
+      BCK(cudaEventSynchronize(e1), "event sync");
+      float ms = 0.f;
+      BCK(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+      const double rate = (double)cand * B->ns * reps / (ms * 1e-3);
+      if (rate > best) { best = rate; best_cols = cand; best_order = order; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  B->order_mode = best_order;
+  *cols_out = best_cols;
+  if (order_out) *order_out = best_order;
+  if (snps_per_s_out) *snps_per_s_out = best;
+  for (int i = 0; i < B->ns; ++i) {
+    int rc = check_device_status(B->ctx[i]);
+    if (rc != GWAS_OK) return bfail(B, rc, "device-side wait ran out");
+  }
+  return GWAS_OK;
+}
+
+int64_t gwas_batch_kernel_launches(const gwas_batch* B) { return B ? B->launches : 0; }
+const char* gwas_batch_last_error_detail(const gwas_batch* B) { return B ? B->detail.c_str() : ""; }
+void gwas_batch_destroy(gwas_batch* B) { batch_free(B); }
+
 int gwas_synchronize(gwas_ctx* ctx) {
   if (!ctx) return GWAS_ERR_ARG;
   CK(cudaSetDevice(ctx->dev));

@@ -39,6 +39,8 @@
 #include <cuda_bf16.h>
 
 #include <cstdio>
+#include <cstring>
+#include <vector>
 
 #include "tc_ptx.cuh"
 #include "trsm_tc.cuh"
@@ -68,25 +70,58 @@ struct Cfg {
   static constexpr int SMEM = 1024 + BAR_OFF + NBARS * 8 + TRING * 4 + 16;
 };
 
-struct TcParams {
+constexpr int MAX_STUDIES = 8;  // studies in one batched launch
+
+// One study of a launch: its block geometry and buffers.
+struct TcStudy {
   int P, C, ncols, n;
   const int8_t* shift;  // per-SNP integer shift c_i (x' = x - c_i on rows < n), or null
-  int* flags;
-  unsigned int* counter;
-  float* xt32;   // FP32 X~ (n_pad x bs); the B "hi" piece in TF32 mode
-  void* bhi;     // BF16 mode: hi piece of X~
-  void* blo;     // lo piece of X~ (BF16 or FP32)
+  int* flags;           // P x C finished-flags of this launch
+  float* xt32;          // FP32 X~ (n_pad x bs); the B "hi" piece in TF32 mode
+  void* bhi;            // BF16 mode: hi piece of X~
+  void* blo;            // lo piece of X~ (BF16 or FP32)
   int64_t ldt;
+};
+
+// The tensor maps of one study: block operator hi/lo, X~ hi/lo, int8 block.
+struct TcMaps {
+  CUtensorMap Ahi, Alo, Bhi, Blo, X8;
+};
+
+// A launch over one or several studies (the batching form): tiles of all
+// studies are handed out from one counter in the order of `order`, which
+// interleaves the studies row panel by row panel so that every study's
+// dependency chain advances while the SMs stay busy.
+struct TcBatch {
+  TcMaps maps[MAX_STUDIES];
+  TcStudy s0;                 // the study when there is only one (order == null)
+  const TcStudy* studies;     // device copies of the studies when order != null
+  const uint32_t* order;      // tile t -> (study << 28) | (k << 14) | c
+  int nstudies, ntiles;
+  unsigned int* counter;
   DevStatus* st;
 };
+
+__device__ __forceinline__ void decode_tile(const TcBatch& b, int t, int& s, int& k, int& c, TcStudy& S) {
+  if (b.order) {
+    const uint32_t v = __ldg(b.order + t);
+    s = (int)(v >> 28);
+    k = (int)((v >> 14) & 0x3FFFu);
+    c = (int)(v & 0x3FFFu);
+    S = b.studies[s];
+  } else {
+    S = b.s0;
+    s = 0;
+    k = t / S.C;
+    c = t % S.C;
+  }
+}
 
 __device__ __forceinline__ uint32_t tf32_trunc_bits(float x) { return __float_as_uint(x) & 0xFFFFE000u; }
 
 template <bool TF32>
 __global__ void __launch_bounds__(THREADS, 1)
-    trsm_tc_kernel(const __grid_constant__ CUtensorMap mAhi, const __grid_constant__ CUtensorMap mAlo,
-                   const __grid_constant__ CUtensorMap mBhi, const __grid_constant__ CUtensorMap mBlo,
-                   const __grid_constant__ CUtensorMap mX8, const TcParams p) {
+    trsm_tc_kernel(const __grid_constant__ TcBatch b) {
   using K = Cfg<TF32>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -105,8 +140,8 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tile_ring + TRING);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ntiles = p.P * p.C;
-  DevStatus* st = p.st;
+  const int ntiles = b.ntiles;
+  DevStatus* st = b.st;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -125,11 +160,13 @@ __global__ void __launch_bounds__(THREADS, 1)
     ptx::mbar_init(x8_empty, 1);
     ptx::mbar_init(drain, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    ptx::prefetch_tensormap(&mAhi);
-    ptx::prefetch_tensormap(&mAlo);
-    ptx::prefetch_tensormap(&mBhi);
-    ptx::prefetch_tensormap(&mBlo);
-    ptx::prefetch_tensormap(&mX8);
+    for (int q = 0; q < b.nstudies; ++q) {
+      ptx::prefetch_tensormap(&b.maps[q].Ahi);
+      ptx::prefetch_tensormap(&b.maps[q].Alo);
+      ptx::prefetch_tensormap(&b.maps[q].Bhi);
+      ptx::prefetch_tensormap(&b.maps[q].Blo);
+      ptx::prefetch_tensormap(&b.maps[q].X8);
+    }
   }
   if (warp == 2) {
     ptx::tmem_alloc(tmem_slot, 2 * TN);
@@ -148,20 +185,23 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int slot = it % TRING;
         const uint32_t use = it / TRING;
         if (!ptx::mbar_wait(&tile_empty[slot], (use & 1) ^ 1, st)) break;
-        int t = ptx::aborting(st) ? ntiles : (int)atomicAdd(p.counter, 1u);
+        int t = ptx::aborting(st) ? ntiles : (int)atomicAdd(b.counter, 1u);
         if (t > ntiles) t = ntiles;
         tile_ring[slot] = t;
         ptx::mbar_arrive(&tile_full[slot]);
         if (t >= ntiles) break;
-        const int k = t / p.C, c = t % p.C;
+        int sidx, k, c;
+        TcStudy S;
+        decode_tile(b, t, sidx, k, c, S);
+        const TcMaps& M = b.maps[sidx];
         if (!ptx::mbar_wait(x8_empty, (it & 1) ^ 1, st)) break;
         ptx::mbar_arrive_expect_tx(x8_full, K::X8_BYTES);
-        ptx::tma_load_2d(x8, &mX8, x8_full, k * TB, c * TN);
+        ptx::tma_load_2d(x8, &M.X8, x8_full, k * TB, c * TN);
         bool ok = true;
         for (int jj = 0; jj <= k && ok; ++jj) {
           const int j = (jj == 0) ? k : jj - 1;
           if (jj > 0) {
-            if (!ptx::wait_flag(&p.flags[j * p.C + c], st)) { ok = false; break; }
+            if (!ptx::wait_flag(&S.flags[j * S.C + c], st)) { ok = false; break; }
             ptx::fence_proxy_async_global();
           }
           for (int h = 0; h < K::CPB; ++h, ++cnt) {
@@ -172,14 +212,14 @@ __global__ void __launch_bounds__(THREADS, 1)
             const int kx = j * TB + h * K::KCH;
             if (jj == 0) {
               ptx::mbar_arrive_expect_tx(&full[s], 2 * K::A_BYTES);
-              ptx::tma_load_2d(sb, &mAhi, &full[s], kx, k * TB);
-              ptx::tma_load_2d(sb + K::A_BYTES, &mAlo, &full[s], kx, k * TB);
+              ptx::tma_load_2d(sb, &M.Ahi, &full[s], kx, k * TB);
+              ptx::tma_load_2d(sb + K::A_BYTES, &M.Alo, &full[s], kx, k * TB);
             } else {
               ptx::mbar_arrive_expect_tx(&full[s], 2 * K::A_BYTES + 2 * K::B_BYTES);
-              ptx::tma_load_2d(sb, &mAhi, &full[s], kx, k * TB);
-              ptx::tma_load_2d(sb + K::A_BYTES, &mAlo, &full[s], kx, k * TB);
-              ptx::tma_load_2d(sb + 2 * K::A_BYTES, &mBhi, &full[s], kx, c * TN);
-              ptx::tma_load_2d(sb + 2 * K::A_BYTES + K::B_BYTES, &mBlo, &full[s], kx, c * TN);
+              ptx::tma_load_2d(sb, &M.Ahi, &full[s], kx, k * TB);
+              ptx::tma_load_2d(sb + K::A_BYTES, &M.Alo, &full[s], kx, k * TB);
+              ptx::tma_load_2d(sb + 2 * K::A_BYTES, &M.Bhi, &full[s], kx, c * TN);
+              ptx::tma_load_2d(sb + 2 * K::A_BYTES + K::B_BYTES, &M.Blo, &full[s], kx, c * TN);
               ptx::mbar_arrive(&full[s]);
             }
           }
@@ -199,7 +239,9 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int t = tile_ring[slot];
         ptx::mbar_arrive(&tile_empty[slot]);
         if (t >= ntiles) break;
-        const int k = t / p.C;
+        int sidx, k, c;
+        TcStudy S;
+        decode_tile(b, t, sidx, k, c, S);
         bool ok = true;
         for (int jj = 0; jj <= k && ok; ++jj, ++kb) {
           // a fresh partial per K-block, alternating between the two TMEM buffers
@@ -248,7 +290,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       ptx::named_bar(2, 64);
       if (lane == 0) ptx::mbar_arrive(&tile_empty[slot]);
       if (t >= ntiles) break;
-      const int k = t / p.C, ctile = t % p.C;
+      int sidx, k, ctile;
+      TcStudy S;
+      decode_tile(b, t, sidx, k, ctile, S);
       if (!ptx::group_and(2, 64, ptx::mbar_wait(x8_full, it & 1, st))) break;
       bool ok = true;
       for (int h = 0; h < K::CPB; ++h) {
@@ -259,7 +303,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int col = ct; col < TN; col += 64) {
           const int8_t* src = reinterpret_cast<const int8_t*>(x8 + col * TB + h * K::KCH);
           const int colg = ctile * TN + col;
-          const int csh = (p.shift && colg < p.ncols) ? p.shift[colg] : 0;
+          const int csh = (S.shift && colg < S.ncols) ? S.shift[colg] : 0;
           const int row0 = k * TB + h * K::KCH;
 #pragma unroll
           for (int q = 0; q < 4; ++q) {  // four 16-byte chunks per 64-byte row
@@ -269,13 +313,13 @@ __global__ void __launch_bounds__(THREADS, 1)
               const char4 v = *reinterpret_cast<const char4*>(src + q * E);
               const signed char e4[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-              for (int i = 0; i < 4; ++i) f[i] = (row0 + q * E + i < p.n) ? (float)(e4[i] - csh) : 0.f;
+              for (int i = 0; i < 4; ++i) f[i] = (row0 + q * E + i < S.n) ? (float)(e4[i] - csh) : 0.f;
             } else {
               const char4 v0 = *reinterpret_cast<const char4*>(src + q * E);
               const char4 v1 = *reinterpret_cast<const char4*>(src + q * E + 4);
               const signed char e8[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
 #pragma unroll
-              for (int i = 0; i < 8; ++i) f[i] = (row0 + q * E + i < p.n) ? (float)(e8[i] - csh) : 0.f;
+              for (int i = 0; i < 8; ++i) f[i] = (row0 + q * E + i < S.n) ? (float)(e8[i] - csh) : 0.f;
             }
             uint32_t w[4];
             if constexpr (TF32) {
@@ -318,7 +362,9 @@ __global__ void __launch_bounds__(THREADS, 1)
       ptx::named_bar(1, NT);
       if (lane == 0) ptx::mbar_arrive(&tile_empty[slot]);
       if (t >= ntiles) break;
-      const int k = t / p.C, c = t % p.C;
+      int sidx, k, c;
+      TcStudy S;
+      decode_tile(b, t, sidx, k, c, S);
 #pragma unroll
       for (int i = 0; i < EPI_COLS; ++i) master[i] = 0.f;
       bool ok = true;
@@ -345,16 +391,16 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
       for (int i = 0; i < EPI_COLS; ++i) {
         const int col = col0 + i;
-        if (col < p.ncols) {
+        if (col < S.ncols) {
           const float x = master[i];
-          const int64_t idx = (int64_t)col * p.ldt + row;
-          p.xt32[idx] = x;
+          const int64_t idx = (int64_t)col * S.ldt + row;
+          S.xt32[idx] = x;
           if constexpr (TF32) {
-            static_cast<float*>(p.blo)[idx] = x - __uint_as_float(tf32_trunc_bits(x));
+            static_cast<float*>(S.blo)[idx] = x - __uint_as_float(tf32_trunc_bits(x));
           } else {
             const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-            static_cast<__nv_bfloat16*>(p.bhi)[idx] = hi;
-            static_cast<__nv_bfloat16*>(p.blo)[idx] = __float2bfloat16_rn(x - __bfloat162float(hi));
+            static_cast<__nv_bfloat16*>(S.bhi)[idx] = hi;
+            static_cast<__nv_bfloat16*>(S.blo)[idx] = __float2bfloat16_rn(x - __bfloat162float(hi));
           }
         }
       }
@@ -362,7 +408,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       if (e == 0 && lane == 0) {
         ptx::fence_proxy_async_global();
         __threadfence();
-        ptx::st_release(&p.flags[k * p.C + c], 1);
+        ptx::st_release(&S.flags[k * S.C + c], 1);
       }
     }
   }
@@ -544,16 +590,15 @@ cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_p
   return cudaSuccess;
 }
 
-cudaError_t run_block(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaStream_t s, int64_t* launches) {
-  if (ncols <= 0) return cudaSuccess;
+// The study part of one launch: int8 map, cleared flags, integer shifts.
+static cudaError_t prepare_study(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaStream_t s,
+                                 int64_t* launches, TcStudy* S, CUtensorMap* mX8) {
   if (ncols > t->bs || (reinterpret_cast<uintptr_t>(X) & 15) || (ldx & 15) || ldx < t->n)
     return cudaErrorInvalidValue;
-  CUtensorMap mX8;
-  cudaError_t e = make_map(t->encode, &mX8, CU_TENSOR_MAP_DATA_TYPE_UINT8, X, (uint64_t)t->n, (uint64_t)ncols,
+  cudaError_t e = make_map(t->encode, mX8, CU_TENSOR_MAP_DATA_TYPE_UINT8, X, (uint64_t)t->n, (uint64_t)ncols,
                            (uint64_t)ldx, TB, TN, false);
   if (e != cudaSuccess) return e;
   const int C = (ncols + TN - 1) / TN;
-  const int ntiles = t->P * C;
   e = cudaMemsetAsync(t->sched, 0, 128 + sizeof(int) * (size_t)t->P * C, s);
   if (e != cudaSuccess) return e;
   if (t->center) {
@@ -561,26 +606,182 @@ cudaError_t run_block(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaS
     ++*launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  TcParams p;
-  p.P = t->P;
-  p.C = C;
-  p.ncols = ncols;
-  p.n = t->n;
-  p.shift = t->center ? t->shift : nullptr;
-  p.counter = t->sched;
-  p.flags = reinterpret_cast<int*>(t->sched + 32);
-  p.xt32 = t->xt32;
-  p.bhi = t->bhi;
-  p.blo = t->blo;
-  p.ldt = t->ldt;
-  p.st = t->st;
-  const int grid = ntiles < t->num_sms ? ntiles : t->num_sms;
-  if (t->tf32)
-    trsm_tc_kernel<true><<<grid, THREADS, Cfg<true>::SMEM, s>>>(t->mAhi, t->mAlo, t->mBhi, t->mBlo, mX8, p);
+  S->P = t->P;
+  S->C = C;
+  S->ncols = ncols;
+  S->n = t->n;
+  S->shift = t->center ? t->shift : nullptr;
+  S->flags = reinterpret_cast<int*>(t->sched + 32);
+  S->xt32 = t->xt32;
+  S->bhi = t->bhi;
+  S->blo = t->blo;
+  S->ldt = t->ldt;
+  return cudaSuccess;
+}
+
+static cudaError_t launch_kernel(bool tf32, const TcBatch& b, int num_sms, cudaStream_t s, int64_t* launches) {
+  const int grid = b.ntiles < num_sms ? b.ntiles : num_sms;
+  if (tf32)
+    trsm_tc_kernel<true><<<grid, THREADS, Cfg<true>::SMEM, s>>>(b);
   else
-    trsm_tc_kernel<false><<<grid, THREADS, Cfg<false>::SMEM, s>>>(t->mAhi, t->mAlo, t->mBhi, t->mBlo, mX8, p);
+    trsm_tc_kernel<false><<<grid, THREADS, Cfg<false>::SMEM, s>>>(b);
   ++*launches;
   return cudaGetLastError();
+}
+
+cudaError_t run_block(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaStream_t s, int64_t* launches) {
+  if (ncols <= 0) return cudaSuccess;
+  TcBatch b;
+  memset(&b, 0, sizeof b);
+  cudaError_t e = prepare_study(t, X, ldx, ncols, s, launches, &b.s0, &b.maps[0].X8);
+  if (e != cudaSuccess) return e;
+  b.maps[0].Ahi = t->mAhi;
+  b.maps[0].Alo = t->mAlo;
+  b.maps[0].Bhi = t->mBhi;
+  b.maps[0].Blo = t->mBlo;
+  b.nstudies = 1;
+  b.ntiles = t->P * b.s0.C;
+  b.counter = t->sched;
+  b.st = t->st;
+  return launch_kernel(t->tf32, b, t->num_sms, s, launches);
+}
+
+// ------------------------------------------------------------- batched launch
+struct TcBatchState {
+  int nstudies = 0;
+  int ntiles = 0;
+  TcStudy S[MAX_STUDIES];
+  CUtensorMap mX8[MAX_STUDIES];
+  const int8_t* X[MAX_STUDIES];
+  int64_t ldx[MAX_STUDIES];
+  bool tf32 = false;
+  int num_sms = 0;
+  TcStudy* d_studies = nullptr;  // device copies
+  uint32_t* d_order = nullptr;
+  unsigned int* d_counter = nullptr;
+  size_t order_cap = 0;
+  DevStatus* st = nullptr;
+};
+
+cudaError_t batch_create(TcBatchState** out, TcState* const* ts, int nstudies) {
+  *out = nullptr;
+  if (nstudies < 1 || nstudies > MAX_STUDIES) return cudaErrorInvalidValue;
+  for (int i = 1; i < nstudies; ++i)
+    if (ts[i]->tf32 != ts[0]->tf32) return cudaErrorInvalidValue;
+  TcBatchState* B = new TcBatchState;
+  B->nstudies = nstudies;
+  B->tf32 = ts[0]->tf32;
+  B->num_sms = ts[0]->num_sms;
+  B->st = ts[0]->st;
+  size_t cap = 0;
+  for (int i = 0; i < nstudies; ++i) cap += (size_t)ts[i]->P * ((ts[i]->bs + TN - 1) / TN);
+  B->order_cap = cap;
+  cudaError_t e;
+  if ((e = cudaMalloc(&B->d_studies, sizeof(TcStudy) * MAX_STUDIES)) != cudaSuccess ||
+      (e = cudaMalloc(&B->d_order, sizeof(uint32_t) * cap)) != cudaSuccess ||
+      (e = cudaMalloc(&B->d_counter, 128)) != cudaSuccess) {
+    batch_destroy(B);
+    return e;
+  }
+  *out = B;
+  return cudaSuccess;
+}
+
+// Fixes the launch geometry: the study descriptors and the tile order
+// (order_mode 0: row panel by row panel across the studies; 1: study after
+// study).  Synchronizes the stream (host copies).  The X pointers are the
+// device blocks later launches will read.
+cudaError_t batch_plan(TcBatchState* B, TcState* const* ts, const int8_t* const* X, const int64_t* ldx,
+                       const int* ncols, int order_mode, cudaStream_t s) {
+  TcStudy S[MAX_STUDIES];
+  memset(S, 0, sizeof S);
+  int pmax = 0, total = 0;
+  for (int i = 0; i < B->nstudies; ++i) {
+    TcState* t = ts[i];
+    if (ncols[i] < 0 || ncols[i] > t->bs) return cudaErrorInvalidValue;
+    if (ncols[i] == 0) continue;
+    if ((reinterpret_cast<uintptr_t>(X[i]) & 15) || (ldx[i] & 15) || ldx[i] < t->n) return cudaErrorInvalidValue;
+    cudaError_t e = make_map(t->encode, &B->mX8[i], CU_TENSOR_MAP_DATA_TYPE_UINT8, X[i], (uint64_t)t->n,
+                             (uint64_t)ncols[i], (uint64_t)ldx[i], TB, TN, false);
+    if (e != cudaSuccess) return e;
+    S[i].P = t->P;
+    S[i].C = (ncols[i] + TN - 1) / TN;
+    S[i].ncols = ncols[i];
+    S[i].n = t->n;
+    S[i].shift = t->center ? t->shift : nullptr;
+    S[i].flags = reinterpret_cast<int*>(t->sched + 32);
+    S[i].xt32 = t->xt32;
+    S[i].bhi = t->bhi;
+    S[i].blo = t->blo;
+    S[i].ldt = t->ldt;
+    pmax = t->P > pmax ? t->P : pmax;
+    total += S[i].P * S[i].C;
+  }
+  std::vector<uint32_t> order;
+  order.reserve(total);
+  if (order_mode == 0) {
+    for (int k = 0; k < pmax; ++k)
+      for (int i = 0; i < B->nstudies; ++i)
+        if (ncols[i] > 0 && k < S[i].P)
+          for (int c = 0; c < S[i].C; ++c) order.push_back(((uint32_t)i << 28) | ((uint32_t)k << 14) | (uint32_t)c);
+  } else {
+    for (int i = 0; i < B->nstudies; ++i)
+      for (int k = 0; ncols[i] > 0 && k < S[i].P; ++k)
+        for (int c = 0; c < S[i].C; ++c) order.push_back(((uint32_t)i << 28) | ((uint32_t)k << 14) | (uint32_t)c);
+  }
+  cudaError_t e;
+  if (total > 0 &&
+      (e = cudaMemcpyAsync(B->d_order, order.data(), sizeof(uint32_t) * order.size(), cudaMemcpyHostToDevice, s)) !=
+          cudaSuccess)
+    return e;
+  if ((e = cudaMemcpyAsync(B->d_studies, S, sizeof(TcStudy) * MAX_STUDIES, cudaMemcpyHostToDevice, s)) != cudaSuccess)
+    return e;
+  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
+  memcpy(B->S, S, sizeof S);
+  memcpy(B->X, X, sizeof(const int8_t*) * B->nstudies);
+  memcpy(B->ldx, ldx, sizeof(int64_t) * B->nstudies);
+  B->ntiles = total;
+  return cudaSuccess;
+}
+
+// One planned launch: clear flags and counter, shift pre-passes, the batched
+// kernel.  Only stream-ordered work: can be captured into a CUDA graph.
+cudaError_t batch_launch(TcBatchState* B, TcState* const* ts, cudaStream_t s, int64_t* launches) {
+  if (B->ntiles == 0) return cudaSuccess;
+  TcBatch b;
+  memset(&b, 0, sizeof b);
+  cudaError_t e;
+  for (int i = 0; i < B->nstudies; ++i) {
+    if (B->S[i].ncols == 0) continue;
+    TcState* t = ts[i];
+    if ((e = cudaMemsetAsync(t->sched, 0, 128 + sizeof(int) * (size_t)t->P * B->S[i].C, s)) != cudaSuccess) return e;
+    if (t->center) {
+      column_shift_kernel<<<(B->S[i].ncols + 7) / 8, 256, 0, s>>>(B->X[i], B->ldx[i], t->n, B->S[i].ncols, t->shift);
+      ++*launches;
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    }
+    b.maps[i].Ahi = t->mAhi;
+    b.maps[i].Alo = t->mAlo;
+    b.maps[i].Bhi = t->mBhi;
+    b.maps[i].Blo = t->mBlo;
+    b.maps[i].X8 = B->mX8[i];
+  }
+  if ((e = cudaMemsetAsync(B->d_counter, 0, 128, s)) != cudaSuccess) return e;
+  b.studies = B->d_studies;
+  b.order = B->d_order;
+  b.nstudies = B->nstudies;
+  b.ntiles = B->ntiles;
+  b.counter = B->d_counter;
+  b.st = B->st;
+  return launch_kernel(B->tf32, b, B->num_sms, s, launches);
+}
+
+void batch_destroy(TcBatchState* B) {
+  if (!B) return;
+  cudaFree(B->d_studies);
+  cudaFree(B->d_order);
+  cudaFree(B->d_counter);
+  delete B;
 }
 
 const float* xt_f32(const TcState* t) { return t->xt32; }

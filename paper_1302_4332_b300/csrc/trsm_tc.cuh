@@ -27,6 +27,21 @@ cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_p
 // The FP32 result is left in xt_f32() with leading dimension xt_ld().
 cudaError_t run_block(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaStream_t s, int64_t* launches);
 
+// The batching form: one persistent launch over several studies (each with its
+// own operator and buffers; all BF16 or all TF32).  ts[i] solves ncols[i]
+// columns of X[i]; results land in each study's xt_f32().
+struct TcBatchState;
+cudaError_t batch_create(TcBatchState** out, TcState* const* ts, int nstudies);
+// Fixes the geometry of later launches (device blocks X[i], ncols[i];
+// order_mode 0 interleaves the studies row panel by row panel, 1 runs them
+// one after another); synchronizes the stream.
+cudaError_t batch_plan(TcBatchState* B, TcState* const* ts, const int8_t* const* X, const int64_t* ldx,
+                       const int* ncols, int order_mode, cudaStream_t s);
+// One launch of the planned batch (stream-ordered only: capturable).
+cudaError_t batch_launch(TcBatchState* B, TcState* const* ts, cudaStream_t s, int64_t* launches);
+void batch_destroy(TcBatchState* B);
+constexpr int kMaxBatchStudies = 8;
+
 const float* xt_f32(const TcState* t);
 const int8_t* shift_of(const TcState* t);  // per-SNP shifts of the last block, or null
 int64_t xt_ld(const TcState* t);

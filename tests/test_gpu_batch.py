@@ -1,0 +1,78 @@
+"""The batching form: studies of uneven n in one persistent launch (CUDA
+graph), against each study solved alone and against the FP64 oracle."""
+import numpy as np
+import pytest
+
+import gwas_synth
+import oracle
+import paper_1302_4332_b300 as gw
+from oracle.metrics import compare
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    from paper_1302_4332_b300 import build
+    build.build()
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+
+
+NS = (300, 700, 129, 1000)  # uneven study sizes, one of them a single ragged panel + 1
+
+
+def _studies(prec, bs=512):
+    out = []
+    for i, n in enumerate(NS):
+        s = gwas_synth.study(n, 4, 2 * n, 0.5, 1.0, seed=30, study_id=i)
+        out.append((s, gw.GLS(s["Phi"], s["XL"], s["y"], 0.5, 1.0, precision=prec, bs=bs)))
+    return out
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+def test_batch_matches_single_and_oracle(prec):
+    studies = _studies(prec)
+    gls = [g for _, g in studies]
+    try:
+        with gw.GLSBatch(gls) as B:
+            for rep, c0 in enumerate((0, 512)):  # two steps: the captured graph replays with new data
+                blocks = [gwas_synth.dosages(s["n"], c0, c0 + m, seed=30, study=i)
+                          for i, ((s, _), m) in enumerate(zip(studies, (512, 300, 64, 511)))]
+                outs = B.solve(blocks)
+                for i, ((s, g), X, (b, se, st)) in enumerate(zip(studies, blocks, outs)):
+                    b1, se1, st1 = g.solve_block(X)
+                    np.testing.assert_array_equal(st, st1)
+                    assert np.array_equal(b, b1) and np.array_equal(se, se1), (prec, i, rep)
+                    L = oracle.potrf(oracle.form_m(s["Phi"], 0.5, 1.0))
+                    pick = np.arange(0, X.shape[1], 17)
+                    r, se_o, _, st_o = oracle.gls(L, s["XL"], s["y"], X[:, pick])
+                    e = compare(b[:, pick], se[:, pick], st[pick], r, se_o, st_o)
+                    assert e["b_norm"] <= 1e-5 and e["se_rel"] <= 1e-5, (prec, i, e)
+            # study-after-study order: the same results
+            B.set_order(1)
+            outs2 = B.solve(blocks)
+            for (b, se, st), (b2, se2, st2) in zip(outs, outs2):
+                assert np.array_equal(b, b2) and np.array_equal(st, st2)
+    finally:
+        for g in gls:
+            g.close()
+
+
+def test_batch_autotune_and_skipped_study():
+    studies = _studies("bf16x3", bs=1024)
+    gls = [g for _, g in studies]
+    try:
+        with gw.GLSBatch(gls) as B:
+            cols, order, rate = B.autotune(reps=2)
+            assert cols in (512, 1024) and order in (0, 1) and rate > 0
+            s0, g0 = studies[0]
+            X = gwas_synth.dosages(s0["n"], 0, cols, seed=30, study=0)
+            outs = B.solve([X, None, None, None])
+            assert outs[1] is None
+            b1, se1, st1 = g0.solve_block(X)
+            assert np.array_equal(outs[0][0], b1)
+    finally:
+        for g in gls:
+            g.close()
