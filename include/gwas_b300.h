@@ -214,6 +214,31 @@ int64_t gwas_batch_kernel_launches(const gwas_batch *B);
 const char *gwas_batch_last_error_detail(const gwas_batch *B);
 void gwas_batch_destroy(gwas_batch *B);
 
+/* Out-of-core streaming from a file (Sec. 3.1: disk -> main memory -> GPU).
+ * The file holds n x M int8 dosages, column-major with leading dimension ldx
+ * bytes, after header_bytes; columns col0 .. col0+m-1 are solved (so a run
+ * can resume from a column cursor).  A reader thread prefetches blocks of
+ * cfg.bs columns into three pinned host buffers while earlier blocks are
+ * copied into the device ring and solved; results go to b_host, se_host,
+ * status_host (p x m, p x m, m; the last two may be NULL).
+ * Errors: GWAS_ERR_IO (open failure, read error, file too short),
+ * GWAS_ERR_TIMEOUT (no block within 120 s), and those of gwas_solve_block. */
+int gwas_solve_file(gwas_ctx *ctx, const char *path, int64_t header_bytes, int64_t ldx, int64_t col0, int64_t m,
+                    double *b_host, double *se_host, int *status_host);
+
+/* The prefetching file reader on its own: blocks of block_bytes bytes (the
+ * last one last_bytes, 0 = full) from `offset`, read by a host thread into
+ * `depth` >= 2 pinned buffers ahead of the consumer.  gwas_reader_next waits
+ * (at most timeout_ms) for the next block in file order; its buffer stays
+ * valid until the matching gwas_reader_release (oldest first). */
+typedef struct gwas_reader gwas_reader;
+int gwas_reader_open(gwas_reader **out, const char *path, int64_t offset, int64_t block_bytes, int64_t nblocks,
+                     int64_t last_bytes, int depth);
+int gwas_reader_next(gwas_reader *r, const void **buf, int64_t *bytes, int timeout_ms);
+int gwas_reader_release(gwas_reader *r);
+const char *gwas_reader_error_detail(const gwas_reader *r);
+void gwas_reader_close(gwas_reader *r);
+
 /* Waits for the context's queued work and reports device-side errors
  * (GWAS_ERR_TIMEOUT when a bounded wait inside a kernel gave up). */
 int gwas_synchronize(gwas_ctx *ctx);

@@ -37,7 +37,8 @@ EXPORTS = (
     "gwas_timing_enable", "gwas_timing_read", "gwas_solve_block_static", "gwas_adjoint_block",
     "gwas_reml_eval", "gwas_reml_fit", "gwas_batch_create", "gwas_batch_solve", "gwas_batch_synchronize",
     "gwas_batch_set_order", "gwas_batch_autotune", "gwas_batch_kernel_launches", "gwas_batch_last_error_detail",
-    "gwas_batch_destroy",
+    "gwas_batch_destroy", "gwas_solve_file", "gwas_reader_open", "gwas_reader_next", "gwas_reader_release",
+    "gwas_reader_error_detail", "gwas_reader_close",
 )
 STAGES = ("h2d", "trsm", "reduce", "d2h")
 
@@ -130,6 +131,18 @@ def load(path: str | None = None):
     lib.gwas_batch_last_error_detail.restype = ctypes.c_char_p
     lib.gwas_batch_destroy.argtypes = [vp]
     lib.gwas_batch_destroy.restype = None
+    lib.gwas_solve_file.argtypes = [vp, ctypes.c_char_p, i64, i64, i64, i64, vp, vp, vp]
+    lib.gwas_solve_file.restype = c_int
+    lib.gwas_reader_open.argtypes = [P(vp), ctypes.c_char_p, i64, i64, i64, i64, c_int]
+    lib.gwas_reader_open.restype = c_int
+    lib.gwas_reader_next.argtypes = [vp, P(vp), P(i64), c_int]
+    lib.gwas_reader_next.restype = c_int
+    lib.gwas_reader_release.argtypes = [vp]
+    lib.gwas_reader_release.restype = c_int
+    lib.gwas_reader_error_detail.argtypes = [vp]
+    lib.gwas_reader_error_detail.restype = ctypes.c_char_p
+    lib.gwas_reader_close.argtypes = [vp]
+    lib.gwas_reader_close.restype = None
     lib.gwas_destroy.argtypes = [vp]
     lib.gwas_destroy.restype = None
     _lib = lib
@@ -346,6 +359,16 @@ class GLS:
                                               ptr(dy_accum)))
         return chi2, dchi2_dh, dh_accum, dy_accum
 
+    def solve_file(self, path: str, m: int, ldx: int | None = None, col0: int = 0, header_bytes: int = 0):
+        """Columns col0 .. col0+m-1 of an n x M int8 column-major file (leading
+        dimension ldx bytes, default n), streamed disk -> pinned host -> GPU."""
+        b = np.empty((self.p, m), order="F")
+        se = np.empty((self.p, m), order="F")
+        st = np.empty(m, dtype=np.int32)
+        self._check(load().gwas_solve_file(self._ctx, os.fsencode(path), int(header_bytes), int(ldx or self.n),
+                                           int(col0), int(m), b.ctypes.data, se.ctypes.data, st.ctypes.data))
+        return b, se, st
+
     def synchronize(self):
         self._check(load().gwas_synchronize(self._ctx))
 
@@ -474,3 +497,40 @@ class GLSBatch:
             self.close()
         except Exception:
             pass
+
+
+class Reader:
+    """Prefetching file reader (disk -> pinned host buffers on a host thread)."""
+
+    def __init__(self, path: str, offset: int, block_bytes: int, nblocks: int, last_bytes: int = 0, depth: int = 3):
+        lib = load()
+        r = ctypes.c_void_p()
+        rc = lib.gwas_reader_open(ctypes.byref(r), os.fsencode(path), int(offset), int(block_bytes), int(nblocks),
+                                  int(last_bytes), int(depth))
+        if rc != GWAS_OK:
+            raise GwasError(rc, f"cannot open {path}")
+        self._r = r
+
+    def next(self, timeout_ms: int = 120000):
+        """(pointer, bytes) of the next block; valid until release()."""
+        buf, nb = ctypes.c_void_p(), ctypes.c_int64()
+        rc = load().gwas_reader_next(self._r, ctypes.byref(buf), ctypes.byref(nb), int(timeout_ms))
+        if rc != GWAS_OK:
+            raise GwasError(rc, (load().gwas_reader_error_detail(self._r) or b"").decode())
+        return buf.value, nb.value
+
+    def release(self):
+        rc = load().gwas_reader_release(self._r)
+        if rc != GWAS_OK:
+            raise GwasError(rc, "release without a taken block")
+
+    def close(self):
+        if getattr(self, "_r", None):
+            load().gwas_reader_close(self._r)
+            self._r = None
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()

@@ -588,6 +588,79 @@ int gwas_solve_stream(gwas_ctx* ctx, const int8_t* XR_host, int64_t ldx, int64_t
   return check_device_status(ctx);
 }
 
+int gwas_solve_file(gwas_ctx* ctx, const char* path, int64_t header_bytes, int64_t ldx, int64_t col0, int64_t m,
+                    double* b_host, double* se_host, int* status_host) {
+  if (!ctx) return GWAS_ERR_ARG;
+  if (!path || !b_host || header_bytes < 0 || ldx < ctx->n || col0 < 0 || m < 0)
+    return fail(ctx, GWAS_ERR_ARG, "bad arguments to gwas_solve_file");
+  if (m == 0) return GWAS_OK;
+  CK(cudaSetDevice(ctx->dev));
+  const int R = ctx->ring_depth, bs = ctx->bs, p = ctx->p;
+  const int64_t nblk = (m + bs - 1) / bs;
+  auto cols_of = [&](int64_t blk) { return (int)std::min<int64_t>(bs, m - blk * bs); };
+  gwas_reader* rd = nullptr;
+  int rc = gwas_reader_open(&rd, path, header_bytes + col0 * ldx, ldx * bs, nblk, ldx * cols_of(nblk - 1), 3);
+  if (rc != GWAS_OK) return fail(ctx, rc, "cannot open or buffer %s", path);
+  auto drain = [&](int64_t blk) -> int {
+    const int slot = (int)(blk % R), nc = cols_of(blk);
+    CK(cudaEventSynchronize(ctx->ev_out[slot]));
+    std::memcpy(b_host + blk * bs * p, ctx->h_b + (size_t)slot * p * bs, sizeof(double) * (size_t)p * nc);
+    if (se_host)
+      std::memcpy(se_host + blk * bs * p, ctx->h_se + (size_t)slot * p * bs, sizeof(double) * (size_t)p * nc);
+    if (status_host)
+      std::memcpy(status_host + blk * bs, ctx->h_status + (size_t)slot * bs, sizeof(int) * (size_t)nc);
+    return GWAS_OK;
+  };
+  rc = [&]() -> int {
+    for (int sl = 0; sl < R; ++sl) CK(cudaEventRecord(ctx->ev_free[sl], ctx->stream));
+    for (int64_t blk = 0; blk < nblk; ++blk) {
+      const int slot = (int)(blk % R), nc = cols_of(blk);
+      const void* hb = nullptr;
+      int64_t got = 0;
+      int r2 = gwas_reader_next(rd, &hb, &got, 120000);
+      if (r2 != GWAS_OK) return fail(ctx, r2, "reading block %lld: %s", (long long)blk, gwas_reader_error_detail(rd));
+      CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_free[slot], 0));
+      {
+        StageMark mk(ctx, GWAS_STAGE_H2D, ctx->copy_stream);
+        CK(cudaMemcpy2DAsync(ctx->ring[slot], (size_t)ctx->n_pad, hb, (size_t)ldx, (size_t)ctx->n, (size_t)nc,
+                             cudaMemcpyHostToDevice, ctx->copy_stream));
+      }
+      CK(cudaEventRecord(ctx->ev_copied[slot], ctx->copy_stream));
+      CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_copied[slot], 0));
+      double* ob = ctx->d_b + (size_t)slot * p * bs;
+      double* ose = ctx->d_se + (size_t)slot * p * bs;
+      int* ost = ctx->d_status + (size_t)slot * bs;
+      if ((r2 = run_block(ctx, ctx->ring[slot], true, ctx->n_pad, nc, ob, ose, ost)) != GWAS_OK) return r2;
+      CK(cudaEventRecord(ctx->ev_free[slot], ctx->stream));
+      {
+        StageMark mk(ctx, GWAS_STAGE_D2H, ctx->stream);
+        CK(cudaMemcpyAsync(ctx->h_b + (size_t)slot * p * bs, ob, sizeof(double) * (size_t)p * nc,
+                           cudaMemcpyDeviceToHost, ctx->stream));
+        if (se_host)
+          CK(cudaMemcpyAsync(ctx->h_se + (size_t)slot * p * bs, ose, sizeof(double) * (size_t)p * nc,
+                             cudaMemcpyDeviceToHost, ctx->stream));
+        if (status_host)
+          CK(cudaMemcpyAsync(ctx->h_status + (size_t)slot * bs, ost, sizeof(int) * (size_t)nc, cudaMemcpyDeviceToHost,
+                             ctx->stream));
+      }
+      CK(cudaEventRecord(ctx->ev_out[slot], ctx->stream));
+      // the host buffer of the previous block goes back to the reader once its copy landed
+      if (blk >= 1) {
+        CK(cudaEventSynchronize(ctx->ev_copied[(blk - 1) % R]));
+        gwas_reader_release(rd);
+        if ((r2 = drain(blk - 1)) != GWAS_OK) return r2;
+      }
+    }
+    CK(cudaEventSynchronize(ctx->ev_copied[(nblk - 1) % R]));
+    gwas_reader_release(rd);
+    int r3 = drain(nblk - 1);
+    if (r3 != GWAS_OK) return r3;
+    return check_device_status(ctx);
+  }();
+  gwas_reader_close(rd);
+  return rc;
+}
+
 int gwas_adjoint_block(gwas_ctx* ctx, const int8_t* XR, int64_t ldx, int ncols, double* chi2, double* dchi2_dh,
                        double* dh_accum, double* dy_accum) {
   if (!ctx) return GWAS_ERR_ARG;

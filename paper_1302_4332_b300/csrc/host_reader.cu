@@ -1,0 +1,153 @@
+// Disk -> pinned host memory, ahead of the GPU (Sec. 3.1: the data is
+// streamed from disk to main memory to the GPU; the paper keeps three host
+// buffers so that a disk read, a host->GPU copy and the CPU's own work can
+// proceed at once).  A reader thread fills a ring of `depth` pinned buffers
+// with consecutive blocks of a file (pread, 64-bit offsets); the consumer
+// takes them in order and hands each back once its host->GPU copy is done.
+// Every wait is bounded; read errors and short reads surface as GWAS_ERR_IO.
+#include <cuda_runtime.h>
+#include <fcntl.h>
+#include <unistd.h>
+
+#include <cerrno>
+#include <chrono>
+#include <condition_variable>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <vector>
+
+#include "gwas_internal.cuh"
+
+struct gwas_reader {
+  int fd = -1;
+  int64_t offset = 0, block_bytes = 0, nblocks = 0, last_bytes = 0;
+  int depth = 0;
+  std::vector<void*> buf;      // pinned
+  std::vector<int64_t> bytes;  // bytes held by each buffer
+  // slot s holds block b when b % depth == s; `filled` counts blocks read,
+  // `taken` blocks handed to the consumer, `released` blocks given back
+  int64_t filled = 0, taken = 0, released = 0;
+  int error = 0;  // GWAS_ERR_IO after a failed or short read
+  std::string detail;
+  bool stop = false;
+  std::mutex mu;
+  std::condition_variable cv;
+  std::thread th;
+};
+
+namespace {
+
+void reader_loop(gwas_reader* r) {
+  for (int64_t b = 0; b < r->nblocks; ++b) {
+    {
+      std::unique_lock<std::mutex> lk(r->mu);
+      r->cv.wait(lk, [&] { return r->stop || b - r->released < r->depth; });
+      if (r->stop) return;
+    }
+    const int s = (int)(b % r->depth);
+    const int64_t want = (b == r->nblocks - 1) ? r->last_bytes : r->block_bytes;
+    int64_t got = 0;
+    char* dst = static_cast<char*>(r->buf[s]);
+    while (got < want) {
+      const ssize_t k = pread(r->fd, dst + got, (size_t)(want - got), (off_t)(r->offset + b * r->block_bytes + got));
+      if (k < 0 && errno == EINTR) continue;
+      if (k <= 0) {
+        std::lock_guard<std::mutex> lk(r->mu);
+        r->error = GWAS_ERR_IO;
+        r->detail = k < 0 ? std::string("read failed: ") + strerror(errno) : "file shorter than the requested blocks";
+        r->cv.notify_all();
+        return;
+      }
+      got += k;
+    }
+    std::lock_guard<std::mutex> lk(r->mu);
+    r->bytes[s] = want;
+    r->filled = b + 1;
+    r->cv.notify_all();
+  }
+}
+
+}  // namespace
+
+extern "C" {
+
+int gwas_reader_open(gwas_reader** out, const char* path, int64_t offset, int64_t block_bytes, int64_t nblocks,
+                     int64_t last_bytes, int depth) {
+  if (!out || !path || offset < 0 || block_bytes < 1 || nblocks < 0 || depth < 2 || last_bytes < 0 ||
+      last_bytes > block_bytes)
+    return GWAS_ERR_ARG;
+  *out = nullptr;
+  gwas_reader* r = new gwas_reader;
+  r->offset = offset;
+  r->block_bytes = block_bytes;
+  r->nblocks = nblocks;
+  r->last_bytes = last_bytes ? last_bytes : block_bytes;
+  r->depth = depth;
+  r->fd = open(path, O_RDONLY);
+  if (r->fd < 0) {
+    delete r;
+    return GWAS_ERR_IO;
+  }
+  r->buf.assign(depth, nullptr);
+  r->bytes.assign(depth, 0);
+  for (auto& p : r->buf) {
+    if (cudaMallocHost(&p, (size_t)block_bytes) != cudaSuccess) {
+      cudaGetLastError();
+      for (auto* q : r->buf) cudaFreeHost(q);
+      close(r->fd);
+      delete r;
+      return GWAS_ERR_NOMEM;
+    }
+  }
+  r->th = std::thread(reader_loop, r);
+  *out = r;
+  return GWAS_OK;
+}
+
+// The next block in file order: *buf (pinned) and *bytes; waits at most
+// timeout_ms.  The buffer stays valid until gwas_reader_release.
+int gwas_reader_next(gwas_reader* r, const void** buf, int64_t* bytes, int timeout_ms) {
+  if (!r || !buf || !bytes) return GWAS_ERR_ARG;
+  std::unique_lock<std::mutex> lk(r->mu);
+  if (r->taken >= r->nblocks) return GWAS_ERR_ARG;
+  const bool ok = r->cv.wait_for(lk, std::chrono::milliseconds(timeout_ms),
+                                 [&] { return r->error || r->filled > r->taken; });
+  if (r->filled > r->taken) {
+    const int s = (int)(r->taken % r->depth);
+    *buf = r->buf[s];
+    *bytes = r->bytes[s];
+    ++r->taken;
+    return GWAS_OK;
+  }
+  if (r->error) return r->error;
+  return ok ? GWAS_ERR_IO : GWAS_ERR_TIMEOUT;
+}
+
+// Gives the oldest taken buffer back to the reader (its copy must be done).
+int gwas_reader_release(gwas_reader* r) {
+  if (!r) return GWAS_ERR_ARG;
+  std::lock_guard<std::mutex> lk(r->mu);
+  if (r->released >= r->taken) return GWAS_ERR_ARG;
+  ++r->released;
+  r->cv.notify_all();
+  return GWAS_OK;
+}
+
+const char* gwas_reader_error_detail(const gwas_reader* r) { return r ? r->detail.c_str() : ""; }
+
+void gwas_reader_close(gwas_reader* r) {
+  if (!r) return;
+  {
+    std::lock_guard<std::mutex> lk(r->mu);
+    r->stop = true;
+    r->cv.notify_all();
+  }
+  if (r->th.joinable()) r->th.join();
+  for (auto* p : r->buf) cudaFreeHost(p);
+  if (r->fd >= 0) close(r->fd);
+  delete r;
+}
+
+}  // extern "C"
