@@ -57,6 +57,7 @@ def parse_args():
     ap.add_argument("--bs", type=int, default=None, help="override bs (smaller smoke runs only)")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-forms", action="store_true", help="skip the batch / disk / adjoint / REML measurements")
     ap.add_argument("--fp64-steps", type=int, default=None,
                     help="steps of the fp64 path when a split path is the headline (default 1)")
     return ap.parse_args()
@@ -357,6 +358,95 @@ def run_ours(args, rank, world, local_rank, dist):
     return dict(w=w, s=s, blocks_h=blocks_h, results=results, peaks=peaks, extra=extra, gen_s=gen_s)
 
 
+STUDY_SIZES = (2000, 3500, 5000, 7000, 9000, 11000, 13500, 16000)  # the multi-study batching workload
+
+
+def measure_forms(args, out):
+    """The other forms on one GPU (rank 0, N = 1): the multi-study batch, disk
+    streaming of the headline path, the adjoint and the REML fit."""
+    import tempfile
+    import torch
+    import gwas_synth
+    import paper_1302_4332_b300 as gw
+    dev = torch.device("cuda", 0)
+    forms = {}
+    # --- batching: 8 studies of uneven n, one persistent graph-captured launch, autotuned
+    t0 = time.time()
+    studies = [gwas_synth.study(n, 4, 2000, 0.6, 1.0, study_id=i) for i, n in enumerate(STUDY_SIZES)]
+    gls = [gw.GLS(s["Phi"], s["XL"], s["y"], 0.6, 1.0, precision="bf16x3", bs=4096) for s in studies]
+    setup_s = time.time() - t0
+    with gw.GLSBatch(gls) as B:
+        cols, order, tuned = B.autotune(reps=2)
+        blocks = [torch.from_numpy(np.ascontiguousarray(gwas_synth.dosages(n, 0, cols, study=i).T)).to(dev).T
+                  for i, n in enumerate(STUDY_SIZES)]
+        for _ in range(2):
+            B.solve(blocks)
+        B.synchronize()
+        l0 = B.kernel_launches
+        steps = max(3, args.steps // 2)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        ev0.record()
+        for _ in range(steps):
+            B.solve(blocks)
+        B.synchronize()
+        ev1.record()
+        torch.cuda.synchronize()
+        t = ev0.elapsed_time(ev1) / 1e3
+        forms["batch"] = dict(
+            workload="8 studies n=" + ",".join(map(str, STUDY_SIZES)) + ", p=4, bf16x3, int8 dosages",
+            snps_per_s=len(STUDY_SIZES) * cols * steps / t, ms_per_step=1e3 * t / steps,
+            snps_per_step=len(STUDY_SIZES) * cols, autotuned_cols_per_study=cols,
+            autotuned_order=("row-panel interleaved" if order == 0 else "study after study"),
+            autotune_snps_per_s=tuned, gpu_launches=B.kernel_launches - l0, steps=steps, setup_s=setup_s,
+            algorithmic_tflops=sum(float(n) * n for n in STUDY_SIZES) * cols * steps / t / 1e12)
+    for g in gls:
+        g.close()
+    del studies, gls, blocks
+    torch.cuda.empty_cache()
+    # --- disk -> pinned host -> GPU for the headline path (the 8 resident blocks in one file)
+    w, s = out["w"], out["s"]
+    n, bs = w["n"], w["bs"]
+    with tempfile.TemporaryDirectory() as td:
+        path = os.path.join(td, "dosages.bin")
+        with open(path, "wb") as f:
+            for X in out["blocks_h"]:
+                f.write(np.ascontiguousarray(X.T).tobytes())
+        m = len(out["blocks_h"]) * bs
+        with gw.GLS(s["Phi"], s["XL"], s["y"], w["h"], w["sigma2"], precision="bf16x3", bs=bs) as g:
+            g.solve_file(path, bs)  # warm
+            t1 = time.perf_counter()
+            reps = 3
+            for _ in range(reps):
+                g.solve_file(path, m)
+            t = time.perf_counter() - t1
+        forms["disk_e2e"] = dict(snps_per_s=reps * m / t, snps=m * reps, bytes_read=reps * m * n,
+                                 note="file just written: served from the page cache")
+    # --- the differentiation workload: n = 5,000, p = 4, FP64 adjoint of one 4096-SNP block
+    s4 = gwas_synth.study(5000, 4, 5000, 0.5, 1.0, study_id=4)
+    X4 = torch.from_numpy(np.ascontiguousarray(gwas_synth.dosages(5000, 0, 4096, study=4).T)).to(dev).T
+    with gw.GLS(s4["Phi"], s4["XL"], s4["y"], 0.5, 1.0, bs=4096) as g:
+        chi2 = torch.zeros(4096, dtype=torch.float64, device=dev)
+        dch = torch.zeros(4096, dtype=torch.float64, device=dev)
+        dh = torch.zeros(1, dtype=torch.float64, device=dev)
+        dy = torch.zeros(5000, dtype=torch.float64, device=dev)
+        g.adjoint_block(X4, dh, dy, chi2, dch)
+        g.synchronize()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for _ in range(2):
+            g.adjoint_block(X4, dh, dy, chi2, dch)
+        g.synchronize()
+        t = (time.perf_counter() - t1) / 2
+    forms["adjoint_fp64"] = dict(workload="n=5000, p=4, 4096 SNPs per block", snps_per_s=4096 / t,
+                                 ms_per_block=1e3 * t)
+    t1 = time.perf_counter()
+    h_hat, ll, evals = gw.reml_fit(s4["Phi"], s4["XL"][:, :3], s4["y"], h0=0.2, tol=1e-8)
+    forms["reml_fit"] = dict(workload="null model n=5000, q=3, true h=0.5, from h0=0.2", h_hat=h_hat,
+                             loglik=ll, likelihood_evaluations=evals, seconds=time.perf_counter() - t1)
+    return forms
+
+
 def cpu_baseline(w, s, X_sample, target_s=12.0):
     """The oracle as it stands on the host cores: Cholesky first (not timed,
     as the paper leaves set-up out), then per-SNP GLS on a bounded sample."""
@@ -412,6 +502,12 @@ def main():
             dist.destroy_process_group()
         return 0
 
+    forms = None
+    if world == 1 and not args.no_forms:
+        try:
+            forms = measure_forms(args, out)
+        except Exception as e:  # report, do not hide
+            forms = {"error": repr(e)}
     cpu = None
     oracle_out = None
     if world == 1 and not args.no_cpu_baseline:
@@ -443,7 +539,7 @@ def main():
                    "headline_path": head, "parallelism": f"snp-shard x{world}",
                    "l2": "inputs larger than L2: 8 resident int8 blocks (328 MB) per step plus the n x n block operator streamed every block"},
         "roofline": hr["roofline"], "e2e": hr.get("e2e"), "gpu_launches": hr["gpu_launches"],
-        "clocks": hr["clocks"], "cpu_baseline": cpu, "paths": paths_out,
+        "clocks": hr["clocks"], "cpu_baseline": cpu, "paths": paths_out, "forms": forms,
         "peaks": {"measured_file": {k: out["peaks"].get(k) for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained")},
                   "measured_here": out["extra"]},
     }

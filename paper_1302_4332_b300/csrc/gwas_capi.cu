@@ -46,6 +46,9 @@ struct gwas_ctx {
   double* What = nullptr;      // n_pad x (q+1): [X^_L | y^]
   double* GH = nullptr;        // (q+1)^2 Gram of What
   double* adj = nullptr;       // per-SNP chi2 (bs), dh (bs), y-weights (bs x p), uT (q), dh/dy staging (1 + n)
+  // pinned host buffers of the file reader, kept across gwas_solve_file calls
+  std::vector<void*> file_buf;
+  int64_t file_buf_bytes = 0;
   // device staging for host arguments
   std::vector<int8_t*> ring;      // ring_depth slots of n_pad x bs int8
   std::vector<cudaEvent_t> ev_copied, ev_free, ev_out;
@@ -302,6 +305,7 @@ void free_all(gwas_ctx* c) {
   cudaFree(c->AopT); cudaFree(c->Xhat); cudaFree(c->What); cudaFree(c->GH); cudaFree(c->adj);
   cudaFreeHost(c->h_b); cudaFreeHost(c->h_se); cudaFreeHost(c->h_status);
   if (c->tcs) tc::destroy(c->tcs);
+  for (auto* p : c->file_buf) cudaFreeHost(p);
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   delete c;
 }
@@ -598,9 +602,17 @@ int gwas_solve_file(gwas_ctx* ctx, const char* path, int64_t header_bytes, int64
   const int R = ctx->ring_depth, bs = ctx->bs, p = ctx->p;
   const int64_t nblk = (m + bs - 1) / bs;
   auto cols_of = [&](int64_t blk) { return (int)std::min<int64_t>(bs, m - blk * bs); };
+  if (ctx->file_buf_bytes < ldx * bs) {
+    for (auto* q : ctx->file_buf) cudaFreeHost(q);
+    ctx->file_buf.assign(3, nullptr);
+    ctx->file_buf_bytes = 0;
+    for (auto& q : ctx->file_buf) CK(cudaMallocHost(&q, (size_t)(ldx * bs)));
+    ctx->file_buf_bytes = ldx * bs;
+  }
   gwas_reader* rd = nullptr;
-  int rc = gwas_reader_open(&rd, path, header_bytes + col0 * ldx, ldx * bs, nblk, ldx * cols_of(nblk - 1), 3);
-  if (rc != GWAS_OK) return fail(ctx, rc, "cannot open or buffer %s", path);
+  int rc = reader_open_with(&rd, path, header_bytes + col0 * ldx, ldx * bs, nblk, ldx * cols_of(nblk - 1), 3,
+                            ctx->file_buf.data());
+  if (rc != GWAS_OK) return fail(ctx, rc, "cannot open %s", path);
   auto drain = [&](int64_t blk) -> int {
     const int slot = (int)(blk % R), nc = cols_of(blk);
     CK(cudaEventSynchronize(ctx->ev_out[slot]));

@@ -151,4 +151,8 @@ struct CtxView {
 };
 bool ctx_view(gwas_ctx* ctx, CtxView* v);
 
+// The file reader over caller-owned pinned buffers (host_reader.cu).
+int reader_open_with(gwas_reader** out, const char* path, int64_t offset, int64_t block_bytes, int64_t nblocks,
+                     int64_t last_bytes, int depth, void* const* buffers);
+
 }  // namespace gwas

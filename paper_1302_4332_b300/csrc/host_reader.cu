@@ -25,6 +25,7 @@ struct gwas_reader {
   int64_t offset = 0, block_bytes = 0, nblocks = 0, last_bytes = 0;
   int depth = 0;
   std::vector<void*> buf;      // pinned
+  bool own_buffers = true;     // false: the caller's buffers, kept on close
   std::vector<int64_t> bytes;  // bytes held by each buffer
   // slot s holds block b when b % depth == s; `filled` counts blocks read,
   // `taken` blocks handed to the consumer, `released` blocks given back
@@ -70,6 +71,37 @@ void reader_loop(gwas_reader* r) {
 }
 
 }  // namespace
+
+namespace gwas {
+
+// As gwas_reader_open with `depth` caller-owned pinned buffers of at least
+// block_bytes each (not freed on close): repeated streams reuse one pinned pool.
+int reader_open_with(gwas_reader** out, const char* path, int64_t offset, int64_t block_bytes, int64_t nblocks,
+                     int64_t last_bytes, int depth, void* const* buffers) {
+  if (!out || !path || !buffers || offset < 0 || block_bytes < 1 || nblocks < 0 || depth < 2 || last_bytes < 0 ||
+      last_bytes > block_bytes)
+    return GWAS_ERR_ARG;
+  *out = nullptr;
+  gwas_reader* r = new gwas_reader;
+  r->offset = offset;
+  r->block_bytes = block_bytes;
+  r->nblocks = nblocks;
+  r->last_bytes = last_bytes ? last_bytes : block_bytes;
+  r->depth = depth;
+  r->fd = open(path, O_RDONLY);
+  if (r->fd < 0) {
+    delete r;
+    return GWAS_ERR_IO;
+  }
+  r->buf.assign(buffers, buffers + depth);
+  r->bytes.assign(depth, 0);
+  r->own_buffers = false;
+  r->th = std::thread(reader_loop, r);
+  *out = r;
+  return GWAS_OK;
+}
+
+}  // namespace gwas
 
 extern "C" {
 
@@ -145,7 +177,8 @@ void gwas_reader_close(gwas_reader* r) {
     r->cv.notify_all();
   }
   if (r->th.joinable()) r->th.join();
-  for (auto* p : r->buf) cudaFreeHost(p);
+  if (r->own_buffers)
+    for (auto* p : r->buf) cudaFreeHost(p);
   if (r->fd >= 0) close(r->fd);
   delete r;
 }
