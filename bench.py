@@ -43,6 +43,7 @@ METRIC = "GLS solves/sec (SNPs/s) at n=10k,p=4: split-prec vs FP64 path, % roofl
 UNIT = "SNPs/s"
 WORKLOAD = "n10k_p4_m1M_int8"
 SPLIT_PATHS = ("bf16x3", "tf32x3")
+STRIP_GROUP = 0  # tile order of the split paths: strips per group (0 = all)
 N_RESIDENT_BLOCKS = 8
 
 
@@ -58,6 +59,8 @@ def parse_args():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-forms", action="store_true", help="skip the batch / disk / adjoint / REML measurements")
+    ap.add_argument("--strip-group", type=int, default=None,
+                    help="split paths: column strips per tile-order group (0 = all; default: the measured best)")
     ap.add_argument("--fp64-steps", type=int, default=None,
                     help="steps of the fp64 path when a split path is the headline (default 1)")
     return ap.parse_args()
@@ -279,7 +282,9 @@ def run_ours(args, rank, world, local_rank, dist):
             # the FP64 path is two orders of magnitude slower: one step, a few warm-up blocks
             steps, warm_blocks = (args.fp64_steps or 1), args.warmup
         t_init = time.time()
-        g = gw.GLS(s["Phi"], s["XL"], s["y"], w["h"], w["sigma2"], precision=path, bs=bs)
+        sg = STRIP_GROUP if args.strip_group is None else args.strip_group
+        g = gw.GLS(s["Phi"], s["XL"], s["y"], w["h"], w["sigma2"], precision=path, bs=bs,
+                   strip_group=sg if path != "fp64" else 0)
         init_s = time.time() - t_init
         b = torch.empty((bs, p), dtype=torch.float64, device=dev).T
         se = torch.empty((bs, p), dtype=torch.float64, device=dev).T
@@ -308,6 +313,7 @@ def run_ours(args, rank, world, local_rank, dist):
         g.timing(False)
         res = dict(snps_per_s=job_rate(world, steps * step_snps, elapsed), ms_per_step=1e3 * elapsed / steps, steps=steps,
                    warmup_blocks=warm_blocks, snps_per_step=step_snps, init_s=init_s, gpu_launches=launches,
+                   strip_group=(sg if path != "fp64" else None),
                    clocks=clk.summary(),
                    stage_ms_per_block={k: v[0] / max(v[1], 1) for k, v in stages.items() if v[1]})
         trsm_ms = stages["trsm"][0] / max(stages["trsm"][1], 1)

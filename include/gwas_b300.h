@@ -78,7 +78,10 @@ typedef struct {
   int bs;          /* SNP columns per block: the most columns one solve call takes (>= 1) */
   int ring_depth;  /* device slots of the host->device block ring used by gwas_solve_stream (>= 2) */
   int device;      /* CUDA device ordinal; -1 = the current device */
-  int reserved[4]; /* must be zero */
+  int strip_group; /* split modes: tiles are handed out row panel by row panel over groups of this
+                      many 256-column strips (0 = all strips of the block at once); smaller groups keep
+                      the strips being re-read inside the L2 */
+  int reserved[3]; /* must be zero */
 } gwas_config;
 
 typedef struct gwas_ctx gwas_ctx; /* opaque; owned by the library */

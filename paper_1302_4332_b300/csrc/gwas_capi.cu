@@ -347,7 +347,7 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
   gwas_config_default(&cfg);
   if (cfg_in) cfg = *cfg_in;
   if (n < 1 || p < 1 || p > QMAX + 1 || !phi_or_L || !y || (p > 1 && !XL) || !(h >= 0.0 && h <= 1.0) ||
-      !(sigma2 > 0.0) || cfg.bs < 1 || cfg.ring_depth < 2 || cfg.precision < GWAS_FP64 ||
+      !(sigma2 > 0.0) || cfg.bs < 1 || cfg.ring_depth < 2 || cfg.strip_group < 0 || cfg.precision < GWAS_FP64 ||
       cfg.precision > GWAS_BF16X3)
     return GWAS_ERR_ARG;
   for (int r : cfg.reserved)
@@ -473,7 +473,7 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
       int64_t nl = 0;
       cudaError_t e = tc::create(&ctx->tcs, ctx->prec == GWAS_BF16X3 ? tc::SPLIT_BF16 : tc::SPLIT_TF32, ctx->Aop,
                                  ctx->n, ctx->n_pad, cfg.bs, ctx->num_sms, ctx->intercept, ctx->st, ctx->stream,
-                                 &nl);
+                                 &nl, cfg.strip_group);
       ctx->launches += nl;
       if (e != cudaSuccess)
         return fail(ctx, e == cudaErrorMemoryAllocation ? GWAS_ERR_NOMEM : GWAS_ERR_CUDA, "split set-up: %s",
@@ -898,7 +898,9 @@ struct gwas_batch {
   cudaGraphExec_t exec = nullptr;
   std::vector<int> planned_cols;
   int planned_order = -1;
+  int planned_group = -1;
   int order_mode = 0;
+  int strip_group = 0;
   int64_t launches = 0;
   int64_t launches_per_step = 0;
   std::string detail;
@@ -933,14 +935,15 @@ void batch_free(gwas_batch* B) {
 }
 
 // Plans for cols[] and captures the whole step into a CUDA graph.
-int batch_capture(gwas_batch* B, const std::vector<int>& cols, int order) {
+int batch_capture(gwas_batch* B, const std::vector<int>& cols, int order, int group) {
   std::vector<const int8_t*> X(B->ns);
   std::vector<int64_t> ld(B->ns);
   for (int i = 0; i < B->ns; ++i) {
     X[i] = B->slot[i];
     ld[i] = B->ctx[i]->n_pad;
   }
-  BCK(tc::batch_plan(B->tb, B->ts.data(), X.data(), ld.data(), cols.data(), order, B->stream), "batch plan");
+  BCK(tc::batch_plan(B->tb, B->ts.data(), X.data(), ld.data(), cols.data(), order, B->stream, group),
+      "batch plan");
   if (B->exec) { cudaGraphExecDestroy(B->exec); B->exec = nullptr; }
   if (B->graph) { cudaGraphDestroy(B->graph); B->graph = nullptr; }
   BCK(cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
@@ -961,6 +964,7 @@ int batch_capture(gwas_batch* B, const std::vector<int>& cols, int order) {
   BCK(cudaGraphInstantiate(&B->exec, g, 0), "instantiate");
   B->planned_cols = cols;
   B->planned_order = order;
+  B->planned_group = group;
   B->launches_per_step = nl;
   return GWAS_OK;
 }
@@ -1044,8 +1048,9 @@ int gwas_batch_solve(gwas_batch* B, const int8_t* const* XR, const int64_t* ldx,
                           dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, B->stream),
         "input copy");
   }
-  if (!B->exec || cols != B->planned_cols || B->order_mode != B->planned_order) {
-    int rc = batch_capture(B, cols, B->order_mode);
+  if (!B->exec || cols != B->planned_cols || B->order_mode != B->planned_order ||
+      B->strip_group != B->planned_group) {
+    int rc = batch_capture(B, cols, B->order_mode, B->strip_group);
     if (rc != GWAS_OK) return rc;
   }
   BCK(cudaGraphLaunch(B->exec, B->stream), "graph launch");
@@ -1097,10 +1102,15 @@ int gwas_batch_autotune(gwas_batch* B, int reps, int* cols_out, int* order_out, 
   BCK(cudaEventCreate(&e1), "event");
   double best = -1.0;
   int best_cols = 0, best_order = 0;
+  int best_group = 0;
   for (int cand = 512; cand <= maxc; cand *= 2) {
-    for (int order = 0; order <= 1; ++order) {
+    for (int variant = 0; variant < 4; ++variant) {
+      // order 0; order 1 with all strips, groups of 8, groups of 4
+      const int order = variant == 0 ? 0 : 1;
+      const int group = variant <= 1 ? 0 : (variant == 2 ? 8 : 4);
+      if (group && group >= (cand + 255) / 256) continue;
       std::vector<int> cols(B->ns, cand);
-      int rc = batch_capture(B, cols, order);
+      int rc = batch_capture(B, cols, order, group);
       if (rc != GWAS_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
       BCK(cudaGraphLaunch(B->exec, B->stream), "warm-up");
       BCK(cudaEventRecord(e0, B->stream), "event");
@@ -1110,12 +1120,13 @@ int gwas_batch_autotune(gwas_batch* B, int reps, int* cols_out, int* order_out, 
       float ms = 0.f;
       BCK(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
       const double rate = (double)cand * B->ns * reps / (ms * 1e-3);
-      if (rate > best) { best = rate; best_cols = cand; best_order = order; }
+      if (rate > best) { best = rate; best_cols = cand; best_order = order; best_group = group; }
     }
   }
   cudaEventDestroy(e0);
   cudaEventDestroy(e1);
   B->order_mode = best_order;
+  B->strip_group = best_group;
   *cols_out = best_cols;
   if (order_out) *order_out = best_order;
   if (snps_per_s_out) *snps_per_s_out = best;

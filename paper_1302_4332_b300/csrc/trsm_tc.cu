@@ -499,6 +499,10 @@ struct TcState {
   int64_t ldt = 0;
   int8_t* shift = nullptr;        // per-SNP integer shift (bs)
   bool center = false;            // X_L[:, 0] is the intercept: shift SNP columns
+  int strip_group = 0;            // tile order over groups of column strips (0: all)
+  uint32_t* order = nullptr;      // device tile order when strip_group > 0
+  TcStudy* study_dev = nullptr;   // device copy of the study descriptor (grouped order)
+  int order_C = -1;               // the column-strip count the order was built for
   unsigned int* sched = nullptr;  // [0] counter, flags from +32
   size_t sched_bytes = 0;
   DevStatus* st = nullptr;
@@ -537,7 +541,7 @@ static cudaError_t set_smem_attr() {
 }
 
 cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_pad, int bs, int num_sms,
-                   bool center, DevStatus* st, cudaStream_t s, int64_t* launches) {
+                   bool center, DevStatus* st, cudaStream_t s, int64_t* launches, int strip_group) {
   *out = nullptr;
   TcState* t = new TcState;
   t->tf32 = (split == SPLIT_TF32);
@@ -568,6 +572,11 @@ cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_p
   TRY(cudaMalloc(&t->blo, esz * (size_t)n_pad * bs));
   TRY(cudaMalloc(&t->shift, (size_t)bs));
   t->center = center;
+  t->strip_group = strip_group;
+  if (strip_group > 0) {
+    TRY(cudaMalloc(&t->order, sizeof(uint32_t) * (size_t)t->P * Cmax));
+    TRY(cudaMalloc(&t->study_dev, sizeof(TcStudy)));
+  }
   t->sched_bytes = 128 + sizeof(int) * (size_t)t->P * Cmax;
   TRY(cudaMalloc(&t->sched, t->sched_bytes));
   TRY(cudaMemsetAsync(t->sched, 0, t->sched_bytes, s));
@@ -588,6 +597,16 @@ cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_p
 #undef TRY
   *out = t;
   return cudaSuccess;
+}
+
+// Tile order of one study: row panel by row panel over groups of G column
+// strips (G <= 0 or G >= C: all strips), study index `si` in the top bits.
+static void append_study_order(std::vector<uint32_t>& order, int si, int P, int C, int G) {
+  if (G <= 0 || G > C) G = C;
+  for (int c0 = 0; c0 < C; c0 += G)
+    for (int k = 0; k < P; ++k)
+      for (int c = c0; c < c0 + G && c < C; ++c)
+        order.push_back(((uint32_t)si << 28) | ((uint32_t)k << 14) | (uint32_t)c);
 }
 
 // The study part of one launch: int8 map, cleared flags, integer shifts.
@@ -643,6 +662,21 @@ cudaError_t run_block(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaS
   b.ntiles = t->P * b.s0.C;
   b.counter = t->sched;
   b.st = t->st;
+  if (t->strip_group > 0 && t->strip_group < b.s0.C) {
+    if (t->order_C != b.s0.C) {  // (re)build the grouped order for this strip count
+      std::vector<uint32_t> order;
+      append_study_order(order, 0, t->P, b.s0.C, t->strip_group);
+      if ((e = cudaMemcpyAsync(t->order, order.data(), sizeof(uint32_t) * order.size(), cudaMemcpyHostToDevice, s)) !=
+              cudaSuccess ||
+          (e = cudaStreamSynchronize(s)) != cudaSuccess)
+        return e;
+      t->order_C = b.s0.C;
+    }
+    // the grouped order reads the study descriptor from device memory
+    if ((e = cudaMemcpyAsync(t->study_dev, &b.s0, sizeof(TcStudy), cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
+    b.order = t->order;
+    b.studies = t->study_dev;
+  }
   return launch_kernel(t->tf32, b, t->num_sms, s, launches);
 }
 
@@ -692,7 +726,7 @@ cudaError_t batch_create(TcBatchState** out, TcState* const* ts, int nstudies) {
 // study).  Synchronizes the stream (host copies).  The X pointers are the
 // device blocks later launches will read.
 cudaError_t batch_plan(TcBatchState* B, TcState* const* ts, const int8_t* const* X, const int64_t* ldx,
-                       const int* ncols, int order_mode, cudaStream_t s) {
+                       const int* ncols, int order_mode, cudaStream_t s, int strip_group) {
   TcStudy S[MAX_STUDIES];
   memset(S, 0, sizeof S);
   int pmax = 0, total = 0;
@@ -726,8 +760,7 @@ cudaError_t batch_plan(TcBatchState* B, TcState* const* ts, const int8_t* const*
           for (int c = 0; c < S[i].C; ++c) order.push_back(((uint32_t)i << 28) | ((uint32_t)k << 14) | (uint32_t)c);
   } else {
     for (int i = 0; i < B->nstudies; ++i)
-      for (int k = 0; ncols[i] > 0 && k < S[i].P; ++k)
-        for (int c = 0; c < S[i].C; ++c) order.push_back(((uint32_t)i << 28) | ((uint32_t)k << 14) | (uint32_t)c);
+      if (ncols[i] > 0) append_study_order(order, i, S[i].P, S[i].C, strip_group);
   }
   cudaError_t e;
   if (total > 0 &&
@@ -797,6 +830,8 @@ void destroy(TcState* t) {
   cudaFree(t->blo);
   cudaFree(t->sched);
   cudaFree(t->shift);
+  cudaFree(t->order);
+  cudaFree(t->study_dev);
   delete t;
 }
 

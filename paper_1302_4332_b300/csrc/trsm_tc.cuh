@@ -20,8 +20,10 @@ struct TcState;
 // integer nearest its mean (exact in BF16/TF32; the reductions map the results
 // back), which removes most of the cancellation between the SNP and the
 // intercept in S_BR - S_BL S_TL^-1 S_BL^T.
+// strip_group > 0: tiles go out row panel by row panel over groups of that
+// many column strips (the strips' X~ stays in L2 while it is re-read).
 cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_pad, int bs, int num_sms,
-                   bool center, DevStatus* st, cudaStream_t s, int64_t* launches);
+                   bool center, DevStatus* st, cudaStream_t s, int64_t* launches, int strip_group = 0);
 
 // X~ = L^-1 X for ncols <= bs int8 columns (X 16-byte aligned, ldx % 16 == 0).
 // The FP32 result is left in xt_f32() with leading dimension xt_ld().
@@ -36,7 +38,7 @@ cudaError_t batch_create(TcBatchState** out, TcState* const* ts, int nstudies);
 // order_mode 0 interleaves the studies row panel by row panel, 1 runs them
 // one after another); synchronizes the stream.
 cudaError_t batch_plan(TcBatchState* B, TcState* const* ts, const int8_t* const* X, const int64_t* ldx,
-                       const int* ncols, int order_mode, cudaStream_t s);
+                       const int* ncols, int order_mode, cudaStream_t s, int strip_group = 0);
 // One launch of the planned batch (stream-ordered only: capturable).
 cudaError_t batch_launch(TcBatchState* B, TcState* const* ts, cudaStream_t s, int64_t* launches);
 void batch_destroy(TcBatchState* B);
