@@ -178,57 +178,101 @@ __global__ void __launch_bounds__(256) reduce_solve_kernel(const double* __restr
   if (lane == 0) solve_store<QM>(acc, sc, q, col, b, se, status);
 }
 
-// FP32 X~ (the split paths).  One warp per SNP; each lane takes 4 consecutive
-// rows per 16-byte load of X~ (rows is a multiple of 128, columns 16-byte
-// aligned) with the matching 4 rows of W32 (FP32, row-major, stride WS).
-// FP32 products are summed over 16 rows per lane and each partial is folded
-// into FP64 (B300 runs FP64 at a small fraction of the FP32 rate, and X~
-// itself carries FP32 precision).
-template <int QM, int WS>
-__global__ void __launch_bounds__(256) reduce_solve_f32_kernel(const float* __restrict__ Xt, int64_t ldt, int rows,
-                                                               const float* __restrict__ W32,
-                                                               const SolveConsts* __restrict__ sc, int q,
-                                                               int ncols, double* __restrict__ b,
-                                                               double* __restrict__ se, int* __restrict__ status,
-                                                               const int8_t* __restrict__ shift) {
-  const int lane = threadIdx.x & 31;
-  const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (col >= ncols) return;
-  const float4* x4 = reinterpret_cast<const float4*>(Xt + (int64_t)col * ldt);
-  double acc[QM + 2];
+// FP32 X~ (the split paths).  A block takes 32 SNP columns, one per lane, and
+// splits the rows into SL slices, one per warp.  Each thread streams 32-row
+// runs (one 128-byte line) of its own column, the next run's loads in flight
+// while the current one is summed.  The run's 32 rows of W32 (FP32,
+// row-major, row stride WS) are the same for every lane: the warp loads them
+// once, coalesced, into shared memory and reads them back as broadcasts.  A
+// run's products are summed in FP32, runs are added with Kahan compensation
+// (still FP32: B300 runs FP64 at a small fraction of the FP32 rate), and only
+// the SL slice totals of a column are added in FP64, in a fixed order, so the
+// result is deterministic.  Lanes past ncols read column 0 and discard it.
+constexpr int RS_RUN = 32;
+
+template <int QM, int WS, int SL>
+__global__ void __launch_bounds__(32 * SL) reduce_solve_f32_kernel(
+    const float* __restrict__ Xt, int64_t ldt, int rows, const float* __restrict__ W32,
+    const SolveConsts* __restrict__ sc, int q, int ncols, double* __restrict__ b, double* __restrict__ se,
+    int* __restrict__ status, const int8_t* __restrict__ shift) {
+  constexpr int NA = QM + 2, NW4 = WS / 4, NX4 = RS_RUN / 4;
+  // the W runs (inside the row loop) and the slice totals (after it) share one buffer
+  constexpr int TOT_BYTES = SL * NA * 32 * 8, WSM_BYTES = SL * RS_RUN * NW4 * 16;
+  __shared__ __align__(16) unsigned char smem[TOT_BYTES > WSM_BYTES ? TOT_BYTES : WSM_BYTES];
+  auto tot = reinterpret_cast<double(*)[NA][32]>(smem);
+  auto wsm = reinterpret_cast<float4(*)[RS_RUN * NW4]>(smem);
+  const int lane = threadIdx.x & 31, slice = threadIdx.x >> 5;
+  const int col = blockIdx.x * 32 + lane;
+  const bool live = col < ncols;
+  const float4* x4 = reinterpret_cast<const float4*>(Xt + (int64_t)(live ? col : 0) * ldt);
+  const float4* w4 = reinterpret_cast<const float4*>(W32);
+  float4* wmine = wsm[slice];
+  float ks[NA], kc[NA];  // Kahan sum and compensation
 #pragma unroll
-  for (int a = 0; a < QM + 2; ++a) acc[a] = 0.0;
-  const int nv = rows >> 2;  // float4 groups of rows
-  for (int v0 = lane; v0 < nv; v0 += 32 * 4) {
-    float part[QM + 2];
+  for (int a = 0; a < NA; ++a) ks[a] = kc[a] = 0.f;
+  const int nrun = rows / RS_RUN;
+  float4 xn[NX4], wn[NW4];
+  if (slice < nrun) {
 #pragma unroll
-    for (int a = 0; a < QM + 2; ++a) part[a] = 0.f;
+    for (int i = 0; i < NX4; ++i) xn[i] = __ldcs(x4 + slice * NX4 + i);
 #pragma unroll
-    for (int i = 0; i < 4; ++i) {
-      const int v = v0 + 32 * i;
-      if (v < nv) {
-        const float4 xv = __ldcs(x4 + v);
-        const float xs[4] = {xv.x, xv.y, xv.z, xv.w};
+    for (int v4 = 0; v4 < NW4; ++v4) wn[v4] = __ldg(w4 + (int64_t)(slice * RS_RUN + lane) * NW4 + v4);
+  }
+  for (int run = slice; run < nrun; run += SL) {
+    float4 xv[NX4];
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
-          const float4* wr = reinterpret_cast<const float4*>(W32 + (int64_t)(4 * v + e) * WS);
+    for (int i = 0; i < NX4; ++i) xv[i] = xn[i];
+    __syncwarp();  // the previous run's reads of wmine are done
 #pragma unroll
-          for (int v4 = 0; v4 < WS / 4; ++v4) {
-            const float4 w = __ldg(wr + v4);
-            const float wv[4] = {w.x, w.y, w.z, w.w};
+    for (int v4 = 0; v4 < NW4; ++v4) wmine[lane * NW4 + v4] = wn[v4];
+    __syncwarp();
+    const int nxt = run + SL;
+    if (nxt < nrun) {
 #pragma unroll
-            for (int t = 0; t < 4; ++t)
-              if (4 * v4 + t <= QM) part[4 * v4 + t] = fmaf(xs[e], wv[t], part[4 * v4 + t]);
-          }
-          part[QM + 1] = fmaf(xs[e], xs[e], part[QM + 1]);
+      for (int i = 0; i < NX4; ++i) xn[i] = __ldcs(x4 + nxt * NX4 + i);
+#pragma unroll
+      for (int v4 = 0; v4 < NW4; ++v4) wn[v4] = __ldg(w4 + (int64_t)(nxt * RS_RUN + lane) * NW4 + v4);
+    }
+    float part[NA];
+#pragma unroll
+    for (int a = 0; a < NA; ++a) part[a] = 0.f;
+#pragma unroll
+    for (int i = 0; i < NX4; ++i) {
+      const float xs[4] = {xv[i].x, xv[i].y, xv[i].z, xv[i].w};
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+#pragma unroll
+        for (int v4 = 0; v4 < NW4; ++v4) {
+          const float4 w = wmine[(4 * i + e) * NW4 + v4];
+          const float wv[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+          for (int t = 0; t < 4; ++t)
+            if (4 * v4 + t <= QM) part[4 * v4 + t] = fmaf(xs[e], wv[t], part[4 * v4 + t]);
         }
+        part[QM + 1] = fmaf(xs[e], xs[e], part[QM + 1]);
       }
     }
 #pragma unroll
-    for (int a = 0; a < QM + 2; ++a) acc[a] += (double)part[a];
+    for (int a = 0; a < NA; ++a) {
+      const float y = part[a] - kc[a];
+      const float t = ks[a] + y;
+      kc[a] = (t - ks[a]) - y;
+      ks[a] = t;
+    }
   }
-  warp_sum<QM>(acc);
-  if (lane == 0) solve_store<QM>(acc, sc, q, col, b, se, status, shift ? (double)shift[col] : 0.0);
+  __syncthreads();  // every warp is done with its W runs
+#pragma unroll
+  for (int a = 0; a < NA; ++a) tot[slice][a][lane] = (double)ks[a] - (double)kc[a];
+  __syncthreads();
+  if (slice != 0 || !live) return;
+  double sum[NA];
+#pragma unroll
+  for (int a = 0; a < NA; ++a) {
+    double t = tot[0][a][lane];
+    for (int s2 = 1; s2 < SL; ++s2) t += tot[s2][a][lane];
+    sum[a] = t;
+  }
+  solve_store<QM>(sum, sc, q, col, b, se, status, shift ? (double)shift[col] : 0.0);
 }
 
 cudaError_t launch_reduce_solve(const void* Xt, XtKind kind, int64_t ldt, int rows, const double* W,
@@ -248,13 +292,14 @@ cudaError_t launch_reduce_solve(const void* Xt, XtKind kind, int64_t ldt, int ro
   }
   if (!W32) return cudaErrorInvalidValue;
   const float* X = static_cast<const float*>(Xt);
-  if ((rows & 3) || (ldt & 3)) return cudaErrorInvalidValue;  // 16-byte rows groups
+  if ((rows % RS_RUN) || (ldt % RS_RUN)) return cudaErrorInvalidValue;  // whole 128-byte runs
+  const int g32 = (ncols + 31) / 32;
   if (q <= 3)
-    reduce_solve_f32_kernel<3, 4><<<grid, 256, 0, s>>>(X, ldt, rows, W32, sc, q, ncols, b, se, status, shift);
+    reduce_solve_f32_kernel<3, 4, 16><<<g32, 512, 0, s>>>(X, ldt, rows, W32, sc, q, ncols, b, se, status, shift);
   else if (q <= 7)
-    reduce_solve_f32_kernel<7, 8><<<grid, 256, 0, s>>>(X, ldt, rows, W32, sc, q, ncols, b, se, status, shift);
+    reduce_solve_f32_kernel<7, 8, 16><<<g32, 512, 0, s>>>(X, ldt, rows, W32, sc, q, ncols, b, se, status, shift);
   else
-    reduce_solve_f32_kernel<QMAX, 16><<<grid, 256, 0, s>>>(X, ldt, rows, W32, sc, q, ncols, b, se, status, shift);
+    reduce_solve_f32_kernel<QMAX, 16, 8><<<g32, 256, 0, s>>>(X, ldt, rows, W32, sc, q, ncols, b, se, status, shift);
   return cudaGetLastError();
 }
 
