@@ -61,6 +61,10 @@ def parse_args():
     ap.add_argument("--no-forms", action="store_true", help="skip the batch / disk / adjoint / REML measurements")
     ap.add_argument("--strip-group", type=int, default=None,
                     help="split paths: column strips per tile-order group (0 = all; default: the measured best)")
+    ap.add_argument("--tiles", choices=("auto", "single", "pair_multicast", "pair_mma"), default="auto",
+                    help="split paths: tiles on SMs (auto: the measured fastest; single: one 128-row tile per SM; "
+                         "pair_multicast: row-panel pairs per 2-SM cluster with shared loads; pair_mma: pairs as "
+                         "one 256-row product per cluster)")
     ap.add_argument("--fp64-steps", type=int, default=None,
                     help="steps of the fp64 path when a split path is the headline (default 1)")
     return ap.parse_args()
@@ -284,7 +288,7 @@ def run_ours(args, rank, world, local_rank, dist):
         t_init = time.time()
         sg = STRIP_GROUP if args.strip_group is None else args.strip_group
         g = gw.GLS(s["Phi"], s["XL"], s["y"], w["h"], w["sigma2"], precision=path, bs=bs,
-                   strip_group=sg if path != "fp64" else 0)
+                   strip_group=sg if path != "fp64" else 0, tiles=args.tiles)
         init_s = time.time() - t_init
         b = torch.empty((bs, p), dtype=torch.float64, device=dev).T
         se = torch.empty((bs, p), dtype=torch.float64, device=dev).T
@@ -314,6 +318,7 @@ def run_ours(args, rank, world, local_rank, dist):
         res = dict(snps_per_s=job_rate(world, steps * step_snps, elapsed), ms_per_step=1e3 * elapsed / steps, steps=steps,
                    warmup_blocks=warm_blocks, snps_per_step=step_snps, init_s=init_s, gpu_launches=launches,
                    strip_group=(sg if path != "fp64" else None),
+                   solve_shape=dict(zip(("ctas", "cluster", "tiles"), g.solve_shape())),
                    clocks=clk.summary(),
                    stage_ms_per_block={k: v[0] / max(v[1], 1) for k, v in stages.items() if v[1]})
         trsm_ms = stages["trsm"][0] / max(stages["trsm"][1], 1)

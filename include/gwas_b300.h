@@ -81,8 +81,18 @@ typedef struct {
   int strip_group; /* split modes: tiles are handed out row panel by row panel over groups of this
                       many 256-column strips (0 = all strips of the block at once); smaller groups keep
                       the strips being re-read inside the L2 */
-  int reserved[3]; /* must be zero */
+  int tile_mode;   /* split modes, how the solve's tiles map onto the SMs:
+                      GWAS_TILES_AUTO (0, default): the measured fastest of the others for the split;
+                      GWAS_TILES_SINGLE (1): every 128-row tile on its own SM;
+                      GWAS_TILES_PAIR_MULTICAST (2): the row panels 2u and 2u+1 of a column strip on
+                        the two SMs of a thread-block cluster, each with its own product, the solved
+                        blocks both need fetched once;
+                      GWAS_TILES_PAIR_MMA (3): panels 2u and 2u+1 as one 256-row tensor-core product
+                        on the two SMs of a cluster */
+  int reserved[2]; /* must be zero */
 } gwas_config;
+
+enum { GWAS_TILES_AUTO = 0, GWAS_TILES_SINGLE = 1, GWAS_TILES_PAIR_MULTICAST = 2, GWAS_TILES_PAIR_MMA = 3 };
 
 typedef struct gwas_ctx gwas_ctx; /* opaque; owned by the library */
 
@@ -251,6 +261,12 @@ int gwas_set_stream(gwas_ctx *ctx, void *stream);
 
 /* Study facts: n, p, the padded row count of the device layout, precision. */
 int gwas_get_info(const gwas_ctx *ctx, int *n, int *p, int *n_pad, int *precision, int *bs);
+
+/* Launch shape of the blocked triangular solve for a full block: *ctas thread blocks (one per SM),
+   in clusters of *cluster_size (2 in the pair tile modes, else 1), and *tile_mode, the resolved
+   gwas_config.tile_mode (never GWAS_TILES_AUTO).  FP64 contexts report the occupancy-bound grid of
+   the FP64 solve, 1 and GWAS_TILES_SINGLE.  Any output pointer may be NULL. */
+int gwas_solve_shape(const gwas_ctx *ctx, int *ctas, int *cluster_size, int *tile_mode);
 
 /* Index of the first failing Cholesky pivot after GWAS_ERR_NOT_SPD, else -1. */
 int64_t gwas_not_spd_index(const gwas_ctx *ctx);

@@ -26,13 +26,15 @@ ERRORS = {
     -5: "GWAS_ERR_IO", -6: "GWAS_ERR_NOMEM", -7: "GWAS_ERR_UNSUPPORTED",
 }
 PRECISIONS = {"fp64": 0, "tf32x3": 1, "bf16x3": 2}
+# split modes: how the solve's tiles map onto SMs (gwas_config.tile_mode)
+TILE_MODES = {"auto": 0, "single": 1, "pair_multicast": 2, "pair_mma": 3}
 BUILT_PRECISIONS = ("fp64", "bf16x3", "tf32x3")
 SNP_OK, SNP_SINGULAR = 0, 1
 
 # Every symbol the header declares (checked by the CPU test suite).
 EXPORTS = (
     "gwas_config_default", "gwas_init", "gwas_solve_block", "gwas_solve_block_f64", "gwas_solve_stream",
-    "gwas_synchronize", "gwas_set_stream", "gwas_get_info", "gwas_not_spd_index", "gwas_copy_factor",
+    "gwas_synchronize", "gwas_set_stream", "gwas_get_info", "gwas_solve_shape", "gwas_not_spd_index", "gwas_copy_factor",
     "gwas_kernel_launches", "gwas_strerror", "gwas_last_error_detail", "gwas_destroy",
     "gwas_timing_enable", "gwas_timing_read", "gwas_solve_block_static", "gwas_adjoint_block",
     "gwas_reml_eval", "gwas_reml_fit", "gwas_batch_create", "gwas_batch_solve", "gwas_batch_synchronize",
@@ -58,7 +60,8 @@ class NotSPDError(GwasError):
 
 class _Config(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("bs", ctypes.c_int), ("ring_depth", ctypes.c_int),
-                ("device", ctypes.c_int), ("strip_group", ctypes.c_int), ("reserved", ctypes.c_int * 3)]
+                ("device", ctypes.c_int), ("strip_group", ctypes.c_int), ("tile_mode", ctypes.c_int),
+                ("reserved", ctypes.c_int * 2)]
 
 
 _lib = None
@@ -91,6 +94,8 @@ def load(path: str | None = None):
     lib.gwas_set_stream.restype = c_int
     lib.gwas_get_info.argtypes = [vp] + [ctypes.POINTER(c_int)] * 5
     lib.gwas_get_info.restype = c_int
+    lib.gwas_solve_shape.argtypes = [vp, ctypes.POINTER(c_int), ctypes.POINTER(c_int), ctypes.POINTER(c_int)]
+    lib.gwas_solve_shape.restype = c_int
     lib.gwas_not_spd_index.argtypes = [vp]
     lib.gwas_not_spd_index.restype = i64
     lib.gwas_copy_factor.argtypes = [vp, vp, i64]
@@ -241,7 +246,7 @@ class GLS:
 
     def __init__(self, phi_or_L, XL, y, h: float, sigma2: float = 1.0, *, precision: str = "fp64",
                  bs: int = 4096, ring_depth: int = 3, is_L: bool = False, device: int = -1, stream=None,
-                 strip_group: int = 0):
+                 strip_group: int = 0, tiles: str = "auto"):
         lib = load()
         n = int(np.shape(y)[0]) if not _is_torch(y) else int(y.shape[0])
         q = 0 if XL is None else (int(XL.shape[1]) if np.ndim(XL) == 2 or _is_torch(XL) else 1)
@@ -260,6 +265,7 @@ class GLS:
         cfg.ring_depth = int(ring_depth)
         cfg.device = int(device)
         cfg.strip_group = int(strip_group)
+        cfg.tile_mode = TILE_MODES[tiles]
         self.precision, self.bs = precision, int(bs)
         stream_p = None
         if stream is not None:
@@ -277,6 +283,13 @@ class GLS:
         info = [ctypes.c_int() for _ in range(5)]
         lib.gwas_get_info(ctx, *[ctypes.byref(i) for i in info])
         self.n_pad = info[2].value
+
+    def solve_shape(self) -> tuple[int, int, str]:
+        """(CTAs, cluster size, resolved tile mode) of the blocked triangular solve over a full block."""
+        ctas, cl, mode = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        self._check(load().gwas_solve_shape(self._ctx, ctypes.byref(ctas), ctypes.byref(cl), ctypes.byref(mode)))
+        names = {v: k for k, v in TILE_MODES.items()}
+        return ctas.value, cl.value, names[mode.value]
 
     # -- helpers ---------------------------------------------------------------
     def _check(self, rc: int):

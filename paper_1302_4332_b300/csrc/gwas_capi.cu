@@ -347,7 +347,8 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
   gwas_config_default(&cfg);
   if (cfg_in) cfg = *cfg_in;
   if (n < 1 || p < 1 || p > QMAX + 1 || !phi_or_L || !y || (p > 1 && !XL) || !(h >= 0.0 && h <= 1.0) ||
-      !(sigma2 > 0.0) || cfg.bs < 1 || cfg.ring_depth < 2 || cfg.strip_group < 0 || cfg.precision < GWAS_FP64 ||
+      !(sigma2 > 0.0) || cfg.bs < 1 || cfg.ring_depth < 2 || cfg.strip_group < 0 || cfg.tile_mode < GWAS_TILES_AUTO || cfg.tile_mode > GWAS_TILES_PAIR_MMA ||
+      cfg.precision < GWAS_FP64 ||
       cfg.precision > GWAS_BF16X3)
     return GWAS_ERR_ARG;
   for (int r : cfg.reserved)
@@ -473,7 +474,7 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
       int64_t nl = 0;
       cudaError_t e = tc::create(&ctx->tcs, ctx->prec == GWAS_BF16X3 ? tc::SPLIT_BF16 : tc::SPLIT_TF32, ctx->Aop,
                                  ctx->n, ctx->n_pad, cfg.bs, ctx->num_sms, ctx->intercept, ctx->st, ctx->stream,
-                                 &nl, cfg.strip_group);
+                                 &nl, cfg.strip_group, static_cast<tc::TileMode>(cfg.tile_mode));
       ctx->launches += nl;
       if (e != cudaSuccess)
         return fail(ctx, e == cudaErrorMemoryAllocation ? GWAS_ERR_NOMEM : GWAS_ERR_CUDA, "split set-up: %s",
@@ -1161,6 +1162,27 @@ int gwas_get_info(const gwas_ctx* ctx, int* n, int* p, int* n_pad, int* precisio
   if (n_pad) *n_pad = ctx->n_pad;
   if (precision) *precision = ctx->prec;
   if (bs) *bs = ctx->bs;
+  return GWAS_OK;
+}
+
+int gwas_solve_shape(const gwas_ctx* ctx, int* ctas, int* cluster_size, int* tile_mode) {
+  if (!ctx) return GWAS_ERR_ARG;
+  if (cudaSetDevice(ctx->dev) != cudaSuccess) {
+    cudaGetLastError();
+    return GWAS_ERR_CUDA;
+  }
+  int g = 0, cl = 1, mode = GWAS_TILES_SINGLE;
+  if (ctx->tcs) {
+    tc::launch_shape(ctx->tcs, &g, &cl);
+    mode = static_cast<int>(tc::tile_mode(ctx->tcs));
+  } else {
+    const int tiles = (ctx->n_pad / TB) * ((ctx->bs + F64_TN - 1) / F64_TN);
+    g = trsm_f64_grid(ctx->num_sms);
+    if (g > tiles) g = tiles;
+  }
+  if (ctas) *ctas = g;
+  if (cluster_size) *cluster_size = cl;
+  if (tile_mode) *tile_mode = mode;
   return GWAS_OK;
 }
 

@@ -101,6 +101,8 @@ struct TrsmF64Args {
 // upper = true: Xt = L^-T X with Aop the transpose block operator (FP64 input only).
 cudaError_t launch_trsm_f64(const TrsmF64Args& a, bool int8_input, cudaStream_t s, int num_sms,
                             bool upper = false);
+// CTAs of the FP64 solve when there are at least that many tiles.
+int trsm_f64_grid(int num_sms);
 
 // The transpose block operator (row-major): row panel k holds D_k^-T at
 // block k and -D_k^-T L_jk^T at blocks j > k.

@@ -152,6 +152,15 @@ __global__ void __launch_bounds__(256, 2) trsm_f64_kernel(TrsmF64Args a) {
   }
 }
 
+int trsm_f64_grid(int num_sms) {
+  int per_sm = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, trsm_f64_kernel<int8_t, false>, 256, 0) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return num_sms * (per_sm < 1 ? 1 : per_sm);
+}
+
 cudaError_t launch_trsm_f64(const TrsmF64Args& a, bool int8_input, cudaStream_t s, int num_sms, bool upper) {
   if (a.ncols <= 0) return cudaSuccess;
   int per_sm = 0;

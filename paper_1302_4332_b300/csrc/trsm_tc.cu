@@ -17,11 +17,11 @@
 //     FP64 reductions.
 //
 // Accumulation: the tensor core adds each K-step into its FP32 accumulator
-// with truncation, which biases long sums toward zero.  So every 128-wide
-// K-block (one j) accumulates into a fresh TMEM partial, and the epilogue
-// warps add that partial into an FP32 master held in registers with
-// round-to-nearest adds.  Two TMEM partials alternate so the MMAs of block
-// j+1 overlap the promotion of block j.
+// with truncation, which biases long sums toward zero.  So every PROMOTE
+// 128-wide K-blocks (PROMOTE values of j) accumulate into a fresh TMEM
+// partial, and the epilogue warps add that partial into an FP32 master held
+// in registers with round-to-nearest adds.  Two TMEM partials alternate so
+// the MMAs of the next blocks overlap the promotion of the last ones.
 //
 // One persistent CTA per SM, 12 warps:
 //   warp 0     tile scheduler + TMA producer (one thread)
@@ -54,6 +54,7 @@ constexpr int TRING = 2;     // tile-id ring between the scheduler and the other
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 32 * (4 + EPI_WARPS);
 constexpr int EPI_COLS = TN / 2;  // SNP columns per epilogue warp
+constexpr int PROMOTE = 2;        // K-blocks accumulated in one TMEM partial
 
 template <bool TF32>
 struct Cfg {
@@ -66,7 +67,7 @@ struct Cfg {
   static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
   static constexpr int X8_BYTES = TN * TB;       // int8 diagonal block: 32 KB
   static constexpr int BAR_OFF = STAGES * STAGE_BYTES + X8_BYTES;
-  static constexpr int NBARS = 2 * STAGES + 4 + 2 * TRING + 3;
+  static constexpr int NBARS = 2 * STAGES + 4 + 3 * TRING + 3;
   static constexpr int SMEM = 1024 + BAR_OFF + NBARS * 8 + TRING * 4 + 16;
 };
 
@@ -86,6 +87,7 @@ struct TcStudy {
 // The tensor maps of one study: block operator hi/lo, X~ hi/lo, int8 block.
 struct TcMaps {
   CUtensorMap Ahi, Alo, Bhi, Blo, X8;
+  CUtensorMap BhiH, BloH, X8H;  // half-width boxes (128 SNP columns) for the pair modes
 };
 
 // A launch over one or several studies (the batching form): tiles of all
@@ -119,7 +121,87 @@ __device__ __forceinline__ void decode_tile(const TcBatch& b, int t, int& s, int
 
 __device__ __forceinline__ uint32_t tf32_trunc_bits(float x) { return __float_as_uint(x) & 0xFFFFE000u; }
 
+// Epilogue stores of one warp's 32 rows x EPI_COLS columns of X~: the FP32
+// value (for the reductions; in TF32 mode also the hi operand) and the lo
+// piece, plus the BF16 hi piece in BF16 mode.
 template <bool TF32>
+__device__ __forceinline__ void store_tile(const float (&master)[EPI_COLS], const TcStudy& S, int64_t xrow,
+                                           int col0) {
+#pragma unroll
+  for (int i = 0; i < EPI_COLS; ++i) {
+    const int col = col0 + i;
+    if (col < S.ncols) {
+      const float x = master[i];
+      const int64_t idx = (int64_t)col * S.ldt + xrow;
+      S.xt32[idx] = x;
+      if constexpr (TF32) {
+        static_cast<float*>(S.blo)[idx] = x - __uint_as_float(tf32_trunc_bits(x));
+      } else {
+        const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+        static_cast<__nv_bfloat16*>(S.bhi)[idx] = hi;
+        static_cast<__nv_bfloat16*>(S.blo)[idx] = __float2bfloat16_rn(x - __bfloat162float(hi));
+      }
+    }
+  }
+}
+
+// K-block kinds of a work unit's stage sequence.
+enum KbKind : int {
+  KB_DIAG = 0,    // j == k: Aop hi/lo by TMA, B = the int8 block cast in shared memory
+  KB_SHARED = 1,  // pair mode, j < 2u: each CTA loads its own Aop and half of X~_jc for both
+  KB_LOCAL = 2,   // Aop and all of X~_jc by this CTA alone
+  KB_NULL = 3     // no loads, no MMA: keeps the two CTAs' stage rings in step
+};
+
+// A work unit.  Single mode: the tile (k, c).  Pair mode: the tiles (2u, c)
+// and (2u+1, c) on the two CTAs of a cluster (rank r takes row panel 2u + r).
+struct Unit {
+  int k;        // this CTA's row panel
+  bool has;     // this CTA has a tile (the last unit of an odd P has one)
+  bool paired;  // both CTAs have a tile
+  int nkb;      // K-blocks in the unit's stage sequence (the same on both CTAs)
+};
+
+template <bool PAIR>
+__device__ __forceinline__ Unit make_unit(int row, const TcStudy& S, uint32_t rank) {
+  Unit u;
+  if (PAIR) {
+    u.k = 2 * row + (int)rank;
+    u.has = u.k < S.P;
+    u.paired = 2 * row + 1 < S.P;
+    u.nkb = 2 * row + (u.paired ? 2 : 1);
+  } else {
+    u.k = row;
+    u.has = true;
+    u.paired = false;
+    u.nkb = row + 1;
+  }
+  return u;
+}
+
+// K-block jj of a unit: its kind, and j, the block column of Aop it multiplies.
+// Pair mode, both tiles present: rank 0 runs [diag 2u, shared 0..2u-1, null],
+// rank 1 [diag 2u+1, shared 0..2u-1, local 2u] (X~ of rank 0's own tile).
+template <bool PAIR>
+__device__ __forceinline__ KbKind kb_kind(const Unit& u, int row, uint32_t rank, int jj, int& j) {
+  if (jj == 0) {
+    j = u.k;
+    return u.has ? KB_DIAG : KB_NULL;
+  }
+  if (!PAIR) {
+    j = jj - 1;
+    return KB_LOCAL;
+  }
+  if (jj <= 2 * row) {
+    j = jj - 1;
+    if (u.paired) return KB_SHARED;
+    return rank == 0 ? KB_LOCAL : KB_NULL;
+  }
+  j = 2 * row;
+  return rank == 1 ? KB_LOCAL : KB_NULL;
+}
+
+template <bool TF32, bool PAIR>
 __global__ void __launch_bounds__(THREADS, 1)
     trsm_tc_kernel(const __grid_constant__ TcBatch b) {
   using K = Cfg<TF32>;
@@ -136,17 +218,20 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint64_t* x8_full = tile_empty + TRING;
   uint64_t* x8_empty = x8_full + 1;
   uint64_t* drain = x8_empty + 1;
-  int* tile_ring = reinterpret_cast<int*>(drain + 1);
+  uint64_t* peer_free = drain + 1;  // pair mode, rank 0: rank 1 is done with a tile-ring slot
+  int* tile_ring = reinterpret_cast<int*>(peer_free + TRING);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tile_ring + TRING);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int ntiles = b.ntiles;
+  const int ntiles = b.ntiles;  // work units
   DevStatus* st = b.st;
+  const uint32_t rank = PAIR ? ptx::cluster_ctarank() : 0u;
+  constexpr uint16_t BOTH = 3;  // multicast mask: both CTAs of the pair
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
-      ptx::mbar_init(&full[s], 2);   // producer (+tx) and producer-or-cast
-      ptx::mbar_init(&empty[s], 1);  // MMA commit
+      ptx::mbar_init(&full[s], 2);             // producer (+tx) and producer-or-cast
+      ptx::mbar_init(&empty[s], PAIR ? 2 : 1);  // the MMA commit of every CTA that reads the stage
     }
     for (int a = 0; a < 2; ++a) {
       ptx::mbar_init(&part_full[a], 1);           // MMA commit
@@ -155,6 +240,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int i = 0; i < TRING; ++i) {
       ptx::mbar_init(&tile_full[i], 1);
       ptx::mbar_init(&tile_empty[i], 1 + 2 + EPI_WARPS);  // MMA + cast warps + epilogue warps
+      ptx::mbar_init(&peer_free[i], 1);
     }
     ptx::mbar_init(x8_full, 1);
     ptx::mbar_init(x8_empty, 1);
@@ -166,6 +252,10 @@ __global__ void __launch_bounds__(THREADS, 1)
       ptx::prefetch_tensormap(&b.maps[q].Bhi);
       ptx::prefetch_tensormap(&b.maps[q].Blo);
       ptx::prefetch_tensormap(&b.maps[q].X8);
+      if (PAIR) {
+        ptx::prefetch_tensormap(&b.maps[q].BhiH);
+        ptx::prefetch_tensormap(&b.maps[q].BloH);
+      }
     }
   }
   if (warp == 2) {
@@ -175,32 +265,50 @@ __global__ void __launch_bounds__(THREADS, 1)
   ptx::tc_fence_before();
   __syncthreads();
   ptx::tc_fence_after();
+  if (PAIR) ptx::cluster_sync();  // the peer's barriers exist before any remote access
   const uint32_t tmem_base = *tmem_slot;
 
   if (warp == 0) {
     // ------------------------------------------------ scheduler + TMA producer
     if (lane == 0) {
-      uint32_t cnt = 0;
+      uint32_t cnt = 0, x8n = 0;
       for (int it = 0;; ++it) {
         const int slot = it % TRING;
         const uint32_t use = it / TRING;
         if (!ptx::mbar_wait(&tile_empty[slot], (use & 1) ^ 1, st)) break;
-        int t = ptx::aborting(st) ? ntiles : (int)atomicAdd(b.counter, 1u);
-        if (t > ntiles) t = ntiles;
-        tile_ring[slot] = t;
-        ptx::mbar_arrive(&tile_full[slot]);
+        int t;
+        if (!PAIR || rank == 0) {
+          // pair mode: rank 0 takes the unit for both CTAs and writes it into
+          // rank 1's ring as well, once rank 1 has released the slot
+          if (PAIR && !ptx::mbar_wait(&peer_free[slot], use & 1, st)) break;
+          t = ptx::aborting(st) ? ntiles : (int)atomicAdd(b.counter, 1u);
+          if (t > ntiles) t = ntiles;
+          tile_ring[slot] = t;
+          if (PAIR) ptx::st_peer_u32(ptx::peer_addr(&tile_ring[slot], 1), (uint32_t)t);
+          ptx::mbar_arrive(&tile_full[slot]);
+          if (PAIR) ptx::mbar_arrive_peer(ptx::peer_addr(&tile_full[slot], 1));
+        } else {
+          ptx::mbar_arrive_peer(ptx::peer_addr(&peer_free[slot], 0));
+          if (!ptx::mbar_wait_s<true>(&tile_full[slot], use & 1, st)) break;
+          t = tile_ring[slot];
+        }
         if (t >= ntiles) break;
-        int sidx, k, c;
+        int sidx, row, c;
         TcStudy S;
-        decode_tile(b, t, sidx, k, c, S);
+        decode_tile(b, t, sidx, row, c, S);
         const TcMaps& M = b.maps[sidx];
-        if (!ptx::mbar_wait(x8_empty, (it & 1) ^ 1, st)) break;
-        ptx::mbar_arrive_expect_tx(x8_full, K::X8_BYTES);
-        ptx::tma_load_2d(x8, &M.X8, x8_full, k * TB, c * TN);
+        const Unit u = make_unit<PAIR>(row, S, rank);
+        if (u.has) {
+          if (!ptx::mbar_wait(x8_empty, (x8n & 1) ^ 1, st)) break;
+          ptx::mbar_arrive_expect_tx(x8_full, K::X8_BYTES);
+          ptx::tma_load_2d(x8, &M.X8, x8_full, u.k * TB, c * TN);
+          ++x8n;
+        }
         bool ok = true;
-        for (int jj = 0; jj <= k && ok; ++jj) {
-          const int j = (jj == 0) ? k : jj - 1;
-          if (jj > 0) {
+        for (int jj = 0; jj < u.nkb && ok; ++jj) {
+          int j;
+          const KbKind kind = kb_kind<PAIR>(u, row, rank, jj, j);
+          if (kind == KB_SHARED || kind == KB_LOCAL) {
             if (!ptx::wait_flag(&S.flags[j * S.C + c], st)) { ok = false; break; }
             ptx::fence_proxy_async_global();
           }
@@ -210,16 +318,29 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (!ptx::mbar_wait(&empty[s], (r & 1) ^ 1, st)) { ok = false; break; }
             uint8_t* sb = smem + s * K::STAGE_BYTES;
             const int kx = j * TB + h * K::KCH;
-            if (jj == 0) {
+            if (kind == KB_NULL) {
+              ptx::mbar_arrive(&full[s]);
+              ptx::mbar_arrive(&full[s]);
+            } else if (kind == KB_DIAG) {
               ptx::mbar_arrive_expect_tx(&full[s], 2 * K::A_BYTES);
-              ptx::tma_load_2d(sb, &M.Ahi, &full[s], kx, k * TB);
-              ptx::tma_load_2d(sb + K::A_BYTES, &M.Alo, &full[s], kx, k * TB);
+              ptx::tma_load_2d(sb, &M.Ahi, &full[s], kx, u.k * TB);
+              ptx::tma_load_2d(sb + K::A_BYTES, &M.Alo, &full[s], kx, u.k * TB);
             } else {
               ptx::mbar_arrive_expect_tx(&full[s], 2 * K::A_BYTES + 2 * K::B_BYTES);
-              ptx::tma_load_2d(sb, &M.Ahi, &full[s], kx, k * TB);
-              ptx::tma_load_2d(sb + K::A_BYTES, &M.Alo, &full[s], kx, k * TB);
-              ptx::tma_load_2d(sb + 2 * K::A_BYTES, &M.Bhi, &full[s], kx, c * TN);
-              ptx::tma_load_2d(sb + 2 * K::A_BYTES + K::B_BYTES, &M.Blo, &full[s], kx, c * TN);
+              ptx::tma_load_2d(sb, &M.Ahi, &full[s], kx, u.k * TB);
+              ptx::tma_load_2d(sb + K::A_BYTES, &M.Alo, &full[s], kx, u.k * TB);
+              if (PAIR && kind == KB_SHARED) {
+                // this CTA's half of the strip's columns, into both CTAs (the
+                // peer sends the other half); the 8 KB offset keeps the
+                // 512-byte swizzle atoms of a full-width load
+                constexpr int HB = K::B_BYTES / 2;
+                const int y = c * TN + (int)rank * (TN / 2);
+                ptx::tma_load_2d_mc(sb + 2 * K::A_BYTES + rank * HB, &M.BhiH, &full[s], kx, y, BOTH);
+                ptx::tma_load_2d_mc(sb + 2 * K::A_BYTES + K::B_BYTES + rank * HB, &M.BloH, &full[s], kx, y, BOTH);
+              } else {
+                ptx::tma_load_2d(sb + 2 * K::A_BYTES, &M.Bhi, &full[s], kx, c * TN);
+                ptx::tma_load_2d(sb + 2 * K::A_BYTES + K::B_BYTES, &M.Blo, &full[s], kx, c * TN);
+              }
               ptx::mbar_arrive(&full[s]);
             }
           }
@@ -232,24 +353,48 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (lane == 0) {
       constexpr uint32_t idesc = ptx::idesc_f32acc<TF32>(TB, TN);
       uint32_t cnt = 0, kb = 0;
+      // a consumed stage is released to every CTA that writes it
+      auto release = [&](int s) {
+        if (PAIR)
+          ptx::mma_commit_mc(&empty[s], BOTH);
+        else
+          ptx::mma_commit(&empty[s]);
+      };
       for (int it = 0;; ++it) {
         const int slot = it % TRING;
         const uint32_t use = it / TRING;
-        if (!ptx::mbar_wait(&tile_full[slot], use & 1, st)) break;
+        if (!ptx::mbar_wait_s<PAIR>(&tile_full[slot], use & 1, st)) break;
         const int t = tile_ring[slot];
         ptx::mbar_arrive(&tile_empty[slot]);
         if (t >= ntiles) break;
-        int sidx, k, c;
+        int sidx, row, c;
         TcStudy S;
-        decode_tile(b, t, sidx, k, c, S);
+        decode_tile(b, t, sidx, row, c, S);
+        const Unit u = make_unit<PAIR>(row, S, rank);
         bool ok = true;
-        for (int jj = 0; jj <= k && ok; ++jj, ++kb) {
-          // a fresh partial per K-block, alternating between the two TMEM buffers
-          const int a = kb & 1;
-          if (!ptx::mbar_wait(&part_empty[a], ((kb >> 1) & 1) ^ 1, st)) { ok = false; break; }
-          ptx::tc_fence_after();
-          const uint32_t d = tmem_base + a * TN;
-          uint32_t accumulate = 0;
+        int q = 0;  // K-blocks of this CTA's tile issued so far (k + 1 in all)
+        int a = 0;
+        uint32_t d = 0, accumulate = 0;
+        for (int jj = 0; jj < u.nkb && ok; ++jj) {
+          int j;
+          const KbKind kind = kb_kind<PAIR>(u, row, rank, jj, j);
+          if (kind == KB_NULL) {
+            for (int h = 0; h < K::CPB; ++h, ++cnt) {
+              const int s = cnt % STAGES;
+              if (!ptx::mbar_wait(&full[s], (cnt / STAGES) & 1, st)) { ok = false; break; }
+              release(s);
+            }
+            continue;
+          }
+          if (q % PROMOTE == 0) {
+            // a fresh partial every PROMOTE K-blocks, alternating between the two TMEM buffers
+            a = kb & 1;
+            if (!ptx::mbar_wait(&part_empty[a], ((kb >> 1) & 1) ^ 1, st)) { ok = false; break; }
+            ++kb;
+            ptx::tc_fence_after();
+            d = tmem_base + a * TN;
+            accumulate = 0;
+          }
           for (int h = 0; h < K::CPB; ++h, ++cnt) {
             const int s = cnt % STAGES;
             const uint32_t r = cnt / STAGES;
@@ -265,13 +410,14 @@ __global__ void __launch_bounds__(THREADS, 1)
               const uint64_t blo = ptx::sdesc_k64(base + 2 * K::A_BYTES + K::B_BYTES + off);
               ptx::mma<TF32>(d, alo, bhi, idesc, accumulate);
               accumulate = 1;
-              if (jj > 0) ptx::mma<TF32>(d, ahi, blo, idesc, 1);
+              if (kind != KB_DIAG) ptx::mma<TF32>(d, ahi, blo, idesc, 1);
               ptx::mma<TF32>(d, ahi, bhi, idesc, 1);
             }
-            ptx::mma_commit(&empty[s]);
+            release(s);
           }
           if (!ok) break;
-          ptx::mma_commit(&part_full[a]);
+          if (q % PROMOTE == PROMOTE - 1 || q == u.k) ptx::mma_commit(&part_full[a]);
+          ++q;
         }
         if (!ok) break;
       }
@@ -281,69 +427,74 @@ __global__ void __launch_bounds__(THREADS, 1)
     // The 64 threads decide together (group_and) after every wait.
     const int ct = threadIdx.x - 64;  // 0..63
     constexpr int E = 16 / K::ESZ;    // elements per 16-byte chunk
-    uint32_t cnt = 0;
+    uint32_t cnt = 0, x8n = 0;
     for (int it = 0;; ++it) {
       const int slot = it % TRING;
       const uint32_t use = it / TRING;
-      if (!ptx::group_and(2, 64, ptx::mbar_wait(&tile_full[slot], use & 1, st))) break;
+      if (!ptx::group_and(2, 64, ptx::mbar_wait_s<PAIR>(&tile_full[slot], use & 1, st))) break;
       const int t = tile_ring[slot];
       ptx::named_bar(2, 64);
       if (lane == 0) ptx::mbar_arrive(&tile_empty[slot]);
       if (t >= ntiles) break;
-      int sidx, k, ctile;
+      int sidx, row, ctile;
       TcStudy S;
-      decode_tile(b, t, sidx, k, ctile, S);
-      if (!ptx::group_and(2, 64, ptx::mbar_wait(x8_full, it & 1, st))) break;
-      bool ok = true;
-      for (int h = 0; h < K::CPB; ++h) {
-        const int s = (cnt + h) % STAGES;
-        const uint32_t r = (cnt + h) / STAGES;
-        if (!ptx::group_and(2, 64, ptx::mbar_wait(&empty[s], (r & 1) ^ 1, st))) { ok = false; break; }
-        uint8_t* bh = smem + s * K::STAGE_BYTES + 2 * K::A_BYTES;
-        for (int col = ct; col < TN; col += 64) {
-          const int8_t* src = reinterpret_cast<const int8_t*>(x8 + col * TB + h * K::KCH);
-          const int colg = ctile * TN + col;
-          const int csh = (S.shift && colg < S.ncols) ? S.shift[colg] : 0;
-          const int row0 = k * TB + h * K::KCH;
+      decode_tile(b, t, sidx, row, ctile, S);
+      const Unit u = make_unit<PAIR>(row, S, rank);
+      if (u.has) {
+        const int k = u.k;
+        if (!ptx::group_and(2, 64, ptx::mbar_wait(x8_full, x8n & 1, st))) break;
+        bool ok = true;
+        for (int h = 0; h < K::CPB; ++h) {
+          const int s = (cnt + h) % STAGES;
+          const uint32_t r = (cnt + h) / STAGES;
+          if (!ptx::group_and(2, 64, ptx::mbar_wait(&empty[s], (r & 1) ^ 1, st))) { ok = false; break; }
+          uint8_t* bh = smem + s * K::STAGE_BYTES + 2 * K::A_BYTES;
+          for (int col = ct; col < TN; col += 64) {
+            const int8_t* src = reinterpret_cast<const int8_t*>(x8 + col * TB + h * K::KCH);
+            const int colg = ctile * TN + col;
+            const int csh = (S.shift && colg < S.ncols) ? S.shift[colg] : 0;
+            const int row0 = k * TB + h * K::KCH;
 #pragma unroll
-          for (int q = 0; q < 4; ++q) {  // four 16-byte chunks per 64-byte row
-            // x' = x - c on the n sample rows, 0 on the padding (exact small integers)
-            float f[E];
-            if constexpr (TF32) {
-              const char4 v = *reinterpret_cast<const char4*>(src + q * E);
-              const signed char e4[4] = {v.x, v.y, v.z, v.w};
+            for (int q = 0; q < 4; ++q) {  // four 16-byte chunks per 64-byte row
+              // x' = x - c on the n sample rows, 0 on the padding (exact small integers)
+              float f[E];
+              if constexpr (TF32) {
+                const char4 v = *reinterpret_cast<const char4*>(src + q * E);
+                const signed char e4[4] = {v.x, v.y, v.z, v.w};
 #pragma unroll
-              for (int i = 0; i < 4; ++i) f[i] = (row0 + q * E + i < S.n) ? (float)(e4[i] - csh) : 0.f;
-            } else {
-              const char4 v0 = *reinterpret_cast<const char4*>(src + q * E);
-              const char4 v1 = *reinterpret_cast<const char4*>(src + q * E + 4);
-              const signed char e8[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+                for (int i = 0; i < 4; ++i) f[i] = (row0 + q * E + i < S.n) ? (float)(e4[i] - csh) : 0.f;
+              } else {
+                const char4 v0 = *reinterpret_cast<const char4*>(src + q * E);
+                const char4 v1 = *reinterpret_cast<const char4*>(src + q * E + 4);
+                const signed char e8[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
 #pragma unroll
-              for (int i = 0; i < 8; ++i) f[i] = (row0 + q * E + i < S.n) ? (float)(e8[i] - csh) : 0.f;
-            }
-            uint32_t w[4];
-            if constexpr (TF32) {
-#pragma unroll
-              for (int i = 0; i < 4; ++i) w[i] = __float_as_uint(f[i]);
-            } else {
-#pragma unroll
-              for (int i = 0; i < 4; ++i) {
-                const __nv_bfloat162 b2 = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
-                w[i] = *reinterpret_cast<const uint32_t*>(&b2);
+                for (int i = 0; i < 8; ++i) f[i] = (row0 + q * E + i < S.n) ? (float)(e8[i] - csh) : 0.f;
               }
+              uint32_t w[4];
+              if constexpr (TF32) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) w[i] = __float_as_uint(f[i]);
+              } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                  const __nv_bfloat162 b2 = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
+                  w[i] = *reinterpret_cast<const uint32_t*>(&b2);
+                }
+              }
+              // 64-byte swizzle: 16-byte chunk q of row col sits at chunk q ^ ((col >> 1) & 3)
+              *reinterpret_cast<uint4*>(bh + col * 64 + ((q ^ ((col >> 1) & 3)) << 4)) =
+                  make_uint4(w[0], w[1], w[2], w[3]);
             }
-            // 64-byte swizzle: 16-byte chunk q of row col sits at chunk q ^ ((col >> 1) & 3)
-            *reinterpret_cast<uint4*>(bh + col * 64 + ((q ^ ((col >> 1) & 3)) << 4)) =
-                make_uint4(w[0], w[1], w[2], w[3]);
           }
+          ptx::fence_proxy_async_shared();
+          ptx::named_bar(2, 64);
+          if (ct == 0) ptx::mbar_arrive(&full[s]);
         }
-        ptx::fence_proxy_async_shared();
-        ptx::named_bar(2, 64);
-        if (ct == 0) ptx::mbar_arrive(&full[s]);
+        if (!ok) break;
+        if (ct == 0) ptx::mbar_arrive(x8_empty);
+        ++x8n;
       }
-      if (!ok) break;
-      if (ct == 0) ptx::mbar_arrive(x8_empty);
-      cnt += K::CPB * (k + 1);
+      cnt += K::CPB * u.nkb;
     }
   } else {
     // ----------------------------------------------------------------- epilogue
@@ -357,18 +508,22 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int it = 0;; ++it) {
       const int slot = it % TRING;
       const uint32_t use = it / TRING;
-      if (!ptx::group_and(1, NT, ptx::mbar_wait(&tile_full[slot], use & 1, st))) break;
+      if (!ptx::group_and(1, NT, ptx::mbar_wait_s<PAIR>(&tile_full[slot], use & 1, st))) break;
       const int t = tile_ring[slot];
       ptx::named_bar(1, NT);
       if (lane == 0) ptx::mbar_arrive(&tile_empty[slot]);
       if (t >= ntiles) break;
-      int sidx, k, c;
+      int sidx, row, c;
       TcStudy S;
-      decode_tile(b, t, sidx, k, c, S);
+      decode_tile(b, t, sidx, row, c, S);
+      const Unit u = make_unit<PAIR>(row, S, rank);
+      if (!u.has) continue;
+      const int k = u.k;
 #pragma unroll
       for (int i = 0; i < EPI_COLS; ++i) master[i] = 0.f;
       bool ok = true;
-      for (int jj = 0; jj <= k; ++jj, ++kb) {
+      const int npart = (k + PROMOTE) / PROMOTE;  // ceil((k + 1) / PROMOTE)
+      for (int jp = 0; jp < npart; ++jp, ++kb) {
         const int a = kb & 1;
         if (!ptx::group_and(1, NT, ptx::mbar_wait(&part_full[a], (kb >> 1) & 1, st))) { ok = false; break; }
         ptx::tc_fence_after();
@@ -386,30 +541,11 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (lane == 0) ptx::mbar_arrive(&part_empty[a]);
       }
       if (!ok) break;
-      const int64_t row = (int64_t)k * TB + 32 * lq + lane;
+      const int64_t xrow = (int64_t)k * TB + 32 * lq + lane;
       const int col0 = c * TN + chalf * EPI_COLS;
-#pragma unroll
-      for (int i = 0; i < EPI_COLS; ++i) {
-        const int col = col0 + i;
-        if (col < S.ncols) {
-          const float x = master[i];
-          const int64_t idx = (int64_t)col * S.ldt + row;
-          S.xt32[idx] = x;
-          if constexpr (TF32) {
-            static_cast<float*>(S.blo)[idx] = x - __uint_as_float(tf32_trunc_bits(x));
-          } else {
-            const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-            static_cast<__nv_bfloat16*>(S.bhi)[idx] = hi;
-            static_cast<__nv_bfloat16*>(S.blo)[idx] = __float2bfloat16_rn(x - __bfloat162float(hi));
-          }
-        }
-      }
+      store_tile<TF32>(master, S, xrow, col0);
       ptx::named_bar(1, NT);
-      if (e == 0 && lane == 0) {
-        ptx::fence_proxy_async_global();
-        __threadfence();
-        ptx::st_release(&S.flags[k * S.C + c], 1);
-      }
+      ptx::publish_flag(&S.flags[k * S.C + c], e == 0 && lane == 0);
     }
   }
 
@@ -428,10 +564,461 @@ __global__ void __launch_bounds__(THREADS, 1)
     while (ptx::globaltimer() - t0 < 2000000LL) {
     }
   }
+  // pair mode: neither CTA retires while the other may still write its shared
+  // memory or arrive on its barriers
+  if (PAIR) ptx::cluster_sync();
   ptx::tc_fence_before();
   __syncthreads();
   ptx::tc_fence_after();
   if (warp == 2) ptx::tmem_dealloc(tmem_base, 2 * TN);
+}
+
+// ---------------------------------------------------------------------------
+// Pair-MMA mode: the row panels 2u and 2u+1 of a strip as one M = 256 product
+// on the two SMs of a cluster (tcgen05 cta_group::2).  CTA r holds the block
+// operator rows of panel 2u + r and SNP columns r*128.. of the strip's X~
+// blocks; the pair's tensor cores share the two B halves, so each CTA lands
+// 128 KB per K-block (not 192 KB) and six 32 KB stages fit.  The K-blocks in
+// which the two panels need different B are products with the other panel's
+// A rows zero (a TMA box wholly outside the operator reads zeros):
+//   D0   A = [Aop_{2u,2u} ; 0],        B = X_{2u}    (int8, cast in shared memory)
+//   D1   A = [0 ; Aop_{2u+1,2u+1}],    B = X_{2u+1}  (int8)
+//   M_j  A = [Aop_{2u,j} ; Aop_{2u+1,j}], B = X~_j,  j < 2u
+//   E    A = [0 ; Aop_{2u+1,2u}],      B = X~_{2u}   (after panel 2u is published)
+// D0, D1 and the M_j go into the shared partials, E into a partial of its own
+// that only CTA 1 adds.  The last unit of an odd P has panel 2u only: D0 and
+// the M_j, with CTA 1's A rows zero.  CTA 0 issues every MMA; both CTAs'
+// loads and casts complete on CTA 0's stage barriers, and CTA 0's commits
+// release both CTAs' stages and partials.
+namespace pair2 {
+constexpr int STAGES = 6;
+
+template <bool TF32>
+struct Cfg {
+  static constexpr int ESZ = TF32 ? 4 : 2;
+  static constexpr int KCH = 64 / ESZ;
+  static constexpr int KMMA = TF32 ? 8 : 16;
+  static constexpr int CPB = TB / KCH;
+  static constexpr int A_BYTES = TB * 64;                        // one piece of this CTA's A rows: 8 KB
+  static constexpr int B_BYTES = (TN / 2) * 64;                  // one piece of this CTA's B half: 8 KB
+  static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // 32 KB
+  static constexpr int X8H_BYTES = (TN / 2) * TB;                // int8 block, this CTA's columns: 16 KB
+  static constexpr int BAR_OFF = STAGES * STAGE_BYTES + 2 * X8H_BYTES;
+  static constexpr int NBARS = 2 * STAGES + 4 + 3 * TRING + 3;
+  static constexpr int SMEM = 1024 + BAR_OFF + NBARS * 8 + TRING * 4 + 16;
+};
+
+enum Kind : int { D0 = 0, D1 = 1, MJ = 2, EX = 3 };
+
+struct Unit {
+  int k0;       // panel 2u (CTA 0); CTA 1 has panel k0 + 1 when paired
+  bool paired;  // panel k0 + 1 exists
+  int nmain;    // K-blocks into the shared partials
+  int nkb;      // all K-blocks (nmain, and E when paired)
+};
+
+__device__ __forceinline__ Unit make_unit(int row, const TcStudy& S) {
+  Unit u;
+  u.k0 = 2 * row;
+  u.paired = u.k0 + 1 < S.P;
+  u.nmain = u.k0 + (u.paired ? 2 : 1);
+  u.nkb = u.nmain + (u.paired ? 1 : 0);
+  return u;
+}
+
+// K-block jj of a unit: its kind, the operator block column j, and the
+// operator row panel of this CTA's A rows (-1: zero rows).
+__device__ __forceinline__ Kind kind_of(const Unit& u, uint32_t rank, int jj, int& j, int& arow) {
+  const int k1 = u.k0 + 1;
+  if (jj == 0) {
+    j = u.k0;
+    arow = rank == 0 ? u.k0 : -1;
+    return D0;
+  }
+  if (u.paired && jj == 1) {
+    j = k1;
+    arow = rank == 1 ? k1 : -1;
+    return D1;
+  }
+  if (jj < u.nmain) {
+    j = jj - (u.paired ? 2 : 1);
+    arow = rank == 0 ? u.k0 : (u.paired ? k1 : -1);
+    return MJ;
+  }
+  j = u.k0;
+  arow = rank == 1 ? k1 : -1;
+  return EX;
+}
+}  // namespace pair2
+
+template <bool TF32>
+__global__ void __launch_bounds__(THREADS, 1)
+    trsm_tc_pair_mma_kernel(const __grid_constant__ TcBatch b) {
+  using K = pair2::Cfg<TF32>;
+  constexpr int ST = pair2::STAGES;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint8_t* x8 = smem + ST * K::STAGE_BYTES;  // int8 blocks of panels 2u, 2u+1 (this CTA's columns)
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + K::BAR_OFF);
+  uint64_t* full = bars;               // CTA 0: both CTAs' loads and casts of a stage
+  uint64_t* empty = full + ST;         // CTA 0's commit: the stage's MMAs are done
+  uint64_t* part_full = empty + ST;    // CTA 0's commit: a partial is complete
+  uint64_t* part_empty = part_full + 2;  // CTA 0: both CTAs' epilogues are done with a partial
+  uint64_t* tile_full = part_empty + 2;
+  uint64_t* tile_empty = tile_full + TRING;
+  uint64_t* x8_full = tile_empty + TRING;
+  uint64_t* x8_empty = x8_full + 1;
+  uint64_t* drain = x8_empty + 1;
+  uint64_t* peer_free = drain + 1;
+  int* tile_ring = reinterpret_cast<int*>(peer_free + TRING);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tile_ring + TRING);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntiles = b.ntiles;  // work units: row-panel pairs of a strip
+  DevStatus* st = b.st;
+  const uint32_t rank = ptx::cluster_ctarank();
+  const bool leader = rank == 0;
+  constexpr uint16_t BOTH = 3;
+  // a barrier of CTA 0, as this CTA addresses it
+  auto lead_addr = [&](uint64_t* bar) -> uint32_t { return leader ? ptx::smem_u32(bar) : ptx::peer_addr(bar, 0); };
+  // counting arrival on a barrier of CTA 0 (no data of this thread to publish)
+  auto count_lead = [&](uint64_t* bar) {
+    if (leader)
+      ptx::mbar_arrive(bar);
+    else
+      ptx::mbar_arrive_peer_count(ptx::peer_addr(bar, 0));
+  };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ST; ++s) {
+      ptx::mbar_init(&full[s], 4);   // two arrivals from each CTA (+ the bytes of both)
+      ptx::mbar_init(&empty[s], 1);  // CTA 0's commit
+    }
+    for (int a = 0; a < 2; ++a) {
+      ptx::mbar_init(&part_full[a], 1);
+      ptx::mbar_init(&part_empty[a], 2 * EPI_WARPS);
+    }
+    for (int i = 0; i < TRING; ++i) {
+      ptx::mbar_init(&tile_full[i], 1);
+      ptx::mbar_init(&tile_empty[i], 1 + 2 + EPI_WARPS);
+      ptx::mbar_init(&peer_free[i], 1);
+    }
+    ptx::mbar_init(x8_full, 1);
+    ptx::mbar_init(x8_empty, 1);
+    ptx::mbar_init(drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int q = 0; q < b.nstudies; ++q) {
+      ptx::prefetch_tensormap(&b.maps[q].Ahi);
+      ptx::prefetch_tensormap(&b.maps[q].Alo);
+      ptx::prefetch_tensormap(&b.maps[q].BhiH);
+      ptx::prefetch_tensormap(&b.maps[q].BloH);
+      ptx::prefetch_tensormap(&b.maps[q].X8H);
+    }
+  }
+  if (warp == 2) {
+    ptx::tmem_alloc_pair(tmem_slot, 2 * TN);
+    ptx::tmem_relinquish_pair();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  ptx::cluster_sync();  // both CTAs' barriers and tensor memory exist before any remote access
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------ scheduler + TMA producer
+    if (lane == 0) {
+      uint32_t cnt = 0, x8n = 0;
+      for (int it = 0;; ++it) {
+        const int slot = it % TRING;
+        const uint32_t use = it / TRING;
+        if (!ptx::mbar_wait(&tile_empty[slot], (use & 1) ^ 1, st)) break;
+        int t;
+        if (leader) {
+          if (!ptx::mbar_wait(&peer_free[slot], use & 1, st)) break;
+          t = ptx::aborting(st) ? ntiles : (int)atomicAdd(b.counter, 1u);
+          if (t > ntiles) t = ntiles;
+          tile_ring[slot] = t;
+          ptx::st_peer_u32(ptx::peer_addr(&tile_ring[slot], 1), (uint32_t)t);
+          ptx::mbar_arrive(&tile_full[slot]);
+          ptx::mbar_arrive_peer(ptx::peer_addr(&tile_full[slot], 1));
+        } else {
+          ptx::mbar_arrive_peer(ptx::peer_addr(&peer_free[slot], 0));
+          if (!ptx::mbar_wait_s<true>(&tile_full[slot], use & 1, st)) break;
+          t = tile_ring[slot];
+        }
+        if (t >= ntiles) break;
+        int sidx, row, c;
+        TcStudy S;
+        decode_tile(b, t, sidx, row, c, S);
+        const TcMaps& M = b.maps[sidx];
+        const pair2::Unit u = pair2::make_unit(row, S);
+        const int ycol = c * TN + (int)rank * (TN / 2);  // this CTA's SNP columns
+        if (!ptx::mbar_wait(x8_empty, (x8n & 1) ^ 1, st)) break;
+        ptx::mbar_arrive_expect_tx(x8_full, (u.paired ? 2 : 1) * K::X8H_BYTES);
+        ptx::tma_load_2d(x8, &M.X8H, x8_full, u.k0 * TB, ycol);
+        if (u.paired) ptx::tma_load_2d(x8 + K::X8H_BYTES, &M.X8H, x8_full, (u.k0 + 1) * TB, ycol);
+        ++x8n;
+        bool ok = true;
+        for (int jj = 0; jj < u.nkb && ok; ++jj) {
+          int j, arow;
+          const pair2::Kind kind = pair2::kind_of(u, rank, jj, j, arow);
+          const bool btma = kind == pair2::MJ || kind == pair2::EX;  // else B is cast from int8
+          if (btma) {
+            if (!ptx::wait_flag(&S.flags[j * S.C + c], st)) { ok = false; break; }
+            ptx::fence_proxy_async_global();
+          }
+          const int ay = arow >= 0 ? arow * TB : -TB;  // -TB: wholly outside, reads zeros
+          for (int h = 0; h < K::CPB; ++h, ++cnt) {
+            const int s = cnt % ST;
+            const uint32_t r = cnt / ST;
+            if (!ptx::mbar_wait(&empty[s], (r & 1) ^ 1, st)) { ok = false; break; }
+            uint8_t* sb = smem + s * K::STAGE_BYTES;
+            const int kx = j * TB + h * K::KCH;
+            const uint32_t fb = lead_addr(&full[s]);
+            if (leader)
+              ptx::mbar_arrive_expect_tx(&full[s], 2 * (2 * K::A_BYTES + (btma ? 2 * K::B_BYTES : 0)));
+            else
+              ptx::mbar_arrive_peer_count(fb);
+            ptx::tma_load_2d_pair(sb, &M.Ahi, fb, kx, ay);
+            ptx::tma_load_2d_pair(sb + K::A_BYTES, &M.Alo, fb, kx, ay);
+            if (btma) {
+              ptx::tma_load_2d_pair(sb + 2 * K::A_BYTES, &M.BhiH, fb, kx, ycol);
+              ptx::tma_load_2d_pair(sb + 2 * K::A_BYTES + K::B_BYTES, &M.BloH, fb, kx, ycol);
+              count_lead(&full[s]);
+            }
+          }
+        }
+        if (!ok) break;
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------- MMA issuer (CTA 0 only)
+    if (lane == 0) {
+      constexpr uint32_t idesc = ptx::idesc_f32acc<TF32>(2 * TB, TN);
+      uint32_t cnt = 0, kb = 0;
+      for (int it = 0;; ++it) {
+        const int slot = it % TRING;
+        const uint32_t use = it / TRING;
+        if (!ptx::mbar_wait_s<true>(&tile_full[slot], use & 1, st)) break;
+        const int t = tile_ring[slot];
+        ptx::mbar_arrive(&tile_empty[slot]);
+        if (t >= ntiles) break;
+        if (!leader) continue;
+        int sidx, row, c;
+        TcStudy S;
+        decode_tile(b, t, sidx, row, c, S);
+        const pair2::Unit u = pair2::make_unit(row, S);
+        bool ok = true;
+        int q = 0, a = 0;
+        uint32_t d = 0, accumulate = 0;
+        for (int jj = 0; jj < u.nkb && ok; ++jj) {
+          int j, arow;
+          const pair2::Kind kind = pair2::kind_of(u, rank, jj, j, arow);
+          if (kind == pair2::EX || q % PROMOTE == 0) {
+            // a fresh partial every PROMOTE main K-blocks, and one for E
+            a = kb & 1;
+            if (!ptx::mbar_wait(&part_empty[a], ((kb >> 1) & 1) ^ 1, st)) { ok = false; break; }
+            ++kb;
+            ptx::tc_fence_after();
+            d = tmem_base + a * TN;
+            accumulate = 0;
+          }
+          const bool three = kind == pair2::MJ || kind == pair2::EX;  // X~ has a lo piece
+          for (int h = 0; h < K::CPB; ++h, ++cnt) {
+            const int s = cnt % ST;
+            const uint32_t r = cnt / ST;
+            if (!ptx::mbar_wait(&full[s], r & 1, st)) { ok = false; break; }
+            ptx::tc_fence_after();
+            const uint32_t base = ptx::smem_u32(smem + s * K::STAGE_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < K::KCH / K::KMMA; ++kk) {
+              const uint32_t off = kk * K::KMMA * K::ESZ;
+              const uint64_t ahi = ptx::sdesc_k64(base + off);
+              const uint64_t alo = ptx::sdesc_k64(base + K::A_BYTES + off);
+              const uint64_t bhi = ptx::sdesc_k64(base + 2 * K::A_BYTES + off);
+              const uint64_t blo = ptx::sdesc_k64(base + 2 * K::A_BYTES + K::B_BYTES + off);
+              ptx::mma_pair<TF32>(d, alo, bhi, idesc, accumulate);
+              accumulate = 1;
+              if (three) ptx::mma_pair<TF32>(d, ahi, blo, idesc, 1);
+              ptx::mma_pair<TF32>(d, ahi, bhi, idesc, 1);
+            }
+            ptx::mma_commit_pair(&empty[s], BOTH);
+          }
+          if (!ok) break;
+          if (kind == pair2::EX || q % PROMOTE == PROMOTE - 1 || jj == u.nmain - 1)
+            ptx::mma_commit_pair(&part_full[a], BOTH);
+          if (kind != pair2::EX) ++q;
+        }
+        if (!ok) break;
+      }
+    }
+  } else if (warp < 4) {
+    // ----------------------- int8 -> BF16/TF32 cast of D0 and D1 (this CTA's columns)
+    const int ct = threadIdx.x - 64;  // 0..63
+    constexpr int E = 16 / K::ESZ;    // elements per 16-byte chunk
+    uint32_t cnt = 0, x8n = 0;
+    for (int it = 0;; ++it) {
+      const int slot = it % TRING;
+      const uint32_t use = it / TRING;
+      if (!ptx::group_and(2, 64, ptx::mbar_wait_s<true>(&tile_full[slot], use & 1, st))) break;
+      const int t = tile_ring[slot];
+      ptx::named_bar(2, 64);
+      if (lane == 0) ptx::mbar_arrive(&tile_empty[slot]);
+      if (t >= ntiles) break;
+      int sidx, row, ctile;
+      TcStudy S;
+      decode_tile(b, t, sidx, row, ctile, S);
+      const pair2::Unit u = pair2::make_unit(row, S);
+      if (!ptx::group_and(2, 64, ptx::mbar_wait(x8_full, x8n & 1, st))) break;
+      bool ok = true;
+      const int nd = u.paired ? 2 : 1;  // D0, D1
+      for (int dd = 0; dd < nd && ok; ++dd) {
+        const int panel = u.k0 + dd;
+        for (int h = 0; h < K::CPB; ++h) {
+          const uint32_t pos = cnt + dd * K::CPB + h;
+          const int s = pos % ST;
+          const uint32_t r = pos / ST;
+          if (!ptx::group_and(2, 64, ptx::mbar_wait(&empty[s], (r & 1) ^ 1, st))) { ok = false; break; }
+          uint8_t* bh = smem + s * K::STAGE_BYTES + 2 * K::A_BYTES;
+          for (int col = ct; col < TN / 2; col += 64) {
+            const int8_t* src = reinterpret_cast<const int8_t*>(x8 + dd * K::X8H_BYTES + col * TB + h * K::KCH);
+            const int colg = ctile * TN + (int)rank * (TN / 2) + col;
+            const int csh = (S.shift && colg < S.ncols) ? S.shift[colg] : 0;
+            const int row0 = panel * TB + h * K::KCH;
+#pragma unroll
+            for (int q = 0; q < 4; ++q) {  // four 16-byte chunks per 64-byte row
+              float f[E];
+              if constexpr (TF32) {
+                const char4 v = *reinterpret_cast<const char4*>(src + q * E);
+                const signed char e4[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+                for (int i = 0; i < 4; ++i) f[i] = (row0 + q * E + i < S.n) ? (float)(e4[i] - csh) : 0.f;
+              } else {
+                const char4 v0 = *reinterpret_cast<const char4*>(src + q * E);
+                const char4 v1 = *reinterpret_cast<const char4*>(src + q * E + 4);
+                const signed char e8[8] = {v0.x, v0.y, v0.z, v0.w, v1.x, v1.y, v1.z, v1.w};
+#pragma unroll
+                for (int i = 0; i < 8; ++i) f[i] = (row0 + q * E + i < S.n) ? (float)(e8[i] - csh) : 0.f;
+              }
+              uint32_t w[4];
+              if constexpr (TF32) {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) w[i] = __float_as_uint(f[i]);
+              } else {
+#pragma unroll
+                for (int i = 0; i < 4; ++i) {
+                  const __nv_bfloat162 b2 = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
+                  w[i] = *reinterpret_cast<const uint32_t*>(&b2);
+                }
+              }
+              *reinterpret_cast<uint4*>(bh + col * 64 + ((q ^ ((col >> 1) & 3)) << 4)) =
+                  make_uint4(w[0], w[1], w[2], w[3]);
+            }
+          }
+          ptx::fence_proxy_async_shared();
+          ptx::named_bar(2, 64);
+          // the pair's tensor cores read these generic writes: cluster-scope release
+          if (ct == 0) {
+            if (leader)
+              ptx::mbar_arrive(&full[s]);
+            else
+              ptx::mbar_arrive_peer(ptx::peer_addr(&full[s], 0));
+          }
+        }
+      }
+      if (!ok) break;
+      if (ct == 0) ptx::mbar_arrive(x8_empty);
+      ++x8n;
+      cnt += K::CPB * u.nkb;
+    }
+  } else {
+    // ----------------------------------------------------------------- epilogue
+    constexpr int NT = 32 * EPI_WARPS;
+    const int e = warp - 4;
+    const int lq = e & 3;
+    const int chalf = e >> 2;
+    uint32_t kb = 0;
+    float master[EPI_COLS];
+    for (int it = 0;; ++it) {
+      const int slot = it % TRING;
+      const uint32_t use = it / TRING;
+      if (!ptx::group_and(1, NT, ptx::mbar_wait_s<true>(&tile_full[slot], use & 1, st))) break;
+      const int t = tile_ring[slot];
+      ptx::named_bar(1, NT);
+      if (lane == 0) ptx::mbar_arrive(&tile_empty[slot]);
+      if (t >= ntiles) break;
+      int sidx, row, c;
+      TcStudy S;
+      decode_tile(b, t, sidx, row, c, S);
+      const pair2::Unit u = pair2::make_unit(row, S);
+      const bool has = leader || u.paired;  // this CTA has a tile
+      const int k = u.k0 + (int)rank;
+      const int npm = (u.nmain + PROMOTE - 1) / PROMOTE;  // shared partials
+#pragma unroll
+      for (int i = 0; i < EPI_COLS; ++i) master[i] = 0.f;
+      // waits for partial kb, adds it into the master when `add`, hands it back to CTA 0
+      auto take = [&](bool add) -> bool {
+        const int a = kb & 1;
+        if (!ptx::group_and(1, NT, ptx::mbar_wait(&part_full[a], (kb >> 1) & 1, st))) return false;
+        ptx::tc_fence_after();
+        if (add) {
+          const uint32_t tb = tmem_base + (static_cast<uint32_t>(32 * lq) << 16) + a * TN + chalf * EPI_COLS;
+#pragma unroll
+          for (int ch = 0; ch < EPI_COLS / 16; ++ch) {
+            uint32_t v[16];
+            ptx::tmem_ld_32x32b_x16(tb + ch * 16, v);
+            ptx::tmem_ld_wait();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) master[ch * 16 + i] += __uint_as_float(v[i]);  // round to nearest
+          }
+        }
+        ptx::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) count_lead(&part_empty[a]);
+        ++kb;
+        return true;
+      };
+      // X~ of this CTA's tile to HBM, then its finished-flag
+      auto publish = [&]() {
+        const int64_t xrow = (int64_t)k * TB + 32 * lq + lane;
+        const int col0 = c * TN + chalf * EPI_COLS;
+        store_tile<TF32>(master, S, xrow, col0);
+        ptx::named_bar(1, NT);
+        ptx::publish_flag(&S.flags[k * S.C + c], e == 0 && lane == 0);
+      };
+      bool ok = true;
+      for (int pp = 0; pp < npm && ok; ++pp) ok = take(has);
+      if (!ok) break;
+      // CTA 0 publishes before E (which reads its panel); CTA 1 adds E, then publishes
+      if (leader) publish();
+      if (u.paired) {
+        if (!take(!leader)) break;
+        if (!leader) publish();
+      }
+    }
+  }
+
+  // ---------------------------------------------------------------- teardown
+  if (warp == 1 && lane == 0 && leader) {
+    // every MMA of the pair has completed before tensor memory is released
+    ptx::mma_commit_pair(drain, 1);
+    const long long t0 = ptx::globaltimer();
+    while (!ptx::mbar_try_wait(drain, 0) && ptx::globaltimer() - t0 < 100000000LL) {
+    }
+  }
+  if (ptx::aborting(st)) {
+    const long long t0 = ptx::globaltimer();
+    while (ptx::globaltimer() - t0 < 2000000LL) {
+    }
+  }
+  // neither CTA retires (or frees tensor memory) while the other may still
+  // read its shared memory, arrive on its barriers or write its partials
+  ptx::cluster_sync();
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  if (warp == 2) ptx::tmem_dealloc_pair(tmem_base, 2 * TN);
 }
 
 // ------------------------------------------- per-SNP integer shift (pre-pass)
@@ -500,15 +1087,20 @@ struct TcState {
   int8_t* shift = nullptr;        // per-SNP integer shift (bs)
   bool center = false;            // X_L[:, 0] is the intercept: shift SNP columns
   int strip_group = 0;            // tile order over groups of column strips (0: all)
+  TileMode mode = TILES_SINGLE;    // how tiles map onto CTAs
+  int max_clusters = 0;            // pair modes: co-resident 2-CTA clusters of the kernel
   uint32_t* order = nullptr;      // device tile order when strip_group > 0
   TcStudy* study_dev = nullptr;   // device copy of the study descriptor (grouped order)
   int order_C = -1;               // the column-strip count the order was built for
   unsigned int* sched = nullptr;  // [0] counter, flags from +32
   size_t sched_bytes = 0;
   DevStatus* st = nullptr;
-  CUtensorMap mAhi, mAlo, mBhi, mBlo;
+  CUtensorMap mAhi, mAlo, mBhi, mBlo, mBhiH, mBloH;
   EncodeTiledFn encode = nullptr;
 };
+
+// Row entries of the tile order: row panels, or row-panel pairs in pair mode.
+static int unit_rows(const TcState* t) { return t->mode == TILES_SINGLE ? t->P : (t->P + 1) / 2; }
 
 static cudaError_t get_encode(EncodeTiledFn* fn) {
   void* f = nullptr;
@@ -535,13 +1127,47 @@ static cudaError_t make_map(EncodeTiledFn enc, CUtensorMap* m, CUtensorMapDataTy
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
 
-template <bool TF32>
+template <bool TF32, bool PAIR>
 static cudaError_t set_smem_attr() {
-  return cudaFuncSetAttribute(trsm_tc_kernel<TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, Cfg<TF32>::SMEM);
+  return cudaFuncSetAttribute(trsm_tc_kernel<TF32, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              Cfg<TF32>::SMEM);
+}
+
+template <bool TF32>
+static cudaError_t set_smem_attr_pair_mma() {
+  return cudaFuncSetAttribute(trsm_tc_pair_mma_kernel<TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              pair2::Cfg<TF32>::SMEM);
+}
+
+template <bool TF32>
+static cudaLaunchConfig_t pair_config(cudaLaunchAttribute* attr, int grid, cudaStream_t s, TileMode mode) {
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof cfg);
+  cfg.gridDim = dim3(grid);
+  cfg.blockDim = dim3(THREADS);
+  cfg.dynamicSmemBytes = mode == TILES_PAIR_MMA ? pair2::Cfg<TF32>::SMEM : Cfg<TF32>::SMEM;
+  cfg.stream = s;
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cfg;
+}
+
+// Co-resident 2-CTA clusters of a pair kernel (one CTA per SM).
+template <bool TF32>
+static cudaError_t query_clusters(int num_sms, TileMode mode, int* out) {
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = pair_config<TF32>(attr, 2 * (num_sms / 2), nullptr, mode);
+  const void* fn = mode == TILES_PAIR_MMA ? (const void*)trsm_tc_pair_mma_kernel<TF32>
+                                          : (const void*)trsm_tc_kernel<TF32, true>;
+  return cudaOccupancyMaxActiveClusters(out, fn, &cfg);
 }
 
 cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_pad, int bs, int num_sms,
-                   bool center, DevStatus* st, cudaStream_t s, int64_t* launches, int strip_group) {
+                   bool center, DevStatus* st, cudaStream_t s, int64_t* launches, int strip_group, TileMode mode) {
   *out = nullptr;
   TcState* t = new TcState;
   t->tf32 = (split == SPLIT_TF32);
@@ -573,6 +1199,10 @@ cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_p
   TRY(cudaMalloc(&t->shift, (size_t)bs));
   t->center = center;
   t->strip_group = strip_group;
+  // measured at n = 1e4, 4096-column blocks: BF16 fastest with multicast pairs,
+  // TF32 with the pair product
+  if (mode == TILES_AUTO) mode = t->tf32 ? TILES_PAIR_MMA : TILES_PAIR_MULTICAST;
+  t->mode = mode;
   if (strip_group > 0) {
     TRY(cudaMalloc(&t->order, sizeof(uint32_t) * (size_t)t->P * Cmax));
     TRY(cudaMalloc(&t->study_dev, sizeof(TcStudy)));
@@ -593,7 +1223,16 @@ cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_p
   const void* bhi_base = t->tf32 ? static_cast<const void*>(t->xt32) : t->bhi;
   TRY(make_map(t->encode, &t->mBhi, dt, bhi_base, n_pad, bs, esz * n_pad, kch, TN, true));
   TRY(make_map(t->encode, &t->mBlo, dt, t->blo, n_pad, bs, esz * n_pad, kch, TN, true));
-  TRY(t->tf32 ? set_smem_attr<true>() : set_smem_attr<false>());
+  TRY(make_map(t->encode, &t->mBhiH, dt, bhi_base, n_pad, bs, esz * n_pad, kch, TN / 2, true));
+  TRY(make_map(t->encode, &t->mBloH, dt, t->blo, n_pad, bs, esz * n_pad, kch, TN / 2, true));
+  TRY((t->tf32 ? set_smem_attr<true, false>() : set_smem_attr<false, false>()));
+  if (mode != TILES_SINGLE) {
+    TRY((t->tf32 ? set_smem_attr<true, true>() : set_smem_attr<false, true>()));
+    TRY((t->tf32 ? set_smem_attr_pair_mma<true>() : set_smem_attr_pair_mma<false>()));
+    TRY((t->tf32 ? query_clusters<true>(num_sms, mode, &t->max_clusters)
+                 : query_clusters<false>(num_sms, mode, &t->max_clusters)));
+    if (t->max_clusters < 1) TRY(cudaErrorLaunchOutOfResources);
+  }
 #undef TRY
   *out = t;
   return cudaSuccess;
@@ -611,11 +1250,14 @@ static void append_study_order(std::vector<uint32_t>& order, int si, int P, int 
 
 // The study part of one launch: int8 map, cleared flags, integer shifts.
 static cudaError_t prepare_study(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaStream_t s,
-                                 int64_t* launches, TcStudy* S, CUtensorMap* mX8) {
+                                 int64_t* launches, TcStudy* S, CUtensorMap* mX8, CUtensorMap* mX8H) {
   if (ncols > t->bs || (reinterpret_cast<uintptr_t>(X) & 15) || (ldx & 15) || ldx < t->n)
     return cudaErrorInvalidValue;
   cudaError_t e = make_map(t->encode, mX8, CU_TENSOR_MAP_DATA_TYPE_UINT8, X, (uint64_t)t->n, (uint64_t)ncols,
                            (uint64_t)ldx, TB, TN, false);
+  if (e != cudaSuccess) return e;
+  e = make_map(t->encode, mX8H, CU_TENSOR_MAP_DATA_TYPE_UINT8, X, (uint64_t)t->n, (uint64_t)ncols, (uint64_t)ldx,
+               TB, TN / 2, false);
   if (e != cudaSuccess) return e;
   const int C = (ncols + TN - 1) / TN;
   e = cudaMemsetAsync(t->sched, 0, 128 + sizeof(int) * (size_t)t->P * C, s);
@@ -638,13 +1280,29 @@ static cudaError_t prepare_study(TcState* t, const int8_t* X, int64_t ldx, int n
   return cudaSuccess;
 }
 
-static cudaError_t launch_kernel(bool tf32, const TcBatch& b, int num_sms, cudaStream_t s, int64_t* launches) {
+template <bool TF32>
+static cudaError_t launch_pair(const TcBatch& b, int max_clusters, cudaStream_t s, TileMode mode) {
+  const int ncl = b.ntiles < max_clusters ? b.ntiles : max_clusters;
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = pair_config<TF32>(attr, 2 * ncl, s, mode);
+  if (mode == TILES_PAIR_MMA) return cudaLaunchKernelEx(&cfg, trsm_tc_pair_mma_kernel<TF32>, b);
+  return cudaLaunchKernelEx(&cfg, trsm_tc_kernel<TF32, true>, b);
+}
+
+// b.ntiles work units: tiles, or (pair modes) row-panel pairs of a strip.
+static cudaError_t launch_kernel(bool tf32, TileMode mode, const TcBatch& b, int num_sms, int max_clusters,
+                                 cudaStream_t s, int64_t* launches) {
+  ++*launches;
+  if (mode != TILES_SINGLE) {
+    const cudaError_t e =
+        tf32 ? launch_pair<true>(b, max_clusters, s, mode) : launch_pair<false>(b, max_clusters, s, mode);
+    return e != cudaSuccess ? e : cudaGetLastError();
+  }
   const int grid = b.ntiles < num_sms ? b.ntiles : num_sms;
   if (tf32)
-    trsm_tc_kernel<true><<<grid, THREADS, Cfg<true>::SMEM, s>>>(b);
+    trsm_tc_kernel<true, false><<<grid, THREADS, Cfg<true>::SMEM, s>>>(b);
   else
-    trsm_tc_kernel<false><<<grid, THREADS, Cfg<false>::SMEM, s>>>(b);
-  ++*launches;
+    trsm_tc_kernel<false, false><<<grid, THREADS, Cfg<false>::SMEM, s>>>(b);
   return cudaGetLastError();
 }
 
@@ -652,20 +1310,22 @@ cudaError_t run_block(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaS
   if (ncols <= 0) return cudaSuccess;
   TcBatch b;
   memset(&b, 0, sizeof b);
-  cudaError_t e = prepare_study(t, X, ldx, ncols, s, launches, &b.s0, &b.maps[0].X8);
+  cudaError_t e = prepare_study(t, X, ldx, ncols, s, launches, &b.s0, &b.maps[0].X8, &b.maps[0].X8H);
   if (e != cudaSuccess) return e;
   b.maps[0].Ahi = t->mAhi;
   b.maps[0].Alo = t->mAlo;
   b.maps[0].Bhi = t->mBhi;
   b.maps[0].Blo = t->mBlo;
+  b.maps[0].BhiH = t->mBhiH;
+  b.maps[0].BloH = t->mBloH;
   b.nstudies = 1;
-  b.ntiles = t->P * b.s0.C;
+  b.ntiles = unit_rows(t) * b.s0.C;
   b.counter = t->sched;
   b.st = t->st;
   if (t->strip_group > 0 && t->strip_group < b.s0.C) {
     if (t->order_C != b.s0.C) {  // (re)build the grouped order for this strip count
       std::vector<uint32_t> order;
-      append_study_order(order, 0, t->P, b.s0.C, t->strip_group);
+      append_study_order(order, 0, unit_rows(t), b.s0.C, t->strip_group);
       if ((e = cudaMemcpyAsync(t->order, order.data(), sizeof(uint32_t) * order.size(), cudaMemcpyHostToDevice, s)) !=
               cudaSuccess ||
           (e = cudaStreamSynchronize(s)) != cudaSuccess)
@@ -677,7 +1337,7 @@ cudaError_t run_block(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaS
     b.order = t->order;
     b.studies = t->study_dev;
   }
-  return launch_kernel(t->tf32, b, t->num_sms, s, launches);
+  return launch_kernel(t->tf32, t->mode, b, t->num_sms, t->max_clusters, s, launches);
 }
 
 // ------------------------------------------------------------- batched launch
@@ -685,11 +1345,12 @@ struct TcBatchState {
   int nstudies = 0;
   int ntiles = 0;
   TcStudy S[MAX_STUDIES];
-  CUtensorMap mX8[MAX_STUDIES];
+  CUtensorMap mX8[MAX_STUDIES], mX8H[MAX_STUDIES];
   const int8_t* X[MAX_STUDIES];
   int64_t ldx[MAX_STUDIES];
   bool tf32 = false;
-  int num_sms = 0;
+  TileMode mode = TILES_SINGLE;
+  int num_sms = 0, max_clusters = 0;
   TcStudy* d_studies = nullptr;  // device copies
   uint32_t* d_order = nullptr;
   unsigned int* d_counter = nullptr;
@@ -701,14 +1362,16 @@ cudaError_t batch_create(TcBatchState** out, TcState* const* ts, int nstudies) {
   *out = nullptr;
   if (nstudies < 1 || nstudies > MAX_STUDIES) return cudaErrorInvalidValue;
   for (int i = 1; i < nstudies; ++i)
-    if (ts[i]->tf32 != ts[0]->tf32) return cudaErrorInvalidValue;
+    if (ts[i]->tf32 != ts[0]->tf32 || ts[i]->mode != ts[0]->mode) return cudaErrorInvalidValue;
   TcBatchState* B = new TcBatchState;
   B->nstudies = nstudies;
   B->tf32 = ts[0]->tf32;
+  B->mode = ts[0]->mode;
   B->num_sms = ts[0]->num_sms;
+  B->max_clusters = ts[0]->max_clusters;
   B->st = ts[0]->st;
   size_t cap = 0;
-  for (int i = 0; i < nstudies; ++i) cap += (size_t)ts[i]->P * ((ts[i]->bs + TN - 1) / TN);
+  for (int i = 0; i < nstudies; ++i) cap += (size_t)unit_rows(ts[i]) * ((ts[i]->bs + TN - 1) / TN);
   B->order_cap = cap;
   cudaError_t e;
   if ((e = cudaMalloc(&B->d_studies, sizeof(TcStudy) * MAX_STUDIES)) != cudaSuccess ||
@@ -738,6 +1401,9 @@ cudaError_t batch_plan(TcBatchState* B, TcState* const* ts, const int8_t* const*
     cudaError_t e = make_map(t->encode, &B->mX8[i], CU_TENSOR_MAP_DATA_TYPE_UINT8, X[i], (uint64_t)t->n,
                              (uint64_t)ncols[i], (uint64_t)ldx[i], TB, TN, false);
     if (e != cudaSuccess) return e;
+    e = make_map(t->encode, &B->mX8H[i], CU_TENSOR_MAP_DATA_TYPE_UINT8, X[i], (uint64_t)t->n, (uint64_t)ncols[i],
+                 (uint64_t)ldx[i], TB, TN / 2, false);
+    if (e != cudaSuccess) return e;
     S[i].P = t->P;
     S[i].C = (ncols[i] + TN - 1) / TN;
     S[i].ncols = ncols[i];
@@ -748,19 +1414,19 @@ cudaError_t batch_plan(TcBatchState* B, TcState* const* ts, const int8_t* const*
     S[i].bhi = t->bhi;
     S[i].blo = t->blo;
     S[i].ldt = t->ldt;
-    pmax = t->P > pmax ? t->P : pmax;
-    total += S[i].P * S[i].C;
+    pmax = unit_rows(t) > pmax ? unit_rows(t) : pmax;
+    total += unit_rows(t) * S[i].C;
   }
   std::vector<uint32_t> order;
   order.reserve(total);
   if (order_mode == 0) {
     for (int k = 0; k < pmax; ++k)
       for (int i = 0; i < B->nstudies; ++i)
-        if (ncols[i] > 0 && k < S[i].P)
+        if (ncols[i] > 0 && k < unit_rows(ts[i]))
           for (int c = 0; c < S[i].C; ++c) order.push_back(((uint32_t)i << 28) | ((uint32_t)k << 14) | (uint32_t)c);
   } else {
     for (int i = 0; i < B->nstudies; ++i)
-      if (ncols[i] > 0) append_study_order(order, i, S[i].P, S[i].C, strip_group);
+      if (ncols[i] > 0) append_study_order(order, i, unit_rows(ts[i]), S[i].C, strip_group);
   }
   cudaError_t e;
   if (total > 0 &&
@@ -798,6 +1464,9 @@ cudaError_t batch_launch(TcBatchState* B, TcState* const* ts, cudaStream_t s, in
     b.maps[i].Bhi = t->mBhi;
     b.maps[i].Blo = t->mBlo;
     b.maps[i].X8 = B->mX8[i];
+    b.maps[i].BhiH = t->mBhiH;
+    b.maps[i].BloH = t->mBloH;
+    b.maps[i].X8H = B->mX8H[i];
   }
   if ((e = cudaMemsetAsync(B->d_counter, 0, 128, s)) != cudaSuccess) return e;
   b.studies = B->d_studies;
@@ -806,7 +1475,7 @@ cudaError_t batch_launch(TcBatchState* B, TcState* const* ts, cudaStream_t s, in
   b.ntiles = B->ntiles;
   b.counter = B->d_counter;
   b.st = B->st;
-  return launch_kernel(B->tf32, b, B->num_sms, s, launches);
+  return launch_kernel(B->tf32, B->mode, b, B->num_sms, B->max_clusters, s, launches);
 }
 
 void batch_destroy(TcBatchState* B) {
@@ -820,6 +1489,18 @@ void batch_destroy(TcBatchState* B) {
 const float* xt_f32(const TcState* t) { return t->xt32; }
 const int8_t* shift_of(const TcState* t) { return t->center ? t->shift : nullptr; }
 int64_t xt_ld(const TcState* t) { return t->ldt; }
+TileMode tile_mode(const TcState* t) { return t->mode; }
+
+void launch_shape(const TcState* t, int* ctas, int* cluster_size) {
+  const int units = unit_rows(t) * ((t->bs + TN - 1) / TN);
+  if (t->mode == TILES_SINGLE) {
+    *ctas = units < t->num_sms ? units : t->num_sms;
+    *cluster_size = 1;
+  } else {
+    *ctas = 2 * (units < t->max_clusters ? units : t->max_clusters);
+    *cluster_size = 2;
+  }
+}
 
 void destroy(TcState* t) {
   if (!t) return;

@@ -12,6 +12,14 @@ namespace tc {
 
 enum Split : int { SPLIT_BF16 = 0, SPLIT_TF32 = 1 };
 
+// How tiles (row panel k, strip c) map onto CTAs.
+enum TileMode : int {
+  TILES_AUTO = 0,            // the measured fastest for the split (resolved by create)
+  TILES_SINGLE = 1,          // every tile on its own CTA
+  TILES_PAIR_MULTICAST = 2,  // panels 2u, 2u+1 on a 2-CTA cluster, shared X~ loads by TMA multicast
+  TILES_PAIR_MMA = 3,        // panels 2u, 2u+1: one M = 256 product on a 2-CTA cluster (cta_group::2)
+};
+
 struct TcState;
 
 // Splits the FP64 block operator Aop into hi + lo pieces (BF16 or TF32) and
@@ -23,7 +31,8 @@ struct TcState;
 // strip_group > 0: tiles go out row panel by row panel over groups of that
 // many column strips (the strips' X~ stays in L2 while it is re-read).
 cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_pad, int bs, int num_sms,
-                   bool center, DevStatus* st, cudaStream_t s, int64_t* launches, int strip_group = 0);
+                   bool center, DevStatus* st, cudaStream_t s, int64_t* launches, int strip_group = 0,
+                   TileMode mode = TILES_AUTO);
 
 // X~ = L^-1 X for ncols <= bs int8 columns (X 16-byte aligned, ldx % 16 == 0).
 // The FP32 result is left in xt_f32() with leading dimension xt_ld().
@@ -47,6 +56,9 @@ constexpr int kMaxBatchStudies = 8;
 const float* xt_f32(const TcState* t);
 const int8_t* shift_of(const TcState* t);  // per-SNP shifts of the last block, or null
 int64_t xt_ld(const TcState* t);
+TileMode tile_mode(const TcState* t);  // the resolved mode
+// CTAs of a launch over a full block (bs columns) and its cluster size.
+void launch_shape(const TcState* t, int* ctas, int* cluster_size);
 void destroy(TcState* t);
 
 }  // namespace tc

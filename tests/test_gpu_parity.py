@@ -144,12 +144,18 @@ def test_stream_matches_blocks(small_study):
 # ---------------------------------------------------------------- split precision
 TOL_SPLIT = 1e-5
 SPLITS = ("bf16x3", "tf32x3")
+# how the tensor-core solve's tiles map onto SMs: one per SM, row-panel pairs on
+# a 2-SM cluster with shared loads, row-panel pairs as one 256-row product
+TILES = ("single", "pair_multicast", "pair_mma")
 
 
+@pytest.mark.parametrize("tiles", TILES)
 @pytest.mark.parametrize("prec", SPLITS)
-def test_split_precision_parity(small_study, prec):
+def test_split_precision_parity(small_study, prec, tiles):
     s, X, L, (r, se, st) = small_study
-    with gw.GLS(s["Phi"], s["XL"], s["y"], s["h"], s["sigma2"], precision=prec, bs=1024) as g:
+    with gw.GLS(s["Phi"], s["XL"], s["y"], s["h"], s["sigma2"], precision=prec, bs=1024, tiles=tiles) as g:
+        ctas, cluster, mode = g.solve_shape()
+        assert mode == tiles and cluster == (1 if tiles == "single" else 2) and 0 < ctas <= 148
         outs = [g.solve_block(X[:, c0:c0 + 1024]) for c0 in range(0, X.shape[1], 1024)]
     b = np.concatenate([o[0] for o in outs], axis=1)
     se_g = np.concatenate([o[1] for o in outs], axis=1)
@@ -159,14 +165,19 @@ def test_split_precision_parity(small_study, prec):
     assert e["b_norm"] <= TOL_SPLIT and e["se_rel"] <= TOL_SPLIT, e
 
 
+@pytest.mark.parametrize("tiles", TILES)
 @pytest.mark.parametrize("prec", SPLITS)
-@pytest.mark.parametrize("n,p,m", [(1, 1, 3), (127, 4, 63), (129, 2, 257), (300, 7, 300), (1000, 4, 513)])
-def test_split_ragged_shapes(prec, n, p, m):
+@pytest.mark.parametrize("n,p,m", [(1, 1, 3), (127, 4, 63), (129, 2, 257), (300, 7, 300), (1000, 4, 513),
+                                   (1200, 3, 300)])
+def test_split_ragged_shapes(prec, tiles, n, p, m):
+    # n = 1..129: one or two row panels (a pair with and without its second
+    # panel); n = 300, 1000, 1200: 3, 8 and 10 panels, odd and even counts
     s, X, L, (r, se, st) = _case(n, p, max(2 * n, 4), 0.5, sigma2=1.3, m=m)
-    with gw.GLS(s["Phi"], s["XL"] if p > 1 else None, s["y"], 0.5, 1.3, precision=prec, bs=max(m, 1)) as g:
+    with gw.GLS(s["Phi"], s["XL"] if p > 1 else None, s["y"], 0.5, 1.3, precision=prec, bs=max(m, 1),
+                tiles=tiles) as g:
         b, se_g, st_g = g.solve_block(X)
     e = compare(b, se_g, st_g, r, se, st)
-    assert e["b_norm"] <= TOL_SPLIT and e["se_rel"] <= TOL_SPLIT, (prec, e)
+    assert e["b_norm"] <= TOL_SPLIT and e["se_rel"] <= TOL_SPLIT, (prec, tiles, e)
 
 
 @pytest.mark.parametrize("prec", SPLITS)
@@ -240,12 +251,12 @@ def paper_scale():
 FULL_TOL = {"fp64": (1e-10, 1e-10), "bf16x3": (1e-5, 1e-5), "tf32x3": (1e-5, 1e-5)}
 
 
-@pytest.mark.parametrize("prec", ["fp64", "bf16x3", "tf32x3"])
-def test_full_size_sampled(paper_scale, prec):
+@pytest.mark.parametrize("prec,tiles", [("fp64", "auto")] + [(p, t) for p in SPLITS for t in ("auto",) + TILES])
+def test_full_size_sampled(paper_scale, prec, tiles):
     import torch
     w, s, first, last, pf, pl, ref_first, ref_last = paper_scale
     tb, ts = FULL_TOL[prec]
-    with gw.GLS(s["Phi"], s["XL"], s["y"], w["h"], w["sigma2"], precision=prec, bs=w["bs"]) as g:
+    with gw.GLS(s["Phi"], s["XL"], s["y"], w["h"], w["sigma2"], precision=prec, bs=w["bs"], tiles=tiles) as g:
         for X, pick, (r, se, _, st) in ((first, pf, ref_first), (last, pl, ref_last)):
             Xd = torch.from_numpy(np.ascontiguousarray(X.T)).cuda().T
             b, se_g, st_g = g.solve_block(Xd)
