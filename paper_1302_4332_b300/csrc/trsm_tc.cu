@@ -88,6 +88,7 @@ struct TcStudy {
 struct TcMaps {
   CUtensorMap Ahi, Alo, Bhi, Blo, X8;
   CUtensorMap BhiH, BloH, X8H;  // half-width boxes (128 SNP columns) for the pair modes
+  CUtensorMap StX, StHi, StLo;  // pair product's epilogue stores: FP32 X~, hi piece (BF16), lo piece
 };
 
 // A launch over one or several studies (the batching form): tiles of all
@@ -591,7 +592,8 @@ __global__ void __launch_bounds__(THREADS, 1)
 // loads and casts complete on CTA 0's stage barriers, and CTA 0's commits
 // release both CTAs' stages and partials.
 namespace pair2 {
-constexpr int STAGES = 6;
+constexpr int STAGES = 5;
+constexpr int ST_COLS = 8;  // SNP columns per epilogue store chunk
 
 template <bool TF32>
 struct Cfg {
@@ -603,7 +605,11 @@ struct Cfg {
   static constexpr int B_BYTES = (TN / 2) * 64;                  // one piece of this CTA's B half: 8 KB
   static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // 32 KB
   static constexpr int X8H_BYTES = (TN / 2) * TB;                // int8 block, this CTA's columns: 16 KB
-  static constexpr int BAR_OFF = STAGES * STAGE_BYTES + 2 * X8H_BYTES;
+  // epilogue staging, per warp two buffers of one chunk (32 rows x ST_COLS
+  // columns): FP32 value, then BF16 hi and lo (or the TF32 lo piece)
+  static constexpr int CHUNK_BYTES = 32 * ST_COLS * 8;          // 2 KB
+  static constexpr int STG_OFF = STAGES * STAGE_BYTES + 2 * X8H_BYTES;
+  static constexpr int BAR_OFF = STG_OFF + EPI_WARPS * 2 * CHUNK_BYTES;
   static constexpr int NBARS = 2 * STAGES + 4 + 3 * TRING + 3;
   static constexpr int SMEM = 1024 + BAR_OFF + NBARS * 8 + TRING * 4 + 16;
 };
@@ -979,13 +985,57 @@ __global__ void __launch_bounds__(THREADS, 1)
         ++kb;
         return true;
       };
-      // X~ of this CTA's tile to HBM, then its finished-flag
+      // X~ of this CTA's tile to HBM by TMA stores of shared-memory chunks,
+      // then its finished-flag
       auto publish = [&]() {
-        const int64_t xrow = (int64_t)k * TB + 32 * lq + lane;
-        const int col0 = c * TN + chalf * EPI_COLS;
-        store_tile<TF32>(master, S, xrow, col0);
+        const TcMaps& M = b.maps[sidx];
+        uint8_t* stg = smem + K::STG_OFF + e * 2 * K::CHUNK_BYTES;
+        const int r0 = k * TB + 32 * lq;
+        const int c0 = c * TN + chalf * EPI_COLS;
+#pragma unroll
+        for (int q = 0; q < EPI_COLS / pair2::ST_COLS; ++q) {
+          uint8_t* buf = stg + (q & 1) * K::CHUNK_BYTES;
+          if (q >= 2) {
+            if (lane == 0) ptx::bulk_wait_read<1>();  // the buffer's last stores have read it
+            __syncwarp();
+          }
+          float* bx = reinterpret_cast<float*>(buf);
+#pragma unroll
+          for (int i = 0; i < pair2::ST_COLS; ++i) {
+            const float x = master[q * pair2::ST_COLS + i];
+            bx[i * 32 + lane] = x;
+            if constexpr (TF32) {
+              reinterpret_cast<float*>(buf + 1024)[i * 32 + lane] = x - __uint_as_float(tf32_trunc_bits(x));
+            } else {
+              const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+              reinterpret_cast<__nv_bfloat16*>(buf + 1024)[i * 32 + lane] = hi;
+              reinterpret_cast<__nv_bfloat16*>(buf + 1536)[i * 32 + lane] =
+                  __float2bfloat16_rn(x - __bfloat162float(hi));
+            }
+          }
+          ptx::fence_proxy_async_shared();
+          __syncwarp();
+          if (lane == 0) {
+            const int y = c0 + q * pair2::ST_COLS;
+            ptx::tma_store_2d(&M.StX, buf, r0, y);
+            if constexpr (TF32) {
+              ptx::tma_store_2d(&M.StLo, buf + 1024, r0, y);
+            } else {
+              ptx::tma_store_2d(&M.StHi, buf + 1024, r0, y);
+              ptx::tma_store_2d(&M.StLo, buf + 1536, r0, y);
+            }
+            ptx::bulk_commit();
+          }
+        }
+        if (lane == 0) {
+          // this warp's stores are complete and visible device-wide before the flag
+          ptx::bulk_wait_all();
+          ptx::fence_proxy_async_global();
+          asm volatile("fence.acq_rel.gpu;" ::: "memory");
+        }
+        __syncwarp();
         ptx::named_bar(1, NT);
-        ptx::publish_flag(&S.flags[k * S.C + c], e == 0 && lane == 0);
+        if (e == 0 && lane == 0) ptx::st_release(&S.flags[k * S.C + c], 1);
       };
       bool ok = true;
       for (int pp = 0; pp < npm && ok; ++pp) ok = take(has);
@@ -1096,6 +1146,7 @@ struct TcState {
   size_t sched_bytes = 0;
   DevStatus* st = nullptr;
   CUtensorMap mAhi, mAlo, mBhi, mBlo, mBhiH, mBloH;
+  CUtensorMap mStX, mStHi, mStLo;  // pair product's epilogue stores
   EncodeTiledFn encode = nullptr;
 };
 
@@ -1199,9 +1250,9 @@ cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_p
   TRY(cudaMalloc(&t->shift, (size_t)bs));
   t->center = center;
   t->strip_group = strip_group;
-  // measured at n = 1e4, 4096-column blocks: BF16 fastest with multicast pairs,
-  // TF32 with the pair product
-  if (mode == TILES_AUTO) mode = t->tf32 ? TILES_PAIR_MMA : TILES_PAIR_MULTICAST;
+  // measured at n = 1e4 with 4096-column blocks: the pair product is the
+  // fastest for both splits
+  if (mode == TILES_AUTO) mode = TILES_PAIR_MMA;
   t->mode = mode;
   if (strip_group > 0) {
     TRY(cudaMalloc(&t->order, sizeof(uint32_t) * (size_t)t->P * Cmax));
@@ -1225,6 +1276,12 @@ cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_p
   TRY(make_map(t->encode, &t->mBlo, dt, t->blo, n_pad, bs, esz * n_pad, kch, TN, true));
   TRY(make_map(t->encode, &t->mBhiH, dt, bhi_base, n_pad, bs, esz * n_pad, kch, TN / 2, true));
   TRY(make_map(t->encode, &t->mBloH, dt, t->blo, n_pad, bs, esz * n_pad, kch, TN / 2, true));
+  TRY(make_map(t->encode, &t->mStX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, t->xt32, n_pad, bs, 4 * (size_t)n_pad, 32,
+               pair2::ST_COLS, false));
+  memset(&t->mStHi, 0, sizeof t->mStHi);
+  if (!t->tf32)
+    TRY(make_map(t->encode, &t->mStHi, dt, t->bhi, n_pad, bs, esz * n_pad, 32, pair2::ST_COLS, false));
+  TRY(make_map(t->encode, &t->mStLo, dt, t->blo, n_pad, bs, esz * n_pad, 32, pair2::ST_COLS, false));
   TRY((t->tf32 ? set_smem_attr<true, false>() : set_smem_attr<false, false>()));
   if (mode != TILES_SINGLE) {
     TRY((t->tf32 ? set_smem_attr<true, true>() : set_smem_attr<false, true>()));
@@ -1318,6 +1375,9 @@ cudaError_t run_block(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaS
   b.maps[0].Blo = t->mBlo;
   b.maps[0].BhiH = t->mBhiH;
   b.maps[0].BloH = t->mBloH;
+  b.maps[0].StX = t->mStX;
+  b.maps[0].StHi = t->mStHi;
+  b.maps[0].StLo = t->mStLo;
   b.nstudies = 1;
   b.ntiles = unit_rows(t) * b.s0.C;
   b.counter = t->sched;
@@ -1467,6 +1527,9 @@ cudaError_t batch_launch(TcBatchState* B, TcState* const* ts, cudaStream_t s, in
     b.maps[i].BhiH = t->mBhiH;
     b.maps[i].BloH = t->mBloH;
     b.maps[i].X8H = B->mX8H[i];
+    b.maps[i].StX = t->mStX;
+    b.maps[i].StHi = t->mStHi;
+    b.maps[i].StLo = t->mStLo;
   }
   if ((e = cudaMemsetAsync(B->d_counter, 0, 128, s)) != cudaSuccess) return e;
   b.studies = B->d_studies;
