@@ -593,7 +593,10 @@ __global__ void __launch_bounds__(THREADS, 1)
 // release both CTAs' stages and partials.
 namespace pair2 {
 constexpr int STAGES = 5;
-constexpr int ST_COLS = 8;  // SNP columns per epilogue store chunk
+// SNP columns per 2 KB epilogue store chunk (32 rows): BF16 mode stores hi+lo
+// chunks (4 B per element), then FP32 chunks; TF32 mode FP32+lo chunks (8 B)
+template <bool TF32>
+constexpr int st_cols() { return TF32 ? 8 : 16; }
 
 template <bool TF32>
 struct Cfg {
@@ -605,9 +608,8 @@ struct Cfg {
   static constexpr int B_BYTES = (TN / 2) * 64;                  // one piece of this CTA's B half: 8 KB
   static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;  // 32 KB
   static constexpr int X8H_BYTES = (TN / 2) * TB;                // int8 block, this CTA's columns: 16 KB
-  // epilogue staging, per warp two buffers of one chunk (32 rows x ST_COLS
-  // columns): FP32 value, then BF16 hi and lo (or the TF32 lo piece)
-  static constexpr int CHUNK_BYTES = 32 * ST_COLS * 8;          // 2 KB
+  // epilogue staging, per warp two 2 KB chunk buffers (32 rows x st_cols())
+  static constexpr int CHUNK_BYTES = 2048;
   static constexpr int STG_OFF = STAGES * STAGE_BYTES + 2 * X8H_BYTES;
   static constexpr int BAR_OFF = STG_OFF + EPI_WARPS * 2 * CHUNK_BYTES;
   static constexpr int NBARS = 2 * STAGES + 4 + 3 * TRING + 3;
@@ -944,7 +946,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     const int e = warp - 4;
     const int lq = e & 3;
     const int chalf = e >> 2;
-    uint32_t kb = 0;
+    uint32_t kb = 0, gq = 0;  // partials taken; store chunks issued
     float master[EPI_COLS];
     for (int it = 0;; ++it) {
       const int slot = it % TRING;
@@ -985,50 +987,53 @@ __global__ void __launch_bounds__(THREADS, 1)
         ++kb;
         return true;
       };
-      // X~ of this CTA's tile to HBM by TMA stores of shared-memory chunks,
-      // then its finished-flag
+      // X~ of this CTA's tile to HBM by TMA stores of shared-memory chunks.
+      // The MMA operand pieces go first (BF16: hi, lo; TF32: the FP32 value,
+      // read as TF32 hi, and lo), then the tile's finished-flag; in BF16 mode
+      // the FP32 copy for the reductions follows off the dependency chain.
       auto publish = [&]() {
+        constexpr int CC = pair2::st_cols<TF32>();
         const TcMaps& M = b.maps[sidx];
         uint8_t* stg = smem + K::STG_OFF + e * 2 * K::CHUNK_BYTES;
         const int r0 = k * TB + 32 * lq;
         const int c0 = c * TN + chalf * EPI_COLS;
-#pragma unroll
-        for (int q = 0; q < EPI_COLS / pair2::ST_COLS; ++q) {
-          uint8_t* buf = stg + (q & 1) * K::CHUNK_BYTES;
-          if (q >= 2) {
-            if (lane == 0) ptx::bulk_wait_read<1>();  // the buffer's last stores have read it
+        // the next staging buffer, once the store group that last read it is done
+        auto next_buf = [&]() -> uint8_t* {
+          uint8_t* buf = stg + (gq & 1) * K::CHUNK_BYTES;
+          if (gq >= 2) {
+            if (lane == 0) ptx::bulk_wait_read<1>();
             __syncwarp();
           }
-          float* bx = reinterpret_cast<float*>(buf);
+          ++gq;
+          return buf;
+        };
 #pragma unroll
-          for (int i = 0; i < pair2::ST_COLS; ++i) {
-            const float x = master[q * pair2::ST_COLS + i];
-            bx[i * 32 + lane] = x;
+        for (int q = 0; q < EPI_COLS / CC; ++q) {
+          uint8_t* buf = next_buf();
+#pragma unroll
+          for (int i = 0; i < CC; ++i) {
+            const float x = master[q * CC + i];
             if constexpr (TF32) {
+              reinterpret_cast<float*>(buf)[i * 32 + lane] = x;
               reinterpret_cast<float*>(buf + 1024)[i * 32 + lane] = x - __uint_as_float(tf32_trunc_bits(x));
             } else {
               const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-              reinterpret_cast<__nv_bfloat16*>(buf + 1024)[i * 32 + lane] = hi;
-              reinterpret_cast<__nv_bfloat16*>(buf + 1536)[i * 32 + lane] =
+              reinterpret_cast<__nv_bfloat16*>(buf)[i * 32 + lane] = hi;
+              reinterpret_cast<__nv_bfloat16*>(buf + 1024)[i * 32 + lane] =
                   __float2bfloat16_rn(x - __bfloat162float(hi));
             }
           }
           ptx::fence_proxy_async_shared();
           __syncwarp();
           if (lane == 0) {
-            const int y = c0 + q * pair2::ST_COLS;
-            ptx::tma_store_2d(&M.StX, buf, r0, y);
-            if constexpr (TF32) {
-              ptx::tma_store_2d(&M.StLo, buf + 1024, r0, y);
-            } else {
-              ptx::tma_store_2d(&M.StHi, buf + 1024, r0, y);
-              ptx::tma_store_2d(&M.StLo, buf + 1536, r0, y);
-            }
+            const int y = c0 + q * CC;
+            ptx::tma_store_2d(TF32 ? &M.StX : &M.StHi, buf, r0, y);
+            ptx::tma_store_2d(&M.StLo, buf + 1024, r0, y);
             ptx::bulk_commit();
           }
         }
         if (lane == 0) {
-          // this warp's stores are complete and visible device-wide before the flag
+          // this warp's operand stores are complete and visible device-wide before the flag
           ptx::bulk_wait_all();
           ptx::fence_proxy_async_global();
           asm volatile("fence.acq_rel.gpu;" ::: "memory");
@@ -1036,6 +1041,20 @@ __global__ void __launch_bounds__(THREADS, 1)
         __syncwarp();
         ptx::named_bar(1, NT);
         if (e == 0 && lane == 0) ptx::st_release(&S.flags[k * S.C + c], 1);
+        if constexpr (!TF32) {
+#pragma unroll
+          for (int q = 0; q < EPI_COLS / CC; ++q) {
+            uint8_t* buf = next_buf();
+#pragma unroll
+            for (int i = 0; i < CC; ++i) reinterpret_cast<float*>(buf)[i * 32 + lane] = master[q * CC + i];
+            ptx::fence_proxy_async_shared();
+            __syncwarp();
+            if (lane == 0) {
+              ptx::tma_store_2d(&M.StX, buf, r0, c0 + q * CC);
+              ptx::bulk_commit();
+            }
+          }
+        }
       };
       bool ok = true;
       for (int pp = 0; pp < npm && ok; ++pp) ok = take(has);
@@ -1047,6 +1066,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         if (!leader) publish();
       }
     }
+    if (lane == 0) ptx::bulk_wait_all();  // the last stores have read the staging buffers
   }
 
   // ---------------------------------------------------------------- teardown
@@ -1276,12 +1296,12 @@ cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_p
   TRY(make_map(t->encode, &t->mBlo, dt, t->blo, n_pad, bs, esz * n_pad, kch, TN, true));
   TRY(make_map(t->encode, &t->mBhiH, dt, bhi_base, n_pad, bs, esz * n_pad, kch, TN / 2, true));
   TRY(make_map(t->encode, &t->mBloH, dt, t->blo, n_pad, bs, esz * n_pad, kch, TN / 2, true));
-  TRY(make_map(t->encode, &t->mStX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, t->xt32, n_pad, bs, 4 * (size_t)n_pad, 32,
-               pair2::ST_COLS, false));
+  const uint32_t stc = t->tf32 ? pair2::st_cols<true>() : pair2::st_cols<false>();
+  TRY(make_map(t->encode, &t->mStX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, t->xt32, n_pad, bs, 4 * (size_t)n_pad, 32, stc,
+               false));
   memset(&t->mStHi, 0, sizeof t->mStHi);
-  if (!t->tf32)
-    TRY(make_map(t->encode, &t->mStHi, dt, t->bhi, n_pad, bs, esz * n_pad, 32, pair2::ST_COLS, false));
-  TRY(make_map(t->encode, &t->mStLo, dt, t->blo, n_pad, bs, esz * n_pad, 32, pair2::ST_COLS, false));
+  if (!t->tf32) TRY(make_map(t->encode, &t->mStHi, dt, t->bhi, n_pad, bs, esz * n_pad, 32, stc, false));
+  TRY(make_map(t->encode, &t->mStLo, dt, t->blo, n_pad, bs, esz * n_pad, 32, stc, false));
   TRY((t->tf32 ? set_smem_attr<true, false>() : set_smem_attr<false, false>()));
   if (mode != TILES_SINGLE) {
     TRY((t->tf32 ? set_smem_attr<true, true>() : set_smem_attr<false, true>()));
