@@ -223,6 +223,18 @@ int gwas_batch_set_order(gwas_batch *B, int order_mode);
  * smallest bs, and both tile orders; keeps the fastest order and reports its
  * columns and rate (SNPs/s over all studies).  Overwrites the input slots. */
 int gwas_batch_autotune(gwas_batch *B, int reps, int *cols_out, int *order_out, double *snps_per_s_out);
+/* The batching form out of core (Sec. 3.1's disk -> main memory -> GPU, for several studies):
+ * study i's int8 dosages are columns col0[i] .. col0[i]+m[i]-1 of the file paths[i] (n_i rows,
+ * column-major, leading dimension ldx[i] bytes after header_bytes[i]).  One reader thread per
+ * study prefetches blocks of `cols` columns (1 <= cols <= every study's bs) into three pinned host
+ * buffers; each step copies one block per study into the batch's device slots and replays the
+ * captured batched launch, while the readers fetch the next blocks.  A study whose columns are
+ * done drops out of the later steps.  Results: b_host[i] (p_i x m[i], column-major), se_host[i]
+ * and status_host[i] (may be NULL, as may the arrays of them).  Errors: GWAS_ERR_IO (open, read,
+ * file too short), GWAS_ERR_TIMEOUT (no block within 120 s), and those of gwas_batch_solve. */
+int gwas_batch_solve_files(gwas_batch *B, const char *const *paths, const int64_t *header_bytes, const int64_t *ldx,
+                           const int64_t *col0, const int64_t *m, int cols, double *const *b_host,
+                           double *const *se_host, int *const *status_host);
 int64_t gwas_batch_kernel_launches(const gwas_batch *B);
 const char *gwas_batch_last_error_detail(const gwas_batch *B);
 void gwas_batch_destroy(gwas_batch *B);

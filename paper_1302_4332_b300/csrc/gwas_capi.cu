@@ -1138,6 +1138,70 @@ int gwas_batch_autotune(gwas_batch* B, int reps, int* cols_out, int* order_out, 
   return GWAS_OK;
 }
 
+int gwas_batch_solve_files(gwas_batch* B, const char* const* paths, const int64_t* header_bytes, const int64_t* ldx,
+                           const int64_t* col0, const int64_t* m, int cols, double* const* b_host,
+                           double* const* se_host, int* const* status_host) {
+  if (!B || !paths || !header_bytes || !ldx || !col0 || !m || !b_host || cols < 1) return GWAS_ERR_ARG;
+  const int ns = B->ns;
+  for (int i = 0; i < ns; ++i) {
+    const gwas_ctx* c = B->ctx[i];
+    if (!paths[i] || header_bytes[i] < 0 || ldx[i] < c->n || col0[i] < 0 || m[i] < 0 || cols > c->bs ||
+        (m[i] > 0 && !b_host[i]))
+      return bfail(B, GWAS_ERR_ARG, "bad arguments to gwas_batch_solve_files");
+  }
+  std::vector<int64_t> nblk(ns);
+  int64_t steps = 0;
+  for (int i = 0; i < ns; ++i) {
+    nblk[i] = (m[i] + cols - 1) / cols;
+    steps = std::max(steps, nblk[i]);
+  }
+  auto cols_of = [&](int i, int64_t k) { return (int)std::min<int64_t>(cols, m[i] - k * cols); };
+  std::vector<gwas_reader*> rd(ns, nullptr);
+  auto close_all = [&]() {
+    for (auto* r : rd) gwas_reader_close(r);
+  };
+  for (int i = 0; i < ns; ++i) {
+    if (nblk[i] == 0) continue;
+    const int rc = gwas_reader_open(&rd[i], paths[i], header_bytes[i] + col0[i] * ldx[i], ldx[i] * cols, nblk[i],
+                                    ldx[i] * cols_of(i, nblk[i] - 1), 3);
+    if (rc != GWAS_OK) {
+      close_all();
+      return bfail(B, rc, "cannot open a study's dosage file");
+    }
+  }
+  std::vector<const int8_t*> xr(ns, nullptr);
+  std::vector<int> nc(ns, 0);
+  std::vector<double*> bo(ns, nullptr), so(ns, nullptr);
+  std::vector<int*> sto(ns, nullptr);
+  int rc = GWAS_OK;
+  for (int64_t k = 0; k < steps && rc == GWAS_OK; ++k) {
+    for (int i = 0; i < ns && rc == GWAS_OK; ++i) {
+      nc[i] = k < nblk[i] ? cols_of(i, k) : 0;
+      xr[i] = nullptr;
+      if (nc[i] == 0) continue;
+      const void* hb = nullptr;
+      int64_t got = 0;
+      rc = gwas_reader_next(rd[i], &hb, &got, 120000);
+      if (rc != GWAS_OK) {
+        B->detail = std::string("reading a study's dosage file: ") + gwas_reader_error_detail(rd[i]);
+        break;
+      }
+      const int p = B->ctx[i]->p;
+      xr[i] = static_cast<const int8_t*>(hb);
+      bo[i] = b_host[i] + k * cols * p;
+      so[i] = (se_host && se_host[i]) ? se_host[i] + k * cols * p : nullptr;
+      sto[i] = (status_host && status_host[i]) ? status_host[i] + k * cols : nullptr;
+    }
+    if (rc != GWAS_OK) break;
+    // host inputs and outputs: returns once the step's results are in host memory
+    rc = gwas_batch_solve(B, xr.data(), ldx, nc.data(), bo.data(), so.data(), sto.data());
+    for (int i = 0; i < ns; ++i)
+      if (nc[i] > 0) gwas_reader_release(rd[i]);
+  }
+  close_all();
+  return rc;
+}
+
 int64_t gwas_batch_kernel_launches(const gwas_batch* B) { return B ? B->launches : 0; }
 const char* gwas_batch_last_error_detail(const gwas_batch* B) { return B ? B->detail.c_str() : ""; }
 void gwas_batch_destroy(gwas_batch* B) { batch_free(B); }

@@ -18,7 +18,7 @@
 //
 // Accumulation: the tensor core adds each K-step into its FP32 accumulator
 // with truncation, which biases long sums toward zero.  So every 128-wide
-// K-block (two in the pair product) accumulates into a fresh TMEM
+// K-block accumulates into a fresh TMEM
 // partial, and the epilogue warps add that partial into an FP32 master held
 // in registers with round-to-nearest adds.  Two TMEM partials alternate so
 // the MMAs of the next blocks overlap the promotion of the last ones.
@@ -54,11 +54,10 @@ constexpr int TRING = 2;     // tile-id ring between the scheduler and the other
 constexpr int EPI_WARPS = 8;
 constexpr int THREADS = 32 * (4 + EPI_WARPS);
 constexpr int EPI_COLS = TN / 2;  // SNP columns per epilogue warp
-// K-blocks accumulated in one TMEM partial: one in the single-CTA and
-// multicast-pair kernel (two measured no faster there and raised the se
-// error 1e-7 -> 1e-6), two in the pair product (se stays ~3e-7)
-constexpr int PROMOTE_CTA = 1;
-constexpr int PROMOTE_PAIR = 2;
+// K-blocks accumulated in one TMEM partial before the epilogue promotes it:
+// one (two measured no faster and raised the error of se up to tenfold); with
+// one, all tile modes give the same results bit for bit
+constexpr int PROMOTE = 1;
 
 template <bool TF32>
 struct Cfg {
@@ -391,8 +390,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             }
             continue;
           }
-          if (q % PROMOTE_CTA == 0) {
-            // a fresh partial every PROMOTE_CTA K-blocks, alternating between the two TMEM buffers
+          if (q % PROMOTE == 0) {
+            // a fresh partial every PROMOTE K-blocks, alternating between the two TMEM buffers
             a = kb & 1;
             if (!ptx::mbar_wait(&part_empty[a], ((kb >> 1) & 1) ^ 1, st)) { ok = false; break; }
             ++kb;
@@ -421,7 +420,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             release(s);
           }
           if (!ok) break;
-          if (q % PROMOTE_CTA == PROMOTE_CTA - 1 || q == u.k) ptx::mma_commit(&part_full[a]);
+          if (q % PROMOTE == PROMOTE - 1 || q == u.k) ptx::mma_commit(&part_full[a]);
           ++q;
         }
         if (!ok) break;
@@ -527,7 +526,7 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
       for (int i = 0; i < EPI_COLS; ++i) master[i] = 0.f;
       bool ok = true;
-      const int npart = (k + PROMOTE_CTA) / PROMOTE_CTA;  // ceil((k + 1) / PROMOTE_CTA)
+      const int npart = (k + PROMOTE) / PROMOTE;  // ceil((k + 1) / PROMOTE)
       for (int jp = 0; jp < npart; ++jp, ++kb) {
         const int a = kb & 1;
         if (!ptx::group_and(1, NT, ptx::mbar_wait(&part_full[a], (kb >> 1) & 1, st))) { ok = false; break; }
@@ -827,8 +826,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int jj = 0; jj < u.nkb && ok; ++jj) {
           int j, arow;
           const pair2::Kind kind = pair2::kind_of(u, rank, jj, j, arow);
-          if (kind == pair2::EX || q % PROMOTE_PAIR == 0) {
-            // a fresh partial every PROMOTE_PAIR main K-blocks, and one for E
+          if (kind == pair2::EX || q % PROMOTE == 0) {
+            // a fresh partial every PROMOTE main K-blocks, and one for E
             a = kb & 1;
             if (!ptx::mbar_wait(&part_empty[a], ((kb >> 1) & 1) ^ 1, st)) { ok = false; break; }
             ++kb;
@@ -858,7 +857,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             ptx::mma_commit_pair(&empty[s], BOTH);
           }
           if (!ok) break;
-          if (kind == pair2::EX || q % PROMOTE_PAIR == PROMOTE_PAIR - 1 || jj == u.nmain - 1)
+          if (kind == pair2::EX || q % PROMOTE == PROMOTE - 1 || jj == u.nmain - 1)
             ptx::mma_commit_pair(&part_full[a], BOTH);
           if (kind != pair2::EX) ++q;
         }
@@ -966,7 +965,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       const pair2::Unit u = pair2::make_unit(row, S);
       const bool has = leader || u.paired;  // this CTA has a tile
       const int k = u.k0 + (int)rank;
-      const int npm = (u.nmain + PROMOTE_PAIR - 1) / PROMOTE_PAIR;  // shared partials
+      const int npm = (u.nmain + PROMOTE - 1) / PROMOTE;  // shared partials
 #pragma unroll
       for (int i = 0; i < EPI_COLS; ++i) master[i] = 0.f;
       // waits for partial kb, adds it into the master when `add`, hands it back to CTA 0

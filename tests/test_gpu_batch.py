@@ -76,3 +76,48 @@ def test_batch_autotune_and_skipped_study():
     finally:
         for g in gls:
             g.close()
+
+
+def test_batch_solve_files_matches_in_memory(tmp_path):
+    """Out of core: each study's dosages in its own file (own leading dimension
+    and header); the streamed batch equals the in-memory batch step by step and
+    the oracle on a sample; a study that runs out of columns drops out."""
+    studies = _studies("bf16x3")
+    gls = [g for _, g in studies]
+    cols, ms = 256, (700, 1000, 300, 513)
+    paths, lds, heads, Xs = [], [], [], []
+    for i, ((s, _), m) in enumerate(zip(studies, ms)):
+        X = gwas_synth.dosages(s["n"], 0, m, seed=31, study=i)
+        ld, head = s["n"] + 5 + i, 16 * i
+        raw = np.zeros((m, ld), dtype=np.int8)
+        raw[:, :s["n"]] = X.T
+        path = tmp_path / f"study{i}.bin"
+        with open(path, "wb") as f:
+            f.write(b"\x55" * head)
+            f.write(raw.tobytes())
+        paths.append(str(path)); lds.append(ld); heads.append(head); Xs.append(X)
+    try:
+        with gw.GLSBatch(gls) as B:
+            outs = B.solve_files(paths, ms, cols, ldx=lds, header_bytes=heads)
+            nsteps = max((m + cols - 1) // cols for m in ms)
+            for k in range(nsteps):
+                blocks = [X[:, k * cols:(k + 1) * cols] if k * cols < X.shape[1] else None for X in Xs]
+                ref = B.solve(blocks)
+                for i, r in enumerate(ref):
+                    if r is None:
+                        continue
+                    sl = slice(k * cols, k * cols + r[0].shape[1])
+                    assert np.array_equal(outs[i][0][:, sl], r[0]) and np.array_equal(outs[i][2][sl], r[2]), (i, k)
+            for i, ((s, _), X, (b, se, st)) in enumerate(zip(studies, Xs, outs)):
+                L = oracle.potrf(oracle.form_m(s["Phi"], 0.5, 1.0))
+                pick = np.arange(0, X.shape[1], 23)
+                r, se_o, _, st_o = oracle.gls(L, s["XL"], s["y"], X[:, pick])
+                e = compare(b[:, pick], se[:, pick], st[pick], r, se_o, st_o)
+                assert e["b_norm"] <= 1e-5 and e["se_rel"] <= 1e-5, (i, e)
+            # a file that is too short is an IO error, not a hang
+            with pytest.raises(gw.GwasError) as err:
+                B.solve_files(paths, [m + 300 for m in ms], cols, ldx=lds, header_bytes=heads)
+            assert err.value.name == "GWAS_ERR_IO"
+    finally:
+        for g in gls:
+            g.close()
