@@ -470,6 +470,18 @@ def measure_forms(args, out):
         t = (time.perf_counter() - t1) / 2
     forms["adjoint_fp64"] = dict(workload="n=5000, p=4, 4096 SNPs per block", snps_per_s=4096 / t,
                                  ms_per_block=1e3 * t)
+    # the split adjoint: block solve and transpose solve on the tensor cores
+    with gw.GLS(s4["Phi"], s4["XL"], s4["y"], 0.5, 1.0, bs=4096, precision="bf16x3") as g:
+        g.adjoint_block(X4, dh, dy, chi2, dch)
+        g.synchronize()
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        for _ in range(5):
+            g.adjoint_block(X4, dh, dy, chi2, dch)
+        g.synchronize()
+        t = (time.perf_counter() - t1) / 5
+    forms["adjoint_bf16x3"] = dict(workload="n=5000, p=4, 4096 SNPs per block", snps_per_s=4096 / t,
+                                   ms_per_block=1e3 * t)
     t1 = time.perf_counter()
     h_hat, ll, evals = gw.reml_fit(s4["Phi"], s4["XL"][:, :3], s4["y"], h0=0.2, tol=1e-8)
     forms["reml_fit"] = dict(workload="null model n=5000, q=3, true h=0.5, from h0=0.2", h_hat=h_hat,

@@ -15,13 +15,13 @@ class WaldChi2Sum(torch.autograd.Function):
     come from one adjoint pass per block (computed during forward)."""
 
     @staticmethod
-    def forward(ctx, h, y, phi, XL, blocks, sigma2=1.0, bs=4096):
+    def forward(ctx, h, y, phi, XL, blocks, sigma2=1.0, bs=4096, precision="fp64"):
         hv = float(h.detach().cpu())
         yv = y.detach().to("cpu", torch.float64).numpy()
         dh = np.zeros(1)
         dy = np.zeros(yv.shape[0])
         total = 0.0
-        with GLS(phi, XL, yv, hv, sigma2, bs=bs) as g:
+        with GLS(phi, XL, yv, hv, sigma2, bs=bs, precision=precision) as g:
             for X in blocks:
                 chi2, _, dh, dy = g.adjoint_block(X, dh_accum=dh, dy_accum=dy)
                 total += float(np.nansum(chi2))
@@ -33,8 +33,10 @@ class WaldChi2Sum(torch.autograd.Function):
     def backward(ctx, grad_out):
         dh, dy = ctx.saved_tensors
         g = grad_out.detach().to("cpu", torch.float64)
-        return (g * dh).to(grad_out.device), (g * dy).to(ctx.y_device), None, None, None, None, None
+        return (g * dh).to(grad_out.device), (g * dy).to(ctx.y_device), None, None, None, None, None, None
 
 
-def wald_chi2_sum(h, y, phi, XL, blocks, sigma2: float = 1.0, bs: int = 4096):
-    return WaldChi2Sum.apply(h, y, phi, XL, blocks, sigma2, bs)
+def wald_chi2_sum(h, y, phi, XL, blocks, sigma2: float = 1.0, bs: int = 4096, precision: str = "fp64"):
+    """precision: "fp64", or "bf16x3" / "tf32x3" (the block solve and the
+    transpose solve on the tensor cores; the per-SNP adjoint arithmetic FP64)."""
+    return WaldChi2Sum.apply(h, y, phi, XL, blocks, sigma2, bs, precision)

@@ -234,4 +234,26 @@ cudaError_t launch_null_residual(const double* W, int64_t ldw, int rows, int q, 
   return cudaGetLastError();
 }
 
+// The split adjoint's hand-over to the FP64 adjoint kernels: dst = (double)src
+// over rows x ncols, plus shift[c] * col0 on column c when the solve ran on the
+// integer-shifted SNP column x - c*1 (exact undo: L^-1 and L^-T are linear and
+// col0 is the solved intercept column).
+__global__ void widen_kernel(const float* __restrict__ src, int64_t lds, double* __restrict__ dst, int64_t ldd,
+                             int rows, int ncols, const int8_t* __restrict__ shift, const double* __restrict__ col0) {
+  const int64_t total = (int64_t)rows * ncols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int c = (int)(e / rows), r = (int)(e % rows);
+    double v = (double)src[(int64_t)c * lds + r];
+    if (shift) v = fma((double)shift[c], col0[r], v);
+    dst[(int64_t)c * ldd + r] = v;
+  }
+}
+
+cudaError_t launch_widen(const float* src, int64_t lds, double* dst, int64_t ldd, int rows, int ncols,
+                         const int8_t* shift, const double* col0, cudaStream_t s) {
+  if (rows <= 0 || ncols <= 0) return cudaSuccess;
+  widen_kernel<<<1184, 256, 0, s>>>(src, lds, dst, ldd, rows, ncols, shift, col0);
+  return cudaGetLastError();
+}
+
 }  // namespace gwas

@@ -697,16 +697,37 @@ int gwas_adjoint_block(gwas_ctx* ctx, const int8_t* XR, int64_t ldx, int ncols, 
     CK(cudaMemcpyAsync(d_acc, dh_accum, sizeof(double), cudaMemcpyHostToDevice, ctx->stream));
     CK(cudaMemcpyAsync(d_acc + 1, dy_accum, sizeof(double) * n, cudaMemcpyHostToDevice, ctx->stream));
   }
-  // forward solve X~ (FP64) of the int8 block
+  // forward solve X~ of the int8 block
   const void* xin = XR;
   int64_t ld_in = ldx;
-  if (!is_device_ptr(XR)) {
+  const bool split = ctx->prec != GWAS_FP64;
+  if (!is_device_ptr(XR) || (split && ((reinterpret_cast<uintptr_t>(XR) & 15) || (ldx & 15)))) {
     CK(cudaMemcpy2DAsync(ctx->ring[0], (size_t)ctx->n_pad, XR, (size_t)ldx, (size_t)n, (size_t)ncols,
-                         cudaMemcpyHostToDevice, ctx->stream));
+                         cudaMemcpyDefault, ctx->stream));
     xin = ctx->ring[0];
     ld_in = ctx->n_pad;
   }
-  {
+  if (split) {
+    // the split adjoint: X~ and X^ = L^-T X~ on the tensor cores (both on the
+    // integer-shifted SNP columns), widened to FP64 with the shift undone;
+    // the per-SNP adjoint arithmetic below stays FP64
+    int64_t nl = 0;
+    cudaError_t e;
+    {
+      StageMark m(ctx, GWAS_STAGE_TRSM, ctx->stream);
+      e = tc::run_block(ctx->tcs, static_cast<const int8_t*>(xin), ld_in, ncols, ctx->stream, &nl);
+      if (e == cudaSuccess) e = tc::ensure_transpose(ctx->tcs, ctx->AopT, ctx->stream, &nl);
+      if (e == cudaSuccess) e = tc::run_transpose(ctx->tcs, ncols, ctx->stream, &nl);
+    }
+    ctx->launches += nl;
+    if (e != cudaSuccess) return fail(ctx, GWAS_ERR_CUDA, "split adjoint solves: %s", cudaGetErrorString(e));
+    const int8_t* sh = tc::shift_of(ctx->tcs);
+    CK(launch_widen(tc::xt_f32(ctx->tcs), tc::xt_ld(ctx->tcs), ctx->Xt, ctx->n_pad, ctx->n_pad, ncols, sh, ctx->W,
+                    ctx->stream));
+    CK(launch_widen(tc::xhat_f32(ctx->tcs), tc::xt_ld(ctx->tcs), ctx->Xhat, ctx->n_pad, ctx->n_pad, ncols, sh,
+                    ctx->What, ctx->stream));
+    ctx->launches += 2;
+  } else {
     const int C64 = (ncols + F64_TN - 1) / F64_TN;
     CK(cudaMemsetAsync(ctx->sched, 0, sizeof(Sched) + sizeof(int) * (size_t)ctx->P * C64, ctx->stream));
     TrsmF64Args a{};
@@ -720,7 +741,7 @@ int gwas_adjoint_block(gwas_ctx* ctx, const int8_t* XR, int64_t ldx, int ncols, 
     ctx->launches += 1;
   }
   // transpose solve X^ = L^-T X~
-  {
+  if (!split) {
     StageMark m(ctx, GWAS_STAGE_TRSM, ctx->stream);
     if ((rc = solve_f64_cols(ctx, ctx->Xt, ctx->n_pad, ctx->n_pad, ncols, ctx->Xhat, true)) != GWAS_OK) return rc;
   }

@@ -130,6 +130,9 @@ cudaError_t launch_make_w32(const double* W, int64_t ldw, int rows, int q, float
 
 // a11: per-SNP adjoint (chi2, d chi2/dh, y-weights), their sums over SNPs and
 // the y-gradient; FP64.  GH = What^T What, What = [X^_L | y^] = L^-T W.
+// FP32 -> FP64 with the integer shift undone (shift[c] * col0 added to column c; shift may be null).
+cudaError_t launch_widen(const float* src, int64_t lds, double* dst, int64_t ldd, int rows, int ncols,
+                         const int8_t* shift, const double* col0, cudaStream_t s);
 cudaError_t launch_adjoint(const double* Xt, const double* Xh, int64_t ldt, int rows, int n, const double* W,
                            const double* Wh, int64_t ldw, const SolveConsts* sc, const double* GH, int q,
                            int ncols, double h, double sigma2, double* chi2, double* dh, double* wv, double* uT,

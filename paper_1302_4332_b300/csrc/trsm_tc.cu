@@ -92,6 +92,7 @@ struct TcMaps {
   CUtensorMap Ahi, Alo, Bhi, Blo, X8;
   CUtensorMap BhiH, BloH, X8H;  // half-width boxes (128 SNP columns) for the pair modes
   CUtensorMap StX, StHi, StLo;  // pair product's epilogue stores: FP32 X~, hi piece (BF16), lo piece
+  CUtensorMap BinHi, BinLo;     // transpose solve: X~ pieces of the forward solve (its diagonal-block input)
 };
 
 // A launch over one or several studies (the batching form): tiles of all
@@ -154,7 +155,8 @@ enum KbKind : int {
   KB_DIAG = 0,    // j == k: Aop hi/lo by TMA, B = the int8 block cast in shared memory
   KB_SHARED = 1,  // pair mode, j < 2u: each CTA loads its own Aop and half of X~_jc for both
   KB_LOCAL = 2,   // Aop and all of X~_jc by this CTA alone
-  KB_NULL = 3     // no loads, no MMA: keeps the two CTAs' stage rings in step
+  KB_NULL = 3,    // no loads, no MMA: keeps the two CTAs' stage rings in step
+  KB_DIAG_IN = 4  // transpose solve, j == k: B = the forward solve's X~ pieces by TMA (3 products)
 };
 
 // A work unit.  Single mode: the tile (k, c).  Pair mode: the tiles (2u, c)
@@ -166,10 +168,17 @@ struct Unit {
   int nkb;      // K-blocks in the unit's stage sequence (the same on both CTAs)
 };
 
-template <bool PAIR>
+// UPPER (transpose solve X^ = L^-T X~, single CTAs): row panels from the
+// last one up; tile (k, c) walks j = k (its own X~ input), then P-1 .. k+1.
+template <bool PAIR, bool UPPER = false>
 __device__ __forceinline__ Unit make_unit(int row, const TcStudy& S, uint32_t rank) {
   Unit u;
-  if (PAIR) {
+  if (UPPER) {
+    u.k = S.P - 1 - row;
+    u.has = true;
+    u.paired = false;
+    u.nkb = S.P - u.k;
+  } else if (PAIR) {
     u.k = 2 * row + (int)rank;
     u.has = u.k < S.P;
     u.paired = 2 * row + 1 < S.P;
@@ -186,8 +195,12 @@ __device__ __forceinline__ Unit make_unit(int row, const TcStudy& S, uint32_t ra
 // K-block jj of a unit: its kind, and j, the block column of Aop it multiplies.
 // Pair mode, both tiles present: rank 0 runs [diag 2u, shared 0..2u-1, null],
 // rank 1 [diag 2u+1, shared 0..2u-1, local 2u] (X~ of rank 0's own tile).
-template <bool PAIR>
+template <bool PAIR, bool UPPER = false>
 __device__ __forceinline__ KbKind kb_kind(const Unit& u, int row, uint32_t rank, int jj, int& j) {
+  if (UPPER) {
+    j = jj == 0 ? u.k : u.k + u.nkb - jj;  // k, then P-1 .. k+1
+    return jj == 0 ? KB_DIAG_IN : KB_LOCAL;
+  }
   if (jj == 0) {
     j = u.k;
     return u.has ? KB_DIAG : KB_NULL;
@@ -205,9 +218,10 @@ __device__ __forceinline__ KbKind kb_kind(const Unit& u, int row, uint32_t rank,
   return rank == 1 ? KB_LOCAL : KB_NULL;
 }
 
-template <bool TF32, bool PAIR>
+template <bool TF32, bool PAIR, bool UPPER = false>
 __global__ void __launch_bounds__(THREADS, 1)
     trsm_tc_kernel(const __grid_constant__ TcBatch b) {
+  static_assert(!(PAIR && UPPER), "the transpose solve runs on single CTAs");
   using K = Cfg<TF32>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -301,8 +315,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         TcStudy S;
         decode_tile(b, t, sidx, row, c, S);
         const TcMaps& M = b.maps[sidx];
-        const Unit u = make_unit<PAIR>(row, S, rank);
-        if (u.has) {
+        const Unit u = make_unit<PAIR, UPPER>(row, S, rank);
+        if (u.has && !UPPER) {
           if (!ptx::mbar_wait(x8_empty, (x8n & 1) ^ 1, st)) break;
           ptx::mbar_arrive_expect_tx(x8_full, K::X8_BYTES);
           ptx::tma_load_2d(x8, &M.X8, x8_full, u.k * TB, c * TN);
@@ -311,7 +325,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         bool ok = true;
         for (int jj = 0; jj < u.nkb && ok; ++jj) {
           int j;
-          const KbKind kind = kb_kind<PAIR>(u, row, rank, jj, j);
+          const KbKind kind = kb_kind<PAIR, UPPER>(u, row, rank, jj, j);
           if (kind == KB_SHARED || kind == KB_LOCAL) {
             if (!ptx::wait_flag(&S.flags[j * S.C + c], st)) { ok = false; break; }
             ptx::fence_proxy_async_global();
@@ -341,6 +355,9 @@ __global__ void __launch_bounds__(THREADS, 1)
                 const int y = c * TN + (int)rank * (TN / 2);
                 ptx::tma_load_2d_mc(sb + 2 * K::A_BYTES + rank * HB, &M.BhiH, &full[s], kx, y, BOTH);
                 ptx::tma_load_2d_mc(sb + 2 * K::A_BYTES + K::B_BYTES + rank * HB, &M.BloH, &full[s], kx, y, BOTH);
+              } else if (UPPER && kind == KB_DIAG_IN) {
+                ptx::tma_load_2d(sb + 2 * K::A_BYTES, &M.BinHi, &full[s], kx, c * TN);
+                ptx::tma_load_2d(sb + 2 * K::A_BYTES + K::B_BYTES, &M.BinLo, &full[s], kx, c * TN);
               } else {
                 ptx::tma_load_2d(sb + 2 * K::A_BYTES, &M.Bhi, &full[s], kx, c * TN);
                 ptx::tma_load_2d(sb + 2 * K::A_BYTES + K::B_BYTES, &M.Blo, &full[s], kx, c * TN);
@@ -374,14 +391,14 @@ __global__ void __launch_bounds__(THREADS, 1)
         int sidx, row, c;
         TcStudy S;
         decode_tile(b, t, sidx, row, c, S);
-        const Unit u = make_unit<PAIR>(row, S, rank);
+        const Unit u = make_unit<PAIR, UPPER>(row, S, rank);
         bool ok = true;
         int q = 0;  // K-blocks of this CTA's tile issued so far (k + 1 in all)
         int a = 0;
         uint32_t d = 0, accumulate = 0;
         for (int jj = 0; jj < u.nkb && ok; ++jj) {
           int j;
-          const KbKind kind = kb_kind<PAIR>(u, row, rank, jj, j);
+          const KbKind kind = kb_kind<PAIR, UPPER>(u, row, rank, jj, j);
           if (kind == KB_NULL) {
             for (int h = 0; h < K::CPB; ++h, ++cnt) {
               const int s = cnt % STAGES;
@@ -420,7 +437,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             release(s);
           }
           if (!ok) break;
-          if (q % PROMOTE == PROMOTE - 1 || q == u.k) ptx::mma_commit(&part_full[a]);
+          const int nk = UPPER ? u.nkb : u.k + 1;  // the tile's K-blocks
+          if (q % PROMOTE == PROMOTE - 1 || q == nk - 1) ptx::mma_commit(&part_full[a]);
           ++q;
         }
         if (!ok) break;
@@ -443,8 +461,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       int sidx, row, ctile;
       TcStudy S;
       decode_tile(b, t, sidx, row, ctile, S);
-      const Unit u = make_unit<PAIR>(row, S, rank);
-      if (u.has) {
+      const Unit u = make_unit<PAIR, UPPER>(row, S, rank);
+      if (u.has && !UPPER) {
         const int k = u.k;
         if (!ptx::group_and(2, 64, ptx::mbar_wait(x8_full, x8n & 1, st))) break;
         bool ok = true;
@@ -520,13 +538,14 @@ __global__ void __launch_bounds__(THREADS, 1)
       int sidx, row, c;
       TcStudy S;
       decode_tile(b, t, sidx, row, c, S);
-      const Unit u = make_unit<PAIR>(row, S, rank);
+      const Unit u = make_unit<PAIR, UPPER>(row, S, rank);
       if (!u.has) continue;
       const int k = u.k;
 #pragma unroll
       for (int i = 0; i < EPI_COLS; ++i) master[i] = 0.f;
       bool ok = true;
-      const int npart = (k + PROMOTE) / PROMOTE;  // ceil((k + 1) / PROMOTE)
+      const int nk = UPPER ? u.nkb : k + 1;  // the tile's K-blocks
+      const int npart = (nk + PROMOTE - 1) / PROMOTE;
       for (int jp = 0; jp < npart; ++jp, ++kb) {
         const int a = kb & 1;
         if (!ptx::group_and(1, NT, ptx::mbar_wait(&part_full[a], (kb >> 1) & 1, st))) { ok = false; break; }
@@ -1170,6 +1189,14 @@ struct TcState {
   DevStatus* st = nullptr;
   CUtensorMap mAhi, mAlo, mBhi, mBlo, mBhiH, mBloH;
   CUtensorMap mStX, mStHi, mStLo;  // pair product's epilogue stores
+  // transpose solve (the adjoint form): the transpose block operator split hi/lo,
+  // X^ = L^-T X~ in FP32 + pieces, and their maps
+  void* ahiT = nullptr;
+  void* aloT = nullptr;
+  float* xh32 = nullptr;
+  void* xhhi = nullptr;
+  void* xhlo = nullptr;
+  CUtensorMap mAhiT, mAloT, mBhiT, mBloT;
   EncodeTiledFn encode = nullptr;
 };
 
@@ -1204,6 +1231,12 @@ static cudaError_t make_map(EncodeTiledFn enc, CUtensorMap* m, CUtensorMapDataTy
 template <bool TF32, bool PAIR>
 static cudaError_t set_smem_attr() {
   return cudaFuncSetAttribute(trsm_tc_kernel<TF32, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              Cfg<TF32>::SMEM);
+}
+
+template <bool TF32>
+static cudaError_t set_smem_attr_upper() {
+  return cudaFuncSetAttribute(trsm_tc_kernel<TF32, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                               Cfg<TF32>::SMEM);
 }
 
@@ -1423,6 +1456,74 @@ cudaError_t run_block(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaS
   return launch_kernel(t->tf32, t->mode, b, t->num_sms, t->max_clusters, s, launches);
 }
 
+// ------------------------------------------------------ transpose solve (adjoint)
+cudaError_t ensure_transpose(TcState* t, const double* AopT, cudaStream_t s, int64_t* launches) {
+  if (t->ahiT) return cudaSuccess;
+  const size_t esz = t->tf32 ? 4 : 2;
+  const size_t np = (size_t)t->n_pad, n2 = np * np;
+  cudaError_t e;
+  if ((e = cudaMalloc(&t->ahiT, esz * n2)) != cudaSuccess || (e = cudaMalloc(&t->aloT, esz * n2)) != cudaSuccess ||
+      (e = cudaMalloc(&t->xh32, sizeof(float) * np * t->bs)) != cudaSuccess ||
+      (!t->tf32 && (e = cudaMalloc(&t->xhhi, 2 * np * t->bs)) != cudaSuccess) ||
+      (e = cudaMalloc(&t->xhlo, esz * np * t->bs)) != cudaSuccess)
+    return e;
+  if (t->tf32)
+    split_aop_kernel<true><<<1184, 256, 0, s>>>(AopT, (int64_t)n2, t->ahiT, t->aloT);
+  else
+    split_aop_kernel<false><<<1184, 256, 0, s>>>(AopT, (int64_t)n2, t->ahiT, t->aloT);
+  ++*launches;
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  const CUtensorMapDataType dt = t->tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const uint32_t kch = t->tf32 ? Cfg<true>::KCH : Cfg<false>::KCH;
+  const void* bhi = t->tf32 ? static_cast<const void*>(t->xh32) : t->xhhi;
+  if ((e = make_map(t->encode, &t->mAhiT, dt, t->ahiT, np, np, esz * np, kch, TB, true)) != cudaSuccess ||
+      (e = make_map(t->encode, &t->mAloT, dt, t->aloT, np, np, esz * np, kch, TB, true)) != cudaSuccess ||
+      (e = make_map(t->encode, &t->mBhiT, dt, bhi, np, t->bs, esz * np, kch, TN, true)) != cudaSuccess ||
+      (e = make_map(t->encode, &t->mBloT, dt, t->xhlo, np, t->bs, esz * np, kch, TN, true)) != cudaSuccess)
+    return e;
+  return t->tf32 ? set_smem_attr_upper<true>() : set_smem_attr_upper<false>();
+}
+
+cudaError_t run_transpose(TcState* t, int ncols, cudaStream_t s, int64_t* launches) {
+  if (ncols <= 0) return cudaSuccess;
+  if (!t->ahiT || ncols > t->bs) return cudaErrorInvalidValue;
+  TcBatch b;
+  memset(&b, 0, sizeof b);
+  const int C = (ncols + TN - 1) / TN;
+  cudaError_t e = cudaMemsetAsync(t->sched, 0, 128 + sizeof(int) * (size_t)t->P * C, s);
+  if (e != cudaSuccess) return e;
+  TcStudy& S = b.s0;
+  S.P = t->P;
+  S.C = C;
+  S.ncols = ncols;
+  S.n = t->n;
+  S.shift = nullptr;
+  S.flags = reinterpret_cast<int*>(t->sched + 32);
+  S.xt32 = t->xh32;
+  S.bhi = t->xhhi;
+  S.blo = t->xhlo;
+  S.ldt = t->ldt;
+  b.maps[0].Ahi = t->mAhiT;
+  b.maps[0].Alo = t->mAloT;
+  b.maps[0].Bhi = t->mBhiT;
+  b.maps[0].Blo = t->mBloT;
+  b.maps[0].BinHi = t->mBhi;  // the forward solve's X~ pieces
+  b.maps[0].BinLo = t->mBlo;
+  b.nstudies = 1;
+  b.ntiles = t->P * C;
+  b.counter = t->sched;
+  b.st = t->st;
+  const int grid = b.ntiles < t->num_sms ? b.ntiles : t->num_sms;
+  if (t->tf32)
+    trsm_tc_kernel<true, false, true><<<grid, THREADS, Cfg<true>::SMEM, s>>>(b);
+  else
+    trsm_tc_kernel<false, false, true><<<grid, THREADS, Cfg<false>::SMEM, s>>>(b);
+  ++*launches;
+  return cudaGetLastError();
+}
+
+const float* xhat_f32(const TcState* t) { return t->xh32; }
+
 // ------------------------------------------------------------- batched launch
 struct TcBatchState {
   int nstudies = 0;
@@ -1590,6 +1691,11 @@ void launch_shape(const TcState* t, int* ctas, int* cluster_size) {
 
 void destroy(TcState* t) {
   if (!t) return;
+  cudaFree(t->ahiT);
+  cudaFree(t->aloT);
+  cudaFree(t->xh32);
+  cudaFree(t->xhhi);
+  cudaFree(t->xhlo);
   cudaFree(t->ahi);
   cudaFree(t->alo);
   cudaFree(t->xt32);

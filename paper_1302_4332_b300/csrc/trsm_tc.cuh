@@ -53,6 +53,15 @@ cudaError_t batch_launch(TcBatchState* B, TcState* const* ts, cudaStream_t s, in
 void batch_destroy(TcBatchState* B);
 constexpr int kMaxBatchStudies = 8;
 
+// The transpose solve of the adjoint form: X^ = L^-T X~ on the tensor cores,
+// X~ being the last run_block's result (its FP32 value and split pieces).
+// ensure_transpose splits the FP64 transpose block operator AopT (row panel k
+// = [D_k^-T at block k | -D_k^-T L_jk^T for j > k], row-major) once; the
+// result lands in xhat_f32() (leading dimension xt_ld()).
+cudaError_t ensure_transpose(TcState* t, const double* AopT, cudaStream_t s, int64_t* launches);
+cudaError_t run_transpose(TcState* t, int ncols, cudaStream_t s, int64_t* launches);
+const float* xhat_f32(const TcState* t);
+
 const float* xt_f32(const TcState* t);
 const int8_t* shift_of(const TcState* t);  // per-SNP shifts of the last block, or null
 int64_t xt_ld(const TcState* t);

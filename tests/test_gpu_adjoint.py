@@ -81,6 +81,71 @@ def test_adjoint_paper_scale_n5000():
     assert _rel(dy, dy_ref) <= 1e-6
 
 
+# ---------------------------------------------------------- split precision
+# The split adjoint runs the block solve and the transpose solve on the tensor
+# cores (BF16x3 / TF32x3 operands, FP32 accumulation) and the per-SNP adjoint
+# arithmetic in FP64; its errors against the FP64 oracle are stated here per
+# result.
+SPLIT_ADJ_TOL = {"bf16x3": 1e-4, "tf32x3": 2e-5}
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+@pytest.mark.parametrize("n,p,m,h,sigma2", [(300, 4, 300, 0.5, 1.3), (1000, 3, 513, 0.7, 1.0)])
+def test_split_adjoint_matches_oracle(prec, n, p, m, h, sigma2):
+    s = gwas_synth.study(n, p, 2 * n, h, sigma2, seed=6)
+    X = gwas_synth.dosages(n, 0, m, seed=6)
+    L = oracle.potrf(oracle.form_m(s["Phi"], h, sigma2))
+    c_ref, dh_ref, dy_ref = oracle.gls_grad(L, s["Phi"], h, sigma2, s["XL"], s["y"], X)
+    with gw.GLS(s["Phi"], s["XL"], s["y"], h, sigma2, bs=512, precision=prec) as g:
+        dh, dy = np.zeros(1), np.zeros(n)
+        chi2, dch = [], []
+        for c0 in range(0, m, 512):
+            c, d, dh, dy = g.adjoint_block(X[:, c0:c0 + 512], dh_accum=dh, dy_accum=dy)
+            chi2.append(c.copy())
+            dch.append(d.copy())
+    chi2, dch = np.concatenate(chi2), np.concatenate(dch)
+    errs = dict(chi2=_rel(chi2, c_ref), dchi2_dh=_rel(dch, dh_ref),
+                dh_sum=abs(dh[0] - dh_ref.sum()) / np.abs(dh_ref).sum(), dy=_rel(dy, dy_ref))
+    print(prec, n, "split adjoint", errs)
+    tol = SPLIT_ADJ_TOL[prec]
+    assert all(v <= tol for v in errs.values()), (prec, errs)
+
+
+@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+def test_split_adjoint_paper_scale_n5000(prec):
+    n, p, m = 5000, 4, 512
+    s = gwas_synth.study(n, p, 5000, 0.5, 1.0, seed=4)
+    X = gwas_synth.dosages(n, 0, m, seed=4)
+    L = oracle.potrf(oracle.form_m(s["Phi"], 0.5, 1.0))
+    c_ref, dh_ref, dy_ref = oracle.gls_grad(L, s["Phi"], 0.5, 1.0, s["XL"], s["y"], X)
+    with gw.GLS(s["Phi"], s["XL"], s["y"], 0.5, 1.0, bs=m, precision=prec) as g:
+        chi2, dch, dh, dy = g.adjoint_block(X)
+    errs = dict(chi2=_rel(chi2, c_ref), dchi2_dh=_rel(dch, dh_ref),
+                dh_sum=abs(dh[0] - dh_ref.sum()) / np.abs(dh_ref).sum(), dy=_rel(dy, dy_ref))
+    print(prec, n, "split adjoint", errs)
+    tol = SPLIT_ADJ_TOL[prec]
+    assert all(v <= tol for v in errs.values()), (prec, errs)
+
+
+def test_split_autograd_matches_central_differences():
+    """The split adjoint's gradient against central differences of the split
+    forward loss itself (both sides on the tensor cores)."""
+    import torch
+    from paper_1302_4332_b300.autograd import wald_chi2_sum
+    n, m = 300, 128
+    s = gwas_synth.study(n, 4, 600, 0.6, 1.0, seed=9)
+    blocks = [gwas_synth.dosages(n, 0, m, seed=9)]
+    h = torch.tensor(0.6, dtype=torch.float64, requires_grad=True)
+    loss = wald_chi2_sum(h, torch.tensor(s["y"]), s["Phi"], s["XL"], blocks, bs=m, precision="tf32x3")
+    loss.backward()
+    f = lambda hh: float(wald_chi2_sum(torch.tensor(hh, dtype=torch.float64), torch.tensor(s["y"]), s["Phi"],
+                                       s["XL"], blocks, bs=m, precision="tf32x3"))
+    d = 1e-4  # the split loss is smooth only to ~1e-7 relative: a wider step than FP64's
+    fd_h = (f(0.6 + d) - f(0.6 - d)) / (2 * d)
+    print("split autograd", h.grad.item(), fd_h)
+    assert abs(h.grad.item() - fd_h) <= 1e-3 * abs(fd_h)
+
+
 @pytest.mark.parametrize("h", [0.2, 0.5, 0.9])
 def test_reml_eval_matches_oracle(h):
     s = gwas_synth.study(400, 3, 800, 0.5, seed=6)
