@@ -601,18 +601,18 @@ __global__ void __launch_bounds__(THREADS, 1)
 // on the two SMs of a cluster (tcgen05 cta_group::2).  CTA r holds the block
 // operator rows of panel 2u + r and SNP columns r*128.. of the strip's X~
 // blocks; the pair's tensor cores share the two B halves, so each CTA lands
-// 128 KB per K-block (not 192 KB) and six 32 KB stages fit.  The K-blocks in
-// which the two panels need different B are products with the other panel's
-// A rows zero (a TMA box wholly outside the operator reads zeros):
-//   D0   A = [Aop_{2u,2u} ; 0],        B = X_{2u}    (int8, cast in shared memory)
-//   D1   A = [0 ; Aop_{2u+1,2u+1}],    B = X_{2u+1}  (int8)
-//   M_j  A = [Aop_{2u,j} ; Aop_{2u+1,j}], B = X~_j,  j < 2u
-//   E    A = [0 ; Aop_{2u+1,2u}],      B = X~_{2u}   (after panel 2u is published)
-// D0, D1 and the M_j go into the shared partials, E into a partial of its own
-// that only CTA 1 adds.  The last unit of an odd P has panel 2u only: D0 and
-// the M_j, with CTA 1's A rows zero.  CTA 0 issues every MMA; both CTAs'
-// loads and casts complete on CTA 0's stage barriers, and CTA 0's commits
-// release both CTAs' stages and partials.
+// 128 KB per K-block (not 192 KB).  The operator's odd row panels are the
+// pair form A' (built at set-up, pair_rows_kernel): panel 2u+1 re-expressed
+// through panel 2u's own equation, so that neither row of a pair needs the
+// other's result (the blocked solve with 256-row diagonal blocks):
+//   D0   A = [A_{2u,2u} ; A'_{2u+1,2u}],   B = X_{2u}    (int8, cast in shared memory)
+//   D1   A = [0 ; A_{2u+1,2u+1}],          B = X_{2u+1}  (int8; a TMA box wholly
+//                                                          outside the operator reads zeros)
+//   M_j  A = [A_{2u,j} ; A'_{2u+1,j}],     B = X~_j,  j < 2u
+// all into the shared partials.  The last unit of an odd P has panel 2u
+// only: D0 and the M_j with CTA 1's A rows zero.  CTA 0 issues every MMA;
+// both CTAs' loads and casts complete on CTA 0's stage barriers, and CTA 0's
+// commits release both CTAs' stages and partials.
 namespace pair2 {
 constexpr int STAGES = 5;
 // SNP columns per 2 KB epilogue store chunk (32 rows): BF16 mode stores hi+lo
@@ -638,21 +638,19 @@ struct Cfg {
   static constexpr int SMEM = 1024 + BAR_OFF + NBARS * 8 + TRING * 4 + 16;
 };
 
-enum Kind : int { D0 = 0, D1 = 1, MJ = 2, EX = 3 };
+enum Kind : int { D0 = 0, D1 = 1, MJ = 2 };
 
 struct Unit {
   int k0;       // panel 2u (CTA 0); CTA 1 has panel k0 + 1 when paired
   bool paired;  // panel k0 + 1 exists
-  int nmain;    // K-blocks into the shared partials
-  int nkb;      // all K-blocks (nmain, and E when paired)
+  int nkb;      // K-blocks, all into the shared partials
 };
 
 __device__ __forceinline__ Unit make_unit(int row, const TcStudy& S) {
   Unit u;
   u.k0 = 2 * row;
   u.paired = u.k0 + 1 < S.P;
-  u.nmain = u.k0 + (u.paired ? 2 : 1);
-  u.nkb = u.nmain + (u.paired ? 1 : 0);
+  u.nkb = u.k0 + (u.paired ? 2 : 1);
   return u;
 }
 
@@ -662,7 +660,7 @@ __device__ __forceinline__ Kind kind_of(const Unit& u, uint32_t rank, int jj, in
   const int k1 = u.k0 + 1;
   if (jj == 0) {
     j = u.k0;
-    arow = rank == 0 ? u.k0 : -1;
+    arow = rank == 0 ? u.k0 : (u.paired ? k1 : -1);
     return D0;
   }
   if (u.paired && jj == 1) {
@@ -670,14 +668,9 @@ __device__ __forceinline__ Kind kind_of(const Unit& u, uint32_t rank, int jj, in
     arow = rank == 1 ? k1 : -1;
     return D1;
   }
-  if (jj < u.nmain) {
-    j = jj - (u.paired ? 2 : 1);
-    arow = rank == 0 ? u.k0 : (u.paired ? k1 : -1);
-    return MJ;
-  }
-  j = u.k0;
-  arow = rank == 1 ? k1 : -1;
-  return EX;
+  j = jj - (u.paired ? 2 : 1);
+  arow = rank == 0 ? u.k0 : (u.paired ? k1 : -1);
+  return MJ;
 }
 }  // namespace pair2
 
@@ -793,7 +786,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int jj = 0; jj < u.nkb && ok; ++jj) {
           int j, arow;
           const pair2::Kind kind = pair2::kind_of(u, rank, jj, j, arow);
-          const bool btma = kind == pair2::MJ || kind == pair2::EX;  // else B is cast from int8
+          const bool btma = kind == pair2::MJ;  // else B is cast from int8
           if (btma) {
             if (!ptx::wait_flag(&S.flags[j * S.C + c], st)) { ok = false; break; }
             ptx::fence_proxy_async_global();
@@ -845,8 +838,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         for (int jj = 0; jj < u.nkb && ok; ++jj) {
           int j, arow;
           const pair2::Kind kind = pair2::kind_of(u, rank, jj, j, arow);
-          if (kind == pair2::EX || q % PROMOTE == 0) {
-            // a fresh partial every PROMOTE main K-blocks, and one for E
+          if (q % PROMOTE == 0) {
+            // a fresh partial every PROMOTE K-blocks
             a = kb & 1;
             if (!ptx::mbar_wait(&part_empty[a], ((kb >> 1) & 1) ^ 1, st)) { ok = false; break; }
             ++kb;
@@ -854,7 +847,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             d = tmem_base + a * TN;
             accumulate = 0;
           }
-          const bool three = kind == pair2::MJ || kind == pair2::EX;  // X~ has a lo piece
+          const bool three = kind == pair2::MJ;  // X~ has a lo piece
           for (int h = 0; h < K::CPB; ++h, ++cnt) {
             const int s = cnt % ST;
             const uint32_t r = cnt / ST;
@@ -876,9 +869,8 @@ __global__ void __launch_bounds__(THREADS, 1)
             ptx::mma_commit_pair(&empty[s], BOTH);
           }
           if (!ok) break;
-          if (kind == pair2::EX || q % PROMOTE == PROMOTE - 1 || jj == u.nmain - 1)
-            ptx::mma_commit_pair(&part_full[a], BOTH);
-          if (kind != pair2::EX) ++q;
+          if (q % PROMOTE == PROMOTE - 1 || jj == u.nkb - 1) ptx::mma_commit_pair(&part_full[a], BOTH);
+          ++q;
         }
         if (!ok) break;
       }
@@ -984,7 +976,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       const pair2::Unit u = pair2::make_unit(row, S);
       const bool has = leader || u.paired;  // this CTA has a tile
       const int k = u.k0 + (int)rank;
-      const int npm = (u.nmain + PROMOTE - 1) / PROMOTE;  // shared partials
+      const int npm = (u.nkb + PROMOTE - 1) / PROMOTE;  // shared partials
 #pragma unroll
       for (int i = 0; i < EPI_COLS; ++i) master[i] = 0.f;
       // waits for partial kb, adds it into the master when `add`, hands it back to CTA 0
@@ -1081,12 +1073,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       bool ok = true;
       for (int pp = 0; pp < npm && ok; ++pp) ok = take(has);
       if (!ok) break;
-      // CTA 0 publishes before E (which reads its panel); CTA 1 adds E, then publishes
-      if (leader) publish();
-      if (u.paired) {
-        if (!take(!leader)) break;
-        if (!leader) publish();
-      }
+      if (has) publish();
     }
     if (lane == 0) ptx::bulk_wait_all();  // the last stores have read the staging buffers
   }
@@ -1143,6 +1130,61 @@ __global__ void column_shift_kernel(const int8_t* __restrict__ X, int64_t ldx, i
 }
 
 // ------------------------------------------------------------ set-up kernels
+// Pair form of the block operator (FP64, set-up of the pair product): the odd
+// row panels re-expressed through the even one before them, so neither row of
+// a pair needs the other's result.  With A = Aop (row panel k =
+// [A_k0 .. A_k,k-1 | A_kk = D_k^-1], row-major, leading dimension ld) and a
+// pair (2u, 2u+1):
+//   A'_{2u+1,j}  = A_{2u+1,j} + A_{2u+1,2u} A_{2u,j}   (j < 2u)
+//   A'_{2u+1,2u} = A_{2u+1,2u} A_{2u,2u}               (it multiplies the int8 X_{2u})
+// (A'_{2u+1,2u+1} = A_{2u+1,2u+1}), from substituting panel 2u's equation
+// X~_{2u} = sum_{j<2u} A_{2u,j} X~_j + A_{2u,2u} X_{2u} into panel 2u+1's.
+// `out` holds a copy of Aop; this kernel overwrites the odd rows' columns
+// < (2u+1)*TB.  Block (x, u): rows of panel 2u+1, columns 64x .. 64x+63.
+__global__ void __launch_bounds__(256) pair_rows_kernel(const double* __restrict__ A, double* __restrict__ out,
+                                                        int64_t ld, int P) {
+  const int k0 = 2 * blockIdx.y, k1 = k0 + 1;
+  const int c0 = blockIdx.x * 64;
+  if (k1 >= P || c0 >= k1 * TB) return;
+  constexpr int KC = 16;             // t per chunk
+  __shared__ double G[KC][TB + 1];   // A_{k1,k0}: [t][row] of the chunk
+  __shared__ double Bk[KC][64 + 1];  // panel k0, rows t of the chunk, columns c0 ..
+  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
+  double acc[8][4];
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[i][q] = 0.0;
+  for (int tc = 0; tc < TB; tc += KC) {
+    for (int e = tid; e < KC * TB; e += 256) {
+      const int r = e / KC, t = e % KC;
+      G[t][r] = A[(int64_t)(k1 * TB + r) * ld + k0 * TB + tc + t];
+    }
+    for (int e = tid; e < KC * 64; e += 256) {
+      const int t = e / 64, cc = e % 64;
+      Bk[t][cc] = A[(int64_t)(k0 * TB + tc + t) * ld + c0 + cc];
+    }
+    __syncthreads();
+#pragma unroll 4
+    for (int t = 0; t < KC; ++t)
+#pragma unroll
+      for (int i = 0; i < 8; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[i][q] = fma(G[t][ty * 8 + i], Bk[t][tx * 4 + q], acc[i][q]);
+    __syncthreads();
+  }
+#pragma unroll
+  for (int i = 0; i < 8; ++i)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int col = c0 + tx * 4 + q;
+      if (col >= k1 * TB) continue;
+      const int64_t idx = (int64_t)(k1 * TB + ty * 8 + i) * ld + col;
+      // j < 2u: the original block plus the product; j = 2u: the product alone
+      out[idx] = (col < k0 * TB ? A[idx] : 0.0) + acc[i][q];
+    }
+}
+
 template <bool TF32>
 __global__ void split_aop_kernel(const double* __restrict__ A, int64_t count, void* __restrict__ hi,
                                  void* __restrict__ lo) {
@@ -1317,11 +1359,23 @@ cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_p
   t->sched_bytes = 128 + sizeof(int) * (size_t)t->P * Cmax;
   TRY(cudaMalloc(&t->sched, t->sched_bytes));
   TRY(cudaMemsetAsync(t->sched, 0, t->sched_bytes, s));
+  // the pair product multiplies the pair form of the operator (pair_rows_kernel)
+  const double* src = Aop;
+  double* pair_form = nullptr;
+  if (mode == TILES_PAIR_MMA && t->P > 1) {
+    TRY(cudaMallocAsync(&pair_form, sizeof(double) * n2, s));
+    TRY(cudaMemcpyAsync(pair_form, Aop, sizeof(double) * n2, cudaMemcpyDeviceToDevice, s));
+    pair_rows_kernel<<<dim3(n_pad / 64, t->P / 2), 256, 0, s>>>(Aop, pair_form, n_pad, t->P);
+    ++*launches;
+    TRY(cudaGetLastError());
+    src = pair_form;
+  }
   if (t->tf32)
-    split_aop_kernel<true><<<1184, 256, 0, s>>>(Aop, (int64_t)n2, t->ahi, t->alo);
+    split_aop_kernel<true><<<1184, 256, 0, s>>>(src, (int64_t)n2, t->ahi, t->alo);
   else
-    split_aop_kernel<false><<<1184, 256, 0, s>>>(Aop, (int64_t)n2, t->ahi, t->alo);
+    split_aop_kernel<false><<<1184, 256, 0, s>>>(src, (int64_t)n2, t->ahi, t->alo);
   ++*launches;
+  if (pair_form) TRY(cudaFreeAsync(pair_form, s));
   TRY(cudaGetLastError());
   const CUtensorMapDataType dt = t->tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   const uint32_t kch = t->tf32 ? Cfg<true>::KCH : Cfg<false>::KCH;
