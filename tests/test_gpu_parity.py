@@ -180,6 +180,19 @@ def test_split_ragged_shapes(prec, tiles, n, p, m):
     assert e["b_norm"] <= TOL_SPLIT and e["se_rel"] <= TOL_SPLIT, (prec, tiles, e)
 
 
+@pytest.mark.parametrize("tiles", TILES)
+@pytest.mark.parametrize("prec", SPLITS)
+def test_split_grouped_tile_order(small_study, prec, tiles):
+    """Tiles handed out over groups of 2 column strips (a device order table; in
+    the pair modes its rows are row-panel pairs): same parity."""
+    s, X, L, (r, se, st) = small_study
+    with gw.GLS(s["Phi"], s["XL"], s["y"], s["h"], s["sigma2"], precision=prec, bs=1024, tiles=tiles,
+                strip_group=2) as g:
+        b, se_g, st_g = g.solve_block(X[:, :1000])
+    e = compare(b, se_g, st_g, r[:, :1000], se[:, :1000], st[:1000])
+    assert e["b_norm"] <= TOL_SPLIT and e["se_rel"] <= TOL_SPLIT, (prec, tiles, e)
+
+
 @pytest.mark.parametrize("prec", SPLITS)
 def test_split_unaligned_device_input(prec):
     import torch
