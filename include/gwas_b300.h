@@ -58,7 +58,7 @@ extern "C" {
 #define GWAS_ERR_TIMEOUT (-4)    /* a bounded device-side or host-side wait ran out */
 #define GWAS_ERR_IO (-5)         /* host-side input/output failure */
 #define GWAS_ERR_NOMEM (-6)      /* device or pinned-host allocation failed */
-#define GWAS_ERR_UNSUPPORTED (-7)/* configuration this build does not provide */
+#define GWAS_ERR_UNSUPPORTED (-7)/* a configuration the library was compiled without */
 
 #define GWAS_SNP_OK 0
 #define GWAS_SNP_SINGULAR 1
