@@ -335,8 +335,11 @@ def run_ours(args, rank, world, local_rank, dist):
             pk = base / 3.0
             roof = dict(bound="tensor", achieved=achieved, peak=pk, unit="TFLOP/s", frac=achieved / pk,
                         traffic=kernel_traffic(path),
-                        peak_basis=(f"{'bf16' if path == 'bf16x3' else 'tf32'} dense tensor peak (of measured) / 3: "
-                                    "three split products per algorithmic product"))
+                        peak_basis=(f"{'bf16' if path == 'bf16x3' else 'tf32'} dense tensor peak (of measured, "
+                                    "burst) / 3: three split products per algorithmic product"))
+            sus = peaks.get("bf16_tflops_sustained")
+            if path == "bf16x3" and sus:  # the timed region runs ~0.2 s under the power cap
+                roof["frac_of_sustained"] = achieved / (sus / 3.0)
         res["roofline"] = roof
         res["trsm_ms_per_launch"] = trsm_ms
         # end to end: the 8 blocks in pinned host memory, streamed through the block ring every step
