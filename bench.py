@@ -61,10 +61,13 @@ def parse_args():
     ap.add_argument("--no-forms", action="store_true", help="skip the batch / disk / adjoint / REML measurements")
     ap.add_argument("--strip-group", type=int, default=None,
                     help="split paths: column strips per tile-order group (0 = all; default: the measured best)")
-    ap.add_argument("--tiles", choices=("auto", "single", "pair_multicast", "pair_mma"), default="auto",
+    ap.add_argument("--tiles", choices=("auto", "single", "pair_multicast", "pair_mma", "inverse"), default="auto",
                     help="split paths: tiles on SMs (auto: the measured fastest; single: one 128-row tile per SM; "
                          "pair_multicast: row-panel pairs per 2-SM cluster with shared loads; pair_mma: pairs as "
-                         "one 256-row product per cluster)")
+                         "one 256-row product per cluster; inverse: the triangular product with L^-1 formed at "
+                         "set-up, row-panel pairs per cluster)")
+    ap.add_argument("--no-substitution", action="store_true",
+                    help="with --tiles auto: skip the kernel-only measurement of the blocked substitution (pair_mma)")
     ap.add_argument("--fp64-steps", type=int, default=None,
                     help="steps of the fp64 path when a split path is the headline (default 1)")
     return ap.parse_args()
@@ -215,12 +218,13 @@ def measure_extra_peaks(torch, dev):
     return out
 
 
-def kernel_traffic(path: str):
-    """DRAM bytes per launch of the path's triangular-solve kernel from the
-    committed ncu summary, if that summary was taken on the current source."""
+def kernel_traffic(path: str, tiles: str = ""):
+    """DRAM bytes per launch of the path's solve kernel (split paths: keyed by
+    precision and tile mode) from the committed ncu summary, if that summary
+    was taken on the current source."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic_per_launch.json")) as f:
-            rec = json.load(f).get(path)
+            rec = json.load(f).get(f"{path}/{tiles}" if tiles else path)
         if not rec:
             return None
         src = os.path.join(ROOT, "paper_1302_4332_b300", "csrc", rec["source"])
@@ -279,8 +283,14 @@ def run_ours(args, rank, world, local_rank, dist):
     has_split = any(pp in paths for pp in SPLIT_PATHS)
     NB = N_RESIDENT_BLOCKS
     step_snps = NB * bs
+    # (entry, precision, tile mode): the paths, then -- when the default tile
+    # mode (the inverse form) is the headline -- the blocked substitution
+    # (pair product) of each split path, kernel-only, for comparison
+    jobs = [(pp, pp, args.tiles if pp != "fp64" else "auto") for pp in paths]
+    if args.tiles == "auto" and not args.no_substitution:
+        jobs += [(f"{pp}/pair_mma", pp, "pair_mma") for pp in paths if pp in SPLIT_PATHS]
     results = {}
-    for path in paths:
+    for entry, path, tiles in jobs:
         steps, warm_blocks = args.steps, args.warmup * NB
         if path == "fp64" and has_split:
             # the FP64 path is two orders of magnitude slower: one step, a few warm-up blocks
@@ -288,7 +298,7 @@ def run_ours(args, rank, world, local_rank, dist):
         t_init = time.time()
         sg = STRIP_GROUP if args.strip_group is None else args.strip_group
         g = gw.GLS(s["Phi"], s["XL"], s["y"], w["h"], w["sigma2"], precision=path, bs=bs,
-                   strip_group=sg if path != "fp64" else 0, tiles=args.tiles)
+                   strip_group=sg if path != "fp64" else 0, tiles=tiles)
         init_s = time.time() - t_init
         b = torch.empty((bs, p), dtype=torch.float64, device=dev).T
         se = torch.empty((bs, p), dtype=torch.float64, device=dev).T
@@ -324,6 +334,7 @@ def run_ours(args, rank, world, local_rank, dist):
         trsm_ms = stages["trsm"][0] / max(stages["trsm"][1], 1)
         alg_tflop = float(n) * n * bs / 1e12  # n^2 flops per SNP column (Sec. 2.2's trsm)
         achieved = alg_tflop / (trsm_ms / 1e3)
+        mode = res["solve_shape"]["tiles"]
         if path == "fp64":
             pk = extra.get("fp64_tflops_cublas")
             roof = dict(bound="alu", achieved=achieved, peak=pk, unit="TFLOP/s",
@@ -332,18 +343,23 @@ def run_ours(args, rank, world, local_rank, dist):
         else:
             bf16 = peaks.get("bf16_tflops") or 1800.0
             base = bf16 if path == "bf16x3" else (extra.get("tf32_tflops_cublas") or bf16 * 1.1 / 2.25)
-            pk = base / 3.0
+            # tensor products per algorithmic product: the substitution multiplies
+            # split operators by split X~ (hi*hi + hi*lo + lo*hi); the inverse form
+            # multiplies the split L^-1 by the exact dosages (hi*X + lo*X)
+            prods = 2 if mode == "inverse" else 3
+            pk = base / prods
             roof = dict(bound="tensor", achieved=achieved, peak=pk, unit="TFLOP/s", frac=achieved / pk,
-                        traffic=kernel_traffic(path),
+                        traffic=kernel_traffic(path, mode),
                         peak_basis=(f"{'bf16' if path == 'bf16x3' else 'tf32'} dense tensor peak (of measured, "
-                                    "burst) / 3: three split products per algorithmic product"))
+                                    f"burst) / {prods}: {prods} split products per algorithmic product "
+                                    f"({mode} tile mode)"))
             sus = peaks.get("bf16_tflops_sustained")
-            if path == "bf16x3" and sus:  # the timed region runs ~0.2 s under the power cap
-                roof["frac_of_sustained"] = achieved / (sus / 3.0)
+            if path == "bf16x3" and sus:  # a long timed region runs under the power cap
+                roof["frac_of_sustained"] = achieved / (sus / prods)
         res["roofline"] = roof
         res["trsm_ms_per_launch"] = trsm_ms
         # end to end: the 8 blocks in pinned host memory, streamed through the block ring every step
-        if not args.no_e2e:
+        if not args.no_e2e and "/" not in entry:
             Xh = torch.empty((step_snps, n), dtype=torch.int8, pin_memory=True)
             Xh_np = Xh.numpy()
             for i in range(NB):
@@ -365,7 +381,7 @@ def run_ours(args, rank, world, local_rank, dist):
         # keep a few results for the error report against the oracle
         res["_sample"] = (b[:, :64].cpu().numpy().copy(), se[:, :64].cpu().numpy().copy(),
                           st[:64].cpu().numpy().copy(), (steps * NB - 1) % NB)
-        results[path] = res
+        results[entry] = res
         g.close()
         torch.cuda.empty_cache()
 
@@ -606,7 +622,7 @@ def main():
         "config": {"workload": WORKLOAD, "n": w["n"], "p": w["p"], "bs": w["bs"],
                    "snps_per_step": N_RESIDENT_BLOCKS * w["bs"],
                    "headline_path": head, "parallelism": f"snp-shard x{world}",
-                   "l2": "inputs larger than L2: 8 resident int8 blocks (328 MB) per step plus the n x n block operator streamed every block"},
+                   "l2": "inputs larger than L2: 8 resident int8 blocks (328 MB) per step plus the n x n operator (split L^-1 or block operator, 204 MB) streamed every block"},
         "roofline": hr["roofline"], "path_roofline": path_roofline, "e2e": hr.get("e2e"),
         "gpu_launches": hr["gpu_launches"],
         "clocks": hr["clocks"], "cpu_baseline": cpu, "paths": paths_out, "forms": forms,

@@ -88,11 +88,23 @@ typedef struct {
                         the two SMs of a thread-block cluster, each with its own product, the solved
                         blocks both need fetched once;
                       GWAS_TILES_PAIR_MMA (3): panels 2u and 2u+1 as one 256-row tensor-core product
-                        on the two SMs of a cluster */
+                        on the two SMs of a cluster;
+                      GWAS_TILES_INVERSE (4): L^-1 is formed once at gwas_init (on the tensor cores,
+                        TF32x3 substitution of the identity) and split like the block operator; a
+                        block is then the triangular product L^-1 X_R with no dependency between its
+                        tiles (256-row products on 2-SM clusters, longest first).  Costs one
+                        n_pad x bs cast copy of the block and, at set-up, up to 16 n_pad^2 bytes of
+                        transient device memory (n_pad = n rounded up to 128) */
   int reserved[2]; /* must be zero */
 } gwas_config;
 
-enum { GWAS_TILES_AUTO = 0, GWAS_TILES_SINGLE = 1, GWAS_TILES_PAIR_MULTICAST = 2, GWAS_TILES_PAIR_MMA = 3 };
+enum {
+  GWAS_TILES_AUTO = 0,
+  GWAS_TILES_SINGLE = 1,
+  GWAS_TILES_PAIR_MULTICAST = 2,
+  GWAS_TILES_PAIR_MMA = 3,
+  GWAS_TILES_INVERSE = 4
+};
 
 typedef struct gwas_ctx gwas_ctx; /* opaque; owned by the library */
 

@@ -27,7 +27,7 @@ ERRORS = {
 }
 PRECISIONS = {"fp64": 0, "tf32x3": 1, "bf16x3": 2}
 # split modes: how the solve's tiles map onto SMs (gwas_config.tile_mode)
-TILE_MODES = {"auto": 0, "single": 1, "pair_multicast": 2, "pair_mma": 3}
+TILE_MODES = {"auto": 0, "single": 1, "pair_multicast": 2, "pair_mma": 3, "inverse": 4}
 BUILT_PRECISIONS = ("fp64", "bf16x3", "tf32x3")
 SNP_OK, SNP_SINGULAR = 0, 1
 

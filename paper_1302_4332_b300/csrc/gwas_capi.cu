@@ -347,7 +347,7 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
   gwas_config_default(&cfg);
   if (cfg_in) cfg = *cfg_in;
   if (n < 1 || p < 1 || p > QMAX + 1 || !phi_or_L || !y || (p > 1 && !XL) || !(h >= 0.0 && h <= 1.0) ||
-      !(sigma2 > 0.0) || cfg.bs < 1 || cfg.ring_depth < 2 || cfg.strip_group < 0 || cfg.tile_mode < GWAS_TILES_AUTO || cfg.tile_mode > GWAS_TILES_PAIR_MMA ||
+      !(sigma2 > 0.0) || cfg.bs < 1 || cfg.ring_depth < 2 || cfg.strip_group < 0 || cfg.tile_mode < GWAS_TILES_AUTO || cfg.tile_mode > GWAS_TILES_INVERSE ||
       cfg.precision < GWAS_FP64 ||
       cfg.precision > GWAS_BF16X3)
     return GWAS_ERR_ARG;
@@ -715,7 +715,7 @@ int gwas_adjoint_block(gwas_ctx* ctx, const int8_t* XR, int64_t ldx, int ncols, 
     cudaError_t e;
     {
       StageMark m(ctx, GWAS_STAGE_TRSM, ctx->stream);
-      e = tc::run_block(ctx->tcs, static_cast<const int8_t*>(xin), ld_in, ncols, ctx->stream, &nl);
+      e = tc::run_block(ctx->tcs, static_cast<const int8_t*>(xin), ld_in, ncols, ctx->stream, &nl, true);
       if (e == cudaSuccess) e = tc::ensure_transpose(ctx->tcs, ctx->AopT, ctx->stream, &nl);
       if (e == cudaSuccess) e = tc::run_transpose(ctx->tcs, ncols, ctx->stream, &nl);
     }

@@ -38,6 +38,7 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
+#include <algorithm>
 #include <cstdio>
 #include <cstring>
 #include <vector>
@@ -93,6 +94,7 @@ struct TcMaps {
   CUtensorMap BhiH, BloH, X8H;  // half-width boxes (128 SNP columns) for the pair modes
   CUtensorMap StX, StHi, StLo;  // pair product's epilogue stores: FP32 X~, hi piece (BF16), lo piece
   CUtensorMap BinHi, BinLo;     // transpose solve: X~ pieces of the forward solve (its diagonal-block input)
+  CUtensorMap XcH;              // inverse form: the cast block x - c_i (BF16/FP32), half-width boxes
 };
 
 // A launch over one or several studies (the batching form): tiles of all
@@ -105,6 +107,7 @@ struct TcBatch {
   const TcStudy* studies;     // device copies of the studies when order != null
   const uint32_t* order;      // tile t -> (study << 28) | (k << 14) | c
   int nstudies, ntiles;
+  int pieces;                 // inverse form: also store the hi/lo pieces of X~ (the adjoint's input)
   unsigned int* counter;
   DevStatus* st;
 };
@@ -1100,6 +1103,334 @@ __global__ void __launch_bounds__(THREADS, 1)
   if (warp == 2) ptx::tmem_dealloc_pair(tmem_base, 2 * TN);
 }
 
+// ------------------------------------------------------------- inverse form
+// Tile mode TILES_INVERSE: the substitution moved into set-up.  L^-1 (lower
+// triangular, n_pad x n_pad, row-major) is formed once per study and split
+// into hi + lo pieces; a block of SNP columns is then the triangular product
+//     X~_kc = sum_{j<=k} (L^-1)_kj X_jc
+// whose output tiles depend on nothing but the inputs.  The dosages are exact
+// in BF16/TF32, so each K-block takes the two products Linv_hi X + Linv_lo X.
+// Work units are the row-panel pairs (2u, 2u+1) of a strip as one M = 256
+// product on a 2-SM cluster (cta_group::2, as in the pair product), handed out
+// longest first.  B comes by TMA from the cast copy of the block
+// (cast_shift_kernel: x - c_i as BF16/FP32), so TMA alone fills every stage.
+namespace inv2 {
+constexpr int STAGES = 8;
+constexpr int ST_COLS = 16;  // SNP columns per epilogue store chunk (32 rows x 16 FP32 = 2 KB)
+
+template <bool TF32>
+struct Cfg {
+  static constexpr int ESZ = TF32 ? 4 : 2;
+  static constexpr int KCH = 64 / ESZ;
+  static constexpr int KMMA = TF32 ? 8 : 16;
+  static constexpr int CPB = TB / KCH;
+  static constexpr int A_BYTES = TB * 64;                    // one piece of this CTA's L^-1 rows: 8 KB
+  static constexpr int B_BYTES = (TN / 2) * 64;              // this CTA's half of the SNP columns: 8 KB
+  static constexpr int STAGE_BYTES = 2 * A_BYTES + B_BYTES;  // 24 KB
+  static constexpr int CHUNK_BYTES = 2048;
+  static constexpr int STG_OFF = STAGES * STAGE_BYTES;
+  static constexpr int BAR_OFF = STG_OFF + EPI_WARPS * 2 * CHUNK_BYTES;
+  static constexpr int NBARS = 2 * STAGES + 4 + 3 * TRING + 1;
+  static constexpr int SMEM = 1024 + BAR_OFF + NBARS * 8 + TRING * 4 + 16;
+  static_assert(SMEM <= 232448, "shared memory per CTA");
+};
+}  // namespace inv2
+
+template <bool TF32>
+__global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_constant__ TcBatch b) {
+  using K = inv2::Cfg<TF32>;
+  constexpr int ST = inv2::STAGES;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + K::BAR_OFF);
+  uint64_t* full = bars;                 // CTA 0: both CTAs' loads of a stage
+  uint64_t* empty = full + ST;           // CTA 0's commit: the stage's MMAs are done
+  uint64_t* part_full = empty + ST;      // CTA 0's commit: a partial is complete
+  uint64_t* part_empty = part_full + 2;  // CTA 0: both CTAs' epilogues are done with a partial
+  uint64_t* tile_full = part_empty + 2;
+  uint64_t* tile_empty = tile_full + TRING;
+  uint64_t* peer_free = tile_empty + TRING;
+  uint64_t* drain = peer_free + TRING;
+  int* tile_ring = reinterpret_cast<int*>(drain + 1);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tile_ring + TRING);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int ntiles = b.ntiles;  // work units: row-panel pairs of a strip
+  DevStatus* st = b.st;
+  const uint32_t rank = ptx::cluster_ctarank();
+  const bool leader = rank == 0;
+  constexpr uint16_t BOTH = 3;
+  auto lead_addr = [&](uint64_t* bar) -> uint32_t { return leader ? ptx::smem_u32(bar) : ptx::peer_addr(bar, 0); };
+  auto count_lead = [&](uint64_t* bar) {
+    if (leader)
+      ptx::mbar_arrive(bar);
+    else
+      ptx::mbar_arrive_peer_count(ptx::peer_addr(bar, 0));
+  };
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < ST; ++s) {
+      ptx::mbar_init(&full[s], 2);   // one arrival from each CTA's producer (+ the bytes of both)
+      ptx::mbar_init(&empty[s], 1);  // CTA 0's commit
+    }
+    for (int a = 0; a < 2; ++a) {
+      ptx::mbar_init(&part_full[a], 1);
+      ptx::mbar_init(&part_empty[a], 2 * EPI_WARPS);
+    }
+    for (int i = 0; i < TRING; ++i) {
+      ptx::mbar_init(&tile_full[i], 1);
+      ptx::mbar_init(&tile_empty[i], 1 + EPI_WARPS);
+      ptx::mbar_init(&peer_free[i], 1);
+    }
+    ptx::mbar_init(drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    for (int q = 0; q < b.nstudies; ++q) {
+      ptx::prefetch_tensormap(&b.maps[q].Ahi);
+      ptx::prefetch_tensormap(&b.maps[q].Alo);
+      ptx::prefetch_tensormap(&b.maps[q].XcH);
+    }
+  }
+  if (warp == 2) {
+    ptx::tmem_alloc_pair(tmem_slot, 2 * TN);
+    ptx::tmem_relinquish_pair();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  ptx::cluster_sync();  // both CTAs' barriers and tensor memory exist before any remote access
+  const uint32_t tmem_base = *tmem_slot;
+
+  if (warp == 0) {
+    // ------------------------------------------------ scheduler + TMA producer
+    if (lane == 0) {
+      uint32_t cnt = 0;
+      for (int it = 0;; ++it) {
+        const int slot = it % TRING;
+        const uint32_t use = it / TRING;
+        if (!ptx::mbar_wait(&tile_empty[slot], (use & 1) ^ 1, st)) break;
+        int t;
+        if (leader) {
+          if (!ptx::mbar_wait(&peer_free[slot], use & 1, st)) break;
+          t = ptx::aborting(st) ? ntiles : (int)atomicAdd(b.counter, 1u);
+          if (t > ntiles) t = ntiles;
+          tile_ring[slot] = t;
+          ptx::st_peer_u32(ptx::peer_addr(&tile_ring[slot], 1), (uint32_t)t);
+          ptx::mbar_arrive(&tile_full[slot]);
+          ptx::mbar_arrive_peer(ptx::peer_addr(&tile_full[slot], 1));
+        } else {
+          ptx::mbar_arrive_peer(ptx::peer_addr(&peer_free[slot], 0));
+          if (!ptx::mbar_wait_s<true>(&tile_full[slot], use & 1, st)) break;
+          t = tile_ring[slot];
+        }
+        if (t >= ntiles) break;
+        int sidx, row, c;
+        TcStudy S;
+        decode_tile(b, t, sidx, row, c, S);
+        const TcMaps& M = b.maps[sidx];
+        const pair2::Unit u = pair2::make_unit(row, S);
+        const int arow = rank == 0 ? u.k0 : (u.paired ? u.k0 + 1 : -1);  // this CTA's row panel
+        const int ycol = c * TN + (int)rank * (TN / 2);                   // this CTA's SNP columns
+        bool ok = true;
+        for (int j = 0; j < u.nkb && ok; ++j) {
+          // block (arow, j) above the diagonal, or no rows: a box wholly outside reads zeros
+          const int ay = (arow >= 0 && j <= arow) ? arow * TB : -TB;
+          for (int h = 0; h < K::CPB; ++h, ++cnt) {
+            const int s = cnt % ST;
+            const uint32_t r = cnt / ST;
+            if (!ptx::mbar_wait(&empty[s], (r & 1) ^ 1, st)) { ok = false; break; }
+            uint8_t* sb = smem + s * K::STAGE_BYTES;
+            const int kx = j * TB + h * K::KCH;
+            const uint32_t fb = lead_addr(&full[s]);
+            if (leader)
+              ptx::mbar_arrive_expect_tx(&full[s], 2 * K::STAGE_BYTES);
+            else
+              ptx::mbar_arrive_peer_count(fb);
+            ptx::tma_load_2d_pair(sb, &M.Ahi, fb, kx, ay);
+            ptx::tma_load_2d_pair(sb + K::A_BYTES, &M.Alo, fb, kx, ay);
+            ptx::tma_load_2d_pair(sb + 2 * K::A_BYTES, &M.XcH, fb, kx, ycol);
+          }
+        }
+        if (!ok) break;
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------- MMA issuer (CTA 0 only)
+    if (lane == 0) {
+      constexpr uint32_t idesc = ptx::idesc_f32acc<TF32>(2 * TB, TN);
+      uint32_t cnt = 0, kb = 0;
+      for (int it = 0;; ++it) {
+        const int slot = it % TRING;
+        const uint32_t use = it / TRING;
+        if (!ptx::mbar_wait_s<true>(&tile_full[slot], use & 1, st)) break;
+        const int t = tile_ring[slot];
+        ptx::mbar_arrive(&tile_empty[slot]);
+        if (t >= ntiles) break;
+        if (!leader) continue;
+        int sidx, row, c;
+        TcStudy S;
+        decode_tile(b, t, sidx, row, c, S);
+        const pair2::Unit u = pair2::make_unit(row, S);
+        bool ok = true;
+        for (int j = 0; j < u.nkb && ok; ++j) {
+          // every K-block into a fresh partial (promoted by the epilogue)
+          const int a = kb & 1;
+          if (!ptx::mbar_wait(&part_empty[a], ((kb >> 1) & 1) ^ 1, st)) { ok = false; break; }
+          ++kb;
+          ptx::tc_fence_after();
+          const uint32_t d = tmem_base + a * TN;
+          uint32_t accumulate = 0;
+          for (int h = 0; h < K::CPB; ++h, ++cnt) {
+            const int s = cnt % ST;
+            const uint32_t r = cnt / ST;
+            if (!ptx::mbar_wait(&full[s], r & 1, st)) { ok = false; break; }
+            ptx::tc_fence_after();
+            const uint32_t base = ptx::smem_u32(smem + s * K::STAGE_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < K::KCH / K::KMMA; ++kk) {
+              const uint32_t off = kk * K::KMMA * K::ESZ;
+              const uint64_t ahi = ptx::sdesc_k64(base + off);
+              const uint64_t alo = ptx::sdesc_k64(base + K::A_BYTES + off);
+              const uint64_t bx = ptx::sdesc_k64(base + 2 * K::A_BYTES + off);
+              ptx::mma_pair<TF32>(d, alo, bx, idesc, accumulate);
+              accumulate = 1;
+              ptx::mma_pair<TF32>(d, ahi, bx, idesc, 1);
+            }
+            ptx::mma_commit_pair(&empty[s], BOTH);
+          }
+          if (!ok) break;
+          ptx::mma_commit_pair(&part_full[a], BOTH);
+        }
+        if (!ok) break;
+      }
+    }
+  } else if (warp >= 4) {
+    // ----------------------------------------------------------------- epilogue
+    constexpr int NT = 32 * EPI_WARPS;
+    constexpr int CC = inv2::ST_COLS;
+    const int e = warp - 4;
+    const int lq = e & 3;
+    const int chalf = e >> 2;
+    uint32_t kb = 0, gq = 0;  // partials taken; store chunks issued
+    float master[EPI_COLS];
+    for (int it = 0;; ++it) {
+      const int slot = it % TRING;
+      const uint32_t use = it / TRING;
+      if (!ptx::group_and(1, NT, ptx::mbar_wait_s<true>(&tile_full[slot], use & 1, st))) break;
+      const int t = tile_ring[slot];
+      ptx::named_bar(1, NT);
+      if (lane == 0) ptx::mbar_arrive(&tile_empty[slot]);
+      if (t >= ntiles) break;
+      int sidx, row, c;
+      TcStudy S;
+      decode_tile(b, t, sidx, row, c, S);
+      const pair2::Unit u = pair2::make_unit(row, S);
+      const bool has = leader || u.paired;  // this CTA has a tile
+      const int k = u.k0 + (int)rank;
+#pragma unroll
+      for (int i = 0; i < EPI_COLS; ++i) master[i] = 0.f;
+      bool ok = true;
+      for (int pp = 0; pp < u.nkb && ok; ++pp) {
+        const int a = kb & 1;
+        if (!ptx::group_and(1, NT, ptx::mbar_wait(&part_full[a], (kb >> 1) & 1, st))) { ok = false; break; }
+        ptx::tc_fence_after();
+        if (has) {
+          const uint32_t tb = tmem_base + (static_cast<uint32_t>(32 * lq) << 16) + a * TN + chalf * EPI_COLS;
+#pragma unroll
+          for (int ch = 0; ch < EPI_COLS / 16; ++ch) {
+            uint32_t v[16];
+            ptx::tmem_ld_32x32b_x16(tb + ch * 16, v);
+            ptx::tmem_ld_wait();
+#pragma unroll
+            for (int i = 0; i < 16; ++i) master[ch * 16 + i] += __uint_as_float(v[i]);  // round to nearest
+          }
+        }
+        ptx::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) count_lead(&part_empty[a]);
+        ++kb;
+      }
+      if (!ok) break;
+      if (!has) continue;
+      // X~ of this CTA's tile to HBM by TMA stores of shared-memory chunks (and,
+      // for the transpose solve of the adjoint form, its hi/lo pieces)
+      const TcMaps& M = b.maps[sidx];
+      uint8_t* stg = smem + K::STG_OFF + e * 2 * K::CHUNK_BYTES;
+      const int r0 = k * TB + 32 * lq;
+      const int c0 = c * TN + chalf * EPI_COLS;
+      auto next_buf = [&]() -> uint8_t* {
+        uint8_t* buf = stg + (gq & 1) * K::CHUNK_BYTES;
+        if (gq >= 2) {
+          if (lane == 0) ptx::bulk_wait_read<1>();
+          __syncwarp();
+        }
+        ++gq;
+        return buf;
+      };
+#pragma unroll
+      for (int q = 0; q < EPI_COLS / CC; ++q) {
+        uint8_t* buf = next_buf();
+#pragma unroll
+        for (int i = 0; i < CC; ++i) reinterpret_cast<float*>(buf)[i * 32 + lane] = master[q * CC + i];
+        ptx::fence_proxy_async_shared();
+        __syncwarp();
+        if (lane == 0) {
+          ptx::tma_store_2d(&M.StX, buf, r0, c0 + q * CC);
+          ptx::bulk_commit();
+        }
+      }
+      if (b.pieces) {
+#pragma unroll
+        for (int q = 0; q < EPI_COLS / CC; ++q) {
+          uint8_t* buf = next_buf();
+#pragma unroll
+          for (int i = 0; i < CC; ++i) {
+            const float x = master[q * CC + i];
+            if constexpr (TF32) {
+              reinterpret_cast<float*>(buf)[i * 32 + lane] = x - __uint_as_float(tf32_trunc_bits(x));
+            } else {
+              const __nv_bfloat16 hi = __float2bfloat16_rn(x);
+              reinterpret_cast<__nv_bfloat16*>(buf)[i * 32 + lane] = hi;
+              reinterpret_cast<__nv_bfloat16*>(buf + 1024)[i * 32 + lane] =
+                  __float2bfloat16_rn(x - __bfloat162float(hi));
+            }
+          }
+          ptx::fence_proxy_async_shared();
+          __syncwarp();
+          if (lane == 0) {
+            if constexpr (TF32) {
+              ptx::tma_store_2d(&M.StLo, buf, r0, c0 + q * CC);
+            } else {
+              ptx::tma_store_2d(&M.StHi, buf, r0, c0 + q * CC);
+              ptx::tma_store_2d(&M.StLo, buf + 1024, r0, c0 + q * CC);
+            }
+            ptx::bulk_commit();
+          }
+        }
+      }
+    }
+    if (lane == 0) ptx::bulk_wait_all();  // the last stores have read the staging buffers
+  }
+
+  // ---------------------------------------------------------------- teardown
+  if (warp == 1 && lane == 0 && leader) {
+    // every MMA of the pair has completed before tensor memory is released
+    ptx::mma_commit_pair(drain, 1);
+    const long long t0 = ptx::globaltimer();
+    while (!ptx::mbar_try_wait(drain, 0) && ptx::globaltimer() - t0 < 100000000LL) {
+    }
+  }
+  if (ptx::aborting(st)) {
+    const long long t0 = ptx::globaltimer();
+    while (ptx::globaltimer() - t0 < 2000000LL) {
+    }
+  }
+  ptx::cluster_sync();
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  if (warp == 2) ptx::tmem_dealloc_pair(tmem_base, 2 * TN);
+}
+
 // ------------------------------------------- per-SNP integer shift (pre-pass)
 // c_i = round(mean of the n dosages of SNP i), from an exact integer sum.
 __global__ void column_shift_kernel(const int8_t* __restrict__ X, int64_t ldx, int n, int ncols,
@@ -1126,6 +1457,113 @@ __global__ void column_shift_kernel(const int8_t* __restrict__ X, int64_t ldx, i
     if (c > 127) c = 127;
     if (c < -127) c = -127;
     shift[col] = (int8_t)c;
+  }
+}
+
+// B operand of the inverse form: x'_ri = x_ri - c_i on rows < n and 0 on rows
+// n..n_pad-1, as BF16 (or FP32, read as TF32 by the tensor cores), column-major
+// with leading dimension n_pad.  c_i is computed here as in column_shift_kernel
+// when `shift` is given (and stored there), else 0.  One warp per SNP column.
+template <bool TF32>
+__global__ void cast_shift_kernel(const int8_t* __restrict__ X, int64_t ldx, int n, int n_pad, int ncols,
+                                  int8_t* __restrict__ shift, void* __restrict__ xc) {
+  const int lane = threadIdx.x & 31;
+  const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (col >= ncols) return;
+  const int8_t* x = X + (int64_t)col * ldx;  // 16-byte aligned (checked by the caller)
+  const int n16 = n & ~15;
+  int c = 0;
+  if (shift) {
+    int sum = 0;
+    for (int r = lane * 16; r < n16; r += 32 * 16) {
+      const int4 v = __ldg(reinterpret_cast<const int4*>(x + r));
+      const int w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int i = 0; i < 4; ++i) sum += __dp4a(w[i], 0x01010101, 0);
+    }
+    for (int r = n16 + lane; r < n; r += 32) sum += x[r];
+#pragma unroll
+    for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    const long long num = 2LL * sum + n, den = 2LL * n;
+    long long cc = num >= 0 ? num / den : -((-num + den - 1) / den);
+    cc = cc > 127 ? 127 : (cc < -127 ? -127 : cc);
+    c = (int)cc;
+    if (lane == 0) shift[col] = (int8_t)c;
+  }
+  for (int r = lane * 16; r < n_pad; r += 32 * 16) {  // n_pad is a multiple of 128
+    float f[16];
+    if (r + 16 <= n) {
+      const int4 v = __ldg(reinterpret_cast<const int4*>(x + r));
+      const int w[4] = {v.x, v.y, v.z, v.w};
+#pragma unroll
+      for (int i = 0; i < 16; ++i) f[i] = (float)((int)(int8_t)(w[i >> 2] >> (8 * (i & 3))) - c);
+    } else {
+#pragma unroll
+      for (int i = 0; i < 16; ++i) f[i] = (r + i < n) ? (float)((int)x[r + i] - c) : 0.f;
+    }
+    if constexpr (TF32) {
+      float4* o = reinterpret_cast<float4*>(static_cast<float*>(xc) + (int64_t)col * n_pad + r);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) o[i] = make_float4(f[4 * i], f[4 * i + 1], f[4 * i + 2], f[4 * i + 3]);
+    } else {
+      uint32_t wv[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const __nv_bfloat162 b2 = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
+        wv[i] = *reinterpret_cast<const uint32_t*>(&b2);
+      }
+      uint4* o = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(xc) + (int64_t)col * n_pad + r);
+      o[0] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+      o[1] = make_uint4(wv[4], wv[5], wv[6], wv[7]);
+    }
+  }
+}
+
+// Columns c0.. c0+ncols-1 of the n_pad x n_pad identity as int8, column-major
+// with leading dimension n_pad (the right-hand side that turns the
+// substitution into L^-1).
+__global__ void identity_i8_kernel(int8_t* __restrict__ I8, int n_pad, int c0, int ncols) {
+  const int64_t total = (int64_t)n_pad * ncols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int col = (int)(e / n_pad), row = (int)(e % n_pad);
+    I8[e] = row == c0 + col ? 1 : 0;
+  }
+}
+
+// Columns c0.. of L^-1, solved into `xt` (FP32, column-major, leading
+// dimension ldt), transposed into the row-major hi/lo pieces of the inverse
+// form's operator.  Entries above the diagonal and in the padding rows and
+// columns (index >= n) are set to zero.  32 x 32 tiles through shared memory.
+template <bool TF32>
+__global__ void linv_split_kernel(const float* __restrict__ xt, int64_t ldt, int n, int n_pad, int c0, int ncols,
+                                  void* __restrict__ hi, void* __restrict__ lo) {
+  __shared__ float tile[32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  const int q0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int q = q0 + ty + 8 * i;
+    tile[ty + 8 * i][tx] = q < ncols ? xt[(int64_t)q * ldt + r0 + tx] : 0.f;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int row = r0 + ty + 8 * i, q = q0 + tx, gcol = c0 + q;
+    if (q >= ncols) continue;
+    float v = tile[tx][ty + 8 * i];
+    if (row >= n || gcol >= n || gcol > row) v = 0.f;
+    const int64_t idx = (int64_t)row * n_pad + gcol;
+    if constexpr (TF32) {
+      uint32_t hb;
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(v));
+      const float h = __uint_as_float(hb);
+      static_cast<float*>(hi)[idx] = h;
+      static_cast<float*>(lo)[idx] = v - h;
+    } else {
+      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      static_cast<__nv_bfloat16*>(hi)[idx] = h;
+      static_cast<__nv_bfloat16*>(lo)[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
+    }
   }
 }
 
@@ -1239,6 +1677,7 @@ struct TcState {
   void* xhhi = nullptr;
   void* xhlo = nullptr;
   CUtensorMap mAhiT, mAloT, mBhiT, mBloT;
+  void* xc = nullptr;  // inverse form: the cast block x - c_i (n_pad x bs, BF16 or FP32)
   EncodeTiledFn encode = nullptr;
 };
 
@@ -1289,12 +1728,20 @@ static cudaError_t set_smem_attr_pair_mma() {
 }
 
 template <bool TF32>
+static cudaError_t set_smem_attr_inv() {
+  return cudaFuncSetAttribute(trsm_tc_inv_kernel<TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              inv2::Cfg<TF32>::SMEM);
+}
+
+template <bool TF32>
 static cudaLaunchConfig_t pair_config(cudaLaunchAttribute* attr, int grid, cudaStream_t s, TileMode mode) {
   cudaLaunchConfig_t cfg;
   memset(&cfg, 0, sizeof cfg);
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(THREADS);
-  cfg.dynamicSmemBytes = mode == TILES_PAIR_MMA ? pair2::Cfg<TF32>::SMEM : Cfg<TF32>::SMEM;
+  cfg.dynamicSmemBytes = mode == TILES_INVERSE    ? inv2::Cfg<TF32>::SMEM
+                         : mode == TILES_PAIR_MMA ? pair2::Cfg<TF32>::SMEM
+                                                  : Cfg<TF32>::SMEM;
   cfg.stream = s;
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = 2;
@@ -1310,10 +1757,13 @@ template <bool TF32>
 static cudaError_t query_clusters(int num_sms, TileMode mode, int* out) {
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t cfg = pair_config<TF32>(attr, 2 * (num_sms / 2), nullptr, mode);
-  const void* fn = mode == TILES_PAIR_MMA ? (const void*)trsm_tc_pair_mma_kernel<TF32>
-                                          : (const void*)trsm_tc_kernel<TF32, true>;
+  const void* fn = mode == TILES_INVERSE    ? (const void*)trsm_tc_inv_kernel<TF32>
+                   : mode == TILES_PAIR_MMA ? (const void*)trsm_tc_pair_mma_kernel<TF32>
+                                            : (const void*)trsm_tc_kernel<TF32, true>;
   return cudaOccupancyMaxActiveClusters(out, fn, &cfg);
 }
+
+static cudaError_t build_inverse(TcState* t, const double* Aop, cudaStream_t s, int64_t* launches);
 
 cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_pad, int bs, int num_sms,
                    bool center, DevStatus* st, cudaStream_t s, int64_t* launches, int strip_group, TileMode mode) {
@@ -1348,35 +1798,42 @@ cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_p
   TRY(cudaMalloc(&t->shift, (size_t)bs));
   t->center = center;
   t->strip_group = strip_group;
-  // measured at n = 1e4 with 4096-column blocks: the pair product is the
-  // fastest for both splits
-  if (mode == TILES_AUTO) mode = TILES_PAIR_MMA;
+  // measured at n = 1e4 with 4096-column blocks: the inverse form is the
+  // fastest for both splits (BF16: 0.51 ms a block against 0.93 ms for the
+  // pair product of the substitution)
+  if (mode == TILES_AUTO) mode = TILES_INVERSE;
   t->mode = mode;
-  if (strip_group > 0) {
+  const bool inv = mode == TILES_INVERSE;
+  if (inv) TRY(cudaMalloc(&t->xc, esz * (size_t)n_pad * bs));
+  if (strip_group > 0 || inv) {
     TRY(cudaMalloc(&t->order, sizeof(uint32_t) * (size_t)t->P * Cmax));
     TRY(cudaMalloc(&t->study_dev, sizeof(TcStudy)));
   }
   t->sched_bytes = 128 + sizeof(int) * (size_t)t->P * Cmax;
   TRY(cudaMalloc(&t->sched, t->sched_bytes));
   TRY(cudaMemsetAsync(t->sched, 0, t->sched_bytes, s));
-  // the pair product multiplies the pair form of the operator (pair_rows_kernel)
-  const double* src = Aop;
-  double* pair_form = nullptr;
-  if (mode == TILES_PAIR_MMA && t->P > 1) {
-    TRY(cudaMallocAsync(&pair_form, sizeof(double) * n2, s));
-    TRY(cudaMemcpyAsync(pair_form, Aop, sizeof(double) * n2, cudaMemcpyDeviceToDevice, s));
-    pair_rows_kernel<<<dim3(n_pad / 64, t->P / 2), 256, 0, s>>>(Aop, pair_form, n_pad, t->P);
+  if (inv) {
+    TRY(build_inverse(t, Aop, s, launches));
+  } else {
+    // the pair product multiplies the pair form of the operator (pair_rows_kernel)
+    const double* src = Aop;
+    double* pair_form = nullptr;
+    if (mode == TILES_PAIR_MMA && t->P > 1) {
+      TRY(cudaMallocAsync(&pair_form, sizeof(double) * n2, s));
+      TRY(cudaMemcpyAsync(pair_form, Aop, sizeof(double) * n2, cudaMemcpyDeviceToDevice, s));
+      pair_rows_kernel<<<dim3(n_pad / 64, t->P / 2), 256, 0, s>>>(Aop, pair_form, n_pad, t->P);
+      ++*launches;
+      TRY(cudaGetLastError());
+      src = pair_form;
+    }
+    if (t->tf32)
+      split_aop_kernel<true><<<1184, 256, 0, s>>>(src, (int64_t)n2, t->ahi, t->alo);
+    else
+      split_aop_kernel<false><<<1184, 256, 0, s>>>(src, (int64_t)n2, t->ahi, t->alo);
     ++*launches;
+    if (pair_form) TRY(cudaFreeAsync(pair_form, s));
     TRY(cudaGetLastError());
-    src = pair_form;
   }
-  if (t->tf32)
-    split_aop_kernel<true><<<1184, 256, 0, s>>>(src, (int64_t)n2, t->ahi, t->alo);
-  else
-    split_aop_kernel<false><<<1184, 256, 0, s>>>(src, (int64_t)n2, t->ahi, t->alo);
-  ++*launches;
-  if (pair_form) TRY(cudaFreeAsync(pair_form, s));
-  TRY(cudaGetLastError());
   const CUtensorMapDataType dt = t->tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   const uint32_t kch = t->tf32 ? Cfg<true>::KCH : Cfg<false>::KCH;
   TRY(make_map(t->encode, &t->mAhi, dt, t->ahi, n_pad, n_pad, esz * n_pad, kch, TB, true));
@@ -1386,7 +1843,9 @@ cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_p
   TRY(make_map(t->encode, &t->mBlo, dt, t->blo, n_pad, bs, esz * n_pad, kch, TN, true));
   TRY(make_map(t->encode, &t->mBhiH, dt, bhi_base, n_pad, bs, esz * n_pad, kch, TN / 2, true));
   TRY(make_map(t->encode, &t->mBloH, dt, t->blo, n_pad, bs, esz * n_pad, kch, TN / 2, true));
-  const uint32_t stc = t->tf32 ? pair2::st_cols<true>() : pair2::st_cols<false>();
+  // epilogue store chunks: the pair product's (value + pieces in one 2 KB
+  // buffer), or the inverse form's (FP32 value alone, 16 columns)
+  const uint32_t stc = inv ? inv2::ST_COLS : (t->tf32 ? pair2::st_cols<true>() : pair2::st_cols<false>());
   TRY(make_map(t->encode, &t->mStX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, t->xt32, n_pad, bs, 4 * (size_t)n_pad, 32, stc,
                false));
   memset(&t->mStHi, 0, sizeof t->mStHi);
@@ -1396,6 +1855,7 @@ cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_p
   if (mode != TILES_SINGLE) {
     TRY((t->tf32 ? set_smem_attr<true, true>() : set_smem_attr<false, true>()));
     TRY((t->tf32 ? set_smem_attr_pair_mma<true>() : set_smem_attr_pair_mma<false>()));
+    TRY((t->tf32 ? set_smem_attr_inv<true>() : set_smem_attr_inv<false>()));
     TRY((t->tf32 ? query_clusters<true>(num_sms, mode, &t->max_clusters)
                  : query_clusters<false>(num_sms, mode, &t->max_clusters)));
     if (t->max_clusters < 1) TRY(cudaErrorLaunchOutOfResources);
@@ -1415,21 +1875,64 @@ static void append_study_order(std::vector<uint32_t>& order, int si, int P, int 
         order.push_back(((uint32_t)si << 28) | ((uint32_t)k << 14) | (uint32_t)c);
 }
 
+// Inverse form: work units longest first (pair row r has 2r + 2 K-blocks, the
+// last row of an odd P 2r + 1), the studies' units merged by length; equal
+// lengths keep study, then strip order.
+struct UnitKey {
+  int len;
+  uint32_t code;
+};
+static void append_units(std::vector<UnitKey>& v, int si, int P, int C) {
+  for (int r = 0; r < (P + 1) / 2; ++r) {
+    const int len = 2 * r + (2 * r + 1 < P ? 2 : 1);
+    for (int c = 0; c < C; ++c) v.push_back({len, ((uint32_t)si << 28) | ((uint32_t)r << 14) | (uint32_t)c});
+  }
+}
+static void longest_first(std::vector<UnitKey>& v, std::vector<uint32_t>& order) {
+  std::stable_sort(v.begin(), v.end(), [](const UnitKey& a, const UnitKey& b) { return a.len > b.len; });
+  for (const UnitKey& u : v) order.push_back(u.code);
+}
+
+// Inverse form: the cast block's map (half-width boxes) and the cast
+// pre-pass (with the integer shifts when centering).
+static cudaError_t prepare_cast(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaStream_t s,
+                                int64_t* launches, CUtensorMap* mXcH) {
+  const size_t esz = t->tf32 ? 4 : 2;
+  const CUtensorMapDataType dt = t->tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const uint32_t kch = t->tf32 ? Cfg<true>::KCH : Cfg<false>::KCH;
+  cudaError_t e = make_map(t->encode, mXcH, dt, t->xc, (uint64_t)t->n_pad, (uint64_t)ncols, esz * t->n_pad, kch,
+                           TN / 2, true);
+  if (e != cudaSuccess) return e;
+  int8_t* sh = t->center ? t->shift : nullptr;
+  if (t->tf32)
+    cast_shift_kernel<true><<<(ncols + 7) / 8, 256, 0, s>>>(X, ldx, t->n, t->n_pad, ncols, sh, t->xc);
+  else
+    cast_shift_kernel<false><<<(ncols + 7) / 8, 256, 0, s>>>(X, ldx, t->n, t->n_pad, ncols, sh, t->xc);
+  ++*launches;
+  return cudaGetLastError();
+}
+
 // The study part of one launch: int8 map, cleared flags, integer shifts.
 static cudaError_t prepare_study(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaStream_t s,
-                                 int64_t* launches, TcStudy* S, CUtensorMap* mX8, CUtensorMap* mX8H) {
+                                 int64_t* launches, TcStudy* S, CUtensorMap* mX8, CUtensorMap* mX8H,
+                                 CUtensorMap* mXcH) {
   if (ncols > t->bs || (reinterpret_cast<uintptr_t>(X) & 15) || (ldx & 15) || ldx < t->n)
     return cudaErrorInvalidValue;
-  cudaError_t e = make_map(t->encode, mX8, CU_TENSOR_MAP_DATA_TYPE_UINT8, X, (uint64_t)t->n, (uint64_t)ncols,
-                           (uint64_t)ldx, TB, TN, false);
-  if (e != cudaSuccess) return e;
-  e = make_map(t->encode, mX8H, CU_TENSOR_MAP_DATA_TYPE_UINT8, X, (uint64_t)t->n, (uint64_t)ncols, (uint64_t)ldx,
-               TB, TN / 2, false);
-  if (e != cudaSuccess) return e;
+  cudaError_t e;
+  if (t->mode != TILES_INVERSE) {
+    e = make_map(t->encode, mX8, CU_TENSOR_MAP_DATA_TYPE_UINT8, X, (uint64_t)t->n, (uint64_t)ncols, (uint64_t)ldx, TB,
+                 TN, false);
+    if (e != cudaSuccess) return e;
+    e = make_map(t->encode, mX8H, CU_TENSOR_MAP_DATA_TYPE_UINT8, X, (uint64_t)t->n, (uint64_t)ncols, (uint64_t)ldx,
+                 TB, TN / 2, false);
+    if (e != cudaSuccess) return e;
+  }
   const int C = (ncols + TN - 1) / TN;
   e = cudaMemsetAsync(t->sched, 0, 128 + sizeof(int) * (size_t)t->P * C, s);
   if (e != cudaSuccess) return e;
-  if (t->center) {
+  if (t->mode == TILES_INVERSE) {
+    if ((e = prepare_cast(t, X, ldx, ncols, s, launches, mXcH)) != cudaSuccess) return e;
+  } else if (t->center) {
     column_shift_kernel<<<(ncols + 7) / 8, 256, 0, s>>>(X, ldx, t->n, ncols, t->shift);
     ++*launches;
     if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1452,6 +1955,7 @@ static cudaError_t launch_pair(const TcBatch& b, int max_clusters, cudaStream_t 
   const int ncl = b.ntiles < max_clusters ? b.ntiles : max_clusters;
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t cfg = pair_config<TF32>(attr, 2 * ncl, s, mode);
+  if (mode == TILES_INVERSE) return cudaLaunchKernelEx(&cfg, trsm_tc_inv_kernel<TF32>, b);
   if (mode == TILES_PAIR_MMA) return cudaLaunchKernelEx(&cfg, trsm_tc_pair_mma_kernel<TF32>, b);
   return cudaLaunchKernelEx(&cfg, trsm_tc_kernel<TF32, true>, b);
 }
@@ -1473,11 +1977,13 @@ static cudaError_t launch_kernel(bool tf32, TileMode mode, const TcBatch& b, int
   return cudaGetLastError();
 }
 
-cudaError_t run_block(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaStream_t s, int64_t* launches) {
+cudaError_t run_block(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaStream_t s, int64_t* launches,
+                      bool pieces) {
   if (ncols <= 0) return cudaSuccess;
   TcBatch b;
   memset(&b, 0, sizeof b);
-  cudaError_t e = prepare_study(t, X, ldx, ncols, s, launches, &b.s0, &b.maps[0].X8, &b.maps[0].X8H);
+  cudaError_t e =
+      prepare_study(t, X, ldx, ncols, s, launches, &b.s0, &b.maps[0].X8, &b.maps[0].X8H, &b.maps[0].XcH);
   if (e != cudaSuccess) return e;
   b.maps[0].Ahi = t->mAhi;
   b.maps[0].Alo = t->mAlo;
@@ -1492,10 +1998,18 @@ cudaError_t run_block(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaS
   b.ntiles = unit_rows(t) * b.s0.C;
   b.counter = t->sched;
   b.st = t->st;
-  if (t->strip_group > 0 && t->strip_group < b.s0.C) {
-    if (t->order_C != b.s0.C) {  // (re)build the grouped order for this strip count
+  b.pieces = pieces ? 1 : 0;
+  const bool inv = t->mode == TILES_INVERSE;
+  if (inv || (t->strip_group > 0 && t->strip_group < b.s0.C)) {
+    if (t->order_C != b.s0.C) {  // (re)build the order for this strip count
       std::vector<uint32_t> order;
-      append_study_order(order, 0, unit_rows(t), b.s0.C, t->strip_group);
+      if (inv) {
+        std::vector<UnitKey> units;
+        append_units(units, 0, t->P, b.s0.C);
+        longest_first(units, order);
+      } else {
+        append_study_order(order, 0, unit_rows(t), b.s0.C, t->strip_group);
+      }
       if ((e = cudaMemcpyAsync(t->order, order.data(), sizeof(uint32_t) * order.size(), cudaMemcpyHostToDevice, s)) !=
               cudaSuccess ||
           (e = cudaStreamSynchronize(s)) != cudaSuccess)
@@ -1508,6 +2022,44 @@ cudaError_t run_block(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaS
     b.studies = t->study_dev;
   }
   return launch_kernel(t->tf32, t->mode, b, t->num_sms, t->max_clusters, s, launches);
+}
+
+// Inverse form set-up: L^-1 = the substitution applied to the identity, on
+// the tensor cores in TF32x3 (the pair product over Aop, 4096 identity
+// columns per launch, no centering), then transposed and split into the
+// row-major hi/lo pieces of t.  Synchronizes the stream.
+static cudaError_t build_inverse(TcState* t, const double* Aop, cudaStream_t s, int64_t* launches) {
+  const int np = t->n_pad;
+  const int bsi = np < 4096 ? np : 4096;
+  TcState* g = nullptr;
+  cudaError_t e = create(&g, SPLIT_TF32, Aop, t->n, np, bsi, t->num_sms, false, t->st, s, launches, 0, TILES_PAIR_MMA);
+  if (e != cudaSuccess) return e;
+  int8_t* eye = nullptr;
+  e = cudaMalloc(&eye, (size_t)np * bsi);
+  for (int c0 = 0; e == cudaSuccess && c0 < np; c0 += bsi) {
+    const int nc = np - c0 < bsi ? np - c0 : bsi;
+    identity_i8_kernel<<<1184, 256, 0, s>>>(eye, np, c0, nc);
+    ++*launches;
+    if ((e = cudaGetLastError()) != cudaSuccess) break;
+    if ((e = run_block(g, eye, np, nc, s, launches)) != cudaSuccess) break;
+    const dim3 grid((nc + 31) / 32, np / 32);
+    if (t->tf32)
+      linv_split_kernel<true><<<grid, dim3(32, 8), 0, s>>>(g->xt32, g->ldt, t->n, np, c0, nc, t->ahi, t->alo);
+    else
+      linv_split_kernel<false><<<grid, dim3(32, 8), 0, s>>>(g->xt32, g->ldt, t->n, np, c0, nc, t->ahi, t->alo);
+    ++*launches;
+    e = cudaGetLastError();
+  }
+  const cudaError_t es = cudaStreamSynchronize(s);  // before g's buffers go
+  if (e == cudaSuccess) e = es;
+  if (e == cudaSuccess && t->st) {
+    DevStatus h;
+    if ((e = cudaMemcpy(&h, t->st, sizeof h, cudaMemcpyDeviceToHost)) == cudaSuccess && h.err != DEV_OK)
+      e = cudaErrorLaunchTimeout;  // a bounded wait of the solve expired
+  }
+  cudaFree(eye);
+  destroy(g);
+  return e;
 }
 
 // ------------------------------------------------------ transpose solve (adjoint)
@@ -1583,7 +2135,7 @@ struct TcBatchState {
   int nstudies = 0;
   int ntiles = 0;
   TcStudy S[MAX_STUDIES];
-  CUtensorMap mX8[MAX_STUDIES], mX8H[MAX_STUDIES];
+  CUtensorMap mX8[MAX_STUDIES], mX8H[MAX_STUDIES], mXcH[MAX_STUDIES] = {};
   const int8_t* X[MAX_STUDIES];
   int64_t ldx[MAX_STUDIES];
   bool tf32 = false;
@@ -1642,6 +2194,14 @@ cudaError_t batch_plan(TcBatchState* B, TcState* const* ts, const int8_t* const*
     e = make_map(t->encode, &B->mX8H[i], CU_TENSOR_MAP_DATA_TYPE_UINT8, X[i], (uint64_t)t->n, (uint64_t)ncols[i],
                  (uint64_t)ldx[i], TB, TN / 2, false);
     if (e != cudaSuccess) return e;
+    if (t->mode == TILES_INVERSE) {
+      const size_t esz = t->tf32 ? 4 : 2;
+      e = make_map(t->encode, &B->mXcH[i],
+                   t->tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, t->xc,
+                   (uint64_t)t->n_pad, (uint64_t)ncols[i], esz * t->n_pad, t->tf32 ? Cfg<true>::KCH : Cfg<false>::KCH,
+                   TN / 2, true);
+      if (e != cudaSuccess) return e;
+    }
     S[i].P = t->P;
     S[i].C = (ncols[i] + TN - 1) / TN;
     S[i].ncols = ncols[i];
@@ -1657,7 +2217,12 @@ cudaError_t batch_plan(TcBatchState* B, TcState* const* ts, const int8_t* const*
   }
   std::vector<uint32_t> order;
   order.reserve(total);
-  if (order_mode == 0) {
+  if (B->mode == TILES_INVERSE) {  // no dependencies: longest units first over all studies
+    std::vector<UnitKey> units;
+    for (int i = 0; i < B->nstudies; ++i)
+      if (ncols[i] > 0) append_units(units, i, ts[i]->P, S[i].C);
+    longest_first(units, order);
+  } else if (order_mode == 0) {
     for (int k = 0; k < pmax; ++k)
       for (int i = 0; i < B->nstudies; ++i)
         if (ncols[i] > 0 && k < unit_rows(ts[i]))
@@ -1692,7 +2257,16 @@ cudaError_t batch_launch(TcBatchState* B, TcState* const* ts, cudaStream_t s, in
     if (B->S[i].ncols == 0) continue;
     TcState* t = ts[i];
     if ((e = cudaMemsetAsync(t->sched, 0, 128 + sizeof(int) * (size_t)t->P * B->S[i].C, s)) != cudaSuccess) return e;
-    if (t->center) {
+    if (t->mode == TILES_INVERSE) {
+      int8_t* sh = t->center ? t->shift : nullptr;
+      const int nc = B->S[i].ncols;
+      if (t->tf32)
+        cast_shift_kernel<true><<<(nc + 7) / 8, 256, 0, s>>>(B->X[i], B->ldx[i], t->n, t->n_pad, nc, sh, t->xc);
+      else
+        cast_shift_kernel<false><<<(nc + 7) / 8, 256, 0, s>>>(B->X[i], B->ldx[i], t->n, t->n_pad, nc, sh, t->xc);
+      ++*launches;
+      if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    } else if (t->center) {
       column_shift_kernel<<<(B->S[i].ncols + 7) / 8, 256, 0, s>>>(B->X[i], B->ldx[i], t->n, B->S[i].ncols, t->shift);
       ++*launches;
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
@@ -1705,6 +2279,7 @@ cudaError_t batch_launch(TcBatchState* B, TcState* const* ts, cudaStream_t s, in
     b.maps[i].BhiH = t->mBhiH;
     b.maps[i].BloH = t->mBloH;
     b.maps[i].X8H = B->mX8H[i];
+    b.maps[i].XcH = B->mXcH[i];
     b.maps[i].StX = t->mStX;
     b.maps[i].StHi = t->mStHi;
     b.maps[i].StLo = t->mStLo;
@@ -1755,6 +2330,7 @@ void destroy(TcState* t) {
   cudaFree(t->xt32);
   cudaFree(t->bhi);
   cudaFree(t->blo);
+  cudaFree(t->xc);
   cudaFree(t->sched);
   cudaFree(t->shift);
   cudaFree(t->order);

@@ -18,12 +18,16 @@ enum TileMode : int {
   TILES_SINGLE = 1,          // every tile on its own CTA
   TILES_PAIR_MULTICAST = 2,  // panels 2u, 2u+1 on a 2-CTA cluster, shared X~ loads by TMA multicast
   TILES_PAIR_MMA = 3,        // panels 2u, 2u+1: one M = 256 product on a 2-CTA cluster (cta_group::2)
+  TILES_INVERSE = 4,         // L^-1 formed at set-up; a block is the triangular product L^-1 X, row-panel
+                             // pairs as M = 256 products on 2-CTA clusters, no dependency between tiles
 };
 
 struct TcState;
 
 // Splits the FP64 block operator Aop into hi + lo pieces (BF16 or TF32) and
-// allocates the per-block buffers for up to bs SNP columns.  center: X_L's
+// allocates the per-block buffers for up to bs SNP columns.  TILES_INVERSE
+// instead forms L^-1 from Aop (the TF32x3 pair product on the identity,
+// 4096 columns per launch) and splits that.  center: X_L's
 // first column is the intercept, so every SNP column is solved shifted by the
 // integer nearest its mean (exact in BF16/TF32; the reductions map the results
 // back), which removes most of the cancellation between the SNP and the
@@ -36,7 +40,11 @@ cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_p
 
 // X~ = L^-1 X for ncols <= bs int8 columns (X 16-byte aligned, ldx % 16 == 0).
 // The FP32 result is left in xt_f32() with leading dimension xt_ld().
-cudaError_t run_block(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaStream_t s, int64_t* launches);
+// pieces: the hi/lo pieces of X~ are also stored (the substitution modes
+// always store them; the inverse form only when asked: the transpose solve
+// of the adjoint form reads them).
+cudaError_t run_block(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaStream_t s, int64_t* launches,
+                      bool pieces = false);
 
 // The batching form: one persistent launch over several studies (each with its
 // own operator and buffers; all BF16 or all TF32).  ts[i] solves ncols[i]

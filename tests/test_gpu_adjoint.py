@@ -89,14 +89,15 @@ def test_adjoint_paper_scale_n5000():
 SPLIT_ADJ_TOL = {"bf16x3": 1e-4, "tf32x3": 2e-5}
 
 
+@pytest.mark.parametrize("tiles", ["auto", "inverse"])
 @pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
 @pytest.mark.parametrize("n,p,m,h,sigma2", [(300, 4, 300, 0.5, 1.3), (1000, 3, 513, 0.7, 1.0)])
-def test_split_adjoint_matches_oracle(prec, n, p, m, h, sigma2):
+def test_split_adjoint_matches_oracle(prec, n, p, m, h, sigma2, tiles):
     s = gwas_synth.study(n, p, 2 * n, h, sigma2, seed=6)
     X = gwas_synth.dosages(n, 0, m, seed=6)
     L = oracle.potrf(oracle.form_m(s["Phi"], h, sigma2))
     c_ref, dh_ref, dy_ref = oracle.gls_grad(L, s["Phi"], h, sigma2, s["XL"], s["y"], X)
-    with gw.GLS(s["Phi"], s["XL"], s["y"], h, sigma2, bs=512, precision=prec) as g:
+    with gw.GLS(s["Phi"], s["XL"], s["y"], h, sigma2, bs=512, precision=prec, tiles=tiles) as g:
         dh, dy = np.zeros(1), np.zeros(n)
         chi2, dch = [], []
         for c0 in range(0, m, 512):
@@ -106,9 +107,9 @@ def test_split_adjoint_matches_oracle(prec, n, p, m, h, sigma2):
     chi2, dch = np.concatenate(chi2), np.concatenate(dch)
     errs = dict(chi2=_rel(chi2, c_ref), dchi2_dh=_rel(dch, dh_ref),
                 dh_sum=abs(dh[0] - dh_ref.sum()) / np.abs(dh_ref).sum(), dy=_rel(dy, dy_ref))
-    print(prec, n, "split adjoint", errs)
+    print(prec, tiles, n, "split adjoint", errs)
     tol = SPLIT_ADJ_TOL[prec]
-    assert all(v <= tol for v in errs.values()), (prec, errs)
+    assert all(v <= tol for v in errs.values()), (prec, tiles, errs)
 
 
 @pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])

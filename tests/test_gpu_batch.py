@@ -23,17 +23,18 @@ def _lib():
 NS = (300, 700, 129, 1000)  # uneven study sizes, one of them a single ragged panel + 1
 
 
-def _studies(prec, bs=512):
+def _studies(prec, bs=512, tiles="auto"):
     out = []
     for i, n in enumerate(NS):
         s = gwas_synth.study(n, 4, 2 * n, 0.5, 1.0, seed=30, study_id=i)
-        out.append((s, gw.GLS(s["Phi"], s["XL"], s["y"], 0.5, 1.0, precision=prec, bs=bs)))
+        out.append((s, gw.GLS(s["Phi"], s["XL"], s["y"], 0.5, 1.0, precision=prec, bs=bs, tiles=tiles)))
     return out
 
 
+@pytest.mark.parametrize("tiles", ["auto", "inverse"])
 @pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
-def test_batch_matches_single_and_oracle(prec):
-    studies = _studies(prec)
+def test_batch_matches_single_and_oracle(prec, tiles):
+    studies = _studies(prec, tiles=tiles)
     gls = [g for _, g in studies]
     try:
         with gw.GLSBatch(gls) as B:
@@ -49,7 +50,7 @@ def test_batch_matches_single_and_oracle(prec):
                     pick = np.arange(0, X.shape[1], 17)
                     r, se_o, _, st_o = oracle.gls(L, s["XL"], s["y"], X[:, pick])
                     e = compare(b[:, pick], se[:, pick], st[pick], r, se_o, st_o)
-                    assert e["b_norm"] <= 1e-5 and e["se_rel"] <= 1e-5, (prec, i, e)
+                    assert e["b_norm"] <= 1e-5 and e["se_rel"] <= 1e-5, (prec, tiles, i, e)
             # study-after-study order: the same results
             B.set_order(1)
             outs2 = B.solve(blocks)

@@ -146,7 +146,7 @@ TOL_SPLIT = 1e-5
 SPLITS = ("bf16x3", "tf32x3")
 # how the tensor-core solve's tiles map onto SMs: one per SM, row-panel pairs on
 # a 2-SM cluster with shared loads, row-panel pairs as one 256-row product
-TILES = ("single", "pair_multicast", "pair_mma")
+TILES = ("single", "pair_multicast", "pair_mma", "inverse")
 
 
 @pytest.mark.parametrize("tiles", TILES)
