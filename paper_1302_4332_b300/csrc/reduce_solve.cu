@@ -275,6 +275,107 @@ __global__ void __launch_bounds__(32 * SL) reduce_solve_f32_kernel(
   solve_store<QM>(sum, sc, q, col, b, se, status, shift ? (double)shift[col] : 0.0);
 }
 
+// FP32 X~, few covariates (q <= 7): a block takes RC SNP columns and splits
+// the rows into RW slices of whole 128-row chunks, one slice per warp.  Lane l
+// covers rows 4l .. 4l+3 of a chunk, so every float4 load of a column is one
+// coalesced 512-byte segment, and the four W32 rows it needs come from L1.
+// A chunk's products are summed in FP32, chunks are added with Kahan
+// compensation (FP32), a warp's lanes are added in FP64 by a butterfly and the
+// RW slice totals of a column in FP64, in a fixed order (deterministic).
+// Lanes past ncols re-read the last column and discard the result.
+constexpr int RC_RW = 4;  // row slices (warps) per block
+
+template <int QM, int WS, int RC>
+__global__ void __launch_bounds__(32 * RC_RW) reduce_solve_f32c_kernel(
+    const float* __restrict__ Xt, int64_t ldt, int rows, const float* __restrict__ W32,
+    const SolveConsts* __restrict__ sc, int q, int ncols, double* __restrict__ b, double* __restrict__ se,
+    int* __restrict__ status, const int8_t* __restrict__ shift) {
+  constexpr int NA = QM + 2, NW4 = WS / 4;
+  __shared__ double tot[RC_RW][RC][NA];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  const int nchunk = rows >> 7;
+  const int t0 = w * nchunk / RC_RW, t1 = (w + 1) * nchunk / RC_RW;
+  const float4* w4 = reinterpret_cast<const float4*>(W32);
+  const int col0 = blockIdx.x * RC;
+  const float4* xp[RC];
+#pragma unroll
+  for (int c = 0; c < RC; ++c) {
+    const int col = col0 + c < ncols ? col0 + c : ncols - 1;
+    xp[c] = reinterpret_cast<const float4*>(Xt + (int64_t)col * ldt) + lane;
+  }
+  float ks[RC][NA], kc[RC][NA];
+#pragma unroll
+  for (int c = 0; c < RC; ++c)
+#pragma unroll
+    for (int a = 0; a < NA; ++a) ks[c][a] = kc[c][a] = 0.f;
+  float4 xn[RC];
+  if (t0 < t1) {
+#pragma unroll
+    for (int c = 0; c < RC; ++c) xn[c] = __ldcs(xp[c] + t0 * 32);
+  }
+  for (int t = t0; t < t1; ++t) {
+    float4 xv[RC];
+#pragma unroll
+    for (int c = 0; c < RC; ++c) xv[c] = xn[c];
+    if (t + 1 < t1) {
+#pragma unroll
+      for (int c = 0; c < RC; ++c) xn[c] = __ldcs(xp[c] + (t + 1) * 32);
+    }
+    float4 wv[4][NW4];
+    const int64_t r0 = (int64_t)t * 128 + 4 * lane;
+#pragma unroll
+    for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+      for (int v4 = 0; v4 < NW4; ++v4) wv[rr][v4] = __ldg(w4 + (r0 + rr) * NW4 + v4);
+#pragma unroll
+    for (int c = 0; c < RC; ++c) {
+      const float xs[4] = {xv[c].x, xv[c].y, xv[c].z, xv[c].w};
+      float part[NA];
+#pragma unroll
+      for (int a = 0; a < NA; ++a) part[a] = 0.f;
+#pragma unroll
+      for (int rr = 0; rr < 4; ++rr) {
+#pragma unroll
+        for (int v4 = 0; v4 < NW4; ++v4) {
+          const float wr[4] = {wv[rr][v4].x, wv[rr][v4].y, wv[rr][v4].z, wv[rr][v4].w};
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (4 * v4 + e <= QM) part[4 * v4 + e] = fmaf(xs[rr], wr[e], part[4 * v4 + e]);
+        }
+        part[QM + 1] = fmaf(xs[rr], xs[rr], part[QM + 1]);
+      }
+#pragma unroll
+      for (int a = 0; a < NA; ++a) {
+        const float y = part[a] - kc[c][a];
+        const float s2 = ks[c][a] + y;
+        kc[c][a] = (s2 - ks[c][a]) - y;
+        ks[c][a] = s2;
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < RC; ++c)
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+      double v = (double)ks[c][a] - (double)kc[c][a];
+#pragma unroll
+      for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0) tot[w][c][a] = v;
+    }
+  __syncthreads();
+  if (threadIdx.x < RC && col0 + (int)threadIdx.x < ncols) {
+    const int c = threadIdx.x, col = col0 + c;
+    double sum[NA];
+#pragma unroll
+    for (int a = 0; a < NA; ++a) {
+      double v = tot[0][c][a];
+      for (int s2 = 1; s2 < RC_RW; ++s2) v += tot[s2][c][a];
+      sum[a] = v;
+    }
+    solve_store<QM>(sum, sc, q, col, b, se, status, shift ? (double)shift[col] : 0.0);
+  }
+}
+
 cudaError_t launch_reduce_solve(const void* Xt, XtKind kind, int64_t ldt, int rows, const double* W,
                                 int64_t ldw, const SolveConsts* sc, int q, int ncols, double* b, double* se,
                                 int* status, cudaStream_t s, const float* W32, const int8_t* shift) {
@@ -294,8 +395,14 @@ cudaError_t launch_reduce_solve(const void* Xt, XtKind kind, int64_t ldt, int ro
   const float* X = static_cast<const float*>(Xt);
   if ((rows % RS_RUN) || (ldt % RS_RUN)) return cudaErrorInvalidValue;  // whole 128-byte runs
   const int g32 = (ncols + 31) / 32;
-  if (q <= 3)
+  if (q <= 3 && rows % 128 == 0)
+    reduce_solve_f32c_kernel<3, 4, 4><<<(ncols + 3) / 4, 32 * RC_RW, 0, s>>>(X, ldt, rows, W32, sc, q, ncols, b, se,
+                                                                            status, shift);
+  else if (q <= 3)
     reduce_solve_f32_kernel<3, 4, 16><<<g32, 512, 0, s>>>(X, ldt, rows, W32, sc, q, ncols, b, se, status, shift);
+  else if (q <= 7 && rows % 128 == 0)
+    reduce_solve_f32c_kernel<7, 8, 2><<<(ncols + 1) / 2, 32 * RC_RW, 0, s>>>(X, ldt, rows, W32, sc, q, ncols, b, se,
+                                                                            status, shift);
   else if (q <= 7)
     reduce_solve_f32_kernel<7, 8, 16><<<g32, 512, 0, s>>>(X, ldt, rows, W32, sc, q, ncols, b, se, status, shift);
   else

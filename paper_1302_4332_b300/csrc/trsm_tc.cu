@@ -1,6 +1,10 @@
 // a6, split-precision modes: the blocked triangular solve X~ = L^-1 X on the
 // 5th-generation tensor cores (tcgen05), operands brought in by TMA,
-// accumulators in tensor memory (TMEM).
+// accumulators in tensor memory (TMEM).  This file holds the solve kernels --
+// the substitution (single CTAs, pair with multicast, pair product) and the
+// inverse form (the product with a precomputed L^-1, further below) -- and
+// their launch entries; per-study state, set-up and pre-passes are in
+// trsm_tc_host.cu.
 //
 // Same dataflow as the FP64 solve (Sec. 2.2's trsm over a block of SNP
 // columns): output tile (k, c) = rows k*TB.., SNP columns c*TN.. is
@@ -38,79 +42,13 @@
 #include <cuda.h>
 #include <cuda_bf16.h>
 
-#include <algorithm>
-#include <cstdio>
 #include <cstring>
-#include <vector>
 
 #include "tc_ptx.cuh"
-#include "trsm_tc.cuh"
+#include "trsm_tc_kernels.cuh"
 
 namespace gwas {
 namespace tc {
-
-constexpr int TN = 256;      // SNP columns per tile (MMA N)
-constexpr int STAGES = 4;    // operand stages in shared memory
-constexpr int TRING = 2;     // tile-id ring between the scheduler and the other roles
-constexpr int EPI_WARPS = 8;
-constexpr int THREADS = 32 * (4 + EPI_WARPS);
-constexpr int EPI_COLS = TN / 2;  // SNP columns per epilogue warp
-// K-blocks accumulated in one TMEM partial before the epilogue promotes it:
-// one (two measured no faster and raised the error of se up to tenfold); with
-// one, all tile modes give the same results bit for bit
-constexpr int PROMOTE = 1;
-
-template <bool TF32>
-struct Cfg {
-  static constexpr int ESZ = TF32 ? 4 : 2;       // bytes per operand element
-  static constexpr int KCH = 64 / ESZ;           // K per stage: one 64-byte swizzle row
-  static constexpr int KMMA = TF32 ? 8 : 16;     // K per tcgen05.mma
-  static constexpr int CPB = TB / KCH;           // stages per TB-wide block (4 or 8)
-  static constexpr int A_BYTES = TB * 64;        // one piece of A per stage: 8 KB
-  static constexpr int B_BYTES = TN * 64;        // one piece of B per stage: 16 KB
-  static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
-  static constexpr int X8_BYTES = TN * TB;       // int8 diagonal block: 32 KB
-  static constexpr int BAR_OFF = STAGES * STAGE_BYTES + X8_BYTES;
-  static constexpr int NBARS = 2 * STAGES + 4 + 3 * TRING + 3;
-  static constexpr int SMEM = 1024 + BAR_OFF + NBARS * 8 + TRING * 4 + 16;
-};
-
-constexpr int MAX_STUDIES = 8;  // studies in one batched launch
-
-// One study of a launch: its block geometry and buffers.
-struct TcStudy {
-  int P, C, ncols, n;
-  const int8_t* shift;  // per-SNP integer shift c_i (x' = x - c_i on rows < n), or null
-  int* flags;           // P x C finished-flags of this launch
-  float* xt32;          // FP32 X~ (n_pad x bs); the B "hi" piece in TF32 mode
-  void* bhi;            // BF16 mode: hi piece of X~
-  void* blo;            // lo piece of X~ (BF16 or FP32)
-  int64_t ldt;
-};
-
-// The tensor maps of one study: block operator hi/lo, X~ hi/lo, int8 block.
-struct TcMaps {
-  CUtensorMap Ahi, Alo, Bhi, Blo, X8;
-  CUtensorMap BhiH, BloH, X8H;  // half-width boxes (128 SNP columns) for the pair modes
-  CUtensorMap StX, StHi, StLo;  // pair product's epilogue stores: FP32 X~, hi piece (BF16), lo piece
-  CUtensorMap BinHi, BinLo;     // transpose solve: X~ pieces of the forward solve (its diagonal-block input)
-  CUtensorMap XcH;              // inverse form: the cast block x - c_i (BF16/FP32), half-width boxes
-};
-
-// A launch over one or several studies (the batching form): tiles of all
-// studies are handed out from one counter in the order of `order`, which
-// interleaves the studies row panel by row panel so that every study's
-// dependency chain advances while the SMs stay busy.
-struct TcBatch {
-  TcMaps maps[MAX_STUDIES];
-  TcStudy s0;                 // the study when there is only one (order == null)
-  const TcStudy* studies;     // device copies of the studies when order != null
-  const uint32_t* order;      // tile t -> (study << 28) | (k << 14) | c
-  int nstudies, ntiles;
-  int pieces;                 // inverse form: also store the hi/lo pieces of X~ (the adjoint's input)
-  unsigned int* counter;
-  DevStatus* st;
-};
 
 __device__ __forceinline__ void decode_tile(const TcBatch& b, int t, int& s, int& k, int& c, TcStudy& S) {
   if (b.order) {
@@ -618,10 +556,6 @@ __global__ void __launch_bounds__(THREADS, 1)
 // commits release both CTAs' stages and partials.
 namespace pair2 {
 constexpr int STAGES = 5;
-// SNP columns per 2 KB epilogue store chunk (32 rows): BF16 mode stores hi+lo
-// chunks (4 B per element), then FP32 chunks; TF32 mode FP32+lo chunks (8 B)
-template <bool TF32>
-constexpr int st_cols() { return TF32 ? 8 : 16; }
 
 template <bool TF32>
 struct Cfg {
@@ -1116,7 +1050,6 @@ __global__ void __launch_bounds__(THREADS, 1)
 // (cast_shift_kernel: x - c_i as BF16/FP32), so TMA alone fills every stage.
 namespace inv2 {
 constexpr int STAGES = 8;
-constexpr int ST_COLS = 16;  // SNP columns per epilogue store chunk (32 rows x 16 FP32 = 2 KB)
 
 template <bool TF32>
 struct Cfg {
@@ -1431,308 +1364,7 @@ __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_co
   if (warp == 2) ptx::tmem_dealloc_pair(tmem_base, 2 * TN);
 }
 
-// ------------------------------------------- per-SNP integer shift (pre-pass)
-// c_i = round(mean of the n dosages of SNP i), from an exact integer sum.
-__global__ void column_shift_kernel(const int8_t* __restrict__ X, int64_t ldx, int n, int ncols,
-                                    int8_t* __restrict__ shift) {
-  const int lane = threadIdx.x & 31;
-  const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (col >= ncols) return;
-  const int8_t* x = X + (int64_t)col * ldx;  // 16-byte aligned (checked by the caller)
-  int sum = 0;
-  const int n16 = n & ~15;
-  for (int r = lane * 16; r < n16; r += 32 * 16) {
-    const int4 v = __ldg(reinterpret_cast<const int4*>(x + r));
-    const int w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-    for (int i = 0; i < 4; ++i) sum += __dp4a(w[i], 0x01010101, 0);
-  }
-  for (int r = n16 + lane; r < n; r += 32) sum += x[r];
-#pragma unroll
-  for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-  if (lane == 0) {
-    const long long num = 2LL * sum + n;  // floor((2 sum + n) / 2n) = round-half-up of sum / n
-    const long long den = 2LL * n;
-    long long c = num >= 0 ? num / den : -((-num + den - 1) / den);
-    if (c > 127) c = 127;
-    if (c < -127) c = -127;
-    shift[col] = (int8_t)c;
-  }
-}
-
-// B operand of the inverse form: x'_ri = x_ri - c_i on rows < n and 0 on rows
-// n..n_pad-1, as BF16 (or FP32, read as TF32 by the tensor cores), column-major
-// with leading dimension n_pad.  c_i is computed here as in column_shift_kernel
-// when `shift` is given (and stored there), else 0.  One warp per SNP column.
-template <bool TF32>
-__global__ void cast_shift_kernel(const int8_t* __restrict__ X, int64_t ldx, int n, int n_pad, int ncols,
-                                  int8_t* __restrict__ shift, void* __restrict__ xc) {
-  const int lane = threadIdx.x & 31;
-  const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (col >= ncols) return;
-  const int8_t* x = X + (int64_t)col * ldx;  // 16-byte aligned (checked by the caller)
-  const int n16 = n & ~15;
-  int c = 0;
-  if (shift) {
-    int sum = 0;
-    for (int r = lane * 16; r < n16; r += 32 * 16) {
-      const int4 v = __ldg(reinterpret_cast<const int4*>(x + r));
-      const int w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-      for (int i = 0; i < 4; ++i) sum += __dp4a(w[i], 0x01010101, 0);
-    }
-    for (int r = n16 + lane; r < n; r += 32) sum += x[r];
-#pragma unroll
-    for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
-    const long long num = 2LL * sum + n, den = 2LL * n;
-    long long cc = num >= 0 ? num / den : -((-num + den - 1) / den);
-    cc = cc > 127 ? 127 : (cc < -127 ? -127 : cc);
-    c = (int)cc;
-    if (lane == 0) shift[col] = (int8_t)c;
-  }
-  for (int r = lane * 16; r < n_pad; r += 32 * 16) {  // n_pad is a multiple of 128
-    float f[16];
-    if (r + 16 <= n) {
-      const int4 v = __ldg(reinterpret_cast<const int4*>(x + r));
-      const int w[4] = {v.x, v.y, v.z, v.w};
-#pragma unroll
-      for (int i = 0; i < 16; ++i) f[i] = (float)((int)(int8_t)(w[i >> 2] >> (8 * (i & 3))) - c);
-    } else {
-#pragma unroll
-      for (int i = 0; i < 16; ++i) f[i] = (r + i < n) ? (float)((int)x[r + i] - c) : 0.f;
-    }
-    if constexpr (TF32) {
-      float4* o = reinterpret_cast<float4*>(static_cast<float*>(xc) + (int64_t)col * n_pad + r);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) o[i] = make_float4(f[4 * i], f[4 * i + 1], f[4 * i + 2], f[4 * i + 3]);
-    } else {
-      uint32_t wv[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const __nv_bfloat162 b2 = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
-        wv[i] = *reinterpret_cast<const uint32_t*>(&b2);
-      }
-      uint4* o = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(xc) + (int64_t)col * n_pad + r);
-      o[0] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
-      o[1] = make_uint4(wv[4], wv[5], wv[6], wv[7]);
-    }
-  }
-}
-
-// Columns c0.. c0+ncols-1 of the n_pad x n_pad identity as int8, column-major
-// with leading dimension n_pad (the right-hand side that turns the
-// substitution into L^-1).
-__global__ void identity_i8_kernel(int8_t* __restrict__ I8, int n_pad, int c0, int ncols) {
-  const int64_t total = (int64_t)n_pad * ncols;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int col = (int)(e / n_pad), row = (int)(e % n_pad);
-    I8[e] = row == c0 + col ? 1 : 0;
-  }
-}
-
-// Columns c0.. of L^-1, solved into `xt` (FP32, column-major, leading
-// dimension ldt), transposed into the row-major hi/lo pieces of the inverse
-// form's operator.  Entries above the diagonal and in the padding rows and
-// columns (index >= n) are set to zero.  32 x 32 tiles through shared memory.
-template <bool TF32>
-__global__ void linv_split_kernel(const float* __restrict__ xt, int64_t ldt, int n, int n_pad, int c0, int ncols,
-                                  void* __restrict__ hi, void* __restrict__ lo) {
-  __shared__ float tile[32][33];
-  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-  const int q0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int q = q0 + ty + 8 * i;
-    tile[ty + 8 * i][tx] = q < ncols ? xt[(int64_t)q * ldt + r0 + tx] : 0.f;
-  }
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int row = r0 + ty + 8 * i, q = q0 + tx, gcol = c0 + q;
-    if (q >= ncols) continue;
-    float v = tile[tx][ty + 8 * i];
-    if (row >= n || gcol >= n || gcol > row) v = 0.f;
-    const int64_t idx = (int64_t)row * n_pad + gcol;
-    if constexpr (TF32) {
-      uint32_t hb;
-      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(v));
-      const float h = __uint_as_float(hb);
-      static_cast<float*>(hi)[idx] = h;
-      static_cast<float*>(lo)[idx] = v - h;
-    } else {
-      const __nv_bfloat16 h = __float2bfloat16_rn(v);
-      static_cast<__nv_bfloat16*>(hi)[idx] = h;
-      static_cast<__nv_bfloat16*>(lo)[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
-    }
-  }
-}
-
-// ------------------------------------------------------------ set-up kernels
-// Pair form of the block operator (FP64, set-up of the pair product): the odd
-// row panels re-expressed through the even one before them, so neither row of
-// a pair needs the other's result.  With A = Aop (row panel k =
-// [A_k0 .. A_k,k-1 | A_kk = D_k^-1], row-major, leading dimension ld) and a
-// pair (2u, 2u+1):
-//   A'_{2u+1,j}  = A_{2u+1,j} + A_{2u+1,2u} A_{2u,j}   (j < 2u)
-//   A'_{2u+1,2u} = A_{2u+1,2u} A_{2u,2u}               (it multiplies the int8 X_{2u})
-// (A'_{2u+1,2u+1} = A_{2u+1,2u+1}), from substituting panel 2u's equation
-// X~_{2u} = sum_{j<2u} A_{2u,j} X~_j + A_{2u,2u} X_{2u} into panel 2u+1's.
-// `out` holds a copy of Aop; this kernel overwrites the odd rows' columns
-// < (2u+1)*TB.  Block (x, u): rows of panel 2u+1, columns 64x .. 64x+63.
-__global__ void __launch_bounds__(256) pair_rows_kernel(const double* __restrict__ A, double* __restrict__ out,
-                                                        int64_t ld, int P) {
-  const int k0 = 2 * blockIdx.y, k1 = k0 + 1;
-  const int c0 = blockIdx.x * 64;
-  if (k1 >= P || c0 >= k1 * TB) return;
-  constexpr int KC = 16;             // t per chunk
-  __shared__ double G[KC][TB + 1];   // A_{k1,k0}: [t][row] of the chunk
-  __shared__ double Bk[KC][64 + 1];  // panel k0, rows t of the chunk, columns c0 ..
-  const int tid = threadIdx.x, ty = tid >> 4, tx = tid & 15;
-  double acc[8][4];
-#pragma unroll
-  for (int i = 0; i < 8; ++i)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) acc[i][q] = 0.0;
-  for (int tc = 0; tc < TB; tc += KC) {
-    for (int e = tid; e < KC * TB; e += 256) {
-      const int r = e / KC, t = e % KC;
-      G[t][r] = A[(int64_t)(k1 * TB + r) * ld + k0 * TB + tc + t];
-    }
-    for (int e = tid; e < KC * 64; e += 256) {
-      const int t = e / 64, cc = e % 64;
-      Bk[t][cc] = A[(int64_t)(k0 * TB + tc + t) * ld + c0 + cc];
-    }
-    __syncthreads();
-#pragma unroll 4
-    for (int t = 0; t < KC; ++t)
-#pragma unroll
-      for (int i = 0; i < 8; ++i)
-#pragma unroll
-        for (int q = 0; q < 4; ++q) acc[i][q] = fma(G[t][ty * 8 + i], Bk[t][tx * 4 + q], acc[i][q]);
-    __syncthreads();
-  }
-#pragma unroll
-  for (int i = 0; i < 8; ++i)
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int col = c0 + tx * 4 + q;
-      if (col >= k1 * TB) continue;
-      const int64_t idx = (int64_t)(k1 * TB + ty * 8 + i) * ld + col;
-      // j < 2u: the original block plus the product; j = 2u: the product alone
-      out[idx] = (col < k0 * TB ? A[idx] : 0.0) + acc[i][q];
-    }
-}
-
-template <bool TF32>
-__global__ void split_aop_kernel(const double* __restrict__ A, int64_t count, void* __restrict__ hi,
-                                 void* __restrict__ lo) {
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < count; e += (int64_t)gridDim.x * blockDim.x) {
-    const double a = A[e];
-    if constexpr (TF32) {
-      uint32_t hb;
-      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"((float)a));
-      const float h = __uint_as_float(hb);
-      static_cast<float*>(hi)[e] = h;
-      static_cast<float*>(lo)[e] = (float)(a - (double)h);
-    } else {
-      const __nv_bfloat16 h = __double2bfloat16(a);
-      static_cast<__nv_bfloat16*>(hi)[e] = h;
-      static_cast<__nv_bfloat16*>(lo)[e] = __double2bfloat16(a - (double)__bfloat162float(h));
-    }
-  }
-}
-
-// ------------------------------------------------------------------- host side
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
-
-struct TcState {
-  bool tf32 = false;
-  int n = 0, n_pad = 0, bs = 0, P = 0, num_sms = 0;
-  void* ahi = nullptr;
-  void* alo = nullptr;
-  float* xt32 = nullptr;
-  void* bhi = nullptr;
-  void* blo = nullptr;
-  int64_t ldt = 0;
-  int8_t* shift = nullptr;        // per-SNP integer shift (bs)
-  bool center = false;            // X_L[:, 0] is the intercept: shift SNP columns
-  int strip_group = 0;            // tile order over groups of column strips (0: all)
-  TileMode mode = TILES_SINGLE;    // how tiles map onto CTAs
-  int max_clusters = 0;            // pair modes: co-resident 2-CTA clusters of the kernel
-  uint32_t* order = nullptr;      // device tile order when strip_group > 0
-  TcStudy* study_dev = nullptr;   // device copy of the study descriptor (grouped order)
-  int order_C = -1;               // the column-strip count the order was built for
-  unsigned int* sched = nullptr;  // [0] counter, flags from +32
-  size_t sched_bytes = 0;
-  DevStatus* st = nullptr;
-  CUtensorMap mAhi, mAlo, mBhi, mBlo, mBhiH, mBloH;
-  CUtensorMap mStX, mStHi, mStLo;  // pair product's epilogue stores
-  // transpose solve (the adjoint form): the transpose block operator split hi/lo,
-  // X^ = L^-T X~ in FP32 + pieces, and their maps
-  void* ahiT = nullptr;
-  void* aloT = nullptr;
-  float* xh32 = nullptr;
-  void* xhhi = nullptr;
-  void* xhlo = nullptr;
-  CUtensorMap mAhiT, mAloT, mBhiT, mBloT;
-  void* xc = nullptr;  // inverse form: the cast block x - c_i (n_pad x bs, BF16 or FP32)
-  EncodeTiledFn encode = nullptr;
-};
-
-// Row entries of the tile order: row panels, or row-panel pairs in pair mode.
-static int unit_rows(const TcState* t) { return t->mode == TILES_SINGLE ? t->P : (t->P + 1) / 2; }
-
-static cudaError_t get_encode(EncodeTiledFn* fn) {
-  void* f = nullptr;
-  cudaDriverEntryPointQueryResult q;
-  cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q);
-  if (e != cudaSuccess) return e;
-  if (q != cudaDriverEntryPointSuccess || !f) return cudaErrorNotSupported;
-  *fn = reinterpret_cast<EncodeTiledFn>(f);
-  return cudaSuccess;
-}
-
-// 2D tiled map: dims {inner, outer}, outer stride in bytes, box {bi, bo};
-// swz: the 64-byte swizzle of the operand stages (box inner extent 64 bytes).
-static cudaError_t make_map(EncodeTiledFn enc, CUtensorMap* m, CUtensorMapDataType dt, const void* base,
-                            uint64_t inner, uint64_t outer, uint64_t stride_bytes, uint32_t bi, uint32_t bo,
-                            bool swz) {
-  cuuint64_t dims[2] = {inner, outer};
-  cuuint64_t strides[1] = {stride_bytes};
-  cuuint32_t box[2] = {bi, bo};
-  cuuint32_t estr[2] = {1, 1};
-  CUresult r = enc(m, dt, 2, const_cast<void*>(base), dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                   swz ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_NONE,
-                   CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
-  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
-}
-
-template <bool TF32, bool PAIR>
-static cudaError_t set_smem_attr() {
-  return cudaFuncSetAttribute(trsm_tc_kernel<TF32, PAIR>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              Cfg<TF32>::SMEM);
-}
-
-template <bool TF32>
-static cudaError_t set_smem_attr_upper() {
-  return cudaFuncSetAttribute(trsm_tc_kernel<TF32, false, true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              Cfg<TF32>::SMEM);
-}
-
-template <bool TF32>
-static cudaError_t set_smem_attr_pair_mma() {
-  return cudaFuncSetAttribute(trsm_tc_pair_mma_kernel<TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              pair2::Cfg<TF32>::SMEM);
-}
-
-template <bool TF32>
-static cudaError_t set_smem_attr_inv() {
-  return cudaFuncSetAttribute(trsm_tc_inv_kernel<TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              inv2::Cfg<TF32>::SMEM);
-}
-
+// ------------------------------------------------------------ launch entries
 template <bool TF32>
 static cudaLaunchConfig_t pair_config(cudaLaunchAttribute* attr, int grid, cudaStream_t s, TileMode mode) {
   cudaLaunchConfig_t cfg;
@@ -1752,9 +1384,28 @@ static cudaLaunchConfig_t pair_config(cudaLaunchAttribute* attr, int grid, cudaS
   return cfg;
 }
 
-// Co-resident 2-CTA clusters of a pair kernel (one CTA per SM).
 template <bool TF32>
-static cudaError_t query_clusters(int num_sms, TileMode mode, int* out) {
+static cudaError_t set_attrs(bool clusters) {
+  constexpr cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(trsm_tc_kernel<TF32, false>, A, Cfg<TF32>::SMEM);
+  if (e != cudaSuccess || !clusters) return e;
+  if ((e = cudaFuncSetAttribute(trsm_tc_kernel<TF32, true>, A, Cfg<TF32>::SMEM)) != cudaSuccess) return e;
+  if ((e = cudaFuncSetAttribute(trsm_tc_pair_mma_kernel<TF32>, A, pair2::Cfg<TF32>::SMEM)) != cudaSuccess) return e;
+  return cudaFuncSetAttribute(trsm_tc_inv_kernel<TF32>, A, inv2::Cfg<TF32>::SMEM);
+}
+
+cudaError_t set_kernel_attrs(bool tf32, bool clusters) {
+  return tf32 ? set_attrs<true>(clusters) : set_attrs<false>(clusters);
+}
+
+cudaError_t set_upper_attr(bool tf32) {
+  constexpr cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  return tf32 ? cudaFuncSetAttribute(trsm_tc_kernel<true, false, true>, A, Cfg<true>::SMEM)
+              : cudaFuncSetAttribute(trsm_tc_kernel<false, false, true>, A, Cfg<false>::SMEM);
+}
+
+template <bool TF32>
+static cudaError_t clusters_of(int num_sms, TileMode mode, int* out) {
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t cfg = pair_config<TF32>(attr, 2 * (num_sms / 2), nullptr, mode);
   const void* fn = mode == TILES_INVERSE    ? (const void*)trsm_tc_inv_kernel<TF32>
@@ -1763,191 +1414,8 @@ static cudaError_t query_clusters(int num_sms, TileMode mode, int* out) {
   return cudaOccupancyMaxActiveClusters(out, fn, &cfg);
 }
 
-static cudaError_t build_inverse(TcState* t, const double* Aop, cudaStream_t s, int64_t* launches);
-
-cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_pad, int bs, int num_sms,
-                   bool center, DevStatus* st, cudaStream_t s, int64_t* launches, int strip_group, TileMode mode) {
-  *out = nullptr;
-  TcState* t = new TcState;
-  t->tf32 = (split == SPLIT_TF32);
-  t->n = n;
-  t->n_pad = n_pad;
-  t->bs = bs;
-  t->P = n_pad / TB;
-  t->num_sms = num_sms;
-  t->st = st;
-  t->ldt = n_pad;
-  const size_t esz = t->tf32 ? 4 : 2;
-  const size_t n2 = (size_t)n_pad * n_pad;
-  const int Cmax = (bs + TN - 1) / TN;
-  cudaError_t e;
-#define TRY(x)              \
-  do {                      \
-    e = (x);                \
-    if (e != cudaSuccess) { \
-      destroy(t);           \
-      return e;             \
-    }                       \
-  } while (0)
-  TRY(get_encode(&t->encode));
-  TRY(cudaMalloc(&t->ahi, esz * n2));
-  TRY(cudaMalloc(&t->alo, esz * n2));
-  TRY(cudaMalloc(&t->xt32, sizeof(float) * (size_t)n_pad * bs));
-  if (!t->tf32) TRY(cudaMalloc(&t->bhi, 2 * (size_t)n_pad * bs));
-  TRY(cudaMalloc(&t->blo, esz * (size_t)n_pad * bs));
-  TRY(cudaMalloc(&t->shift, (size_t)bs));
-  t->center = center;
-  t->strip_group = strip_group;
-  // measured at n = 1e4 with 4096-column blocks: the inverse form is the
-  // fastest for both splits (BF16: 0.51 ms a block against 0.93 ms for the
-  // pair product of the substitution)
-  if (mode == TILES_AUTO) mode = TILES_INVERSE;
-  t->mode = mode;
-  const bool inv = mode == TILES_INVERSE;
-  if (inv) TRY(cudaMalloc(&t->xc, esz * (size_t)n_pad * bs));
-  if (strip_group > 0 || inv) {
-    TRY(cudaMalloc(&t->order, sizeof(uint32_t) * (size_t)t->P * Cmax));
-    TRY(cudaMalloc(&t->study_dev, sizeof(TcStudy)));
-  }
-  t->sched_bytes = 128 + sizeof(int) * (size_t)t->P * Cmax;
-  TRY(cudaMalloc(&t->sched, t->sched_bytes));
-  TRY(cudaMemsetAsync(t->sched, 0, t->sched_bytes, s));
-  if (inv) {
-    TRY(build_inverse(t, Aop, s, launches));
-  } else {
-    // the pair product multiplies the pair form of the operator (pair_rows_kernel)
-    const double* src = Aop;
-    double* pair_form = nullptr;
-    if (mode == TILES_PAIR_MMA && t->P > 1) {
-      TRY(cudaMallocAsync(&pair_form, sizeof(double) * n2, s));
-      TRY(cudaMemcpyAsync(pair_form, Aop, sizeof(double) * n2, cudaMemcpyDeviceToDevice, s));
-      pair_rows_kernel<<<dim3(n_pad / 64, t->P / 2), 256, 0, s>>>(Aop, pair_form, n_pad, t->P);
-      ++*launches;
-      TRY(cudaGetLastError());
-      src = pair_form;
-    }
-    if (t->tf32)
-      split_aop_kernel<true><<<1184, 256, 0, s>>>(src, (int64_t)n2, t->ahi, t->alo);
-    else
-      split_aop_kernel<false><<<1184, 256, 0, s>>>(src, (int64_t)n2, t->ahi, t->alo);
-    ++*launches;
-    if (pair_form) TRY(cudaFreeAsync(pair_form, s));
-    TRY(cudaGetLastError());
-  }
-  const CUtensorMapDataType dt = t->tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-  const uint32_t kch = t->tf32 ? Cfg<true>::KCH : Cfg<false>::KCH;
-  TRY(make_map(t->encode, &t->mAhi, dt, t->ahi, n_pad, n_pad, esz * n_pad, kch, TB, true));
-  TRY(make_map(t->encode, &t->mAlo, dt, t->alo, n_pad, n_pad, esz * n_pad, kch, TB, true));
-  const void* bhi_base = t->tf32 ? static_cast<const void*>(t->xt32) : t->bhi;
-  TRY(make_map(t->encode, &t->mBhi, dt, bhi_base, n_pad, bs, esz * n_pad, kch, TN, true));
-  TRY(make_map(t->encode, &t->mBlo, dt, t->blo, n_pad, bs, esz * n_pad, kch, TN, true));
-  TRY(make_map(t->encode, &t->mBhiH, dt, bhi_base, n_pad, bs, esz * n_pad, kch, TN / 2, true));
-  TRY(make_map(t->encode, &t->mBloH, dt, t->blo, n_pad, bs, esz * n_pad, kch, TN / 2, true));
-  // epilogue store chunks: the pair product's (value + pieces in one 2 KB
-  // buffer), or the inverse form's (FP32 value alone, 16 columns)
-  const uint32_t stc = inv ? inv2::ST_COLS : (t->tf32 ? pair2::st_cols<true>() : pair2::st_cols<false>());
-  TRY(make_map(t->encode, &t->mStX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, t->xt32, n_pad, bs, 4 * (size_t)n_pad, 32, stc,
-               false));
-  memset(&t->mStHi, 0, sizeof t->mStHi);
-  if (!t->tf32) TRY(make_map(t->encode, &t->mStHi, dt, t->bhi, n_pad, bs, esz * n_pad, 32, stc, false));
-  TRY(make_map(t->encode, &t->mStLo, dt, t->blo, n_pad, bs, esz * n_pad, 32, stc, false));
-  TRY((t->tf32 ? set_smem_attr<true, false>() : set_smem_attr<false, false>()));
-  if (mode != TILES_SINGLE) {
-    TRY((t->tf32 ? set_smem_attr<true, true>() : set_smem_attr<false, true>()));
-    TRY((t->tf32 ? set_smem_attr_pair_mma<true>() : set_smem_attr_pair_mma<false>()));
-    TRY((t->tf32 ? set_smem_attr_inv<true>() : set_smem_attr_inv<false>()));
-    TRY((t->tf32 ? query_clusters<true>(num_sms, mode, &t->max_clusters)
-                 : query_clusters<false>(num_sms, mode, &t->max_clusters)));
-    if (t->max_clusters < 1) TRY(cudaErrorLaunchOutOfResources);
-  }
-#undef TRY
-  *out = t;
-  return cudaSuccess;
-}
-
-// Tile order of one study: row panel by row panel over groups of G column
-// strips (G <= 0 or G >= C: all strips), study index `si` in the top bits.
-static void append_study_order(std::vector<uint32_t>& order, int si, int P, int C, int G) {
-  if (G <= 0 || G > C) G = C;
-  for (int c0 = 0; c0 < C; c0 += G)
-    for (int k = 0; k < P; ++k)
-      for (int c = c0; c < c0 + G && c < C; ++c)
-        order.push_back(((uint32_t)si << 28) | ((uint32_t)k << 14) | (uint32_t)c);
-}
-
-// Inverse form: work units longest first (pair row r has 2r + 2 K-blocks, the
-// last row of an odd P 2r + 1), the studies' units merged by length; equal
-// lengths keep study, then strip order.
-struct UnitKey {
-  int len;
-  uint32_t code;
-};
-static void append_units(std::vector<UnitKey>& v, int si, int P, int C) {
-  for (int r = 0; r < (P + 1) / 2; ++r) {
-    const int len = 2 * r + (2 * r + 1 < P ? 2 : 1);
-    for (int c = 0; c < C; ++c) v.push_back({len, ((uint32_t)si << 28) | ((uint32_t)r << 14) | (uint32_t)c});
-  }
-}
-static void longest_first(std::vector<UnitKey>& v, std::vector<uint32_t>& order) {
-  std::stable_sort(v.begin(), v.end(), [](const UnitKey& a, const UnitKey& b) { return a.len > b.len; });
-  for (const UnitKey& u : v) order.push_back(u.code);
-}
-
-// Inverse form: the cast block's map (half-width boxes) and the cast
-// pre-pass (with the integer shifts when centering).
-static cudaError_t prepare_cast(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaStream_t s,
-                                int64_t* launches, CUtensorMap* mXcH) {
-  const size_t esz = t->tf32 ? 4 : 2;
-  const CUtensorMapDataType dt = t->tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-  const uint32_t kch = t->tf32 ? Cfg<true>::KCH : Cfg<false>::KCH;
-  cudaError_t e = make_map(t->encode, mXcH, dt, t->xc, (uint64_t)t->n_pad, (uint64_t)ncols, esz * t->n_pad, kch,
-                           TN / 2, true);
-  if (e != cudaSuccess) return e;
-  int8_t* sh = t->center ? t->shift : nullptr;
-  if (t->tf32)
-    cast_shift_kernel<true><<<(ncols + 7) / 8, 256, 0, s>>>(X, ldx, t->n, t->n_pad, ncols, sh, t->xc);
-  else
-    cast_shift_kernel<false><<<(ncols + 7) / 8, 256, 0, s>>>(X, ldx, t->n, t->n_pad, ncols, sh, t->xc);
-  ++*launches;
-  return cudaGetLastError();
-}
-
-// The study part of one launch: int8 map, cleared flags, integer shifts.
-static cudaError_t prepare_study(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaStream_t s,
-                                 int64_t* launches, TcStudy* S, CUtensorMap* mX8, CUtensorMap* mX8H,
-                                 CUtensorMap* mXcH) {
-  if (ncols > t->bs || (reinterpret_cast<uintptr_t>(X) & 15) || (ldx & 15) || ldx < t->n)
-    return cudaErrorInvalidValue;
-  cudaError_t e;
-  if (t->mode != TILES_INVERSE) {
-    e = make_map(t->encode, mX8, CU_TENSOR_MAP_DATA_TYPE_UINT8, X, (uint64_t)t->n, (uint64_t)ncols, (uint64_t)ldx, TB,
-                 TN, false);
-    if (e != cudaSuccess) return e;
-    e = make_map(t->encode, mX8H, CU_TENSOR_MAP_DATA_TYPE_UINT8, X, (uint64_t)t->n, (uint64_t)ncols, (uint64_t)ldx,
-                 TB, TN / 2, false);
-    if (e != cudaSuccess) return e;
-  }
-  const int C = (ncols + TN - 1) / TN;
-  e = cudaMemsetAsync(t->sched, 0, 128 + sizeof(int) * (size_t)t->P * C, s);
-  if (e != cudaSuccess) return e;
-  if (t->mode == TILES_INVERSE) {
-    if ((e = prepare_cast(t, X, ldx, ncols, s, launches, mXcH)) != cudaSuccess) return e;
-  } else if (t->center) {
-    column_shift_kernel<<<(ncols + 7) / 8, 256, 0, s>>>(X, ldx, t->n, ncols, t->shift);
-    ++*launches;
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  }
-  S->P = t->P;
-  S->C = C;
-  S->ncols = ncols;
-  S->n = t->n;
-  S->shift = t->center ? t->shift : nullptr;
-  S->flags = reinterpret_cast<int*>(t->sched + 32);
-  S->xt32 = t->xt32;
-  S->bhi = t->bhi;
-  S->blo = t->blo;
-  S->ldt = t->ldt;
-  return cudaSuccess;
+cudaError_t query_clusters(bool tf32, TileMode mode, int num_sms, int* out) {
+  return tf32 ? clusters_of<true>(num_sms, mode, out) : clusters_of<false>(num_sms, mode, out);
 }
 
 template <bool TF32>
@@ -1960,10 +1428,8 @@ static cudaError_t launch_pair(const TcBatch& b, int max_clusters, cudaStream_t 
   return cudaLaunchKernelEx(&cfg, trsm_tc_kernel<TF32, true>, b);
 }
 
-// b.ntiles work units: tiles, or (pair modes) row-panel pairs of a strip.
-static cudaError_t launch_kernel(bool tf32, TileMode mode, const TcBatch& b, int num_sms, int max_clusters,
-                                 cudaStream_t s, int64_t* launches) {
-  ++*launches;
+cudaError_t launch_solve(bool tf32, TileMode mode, const TcBatch& b, int num_sms, int max_clusters,
+                         cudaStream_t s) {
   if (mode != TILES_SINGLE) {
     const cudaError_t e =
         tf32 ? launch_pair<true>(b, max_clusters, s, mode) : launch_pair<false>(b, max_clusters, s, mode);
@@ -1977,365 +1443,12 @@ static cudaError_t launch_kernel(bool tf32, TileMode mode, const TcBatch& b, int
   return cudaGetLastError();
 }
 
-cudaError_t run_block(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaStream_t s, int64_t* launches,
-                      bool pieces) {
-  if (ncols <= 0) return cudaSuccess;
-  TcBatch b;
-  memset(&b, 0, sizeof b);
-  cudaError_t e =
-      prepare_study(t, X, ldx, ncols, s, launches, &b.s0, &b.maps[0].X8, &b.maps[0].X8H, &b.maps[0].XcH);
-  if (e != cudaSuccess) return e;
-  b.maps[0].Ahi = t->mAhi;
-  b.maps[0].Alo = t->mAlo;
-  b.maps[0].Bhi = t->mBhi;
-  b.maps[0].Blo = t->mBlo;
-  b.maps[0].BhiH = t->mBhiH;
-  b.maps[0].BloH = t->mBloH;
-  b.maps[0].StX = t->mStX;
-  b.maps[0].StHi = t->mStHi;
-  b.maps[0].StLo = t->mStLo;
-  b.nstudies = 1;
-  b.ntiles = unit_rows(t) * b.s0.C;
-  b.counter = t->sched;
-  b.st = t->st;
-  b.pieces = pieces ? 1 : 0;
-  const bool inv = t->mode == TILES_INVERSE;
-  if (inv || (t->strip_group > 0 && t->strip_group < b.s0.C)) {
-    if (t->order_C != b.s0.C) {  // (re)build the order for this strip count
-      std::vector<uint32_t> order;
-      if (inv) {
-        std::vector<UnitKey> units;
-        append_units(units, 0, t->P, b.s0.C);
-        longest_first(units, order);
-      } else {
-        append_study_order(order, 0, unit_rows(t), b.s0.C, t->strip_group);
-      }
-      if ((e = cudaMemcpyAsync(t->order, order.data(), sizeof(uint32_t) * order.size(), cudaMemcpyHostToDevice, s)) !=
-              cudaSuccess ||
-          (e = cudaStreamSynchronize(s)) != cudaSuccess)
-        return e;
-      t->order_C = b.s0.C;
-    }
-    // the grouped order reads the study descriptor from device memory
-    if ((e = cudaMemcpyAsync(t->study_dev, &b.s0, sizeof(TcStudy), cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
-    b.order = t->order;
-    b.studies = t->study_dev;
-  }
-  return launch_kernel(t->tf32, t->mode, b, t->num_sms, t->max_clusters, s, launches);
-}
-
-// Inverse form set-up: L^-1 = the substitution applied to the identity, on
-// the tensor cores in TF32x3 (the pair product over Aop, 4096 identity
-// columns per launch, no centering), then transposed and split into the
-// row-major hi/lo pieces of t.  Synchronizes the stream.
-static cudaError_t build_inverse(TcState* t, const double* Aop, cudaStream_t s, int64_t* launches) {
-  const int np = t->n_pad;
-  const int bsi = np < 4096 ? np : 4096;
-  TcState* g = nullptr;
-  cudaError_t e = create(&g, SPLIT_TF32, Aop, t->n, np, bsi, t->num_sms, false, t->st, s, launches, 0, TILES_PAIR_MMA);
-  if (e != cudaSuccess) return e;
-  int8_t* eye = nullptr;
-  e = cudaMalloc(&eye, (size_t)np * bsi);
-  for (int c0 = 0; e == cudaSuccess && c0 < np; c0 += bsi) {
-    const int nc = np - c0 < bsi ? np - c0 : bsi;
-    identity_i8_kernel<<<1184, 256, 0, s>>>(eye, np, c0, nc);
-    ++*launches;
-    if ((e = cudaGetLastError()) != cudaSuccess) break;
-    if ((e = run_block(g, eye, np, nc, s, launches)) != cudaSuccess) break;
-    const dim3 grid((nc + 31) / 32, np / 32);
-    if (t->tf32)
-      linv_split_kernel<true><<<grid, dim3(32, 8), 0, s>>>(g->xt32, g->ldt, t->n, np, c0, nc, t->ahi, t->alo);
-    else
-      linv_split_kernel<false><<<grid, dim3(32, 8), 0, s>>>(g->xt32, g->ldt, t->n, np, c0, nc, t->ahi, t->alo);
-    ++*launches;
-    e = cudaGetLastError();
-  }
-  const cudaError_t es = cudaStreamSynchronize(s);  // before g's buffers go
-  if (e == cudaSuccess) e = es;
-  if (e == cudaSuccess && t->st) {
-    DevStatus h;
-    if ((e = cudaMemcpy(&h, t->st, sizeof h, cudaMemcpyDeviceToHost)) == cudaSuccess && h.err != DEV_OK)
-      e = cudaErrorLaunchTimeout;  // a bounded wait of the solve expired
-  }
-  cudaFree(eye);
-  destroy(g);
-  return e;
-}
-
-// ------------------------------------------------------ transpose solve (adjoint)
-cudaError_t ensure_transpose(TcState* t, const double* AopT, cudaStream_t s, int64_t* launches) {
-  if (t->ahiT) return cudaSuccess;
-  const size_t esz = t->tf32 ? 4 : 2;
-  const size_t np = (size_t)t->n_pad, n2 = np * np;
-  cudaError_t e;
-  if ((e = cudaMalloc(&t->ahiT, esz * n2)) != cudaSuccess || (e = cudaMalloc(&t->aloT, esz * n2)) != cudaSuccess ||
-      (e = cudaMalloc(&t->xh32, sizeof(float) * np * t->bs)) != cudaSuccess ||
-      (!t->tf32 && (e = cudaMalloc(&t->xhhi, 2 * np * t->bs)) != cudaSuccess) ||
-      (e = cudaMalloc(&t->xhlo, esz * np * t->bs)) != cudaSuccess)
-    return e;
-  if (t->tf32)
-    split_aop_kernel<true><<<1184, 256, 0, s>>>(AopT, (int64_t)n2, t->ahiT, t->aloT);
-  else
-    split_aop_kernel<false><<<1184, 256, 0, s>>>(AopT, (int64_t)n2, t->ahiT, t->aloT);
-  ++*launches;
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const CUtensorMapDataType dt = t->tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-  const uint32_t kch = t->tf32 ? Cfg<true>::KCH : Cfg<false>::KCH;
-  const void* bhi = t->tf32 ? static_cast<const void*>(t->xh32) : t->xhhi;
-  if ((e = make_map(t->encode, &t->mAhiT, dt, t->ahiT, np, np, esz * np, kch, TB, true)) != cudaSuccess ||
-      (e = make_map(t->encode, &t->mAloT, dt, t->aloT, np, np, esz * np, kch, TB, true)) != cudaSuccess ||
-      (e = make_map(t->encode, &t->mBhiT, dt, bhi, np, t->bs, esz * np, kch, TN, true)) != cudaSuccess ||
-      (e = make_map(t->encode, &t->mBloT, dt, t->xhlo, np, t->bs, esz * np, kch, TN, true)) != cudaSuccess)
-    return e;
-  return t->tf32 ? set_smem_attr_upper<true>() : set_smem_attr_upper<false>();
-}
-
-cudaError_t run_transpose(TcState* t, int ncols, cudaStream_t s, int64_t* launches) {
-  if (ncols <= 0) return cudaSuccess;
-  if (!t->ahiT || ncols > t->bs) return cudaErrorInvalidValue;
-  TcBatch b;
-  memset(&b, 0, sizeof b);
-  const int C = (ncols + TN - 1) / TN;
-  cudaError_t e = cudaMemsetAsync(t->sched, 0, 128 + sizeof(int) * (size_t)t->P * C, s);
-  if (e != cudaSuccess) return e;
-  TcStudy& S = b.s0;
-  S.P = t->P;
-  S.C = C;
-  S.ncols = ncols;
-  S.n = t->n;
-  S.shift = nullptr;
-  S.flags = reinterpret_cast<int*>(t->sched + 32);
-  S.xt32 = t->xh32;
-  S.bhi = t->xhhi;
-  S.blo = t->xhlo;
-  S.ldt = t->ldt;
-  b.maps[0].Ahi = t->mAhiT;
-  b.maps[0].Alo = t->mAloT;
-  b.maps[0].Bhi = t->mBhiT;
-  b.maps[0].Blo = t->mBloT;
-  b.maps[0].BinHi = t->mBhi;  // the forward solve's X~ pieces
-  b.maps[0].BinLo = t->mBlo;
-  b.nstudies = 1;
-  b.ntiles = t->P * C;
-  b.counter = t->sched;
-  b.st = t->st;
-  const int grid = b.ntiles < t->num_sms ? b.ntiles : t->num_sms;
-  if (t->tf32)
+cudaError_t launch_upper(bool tf32, const TcBatch& b, int grid, cudaStream_t s) {
+  if (tf32)
     trsm_tc_kernel<true, false, true><<<grid, THREADS, Cfg<true>::SMEM, s>>>(b);
   else
     trsm_tc_kernel<false, false, true><<<grid, THREADS, Cfg<false>::SMEM, s>>>(b);
-  ++*launches;
   return cudaGetLastError();
-}
-
-const float* xhat_f32(const TcState* t) { return t->xh32; }
-
-// ------------------------------------------------------------- batched launch
-struct TcBatchState {
-  int nstudies = 0;
-  int ntiles = 0;
-  TcStudy S[MAX_STUDIES];
-  CUtensorMap mX8[MAX_STUDIES], mX8H[MAX_STUDIES], mXcH[MAX_STUDIES] = {};
-  const int8_t* X[MAX_STUDIES];
-  int64_t ldx[MAX_STUDIES];
-  bool tf32 = false;
-  TileMode mode = TILES_SINGLE;
-  int num_sms = 0, max_clusters = 0;
-  TcStudy* d_studies = nullptr;  // device copies
-  uint32_t* d_order = nullptr;
-  unsigned int* d_counter = nullptr;
-  size_t order_cap = 0;
-  DevStatus* st = nullptr;
-};
-
-cudaError_t batch_create(TcBatchState** out, TcState* const* ts, int nstudies) {
-  *out = nullptr;
-  if (nstudies < 1 || nstudies > MAX_STUDIES) return cudaErrorInvalidValue;
-  for (int i = 1; i < nstudies; ++i)
-    if (ts[i]->tf32 != ts[0]->tf32 || ts[i]->mode != ts[0]->mode) return cudaErrorInvalidValue;
-  TcBatchState* B = new TcBatchState;
-  B->nstudies = nstudies;
-  B->tf32 = ts[0]->tf32;
-  B->mode = ts[0]->mode;
-  B->num_sms = ts[0]->num_sms;
-  B->max_clusters = ts[0]->max_clusters;
-  B->st = ts[0]->st;
-  size_t cap = 0;
-  for (int i = 0; i < nstudies; ++i) cap += (size_t)unit_rows(ts[i]) * ((ts[i]->bs + TN - 1) / TN);
-  B->order_cap = cap;
-  cudaError_t e;
-  if ((e = cudaMalloc(&B->d_studies, sizeof(TcStudy) * MAX_STUDIES)) != cudaSuccess ||
-      (e = cudaMalloc(&B->d_order, sizeof(uint32_t) * cap)) != cudaSuccess ||
-      (e = cudaMalloc(&B->d_counter, 128)) != cudaSuccess) {
-    batch_destroy(B);
-    return e;
-  }
-  *out = B;
-  return cudaSuccess;
-}
-
-// Fixes the launch geometry: the study descriptors and the tile order
-// (order_mode 0: row panel by row panel across the studies; 1: study after
-// study).  Synchronizes the stream (host copies).  The X pointers are the
-// device blocks later launches will read.
-cudaError_t batch_plan(TcBatchState* B, TcState* const* ts, const int8_t* const* X, const int64_t* ldx,
-                       const int* ncols, int order_mode, cudaStream_t s, int strip_group) {
-  TcStudy S[MAX_STUDIES];
-  memset(S, 0, sizeof S);
-  int pmax = 0, total = 0;
-  for (int i = 0; i < B->nstudies; ++i) {
-    TcState* t = ts[i];
-    if (ncols[i] < 0 || ncols[i] > t->bs) return cudaErrorInvalidValue;
-    if (ncols[i] == 0) continue;
-    if ((reinterpret_cast<uintptr_t>(X[i]) & 15) || (ldx[i] & 15) || ldx[i] < t->n) return cudaErrorInvalidValue;
-    cudaError_t e = make_map(t->encode, &B->mX8[i], CU_TENSOR_MAP_DATA_TYPE_UINT8, X[i], (uint64_t)t->n,
-                             (uint64_t)ncols[i], (uint64_t)ldx[i], TB, TN, false);
-    if (e != cudaSuccess) return e;
-    e = make_map(t->encode, &B->mX8H[i], CU_TENSOR_MAP_DATA_TYPE_UINT8, X[i], (uint64_t)t->n, (uint64_t)ncols[i],
-                 (uint64_t)ldx[i], TB, TN / 2, false);
-    if (e != cudaSuccess) return e;
-    if (t->mode == TILES_INVERSE) {
-      const size_t esz = t->tf32 ? 4 : 2;
-      e = make_map(t->encode, &B->mXcH[i],
-                   t->tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, t->xc,
-                   (uint64_t)t->n_pad, (uint64_t)ncols[i], esz * t->n_pad, t->tf32 ? Cfg<true>::KCH : Cfg<false>::KCH,
-                   TN / 2, true);
-      if (e != cudaSuccess) return e;
-    }
-    S[i].P = t->P;
-    S[i].C = (ncols[i] + TN - 1) / TN;
-    S[i].ncols = ncols[i];
-    S[i].n = t->n;
-    S[i].shift = t->center ? t->shift : nullptr;
-    S[i].flags = reinterpret_cast<int*>(t->sched + 32);
-    S[i].xt32 = t->xt32;
-    S[i].bhi = t->bhi;
-    S[i].blo = t->blo;
-    S[i].ldt = t->ldt;
-    pmax = unit_rows(t) > pmax ? unit_rows(t) : pmax;
-    total += unit_rows(t) * S[i].C;
-  }
-  std::vector<uint32_t> order;
-  order.reserve(total);
-  if (B->mode == TILES_INVERSE) {  // no dependencies: longest units first over all studies
-    std::vector<UnitKey> units;
-    for (int i = 0; i < B->nstudies; ++i)
-      if (ncols[i] > 0) append_units(units, i, ts[i]->P, S[i].C);
-    longest_first(units, order);
-  } else if (order_mode == 0) {
-    for (int k = 0; k < pmax; ++k)
-      for (int i = 0; i < B->nstudies; ++i)
-        if (ncols[i] > 0 && k < unit_rows(ts[i]))
-          for (int c = 0; c < S[i].C; ++c) order.push_back(((uint32_t)i << 28) | ((uint32_t)k << 14) | (uint32_t)c);
-  } else {
-    for (int i = 0; i < B->nstudies; ++i)
-      if (ncols[i] > 0) append_study_order(order, i, unit_rows(ts[i]), S[i].C, strip_group);
-  }
-  cudaError_t e;
-  if (total > 0 &&
-      (e = cudaMemcpyAsync(B->d_order, order.data(), sizeof(uint32_t) * order.size(), cudaMemcpyHostToDevice, s)) !=
-          cudaSuccess)
-    return e;
-  if ((e = cudaMemcpyAsync(B->d_studies, S, sizeof(TcStudy) * MAX_STUDIES, cudaMemcpyHostToDevice, s)) != cudaSuccess)
-    return e;
-  if ((e = cudaStreamSynchronize(s)) != cudaSuccess) return e;
-  memcpy(B->S, S, sizeof S);
-  memcpy(B->X, X, sizeof(const int8_t*) * B->nstudies);
-  memcpy(B->ldx, ldx, sizeof(int64_t) * B->nstudies);
-  B->ntiles = total;
-  return cudaSuccess;
-}
-
-// One planned launch: clear flags and counter, shift pre-passes, the batched
-// kernel.  Only stream-ordered work: can be captured into a CUDA graph.
-cudaError_t batch_launch(TcBatchState* B, TcState* const* ts, cudaStream_t s, int64_t* launches) {
-  if (B->ntiles == 0) return cudaSuccess;
-  TcBatch b;
-  memset(&b, 0, sizeof b);
-  cudaError_t e;
-  for (int i = 0; i < B->nstudies; ++i) {
-    if (B->S[i].ncols == 0) continue;
-    TcState* t = ts[i];
-    if ((e = cudaMemsetAsync(t->sched, 0, 128 + sizeof(int) * (size_t)t->P * B->S[i].C, s)) != cudaSuccess) return e;
-    if (t->mode == TILES_INVERSE) {
-      int8_t* sh = t->center ? t->shift : nullptr;
-      const int nc = B->S[i].ncols;
-      if (t->tf32)
-        cast_shift_kernel<true><<<(nc + 7) / 8, 256, 0, s>>>(B->X[i], B->ldx[i], t->n, t->n_pad, nc, sh, t->xc);
-      else
-        cast_shift_kernel<false><<<(nc + 7) / 8, 256, 0, s>>>(B->X[i], B->ldx[i], t->n, t->n_pad, nc, sh, t->xc);
-      ++*launches;
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    } else if (t->center) {
-      column_shift_kernel<<<(B->S[i].ncols + 7) / 8, 256, 0, s>>>(B->X[i], B->ldx[i], t->n, B->S[i].ncols, t->shift);
-      ++*launches;
-      if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    }
-    b.maps[i].Ahi = t->mAhi;
-    b.maps[i].Alo = t->mAlo;
-    b.maps[i].Bhi = t->mBhi;
-    b.maps[i].Blo = t->mBlo;
-    b.maps[i].X8 = B->mX8[i];
-    b.maps[i].BhiH = t->mBhiH;
-    b.maps[i].BloH = t->mBloH;
-    b.maps[i].X8H = B->mX8H[i];
-    b.maps[i].XcH = B->mXcH[i];
-    b.maps[i].StX = t->mStX;
-    b.maps[i].StHi = t->mStHi;
-    b.maps[i].StLo = t->mStLo;
-  }
-  if ((e = cudaMemsetAsync(B->d_counter, 0, 128, s)) != cudaSuccess) return e;
-  b.studies = B->d_studies;
-  b.order = B->d_order;
-  b.nstudies = B->nstudies;
-  b.ntiles = B->ntiles;
-  b.counter = B->d_counter;
-  b.st = B->st;
-  return launch_kernel(B->tf32, B->mode, b, B->num_sms, B->max_clusters, s, launches);
-}
-
-void batch_destroy(TcBatchState* B) {
-  if (!B) return;
-  cudaFree(B->d_studies);
-  cudaFree(B->d_order);
-  cudaFree(B->d_counter);
-  delete B;
-}
-
-const float* xt_f32(const TcState* t) { return t->xt32; }
-const int8_t* shift_of(const TcState* t) { return t->center ? t->shift : nullptr; }
-int64_t xt_ld(const TcState* t) { return t->ldt; }
-TileMode tile_mode(const TcState* t) { return t->mode; }
-
-void launch_shape(const TcState* t, int* ctas, int* cluster_size) {
-  const int units = unit_rows(t) * ((t->bs + TN - 1) / TN);
-  if (t->mode == TILES_SINGLE) {
-    *ctas = units < t->num_sms ? units : t->num_sms;
-    *cluster_size = 1;
-  } else {
-    *ctas = 2 * (units < t->max_clusters ? units : t->max_clusters);
-    *cluster_size = 2;
-  }
-}
-
-void destroy(TcState* t) {
-  if (!t) return;
-  cudaFree(t->ahiT);
-  cudaFree(t->aloT);
-  cudaFree(t->xh32);
-  cudaFree(t->xhhi);
-  cudaFree(t->xhlo);
-  cudaFree(t->ahi);
-  cudaFree(t->alo);
-  cudaFree(t->xt32);
-  cudaFree(t->bhi);
-  cudaFree(t->blo);
-  cudaFree(t->xc);
-  cudaFree(t->sched);
-  cudaFree(t->shift);
-  cudaFree(t->order);
-  cudaFree(t->study_dev);
-  delete t;
 }
 
 }  // namespace tc

@@ -1,0 +1,105 @@
+// The split-precision solve's kernels (trsm_tc.cu) and their host side
+// (trsm_tc_host.cu) share this: tile geometry, the launch parameter block
+// (one or several studies' tensor maps and buffers) and the kernels' launch
+// entry points.
+#pragma once
+
+#include <cuda.h>
+
+#include <cstdint>
+
+#include "trsm_tc.cuh"
+
+namespace gwas {
+namespace tc {
+
+constexpr int TN = 256;      // SNP columns per tile (MMA N)
+constexpr int STAGES = 4;    // operand stages in shared memory
+constexpr int TRING = 2;     // tile-id ring between the scheduler and the other roles
+constexpr int EPI_WARPS = 8;
+constexpr int THREADS = 32 * (4 + EPI_WARPS);
+constexpr int EPI_COLS = TN / 2;  // SNP columns per epilogue warp
+// K-blocks accumulated in one TMEM partial before the epilogue promotes it:
+// one (two measured no faster and raised the error of se up to tenfold); with
+// one, all tile modes give the same results bit for bit
+constexpr int PROMOTE = 1;
+
+template <bool TF32>
+struct Cfg {
+  static constexpr int ESZ = TF32 ? 4 : 2;       // bytes per operand element
+  static constexpr int KCH = 64 / ESZ;           // K per stage: one 64-byte swizzle row
+  static constexpr int KMMA = TF32 ? 8 : 16;     // K per tcgen05.mma
+  static constexpr int CPB = TB / KCH;           // stages per TB-wide block (4 or 8)
+  static constexpr int A_BYTES = TB * 64;        // one piece of A per stage: 8 KB
+  static constexpr int B_BYTES = TN * 64;        // one piece of B per stage: 16 KB
+  static constexpr int STAGE_BYTES = 2 * A_BYTES + 2 * B_BYTES;
+  static constexpr int X8_BYTES = TN * TB;       // int8 diagonal block: 32 KB
+  static constexpr int BAR_OFF = STAGES * STAGE_BYTES + X8_BYTES;
+  static constexpr int NBARS = 2 * STAGES + 4 + 3 * TRING + 3;
+  static constexpr int SMEM = 1024 + BAR_OFF + NBARS * 8 + TRING * 4 + 16;
+};
+
+constexpr int MAX_STUDIES = 8;  // studies in one batched launch
+
+// One study of a launch: its block geometry and buffers.
+struct TcStudy {
+  int P, C, ncols, n;
+  const int8_t* shift;  // per-SNP integer shift c_i (x' = x - c_i on rows < n), or null
+  int* flags;           // P x C finished-flags of this launch
+  float* xt32;          // FP32 X~ (n_pad x bs); the B "hi" piece in TF32 mode
+  void* bhi;            // BF16 mode: hi piece of X~
+  void* blo;            // lo piece of X~ (BF16 or FP32)
+  int64_t ldt;
+};
+
+// The tensor maps of one study: block operator hi/lo, X~ hi/lo, int8 block.
+struct TcMaps {
+  CUtensorMap Ahi, Alo, Bhi, Blo, X8;
+  CUtensorMap BhiH, BloH, X8H;  // half-width boxes (128 SNP columns) for the pair modes
+  CUtensorMap StX, StHi, StLo;  // pair product's epilogue stores: FP32 X~, hi piece (BF16), lo piece
+  CUtensorMap BinHi, BinLo;     // transpose solve: X~ pieces of the forward solve (its diagonal-block input)
+  CUtensorMap XcH;              // inverse form: the cast block x - c_i (BF16/FP32), half-width boxes
+};
+
+// A launch over one or several studies (the batching form): tiles of all
+// studies are handed out from one counter in the order of `order`, which
+// interleaves the studies row panel by row panel so that every study's
+// dependency chain advances while the SMs stay busy.
+struct TcBatch {
+  TcMaps maps[MAX_STUDIES];
+  TcStudy s0;                 // the study when there is only one (order == null)
+  const TcStudy* studies;     // device copies of the studies when order != null
+  const uint32_t* order;      // tile t -> (study << 28) | (k << 14) | c
+  int nstudies, ntiles;
+  int pieces;                 // inverse form: also store the hi/lo pieces of X~ (the adjoint's input)
+  unsigned int* counter;
+  DevStatus* st;
+};
+
+namespace pair2 {
+// SNP columns per 2 KB epilogue store chunk of the pair product (32 rows):
+// BF16 mode stores hi+lo chunks (4 B per element), then FP32 chunks; TF32
+// mode FP32+lo chunks (8 B)
+template <bool TF32>
+constexpr int st_cols() { return TF32 ? 8 : 16; }
+}  // namespace pair2
+
+namespace inv2 {
+constexpr int ST_COLS = 16;  // SNP columns per inverse-form store chunk (32 rows x 16 FP32 = 2 KB)
+}  // namespace inv2
+
+// Launch entry points of the kernels (trsm_tc.cu).
+// Opt-in shared memory of the forward kernels (clusters: also the pair and
+// inverse-form kernels) and of the transpose solve.
+cudaError_t set_kernel_attrs(bool tf32, bool clusters);
+cudaError_t set_upper_attr(bool tf32);
+// Co-resident 2-CTA clusters of a cluster-mode kernel (one CTA per SM).
+cudaError_t query_clusters(bool tf32, TileMode mode, int num_sms, int* out);
+// One launch over b.ntiles work units (tiles, or row-panel pairs of a strip).
+cudaError_t launch_solve(bool tf32, TileMode mode, const TcBatch& b, int num_sms, int max_clusters,
+                         cudaStream_t s);
+// The transpose solve of the adjoint form (single CTAs, grid CTAs).
+cudaError_t launch_upper(bool tf32, const TcBatch& b, int grid, cudaStream_t s);
+
+}  // namespace tc
+}  // namespace gwas
