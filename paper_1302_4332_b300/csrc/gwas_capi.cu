@@ -238,7 +238,8 @@ int run_block(gwas_ctx* ctx, const void* X, bool int8_input, int64_t ldx, int nc
   {
     StageMark m(ctx, GWAS_STAGE_REDUCE, ctx->stream);
     CK(launch_reduce_solve(tc::xt_f32(ctx->tcs), XT_F32, tc::xt_ld(ctx->tcs), ctx->n_pad, ctx->W, ctx->n_pad,
-                           ctx->sc, ctx->q, ncols, b, se, status, ctx->stream, ctx->W32, tc::shift_of(ctx->tcs)));
+                           ctx->sc, ctx->q, ncols, b, se, status, ctx->stream, ctx->W32, tc::shift_of(ctx->tcs),
+                           ctx->st, ctx->num_sms, tc::xt_reduce_map(ctx->tcs)));
   }
   ctx->launches += 1;
   return GWAS_OK;
@@ -481,6 +482,7 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
                     cudaGetErrorString(e));
       CK(dmalloc(&ctx->W32, sizeof(float) * np * w32_stride(ctx->q)));
       CK(launch_make_w32(ctx->W, ctx->n_pad, ctx->n_pad, ctx->q, ctx->W32, ctx->stream));
+      CK(prepare_reduce_solve());
       ctx->launches += 1;
     }
 
@@ -985,7 +987,8 @@ int batch_capture(gwas_batch* B, const std::vector<int>& cols, int order, int gr
     gwas_ctx* c = B->ctx[i];
     if (cols[i] == 0) continue;
     e = launch_reduce_solve(tc::xt_f32(c->tcs), XT_F32, tc::xt_ld(c->tcs), c->n_pad, c->W, c->n_pad, c->sc, c->q,
-                            cols[i], B->d_b[i], B->d_se[i], B->d_st[i], B->stream, c->W32, tc::shift_of(c->tcs));
+                            cols[i], B->d_b[i], B->d_se[i], B->d_st[i], B->stream, c->W32, tc::shift_of(c->tcs),
+                            c->st, c->num_sms, tc::xt_reduce_map(c->tcs));
     ++nl;
   }
   cudaGraph_t g = nullptr;

@@ -15,6 +15,7 @@
 //   Xt    n_pad x bs: X~_b = L^-1 X_b for the current block of SNPs.
 #pragma once
 
+#include <cuda.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -124,7 +125,15 @@ enum XtKind : int { XT_F64 = 0, XT_F32 = 1 };
 cudaError_t launch_reduce_solve(const void* Xt, XtKind kind, int64_t ldt, int rows, const double* W,
                                 int64_t ldw, const SolveConsts* sc, int q, int ncols, double* b, double* se,
                                 int* status, cudaStream_t s, const float* W32 = nullptr,
-                                const int8_t* shift = nullptr);
+                                const int8_t* shift = nullptr, DevStatus* st = nullptr, int num_sms = 0,
+                                const CUtensorMap* xmap = nullptr);
+// Opt-in shared memory of the TMA-fed FP32 reduction (called once per split
+// context).  With st, num_sms and xmap (a tiled map of the FP32 X~ buffer:
+// dims {rows, columns}, box {RED_BOX_ROWS, RED_BOX_COLS}, no swizzle) given,
+// launch_reduce_solve streams X~ through it: one persistent block per SM,
+// bounded waits reporting into st.
+constexpr int RED_BOX_ROWS = 256, RED_BOX_COLS = 32;
+cudaError_t prepare_reduce_solve();
 int w32_stride(int q);
 cudaError_t launch_make_w32(const double* W, int64_t ldw, int rows, int q, float* W32, cudaStream_t s);
 

@@ -13,6 +13,7 @@
 // SolveConsts.  A SNP with d^2 <= SINGULAR_TAU * S_BR is numerically
 // collinear with X_L: status GWAS_SNP_SINGULAR and NaN outputs.
 #include "gwas_internal.cuh"
+#include "tc_ptx.cuh"
 
 namespace gwas {
 
@@ -275,110 +276,206 @@ __global__ void __launch_bounds__(32 * SL) reduce_solve_f32_kernel(
   solve_store<QM>(sum, sc, q, col, b, se, status, shift ? (double)shift[col] : 0.0);
 }
 
-// FP32 X~, few covariates (q <= 7): a block takes RC SNP columns and splits
-// the rows into RW slices of whole 128-row chunks, one slice per warp.  Lane l
-// covers rows 4l .. 4l+3 of a chunk, so every float4 load of a column is one
-// coalesced 512-byte segment, and the four W32 rows it needs come from L1.
-// A chunk's products are summed in FP32, chunks are added with Kahan
-// compensation (FP32), a warp's lanes are added in FP64 by a butterfly and the
-// RW slice totals of a column in FP64, in a fixed order (deterministic).
-// Lanes past ncols re-read the last column and discard the result.
-constexpr int RC_RW = 4;  // row slices (warps) per block
+// FP32 X~ streamed by TMA (the split paths, q <= 7).  A persistent block takes
+// a contiguous range of SNP columns in groups of BG; one producer thread
+// streams each group in chunks of BCH rows -- two tiled loads of 256 rows x
+// 32 columns (32 KB each) and one bulk copy of the chunk's W32 rows -- into
+// shared-memory stages completing on the stage's mbarrier, so a block keeps
+// ~150-200 KB of loads in flight without holding them in registers.  Consumer warp w owns columns 2w and 2w+1 of the
+// group (one load of a W row serves both); in each 128-row sub-chunk lane l
+// takes rows 32r + l (r = 0..3), so its shared-memory loads are
+// conflict-free.  Sums: FP32 over a chunk (16 rows per lane), Kahan across
+// chunks, across the lanes a fixed butterfly in double-FP32 (error-free
+// TwoSum steps; FP64 arithmetic is a small fraction of the FP32 rate on this
+// part), then FP64.  The column totals wait in shared memory; at the end one
+// lane per column runs the p x p solve, so the FP64 solves of a block share
+// warp instructions.  Deterministic.
+constexpr int BCW = 16, BG = 2 * BCW, BCH = 2 * RED_BOX_ROWS, BMAXC = 128;  // BMAXC: most columns per block
+static_assert(BG == RED_BOX_COLS, "one tiled load spans the group's columns");
 
-template <int QM, int WS, int RC>
-__global__ void __launch_bounds__(32 * RC_RW) reduce_solve_f32c_kernel(
+// (hi, lo) + (bh, bl) as a double-FP32 pair (TwoSum on the high parts).
+__device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl) {
+  const float s = hi + bh;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (bh - bb);
+  const float l = lo + bl + err;
+  hi = s + l;
+  lo = l - (hi - s);
+}
+
+// After a failed (timed-out or aborted) wait: 2 ms for bulk copies already in
+// flight to land, so that none writes shared memory of a retired block.
+__device__ __forceinline__ void settle() {
+  const long long t0 = ptx::globaltimer();
+  while (ptx::globaltimer() - t0 < 2000000LL) {
+  }
+}
+
+template <int WS>
+struct BulkCfg {
+  static constexpr int HB = RED_BOX_ROWS * 4;              // one column's rows in one tiled load: 1 KB
+  static constexpr int WB = BCH * WS * 4;                  // the chunk's W32 rows: 8 or 16 KB
+  static constexpr int XS = 2 * BG * HB;                   // the group's two tiled loads: 64 KB
+  static constexpr int STAGE = XS + WB;                    // 72 or 80 KB
+  static constexpr int ST = WS == 4 ? 3 : 2;               // stages
+  static constexpr int SMEM = 128 + ST * STAGE + 2 * ST * 8;  // (+ 128: alignment) + the column totals (static)
+};
+
+template <int QM, int WS>
+__global__ void __launch_bounds__(32 * (BCW + 1), 1) reduce_solve_bulk_kernel(
     const float* __restrict__ Xt, int64_t ldt, int rows, const float* __restrict__ W32,
     const SolveConsts* __restrict__ sc, int q, int ncols, double* __restrict__ b, double* __restrict__ se,
-    int* __restrict__ status, const int8_t* __restrict__ shift) {
-  constexpr int NA = QM + 2, NW4 = WS / 4;
-  __shared__ double tot[RC_RW][RC][NA];
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  const int nchunk = rows >> 7;
-  const int t0 = w * nchunk / RC_RW, t1 = (w + 1) * nchunk / RC_RW;
-  const float4* w4 = reinterpret_cast<const float4*>(W32);
-  const int col0 = blockIdx.x * RC;
-  const float4* xp[RC];
-#pragma unroll
-  for (int c = 0; c < RC; ++c) {
-    const int col = col0 + c < ncols ? col0 + c : ncols - 1;
-    xp[c] = reinterpret_cast<const float4*>(Xt + (int64_t)col * ldt) + lane;
-  }
-  float ks[RC][NA], kc[RC][NA];
-#pragma unroll
-  for (int c = 0; c < RC; ++c)
-#pragma unroll
-    for (int a = 0; a < NA; ++a) ks[c][a] = kc[c][a] = 0.f;
-  float4 xn[RC];
-  if (t0 < t1) {
-#pragma unroll
-    for (int c = 0; c < RC; ++c) xn[c] = __ldcs(xp[c] + t0 * 32);
-  }
-  for (int t = t0; t < t1; ++t) {
-    float4 xv[RC];
-#pragma unroll
-    for (int c = 0; c < RC; ++c) xv[c] = xn[c];
-    if (t + 1 < t1) {
-#pragma unroll
-      for (int c = 0; c < RC; ++c) xn[c] = __ldcs(xp[c] + (t + 1) * 32);
+    int* __restrict__ status, const int8_t* __restrict__ shift, DevStatus* st,
+    const __grid_constant__ CUtensorMap xmap) {
+  using K = BulkCfg<WS>;
+  constexpr int NA = QM + 2, NW4 = WS / 4, BST = K::ST;
+  extern __shared__ __align__(128) uint8_t smem_raw[];
+  __shared__ double colsum[BMAXC][NA];  // the block's column totals
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem + BST * K::STAGE);
+  uint64_t* empty = full + BST;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int c_begin = (int)((int64_t)blockIdx.x * ncols / gridDim.x);
+  const int c_end = (int)((int64_t)(blockIdx.x + 1) * ncols / gridDim.x);
+  const int nch = (rows + BCH - 1) / BCH;
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < BST; ++s) {
+      ptx::mbar_init(&full[s], 1);
+      ptx::mbar_init(&empty[s], BCW);
     }
-    float4 wv[4][NW4];
-    const int64_t r0 = (int64_t)t * 128 + 4 * lane;
-#pragma unroll
-    for (int rr = 0; rr < 4; ++rr)
-#pragma unroll
-      for (int v4 = 0; v4 < NW4; ++v4) wv[rr][v4] = __ldg(w4 + (r0 + rr) * NW4 + v4);
-#pragma unroll
-    for (int c = 0; c < RC; ++c) {
-      const float xs[4] = {xv[c].x, xv[c].y, xv[c].z, xv[c].w};
-      float part[NA];
-#pragma unroll
-      for (int a = 0; a < NA; ++a) part[a] = 0.f;
-#pragma unroll
-      for (int rr = 0; rr < 4; ++rr) {
-#pragma unroll
-        for (int v4 = 0; v4 < NW4; ++v4) {
-          const float wr[4] = {wv[rr][v4].x, wv[rr][v4].y, wv[rr][v4].z, wv[rr][v4].w};
-#pragma unroll
-          for (int e = 0; e < 4; ++e)
-            if (4 * v4 + e <= QM) part[4 * v4 + e] = fmaf(xs[rr], wr[e], part[4 * v4 + e]);
-        }
-        part[QM + 1] = fmaf(xs[rr], xs[rr], part[QM + 1]);
-      }
-#pragma unroll
-      for (int a = 0; a < NA; ++a) {
-        const float y = part[a] - kc[c][a];
-        const float s2 = ks[c][a] + y;
-        kc[c][a] = (s2 - ks[c][a]) - y;
-        ks[c][a] = s2;
-      }
-    }
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    ptx::prefetch_tensormap(&xmap);
   }
-#pragma unroll
-  for (int c = 0; c < RC; ++c)
-#pragma unroll
-    for (int a = 0; a < NA; ++a) {
-      double v = (double)ks[c][a] - (double)kc[c][a];
-#pragma unroll
-      for (int o = 16; o; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0) tot[w][c][a] = v;
-    }
   __syncthreads();
-  if (threadIdx.x < RC && col0 + (int)threadIdx.x < ncols) {
-    const int c = threadIdx.x, col = col0 + c;
+  if (warp == BCW) {
+    // ------------------------------------------------------------ producer
+    if (lane == 0) {
+      uint32_t it = 0;
+      for (int g0 = c_begin; g0 < c_end; g0 += BG) {
+        for (int t = 0; t < nch; ++t, ++it) {
+          const int s = it % BST;
+          const uint32_t r = it / BST;
+          if (!ptx::mbar_wait(&empty[s], (r & 1) ^ 1, st)) {
+            settle();  // copies already issued land before the block retires
+            return;
+          }
+          const int rt = rows - t * BCH < BCH ? rows - t * BCH : BCH;
+          uint8_t* sb = smem + s * K::STAGE;
+          // boxes past the last row or column read zeros (and count their bytes)
+          ptx::mbar_arrive_expect_tx(&full[s], (uint32_t)(K::XS + rt * WS * 4));
+          ptx::tma_load_2d(sb, &xmap, &full[s], t * BCH, g0);
+          ptx::tma_load_2d(sb + BG * K::HB, &xmap, &full[s], t * BCH + RED_BOX_ROWS, g0);
+          ptx::bulk_load(sb + K::XS, W32 + (int64_t)t * BCH * WS, rt * WS * 4, &full[s]);
+        }
+      }
+    }
+    return;
+  }
+  // ------------------------------------------------------------ consumers
+  uint32_t it = 0;
+  bool ok = true;
+  for (int g0 = c_begin; g0 < c_end && ok; g0 += BG) {
+    const int ca = g0 + 2 * warp;  // this warp's columns: ca, ca + 1
+    const bool live0 = ca < c_end, live1 = ca + 1 < c_end;
+    float ks[2][NA], kc[2][NA];
+#pragma unroll
+    for (int u = 0; u < 2; ++u)
+#pragma unroll
+      for (int a = 0; a < NA; ++a) ks[u][a] = kc[u][a] = 0.f;
+    for (int t = 0; t < nch; ++t, ++it) {
+      const int s = it % BST;
+      const uint32_t r = it / BST;
+      if (!__all_sync(0xffffffffu, ptx::mbar_wait(&full[s], r & 1, st))) {
+        ok = false;
+        break;
+      }
+      if (live0) {
+        // column c's rows 0..255 of the chunk at c * HB, rows 256..511 at BG * HB + c * HB
+        const float* sx0 = reinterpret_cast<const float*>(smem + s * K::STAGE + (2 * warp) * K::HB);
+        const float* sx1 = sx0 + RED_BOX_ROWS;
+        const float4* sw = reinterpret_cast<const float4*>(smem + s * K::STAGE + K::XS);
+        const int rt = rows - t * BCH < BCH ? rows - t * BCH : BCH;
+        float p0[NA], p1[NA];
+#pragma unroll
+        for (int a = 0; a < NA; ++a) p0[a] = p1[a] = 0.f;
+        for (int i = 0; i < rt / 128; ++i) {
+#pragma unroll
+          for (int rr = 0; rr < 4; ++rr) {
+            const int row = i * 128 + rr * 32 + lane;
+            const int xo = (i >> 1) * (BG * RED_BOX_ROWS) + (i & 1) * 128 + rr * 32 + lane;
+            const float x0 = sx0[xo];
+            const float x1 = sx1[xo];
+#pragma unroll
+            for (int v4 = 0; v4 < NW4; ++v4) {
+              const float4 w = sw[row * NW4 + v4];
+              const float wr[4] = {w.x, w.y, w.z, w.w};
+#pragma unroll
+              for (int e = 0; e < 4; ++e)
+                if (4 * v4 + e <= QM) {
+                  p0[4 * v4 + e] = fmaf(x0, wr[e], p0[4 * v4 + e]);
+                  p1[4 * v4 + e] = fmaf(x1, wr[e], p1[4 * v4 + e]);
+                }
+            }
+            p0[QM + 1] = fmaf(x0, x0, p0[QM + 1]);
+            p1[QM + 1] = fmaf(x1, x1, p1[QM + 1]);
+          }
+        }
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+          float y = p0[a] - kc[0][a];
+          float s2 = ks[0][a] + y;
+          kc[0][a] = (s2 - ks[0][a]) - y;
+          ks[0][a] = s2;
+          y = p1[a] - kc[1][a];
+          s2 = ks[1][a] + y;
+          kc[1][a] = (s2 - ks[1][a]) - y;
+          ks[1][a] = s2;
+        }
+      }
+      __syncwarp();
+      if (lane == 0) ptx::mbar_arrive(&empty[s]);
+    }
+    if (ok) {
+#pragma unroll
+      for (int u = 0; u < 2; ++u) {
+        if (!(u == 0 ? live0 : live1)) continue;
+#pragma unroll
+        for (int a = 0; a < NA; ++a) {
+          float hi = ks[u][a], lo = -kc[u][a];
+#pragma unroll
+          for (int o = 16; o; o >>= 1)
+            df_add(hi, lo, __shfl_xor_sync(0xffffffffu, hi, o), __shfl_xor_sync(0xffffffffu, lo, o));
+          if (lane == 0) colsum[ca + u - c_begin][a] = (double)hi + (double)lo;
+        }
+      }
+    }
+  }
+  // every consumer warp is done (or gave up); the solves, one lane per column
+  if (!ptx::group_and(1, 32 * BCW, ok)) {
+    settle();  // copies already issued land before the block retires
+    return;
+  }
+  for (int j = threadIdx.x; j < c_end - c_begin; j += 32 * BCW) {
     double sum[NA];
 #pragma unroll
-    for (int a = 0; a < NA; ++a) {
-      double v = tot[0][c][a];
-      for (int s2 = 1; s2 < RC_RW; ++s2) v += tot[s2][c][a];
-      sum[a] = v;
-    }
+    for (int a = 0; a < NA; ++a) sum[a] = colsum[j][a];
+    const int col = c_begin + j;
     solve_store<QM>(sum, sc, q, col, b, se, status, shift ? (double)shift[col] : 0.0);
   }
 }
 
+cudaError_t prepare_reduce_solve() {
+  cudaError_t e = cudaFuncSetAttribute(reduce_solve_bulk_kernel<3, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       BulkCfg<4>::SMEM);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(reduce_solve_bulk_kernel<7, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                              BulkCfg<8>::SMEM);
+}
+
 cudaError_t launch_reduce_solve(const void* Xt, XtKind kind, int64_t ldt, int rows, const double* W,
                                 int64_t ldw, const SolveConsts* sc, int q, int ncols, double* b, double* se,
-                                int* status, cudaStream_t s, const float* W32, const int8_t* shift) {
+                                int* status, cudaStream_t s, const float* W32, const int8_t* shift,
+                                DevStatus* st, int num_sms, const CUtensorMap* xmap) {
   if (ncols <= 0) return cudaSuccess;
   const int grid = (ncols + 7) / 8;
   if (kind == XT_F64) {
@@ -395,14 +492,16 @@ cudaError_t launch_reduce_solve(const void* Xt, XtKind kind, int64_t ldt, int ro
   const float* X = static_cast<const float*>(Xt);
   if ((rows % RS_RUN) || (ldt % RS_RUN)) return cudaErrorInvalidValue;  // whole 128-byte runs
   const int g32 = (ncols + 31) / 32;
-  if (q <= 3 && rows % 128 == 0)
-    reduce_solve_f32c_kernel<3, 4, 4><<<(ncols + 3) / 4, 32 * RC_RW, 0, s>>>(X, ldt, rows, W32, sc, q, ncols, b, se,
-                                                                            status, shift);
+  const int gb = ncols < num_sms ? ncols : num_sms;  // persistent blocks of the bulk-fed kernel
+  const bool bulk = xmap && st && num_sms > 0 && rows % 128 == 0 && (ncols + gb - 1) / gb <= BMAXC;
+  if (bulk && q <= 3)
+    reduce_solve_bulk_kernel<3, 4><<<gb, 32 * (BCW + 1), BulkCfg<4>::SMEM, s>>>(X, ldt, rows, W32, sc, q, ncols, b,
+                                                                             se, status, shift, st, *xmap);
+  else if (bulk && q <= 7)
+    reduce_solve_bulk_kernel<7, 8><<<gb, 32 * (BCW + 1), BulkCfg<8>::SMEM, s>>>(X, ldt, rows, W32, sc, q, ncols, b,
+                                                                             se, status, shift, st, *xmap);
   else if (q <= 3)
     reduce_solve_f32_kernel<3, 4, 16><<<g32, 512, 0, s>>>(X, ldt, rows, W32, sc, q, ncols, b, se, status, shift);
-  else if (q <= 7 && rows % 128 == 0)
-    reduce_solve_f32c_kernel<7, 8, 2><<<(ncols + 1) / 2, 32 * RC_RW, 0, s>>>(X, ldt, rows, W32, sc, q, ncols, b, se,
-                                                                            status, shift);
   else if (q <= 7)
     reduce_solve_f32_kernel<7, 8, 16><<<g32, 512, 0, s>>>(X, ldt, rows, W32, sc, q, ncols, b, se, status, shift);
   else

@@ -220,6 +220,16 @@ __device__ __forceinline__ void tma_load_2d_pair(void* dst, const CUtensorMap* m
       : "memory");
 }
 
+// Untiled bulk copy of `bytes` (a multiple of 16) from global memory into
+// this CTA's shared memory (both addresses 16-byte aligned), completing on
+// `bar`'s transaction count.
+__device__ __forceinline__ void bulk_load(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile("cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+                   smem_u32(dst)),
+               "l"(src), "r"(bytes), "r"(smem_u32(bar))
+               : "memory");
+}
+
 // Shared -> global tile store (bulk async-group completion), and its group
 // bookkeeping: commit, wait until at most N groups still read shared memory,
 // wait until all groups' writes are complete.

@@ -71,6 +71,7 @@ cudaError_t run_transpose(TcState* t, int ncols, cudaStream_t s, int64_t* launch
 const float* xhat_f32(const TcState* t);
 
 const float* xt_f32(const TcState* t);
+const CUtensorMap* xt_reduce_map(const TcState* t);  // xt_f32() as the reduction's tiled map
 const int8_t* shift_of(const TcState* t);  // per-SNP shifts of the last block, or null
 int64_t xt_ld(const TcState* t);
 TileMode tile_mode(const TcState* t);  // the resolved mode

@@ -264,6 +264,7 @@ struct TcState {
   DevStatus* st = nullptr;
   CUtensorMap mAhi, mAlo, mBhi, mBlo, mBhiH, mBloH;
   CUtensorMap mStX, mStHi, mStLo;  // pair product's epilogue stores
+  CUtensorMap mRed;                // the reduction's view of the FP32 X~ (box RED_BOX_ROWS x RED_BOX_COLS)
   // transpose solve (the adjoint form): the transpose block operator split hi/lo,
   // X^ = L^-T X~ in FP32 + pieces, and their maps
   void* ahiT = nullptr;
@@ -387,6 +388,8 @@ cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_p
   // epilogue store chunks: the pair product's (value + pieces in one 2 KB
   // buffer), or the inverse form's (FP32 value alone, 16 columns)
   const uint32_t stc = inv ? inv2::ST_COLS : (t->tf32 ? pair2::st_cols<true>() : pair2::st_cols<false>());
+  TRY(make_map(t->encode, &t->mRed, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, t->xt32, n_pad, bs, 4 * (size_t)n_pad,
+               RED_BOX_ROWS, RED_BOX_COLS, false));
   TRY(make_map(t->encode, &t->mStX, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, t->xt32, n_pad, bs, 4 * (size_t)n_pad, 32, stc,
                false));
   memset(&t->mStHi, 0, sizeof t->mStHi);
@@ -816,6 +819,7 @@ void batch_destroy(TcBatchState* B) {
 }
 
 const float* xt_f32(const TcState* t) { return t->xt32; }
+const CUtensorMap* xt_reduce_map(const TcState* t) { return &t->mRed; }
 const int8_t* shift_of(const TcState* t) { return t->center ? t->shift : nullptr; }
 int64_t xt_ld(const TcState* t) { return t->ldt; }
 TileMode tile_mode(const TcState* t) { return t->mode; }
