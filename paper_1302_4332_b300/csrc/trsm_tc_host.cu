@@ -45,6 +45,71 @@ __global__ void column_shift_kernel(const int8_t* __restrict__ X, int64_t ldx, i
   }
 }
 
+// The same in one read of the column: for n <= 512 * NV each lane holds its
+// NV 16-byte pieces of the column in registers between the sum and the
+// cast (all of them in flight at once).
+template <bool TF32, int NV>
+__global__ void __launch_bounds__(256) cast_shift_reg_kernel(const int8_t* __restrict__ X, int64_t ldx, int n,
+                                                             int n_pad, int ncols, int8_t* __restrict__ shift,
+                                                             void* __restrict__ xc) {
+  const int lane = threadIdx.x & 31;
+  const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (col >= ncols) return;
+  const int8_t* x = X + (int64_t)col * ldx;  // 16-byte aligned (checked by the caller)
+  int4 v[NV];
+#pragma unroll
+  for (int j = 0; j < NV; ++j) {
+    const int r = j * 512 + lane * 16;
+    if (r + 16 <= n) {
+      v[j] = __ldg(reinterpret_cast<const int4*>(x + r));
+    } else {  // the ragged piece (bytes past n read as 0)
+      uint32_t w[4] = {0u, 0u, 0u, 0u};
+      for (int i = 0; i < 16 && r + i < n; ++i) w[i >> 2] |= (uint32_t)(uint8_t)x[r + i] << (8 * (i & 3));
+      v[j] = make_int4((int)w[0], (int)w[1], (int)w[2], (int)w[3]);
+    }
+  }
+  int c = 0;
+  if (shift) {
+    int sum = 0;
+#pragma unroll
+    for (int j = 0; j < NV; ++j)
+      sum += __dp4a(v[j].x, 0x01010101, 0) + __dp4a(v[j].y, 0x01010101, 0) + __dp4a(v[j].z, 0x01010101, 0) +
+             __dp4a(v[j].w, 0x01010101, 0);
+#pragma unroll
+    for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    const long long num = 2LL * sum + n, den = 2LL * n;
+    long long cc = num >= 0 ? num / den : -((-num + den - 1) / den);
+    cc = cc > 127 ? 127 : (cc < -127 ? -127 : cc);
+    c = (int)cc;
+    if (lane == 0) shift[col] = (int8_t)c;
+  }
+#pragma unroll
+  for (int j = 0; j <= NV; ++j) {  // piece NV: padding rows only (zeros)
+    const int r = j * 512 + lane * 16;
+    if (r >= n_pad) break;
+    float f[16];
+    const int w[4] = {j < NV ? v[j].x : 0, j < NV ? v[j].y : 0, j < NV ? v[j].z : 0, j < NV ? v[j].w : 0};
+#pragma unroll
+    for (int i = 0; i < 16; ++i)
+      f[i] = r + i < n ? (float)((int)(int8_t)(w[i >> 2] >> (8 * (i & 3))) - c) : 0.f;
+    if constexpr (TF32) {
+      float4* o = reinterpret_cast<float4*>(static_cast<float*>(xc) + (int64_t)col * n_pad + r);
+#pragma unroll
+      for (int i = 0; i < 4; ++i) o[i] = make_float4(f[4 * i], f[4 * i + 1], f[4 * i + 2], f[4 * i + 3]);
+    } else {
+      uint32_t wv[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const __nv_bfloat162 b2 = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
+        wv[i] = *reinterpret_cast<const uint32_t*>(&b2);
+      }
+      uint4* o = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(xc) + (int64_t)col * n_pad + r);
+      o[0] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+      o[1] = make_uint4(wv[4], wv[5], wv[6], wv[7]);
+    }
+  }
+}
+
 // B operand of the inverse form: x'_ri = x_ri - c_i on rows < n and 0 on rows
 // n..n_pad-1, as BF16 (or FP32, read as TF32 by the tensor cores), column-major
 // with leading dimension n_pad.  c_i is computed here as in column_shift_kernel
@@ -112,6 +177,20 @@ __global__ void cast_shift_kernel(const int8_t* __restrict__ X, int64_t ldx, int
       o[1] = make_uint4(wv[4], wv[5], wv[6], wv[7]);
     }
   }
+}
+
+// The cast pre-pass of the inverse form: one read per column while it fits
+// the registers (n <= 16384), else two.
+template <bool TF32>
+static void launch_cast(const int8_t* X, int64_t ldx, int n, int n_pad, int ncols, int8_t* shift, void* xc,
+                        cudaStream_t s) {
+  const int grid = (ncols + 7) / 8;
+  if (n <= 512 * 20)
+    cast_shift_reg_kernel<TF32, 20><<<grid, 256, 0, s>>>(X, ldx, n, n_pad, ncols, shift, xc);
+  else if (n <= 512 * 32)
+    cast_shift_reg_kernel<TF32, 32><<<grid, 256, 0, s>>>(X, ldx, n, n_pad, ncols, shift, xc);
+  else
+    cast_shift_kernel<TF32><<<grid, 256, 0, s>>>(X, ldx, n, n_pad, ncols, shift, xc);
 }
 
 // Columns c0.. c0+ncols-1 of the n_pad x n_pad identity as int8, column-major
@@ -445,9 +524,9 @@ static cudaError_t prepare_cast(TcState* t, const int8_t* X, int64_t ldx, int nc
   if (e != cudaSuccess) return e;
   int8_t* sh = t->center ? t->shift : nullptr;
   if (t->tf32)
-    cast_shift_kernel<true><<<(ncols + 7) / 8, 256, 0, s>>>(X, ldx, t->n, t->n_pad, ncols, sh, t->xc);
+    launch_cast<true>(X, ldx, t->n, t->n_pad, ncols, sh, t->xc, s);
   else
-    cast_shift_kernel<false><<<(ncols + 7) / 8, 256, 0, s>>>(X, ldx, t->n, t->n_pad, ncols, sh, t->xc);
+    launch_cast<false>(X, ldx, t->n, t->n_pad, ncols, sh, t->xc, s);
   ++*launches;
   return cudaGetLastError();
 }
@@ -777,9 +856,9 @@ cudaError_t batch_launch(TcBatchState* B, TcState* const* ts, cudaStream_t s, in
       int8_t* sh = t->center ? t->shift : nullptr;
       const int nc = B->S[i].ncols;
       if (t->tf32)
-        cast_shift_kernel<true><<<(nc + 7) / 8, 256, 0, s>>>(B->X[i], B->ldx[i], t->n, t->n_pad, nc, sh, t->xc);
+        launch_cast<true>(B->X[i], B->ldx[i], t->n, t->n_pad, nc, sh, t->xc, s);
       else
-        cast_shift_kernel<false><<<(nc + 7) / 8, 256, 0, s>>>(B->X[i], B->ldx[i], t->n, t->n_pad, nc, sh, t->xc);
+        launch_cast<false>(B->X[i], B->ldx[i], t->n, t->n_pad, nc, sh, t->xc, s);
       ++*launches;
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     } else if (t->center) {
