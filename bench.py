@@ -42,7 +42,7 @@ sys.path.insert(0, ROOT)
 METRIC = "GLS solves/sec (SNPs/s) at n=10k,p=4: split-prec vs FP64 path, % roofline"
 UNIT = "SNPs/s"
 WORKLOAD = "n10k_p4_m1M_int8"
-SPLIT_PATHS = ("bf16x3", "tf32x3")
+SPLIT_PATHS = ("bf16x3", "tf32x3", "f16x2")
 E2E_REPEATS = 4  # the end-to-end step streams the resident blocks this many times over
 STRIP_GROUP = 0  # tile order of the split paths: strips per group (0 = all)
 N_RESIDENT_BLOCKS = 8
@@ -54,7 +54,7 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=20)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--paths", default="auto", help="comma list of fp64,bf16x3,tf32x3 (auto: all built)")
+    ap.add_argument("--paths", default="auto", help="comma list of fp64,bf16x3,tf32x3,f16x2 (auto: all built)")
     ap.add_argument("--n", type=int, default=None, help="override n (smaller smoke runs only)")
     ap.add_argument("--bs", type=int, default=None, help="override bs (smaller smoke runs only)")
     ap.add_argument("--no-e2e", action="store_true")
@@ -289,7 +289,7 @@ def run_ours(args, rank, world, local_rank, dist):
     # (pair product) of each split path, kernel-only, for comparison
     jobs = [(pp, pp, args.tiles if pp != "fp64" else "auto") for pp in paths]
     if args.tiles == "auto" and not args.no_substitution:
-        jobs += [(f"{pp}/pair_mma", pp, "pair_mma") for pp in paths if pp in SPLIT_PATHS]
+        jobs += [(f"{pp}/pair_mma", pp, "pair_mma") for pp in paths if pp in ("bf16x3", "tf32x3")]
     results = {}
     for entry, path, tiles in jobs:
         steps, warm_blocks = args.steps, args.warmup * NB
@@ -299,7 +299,8 @@ def run_ours(args, rank, world, local_rank, dist):
         t_init = time.time()
         sg = STRIP_GROUP if args.strip_group is None else args.strip_group
         g = gw.GLS(s["Phi"], s["XL"], s["y"], w["h"], w["sigma2"], precision=path, bs=bs,
-                   strip_group=sg if path != "fp64" else 0, tiles=tiles)
+                   strip_group=sg if path != "fp64" else 0, tiles=tiles if path != "f16x2" or tiles == "auto"
+                   else "inverse")
         init_s = time.time() - t_init
         b = torch.empty((bs, p), dtype=torch.float64, device=dev).T
         se = torch.empty((bs, p), dtype=torch.float64, device=dev).T
@@ -343,7 +344,8 @@ def run_ours(args, rank, world, local_rank, dist):
                         peak_basis="FP64 dense GEMM rate measured with cuBLAS DGEMM on this GPU (of measured)")
         else:
             bf16 = peaks.get("bf16_tflops") or 1800.0
-            base = bf16 if path == "bf16x3" else (extra.get("tf32_tflops_cublas") or bf16 * 1.1 / 2.25)
+            # FP16 runs at the BF16 rate on the tensor cores
+            base = bf16 if path in ("bf16x3", "f16x2") else (extra.get("tf32_tflops_cublas") or bf16 * 1.1 / 2.25)
             # tensor products per algorithmic product: the substitution multiplies
             # split operators by split X~ (hi*hi + hi*lo + lo*hi); the inverse form
             # multiplies the split L^-1 by the exact dosages (hi*X + lo*X)
@@ -351,11 +353,11 @@ def run_ours(args, rank, world, local_rank, dist):
             pk = base / prods
             roof = dict(bound="tensor", achieved=achieved, peak=pk, unit="TFLOP/s", frac=achieved / pk,
                         traffic=kernel_traffic(path, mode),
-                        peak_basis=(f"{'bf16' if path == 'bf16x3' else 'tf32'} dense tensor peak (of measured, "
+                        peak_basis=(f"{'tf32' if path == 'tf32x3' else 'bf16'} dense tensor peak (of measured, "
                                     f"burst) / {prods}: {prods} split products per algorithmic product "
                                     f"({mode} tile mode)"))
             sus = peaks.get("bf16_tflops_sustained")
-            if path == "bf16x3" and sus:  # a long timed region runs under the power cap
+            if path in ("bf16x3", "f16x2") and sus:  # a long timed region runs under the power cap
                 roof["frac_of_sustained"] = achieved / (sus / prods)
         res["roofline"] = roof
         res["trsm_ms_per_launch"] = trsm_ms
@@ -626,7 +628,7 @@ def main():
     line = {
         "metric": METRIC, "value": hr["snps_per_s"], "unit": UNIT, "n_gpus": world, "steps": hr["steps"],
         "warmup": args.warmup, "ms_per_step": hr["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"fp64": "f64", "bf16x3": "bf16x3", "tf32x3": "tf32x3"}[head],
+        "vs_baseline": None, "dtype": {"fp64": "f64", "bf16x3": "bf16x3", "tf32x3": "tf32x3", "f16x2": "f16x2"}[head],
         "data": "synthetic (seeded kinship, covariates, phenotype and int8 dosages shaped like the paper's n=1e4, p=4 workload)",
         "config": {"workload": WORKLOAD, "n": w["n"], "p": w["p"], "bs": w["bs"],
                    "snps_per_step": N_RESIDENT_BLOCKS * w["bs"],

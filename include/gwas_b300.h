@@ -70,8 +70,15 @@ extern "C" {
  *   GWAS_TF32X3 : block products on the tensor cores, each FP32 operand split
  *                 into TF32 hi + lo, three products (hi*hi + hi*lo + lo*hi),
  *                 FP32 accumulation.
- *   GWAS_BF16X3 : the same with BF16 hi + lo pieces. */
-typedef enum { GWAS_FP64 = 0, GWAS_TF32X3 = 1, GWAS_BF16X3 = 2 } gwas_precision;
+ *   GWAS_BF16X3 : the same with BF16 hi + lo pieces.
+ *   (In the inverse tile mode the dosages are exact, so hi*X + lo*X: two products.)
+ *   GWAS_F16X2  : inverse tile mode only (tile_mode AUTO or INVERSE; others return
+ *                 GWAS_ERR_ARG): each row of L^-1 is scaled by a power of two so its
+ *                 largest entry lies in [2^13, 2^14), then split into FP16 hi + lo
+ *                 (11 + 11 significant bits against BF16's 8 + 8), the dosages exact
+ *                 in FP16: two products at the BF16 rate; results scaled back exactly.
+ *                 The adjoint's transpose solve of such a context runs in BF16x3. */
+typedef enum { GWAS_FP64 = 0, GWAS_TF32X3 = 1, GWAS_BF16X3 = 2, GWAS_F16X2 = 3 } gwas_precision;
 
 typedef struct {
   int precision;   /* gwas_precision */

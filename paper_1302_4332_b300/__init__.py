@@ -25,10 +25,10 @@ ERRORS = {
     -1: "GWAS_ERR_ARG", -2: "GWAS_ERR_NOT_SPD", -3: "GWAS_ERR_CUDA", -4: "GWAS_ERR_TIMEOUT",
     -5: "GWAS_ERR_IO", -6: "GWAS_ERR_NOMEM", -7: "GWAS_ERR_UNSUPPORTED",
 }
-PRECISIONS = {"fp64": 0, "tf32x3": 1, "bf16x3": 2}
+PRECISIONS = {"fp64": 0, "tf32x3": 1, "bf16x3": 2, "f16x2": 3}
 # split modes: how the solve's tiles map onto SMs (gwas_config.tile_mode)
 TILE_MODES = {"auto": 0, "single": 1, "pair_multicast": 2, "pair_mma": 3, "inverse": 4}
-BUILT_PRECISIONS = ("fp64", "bf16x3", "tf32x3")
+BUILT_PRECISIONS = ("fp64", "bf16x3", "tf32x3", "f16x2")
 SNP_OK, SNP_SINGULAR = 0, 1
 
 # Every symbol the header declares (checked by the CPU test suite).
@@ -245,7 +245,8 @@ class GLS:
 
     phi_or_L: n x n kinship Phi (or, with is_L=True, the lower factor L of M).
     XL: n x (p-1) covariates; y: n phenotypes; M = sigma2 (h Phi + (1-h) I).
-    precision: "fp64", "tf32x3" or "bf16x3" for the blocked triangular solve.
+    precision: "fp64", "tf32x3", "bf16x3" or "f16x2" (the inverse tile mode's
+    row-scaled FP16 pieces of L^-1) for the blocked triangular solve.
     """
 
     def __init__(self, phi_or_L, XL, y, h: float, sigma2: float = 1.0, *, precision: str = "fp64",

@@ -349,8 +349,8 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
   if (cfg_in) cfg = *cfg_in;
   if (n < 1 || p < 1 || p > QMAX + 1 || !phi_or_L || !y || (p > 1 && !XL) || !(h >= 0.0 && h <= 1.0) ||
       !(sigma2 > 0.0) || cfg.bs < 1 || cfg.ring_depth < 2 || cfg.strip_group < 0 || cfg.tile_mode < GWAS_TILES_AUTO || cfg.tile_mode > GWAS_TILES_INVERSE ||
-      cfg.precision < GWAS_FP64 ||
-      cfg.precision > GWAS_BF16X3)
+      cfg.precision < GWAS_FP64 || cfg.precision > GWAS_F16X2 ||
+      (cfg.precision == GWAS_F16X2 && cfg.tile_mode != GWAS_TILES_AUTO && cfg.tile_mode != GWAS_TILES_INVERSE))
     return GWAS_ERR_ARG;
   for (int r : cfg.reserved)
     if (r != 0) return GWAS_ERR_ARG;
@@ -473,7 +473,10 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
     // split-precision operands: hi + lo copies of the block operator
     if (ctx->prec != GWAS_FP64) {
       int64_t nl = 0;
-      cudaError_t e = tc::create(&ctx->tcs, ctx->prec == GWAS_BF16X3 ? tc::SPLIT_BF16 : tc::SPLIT_TF32, ctx->Aop,
+      const tc::Split sp = ctx->prec == GWAS_BF16X3 ? tc::SPLIT_BF16
+                           : ctx->prec == GWAS_F16X2 ? tc::SPLIT_F16
+                                                     : tc::SPLIT_TF32;
+      cudaError_t e = tc::create(&ctx->tcs, sp, ctx->Aop,
                                  ctx->n, ctx->n_pad, cfg.bs, ctx->num_sms, ctx->intercept, ctx->st, ctx->stream,
                                  &nl, cfg.strip_group, static_cast<tc::TileMode>(cfg.tile_mode));
       ctx->launches += nl;

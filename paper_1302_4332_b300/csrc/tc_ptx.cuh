@@ -415,6 +415,10 @@ __host__ __device__ constexpr uint32_t idesc_f32acc(int M, int N) {
   return (1u << 4) | ((TF32 ? 2u : 1u) << 7) | ((TF32 ? 2u : 1u) << 10) | (static_cast<uint32_t>(N >> 3) << 17) |
          (static_cast<uint32_t>(M >> 4) << 24);
 }
+// The same with FP16 A and B (format 0 of kind::f16).
+__host__ __device__ constexpr uint32_t idesc_f32acc_f16(int M, int N) {
+  return (1u << 4) | (static_cast<uint32_t>(N >> 3) << 17) | (static_cast<uint32_t>(M >> 4) << 24);
+}
 
 // Barrier over `count` threads that also ANDs a predicate across them: every
 // thread of the group gets the same verdict, so a group never splits between

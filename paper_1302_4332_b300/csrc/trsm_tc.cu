@@ -1069,7 +1069,10 @@ struct Cfg {
 };
 }  // namespace inv2
 
-template <bool TF32>
+// F16 (with TF32 false): L^-1 pieces and the cast block are FP16; row r of
+// L^-1 was scaled by 1 / rscale[r] (a power of two) before the split, so the
+// epilogue multiplies its results back by rscale[r].
+template <bool TF32, bool F16 = false>
 __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_constant__ TcBatch b) {
   using K = inv2::Cfg<TF32>;
   constexpr int ST = inv2::STAGES;
@@ -1189,7 +1192,7 @@ __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_co
   } else if (warp == 1) {
     // ------------------------------------------------- MMA issuer (CTA 0 only)
     if (lane == 0) {
-      constexpr uint32_t idesc = ptx::idesc_f32acc<TF32>(2 * TB, TN);
+      constexpr uint32_t idesc = F16 ? ptx::idesc_f32acc_f16(2 * TB, TN) : ptx::idesc_f32acc<TF32>(2 * TB, TN);
       uint32_t cnt = 0, kb = 0;
       for (int it = 0;; ++it) {
         const int slot = it % TRING;
@@ -1290,6 +1293,11 @@ __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_co
       uint8_t* stg = smem + K::STG_OFF + e * 2 * K::CHUNK_BYTES;
       const int r0 = k * TB + 32 * lq;
       const int c0 = c * TN + chalf * EPI_COLS;
+      if constexpr (F16) {  // this thread's row back to the scale of L^-1 (exact: a power of two)
+        const float rs = __ldg(S.rscale + r0 + lane);
+#pragma unroll
+        for (int i = 0; i < EPI_COLS; ++i) master[i] *= rs;
+      }
       auto next_buf = [&]() -> uint8_t* {
         uint8_t* buf = stg + (gq & 1) * K::CHUNK_BYTES;
         if (gq >= 2) {
@@ -1391,6 +1399,8 @@ static cudaError_t set_attrs(bool clusters) {
   if (e != cudaSuccess || !clusters) return e;
   if ((e = cudaFuncSetAttribute(trsm_tc_kernel<TF32, true>, A, Cfg<TF32>::SMEM)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(trsm_tc_pair_mma_kernel<TF32>, A, pair2::Cfg<TF32>::SMEM)) != cudaSuccess) return e;
+  if (!TF32 && (e = cudaFuncSetAttribute(trsm_tc_inv_kernel<false, true>, A, inv2::Cfg<false>::SMEM)) != cudaSuccess)
+    return e;
   return cudaFuncSetAttribute(trsm_tc_inv_kernel<TF32>, A, inv2::Cfg<TF32>::SMEM);
 }
 
@@ -1405,34 +1415,37 @@ cudaError_t set_upper_attr(bool tf32) {
 }
 
 template <bool TF32>
-static cudaError_t clusters_of(int num_sms, TileMode mode, int* out) {
+static cudaError_t clusters_of(int num_sms, TileMode mode, int* out, bool f16) {
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t cfg = pair_config<TF32>(attr, 2 * (num_sms / 2), nullptr, mode);
-  const void* fn = mode == TILES_INVERSE    ? (const void*)trsm_tc_inv_kernel<TF32>
+  const void* fn = mode == TILES_INVERSE    ? (f16 ? (const void*)trsm_tc_inv_kernel<false, true>
+                                                   : (const void*)trsm_tc_inv_kernel<TF32>)
                    : mode == TILES_PAIR_MMA ? (const void*)trsm_tc_pair_mma_kernel<TF32>
                                             : (const void*)trsm_tc_kernel<TF32, true>;
   return cudaOccupancyMaxActiveClusters(out, fn, &cfg);
 }
 
-cudaError_t query_clusters(bool tf32, TileMode mode, int num_sms, int* out) {
-  return tf32 ? clusters_of<true>(num_sms, mode, out) : clusters_of<false>(num_sms, mode, out);
+cudaError_t query_clusters(bool tf32, TileMode mode, int num_sms, int* out, bool f16) {
+  return tf32 ? clusters_of<true>(num_sms, mode, out, false) : clusters_of<false>(num_sms, mode, out, f16);
 }
 
 template <bool TF32>
-static cudaError_t launch_pair(const TcBatch& b, int max_clusters, cudaStream_t s, TileMode mode) {
+static cudaError_t launch_pair(const TcBatch& b, int max_clusters, cudaStream_t s, TileMode mode, bool f16) {
   const int ncl = b.ntiles < max_clusters ? b.ntiles : max_clusters;
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t cfg = pair_config<TF32>(attr, 2 * ncl, s, mode);
+  if (mode == TILES_INVERSE && f16 && !TF32) return cudaLaunchKernelEx(&cfg, trsm_tc_inv_kernel<false, true>, b);
   if (mode == TILES_INVERSE) return cudaLaunchKernelEx(&cfg, trsm_tc_inv_kernel<TF32>, b);
   if (mode == TILES_PAIR_MMA) return cudaLaunchKernelEx(&cfg, trsm_tc_pair_mma_kernel<TF32>, b);
   return cudaLaunchKernelEx(&cfg, trsm_tc_kernel<TF32, true>, b);
 }
 
 cudaError_t launch_solve(bool tf32, TileMode mode, const TcBatch& b, int num_sms, int max_clusters,
-                         cudaStream_t s) {
+                         cudaStream_t s, bool f16) {
+  if (f16 && (tf32 || mode != TILES_INVERSE)) return cudaErrorInvalidValue;
   if (mode != TILES_SINGLE) {
-    const cudaError_t e =
-        tf32 ? launch_pair<true>(b, max_clusters, s, mode) : launch_pair<false>(b, max_clusters, s, mode);
+    const cudaError_t e = tf32 ? launch_pair<true>(b, max_clusters, s, mode, false)
+                               : launch_pair<false>(b, max_clusters, s, mode, f16);
     return e != cudaSuccess ? e : cudaGetLastError();
   }
   const int grid = b.ntiles < num_sms ? b.ntiles : num_sms;

@@ -10,7 +10,9 @@
 namespace gwas {
 namespace tc {
 
-enum Split : int { SPLIT_BF16 = 0, SPLIT_TF32 = 1 };
+// SPLIT_F16: the inverse form only, L^-1 split into FP16 hi + lo after a
+// power-of-two scaling of each row (the rest of such a context runs in BF16).
+enum Split : int { SPLIT_BF16 = 0, SPLIT_TF32 = 1, SPLIT_F16 = 2 };
 
 // How tiles (row panel k, strip c) map onto CTAs.
 enum TileMode : int {

@@ -5,6 +5,7 @@
 // themselves are in trsm_tc.cu.
 #include <cuda.h>
 #include <cuda_bf16.h>
+#include <cuda_fp16.h>
 
 #include <algorithm>
 #include <cstdio>
@@ -45,10 +46,37 @@ __global__ void column_shift_kernel(const int8_t* __restrict__ X, int64_t ldx, i
   }
 }
 
+// 16 consecutive values of the cast block at element offset `off` (a multiple
+// of 16): BF16, FP32 (read as TF32) or FP16 -- all exact for |x - c_i| <= 255.
+enum CastOut : int { OUT_BF16 = 0, OUT_F32 = 1, OUT_F16 = 2 };
+template <int OUT>
+__device__ __forceinline__ void store_cast16(void* xc, int64_t off, const float (&f)[16]) {
+  if constexpr (OUT == OUT_F32) {
+    float4* o = reinterpret_cast<float4*>(static_cast<float*>(xc) + off);
+#pragma unroll
+    for (int i = 0; i < 4; ++i) o[i] = make_float4(f[4 * i], f[4 * i + 1], f[4 * i + 2], f[4 * i + 3]);
+  } else {
+    uint32_t wv[8];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      if constexpr (OUT == OUT_F16) {
+        const __half2 h2 = __floats2half2_rn(f[2 * i], f[2 * i + 1]);
+        wv[i] = *reinterpret_cast<const uint32_t*>(&h2);
+      } else {
+        const __nv_bfloat162 b2 = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
+        wv[i] = *reinterpret_cast<const uint32_t*>(&b2);
+      }
+    }
+    uint4* o = reinterpret_cast<uint4*>(static_cast<uint16_t*>(xc) + off);
+    o[0] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
+    o[1] = make_uint4(wv[4], wv[5], wv[6], wv[7]);
+  }
+}
+
 // The same in one read of the column: for n <= 512 * NV each lane holds its
 // NV 16-byte pieces of the column in registers between the sum and the
 // cast (all of them in flight at once).
-template <bool TF32, int NV>
+template <int OUT, int NV>
 __global__ void __launch_bounds__(256) cast_shift_reg_kernel(const int8_t* __restrict__ X, int64_t ldx, int n,
                                                              int n_pad, int ncols, int8_t* __restrict__ shift,
                                                              void* __restrict__ xc) {
@@ -92,29 +120,16 @@ __global__ void __launch_bounds__(256) cast_shift_reg_kernel(const int8_t* __res
 #pragma unroll
     for (int i = 0; i < 16; ++i)
       f[i] = r + i < n ? (float)((int)(int8_t)(w[i >> 2] >> (8 * (i & 3))) - c) : 0.f;
-    if constexpr (TF32) {
-      float4* o = reinterpret_cast<float4*>(static_cast<float*>(xc) + (int64_t)col * n_pad + r);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) o[i] = make_float4(f[4 * i], f[4 * i + 1], f[4 * i + 2], f[4 * i + 3]);
-    } else {
-      uint32_t wv[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const __nv_bfloat162 b2 = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
-        wv[i] = *reinterpret_cast<const uint32_t*>(&b2);
-      }
-      uint4* o = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(xc) + (int64_t)col * n_pad + r);
-      o[0] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
-      o[1] = make_uint4(wv[4], wv[5], wv[6], wv[7]);
-    }
+    store_cast16<OUT>(xc, (int64_t)col * n_pad + r, f);
   }
 }
 
 // B operand of the inverse form: x'_ri = x_ri - c_i on rows < n and 0 on rows
-// n..n_pad-1, as BF16 (or FP32, read as TF32 by the tensor cores), column-major
-// with leading dimension n_pad.  c_i is computed here as in column_shift_kernel
-// when `shift` is given (and stored there), else 0.  One warp per SNP column.
-template <bool TF32>
+// n..n_pad-1, as BF16, FP32 (read as TF32 by the tensor cores) or FP16,
+// column-major with leading dimension n_pad.  c_i is computed here as in
+// column_shift_kernel when `shift` is given (and stored there), else 0.  One
+// warp per SNP column.
+template <int OUT>
 __global__ void cast_shift_kernel(const int8_t* __restrict__ X, int64_t ldx, int n, int n_pad, int ncols,
                                   int8_t* __restrict__ shift, void* __restrict__ xc) {
   const int lane = threadIdx.x & 31;
@@ -161,36 +176,32 @@ __global__ void cast_shift_kernel(const int8_t* __restrict__ X, int64_t ldx, int
 #pragma unroll
       for (int i = 0; i < 16; ++i) f[i] = (r + i < n) ? (float)((int)x[r + i] - c) : 0.f;
     }
-    if constexpr (TF32) {
-      float4* o = reinterpret_cast<float4*>(static_cast<float*>(xc) + (int64_t)col * n_pad + r);
-#pragma unroll
-      for (int i = 0; i < 4; ++i) o[i] = make_float4(f[4 * i], f[4 * i + 1], f[4 * i + 2], f[4 * i + 3]);
-    } else {
-      uint32_t wv[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const __nv_bfloat162 b2 = __floats2bfloat162_rn(f[2 * i], f[2 * i + 1]);
-        wv[i] = *reinterpret_cast<const uint32_t*>(&b2);
-      }
-      uint4* o = reinterpret_cast<uint4*>(static_cast<__nv_bfloat16*>(xc) + (int64_t)col * n_pad + r);
-      o[0] = make_uint4(wv[0], wv[1], wv[2], wv[3]);
-      o[1] = make_uint4(wv[4], wv[5], wv[6], wv[7]);
-    }
+    store_cast16<OUT>(xc, (int64_t)col * n_pad + r, f);
   }
 }
 
 // The cast pre-pass of the inverse form: one read per column while it fits
 // the registers (n <= 16384), else two.
-template <bool TF32>
-static void launch_cast(const int8_t* X, int64_t ldx, int n, int n_pad, int ncols, int8_t* shift, void* xc,
-                        cudaStream_t s) {
+template <int OUT>
+static void launch_cast_t(const int8_t* X, int64_t ldx, int n, int n_pad, int ncols, int8_t* shift, void* xc,
+                          cudaStream_t s) {
   const int grid = (ncols + 7) / 8;
   if (n <= 512 * 20)
-    cast_shift_reg_kernel<TF32, 20><<<grid, 256, 0, s>>>(X, ldx, n, n_pad, ncols, shift, xc);
+    cast_shift_reg_kernel<OUT, 20><<<grid, 256, 0, s>>>(X, ldx, n, n_pad, ncols, shift, xc);
   else if (n <= 512 * 32)
-    cast_shift_reg_kernel<TF32, 32><<<grid, 256, 0, s>>>(X, ldx, n, n_pad, ncols, shift, xc);
+    cast_shift_reg_kernel<OUT, 32><<<grid, 256, 0, s>>>(X, ldx, n, n_pad, ncols, shift, xc);
   else
-    cast_shift_kernel<TF32><<<grid, 256, 0, s>>>(X, ldx, n, n_pad, ncols, shift, xc);
+    cast_shift_kernel<OUT><<<grid, 256, 0, s>>>(X, ldx, n, n_pad, ncols, shift, xc);
+}
+
+static void launch_cast(int out, const int8_t* X, int64_t ldx, int n, int n_pad, int ncols, int8_t* shift,
+                        void* xc, cudaStream_t s) {
+  if (out == OUT_F32)
+    launch_cast_t<OUT_F32>(X, ldx, n, n_pad, ncols, shift, xc, s);
+  else if (out == OUT_F16)
+    launch_cast_t<OUT_F16>(X, ldx, n, n_pad, ncols, shift, xc, s);
+  else
+    launch_cast_t<OUT_BF16>(X, ldx, n, n_pad, ncols, shift, xc, s);
 }
 
 // Columns c0.. c0+ncols-1 of the n_pad x n_pad identity as int8, column-major
@@ -238,6 +249,62 @@ __global__ void linv_split_kernel(const float* __restrict__ xt, int64_t ldt, int
       static_cast<__nv_bfloat16*>(hi)[idx] = h;
       static_cast<__nv_bfloat16*>(lo)[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
     }
+  }
+}
+
+// FP16 form of the inverse's pieces.  linv_rows_kernel transposes solved
+// columns of L^-1 into a row-major FP32 copy (upper triangle and padding
+// zeroed, as linv_split_kernel); then per row r, with m_r = max_j |L^-1_rj|,
+// the row is scaled by s_r = 2^(14 - e_r), 2^(e_r - 1) <= m_r < 2^e_r (so
+// |s_r L^-1_rj| < 2^15, inside FP16's range with 11 significant bits for the
+// hi piece and 11 more for the lo piece, both exact FP32 operations), and
+// rscale[r] = 1 / s_r.
+__global__ void linv_rows_kernel(const float* __restrict__ xt, int64_t ldt, int n, int n_pad, int c0, int ncols,
+                                 float* __restrict__ rows32) {
+  __shared__ float tile[32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  const int q0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int q = q0 + ty + 8 * i;
+    tile[ty + 8 * i][tx] = q < ncols ? xt[(int64_t)q * ldt + r0 + tx] : 0.f;
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int row = r0 + ty + 8 * i, q = q0 + tx, gcol = c0 + q;
+    if (q >= ncols) continue;
+    float v = tile[tx][ty + 8 * i];
+    if (row >= n || gcol >= n || gcol > row) v = 0.f;
+    rows32[(int64_t)row * n_pad + gcol] = v;
+  }
+}
+
+// One block per row of L^-1: its scale, then its FP16 hi/lo pieces.
+__global__ void __launch_bounds__(256) linv_split_f16_kernel(const float* __restrict__ rows32, int n_pad,
+                                                             __half* __restrict__ hi, __half* __restrict__ lo,
+                                                             float* __restrict__ rscale) {
+  __shared__ float wmax[8];
+  const int row = blockIdx.x;
+  const float* src = rows32 + (int64_t)row * n_pad;
+  float m = 0.f;
+  for (int j = threadIdx.x; j <= row && j < n_pad; j += 256) m = fmaxf(m, fabsf(src[j]));
+#pragma unroll
+  for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
+  __syncthreads();
+  m = wmax[0];
+#pragma unroll
+  for (int w = 1; w < 8; ++w) m = fmaxf(m, wmax[w]);
+  int e = 0;
+  if (m > 0.f) frexpf(m, &e);  // m = f * 2^e, 0.5 <= f < 1
+  const float sc = ldexpf(1.f, 14 - e);
+  if (threadIdx.x == 0) rscale[row] = ldexpf(1.f, e - 14);
+  for (int j = threadIdx.x; j < n_pad; j += 256) {
+    const float v = src[j] * sc;
+    const __half h = __float2half_rn(v);
+    hi[(int64_t)row * n_pad + j] = h;
+    lo[(int64_t)row * n_pad + j] = __float2half_rn(v - __half2float(h));
   }
 }
 
@@ -352,7 +419,9 @@ struct TcState {
   void* xhhi = nullptr;
   void* xhlo = nullptr;
   CUtensorMap mAhiT, mAloT, mBhiT, mBloT;
-  void* xc = nullptr;  // inverse form: the cast block x - c_i (n_pad x bs, BF16 or FP32)
+  void* xc = nullptr;  // inverse form: the cast block x - c_i (n_pad x bs, BF16, FP32 or FP16)
+  bool f16 = false;           // inverse form with FP16 pieces of L^-1 (row-scaled) and an FP16 cast block
+  float* rscale = nullptr;    // f16: per-row scale of L^-1 (n_pad)
   EncodeTiledFn encode = nullptr;
 };
 
@@ -389,8 +458,10 @@ static cudaError_t build_inverse(TcState* t, const double* Aop, cudaStream_t s, 
 cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_pad, int bs, int num_sms,
                    bool center, DevStatus* st, cudaStream_t s, int64_t* launches, int strip_group, TileMode mode) {
   *out = nullptr;
+  if (split == SPLIT_F16 && mode != TILES_AUTO && mode != TILES_INVERSE) return cudaErrorInvalidValue;
   TcState* t = new TcState;
   t->tf32 = (split == SPLIT_TF32);
+  t->f16 = (split == SPLIT_F16);  // otherwise BF16 (the transpose solve of an FP16 context runs in BF16)
   t->n = n;
   t->n_pad = n_pad;
   t->bs = bs;
@@ -426,6 +497,7 @@ cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_p
   t->mode = mode;
   const bool inv = mode == TILES_INVERSE;
   if (inv) TRY(cudaMalloc(&t->xc, esz * (size_t)n_pad * bs));
+  if (t->f16) TRY(cudaMalloc(&t->rscale, sizeof(float) * (size_t)n_pad));
   if (strip_group > 0 || inv) {
     TRY(cudaMalloc(&t->order, sizeof(uint32_t) * (size_t)t->P * Cmax));
     TRY(cudaMalloc(&t->study_dev, sizeof(TcStudy)));
@@ -456,9 +528,10 @@ cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_p
     TRY(cudaGetLastError());
   }
   const CUtensorMapDataType dt = t->tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const CUtensorMapDataType dta = t->f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16 : dt;  // the operator pieces
   const uint32_t kch = t->tf32 ? Cfg<true>::KCH : Cfg<false>::KCH;
-  TRY(make_map(t->encode, &t->mAhi, dt, t->ahi, n_pad, n_pad, esz * n_pad, kch, TB, true));
-  TRY(make_map(t->encode, &t->mAlo, dt, t->alo, n_pad, n_pad, esz * n_pad, kch, TB, true));
+  TRY(make_map(t->encode, &t->mAhi, dta, t->ahi, n_pad, n_pad, esz * n_pad, kch, TB, true));
+  TRY(make_map(t->encode, &t->mAlo, dta, t->alo, n_pad, n_pad, esz * n_pad, kch, TB, true));
   const void* bhi_base = t->tf32 ? static_cast<const void*>(t->xt32) : t->bhi;
   TRY(make_map(t->encode, &t->mBhi, dt, bhi_base, n_pad, bs, esz * n_pad, kch, TN, true));
   TRY(make_map(t->encode, &t->mBlo, dt, t->blo, n_pad, bs, esz * n_pad, kch, TN, true));
@@ -476,7 +549,7 @@ cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_p
   TRY(make_map(t->encode, &t->mStLo, dt, t->blo, n_pad, bs, esz * n_pad, 32, stc, false));
   TRY(set_kernel_attrs(t->tf32, mode != TILES_SINGLE));
   if (mode != TILES_SINGLE) {
-    TRY(query_clusters(t->tf32, mode, num_sms, &t->max_clusters));
+    TRY(query_clusters(t->tf32, mode, num_sms, &t->max_clusters, t->f16));
     if (t->max_clusters < 1) TRY(cudaErrorLaunchOutOfResources);
   }
 #undef TRY
@@ -512,21 +585,22 @@ static void longest_first(std::vector<UnitKey>& v, std::vector<uint32_t>& order)
   for (const UnitKey& u : v) order.push_back(u.code);
 }
 
+static int cast_out(const TcState* t) { return t->tf32 ? OUT_F32 : (t->f16 ? OUT_F16 : OUT_BF16); }
+
 // Inverse form: the cast block's map (half-width boxes) and the cast
 // pre-pass (with the integer shifts when centering).
 static cudaError_t prepare_cast(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaStream_t s,
                                 int64_t* launches, CUtensorMap* mXcH) {
   const size_t esz = t->tf32 ? 4 : 2;
-  const CUtensorMapDataType dt = t->tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+  const CUtensorMapDataType dt = t->tf32  ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : t->f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                                          : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
   const uint32_t kch = t->tf32 ? Cfg<true>::KCH : Cfg<false>::KCH;
   cudaError_t e = make_map(t->encode, mXcH, dt, t->xc, (uint64_t)t->n_pad, (uint64_t)ncols, esz * t->n_pad, kch,
                            TN / 2, true);
   if (e != cudaSuccess) return e;
   int8_t* sh = t->center ? t->shift : nullptr;
-  if (t->tf32)
-    launch_cast<true>(X, ldx, t->n, t->n_pad, ncols, sh, t->xc, s);
-  else
-    launch_cast<false>(X, ldx, t->n, t->n_pad, ncols, sh, t->xc, s);
+  launch_cast(cast_out(t), X, ldx, t->n, t->n_pad, ncols, sh, t->xc, s);
   ++*launches;
   return cudaGetLastError();
 }
@@ -566,14 +640,15 @@ static cudaError_t prepare_study(TcState* t, const int8_t* X, int64_t ldx, int n
   S->bhi = t->bhi;
   S->blo = t->blo;
   S->ldt = t->ldt;
+  S->rscale = t->f16 ? t->rscale : nullptr;
   return cudaSuccess;
 }
 
 // b.ntiles work units: tiles, or (cluster modes) row-panel pairs of a strip.
 static cudaError_t launch_kernel(bool tf32, TileMode mode, const TcBatch& b, int num_sms, int max_clusters,
-                                 cudaStream_t s, int64_t* launches) {
+                                 cudaStream_t s, int64_t* launches, bool f16 = false) {
   ++*launches;
-  return launch_solve(tf32, mode, b, num_sms, max_clusters, s);
+  return launch_solve(tf32, mode, b, num_sms, max_clusters, s, f16);
 }
 
 cudaError_t run_block(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaStream_t s, int64_t* launches,
@@ -620,7 +695,7 @@ cudaError_t run_block(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaS
     b.order = t->order;
     b.studies = t->study_dev;
   }
-  return launch_kernel(t->tf32, t->mode, b, t->num_sms, t->max_clusters, s, launches);
+  return launch_kernel(t->tf32, t->mode, b, t->num_sms, t->max_clusters, s, launches, t->f16);
 }
 
 // Inverse form set-up: L^-1 = the substitution applied to the identity, on
@@ -634,7 +709,9 @@ static cudaError_t build_inverse(TcState* t, const double* Aop, cudaStream_t s, 
   cudaError_t e = create(&g, SPLIT_TF32, Aop, t->n, np, bsi, t->num_sms, false, t->st, s, launches, 0, TILES_PAIR_MMA);
   if (e != cudaSuccess) return e;
   int8_t* eye = nullptr;
+  float* rows32 = nullptr;  // FP16 pieces: the whole FP32 L^-1, row-major, before the row scales are known
   e = cudaMalloc(&eye, (size_t)np * bsi);
+  if (e == cudaSuccess && t->f16) e = cudaMalloc(&rows32, sizeof(float) * (size_t)np * np);
   for (int c0 = 0; e == cudaSuccess && c0 < np; c0 += bsi) {
     const int nc = np - c0 < bsi ? np - c0 : bsi;
     identity_i8_kernel<<<1184, 256, 0, s>>>(eye, np, c0, nc);
@@ -642,10 +719,18 @@ static cudaError_t build_inverse(TcState* t, const double* Aop, cudaStream_t s, 
     if ((e = cudaGetLastError()) != cudaSuccess) break;
     if ((e = run_block(g, eye, np, nc, s, launches)) != cudaSuccess) break;
     const dim3 grid((nc + 31) / 32, np / 32);
-    if (t->tf32)
+    if (t->f16)
+      linv_rows_kernel<<<grid, dim3(32, 8), 0, s>>>(g->xt32, g->ldt, t->n, np, c0, nc, rows32);
+    else if (t->tf32)
       linv_split_kernel<true><<<grid, dim3(32, 8), 0, s>>>(g->xt32, g->ldt, t->n, np, c0, nc, t->ahi, t->alo);
     else
       linv_split_kernel<false><<<grid, dim3(32, 8), 0, s>>>(g->xt32, g->ldt, t->n, np, c0, nc, t->ahi, t->alo);
+    ++*launches;
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess && t->f16) {
+    linv_split_f16_kernel<<<np, 256, 0, s>>>(rows32, np, static_cast<__half*>(t->ahi), static_cast<__half*>(t->alo),
+                                              t->rscale);
     ++*launches;
     e = cudaGetLastError();
   }
@@ -657,6 +742,7 @@ static cudaError_t build_inverse(TcState* t, const double* Aop, cudaStream_t s, 
       e = cudaErrorLaunchTimeout;  // a bounded wait of the solve expired
   }
   cudaFree(eye);
+  cudaFree(rows32);
   destroy(g);
   return e;
 }
@@ -733,7 +819,7 @@ struct TcBatchState {
   CUtensorMap mX8[MAX_STUDIES], mX8H[MAX_STUDIES], mXcH[MAX_STUDIES] = {};
   const int8_t* X[MAX_STUDIES];
   int64_t ldx[MAX_STUDIES];
-  bool tf32 = false;
+  bool tf32 = false, f16 = false;
   TileMode mode = TILES_SINGLE;
   int num_sms = 0, max_clusters = 0;
   TcStudy* d_studies = nullptr;  // device copies
@@ -747,10 +833,12 @@ cudaError_t batch_create(TcBatchState** out, TcState* const* ts, int nstudies) {
   *out = nullptr;
   if (nstudies < 1 || nstudies > MAX_STUDIES) return cudaErrorInvalidValue;
   for (int i = 1; i < nstudies; ++i)
-    if (ts[i]->tf32 != ts[0]->tf32 || ts[i]->mode != ts[0]->mode) return cudaErrorInvalidValue;
+    if (ts[i]->tf32 != ts[0]->tf32 || ts[i]->f16 != ts[0]->f16 || ts[i]->mode != ts[0]->mode)
+      return cudaErrorInvalidValue;
   TcBatchState* B = new TcBatchState;
   B->nstudies = nstudies;
   B->tf32 = ts[0]->tf32;
+  B->f16 = ts[0]->f16;
   B->mode = ts[0]->mode;
   B->num_sms = ts[0]->num_sms;
   B->max_clusters = ts[0]->max_clusters;
@@ -792,7 +880,10 @@ cudaError_t batch_plan(TcBatchState* B, TcState* const* ts, const int8_t* const*
     if (t->mode == TILES_INVERSE) {
       const size_t esz = t->tf32 ? 4 : 2;
       e = make_map(t->encode, &B->mXcH[i],
-                   t->tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, t->xc,
+                   t->tf32  ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                   : t->f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
+                            : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16,
+                   t->xc,
                    (uint64_t)t->n_pad, (uint64_t)ncols[i], esz * t->n_pad, t->tf32 ? Cfg<true>::KCH : Cfg<false>::KCH,
                    TN / 2, true);
       if (e != cudaSuccess) return e;
@@ -807,6 +898,7 @@ cudaError_t batch_plan(TcBatchState* B, TcState* const* ts, const int8_t* const*
     S[i].bhi = t->bhi;
     S[i].blo = t->blo;
     S[i].ldt = t->ldt;
+    S[i].rscale = t->f16 ? t->rscale : nullptr;
     pmax = unit_rows(t) > pmax ? unit_rows(t) : pmax;
     total += unit_rows(t) * S[i].C;
   }
@@ -854,11 +946,7 @@ cudaError_t batch_launch(TcBatchState* B, TcState* const* ts, cudaStream_t s, in
     if ((e = cudaMemsetAsync(t->sched, 0, 128 + sizeof(int) * (size_t)t->P * B->S[i].C, s)) != cudaSuccess) return e;
     if (t->mode == TILES_INVERSE) {
       int8_t* sh = t->center ? t->shift : nullptr;
-      const int nc = B->S[i].ncols;
-      if (t->tf32)
-        launch_cast<true>(B->X[i], B->ldx[i], t->n, t->n_pad, nc, sh, t->xc, s);
-      else
-        launch_cast<false>(B->X[i], B->ldx[i], t->n, t->n_pad, nc, sh, t->xc, s);
+      launch_cast(cast_out(t), B->X[i], B->ldx[i], t->n, t->n_pad, B->S[i].ncols, sh, t->xc, s);
       ++*launches;
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     } else if (t->center) {
@@ -886,7 +974,7 @@ cudaError_t batch_launch(TcBatchState* B, TcState* const* ts, cudaStream_t s, in
   b.ntiles = B->ntiles;
   b.counter = B->d_counter;
   b.st = B->st;
-  return launch_kernel(B->tf32, B->mode, b, B->num_sms, B->max_clusters, s, launches);
+  return launch_kernel(B->tf32, B->mode, b, B->num_sms, B->max_clusters, s, launches, B->f16);
 }
 
 void batch_destroy(TcBatchState* B) {
@@ -927,6 +1015,7 @@ void destroy(TcState* t) {
   cudaFree(t->bhi);
   cudaFree(t->blo);
   cudaFree(t->xc);
+  cudaFree(t->rscale);
   cudaFree(t->sched);
   cudaFree(t->shift);
   cudaFree(t->order);

@@ -50,6 +50,7 @@ struct TcStudy {
   void* bhi;            // BF16 mode: hi piece of X~
   void* blo;            // lo piece of X~ (BF16 or FP32)
   int64_t ldt;
+  const float* rscale;  // inverse form with FP16 pieces: row r of L^-1 was split scaled by 1 / rscale[r]
 };
 
 // The tensor maps of one study: block operator hi/lo, X~ hi/lo, int8 block.
@@ -91,13 +92,14 @@ constexpr int ST_COLS = 16;  // SNP columns per inverse-form store chunk (32 row
 // Launch entry points of the kernels (trsm_tc.cu).
 // Opt-in shared memory of the forward kernels (clusters: also the pair and
 // inverse-form kernels) and of the transpose solve.
+// f16: the inverse form's FP16 variant (TILES_INVERSE only, tf32 false).
 cudaError_t set_kernel_attrs(bool tf32, bool clusters);
 cudaError_t set_upper_attr(bool tf32);
 // Co-resident 2-CTA clusters of a cluster-mode kernel (one CTA per SM).
-cudaError_t query_clusters(bool tf32, TileMode mode, int num_sms, int* out);
+cudaError_t query_clusters(bool tf32, TileMode mode, int num_sms, int* out, bool f16 = false);
 // One launch over b.ntiles work units (tiles, or row-panel pairs of a strip).
 cudaError_t launch_solve(bool tf32, TileMode mode, const TcBatch& b, int num_sms, int max_clusters,
-                         cudaStream_t s);
+                         cudaStream_t s, bool f16 = false);
 // The transpose solve of the adjoint form (single CTAs, grid CTAs).
 cudaError_t launch_upper(bool tf32, const TcBatch& b, int grid, cudaStream_t s);
 

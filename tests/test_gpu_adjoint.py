@@ -86,11 +86,11 @@ def test_adjoint_paper_scale_n5000():
 # cores (BF16x3 / TF32x3 operands, FP32 accumulation) and the per-SNP adjoint
 # arithmetic in FP64; its errors against the FP64 oracle are stated here per
 # result.
-SPLIT_ADJ_TOL = {"bf16x3": 1e-4, "tf32x3": 2e-5}
+SPLIT_ADJ_TOL = {"bf16x3": 1e-4, "tf32x3": 2e-5, "f16x2": 1e-4}  # f16x2: its transpose solve is BF16x3
 
 
-@pytest.mark.parametrize("tiles", ["auto", "inverse"])
-@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+@pytest.mark.parametrize("prec,tiles", [("bf16x3", "pair_mma"), ("bf16x3", "inverse"), ("tf32x3", "pair_mma"),
+                                        ("tf32x3", "inverse"), ("f16x2", "inverse")])
 @pytest.mark.parametrize("n,p,m,h,sigma2", [(300, 4, 300, 0.5, 1.3), (1000, 3, 513, 0.7, 1.0)])
 def test_split_adjoint_matches_oracle(prec, n, p, m, h, sigma2, tiles):
     s = gwas_synth.study(n, p, 2 * n, h, sigma2, seed=6)

@@ -31,8 +31,8 @@ def _studies(prec, bs=512, tiles="auto"):
     return out
 
 
-@pytest.mark.parametrize("tiles", ["auto", "inverse"])
-@pytest.mark.parametrize("prec", ["bf16x3", "tf32x3"])
+@pytest.mark.parametrize("prec,tiles", [("bf16x3", "auto"), ("bf16x3", "pair_mma"), ("tf32x3", "auto"),
+                                        ("tf32x3", "pair_mma"), ("f16x2", "auto")])
 def test_batch_matches_single_and_oracle(prec, tiles):
     studies = _studies(prec, tiles=tiles)
     gls = [g for _, g in studies]

@@ -143,14 +143,18 @@ def test_stream_matches_blocks(small_study):
 
 # ---------------------------------------------------------------- split precision
 TOL_SPLIT = 1e-5
-SPLITS = ("bf16x3", "tf32x3")
+SPLITS = ("bf16x3", "tf32x3", "f16x2")
 # how the tensor-core solve's tiles map onto SMs: one per SM, row-panel pairs on
-# a 2-SM cluster with shared loads, row-panel pairs as one 256-row product
+# a 2-SM cluster with shared loads, row-panel pairs as one 256-row product (the
+# substitution), and the product with L^-1 formed at set-up
 TILES = ("single", "pair_multicast", "pair_mma", "inverse")
+# f16x2 exists in the inverse form only
+SPLIT_TILES = [(p, t) for p in SPLITS for t in TILES if p != "f16x2" or t == "inverse"]
+FULL_CASES = [("fp64", "auto")] + [(p, t) for p in SPLITS for t in ("auto",) + TILES
+                                   if p != "f16x2" or t in ("auto", "inverse")]
 
 
-@pytest.mark.parametrize("tiles", TILES)
-@pytest.mark.parametrize("prec", SPLITS)
+@pytest.mark.parametrize("prec,tiles", SPLIT_TILES)
 def test_split_precision_parity(small_study, prec, tiles):
     s, X, L, (r, se, st) = small_study
     with gw.GLS(s["Phi"], s["XL"], s["y"], s["h"], s["sigma2"], precision=prec, bs=1024, tiles=tiles) as g:
@@ -165,8 +169,7 @@ def test_split_precision_parity(small_study, prec, tiles):
     assert e["b_norm"] <= TOL_SPLIT and e["se_rel"] <= TOL_SPLIT, e
 
 
-@pytest.mark.parametrize("tiles", TILES)
-@pytest.mark.parametrize("prec", SPLITS)
+@pytest.mark.parametrize("prec,tiles", SPLIT_TILES)
 @pytest.mark.parametrize("n,p,m", [(1, 1, 3), (127, 4, 63), (129, 2, 257), (300, 7, 300), (1000, 4, 513),
                                    (1200, 3, 300)])
 def test_split_ragged_shapes(prec, tiles, n, p, m):
@@ -180,8 +183,7 @@ def test_split_ragged_shapes(prec, tiles, n, p, m):
     assert e["b_norm"] <= TOL_SPLIT and e["se_rel"] <= TOL_SPLIT, (prec, tiles, e)
 
 
-@pytest.mark.parametrize("tiles", TILES)
-@pytest.mark.parametrize("prec", SPLITS)
+@pytest.mark.parametrize("prec,tiles", SPLIT_TILES)
 def test_split_grouped_tile_order(small_study, prec, tiles):
     """Tiles handed out over groups of 2 column strips (a device order table; in
     the pair modes its rows are row-panel pairs): same parity."""
@@ -191,6 +193,13 @@ def test_split_grouped_tile_order(small_study, prec, tiles):
         b, se_g, st_g = g.solve_block(X[:, :1000])
     e = compare(b, se_g, st_g, r[:, :1000], se[:, :1000], st[:1000])
     assert e["b_norm"] <= TOL_SPLIT and e["se_rel"] <= TOL_SPLIT, (prec, tiles, e)
+
+
+@pytest.mark.parametrize("tiles", ("single", "pair_multicast", "pair_mma"))
+def test_f16x2_needs_the_inverse_form(small_study, tiles):
+    s, *_ = small_study
+    with pytest.raises(gw.GwasError):
+        gw.GLS(s["Phi"], s["XL"], s["y"], s["h"], s["sigma2"], precision="f16x2", bs=256, tiles=tiles)
 
 
 @pytest.mark.parametrize("prec", SPLITS)
@@ -280,7 +289,7 @@ def paper_scale_sample(paper_scale):
     return Xs, ref
 
 
-@pytest.mark.parametrize("prec,tiles", [("fp64", "auto")] + [(p, t) for p in SPLITS for t in ("auto",) + TILES])
+@pytest.mark.parametrize("prec,tiles", FULL_CASES)
 def test_full_size_seeded_sample(paper_scale, paper_scale_sample, prec, tiles):
     """The 2,000 sampled SNPs solved as one block, every one against the oracle."""
     import torch
@@ -299,17 +308,18 @@ def test_full_size_seeded_sample(paper_scale, paper_scale_sample, prec, tiles):
         # stricter extra: component by component on components with |b_j| >= se_j.
         # BF16x3 operands carry ~17 bits (hi + lo of 8 each): the dropped lo*lo term
         # and the representation residual are each ~2^-18, and the worst component
-        # of the 2,000 SNPs sits at ~1.1e-5; TF32x3 (~22 bits) stays near 2e-6
+        # of the 2,000 SNPs sits at ~1.1e-5; TF32x3 (~22 bits) stays near 2e-6; F16x2's
+        # pieces carry ~22 bits as well
         assert e["b_comp_max"] <= COMP_TOL[prec], (prec, tiles, e)
 
 
 # b: per-SNP normwise relative error (the stated bar: 1e-10 FP64, 1e-5 split);
 # se: component-wise relative error, same bars.
-FULL_TOL = {"fp64": (1e-10, 1e-10), "bf16x3": (1e-5, 1e-5), "tf32x3": (1e-5, 1e-5)}
-COMP_TOL = {"bf16x3": 2e-5, "tf32x3": 1e-5}
+FULL_TOL = {"fp64": (1e-10, 1e-10), "bf16x3": (1e-5, 1e-5), "tf32x3": (1e-5, 1e-5), "f16x2": (1e-5, 1e-5)}
+COMP_TOL = {"bf16x3": 2e-5, "tf32x3": 1e-5, "f16x2": 1e-5}
 
 
-@pytest.mark.parametrize("prec,tiles", [("fp64", "auto")] + [(p, t) for p in SPLITS for t in ("auto",) + TILES])
+@pytest.mark.parametrize("prec,tiles", FULL_CASES)
 def test_full_size_sampled(paper_scale, prec, tiles):
     import torch
     w, s, first, last, pf, pl, ref_first, ref_last = paper_scale
