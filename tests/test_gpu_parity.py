@@ -195,6 +195,23 @@ def test_split_grouped_tile_order(small_study, prec, tiles):
     assert e["b_norm"] <= TOL_SPLIT and e["se_rel"] <= TOL_SPLIT, (prec, tiles, e)
 
 
+@pytest.mark.parametrize("prec", SPLITS)
+@pytest.mark.parametrize("sigma2", (1e-6, 1e4))
+def test_split_extreme_sigma2(prec, sigma2):
+    """L^-1 scales as sigma2^-1/2 (entries ~1e3 and ~1e-2 here): the FP16 pieces
+    of f16x2 keep their precision through the per-row power-of-two scaling
+    (unscaled, 1e-2-sized entries would put the lo pieces among FP16's
+    subnormals); b does not depend on sigma2, se scales with its square root.
+    (At sigma2 = 1e6 the noise-dominated fit amplifies the operand error:
+    BF16x3 reaches 8e-6 normwise there, TF32x3 and F16x2 5e-7.)"""
+    s, X, L, (r, se, st) = _case(640, 4, 1280, 0.5, sigma2=sigma2, m=300)
+    with gw.GLS(s["Phi"], s["XL"], s["y"], 0.5, sigma2, precision=prec, bs=300) as g:
+        b, se_g, st_g = g.solve_block(X)
+    e = compare(b, se_g, st_g, r, se, st)
+    print(prec, sigma2, e)
+    assert e["b_norm"] <= TOL_SPLIT and e["se_rel"] <= TOL_SPLIT, (prec, sigma2, e)
+
+
 @pytest.mark.parametrize("tiles", ("single", "pair_multicast", "pair_mma"))
 def test_f16x2_needs_the_inverse_form(small_study, tiles):
     s, *_ = small_study
