@@ -45,7 +45,9 @@ struct gwas_ctx {
   double* Xhat = nullptr;      // n_pad x bs: X^ = L^-T X~
   double* What = nullptr;      // n_pad x (q+1): [X^_L | y^]
   double* GH = nullptr;        // (q+1)^2 Gram of What
-  double* adj = nullptr;       // per-SNP chi2 (bs), dh (bs), y-weights (bs x p), uT (q), dh/dy staging (1 + n)
+  float* Wh32 = nullptr;       // split contexts: What in FP32, row-major (row stride w32_stride(q))
+  double* adj = nullptr;       // per-SNP chi2 (bs), dh (bs), y-weights (bs x p), uT (q), dh/dy staging (1 + n),
+                               // the y-gradient's chunk partials (adjoint_dy_chunks(bs) x n)
   // pinned host buffers of the file reader, kept across gwas_solve_file calls
   std::vector<void*> file_buf;
   int64_t file_buf_bytes = 0;
@@ -187,11 +189,18 @@ int ensure_adjoint(gwas_ctx* ctx) {
   CK(dmalloc(&ctx->Xhat, sizeof(double) * np * std::max(ctx->bs, nc)));
   CK(dmalloc(&ctx->What, sizeof(double) * np * nc));
   CK(dmalloc(&ctx->GH, sizeof(double) * nc * nc));
-  CK(dmalloc(&ctx->adj, sizeof(double) * ((size_t)ctx->bs * (2 + ctx->p) + QMAX + 1 + ctx->n)));
+  CK(dmalloc(&ctx->adj, sizeof(double) * ((size_t)ctx->bs * (2 + ctx->p) + QMAX + 1 + ctx->n +
+                                           (size_t)adjoint_dy_chunks(ctx->bs) * ctx->n)));
   int rc = solve_f64_cols(ctx, ctx->W, ctx->n_pad, ctx->n_pad, nc, ctx->What, true);
   if (rc != GWAS_OK) return rc;
   CK(launch_gram(ctx->What, ctx->n_pad, ctx->n_pad, nc, ctx->GH, ctx->stream));
   ctx->launches += 1;
+  if (ctx->prec != GWAS_FP64 && ctx->q <= 7) {  // the FP32 adjoint sums of the split paths
+    CK(dmalloc(&ctx->Wh32, sizeof(float) * np * w32_stride(ctx->q)));
+    CK(launch_make_w32(ctx->What, ctx->n_pad, ctx->n_pad, ctx->q, ctx->Wh32, ctx->stream));
+    CK(prepare_adjoint_f32());
+    ctx->launches += 1;
+  }
   return GWAS_OK;
 }
 
@@ -303,7 +312,7 @@ void free_all(gwas_ctx* c) {
   cudaFree(c->L); cudaFree(c->Dinv); cudaFree(c->Aop); cudaFree(c->W); cudaFree(c->G);
   cudaFree(c->sc); cudaFree(c->st); cudaFree(c->Xt); cudaFree(c->sched);
   cudaFree(c->d_b); cudaFree(c->d_se); cudaFree(c->d_status); cudaFree(c->f64_in); cudaFree(c->W32);
-  cudaFree(c->AopT); cudaFree(c->Xhat); cudaFree(c->What); cudaFree(c->GH); cudaFree(c->adj);
+  cudaFree(c->AopT); cudaFree(c->Xhat); cudaFree(c->What); cudaFree(c->GH); cudaFree(c->adj); cudaFree(c->Wh32);
   cudaFreeHost(c->h_b); cudaFreeHost(c->h_se); cudaFreeHost(c->h_status);
   if (c->tcs) tc::destroy(c->tcs);
   for (auto* p : c->file_buf) cudaFreeHost(p);
@@ -705,6 +714,7 @@ int gwas_adjoint_block(gwas_ctx* ctx, const int8_t* XR, int64_t ldx, int ncols, 
   double* d_w = d_dh + bs;
   double* d_uT = d_w + (size_t)bs * p;
   double* d_acc = d_uT + QMAX;  // [dh, dy...] staging for host accumulators
+  double* d_dypart = d_acc + 1 + n;  // the y-gradient's per-chunk partial sums
   const bool dev_acc = is_device_ptr(dh_accum) && is_device_ptr(dy_accum);
   double* acc_dh = dev_acc ? dh_accum : d_acc;
   double* acc_dy = dev_acc ? dy_accum : d_acc + 1;
@@ -722,10 +732,13 @@ int gwas_adjoint_block(gwas_ctx* ctx, const int8_t* XR, int64_t ldx, int ncols, 
     xin = ctx->ring[0];
     ld_in = ctx->n_pad;
   }
+  bool f32_sums = false;
   if (split) {
     // the split adjoint: X~ and X^ = L^-T X~ on the tensor cores (both on the
-    // integer-shifted SNP columns), widened to FP64 with the shift undone;
-    // the per-SNP adjoint arithmetic below stays FP64
+    // integer-shifted SNP columns).  Their sums come straight from FP32 (the
+    // shift undone exactly through the Gram matrices) when q <= 7; otherwise
+    // they are widened to FP64 with the shift undone.  The per-SNP adjoint
+    // arithmetic stays FP64.
     int64_t nl = 0;
     cudaError_t e;
     {
@@ -737,11 +750,22 @@ int gwas_adjoint_block(gwas_ctx* ctx, const int8_t* XR, int64_t ldx, int ncols, 
     ctx->launches += nl;
     if (e != cudaSuccess) return fail(ctx, GWAS_ERR_CUDA, "split adjoint solves: %s", cudaGetErrorString(e));
     const int8_t* sh = tc::shift_of(ctx->tcs);
-    CK(launch_widen(tc::xt_f32(ctx->tcs), tc::xt_ld(ctx->tcs), ctx->Xt, ctx->n_pad, ctx->n_pad, ncols, sh, ctx->W,
-                    ctx->stream));
-    CK(launch_widen(tc::xhat_f32(ctx->tcs), tc::xt_ld(ctx->tcs), ctx->Xhat, ctx->n_pad, ctx->n_pad, ncols, sh,
-                    ctx->What, ctx->stream));
-    ctx->launches += 2;
+    f32_sums = ctx->Wh32 != nullptr && ctx->n_pad % 128 == 0 &&
+               (ncols + std::min(ncols, ctx->num_sms) - 1) / std::min(ncols, ctx->num_sms) <= 128;
+    if (f32_sums) {
+      StageMark m(ctx, GWAS_STAGE_REDUCE, ctx->stream);
+      CK(launch_adjoint_f32(tc::xt_reduce_map(ctx->tcs), tc::xhat_reduce_map(ctx->tcs), tc::xhat_f32(ctx->tcs),
+                            tc::xt_ld(ctx->tcs), ctx->n_pad, n, ctx->W32, ctx->Wh32, ctx->G, ctx->What, ctx->n_pad,
+                            ctx->GH, ctx->sc, sh, ctx->q, ncols, ctx->h, ctx->sigma2, d_chi2, d_dh, d_w, d_uT, acc_dh,
+                            acc_dy, d_dypart, ctx->st, ctx->num_sms, ctx->stream));
+      ctx->launches += 4;
+    } else {
+      CK(launch_widen(tc::xt_f32(ctx->tcs), tc::xt_ld(ctx->tcs), ctx->Xt, ctx->n_pad, ctx->n_pad, ncols, sh, ctx->W,
+                      ctx->stream));
+      CK(launch_widen(tc::xhat_f32(ctx->tcs), tc::xt_ld(ctx->tcs), ctx->Xhat, ctx->n_pad, ctx->n_pad, ncols, sh,
+                      ctx->What, ctx->stream));
+      ctx->launches += 2;
+    }
   } else {
     const int C64 = (ncols + F64_TN - 1) / F64_TN;
     CK(cudaMemsetAsync(ctx->sched, 0, sizeof(Sched) + sizeof(int) * (size_t)ctx->P * C64, ctx->stream));
@@ -760,11 +784,12 @@ int gwas_adjoint_block(gwas_ctx* ctx, const int8_t* XR, int64_t ldx, int ncols, 
     StageMark m(ctx, GWAS_STAGE_TRSM, ctx->stream);
     if ((rc = solve_f64_cols(ctx, ctx->Xt, ctx->n_pad, ctx->n_pad, ncols, ctx->Xhat, true)) != GWAS_OK) return rc;
   }
-  {
+  if (!f32_sums) {
     StageMark m(ctx, GWAS_STAGE_REDUCE, ctx->stream);
     CK(launch_adjoint(ctx->Xt, ctx->Xhat, ctx->n_pad, ctx->n_pad, n, ctx->W, ctx->What, ctx->n_pad, ctx->sc, ctx->GH,
-                      ctx->q, ncols, ctx->h, ctx->sigma2, d_chi2, d_dh, d_w, d_uT, acc_dh, acc_dy, ctx->stream));
-    ctx->launches += 3;
+                      ctx->q, ncols, ctx->h, ctx->sigma2, d_chi2, d_dh, d_w, d_uT, acc_dh, acc_dy, d_dypart,
+                      ctx->stream));
+    ctx->launches += 4;
   }
   if (chi2)
     CK(cudaMemcpyAsync(chi2, d_chi2, sizeof(double) * ncols, cudaMemcpyDefault, ctx->stream));

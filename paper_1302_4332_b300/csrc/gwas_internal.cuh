@@ -145,7 +145,21 @@ cudaError_t launch_widen(const float* src, int64_t lds, double* dst, int64_t ldd
 cudaError_t launch_adjoint(const double* Xt, const double* Xh, int64_t ldt, int rows, int n, const double* W,
                            const double* Wh, int64_t ldw, const SolveConsts* sc, const double* GH, int q,
                            int ncols, double h, double sigma2, double* chi2, double* dh, double* wv, double* uT,
-                           double* dh_accum, double* dy_accum, cudaStream_t s);
+                           double* dh_accum, double* dy_accum, double* dy_part, cudaStream_t s);
+// Scratch of the y-gradient: adjoint_dy_chunks(bs) x n doubles (dy_part).
+int adjoint_dy_chunks(int bs);
+// The same from the split solves' FP32 X~ and X^ of the integer-shifted SNP
+// columns (tiled maps of both with box {RED_BOX_ROWS, RED_BOX_COLS}; Xh32 the
+// X^ buffer itself), W32 / Wh32 the FP32 row-major copies of W and What
+// (row stride w32_stride(q)), G and GH their FP64 Gram matrices, shift the
+// per-SNP shifts (or null).  q <= 7; one persistent block per SM.
+cudaError_t launch_adjoint_f32(const CUtensorMap* xtmap, const CUtensorMap* xhmap, const float* Xh32, int64_t ldt,
+                               int rows, int n, const float* W32, const float* Wh32, const double* G,
+                               const double* Wh, int64_t ldw, const double* GH, const SolveConsts* sc,
+                               const int8_t* shift, int q, int ncols, double h, double sigma2, double* chi2,
+                               double* dh, double* wv, double* uT, double* dh_accum, double* dy_accum,
+                               double* dy_part, DevStatus* st, int num_sms, cudaStream_t s);
+cudaError_t prepare_adjoint_f32();
 cudaError_t launch_log_diag(const double* L, int64_t ld, int n, double* out, cudaStream_t s);
 cudaError_t launch_col_sumsq(const double* X, int64_t ld, int n, int ncols, double* out, cudaStream_t s);
 cudaError_t launch_identity_cols(double* E, int n, int c0, int ncols, cudaStream_t s);

@@ -293,23 +293,6 @@ __global__ void __launch_bounds__(32 * SL) reduce_solve_f32_kernel(
 constexpr int BCW = 16, BG = 2 * BCW, BCH = 2 * RED_BOX_ROWS, BMAXC = 128;  // BMAXC: most columns per block
 static_assert(BG == RED_BOX_COLS, "one tiled load spans the group's columns");
 
-// (hi, lo) + (bh, bl) as a double-FP32 pair (TwoSum on the high parts).
-__device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl) {
-  const float s = hi + bh;
-  const float bb = s - hi;
-  const float err = (hi - (s - bb)) + (bh - bb);
-  const float l = lo + bl + err;
-  hi = s + l;
-  lo = l - (hi - s);
-}
-
-// After a failed (timed-out or aborted) wait: 2 ms for bulk copies already in
-// flight to land, so that none writes shared memory of a retired block.
-__device__ __forceinline__ void settle() {
-  const long long t0 = ptx::globaltimer();
-  while (ptx::globaltimer() - t0 < 2000000LL) {
-  }
-}
 
 template <int WS>
 struct BulkCfg {
@@ -356,7 +339,7 @@ __global__ void __launch_bounds__(32 * (BCW + 1), 1) reduce_solve_bulk_kernel(
           const int s = it % BST;
           const uint32_t r = it / BST;
           if (!ptx::mbar_wait(&empty[s], (r & 1) ^ 1, st)) {
-            settle();  // copies already issued land before the block retires
+            ptx::settle();  // copies already issued land before the block retires
             return;
           }
           const int rt = rows - t * BCH < BCH ? rows - t * BCH : BCH;
@@ -444,7 +427,7 @@ __global__ void __launch_bounds__(32 * (BCW + 1), 1) reduce_solve_bulk_kernel(
           float hi = ks[u][a], lo = -kc[u][a];
 #pragma unroll
           for (int o = 16; o; o >>= 1)
-            df_add(hi, lo, __shfl_xor_sync(0xffffffffu, hi, o), __shfl_xor_sync(0xffffffffu, lo, o));
+            ptx::df_add(hi, lo, __shfl_xor_sync(0xffffffffu, hi, o), __shfl_xor_sync(0xffffffffu, lo, o));
           if (lane == 0) colsum[ca + u - c_begin][a] = (double)hi + (double)lo;
         }
       }
@@ -452,7 +435,7 @@ __global__ void __launch_bounds__(32 * (BCW + 1), 1) reduce_solve_bulk_kernel(
   }
   // every consumer warp is done (or gave up); the solves, one lane per column
   if (!ptx::group_and(1, 32 * BCW, ok)) {
-    settle();  // copies already issued land before the block retires
+    ptx::settle();  // copies already issued land before the block retires
     return;
   }
   for (int j = threadIdx.x; j < c_end - c_begin; j += 32 * BCW) {

@@ -439,5 +439,24 @@ __device__ __forceinline__ void named_bar(int id, int count) {
   asm volatile("bar.sync %0, %1;" ::"r"(id), "r"(count) : "memory");
 }
 
+// (hi, lo) + (bh, bl) as a double-FP32 pair (TwoSum on the high parts): sums
+// at twice FP32's precision without B300's narrow FP64 pipe.
+__device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl) {
+  const float s = hi + bh;
+  const float bb = s - hi;
+  const float err = (hi - (s - bb)) + (bh - bb);
+  const float l = lo + bl + err;
+  hi = s + l;
+  lo = l - (hi - s);
+}
+
+// After a failed (timed-out or aborted) wait: 2 ms for bulk copies already in
+// flight to land, so that none writes shared memory of a retired block.
+__device__ __forceinline__ void settle() {
+  const long long t0 = globaltimer();
+  while (globaltimer() - t0 < 2000000LL) {
+  }
+}
+
 }  // namespace ptx
 }  // namespace gwas

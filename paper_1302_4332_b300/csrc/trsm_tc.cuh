@@ -71,6 +71,7 @@ constexpr int kMaxBatchStudies = 8;
 cudaError_t ensure_transpose(TcState* t, const double* AopT, cudaStream_t s, int64_t* launches);
 cudaError_t run_transpose(TcState* t, int ncols, cudaStream_t s, int64_t* launches);
 const float* xhat_f32(const TcState* t);
+const CUtensorMap* xhat_reduce_map(const TcState* t);  // xhat_f32() as the reduction's tiled map
 
 const float* xt_f32(const TcState* t);
 const CUtensorMap* xt_reduce_map(const TcState* t);  // xt_f32() as the reduction's tiled map

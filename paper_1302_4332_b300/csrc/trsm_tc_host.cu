@@ -411,6 +411,7 @@ struct TcState {
   CUtensorMap mAhi, mAlo, mBhi, mBlo, mBhiH, mBloH;
   CUtensorMap mStX, mStHi, mStLo;  // pair product's epilogue stores
   CUtensorMap mRed;                // the reduction's view of the FP32 X~ (box RED_BOX_ROWS x RED_BOX_COLS)
+  CUtensorMap mRedH;               // the same over the transpose solve's X^
   // transpose solve (the adjoint form): the transpose block operator split hi/lo,
   // X^ = L^-T X~ in FP32 + pieces, and their maps
   void* ahiT = nullptr;
@@ -770,7 +771,9 @@ cudaError_t ensure_transpose(TcState* t, const double* AopT, cudaStream_t s, int
   if ((e = make_map(t->encode, &t->mAhiT, dt, t->ahiT, np, np, esz * np, kch, TB, true)) != cudaSuccess ||
       (e = make_map(t->encode, &t->mAloT, dt, t->aloT, np, np, esz * np, kch, TB, true)) != cudaSuccess ||
       (e = make_map(t->encode, &t->mBhiT, dt, bhi, np, t->bs, esz * np, kch, TN, true)) != cudaSuccess ||
-      (e = make_map(t->encode, &t->mBloT, dt, t->xhlo, np, t->bs, esz * np, kch, TN, true)) != cudaSuccess)
+      (e = make_map(t->encode, &t->mBloT, dt, t->xhlo, np, t->bs, esz * np, kch, TN, true)) != cudaSuccess ||
+      (e = make_map(t->encode, &t->mRedH, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, t->xh32, np, t->bs, 4 * np, RED_BOX_ROWS,
+                    RED_BOX_COLS, false)) != cudaSuccess)
     return e;
   return set_upper_attr(t->tf32);
 }
@@ -987,6 +990,7 @@ void batch_destroy(TcBatchState* B) {
 
 const float* xt_f32(const TcState* t) { return t->xt32; }
 const CUtensorMap* xt_reduce_map(const TcState* t) { return &t->mRed; }
+const CUtensorMap* xhat_reduce_map(const TcState* t) { return &t->mRedH; }
 const int8_t* shift_of(const TcState* t) { return t->center ? t->shift : nullptr; }
 int64_t xt_ld(const TcState* t) { return t->ldt; }
 TileMode tile_mode(const TcState* t) { return t->mode; }
