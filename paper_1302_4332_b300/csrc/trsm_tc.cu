@@ -56,7 +56,7 @@ __device__ __forceinline__ void decode_tile(const TcBatch& b, int t, int& s, int
     s = (int)(v >> 28);
     k = (int)((v >> 14) & 0x3FFFu);
     c = (int)(v & 0x3FFFu);
-    S = b.studies[s];
+    S = b.studies ? b.studies[s] : b.s0;  // one study: its descriptor travels in the launch parameters
   } else {
     S = b.s0;
     s = 0;

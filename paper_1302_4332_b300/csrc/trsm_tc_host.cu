@@ -403,7 +403,6 @@ struct TcState {
   TileMode mode = TILES_SINGLE;    // how tiles map onto CTAs
   int max_clusters = 0;            // pair modes: co-resident 2-CTA clusters of the kernel
   uint32_t* order = nullptr;      // device tile order when strip_group > 0
-  TcStudy* study_dev = nullptr;   // device copy of the study descriptor (grouped order)
   int order_C = -1;               // the column-strip count the order was built for
   unsigned int* sched = nullptr;  // [0] counter, flags from +32
   size_t sched_bytes = 0;
@@ -501,7 +500,6 @@ cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_p
   if (t->f16) TRY(cudaMalloc(&t->rscale, sizeof(float) * (size_t)n_pad));
   if (strip_group > 0 || inv) {
     TRY(cudaMalloc(&t->order, sizeof(uint32_t) * (size_t)t->P * Cmax));
-    TRY(cudaMalloc(&t->study_dev, sizeof(TcStudy)));
   }
   t->sched_bytes = 128 + sizeof(int) * (size_t)t->P * Cmax;
   TRY(cudaMalloc(&t->sched, t->sched_bytes));
@@ -691,10 +689,7 @@ cudaError_t run_block(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaS
         return e;
       t->order_C = b.s0.C;
     }
-    // the grouped order reads the study descriptor from device memory
-    if ((e = cudaMemcpyAsync(t->study_dev, &b.s0, sizeof(TcStudy), cudaMemcpyHostToDevice, s)) != cudaSuccess) return e;
-    b.order = t->order;
-    b.studies = t->study_dev;
+    b.order = t->order;  // the study descriptor stays b.s0 (studies null)
   }
   return launch_kernel(t->tf32, t->mode, b, t->num_sms, t->max_clusters, s, launches, t->f16);
 }
@@ -1023,7 +1018,6 @@ void destroy(TcState* t) {
   cudaFree(t->sched);
   cudaFree(t->shift);
   cudaFree(t->order);
-  cudaFree(t->study_dev);
   delete t;
 }
 }  // namespace tc

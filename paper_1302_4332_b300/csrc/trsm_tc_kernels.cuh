@@ -69,7 +69,7 @@ struct TcMaps {
 struct TcBatch {
   TcMaps maps[MAX_STUDIES];
   TcStudy s0;                 // the study when there is only one (order == null)
-  const TcStudy* studies;     // device copies of the studies when order != null
+  const TcStudy* studies;     // device copies of the studies when order != null (null: s0 alone)
   const uint32_t* order;      // tile t -> (study << 28) | (k << 14) | c
   int nstudies, ntiles;
   int pieces;                 // inverse form: also store the hi/lo pieces of X~ (the adjoint's input)
