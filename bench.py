@@ -480,8 +480,17 @@ def measure_forms(args, out):
             for _ in range(reps):
                 g.solve_file(path, m)
             t = time.perf_counter() - t1
+            # disk to disk: the same columns with the results written back (and checkpointed)
+            out_path = os.path.join(td, "results.bin")
+            t1 = time.perf_counter()
+            done = g.solve_file_out(path, m, out_path)
+            t_out = time.perf_counter() - t1
         forms["disk_e2e"] = dict(snps_per_s=reps * m / t, snps=m * reps, bytes_read=reps * m * n,
                                  note="file just written: served from the page cache")
+        forms["disk_to_disk_e2e"] = dict(snps_per_s=done / t_out, snps=done, bytes_read=done * n,
+                                         bytes_written=64 + done * (16 * w["p"] + 8),
+                                         note="gwas_solve_file_out: results written to a file with checkpoints "
+                                              "every 16 blocks (fdatasync); input from the page cache")
     # --- the differentiation workload: n = 5,000, p = 4, FP64 adjoint of one 4096-SNP block
     s4 = gwas_synth.study(5000, 4, 5000, 0.5, 1.0, study_id=4)
     X4 = torch.from_numpy(np.ascontiguousarray(gwas_synth.dosages(5000, 0, 4096, study=4).T)).to(dev).T

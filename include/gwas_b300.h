@@ -270,6 +270,27 @@ void gwas_batch_destroy(gwas_batch *B);
 int gwas_solve_file(gwas_ctx *ctx, const char *path, int64_t header_bytes, int64_t ldx, int64_t col0, int64_t m,
                     double *b_host, double *se_host, int *status_host);
 
+/* Disk to disk, resumable (Sec. 3.1's streaming with the results written back):
+ * columns col0 .. col0+m-1 of the dosage file, as in gwas_solve_file, with the
+ * results of column col0 + j written to out_path as record j:
+ *   out_path = a 64-byte header, then m records of GWAS_RESULT_RECORD_BYTES(p) bytes;
+ *   header: char magic[8] = "GWASRES\0", uint32 version (1), uint32 p, uint64 n,
+ *           uint64 col0, uint64 m, uint32 record_bytes, uint32 precision, 16 bytes 0;
+ *   record: double b[p], double se[p], int32 status, int32 0 (little-endian).
+ * A checkpoint file out_path + ".ckpt" (the same header with magic "GWASCKP\0"
+ * and, at byte 48, uint64 done) advances every 16 blocks and at the end, each
+ * time after the records it covers were flushed to disk (fdatasync).  With
+ * flags & GWAS_RESUME the run continues from the checkpoint's `done` column
+ * (rewriting at most the blocks after it; a missing checkpoint starts at 0); a
+ * checkpoint of another run (p, n, col0, m, precision) is GWAS_ERR_ARG.
+ * *done_out (may be NULL) = the columns on disk when the call returns.
+ * Errors: GWAS_ERR_IO (the input as in gwas_solve_file; creating or writing the
+ * output or checkpoint), and those of gwas_solve_file. */
+#define GWAS_RESUME 1
+#define GWAS_RESULT_RECORD_BYTES(p) (16 * (p) + 8)
+int gwas_solve_file_out(gwas_ctx *ctx, const char *in_path, int64_t header_bytes, int64_t ldx, int64_t col0,
+                        int64_t m, const char *out_path, int flags, int64_t *done_out);
+
 /* The prefetching file reader on its own: blocks of block_bytes bytes (the
  * last one last_bytes, 0 = full) from `offset`, read by a host thread into
  * `depth` >= 2 pinned buffers ahead of the consumer.  gwas_reader_next waits

@@ -40,9 +40,10 @@ EXPORTS = (
     "gwas_reml_eval", "gwas_reml_fit", "gwas_batch_create", "gwas_batch_solve", "gwas_batch_synchronize",
     "gwas_batch_set_order", "gwas_batch_autotune", "gwas_batch_solve_files", "gwas_batch_kernel_launches",
     "gwas_batch_last_error_detail",
-    "gwas_batch_destroy", "gwas_solve_file", "gwas_reader_open", "gwas_reader_next", "gwas_reader_release",
-    "gwas_reader_error_detail", "gwas_reader_close",
+    "gwas_batch_destroy", "gwas_solve_file", "gwas_solve_file_out", "gwas_reader_open", "gwas_reader_next",
+    "gwas_reader_release", "gwas_reader_error_detail", "gwas_reader_close",
 )
+GWAS_RESUME = 1
 STAGES = ("h2d", "trsm", "reduce", "d2h")
 
 
@@ -142,6 +143,9 @@ def load(path: str | None = None):
     lib.gwas_batch_destroy.restype = None
     lib.gwas_solve_file.argtypes = [vp, ctypes.c_char_p, i64, i64, i64, i64, vp, vp, vp]
     lib.gwas_solve_file.restype = c_int
+    lib.gwas_solve_file_out.argtypes = [vp, ctypes.c_char_p, i64, i64, i64, i64, ctypes.c_char_p, c_int,
+                                        ctypes.POINTER(i64)]
+    lib.gwas_solve_file_out.restype = c_int
     lib.gwas_reader_open.argtypes = [P(vp), ctypes.c_char_p, i64, i64, i64, i64, c_int]
     lib.gwas_reader_open.restype = c_int
     lib.gwas_reader_next.argtypes = [vp, P(vp), P(i64), c_int]
@@ -237,6 +241,21 @@ def _colmajor(a, dtype, rows: int, name: str, allow_none=False):
         raise ValueError(f"{name} must have {rows} rows, got {arr.shape}")
     arr = np.asfortranarray(arr)
     return arr.ctypes.data, rows, arr
+
+
+def read_results(path: str):
+    """A result file of GLS.solve_file_out: (header dict, b p x m, se p x m, status m)."""
+    raw = np.fromfile(path, dtype=np.uint8)
+    if raw.size < 64 or bytes(raw[:8]) != b"GWASRES\0":
+        raise ValueError(f"{path}: not a result file")
+    p, n, col0, m, rec, prec = (int(raw[12:16].view("<u4")[0]), int(raw[16:24].view("<u8")[0]),
+                                int(raw[24:32].view("<u8")[0]), int(raw[32:40].view("<u8")[0]),
+                                int(raw[40:44].view("<u4")[0]), int(raw[44:48].view("<u4")[0]))
+    dt = np.dtype([("b", "<f8", (p,)), ("se", "<f8", (p,)), ("status", "<i4"), ("pad", "<i4")])
+    assert dt.itemsize == rec
+    recs = raw[64:64 + m * rec].view(dt)
+    head = dict(p=p, n=n, col0=col0, m=m, record_bytes=rec, precision=prec)
+    return head, np.asfortranarray(recs["b"].T), np.asfortranarray(recs["se"].T), recs["status"].copy()
 
 
 class GLS:
@@ -388,6 +407,18 @@ class GLS:
         self._check(load().gwas_solve_file(self._ctx, os.fsencode(path), int(header_bytes), int(ldx or self.n),
                                            int(col0), int(m), b.ctypes.data, se.ctypes.data, st.ctypes.data))
         return b, se, st
+
+    def solve_file_out(self, path: str, m: int, out_path: str, ldx: int | None = None, col0: int = 0,
+                       header_bytes: int = 0, resume: bool = False) -> int:
+        """Columns col0 .. col0+m-1 of the dosage file, disk to disk: results
+        written to out_path (read them with read_results), with a checkpoint
+        beside it; resume=True continues an interrupted run.  Returns the
+        number of columns on disk."""
+        done = ctypes.c_int64(0)
+        self._check(load().gwas_solve_file_out(self._ctx, os.fsencode(path), int(header_bytes), int(ldx or self.n),
+                                               int(col0), int(m), os.fsencode(out_path),
+                                               GWAS_RESUME if resume else 0, ctypes.byref(done)))
+        return done.value
 
     def synchronize(self):
         self._check(load().gwas_synchronize(self._ctx))

@@ -4,7 +4,11 @@
 #include <cuda.h>
 #include <cuda_runtime.h>
 
+#include <fcntl.h>
+#include <unistd.h>
+
 #include <algorithm>
+#include <cerrno>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -617,12 +621,14 @@ int gwas_solve_stream(gwas_ctx* ctx, const int8_t* XR_host, int64_t ldx, int64_t
   return check_device_status(ctx);
 }
 
-int gwas_solve_file(gwas_ctx* ctx, const char* path, int64_t header_bytes, int64_t ldx, int64_t col0, int64_t m,
-                    double* b_host, double* se_host, int* status_host) {
-  if (!ctx) return GWAS_ERR_ARG;
-  if (!path || !b_host || header_bytes < 0 || ldx < ctx->n || col0 < 0 || m < 0)
-    return fail(ctx, GWAS_ERR_ARG, "bad arguments to gwas_solve_file");
-  if (m == 0) return GWAS_OK;
+}  // extern "C"
+
+// Disk -> pinned host -> GPU over columns col0 .. col0+m-1 of a file; `sink`
+// receives each block's results (pinned host slices of b, se, status) in
+// column order, while the GPU works on later blocks.
+template <typename Sink>
+static int solve_file_impl(gwas_ctx* ctx, const char* path, int64_t header_bytes, int64_t ldx, int64_t col0, int64_t m,
+                           bool want_se, bool want_status, Sink&& sink) {
   CK(cudaSetDevice(ctx->dev));
   const int R = ctx->ring_depth, bs = ctx->bs, p = ctx->p;
   const int64_t nblk = (m + bs - 1) / bs;
@@ -639,14 +645,10 @@ int gwas_solve_file(gwas_ctx* ctx, const char* path, int64_t header_bytes, int64
                             ctx->file_buf.data());
   if (rc != GWAS_OK) return fail(ctx, rc, "cannot open %s", path);
   auto drain = [&](int64_t blk) -> int {
-    const int slot = (int)(blk % R), nc = cols_of(blk);
+    const int slot = (int)(blk % R);
     CK(cudaEventSynchronize(ctx->ev_out[slot]));
-    std::memcpy(b_host + blk * bs * p, ctx->h_b + (size_t)slot * p * bs, sizeof(double) * (size_t)p * nc);
-    if (se_host)
-      std::memcpy(se_host + blk * bs * p, ctx->h_se + (size_t)slot * p * bs, sizeof(double) * (size_t)p * nc);
-    if (status_host)
-      std::memcpy(status_host + blk * bs, ctx->h_status + (size_t)slot * bs, sizeof(int) * (size_t)nc);
-    return GWAS_OK;
+    return sink(blk, cols_of(blk), ctx->h_b + (size_t)slot * p * bs, ctx->h_se + (size_t)slot * p * bs,
+                ctx->h_status + (size_t)slot * bs);
   };
   rc = [&]() -> int {
     for (int sl = 0; sl < R; ++sl) CK(cudaEventRecord(ctx->ev_free[sl], ctx->stream));
@@ -673,10 +675,10 @@ int gwas_solve_file(gwas_ctx* ctx, const char* path, int64_t header_bytes, int64
         StageMark mk(ctx, GWAS_STAGE_D2H, ctx->stream);
         CK(cudaMemcpyAsync(ctx->h_b + (size_t)slot * p * bs, ob, sizeof(double) * (size_t)p * nc,
                            cudaMemcpyDeviceToHost, ctx->stream));
-        if (se_host)
+        if (want_se)
           CK(cudaMemcpyAsync(ctx->h_se + (size_t)slot * p * bs, ose, sizeof(double) * (size_t)p * nc,
                              cudaMemcpyDeviceToHost, ctx->stream));
-        if (status_host)
+        if (want_status)
           CK(cudaMemcpyAsync(ctx->h_status + (size_t)slot * bs, ost, sizeof(int) * (size_t)nc, cudaMemcpyDeviceToHost,
                              ctx->stream));
       }
@@ -695,6 +697,145 @@ int gwas_solve_file(gwas_ctx* ctx, const char* path, int64_t header_bytes, int64
     return check_device_status(ctx);
   }();
   gwas_reader_close(rd);
+  return rc;
+}
+
+// ------------------------------------------------ disk to disk, resumable
+namespace {
+struct ResHeader {  // the result file's and the checkpoint's first 64 bytes
+  char magic[8];
+  uint32_t version, p;
+  uint64_t n, col0, m;
+  uint32_t record_bytes, precision;
+  uint64_t done;  // checkpoint only: columns whose records are on disk
+  uint64_t reserved;
+};
+static_assert(sizeof(ResHeader) == 64, "64-byte header");
+
+bool write_all(int fd, const void* buf, size_t bytes, int64_t off) {
+  const char* p = static_cast<const char*>(buf);
+  while (bytes > 0) {
+    const ssize_t w = pwrite(fd, p, bytes, (off_t)off);
+    if (w < 0 && errno == EINTR) continue;
+    if (w <= 0) return false;
+    p += w;
+    bytes -= (size_t)w;
+    off += w;
+  }
+  return true;
+}
+
+bool read_all(int fd, void* buf, size_t bytes, int64_t off) {
+  char* p = static_cast<char*>(buf);
+  while (bytes > 0) {
+    const ssize_t r = pread(fd, p, bytes, (off_t)off);
+    if (r < 0 && errno == EINTR) continue;
+    if (r <= 0) return false;
+    p += r;
+    bytes -= (size_t)r;
+    off += r;
+  }
+  return true;
+}
+}  // namespace
+
+extern "C" {
+
+int gwas_solve_file(gwas_ctx* ctx, const char* path, int64_t header_bytes, int64_t ldx, int64_t col0, int64_t m,
+                    double* b_host, double* se_host, int* status_host) {
+  if (!ctx) return GWAS_ERR_ARG;
+  if (!path || !b_host || header_bytes < 0 || ldx < ctx->n || col0 < 0 || m < 0)
+    return fail(ctx, GWAS_ERR_ARG, "bad arguments to gwas_solve_file");
+  if (m == 0) return GWAS_OK;
+  const int p = ctx->p, bs = ctx->bs;
+  return solve_file_impl(ctx, path, header_bytes, ldx, col0, m, se_host != nullptr, status_host != nullptr,
+                         [&](int64_t blk, int nc, const double* hb, const double* hse, const int* hst) -> int {
+                           std::memcpy(b_host + blk * bs * p, hb, sizeof(double) * (size_t)p * nc);
+                           if (se_host) std::memcpy(se_host + blk * bs * p, hse, sizeof(double) * (size_t)p * nc);
+                           if (status_host) std::memcpy(status_host + blk * bs, hst, sizeof(int) * (size_t)nc);
+                           return GWAS_OK;
+                         });
+}
+
+int gwas_solve_file_out(gwas_ctx* ctx, const char* in_path, int64_t header_bytes, int64_t ldx, int64_t col0,
+                        int64_t m, const char* out_path, int flags, int64_t* done_out) {
+  if (!ctx) return GWAS_ERR_ARG;
+  if (!in_path || !out_path || header_bytes < 0 || ldx < ctx->n || col0 < 0 || m < 0 || (flags & ~GWAS_RESUME))
+    return fail(ctx, GWAS_ERR_ARG, "bad arguments to gwas_solve_file_out");
+  const int p = ctx->p, bs = ctx->bs;
+  const size_t rec = GWAS_RESULT_RECORD_BYTES(p);
+  ResHeader h{};
+  std::memcpy(h.magic, "GWASRES", 8);
+  h.version = 1;
+  h.p = (uint32_t)p;
+  h.n = (uint64_t)ctx->n;
+  h.col0 = (uint64_t)col0;
+  h.m = (uint64_t)m;
+  h.record_bytes = (uint32_t)rec;
+  h.precision = (uint32_t)ctx->prec;
+  const std::string ckpt_path = std::string(out_path) + ".ckpt";
+  int64_t done = 0;
+  const bool resume = (flags & GWAS_RESUME) != 0;
+  if (resume) {  // the checkpoint must describe this same run
+    const int cfd = open(ckpt_path.c_str(), O_RDONLY);
+    if (cfd >= 0) {
+      ResHeader c{};
+      const bool ok = read_all(cfd, &c, sizeof c, 0);
+      close(cfd);
+      if (!ok || std::memcmp(c.magic, "GWASCKP", 8) != 0 || c.p != h.p || c.n != h.n || c.col0 != h.col0 ||
+          c.m != h.m || c.record_bytes != h.record_bytes || c.precision != h.precision || c.done > h.m)
+        return fail(ctx, GWAS_ERR_ARG, "checkpoint %s does not match this run", ckpt_path.c_str());
+      done = (int64_t)c.done;
+    }
+  }
+  const int ofd = open(out_path, O_RDWR | O_CREAT | (resume ? 0 : O_TRUNC), 0644);
+  if (ofd < 0) return fail(ctx, GWAS_ERR_IO, "cannot open %s: %s", out_path, strerror(errno));
+  const int cfd = open(ckpt_path.c_str(), O_RDWR | O_CREAT, 0644);
+  if (cfd < 0) {
+    close(ofd);
+    return fail(ctx, GWAS_ERR_IO, "cannot open %s: %s", ckpt_path.c_str(), strerror(errno));
+  }
+  ResHeader ck = h;
+  std::memcpy(ck.magic, "GWASCKP", 8);
+  // the checkpoint advances only after the records it covers are on disk
+  auto checkpoint = [&](int64_t d) -> bool {
+    if (fdatasync(ofd) != 0) return false;
+    ck.done = (uint64_t)d;
+    return write_all(cfd, &ck, sizeof ck, 0) && fdatasync(cfd) == 0;
+  };
+  int rc = GWAS_OK;
+  if (!write_all(ofd, &h, sizeof h, 0) || !checkpoint(done))
+    rc = fail(ctx, GWAS_ERR_IO, "writing %s: %s", out_path, strerror(errno));
+  if (rc == GWAS_OK && done < m) {
+    std::vector<char> buf((size_t)bs * rec);
+    const int64_t start = done;
+    int64_t since_sync = 0;
+    rc = solve_file_impl(ctx, in_path, header_bytes, ldx, col0 + start, m - start, true, true,
+                         [&](int64_t blk, int nc, const double* hb, const double* hse, const int* hst) -> int {
+                           for (int c = 0; c < nc; ++c) {
+                             char* r = buf.data() + (size_t)c * rec;
+                             std::memcpy(r, hb + (size_t)c * p, sizeof(double) * p);
+                             std::memcpy(r + 8 * p, hse + (size_t)c * p, sizeof(double) * p);
+                             const int32_t st[2] = {hst[c], 0};
+                             std::memcpy(r + 16 * p, st, 8);
+                           }
+                           const int64_t first = start + blk * bs;
+                           if (!write_all(ofd, buf.data(), (size_t)nc * rec, (int64_t)sizeof h + first * (int64_t)rec))
+                             return fail(ctx, GWAS_ERR_IO, "writing %s: %s", out_path, strerror(errno));
+                           done = first + nc;
+                           // a checkpoint every 16 blocks (and at the end): at most that much is redone
+                           if (++since_sync >= 16 || done == m) {
+                             since_sync = 0;
+                             if (!checkpoint(done))
+                               return fail(ctx, GWAS_ERR_IO, "checkpointing %s: %s", ckpt_path.c_str(),
+                                           strerror(errno));
+                           }
+                           return GWAS_OK;
+                         });
+  }
+  close(ofd);
+  close(cfd);
+  if (done_out) *done_out = done;
   return rc;
 }
 

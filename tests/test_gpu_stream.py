@@ -48,6 +48,41 @@ def test_solve_file_matches_blocks_and_resumes(dosage_file, prec):
         assert np.array_equal(b2, b_ref[:, 1100:]) and np.array_equal(se2, se[:, 1100:])
 
 
+@pytest.mark.parametrize("prec", ["fp64", "f16x2"])
+def test_solve_file_out_writes_results_and_resumes(dosage_file, tmp_path, prec):
+    """Disk to disk: the result file holds exactly what the in-memory stream
+    returns; a run resumed from a checkpoint recomputes what follows it and
+    ends with the same file."""
+    path, n, m, ld, header, X = dosage_file
+    s = gwas_synth.study(n, 4, 2000, 0.6, seed=40)
+    out = str(tmp_path / "results.bin")
+    with gw.GLS(s["Phi"], s["XL"], s["y"], 0.6, 1.0, precision=prec, bs=128) as g:
+        b, se, st = g.solve_file(path, m - 300, ldx=ld, col0=300, header_bytes=header)
+        done = g.solve_file_out(path, m - 300, out, ldx=ld, col0=300, header_bytes=header)
+        assert done == m - 300
+        head, b2, se2, st2 = gw.read_results(out)
+        assert head == dict(p=4, n=n, col0=300, m=m - 300, record_bytes=72, precision=gw.PRECISIONS[prec])
+        assert np.array_equal(b, b2) and np.array_equal(se, se2) and np.array_equal(st, st2)
+        full = open(out, "rb").read()
+        # an interrupted run: the checkpoint says 2 blocks, the records after them are garbage
+        ck = bytearray(open(out + ".ckpt", "rb").read())
+        assert ck[:8] == b"GWASCKP\0" and int.from_bytes(ck[48:56], "little") == m - 300
+        ck[48:56] = (256).to_bytes(8, "little")
+        open(out + ".ckpt", "wb").write(bytes(ck))
+        with open(out, "r+b") as f:
+            f.seek(64 + 256 * 72)
+            f.write(b"\xee" * (72 * 500))
+        assert g.solve_file_out(path, m - 300, out, ldx=ld, col0=300, header_bytes=header, resume=True) == m - 300
+        assert open(out, "rb").read() == full
+        # a checkpoint of another run is refused
+        with pytest.raises(gw.GwasError) as e:
+            g.solve_file_out(path, m - 301, out, ldx=ld, col0=300, header_bytes=header, resume=True)
+        assert e.value.name == "GWAS_ERR_ARG"
+        with pytest.raises(gw.GwasError) as e:
+            g.solve_file_out(path, 10, str(tmp_path / "no_such_dir" / "r.bin"), ldx=ld, header_bytes=header)
+        assert e.value.name == "GWAS_ERR_IO"
+
+
 def test_solve_file_errors(dosage_file):
     path, n, m, ld, header, X = dosage_file
     s = gwas_synth.study(n, 4, 2000, 0.6, seed=40)
