@@ -2,13 +2,17 @@
 // streamed from disk to main memory to the GPU; the paper keeps three host
 // buffers so that a disk read, a host->GPU copy and the CPU's own work can
 // proceed at once).  A reader thread fills a ring of `depth` pinned buffers
-// with consecutive blocks of a file (pread, 64-bit offsets); the consumer
-// takes them in order and hands each back once its host->GPU copy is done.
-// Every wait is bounded; read errors and short reads surface as GWAS_ERR_IO.
+// with consecutive blocks of a file (pread, 64-bit offsets); each block is
+// read by a pool of worker threads in parallel byte ranges (one thread's
+// copies out of the page cache run at a few GB/s, far below the host->GPU
+// link); the consumer takes blocks in order and hands each back once its
+// host->GPU copy is done.  Every wait is bounded; read errors and short reads
+// surface as GWAS_ERR_IO.
 #include <cuda_runtime.h>
 #include <fcntl.h>
 #include <unistd.h>
 
+#include <algorithm>
 #include <cerrno>
 #include <chrono>
 #include <condition_variable>
@@ -36,9 +40,57 @@ struct gwas_reader {
   std::mutex mu;
   std::condition_variable cv;
   std::thread th;
+  // the worker pool: job `job` asks each worker k for its part of one block
+  std::vector<std::thread> workers;
+  std::condition_variable wcv;
+  int64_t job = 0;          // jobs posted
+  char* job_dst = nullptr;  // the block's buffer
+  int64_t job_off = 0, job_bytes = 0;
+  int pending = 0;          // workers still reading the current job
 };
 
 namespace {
+
+constexpr int64_t kPartAlign = 1 << 20;  // workers read whole MiB ranges
+
+// Worker k reads its range of each posted block.
+void worker_loop(gwas_reader* r, int k) {
+  const int nw = (int)r->workers.size();
+  int64_t seen = 0;
+  while (true) {
+    char* dst;
+    int64_t off, bytes;
+    {
+      std::unique_lock<std::mutex> lk(r->mu);
+      r->wcv.wait(lk, [&] { return r->job > seen || r->stop; });
+      if (r->job == seen) return;  // stopped with no job left: a posted job is always finished
+      seen = r->job;
+      dst = r->job_dst;
+      off = r->job_off;
+      bytes = r->job_bytes;
+    }
+    int64_t part = (bytes + nw - 1) / nw;
+    part = (part + kPartAlign - 1) / kPartAlign * kPartAlign;
+    const int64_t lo = std::min<int64_t>(bytes, k * part), hi = std::min<int64_t>(bytes, lo + part);
+    int64_t got = lo;
+    std::string err;
+    while (got < hi) {
+      const ssize_t n = pread(r->fd, dst + got, (size_t)(hi - got), (off_t)(off + got));
+      if (n < 0 && errno == EINTR) continue;
+      if (n <= 0) {
+        err = n < 0 ? std::string("read failed: ") + strerror(errno) : "file shorter than the requested blocks";
+        break;
+      }
+      got += n;
+    }
+    std::lock_guard<std::mutex> lk(r->mu);
+    if (!err.empty() && !r->error) {
+      r->error = GWAS_ERR_IO;
+      r->detail = err;
+    }
+    if (--r->pending == 0) r->cv.notify_all();
+  }
+}
 
 void reader_loop(gwas_reader* r) {
   for (int64_t b = 0; b < r->nblocks; ++b) {
@@ -49,25 +101,36 @@ void reader_loop(gwas_reader* r) {
     }
     const int s = (int)(b % r->depth);
     const int64_t want = (b == r->nblocks - 1) ? r->last_bytes : r->block_bytes;
-    int64_t got = 0;
-    char* dst = static_cast<char*>(r->buf[s]);
-    while (got < want) {
-      const ssize_t k = pread(r->fd, dst + got, (size_t)(want - got), (off_t)(r->offset + b * r->block_bytes + got));
-      if (k < 0 && errno == EINTR) continue;
-      if (k <= 0) {
-        std::lock_guard<std::mutex> lk(r->mu);
-        r->error = GWAS_ERR_IO;
-        r->detail = k < 0 ? std::string("read failed: ") + strerror(errno) : "file shorter than the requested blocks";
-        r->cv.notify_all();
-        return;
-      }
-      got += k;
+    std::unique_lock<std::mutex> lk(r->mu);
+    r->job_dst = static_cast<char*>(r->buf[s]);
+    r->job_off = r->offset + b * r->block_bytes;
+    r->job_bytes = want;
+    r->pending = (int)r->workers.size();
+    ++r->job;
+    r->wcv.notify_all();
+    // workers finish their reads whatever happens (stop is only set once they are idle)
+    r->cv.wait(lk, [&] { return r->pending == 0; });
+    if (r->error) {
+      r->cv.notify_all();
+      return;
     }
-    std::lock_guard<std::mutex> lk(r->mu);
     r->bytes[s] = want;
     r->filled = b + 1;
     r->cv.notify_all();
   }
+}
+
+int reader_threads() {
+  const unsigned hc = std::thread::hardware_concurrency();
+  return hc >= 16 ? 8 : (hc >= 4 ? (int)hc / 2 : 1);
+}
+
+void start_threads(gwas_reader* r) {
+  const int nw = reader_threads();
+  r->workers.reserve(nw);
+  for (int k = 0; k < nw; ++k) r->workers.emplace_back();
+  for (int k = 0; k < nw; ++k) r->workers[k] = std::thread(worker_loop, r, k);
+  r->th = std::thread(reader_loop, r);
 }
 
 }  // namespace
@@ -96,7 +159,7 @@ int reader_open_with(gwas_reader** out, const char* path, int64_t offset, int64_
   r->buf.assign(buffers, buffers + depth);
   r->bytes.assign(depth, 0);
   r->own_buffers = false;
-  r->th = std::thread(reader_loop, r);
+  start_threads(r);
   *out = r;
   return GWAS_OK;
 }
@@ -133,7 +196,7 @@ int gwas_reader_open(gwas_reader** out, const char* path, int64_t offset, int64_
       return GWAS_ERR_NOMEM;
     }
   }
-  r->th = std::thread(reader_loop, r);
+  start_threads(r);
   *out = r;
   return GWAS_OK;
 }
@@ -176,7 +239,13 @@ void gwas_reader_close(gwas_reader* r) {
     r->stop = true;
     r->cv.notify_all();
   }
-  if (r->th.joinable()) r->th.join();
+  if (r->th.joinable()) r->th.join();  // the reader thread returns between jobs
+  {
+    std::lock_guard<std::mutex> lk(r->mu);
+    r->wcv.notify_all();
+  }
+  for (auto& w : r->workers)
+    if (w.joinable()) w.join();
   if (r->own_buffers)
     for (auto* p : r->buf) cudaFreeHost(p);
   if (r->fd >= 0) close(r->fd);
