@@ -102,7 +102,13 @@ typedef struct {
                         tiles (256-row products on 2-SM clusters, longest first).  Costs one
                         n_pad x bs cast copy of the block and, at set-up, up to 16 n_pad^2 bytes of
                         transient device memory (n_pad = n rounded up to 128) */
-  int reserved[2]; /* must be zero */
+  int traits;      /* phenotypes t sharing the study (0 = 1): y is n x t column-major, W = [X~_L | Y~];
+                      1 <= t <= 16 and p - 1 + t <= 16.  The solve of each SNP block is shared by the t
+                      phenotypes; S (so se and status) does not depend on y, only b does: every b output
+                      holds t consecutive p x ncols (or p x m) column-major blocks, phenotype k at
+                      b + k p ncols.  Batches, the adjoint, REML and gwas_solve_block_static take t = 1
+                      (else GWAS_ERR_UNSUPPORTED) */
+  int reserved[1]; /* must be zero */
 } gwas_config;
 
 enum {
@@ -288,6 +294,9 @@ int gwas_solve_file(gwas_ctx *ctx, const char *path, int64_t header_bytes, int64
  * output or checkpoint), and those of gwas_solve_file. */
 #define GWAS_RESUME 1
 #define GWAS_RESULT_RECORD_BYTES(p) (16 * (p) + 8)
+/* With t phenotypes a record holds double b[t][p] (phenotype-major), se[p], status, 0; the header
+ * stores t at byte 56 (uint64). */
+#define GWAS_RESULT_RECORD_BYTES_T(p, t) (8 * (p) * ((t) + 1) + 8)
 int gwas_solve_file_out(gwas_ctx *ctx, const char *in_path, int64_t header_bytes, int64_t ldx, int64_t col0,
                         int64_t m, const char *out_path, int flags, int64_t *done_out);
 

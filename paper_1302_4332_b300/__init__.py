@@ -63,7 +63,7 @@ class NotSPDError(GwasError):
 class _Config(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("bs", ctypes.c_int), ("ring_depth", ctypes.c_int),
                 ("device", ctypes.c_int), ("strip_group", ctypes.c_int), ("tile_mode", ctypes.c_int),
-                ("reserved", ctypes.c_int * 2)]
+                ("traits", ctypes.c_int), ("reserved", ctypes.c_int * 1)]
 
 
 _lib = None
@@ -244,18 +244,24 @@ def _colmajor(a, dtype, rows: int, name: str, allow_none=False):
 
 
 def read_results(path: str):
-    """A result file of GLS.solve_file_out: (header dict, b p x m, se p x m, status m)."""
+    """A result file of GLS.solve_file_out: (header dict, b, se p x m, status m);
+    b is p x m, or p x m x t for t phenotypes."""
     raw = np.fromfile(path, dtype=np.uint8)
     if raw.size < 64 or bytes(raw[:8]) != b"GWASRES\0":
         raise ValueError(f"{path}: not a result file")
     p, n, col0, m, rec, prec = (int(raw[12:16].view("<u4")[0]), int(raw[16:24].view("<u8")[0]),
                                 int(raw[24:32].view("<u8")[0]), int(raw[32:40].view("<u8")[0]),
                                 int(raw[40:44].view("<u4")[0]), int(raw[44:48].view("<u4")[0]))
-    dt = np.dtype([("b", "<f8", (p,)), ("se", "<f8", (p,)), ("status", "<i4"), ("pad", "<i4")])
+    t = int(raw[56:64].view("<u8")[0]) or 1
+    dt = np.dtype([("b", "<f8", (t, p)), ("se", "<f8", (p,)), ("status", "<i4"), ("pad", "<i4")])
     assert dt.itemsize == rec
     recs = raw[64:64 + m * rec].view(dt)
     head = dict(p=p, n=n, col0=col0, m=m, record_bytes=rec, precision=prec)
-    return head, np.asfortranarray(recs["b"].T), np.asfortranarray(recs["se"].T), recs["status"].copy()
+    if t > 1:
+        head["traits"] = t
+    b = np.asfortranarray(np.transpose(recs["b"], (2, 0, 1)))  # (p, m, t)
+    return head, (b[:, :, 0].copy(order="F") if t == 1 else b), np.asfortranarray(recs["se"].T), \
+        recs["status"].copy()
 
 
 class GLS:
@@ -281,7 +287,10 @@ class GLS:
         xl_p, ldxl, self._k2 = _colmajor(XL, np.float64, n, "XL", allow_none=True) if q else (None, n, None)
         if q and ldxl != n:
             raise ValueError("XL must be contiguous with leading dimension n")
-        y_p, _, self._k3 = _colmajor(y, np.float64, n, "y")
+        y_p, ldy, self._k3 = _colmajor(y, np.float64, n, "y")
+        self.t = int(self._k3.shape[1])  # phenotypes: y is n or n x t
+        if ldy != n:
+            raise ValueError("y must be contiguous with leading dimension n")
         cfg = _Config()
         lib.gwas_config_default(ctypes.byref(cfg))
         cfg.precision = PRECISIONS[precision]
@@ -290,6 +299,7 @@ class GLS:
         cfg.device = int(device)
         cfg.strip_group = int(strip_group)
         cfg.tile_mode = TILE_MODES[tiles]
+        cfg.traits = self.t
         self.precision, self.bs = precision, int(bs)
         stream_p = None
         if stream is not None:
@@ -322,17 +332,31 @@ class GLS:
             raise GwasError(rc, detail)
 
     def _outputs(self, ncols: int, like, b, se, status):
-        p = self.p
+        p, t = self.p, self.t
         if b is None:
             if _is_torch(like) and like.is_cuda:
                 torch = _torch()
-                b = torch.empty((ncols, p), dtype=torch.float64, device=like.device).T
+                b = torch.empty((t, ncols, p), dtype=torch.float64, device=like.device).permute(2, 1, 0)
+                if t == 1:
+                    b = b[:, :, 0]
                 se = torch.empty((ncols, p), dtype=torch.float64, device=like.device).T
                 status = torch.empty(ncols, dtype=torch.int32, device=like.device)
             else:
-                b = np.empty((p, ncols), order="F")
+                b = np.empty((p, ncols) if t == 1 else (p, ncols, t), order="F")
                 se = np.empty((p, ncols), order="F")
                 status = np.empty(ncols, dtype=np.int32)
+        if t > 1:  # p x ncols x t, column-major: phenotype k at + k p ncols
+            strides = tuple(b.stride()) if _is_torch(b) else tuple(x // 8 for x in np.asarray(b).strides)
+            if tuple(b.shape) != (p, ncols, t) or strides != (1, p, p * ncols):
+                raise ValueError(f"b must be a contiguous p x ncols x t column-major array, got {tuple(b.shape)}")
+            bptr = b.data_ptr() if _is_torch(b) else np.asarray(b).ctypes.data
+            sp, lds, _ = _colmajor(se, np.float64, p, "se", allow_none=True)
+            if sp is not None and lds != p:
+                raise ValueError("se must be contiguous p x ncols column-major")
+            if status is not None and not _is_torch(status):
+                status = np.ascontiguousarray(status, dtype=np.int32)
+            stp = None if status is None else (status.data_ptr() if _is_torch(status) else status.ctypes.data)
+            return (b, se, status), (bptr, sp, stp)
         bp, ldb, _ = _colmajor(b, np.float64, p, "b")
         sp, lds, _ = _colmajor(se, np.float64, p, "se", allow_none=True)
         if ldb != p or (sp is not None and lds != p):
@@ -366,7 +390,7 @@ class GLS:
             raise ValueError("solve_stream takes host memory")
         m = int(keep.shape[1])
         if b is None:
-            b = np.empty((self.p, m), order="F")
+            b = np.empty((self.p, m) if self.t == 1 else (self.p, m, self.t), order="F")
             se = np.empty((self.p, m), order="F")
             status = np.empty(m, dtype=np.int32)
         _, ptrs = self._outputs(m, keep, b, se, status)
@@ -401,7 +425,7 @@ class GLS:
     def solve_file(self, path: str, m: int, ldx: int | None = None, col0: int = 0, header_bytes: int = 0):
         """Columns col0 .. col0+m-1 of an n x M int8 column-major file (leading
         dimension ldx bytes, default n), streamed disk -> pinned host -> GPU."""
-        b = np.empty((self.p, m), order="F")
+        b = np.empty((self.p, m) if self.t == 1 else (self.p, m, self.t), order="F")
         se = np.empty((self.p, m), order="F")
         st = np.empty(m, dtype=np.int32)
         self._check(load().gwas_solve_file(self._ctx, os.fsencode(path), int(header_bytes), int(ldx or self.n),

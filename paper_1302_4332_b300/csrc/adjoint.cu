@@ -38,7 +38,7 @@ __device__ __forceinline__ void adjoint_store(const double (&af)[QM + 2], const 
     for (int t = 0; t <= i; ++t) v = fma(sc->Cinv[i + t * QMAX], af[t], v);
     l[i] = v;
     ll = fma(v, v, ll);
-    lz = fma(v, sc->zT[i], lz);
+    lz = fma(v, sc->zT[0][i], lz);
   }
   const double sbr = af[QM + 1], rb = af[q];
   const double d2 = sbr - ll;
@@ -55,7 +55,7 @@ __device__ __forceinline__ void adjoint_store(const double (&af)[QM + 2], const 
     double v = 0.0;
     for (int i = j; i < q; ++i) v = fma(sc->Cinv[i + j * QMAX], l[i], v);
     g[j] = v;
-    bT[j] = sc->b0[j] - bp * v;
+    bT[j] = sc->b0[0][j] - bp * v;
   }
   // v = S^-1 e_p:  v_p = 1/d^2, v_T = -g/d^2;  s = v_p
   const double vp = 1.0 / d2, s = vp;
@@ -475,7 +475,7 @@ __global__ void null_residual_kernel(const double* __restrict__ W, int64_t ldw, 
   const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= rows) return;
   double v = W[r + q * ldw];
-  for (int a = 0; a < q; ++a) v -= W[r + a * ldw] * sc->b0[a];
+  for (int a = 0; a < q; ++a) v -= W[r + a * ldw] * sc->b0[0][a];
   R[r] = v;
 }
 

@@ -27,6 +27,7 @@ struct gwas_ctx {
   cudaStream_t stream = nullptr;
   cudaStream_t copy_stream = nullptr;
   int n = 0, p = 0, q = 0, n_pad = 0, P = 0;
+  int t = 1;  // phenotypes sharing the study (columns of y)
   int prec = GWAS_FP64, bs = 0, ring_depth = 0;
   double h = 0.0, sigma2 = 0.0;
   // study data (device)
@@ -228,7 +229,7 @@ int run_block(gwas_ctx* ctx, const void* X, bool int8_input, int64_t ldx, int nc
     {
       StageMark m(ctx, GWAS_STAGE_REDUCE, ctx->stream);
       CK(launch_reduce_solve(ctx->Xt, XT_F64, ctx->n_pad, ctx->n_pad, ctx->W, ctx->n_pad, ctx->sc, ctx->q, ncols,
-                             b, se, status, ctx->stream));
+                             b, se, status, ctx->stream, nullptr, nullptr, nullptr, 0, nullptr, ctx->t));
     }
     ctx->launches += 1;
     return GWAS_OK;
@@ -252,7 +253,7 @@ int run_block(gwas_ctx* ctx, const void* X, bool int8_input, int64_t ldx, int nc
     StageMark m(ctx, GWAS_STAGE_REDUCE, ctx->stream);
     CK(launch_reduce_solve(tc::xt_f32(ctx->tcs), XT_F32, tc::xt_ld(ctx->tcs), ctx->n_pad, ctx->W, ctx->n_pad,
                            ctx->sc, ctx->q, ncols, b, se, status, ctx->stream, ctx->W32, tc::shift_of(ctx->tcs),
-                           ctx->st, ctx->num_sms, tc::xt_reduce_map(ctx->tcs)));
+                           ctx->st, ctx->num_sms, tc::xt_reduce_map(ctx->tcs), ctx->t));
   }
   ctx->launches += 1;
   return GWAS_OK;
@@ -293,7 +294,8 @@ int solve_common(gwas_ctx* ctx, const void* XR, bool int8_input, int64_t ldx, in
   if (dev_in && dev_out) return GWAS_OK;  // asynchronous on the context's stream
   if (!dev_out) {
     StageMark m(ctx, GWAS_STAGE_D2H, ctx->stream);
-    CK(cudaMemcpyAsync(b, ctx->d_b, sizeof(double) * (size_t)ctx->p * ncols, cudaMemcpyDeviceToHost, ctx->stream));
+    CK(cudaMemcpyAsync(b, ctx->d_b, sizeof(double) * (size_t)ctx->p * ncols * ctx->t, cudaMemcpyDeviceToHost,
+                       ctx->stream));
     if (se)
       CK(cudaMemcpyAsync(se, ctx->d_se, sizeof(double) * (size_t)ctx->p * ncols, cudaMemcpyDeviceToHost,
                          ctx->stream));
@@ -367,6 +369,8 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
     return GWAS_ERR_ARG;
   for (int r : cfg.reserved)
     if (r != 0) return GWAS_ERR_ARG;
+  const int traits = cfg.traits == 0 ? 1 : cfg.traits;
+  if (traits < 1 || traits > TMAX || p - 1 + traits > QMAX + 1) return GWAS_ERR_ARG;
 
   gwas_ctx* ctx = new gwas_ctx;
   int dev = cfg.device;
@@ -390,7 +394,7 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
     ctx->num_sms = prop.multiProcessorCount;
     ctx->stream = static_cast<cudaStream_t>(stream);
     CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
-    ctx->n = n; ctx->p = p; ctx->q = p - 1;
+    ctx->n = n; ctx->p = p; ctx->q = p - 1; ctx->t = traits;
     ctx->n_pad = (n + TB - 1) / TB * TB;
     ctx->P = ctx->n_pad / TB;
     ctx->prec = cfg.precision; ctx->bs = cfg.bs; ctx->ring_depth = cfg.ring_depth;
@@ -399,14 +403,15 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
     CK(dmalloc(&ctx->L, sizeof(double) * n2));
     CK(dmalloc(&ctx->Dinv, sizeof(double) * (size_t)ctx->P * TB * TB));
     CK(dmalloc(&ctx->Aop, sizeof(double) * n2));
-    CK(dmalloc(&ctx->W, sizeof(double) * np * (ctx->q + 1)));
-    CK(dmalloc(&ctx->G, sizeof(double) * (ctx->q + 1) * (ctx->q + 1)));
+    const int nw = ctx->q + ctx->t;  // columns of W = [X~_L | Y~]
+    CK(dmalloc(&ctx->W, sizeof(double) * np * nw));
+    CK(dmalloc(&ctx->G, sizeof(double) * nw * nw));
     CK(dmalloc(&ctx->sc, sizeof(SolveConsts)));
     CK(dmalloc(&ctx->st, sizeof(DevStatus)));
     const int maxC = std::max((cfg.bs + F64_TN - 1) / F64_TN, 1);
     ctx->sched_bytes = sizeof(Sched) + sizeof(int) * (size_t)ctx->P * maxC;
     CK(dmalloc(&ctx->sched, ctx->sched_bytes));
-    const int xt_cols = std::max(cfg.bs, p);
+    const int xt_cols = std::max(cfg.bs, nw);
     CK(dmalloc(&ctx->Xt, sizeof(double) * np * xt_cols));
     DevStatus st0{};
     st0.not_spd = ~0ull;
@@ -446,9 +451,9 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
     }
     CK(launch_build_aop(ctx->L, ctx->Dinv, ctx->n_pad, ctx->Aop, ctx->stream, &ctx->launches));
 
-    // a3: [X~_L | y~] = L^-1 [X_L | y] (FP64), G = W^T W, solve constants
+    // a3: [X~_L | Y~] = L^-1 [X_L | Y] (FP64, t phenotype columns), G = W^T W, solve constants
     double* XLy = nullptr;
-    CK(dmalloc(&XLy, sizeof(double) * (size_t)n * (ctx->q + 1)));
+    CK(dmalloc(&XLy, sizeof(double) * (size_t)n * nw));
     if (ctx->q) {
       const bool d = is_device_ptr(XL);
       CK(cudaMemcpyAsync(XLy, XL, sizeof(double) * (size_t)n * ctx->q,
@@ -460,22 +465,22 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
       CK(cudaStreamSynchronize(ctx->stream));
       ctx->intercept = std::all_of(col0.begin(), col0.end(), [](double v) { return v == 1.0; });
     }
-    CK(cudaMemcpyAsync(XLy + (size_t)n * ctx->q, y, sizeof(double) * (size_t)n,
+    CK(cudaMemcpyAsync(XLy + (size_t)n * ctx->q, y, sizeof(double) * (size_t)n * ctx->t,
                        is_device_ptr(y) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, ctx->stream));
     {
-      const int Cw = (ctx->q + 1 + F64_TN - 1) / F64_TN;
+      const int Cw = (nw + F64_TN - 1) / F64_TN;
       CK(cudaMemsetAsync(ctx->sched, 0, sizeof(Sched) + sizeof(int) * (size_t)ctx->P * Cw, ctx->stream));
       TrsmF64Args a{};
       a.Aop = ctx->Aop; a.lda = ctx->n_pad;
       a.X = XLy; a.ldx = n; a.n = n;
       a.Xt = ctx->W; a.ldt = ctx->n_pad;
-      a.P = ctx->P; a.ncols = ctx->q + 1; a.C = Cw;
+      a.P = ctx->P; a.ncols = nw; a.C = Cw;
       a.sched = ctx->sched; a.st = ctx->st;
       CK(launch_trsm_f64(a, false, ctx->stream, ctx->num_sms));
       ctx->launches += 1;
     }
-    CK(launch_gram(ctx->W, ctx->n_pad, ctx->n_pad, ctx->q + 1, ctx->G, ctx->stream));
-    CK(launch_solve_consts(ctx->G, ctx->q, ctx->sc, ctx->st, ctx->stream));
+    CK(launch_gram(ctx->W, ctx->n_pad, ctx->n_pad, nw, ctx->G, ctx->stream));
+    CK(launch_solve_consts(ctx->G, ctx->q, ctx->t, ctx->sc, ctx->st, ctx->stream));
     ctx->launches += 2;
     CK(cudaStreamSynchronize(ctx->stream));
     cudaFree(XLy);
@@ -496,8 +501,8 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
       if (e != cudaSuccess)
         return fail(ctx, e == cudaErrorMemoryAllocation ? GWAS_ERR_NOMEM : GWAS_ERR_CUDA, "split set-up: %s",
                     cudaGetErrorString(e));
-      CK(dmalloc(&ctx->W32, sizeof(float) * np * w32_stride(ctx->q)));
-      CK(launch_make_w32(ctx->W, ctx->n_pad, ctx->n_pad, ctx->q, ctx->W32, ctx->stream));
+      CK(dmalloc(&ctx->W32, sizeof(float) * np * w32_stride(nw - 1)));
+      CK(launch_make_w32(ctx->W, ctx->n_pad, ctx->n_pad, nw - 1, ctx->W32, ctx->stream));
       CK(prepare_reduce_solve());
       ctx->launches += 1;
     }
@@ -509,10 +514,10 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
       CK(dmalloc(&ctx->ring[i], np * cfg.bs));
       CK(cudaMemsetAsync(ctx->ring[i], 0, np * cfg.bs, ctx->stream));
     }
-    CK(dmalloc(&ctx->d_b, sizeof(double) * (size_t)R * p * cfg.bs));
+    CK(dmalloc(&ctx->d_b, sizeof(double) * (size_t)R * p * cfg.bs * ctx->t));
     CK(dmalloc(&ctx->d_se, sizeof(double) * (size_t)R * p * cfg.bs));
     CK(dmalloc(&ctx->d_status, sizeof(int) * (size_t)R * cfg.bs));
-    CK(cudaMallocHost(&ctx->h_b, sizeof(double) * (size_t)R * p * cfg.bs));
+    CK(cudaMallocHost(&ctx->h_b, sizeof(double) * (size_t)R * p * cfg.bs * ctx->t));
     CK(cudaMallocHost(&ctx->h_se, sizeof(double) * (size_t)R * p * cfg.bs));
     CK(cudaMallocHost(&ctx->h_status, sizeof(int) * (size_t)R * cfg.bs));
     for (auto* v : {&ctx->ev_copied, &ctx->ev_free, &ctx->ev_out}) {
@@ -551,14 +556,18 @@ int gwas_solve_stream(gwas_ctx* ctx, const int8_t* XR_host, int64_t ldx, int64_t
     return fail(ctx, GWAS_ERR_ARG, "bad arguments to gwas_solve_stream");
   if (m == 0) return GWAS_OK;
   CK(cudaSetDevice(ctx->dev));
-  const int R = ctx->ring_depth, bs = ctx->bs, p = ctx->p;
+  const int R = ctx->ring_depth, bs = ctx->bs, p = ctx->p, T = ctx->t;
   const int64_t nblk = (m + bs - 1) / bs;
   auto cols_of = [&](int64_t blk) { return (int)std::min<int64_t>(bs, m - blk * bs); };
   // Results of block blk are copied out of pinned slot blk % R once its event fired.
   auto drain = [&](int64_t blk) -> int {
     const int slot = (int)(blk % R), nc = cols_of(blk);
     CK(cudaEventSynchronize(ctx->ev_out[slot]));
-    std::memcpy(b_host + blk * bs * p, ctx->h_b + (size_t)slot * p * bs, sizeof(double) * (size_t)p * nc);
+    // a slot holds the block's phenotypes one after another (p x nc each);
+    // phenotype k's p x m results go to b_host + k p m
+    for (int k = 0; k < T; ++k)
+      std::memcpy(b_host + (k * m + blk * bs) * p, ctx->h_b + (size_t)slot * T * p * bs + (size_t)k * p * nc,
+                  sizeof(double) * (size_t)p * nc);
     if (se_host)
       std::memcpy(se_host + blk * bs * p, ctx->h_se + (size_t)slot * p * bs, sizeof(double) * (size_t)p * nc);
     if (status_host)
@@ -593,14 +602,14 @@ int gwas_solve_stream(gwas_ctx* ctx, const int8_t* XR_host, int64_t ldx, int64_t
   for (int64_t blk = 0; blk < nblk; ++blk) {
     const int slot = (int)(blk % R), nc = cols_of(blk);
     CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_copied[slot], 0));
-    double* ob = ctx->d_b + (size_t)slot * p * bs;
+    double* ob = ctx->d_b + (size_t)slot * T * p * bs;
     double* ose = ctx->d_se + (size_t)slot * p * bs;
     int* ost = ctx->d_status + (size_t)slot * bs;
     if ((rc = run_block(ctx, ctx->ring[slot], true, ld_dev, nc, ob, ose, ost)) != GWAS_OK) return rc;
     CK(cudaEventRecord(ctx->ev_free[slot], ctx->stream));
     {
     StageMark mk(ctx, GWAS_STAGE_D2H, ctx->stream);
-    CK(cudaMemcpyAsync(ctx->h_b + (size_t)slot * p * bs, ob, sizeof(double) * (size_t)p * nc,
+    CK(cudaMemcpyAsync(ctx->h_b + (size_t)slot * T * p * bs, ob, sizeof(double) * (size_t)p * nc * T,
                        cudaMemcpyDeviceToHost, ctx->stream));
     if (se_host)
       CK(cudaMemcpyAsync(ctx->h_se + (size_t)slot * p * bs, ose, sizeof(double) * (size_t)p * nc,
@@ -647,7 +656,7 @@ static int solve_file_impl(gwas_ctx* ctx, const char* path, int64_t header_bytes
   auto drain = [&](int64_t blk) -> int {
     const int slot = (int)(blk % R);
     CK(cudaEventSynchronize(ctx->ev_out[slot]));
-    return sink(blk, cols_of(blk), ctx->h_b + (size_t)slot * p * bs, ctx->h_se + (size_t)slot * p * bs,
+    return sink(blk, cols_of(blk), ctx->h_b + (size_t)slot * ctx->t * p * bs, ctx->h_se + (size_t)slot * p * bs,
                 ctx->h_status + (size_t)slot * bs);
   };
   rc = [&]() -> int {
@@ -666,14 +675,14 @@ static int solve_file_impl(gwas_ctx* ctx, const char* path, int64_t header_bytes
       }
       CK(cudaEventRecord(ctx->ev_copied[slot], ctx->copy_stream));
       CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_copied[slot], 0));
-      double* ob = ctx->d_b + (size_t)slot * p * bs;
+      double* ob = ctx->d_b + (size_t)slot * ctx->t * p * bs;
       double* ose = ctx->d_se + (size_t)slot * p * bs;
       int* ost = ctx->d_status + (size_t)slot * bs;
       if ((r2 = run_block(ctx, ctx->ring[slot], true, ctx->n_pad, nc, ob, ose, ost)) != GWAS_OK) return r2;
       CK(cudaEventRecord(ctx->ev_free[slot], ctx->stream));
       {
         StageMark mk(ctx, GWAS_STAGE_D2H, ctx->stream);
-        CK(cudaMemcpyAsync(ctx->h_b + (size_t)slot * p * bs, ob, sizeof(double) * (size_t)p * nc,
+        CK(cudaMemcpyAsync(ctx->h_b + (size_t)slot * ctx->t * p * bs, ob, sizeof(double) * (size_t)p * nc * ctx->t,
                            cudaMemcpyDeviceToHost, ctx->stream));
         if (want_se)
           CK(cudaMemcpyAsync(ctx->h_se + (size_t)slot * p * bs, ose, sizeof(double) * (size_t)p * nc,
@@ -707,8 +716,8 @@ struct ResHeader {  // the result file's and the checkpoint's first 64 bytes
   uint32_t version, p;
   uint64_t n, col0, m;
   uint32_t record_bytes, precision;
-  uint64_t done;  // checkpoint only: columns whose records are on disk
-  uint64_t reserved;
+  uint64_t done;    // checkpoint only: columns whose records are on disk
+  uint64_t traits;  // phenotypes per record
 };
 static_assert(sizeof(ResHeader) == 64, "64-byte header");
 
@@ -750,7 +759,9 @@ int gwas_solve_file(gwas_ctx* ctx, const char* path, int64_t header_bytes, int64
   const int p = ctx->p, bs = ctx->bs;
   return solve_file_impl(ctx, path, header_bytes, ldx, col0, m, se_host != nullptr, status_host != nullptr,
                          [&](int64_t blk, int nc, const double* hb, const double* hse, const int* hst) -> int {
-                           std::memcpy(b_host + blk * bs * p, hb, sizeof(double) * (size_t)p * nc);
+                           for (int k = 0; k < ctx->t; ++k)  // phenotype k: p x nc at hb + k p nc
+                             std::memcpy(b_host + (k * m + blk * bs) * p, hb + (size_t)k * p * nc,
+                                         sizeof(double) * (size_t)p * nc);
                            if (se_host) std::memcpy(se_host + blk * bs * p, hse, sizeof(double) * (size_t)p * nc);
                            if (status_host) std::memcpy(status_host + blk * bs, hst, sizeof(int) * (size_t)nc);
                            return GWAS_OK;
@@ -762,8 +773,8 @@ int gwas_solve_file_out(gwas_ctx* ctx, const char* in_path, int64_t header_bytes
   if (!ctx) return GWAS_ERR_ARG;
   if (!in_path || !out_path || header_bytes < 0 || ldx < ctx->n || col0 < 0 || m < 0 || (flags & ~GWAS_RESUME))
     return fail(ctx, GWAS_ERR_ARG, "bad arguments to gwas_solve_file_out");
-  const int p = ctx->p, bs = ctx->bs;
-  const size_t rec = GWAS_RESULT_RECORD_BYTES(p);
+  const int p = ctx->p, bs = ctx->bs, T = ctx->t;
+  const size_t rec = GWAS_RESULT_RECORD_BYTES_T(p, T);
   ResHeader h{};
   std::memcpy(h.magic, "GWASRES", 8);
   h.version = 1;
@@ -773,6 +784,7 @@ int gwas_solve_file_out(gwas_ctx* ctx, const char* in_path, int64_t header_bytes
   h.m = (uint64_t)m;
   h.record_bytes = (uint32_t)rec;
   h.precision = (uint32_t)ctx->prec;
+  h.traits = (uint64_t)T;
   const std::string ckpt_path = std::string(out_path) + ".ckpt";
   int64_t done = 0;
   const bool resume = (flags & GWAS_RESUME) != 0;
@@ -783,7 +795,8 @@ int gwas_solve_file_out(gwas_ctx* ctx, const char* in_path, int64_t header_bytes
       const bool ok = read_all(cfd, &c, sizeof c, 0);
       close(cfd);
       if (!ok || std::memcmp(c.magic, "GWASCKP", 8) != 0 || c.p != h.p || c.n != h.n || c.col0 != h.col0 ||
-          c.m != h.m || c.record_bytes != h.record_bytes || c.precision != h.precision || c.done > h.m)
+          c.m != h.m || c.record_bytes != h.record_bytes || c.precision != h.precision || c.traits != h.traits ||
+          c.done > h.m)
         return fail(ctx, GWAS_ERR_ARG, "checkpoint %s does not match this run", ckpt_path.c_str());
       done = (int64_t)c.done;
     }
@@ -814,10 +827,12 @@ int gwas_solve_file_out(gwas_ctx* ctx, const char* in_path, int64_t header_bytes
                          [&](int64_t blk, int nc, const double* hb, const double* hse, const int* hst) -> int {
                            for (int c = 0; c < nc; ++c) {
                              char* r = buf.data() + (size_t)c * rec;
-                             std::memcpy(r, hb + (size_t)c * p, sizeof(double) * p);
-                             std::memcpy(r + 8 * p, hse + (size_t)c * p, sizeof(double) * p);
+                             for (int k = 0; k < T; ++k)  // phenotype k's block: p x nc at hb + k p nc
+                               std::memcpy(r + 8 * p * k, hb + (size_t)k * p * nc + (size_t)c * p,
+                                           sizeof(double) * p);
+                             std::memcpy(r + 8 * p * T, hse + (size_t)c * p, sizeof(double) * p);
                              const int32_t st[2] = {hst[c], 0};
-                             std::memcpy(r + 16 * p, st, 8);
+                             std::memcpy(r + 8 * p * (T + 1), st, 8);
                            }
                            const int64_t first = start + blk * bs;
                            if (!write_all(ofd, buf.data(), (size_t)nc * rec, (int64_t)sizeof h + first * (int64_t)rec))
@@ -845,6 +860,7 @@ int gwas_adjoint_block(gwas_ctx* ctx, const int8_t* XR, int64_t ldx, int ncols, 
   if (!XR || !dh_accum || !dy_accum || ncols < 0 || ncols > ctx->bs || ldx < ctx->n)
     return fail(ctx, GWAS_ERR_ARG, "bad arguments to gwas_adjoint_block");
   if (!(ctx->h > 0.0)) return fail(ctx, GWAS_ERR_ARG, "the adjoint needs h > 0");
+  if (ctx->t != 1) return fail(ctx, GWAS_ERR_UNSUPPORTED, "the adjoint takes one phenotype");
   if (ncols == 0) return GWAS_OK;
   CK(cudaSetDevice(ctx->dev));
   int rc = ensure_adjoint(ctx);
@@ -1183,6 +1199,7 @@ int gwas_batch_create(gwas_batch** out, gwas_ctx* const* studies, int nstudies, 
   for (int i = 0; i < nstudies; ++i) {
     if (!studies[i] || !studies[i]->tcs) return GWAS_ERR_ARG;  // split-precision contexts only
     if (studies[i]->prec != studies[0]->prec || studies[i]->dev != studies[0]->dev) return GWAS_ERR_ARG;
+    if (studies[i]->t != 1) return GWAS_ERR_UNSUPPORTED;  // one phenotype per study in a batch
   }
   gwas_batch* B = new gwas_batch;
   B->ns = nstudies;
@@ -1500,6 +1517,7 @@ void gwas_destroy(gwas_ctx* ctx) { free_all(ctx); }
 
 bool gwas::ctx_view(gwas_ctx* ctx, CtxView* v) {
   if (!ctx || !v) return false;
+  v->t = ctx->t;
   v->dev = ctx->dev;
   v->num_sms = ctx->num_sms;
   v->n = ctx->n;

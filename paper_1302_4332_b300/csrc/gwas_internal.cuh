@@ -44,13 +44,15 @@ struct DevStatus {
 
 // Per-SNP solve constants from the loop-invariant part of Listing 1.
 // With S_TL = C C^T:  Cinv = C^-1, zT = C^-1 r_T, b0 = S_TL^-1 r_T,
-// dSTL_j = (S_TL^-1)_jj.
+// dSTL_j = (S_TL^-1)_jj; zT and b0 per phenotype (t phenotypes share M, X_L and
+// so S_TL; r_T = X~_L^T y~ differs).
+constexpr int TMAX = 16;  // phenotypes sharing one study (q + t <= QMAX + 1 columns of W)
 struct SolveConsts {
   int q;
-  int pad;
+  int t;
   double Cinv[QMAX * QMAX];  // column-major q x q (leading dimension QMAX)
-  double zT[QMAX];
-  double b0[QMAX];
+  double zT[TMAX][QMAX];
+  double b0[TMAX][QMAX];
   double dSTL[QMAX];
   double stl00;  // S_TL[0][0] (uncentered S_BR of a shifted SNP, see reduce_solve.cu)
 };
@@ -113,7 +115,7 @@ cudaError_t launch_build_aop_t(const double* L, const double* Dinv, int n_pad, d
 // a3: G = W^T W (nc x nc, column-major), W n_pad x nc.
 cudaError_t launch_gram(const double* W, int64_t ldw, int n_pad, int nc, double* G, cudaStream_t s);
 // a3: solve constants from G (q covariates), flags S_TL not SPD in st->sc_err.
-cudaError_t launch_solve_consts(const double* G, int q, SolveConsts* sc, DevStatus* st, cudaStream_t s);
+cudaError_t launch_solve_consts(const double* G, int q, int t, SolveConsts* sc, DevStatus* st, cudaStream_t s);
 
 // a7 + a8: per-SNP reductions against W and the p x p solve.
 enum XtKind : int { XT_F64 = 0, XT_F32 = 1 };
@@ -122,11 +124,13 @@ enum XtKind : int { XT_F64 = 0, XT_F32 = 1 };
 // be null): per-SNP integer c_i the SNP column was shifted by before the solve
 // (x' = x - c_i * X_L[:, 0], X_L[:, 0] the intercept); results are mapped back
 // to the unshifted design.
+// t phenotypes: W = [X~_L | Y~] (q + t columns); b holds p x ncols per
+// phenotype, phenotype k at b + k * bstride (bstride 0: p * ncols).
 cudaError_t launch_reduce_solve(const void* Xt, XtKind kind, int64_t ldt, int rows, const double* W,
                                 int64_t ldw, const SolveConsts* sc, int q, int ncols, double* b, double* se,
                                 int* status, cudaStream_t s, const float* W32 = nullptr,
                                 const int8_t* shift = nullptr, DevStatus* st = nullptr, int num_sms = 0,
-                                const CUtensorMap* xmap = nullptr);
+                                const CUtensorMap* xmap = nullptr, int t = 1, int64_t bstride = 0);
 // Opt-in shared memory of the TMA-fed FP32 reduction (called once per split
 // context).  With st, num_sms and xmap (a tiled map of the FP32 X~ buffer:
 // dims {rows, columns}, box {RED_BOX_ROWS, RED_BOX_COLS}, no swizzle) given,
@@ -134,7 +138,7 @@ cudaError_t launch_reduce_solve(const void* Xt, XtKind kind, int64_t ldt, int ro
 // bounded waits reporting into st.
 constexpr int RED_BOX_ROWS = 256, RED_BOX_COLS = 32;
 cudaError_t prepare_reduce_solve();
-int w32_stride(int q);
+int w32_stride(int q);  // q + 1 columns (pass q + t - 1 for t phenotypes)
 cudaError_t launch_make_w32(const double* W, int64_t ldw, int rows, int q, float* W32, cudaStream_t s);
 
 // a11: per-SNP adjoint (chi2, d chi2/dh, y-weights), their sums over SNPs and
@@ -170,6 +174,7 @@ cudaError_t launch_null_residual(const double* W, int64_t ldw, int rows, int q, 
 // live outside the context's own file.
 struct CtxView {
   int dev, num_sms, n, q, n_pad, P;
+  int t;  // phenotypes
   cudaStream_t stream;
   const double* Aop;
   const double* W;

@@ -43,11 +43,12 @@ cudaError_t launch_gram(const double* W, int64_t ldw, int rows, int nc, double* 
 }
 
 // ------------------------------------------------------------ solve constants
-__global__ void solve_consts_kernel(const double* __restrict__ G, int q, SolveConsts* sc, DevStatus* st) {
+__global__ void solve_consts_kernel(const double* __restrict__ G, int q, int t, SolveConsts* sc, DevStatus* st) {
   if (threadIdx.x != 0 || blockIdx.x != 0) return;
-  const int nc = q + 1;
+  const int nc = q + t;  // G = W^T W over [X~_L | Y~]
   double C[QMAX * QMAX];
   sc->q = q;
+  sc->t = t;
   for (int i = 0; i < QMAX * QMAX; ++i) { C[i] = 0.0; sc->Cinv[i] = 0.0; }
   // Cholesky of S_TL = G[0:q, 0:q]
   for (int j = 0; j < q; ++j) {
@@ -71,31 +72,36 @@ __global__ void solve_consts_kernel(const double* __restrict__ G, int q, SolveCo
       sc->Cinv[i + c * QMAX] = v / C[i + i * QMAX];
     }
   }
-  // zT = C^-1 r_T,  b0 = C^-T zT,  dSTL_j = sum_i Cinv_ij^2
-  for (int i = 0; i < q; ++i) {
-    double v = 0.0;
-    for (int t = 0; t <= i; ++t) v += sc->Cinv[i + t * QMAX] * G[t + q * nc];
-    sc->zT[i] = v;
+  // per phenotype k: zT = C^-1 r_T,  b0 = C^-T zT;  dSTL_j = sum_i Cinv_ij^2
+  for (int k = 0; k < t; ++k) {
+    for (int i = 0; i < q; ++i) {
+      double v = 0.0;
+      for (int u = 0; u <= i; ++u) v += sc->Cinv[i + u * QMAX] * G[u + (q + k) * nc];
+      sc->zT[k][i] = v;
+    }
+    for (int j = 0; j < q; ++j) {
+      double v = 0.0;
+      for (int i = j; i < q; ++i) v += sc->Cinv[i + j * QMAX] * sc->zT[k][i];
+      sc->b0[k][j] = v;
+    }
   }
   for (int j = 0; j < q; ++j) {
-    double v = 0.0, d = 0.0;
-    for (int i = j; i < q; ++i) {
-      v += sc->Cinv[i + j * QMAX] * sc->zT[i];
-      d += sc->Cinv[i + j * QMAX] * sc->Cinv[i + j * QMAX];
-    }
-    sc->b0[j] = v;
+    double d = 0.0;
+    for (int i = j; i < q; ++i) d += sc->Cinv[i + j * QMAX] * sc->Cinv[i + j * QMAX];
     sc->dSTL[j] = d;
   }
   sc->stl00 = q > 0 ? G[0] : 0.0;
 }
 
-cudaError_t launch_solve_consts(const double* G, int q, SolveConsts* sc, DevStatus* st, cudaStream_t s) {
-  solve_consts_kernel<<<1, 32, 0, s>>>(G, q, sc, st);
+cudaError_t launch_solve_consts(const double* G, int q, int t, SolveConsts* sc, DevStatus* st, cudaStream_t s) {
+  solve_consts_kernel<<<1, 32, 0, s>>>(G, q, t, sc, st);
   return cudaGetLastError();
 }
 
 // ------------------------------------------------- per-SNP reductions + solve
-// acc[0..q-1] = S_BL, acc[q] = r_B, acc[QM+1] = S_BR (lane 0 after the warp reduction).
+// acc[0..q-1] = S_BL, acc[q + k] = r_B of phenotype k (k < t), acc[QM+1] = S_BR
+// (QM >= q + t - 1).  S, hence d^2, se and the status, is the same for every
+// phenotype; b of phenotype k goes to b + k * bstride.
 // c != 0: the sums are those of the shifted SNP x' = x - c * X_L[:, 0] (X_L[:, 0]
 // the intercept).  [X_L | x'] spans the same space as [X_L | x]:  d^2 and b_p
 // are unchanged, b_0 = b'_0 - c b_p, and with S = T^T S' T (T = I + c e_0 e_p^T)
@@ -104,45 +110,59 @@ cudaError_t launch_solve_consts(const double* G, int q, SolveConsts* sc, DevStat
 template <int QM>
 __device__ __forceinline__ void solve_store(const double (&acc)[QM + 2], const SolveConsts* __restrict__ sc,
                                             int q, int col, double* __restrict__ b, double* __restrict__ se,
-                                            int* __restrict__ status, double c = 0.0) {
+                                            int* __restrict__ status, double c = 0.0, int t = 1,
+                                            int64_t bstride = 0) {
   const int p = q + 1;
-  const double sbr = acc[QM + 1], rb = acc[q];
+  const double sbr = acc[QM + 1];
   const double sbr_test = (c != 0.0 && q > 0) ? sbr + 2.0 * c * acc[0] + c * c * sc->stl00 : sbr;
   double l[QM > 0 ? QM : 1];
-  double ll = 0.0, lz = 0.0;
+  double ll = 0.0;
 #pragma unroll
   for (int i = 0; i < QM; ++i) {
     if (i >= q) break;
     double v = 0.0;
-    for (int t = 0; t <= i; ++t) v = fma(sc->Cinv[i + t * QMAX], acc[t], v);
+    for (int u = 0; u <= i; ++u) v = fma(sc->Cinv[i + u * QMAX], acc[u], v);
     l[i] = v;
     ll = fma(v, v, ll);
-    lz = fma(v, sc->zT[i], lz);
   }
   const double d2 = sbr - ll;
-  double* bo = b + (int64_t)col * p;
   double* so = se ? se + (int64_t)col * p : nullptr;
   if (!(d2 > SINGULAR_TAU * sbr_test)) {
     const double nan = __longlong_as_double(0x7ff8000000000000LL);
-    for (int j = 0; j < p; ++j) {
-      bo[j] = nan;
-      if (so) so[j] = nan;
-    }
+    for (int k = 0; k < t; ++k)
+      for (int j = 0; j < p; ++j) b[k * bstride + (int64_t)col * p + j] = nan;
+    if (so)
+      for (int j = 0; j < p; ++j) so[j] = nan;
     if (status) status[col] = GWAS_SNP_SINGULAR;
     return;
   }
-  const double bp = (rb - lz) / d2;
+  double g[QM > 0 ? QM : 1];  // g = C^-T l (+ c e_0: the shift)
 #pragma unroll
   for (int j = 0; j < QM; ++j) {
     if (j >= q) break;
-    double v = 0.0;  // g_j = (C^-T l)_j
+    double v = 0.0;
     for (int i = j; i < q; ++i) v = fma(sc->Cinv[i + j * QMAX], l[i], v);
     if (j == 0) v += c;
-    bo[j] = sc->b0[j] - bp * v;
+    g[j] = v;
     if (so) so[j] = sqrt(sc->dSTL[j] + v * v / d2);
   }
-  bo[q] = bp;
   if (so) so[q] = sqrt(1.0 / d2);
+  for (int k = 0; k < t; ++k) {
+    double lz = 0.0;
+#pragma unroll
+    for (int i = 0; i < QM; ++i) {
+      if (i >= q) break;
+      lz = fma(l[i], sc->zT[k][i], lz);
+    }
+    const double bp = (acc[q + k] - lz) / d2;
+    double* bo = b + k * bstride + (int64_t)col * p;
+#pragma unroll
+    for (int j = 0; j < QM; ++j) {
+      if (j >= q) break;
+      bo[j] = sc->b0[k][j] - bp * g[j];
+    }
+    bo[q] = bp;
+  }
   if (status) status[col] = GWAS_SNP_OK;
 }
 
@@ -160,7 +180,8 @@ __global__ void __launch_bounds__(256) reduce_solve_kernel(const double* __restr
                                                            const double* __restrict__ W, int64_t ldw,
                                                            const SolveConsts* __restrict__ sc, int q,
                                                            int ncols, double* __restrict__ b,
-                                                           double* __restrict__ se, int* __restrict__ status) {
+                                                           double* __restrict__ se, int* __restrict__ status, int t,
+                                                           int64_t bstride) {
   const int lane = threadIdx.x & 31;
   const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (col >= ncols) return;
@@ -172,11 +193,11 @@ __global__ void __launch_bounds__(256) reduce_solve_kernel(const double* __restr
     const double xv = __ldcs(x + r);
 #pragma unroll
     for (int a = 0; a <= QM; ++a)
-      if (a <= q) acc[a] = fma(xv, W[r + a * ldw], acc[a]);
+      if (a < q + t) acc[a] = fma(xv, W[r + a * ldw], acc[a]);
     acc[QM + 1] = fma(xv, xv, acc[QM + 1]);
   }
   warp_sum<QM>(acc);
-  if (lane == 0) solve_store<QM>(acc, sc, q, col, b, se, status);
+  if (lane == 0) solve_store<QM>(acc, sc, q, col, b, se, status, 0.0, t, bstride);
 }
 
 // FP32 X~ (the split paths).  A block takes 32 SNP columns, one per lane, and
@@ -195,7 +216,7 @@ template <int QM, int WS, int SL>
 __global__ void __launch_bounds__(32 * SL) reduce_solve_f32_kernel(
     const float* __restrict__ Xt, int64_t ldt, int rows, const float* __restrict__ W32,
     const SolveConsts* __restrict__ sc, int q, int ncols, double* __restrict__ b, double* __restrict__ se,
-    int* __restrict__ status, const int8_t* __restrict__ shift) {
+    int* __restrict__ status, const int8_t* __restrict__ shift, int t, int64_t bstride) {
   constexpr int NA = QM + 2, NW4 = WS / 4, NX4 = RS_RUN / 4;
   // the W runs (inside the row loop) and the slice totals (after it) share one buffer
   constexpr int TOT_BYTES = SL * NA * 32 * 8, WSM_BYTES = SL * RS_RUN * NW4 * 16;
@@ -273,7 +294,7 @@ __global__ void __launch_bounds__(32 * SL) reduce_solve_f32_kernel(
     for (int s2 = 1; s2 < SL; ++s2) t += tot[s2][a][lane];
     sum[a] = t;
   }
-  solve_store<QM>(sum, sc, q, col, b, se, status, shift ? (double)shift[col] : 0.0);
+  solve_store<QM>(sum, sc, q, col, b, se, status, shift ? (double)shift[col] : 0.0, t, bstride);
 }
 
 // FP32 X~ streamed by TMA (the split paths, q <= 7).  A persistent block takes
@@ -309,7 +330,7 @@ __global__ void __launch_bounds__(32 * (BCW + 1), 1) reduce_solve_bulk_kernel(
     const float* __restrict__ Xt, int64_t ldt, int rows, const float* __restrict__ W32,
     const SolveConsts* __restrict__ sc, int q, int ncols, double* __restrict__ b, double* __restrict__ se,
     int* __restrict__ status, const int8_t* __restrict__ shift, DevStatus* st,
-    const __grid_constant__ CUtensorMap xmap) {
+    const __grid_constant__ CUtensorMap xmap, int t, int64_t bstride) {
   using K = BulkCfg<WS>;
   constexpr int NA = QM + 2, NW4 = WS / 4, BST = K::ST;
   extern __shared__ __align__(128) uint8_t smem_raw[];
@@ -443,7 +464,7 @@ __global__ void __launch_bounds__(32 * (BCW + 1), 1) reduce_solve_bulk_kernel(
 #pragma unroll
     for (int a = 0; a < NA; ++a) sum[a] = colsum[j][a];
     const int col = c_begin + j;
-    solve_store<QM>(sum, sc, q, col, b, se, status, shift ? (double)shift[col] : 0.0);
+    solve_store<QM>(sum, sc, q, col, b, se, status, shift ? (double)shift[col] : 0.0, t, bstride);
   }
 }
 
@@ -458,17 +479,20 @@ cudaError_t prepare_reduce_solve() {
 cudaError_t launch_reduce_solve(const void* Xt, XtKind kind, int64_t ldt, int rows, const double* W,
                                 int64_t ldw, const SolveConsts* sc, int q, int ncols, double* b, double* se,
                                 int* status, cudaStream_t s, const float* W32, const int8_t* shift,
-                                DevStatus* st, int num_sms, const CUtensorMap* xmap) {
+                                DevStatus* st, int num_sms, const CUtensorMap* xmap, int t, int64_t bstride) {
   if (ncols <= 0) return cudaSuccess;
+  if (t < 1 || q + t > QMAX + 1) return cudaErrorInvalidValue;
+  if (bstride == 0) bstride = (int64_t)(q + 1) * ncols;
+  const int qe = q + t - 1;  // the kernels' bound on the columns of W past the first
   const int grid = (ncols + 7) / 8;
   if (kind == XT_F64) {
     const double* X = static_cast<const double*>(Xt);
-    if (q <= 3)
-      reduce_solve_kernel<3><<<grid, 256, 0, s>>>(X, ldt, rows, W, ldw, sc, q, ncols, b, se, status);
-    else if (q <= 7)
-      reduce_solve_kernel<7><<<grid, 256, 0, s>>>(X, ldt, rows, W, ldw, sc, q, ncols, b, se, status);
+    if (qe <= 3)
+      reduce_solve_kernel<3><<<grid, 256, 0, s>>>(X, ldt, rows, W, ldw, sc, q, ncols, b, se, status, t, bstride);
+    else if (qe <= 7)
+      reduce_solve_kernel<7><<<grid, 256, 0, s>>>(X, ldt, rows, W, ldw, sc, q, ncols, b, se, status, t, bstride);
     else
-      reduce_solve_kernel<QMAX><<<grid, 256, 0, s>>>(X, ldt, rows, W, ldw, sc, q, ncols, b, se, status);
+      reduce_solve_kernel<QMAX><<<grid, 256, 0, s>>>(X, ldt, rows, W, ldw, sc, q, ncols, b, se, status, t, bstride);
     return cudaGetLastError();
   }
   if (!W32) return cudaErrorInvalidValue;
@@ -477,18 +501,23 @@ cudaError_t launch_reduce_solve(const void* Xt, XtKind kind, int64_t ldt, int ro
   const int g32 = (ncols + 31) / 32;
   const int gb = ncols < num_sms ? ncols : num_sms;  // persistent blocks of the bulk-fed kernel
   const bool bulk = xmap && st && num_sms > 0 && rows % 128 == 0 && (ncols + gb - 1) / gb <= BMAXC;
-  if (bulk && q <= 3)
+  if (bulk && qe <= 3)
     reduce_solve_bulk_kernel<3, 4><<<gb, 32 * (BCW + 1), BulkCfg<4>::SMEM, s>>>(X, ldt, rows, W32, sc, q, ncols, b,
-                                                                             se, status, shift, st, *xmap);
-  else if (bulk && q <= 7)
+                                                                             se, status, shift, st, *xmap, t,
+                                                                             bstride);
+  else if (bulk && qe <= 7)
     reduce_solve_bulk_kernel<7, 8><<<gb, 32 * (BCW + 1), BulkCfg<8>::SMEM, s>>>(X, ldt, rows, W32, sc, q, ncols, b,
-                                                                             se, status, shift, st, *xmap);
-  else if (q <= 3)
-    reduce_solve_f32_kernel<3, 4, 16><<<g32, 512, 0, s>>>(X, ldt, rows, W32, sc, q, ncols, b, se, status, shift);
-  else if (q <= 7)
-    reduce_solve_f32_kernel<7, 8, 16><<<g32, 512, 0, s>>>(X, ldt, rows, W32, sc, q, ncols, b, se, status, shift);
+                                                                             se, status, shift, st, *xmap, t,
+                                                                             bstride);
+  else if (qe <= 3)
+    reduce_solve_f32_kernel<3, 4, 16><<<g32, 512, 0, s>>>(X, ldt, rows, W32, sc, q, ncols, b, se, status, shift, t,
+                                                          bstride);
+  else if (qe <= 7)
+    reduce_solve_f32_kernel<7, 8, 16><<<g32, 512, 0, s>>>(X, ldt, rows, W32, sc, q, ncols, b, se, status, shift, t,
+                                                          bstride);
   else
-    reduce_solve_f32_kernel<QMAX, 16, 8><<<g32, 256, 0, s>>>(X, ldt, rows, W32, sc, q, ncols, b, se, status, shift);
+    reduce_solve_f32_kernel<QMAX, 16, 8><<<g32, 256, 0, s>>>(X, ldt, rows, W32, sc, q, ncols, b, se, status, shift,
+                                                             t, bstride);
   return cudaGetLastError();
 }
 

@@ -63,6 +63,7 @@ extern "C" int gwas_solve_block_static(gwas_ctx* ctx, const int8_t* XR, int64_t 
   using namespace gwas;
   CtxView v;
   if (!ctx_view(ctx, &v)) return GWAS_ERR_ARG;
+  if (v.t != 1) return GWAS_ERR_UNSUPPORTED;  // one phenotype
   if (ncols < 0 || ldx < v.n || !XR || !b) return GWAS_ERR_ARG;
   if (ncols == 0) return GWAS_OK;
   if (!is_device(XR) || !is_device(b) || (se && !is_device(se)) || (status && !is_device(status)))

@@ -79,6 +79,15 @@ def test_batch_autotune_and_skipped_study():
             g.close()
 
 
+def test_batch_takes_one_phenotype_per_study():
+    s = gwas_synth.study(300, 4, 600, 0.5, 1.0, seed=30)
+    Y = np.asfortranarray(np.column_stack([s["y"], s["y"]]))
+    with gw.GLS(s["Phi"], s["XL"], Y, 0.5, 1.0, precision="bf16x3", bs=256) as g:
+        with pytest.raises(gw.GwasError) as e:
+            gw.GLSBatch([g])
+        assert e.value.name == "GWAS_ERR_UNSUPPORTED"
+
+
 def test_batch_solve_files_matches_in_memory(tmp_path):
     """Out of core: each study's dosages in its own file (own leading dimension
     and header); the streamed batch equals the in-memory batch step by step and

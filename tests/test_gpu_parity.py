@@ -212,6 +212,50 @@ def test_split_extreme_sigma2(prec, sigma2):
     assert e["b_norm"] <= TOL_SPLIT and e["se_rel"] <= TOL_SPLIT, (prec, sigma2, e)
 
 
+def _phenotypes(s, t, seed=5):
+    """t phenotype columns: the study's y, then y shifted and mixed with independent noise."""
+    rng = np.random.default_rng(seed)
+    cols = [s["y"]] + [0.5 * s["y"] + 0.3 * k + rng.standard_normal(s["n"]) for k in range(1, t)]
+    return np.asfortranarray(np.column_stack(cols))
+
+
+@pytest.mark.parametrize("prec", ("fp64",) + SPLITS)
+@pytest.mark.parametrize("n,p,m,t", [(640, 4, 300, 5), (300, 2, 130, 3), (257, 6, 65, 11)])
+def test_several_phenotypes(prec, n, p, m, t):
+    """t phenotypes sharing one study: b of each equals its own single-phenotype
+    GLS (the oracle run per column of Y); se and status are shared."""
+    s, X, L, _ = _case(n, p, 2 * n, 0.5, m=m)
+    Y = _phenotypes(s, t)
+    tol = TOL64 if prec == "fp64" else TOL_SPLIT
+    with gw.GLS(s["Phi"], s["XL"] if p > 1 else None, Y, 0.5, 1.0, precision=prec, bs=m) as g:
+        b, se_g, st_g = g.solve_block(X)
+        b_s, se_s, st_s = g.solve_stream(np.asfortranarray(X))
+    assert b.shape == (p, m, t)
+    assert np.array_equal(b, b_s) and np.array_equal(se_g, se_s) and np.array_equal(st_g, st_s)
+    for k in range(t):
+        r, se, _, st = oracle.gls(L, s["XL"], Y[:, k], X)
+        e = compare(b[:, :, k], se_g, st_g, r, se, st)
+        assert e["b_norm"] <= tol and e["se_rel"] <= tol, (prec, k, e)
+
+
+def test_several_phenotypes_device_outputs_and_limits():
+    import torch
+    s, X, L, _ = _case(300, 4, 600, 0.5, m=64)
+    Y = _phenotypes(s, 4)
+    with gw.GLS(s["Phi"], s["XL"], Y, 0.5, 1.0, precision="f16x2", bs=64) as g:
+        Xd = torch.from_numpy(np.ascontiguousarray(X.T)).cuda().T
+        b, se_g, st_g = g.solve_block(Xd)
+        g.synchronize()
+        assert tuple(b.shape) == (4, 64, 4) and b.is_cuda
+        b_h, se_h, st_h = g.solve_block(X)
+        assert np.array_equal(b.cpu().numpy(), b_h)
+        with pytest.raises(gw.GwasError) as e:
+            g.adjoint_block(X)
+        assert e.value.name == "GWAS_ERR_UNSUPPORTED"
+    with pytest.raises(gw.GwasError):  # q + t > 16 columns
+        gw.GLS(s["Phi"], s["XL"], _phenotypes(s, 14), 0.5, 1.0, bs=64)
+
+
 @pytest.mark.parametrize("tiles", ("single", "pair_multicast", "pair_mma"))
 def test_f16x2_needs_the_inverse_form(small_study, tiles):
     s, *_ = small_study

@@ -83,6 +83,25 @@ def test_solve_file_out_writes_results_and_resumes(dosage_file, tmp_path, prec):
         assert e.value.name == "GWAS_ERR_IO"
 
 
+def test_solve_file_several_phenotypes(dosage_file, tmp_path):
+    """t phenotypes through the file forms: b is p x m x t, the result file
+    holds every phenotype's b in each record."""
+    path, n, m, ld, header, X = dosage_file
+    s = gwas_synth.study(n, 4, 2000, 0.6, seed=40)
+    rng = np.random.default_rng(3)
+    Y = np.asfortranarray(np.column_stack([s["y"], s["y"] + rng.standard_normal(n), rng.standard_normal(n)]))
+    out = str(tmp_path / "r3.bin")
+    with gw.GLS(s["Phi"], s["XL"], Y, 0.6, 1.0, precision="bf16x3", bs=512) as g:
+        b, se, st = g.solve_file(path, m, ldx=ld, header_bytes=header)
+        assert b.shape == (4, m, 3)
+        ref = [g.solve_block(X[:, c0:c0 + 512]) for c0 in range(0, m, 512)]
+        assert np.array_equal(b, np.concatenate([r[0] for r in ref], axis=1))
+        assert g.solve_file_out(path, m, out, ldx=ld, header_bytes=header) == m
+    head, b2, se2, st2 = gw.read_results(out)
+    assert head["traits"] == 3 and head["record_bytes"] == 8 * 4 * 4 + 8
+    assert np.array_equal(b, b2) and np.array_equal(se, se2) and np.array_equal(st, st2)
+
+
 def test_solve_file_errors(dosage_file):
     path, n, m, ld, header, X = dosage_file
     s = gwas_synth.study(n, 4, 2000, 0.6, seed=40)
