@@ -403,8 +403,9 @@ STUDY_SIZES = (2000, 3500, 5000, 7000, 9000, 11000, 13500, 16000)  # the multi-s
 
 
 def measure_forms(args, out):
-    """The other forms on one GPU (rank 0, N = 1): the multi-study batch, disk
-    streaming of the headline path, the adjoint and the REML fit."""
+    """The other forms on one GPU (rank 0, N = 1): the multi-study batch (in
+    memory and from files), disk streaming (to host memory and disk to disk),
+    several phenotypes sharing one study, the adjoint and the REML fit."""
     import tempfile
     import torch
     import gwas_synth
@@ -491,6 +492,33 @@ def measure_forms(args, out):
                                          bytes_written=64 + done * (16 * w["p"] + 8),
                                          note="gwas_solve_file_out: results written to a file with checkpoints "
                                               "every 16 blocks (fdatasync); input from the page cache")
+    # --- several phenotypes sharing the study (the headline workload, 5 phenotype columns):
+    # one triangular solve per SNP block serves all of them
+    t_ph = 5
+    rng = np.random.default_rng(11)
+    Y = np.asfortranarray(np.column_stack([s["y"]] + [0.5 * s["y"] + rng.standard_normal(n) for _ in range(t_ph - 1)]))
+    blocks_d = [torch.from_numpy(np.ascontiguousarray(X.T)).to(dev).T for X in out["blocks_h"]]
+    with gw.GLS(s["Phi"], s["XL"], Y, w["h"], w["sigma2"], precision="f16x2", bs=bs) as g:
+        b = torch.empty((t_ph, bs, w["p"]), dtype=torch.float64, device=dev).permute(2, 1, 0)
+        se = torch.empty((bs, w["p"]), dtype=torch.float64, device=dev).T
+        st = torch.empty(bs, dtype=torch.int32, device=dev)
+        for X in blocks_d:
+            g.solve_block(X, b, se, st)
+        g.synchronize()
+        reps = max(3, args.steps // 2)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ev0.record()
+        for _ in range(reps):
+            for X in blocks_d:
+                g.solve_block(X, b, se, st)
+        ev1.record()
+        torch.cuda.synchronize()
+        t_s = ev0.elapsed_time(ev1) / 1e3
+    snps = reps * len(blocks_d) * bs
+    forms["phenotypes"] = dict(workload=f"n={n}, p={w['p']}, {t_ph} phenotypes sharing M, f16x2, 4096-SNP blocks",
+                               snps_per_s=snps / t_s, snp_phenotype_tests_per_s=snps * t_ph / t_s,
+                               ms_per_block=1e3 * t_s / (reps * len(blocks_d)))
+    del blocks_d
     # --- the differentiation workload: n = 5,000, p = 4, FP64 adjoint of one 4096-SNP block
     s4 = gwas_synth.study(5000, 4, 5000, 0.5, 1.0, study_id=4)
     X4 = torch.from_numpy(np.ascontiguousarray(gwas_synth.dosages(5000, 0, 4096, study=4).T)).to(dev).T

@@ -1122,6 +1122,9 @@ struct gwas_batch {
   int strip_group = 0;
   int64_t launches = 0;
   int64_t launches_per_step = 0;
+  // per study: the file readers' pinned buffers, kept across gwas_batch_solve_files calls
+  std::vector<std::vector<void*>> file_buf;
+  std::vector<int64_t> file_buf_bytes;
   std::string detail;
 };
 
@@ -1148,6 +1151,8 @@ void batch_free(gwas_batch* B) {
   for (auto* p : B->d_b) cudaFree(p);
   for (auto* p : B->d_se) cudaFree(p);
   for (auto* p : B->d_st) cudaFree(p);
+  for (auto& v : B->file_buf)
+    for (auto* q : v) cudaFreeHost(q);
   if (B->tb) tc::batch_destroy(B->tb);
   if (B->own_stream && B->stream) cudaStreamDestroy(B->stream);
   delete B;
@@ -1380,10 +1385,24 @@ int gwas_batch_solve_files(gwas_batch* B, const char* const* paths, const int64_
   auto close_all = [&]() {
     for (auto* r : rd) gwas_reader_close(r);
   };
+  B->file_buf.resize(ns);
+  B->file_buf_bytes.resize(ns, 0);
   for (int i = 0; i < ns; ++i) {
     if (nblk[i] == 0) continue;
-    const int rc = gwas_reader_open(&rd[i], paths[i], header_bytes[i] + col0[i] * ldx[i], ldx[i] * cols, nblk[i],
-                                    ldx[i] * cols_of(i, nblk[i] - 1), 3);
+    if (B->file_buf_bytes[i] < ldx[i] * cols) {  // (re)allocate study i's pinned read buffers
+      for (auto* q : B->file_buf[i]) cudaFreeHost(q);
+      B->file_buf[i].assign(3, nullptr);
+      B->file_buf_bytes[i] = 0;
+      for (auto& q : B->file_buf[i])
+        if (cudaMallocHost(&q, (size_t)(ldx[i] * cols)) != cudaSuccess) {
+          cudaGetLastError();
+          close_all();
+          return bfail(B, GWAS_ERR_NOMEM, "pinned read buffers");
+        }
+      B->file_buf_bytes[i] = ldx[i] * cols;
+    }
+    const int rc = reader_open_with(&rd[i], paths[i], header_bytes[i] + col0[i] * ldx[i], ldx[i] * cols, nblk[i],
+                                    ldx[i] * cols_of(i, nblk[i] - 1), 3, B->file_buf[i].data());
     if (rc != GWAS_OK) {
       close_all();
       return bfail(B, rc, "cannot open a study's dosage file");
