@@ -353,21 +353,8 @@ __device__ __forceinline__ void mma_commit_pair(uint64_t* bar, uint16_t cta_mask
       : "memory");
 }
 
-// 32 TMEM lanes x 32 consecutive 32-bit columns: thread t of the warp gets
-// lane (base lane + t), columns col .. col + 31.
-__device__ __forceinline__ void tmem_ld_32x32b_x32(uint32_t taddr, uint32_t (&v)[32]) {
-  asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15, "
-      "%16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
-      : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
-        "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15]),
-        "=r"(v[16]), "=r"(v[17]), "=r"(v[18]), "=r"(v[19]), "=r"(v[20]), "=r"(v[21]), "=r"(v[22]), "=r"(v[23]),
-        "=r"(v[24]), "=r"(v[25]), "=r"(v[26]), "=r"(v[27]), "=r"(v[28]), "=r"(v[29]), "=r"(v[30]), "=r"(v[31])
-      : "r"(taddr)
-      : "memory");
-}
-// 32 TMEM lanes x 16 consecutive 32-bit columns.
+// 32 TMEM lanes x 16 consecutive 32-bit columns: thread t of the warp gets
+// lane (base lane + t), columns col .. col + 15.
 __device__ __forceinline__ void tmem_ld_32x32b_x16(uint32_t taddr, uint32_t (&v)[16]) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
@@ -380,23 +367,11 @@ __device__ __forceinline__ void tmem_ld_32x32b_x16(uint32_t taddr, uint32_t (&v)
 __device__ __forceinline__ void tmem_ld_wait() { asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory"); }
 
 // Shared-memory matrix descriptor of a K-major operand tile stored in the
-// 128-byte swizzled canonical layout (rows of 128 bytes, 8-row groups 1024
-// bytes apart; tile base 1024-byte aligned).  Fields: start address >> 4
-// (bits 0-13), leading-dimension byte offset >> 4 (16-29, unused for this
-// layout, set to 1), stride-dimension byte offset >> 4 (32-45) = 1024 >> 4,
-// descriptor version 1 (bits 46-47), layout type 2 = 128-byte swizzle (61-63).
-__device__ __forceinline__ uint64_t sdesc_k128(uint32_t smem_addr) {
-  uint64_t d = 0;
-  d |= static_cast<uint64_t>((smem_addr >> 4) & 0x3FFFu);
-  d |= static_cast<uint64_t>(1u) << 16;
-  d |= static_cast<uint64_t>(1024u >> 4) << 32;
-  d |= static_cast<uint64_t>(1u) << 46;
-  d |= static_cast<uint64_t>(2u) << 61;
-  return d;
-}
-
-// The same for the 64-byte swizzled layout (rows of 64 bytes, 8-row groups
-// 512 bytes apart, layout type 4; tile base 512-byte aligned).
+// 64-byte swizzled canonical layout (rows of 64 bytes, 8-row groups 512 bytes
+// apart; tile base 512-byte aligned).  Fields: start address >> 4 (bits
+// 0-13), leading-dimension byte offset >> 4 (16-29, unused for this layout,
+// set to 1), stride-dimension byte offset >> 4 (32-45) = 512 >> 4, descriptor
+// version 1 (bits 46-47), layout type 4 = 64-byte swizzle (61-63).
 __device__ __forceinline__ uint64_t sdesc_k64(uint32_t smem_addr) {
   uint64_t d = 0;
   d |= static_cast<uint64_t>((smem_addr >> 4) & 0x3FFFu);
