@@ -1049,17 +1049,18 @@ __global__ void __launch_bounds__(THREADS, 1)
 // longest first.  B comes by TMA from the cast copy of the block
 // (cast_shift_kernel: x - c_i as BF16/FP32), so TMA alone fills every stage.
 namespace inv2 {
-constexpr int STAGES = 8;
-
-template <bool TF32>
+// UP: the transposed product X^ = L^-T X~ of the adjoint form (upper
+// triangular A, B the split pieces of X~: two B pieces a stage, six stages)
+template <bool TF32, bool UP = false>
 struct Cfg {
+  static constexpr int STAGES = UP ? 6 : 8;
   static constexpr int ESZ = TF32 ? 4 : 2;
   static constexpr int KCH = 64 / ESZ;
   static constexpr int KMMA = TF32 ? 8 : 16;
   static constexpr int CPB = TB / KCH;
   static constexpr int A_BYTES = TB * 64;                    // one piece of this CTA's L^-1 rows: 8 KB
   static constexpr int B_BYTES = (TN / 2) * 64;              // this CTA's half of the SNP columns: 8 KB
-  static constexpr int STAGE_BYTES = 2 * A_BYTES + B_BYTES;  // 24 KB
+  static constexpr int STAGE_BYTES = 2 * A_BYTES + (UP ? 2 : 1) * B_BYTES;  // 24 KB (32 KB)
   static constexpr int CHUNK_BYTES = 2048;
   static constexpr int STG_OFF = STAGES * STAGE_BYTES;
   static constexpr int BAR_OFF = STG_OFF + EPI_WARPS * 2 * CHUNK_BYTES;
@@ -1072,10 +1073,14 @@ struct Cfg {
 // F16 (with TF32 false): L^-1 pieces and the cast block are FP16; row r of
 // L^-1 was scaled by 1 / rscale[r] (a power of two) before the split, so the
 // epilogue multiplies its results back by rscale[r].
-template <bool TF32, bool F16 = false>
+// UP: the adjoint's X^ = L^-T X~ with the split pieces of L^-T (upper
+// triangular: pair row u multiplies K-blocks 2u .. P-1) and B the hi/lo
+// pieces of the forward X~ (BhiH, BloH): three products a K-step; the
+// FP32 X^ goes out through the StX map the launch sets.
+template <bool TF32, bool F16 = false, bool UP = false>
 __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_constant__ TcBatch b) {
-  using K = inv2::Cfg<TF32>;
-  constexpr int ST = inv2::STAGES;
+  using K = inv2::Cfg<TF32, UP>;
+  constexpr int ST = K::STAGES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + K::BAR_OFF);
@@ -1123,7 +1128,12 @@ __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_co
     for (int q = 0; q < b.nstudies; ++q) {
       ptx::prefetch_tensormap(&b.maps[q].Ahi);
       ptx::prefetch_tensormap(&b.maps[q].Alo);
-      ptx::prefetch_tensormap(&b.maps[q].XcH);
+      if (UP) {
+        ptx::prefetch_tensormap(&b.maps[q].BhiH);
+        ptx::prefetch_tensormap(&b.maps[q].BloH);
+      } else {
+        ptx::prefetch_tensormap(&b.maps[q].XcH);
+      }
     }
   }
   if (warp == 2) {
@@ -1166,10 +1176,11 @@ __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_co
         const pair2::Unit u = pair2::make_unit(row, S);
         const int arow = rank == 0 ? u.k0 : (u.paired ? u.k0 + 1 : -1);  // this CTA's row panel
         const int ycol = c * TN + (int)rank * (TN / 2);                   // this CTA's SNP columns
+        const int j0 = UP ? u.k0 : 0, j1 = UP ? S.P : u.nkb;              // the unit's K-blocks
         bool ok = true;
-        for (int j = 0; j < u.nkb && ok; ++j) {
-          // block (arow, j) above the diagonal, or no rows: a box wholly outside reads zeros
-          const int ay = (arow >= 0 && j <= arow) ? arow * TB : -TB;
+        for (int j = j0; j < j1 && ok; ++j) {
+          // a block outside the triangle, or no rows: a box wholly outside reads zeros
+          const int ay = (arow >= 0 && (UP ? j >= arow : j <= arow)) ? arow * TB : -TB;
           for (int h = 0; h < K::CPB; ++h, ++cnt) {
             const int s = cnt % ST;
             const uint32_t r = cnt / ST;
@@ -1183,7 +1194,12 @@ __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_co
               ptx::mbar_arrive_peer_count(fb);
             ptx::tma_load_2d_pair(sb, &M.Ahi, fb, kx, ay);
             ptx::tma_load_2d_pair(sb + K::A_BYTES, &M.Alo, fb, kx, ay);
-            ptx::tma_load_2d_pair(sb + 2 * K::A_BYTES, &M.XcH, fb, kx, ycol);
+            if (UP) {
+              ptx::tma_load_2d_pair(sb + 2 * K::A_BYTES, &M.BhiH, fb, kx, ycol);
+              ptx::tma_load_2d_pair(sb + 2 * K::A_BYTES + K::B_BYTES, &M.BloH, fb, kx, ycol);
+            } else {
+              ptx::tma_load_2d_pair(sb + 2 * K::A_BYTES, &M.XcH, fb, kx, ycol);
+            }
           }
         }
         if (!ok) break;
@@ -1206,8 +1222,9 @@ __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_co
         TcStudy S;
         decode_tile(b, t, sidx, row, c, S);
         const pair2::Unit u = pair2::make_unit(row, S);
+        const int nkb = UP ? S.P - u.k0 : u.nkb;
         bool ok = true;
-        for (int j = 0; j < u.nkb && ok; ++j) {
+        for (int j = 0; j < nkb && ok; ++j) {
           // every K-block into a fresh partial (promoted by the epilogue)
           const int a = kb & 1;
           if (!ptx::mbar_wait(&part_empty[a], ((kb >> 1) & 1) ^ 1, st)) { ok = false; break; }
@@ -1226,9 +1243,10 @@ __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_co
               const uint32_t off = kk * K::KMMA * K::ESZ;
               const uint64_t ahi = ptx::sdesc_k64(base + off);
               const uint64_t alo = ptx::sdesc_k64(base + K::A_BYTES + off);
-              const uint64_t bx = ptx::sdesc_k64(base + 2 * K::A_BYTES + off);
+              const uint64_t bx = ptx::sdesc_k64(base + 2 * K::A_BYTES + off);  // B, or B's hi piece
               ptx::mma_pair<TF32>(d, alo, bx, idesc, accumulate);
               accumulate = 1;
+              if (UP) ptx::mma_pair<TF32>(d, ahi, ptx::sdesc_k64(base + 2 * K::A_BYTES + K::B_BYTES + off), idesc, 1);
               ptx::mma_pair<TF32>(d, ahi, bx, idesc, 1);
             }
             ptx::mma_commit_pair(&empty[s], BOTH);
@@ -1265,7 +1283,8 @@ __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_co
 #pragma unroll
       for (int i = 0; i < EPI_COLS; ++i) master[i] = 0.f;
       bool ok = true;
-      for (int pp = 0; pp < u.nkb && ok; ++pp) {
+      const int nkb = UP ? S.P - u.k0 : u.nkb;
+      for (int pp = 0; pp < nkb && ok; ++pp) {
         const int a = kb & 1;
         if (!ptx::group_and(1, NT, ptx::mbar_wait(&part_full[a], (kb >> 1) & 1, st))) { ok = false; break; }
         ptx::tc_fence_after();
@@ -1401,6 +1420,9 @@ static cudaError_t set_attrs(bool clusters) {
   if ((e = cudaFuncSetAttribute(trsm_tc_pair_mma_kernel<TF32>, A, pair2::Cfg<TF32>::SMEM)) != cudaSuccess) return e;
   if (!TF32 && (e = cudaFuncSetAttribute(trsm_tc_inv_kernel<false, true>, A, inv2::Cfg<false>::SMEM)) != cudaSuccess)
     return e;
+  if ((e = cudaFuncSetAttribute(trsm_tc_inv_kernel<TF32, false, true>, A, inv2::Cfg<TF32, true>::SMEM)) !=
+      cudaSuccess)
+    return e;
   return cudaFuncSetAttribute(trsm_tc_inv_kernel<TF32>, A, inv2::Cfg<TF32>::SMEM);
 }
 
@@ -1454,6 +1476,20 @@ cudaError_t launch_solve(bool tf32, TileMode mode, const TcBatch& b, int num_sms
   else
     trsm_tc_kernel<false, false><<<grid, THREADS, Cfg<false>::SMEM, s>>>(b);
   return cudaGetLastError();
+}
+
+template <bool TF32>
+static cudaError_t launch_inv_up(const TcBatch& b, int max_clusters, cudaStream_t s) {
+  const int ncl = b.ntiles < max_clusters ? b.ntiles : max_clusters;
+  cudaLaunchAttribute attr[1];
+  cudaLaunchConfig_t cfg = pair_config<TF32>(attr, 2 * ncl, s, TILES_INVERSE);
+  cfg.dynamicSmemBytes = inv2::Cfg<TF32, true>::SMEM;
+  return cudaLaunchKernelEx(&cfg, trsm_tc_inv_kernel<TF32, false, true>, b);
+}
+
+cudaError_t launch_inverse_upper(bool tf32, const TcBatch& b, int max_clusters, cudaStream_t s) {
+  const cudaError_t e = tf32 ? launch_inv_up<true>(b, max_clusters, s) : launch_inv_up<false>(b, max_clusters, s);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 cudaError_t launch_upper(bool tf32, const TcBatch& b, int grid, cudaStream_t s) {

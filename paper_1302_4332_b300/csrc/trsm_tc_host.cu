@@ -419,6 +419,7 @@ struct TcState {
   void* xhhi = nullptr;
   void* xhlo = nullptr;
   CUtensorMap mAhiT, mAloT, mBhiT, mBloT;
+  CUtensorMap mStXh;  // inverse form: the FP32 X^ by the epilogue's store chunks
   void* xc = nullptr;  // inverse form: the cast block x - c_i (n_pad x bs, BF16, FP32 or FP16)
   bool f16 = false;           // inverse form with FP16 pieces of L^-1 (row-scaled) and an FP16 cast block
   float* rscale = nullptr;    // f16: per-row scale of L^-1 (n_pad)
@@ -744,11 +745,88 @@ static cudaError_t build_inverse(TcState* t, const double* Aop, cudaStream_t s, 
 }
 
 // ------------------------------------------------------ transpose solve (adjoint)
+// The inverse form's transpose product reads L^-T: the pieces of L^-1, transposed
+// (a split commutes with the transpose).  32 x 32 tiles through shared memory.
+template <typename T>
+__global__ void transpose_square_kernel(const T* __restrict__ src, T* __restrict__ dst, int n) {
+  __shared__ T tile[32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) tile[ty + 8 * i][tx] = src[(int64_t)(r0 + ty + 8 * i) * n + c0 + tx];
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 4; ++i) dst[(int64_t)(c0 + ty + 8 * i) * n + r0 + tx] = tile[tx][ty + 8 * i];
+}
+
+// The FP16 form's row-scaled pieces back to values (rscale[r] (hi + lo): exact
+// in FP32), transposed and split again as BF16 hi + lo: the operand pieces of
+// the transpose product, which takes the forward solve's BF16 X~ pieces as B.
+__global__ void transpose_resplit_f16_kernel(const __half* __restrict__ hi, const __half* __restrict__ lo,
+                                             const float* __restrict__ rscale, __nv_bfloat16* __restrict__ thi,
+                                             __nv_bfloat16* __restrict__ tlo, int n) {
+  __shared__ float tile[32][33];
+  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int r = r0 + ty + 8 * i;
+    const int64_t idx = (int64_t)r * n + c0 + tx;
+    tile[ty + 8 * i][tx] = __ldg(rscale + r) * (__half2float(hi[idx]) + __half2float(lo[idx]));
+  }
+  __syncthreads();
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const float v = tile[tx][ty + 8 * i];
+    const __nv_bfloat16 h = __float2bfloat16_rn(v);
+    const int64_t idx = (int64_t)(c0 + ty + 8 * i) * n + r0 + tx;
+    thi[idx] = h;
+    tlo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
+  }
+}
+
 cudaError_t ensure_transpose(TcState* t, const double* AopT, cudaStream_t s, int64_t* launches) {
   if (t->ahiT) return cudaSuccess;
   const size_t esz = t->tf32 ? 4 : 2;
   const size_t np = (size_t)t->n_pad, n2 = np * np;
   cudaError_t e;
+  if (t->mode == TILES_INVERSE) {
+    // X^ = L^-T X~ as a product with the transposed pieces of L^-1 (BF16 ones
+    // for the FP16 form: the forward X~ pieces are BF16)
+    if ((e = cudaMalloc(&t->ahiT, esz * n2)) != cudaSuccess || (e = cudaMalloc(&t->aloT, esz * n2)) != cudaSuccess ||
+        (e = cudaMalloc(&t->xh32, sizeof(float) * np * t->bs)) != cudaSuccess)
+      return e;
+    const dim3 grid((unsigned)(np / 32), (unsigned)(np / 32));
+    int nl = 2;
+    if (t->f16) {
+      transpose_resplit_f16_kernel<<<grid, dim3(32, 8), 0, s>>>(
+          static_cast<const __half*>(t->ahi), static_cast<const __half*>(t->alo), t->rscale,
+          static_cast<__nv_bfloat16*>(t->ahiT), static_cast<__nv_bfloat16*>(t->aloT), (int)np);
+      nl = 1;
+    } else if (t->tf32) {
+      transpose_square_kernel<float><<<grid, dim3(32, 8), 0, s>>>(static_cast<const float*>(t->ahi),
+                                                                  static_cast<float*>(t->ahiT), (int)np);
+      transpose_square_kernel<float><<<grid, dim3(32, 8), 0, s>>>(static_cast<const float*>(t->alo),
+                                                                  static_cast<float*>(t->aloT), (int)np);
+    } else {
+      transpose_square_kernel<uint16_t><<<grid, dim3(32, 8), 0, s>>>(static_cast<const uint16_t*>(t->ahi),
+                                                                     static_cast<uint16_t*>(t->ahiT), (int)np);
+      transpose_square_kernel<uint16_t><<<grid, dim3(32, 8), 0, s>>>(static_cast<const uint16_t*>(t->alo),
+                                                                     static_cast<uint16_t*>(t->aloT), (int)np);
+    }
+    *launches += nl;
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
+    const CUtensorMapDataType dt = t->tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
+    const uint32_t kch = t->tf32 ? Cfg<true>::KCH : Cfg<false>::KCH;
+    if ((e = make_map(t->encode, &t->mAhiT, dt, t->ahiT, np, np, esz * np, kch, TB, true)) != cudaSuccess ||
+        (e = make_map(t->encode, &t->mAloT, dt, t->aloT, np, np, esz * np, kch, TB, true)) != cudaSuccess ||
+        (e = make_map(t->encode, &t->mStXh, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, t->xh32, np, t->bs, 4 * np, 32,
+                      inv2::ST_COLS, false)) != cudaSuccess ||
+        (e = make_map(t->encode, &t->mRedH, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, t->xh32, np, t->bs, 4 * np,
+                      RED_BOX_ROWS, RED_BOX_COLS, false)) != cudaSuccess)
+      return e;
+    return cudaSuccess;
+  }
   if ((e = cudaMalloc(&t->ahiT, esz * n2)) != cudaSuccess || (e = cudaMalloc(&t->aloT, esz * n2)) != cudaSuccess ||
       (e = cudaMalloc(&t->xh32, sizeof(float) * np * t->bs)) != cudaSuccess ||
       (!t->tf32 && (e = cudaMalloc(&t->xhhi, 2 * np * t->bs)) != cudaSuccess) ||
@@ -781,6 +859,26 @@ cudaError_t run_transpose(TcState* t, int ncols, cudaStream_t s, int64_t* launch
   const int C = (ncols + TN - 1) / TN;
   cudaError_t e = cudaMemsetAsync(t->sched, 0, 128 + sizeof(int) * (size_t)t->P * C, s);
   if (e != cudaSuccess) return e;
+  if (t->mode == TILES_INVERSE) {
+    // row-panel pairs in their natural order: pair row 0 (P K-blocks) is the longest
+    TcStudy& S = b.s0;
+    S.P = t->P;
+    S.C = C;
+    S.ncols = ncols;
+    S.n = t->n;
+    S.ldt = t->ldt;
+    b.maps[0].Ahi = t->mAhiT;
+    b.maps[0].Alo = t->mAloT;
+    b.maps[0].BhiH = t->mBhiH;  // the forward solve's X~ pieces
+    b.maps[0].BloH = t->mBloH;
+    b.maps[0].StX = t->mStXh;
+    b.nstudies = 1;
+    b.ntiles = unit_rows(t) * C;
+    b.counter = t->sched;
+    b.st = t->st;
+    ++*launches;
+    return launch_inverse_upper(t->tf32, b, t->max_clusters, s);
+  }
   TcStudy& S = b.s0;
   S.P = t->P;
   S.C = C;

@@ -102,6 +102,9 @@ cudaError_t launch_solve(bool tf32, TileMode mode, const TcBatch& b, int num_sms
                          cudaStream_t s, bool f16 = false);
 // The transpose solve of the adjoint form (single CTAs, grid CTAs).
 cudaError_t launch_upper(bool tf32, const TcBatch& b, int grid, cudaStream_t s);
+// The same as the product with the split L^-T (inverse form; 2-CTA clusters
+// over row-panel pairs, units handed out in the order of b.order).
+cudaError_t launch_inverse_upper(bool tf32, const TcBatch& b, int max_clusters, cudaStream_t s);
 
 }  // namespace tc
 }  // namespace gwas
