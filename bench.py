@@ -69,6 +69,8 @@ def parse_args():
                          "set-up, row-panel pairs per cluster)")
     ap.add_argument("--no-substitution", action="store_true",
                     help="with --tiles auto: skip the kernel-only measurement of the blocked substitution (pair_mma)")
+    ap.add_argument("--separate-sums", action="store_true",
+                    help="inverse form: the per-SNP sums as a separate pass over X~ instead of inside the solve")
     ap.add_argument("--fp64-steps", type=int, default=None,
                     help="steps of the fp64 path when a split path is the headline (default 1)")
     return ap.parse_args()
@@ -300,7 +302,7 @@ def run_ours(args, rank, world, local_rank, dist):
         sg = STRIP_GROUP if args.strip_group is None else args.strip_group
         g = gw.GLS(s["Phi"], s["XL"], s["y"], w["h"], w["sigma2"], precision=path, bs=bs,
                    strip_group=sg if path != "fp64" else 0, tiles=tiles if path != "f16x2" or tiles == "auto"
-                   else "inverse")
+                   else "inverse", separate_sums=args.separate_sums)
         init_s = time.time() - t_init
         b = torch.empty((bs, p), dtype=torch.float64, device=dev).T
         se = torch.empty((bs, p), dtype=torch.float64, device=dev).T

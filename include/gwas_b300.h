@@ -108,7 +108,11 @@ typedef struct {
                       holds t consecutive p x ncols (or p x m) column-major blocks, phenotype k at
                       b + k p ncols.  Batches, the adjoint, REML and gwas_solve_block_static take t = 1
                       (else GWAS_ERR_UNSUPPORTED) */
-  int reserved[1]; /* must be zero */
+  int separate_sums; /* inverse tile mode (with p - 1 + t <= 8): 0 (default) forms the per-SNP sums
+                        x~ . [X~_L | Y~] and x~ . x~ inside the solve's launch (two idle warps per SM read
+                        each stored tile back from L2; the launch leaves FP32 hi/lo partial sums per row
+                        panel that a small pass adds in FP64); 1 keeps them a separate pass over X~.
+                        Other modes and sizes always use the separate pass */
 } gwas_config;
 
 enum {

@@ -251,9 +251,13 @@ int run_block(gwas_ctx* ctx, const void* X, bool int8_input, int64_t ldx, int nc
   }
   {
     StageMark m(ctx, GWAS_STAGE_REDUCE, ctx->stream);
-    CK(launch_reduce_solve(tc::xt_f32(ctx->tcs), XT_F32, tc::xt_ld(ctx->tcs), ctx->n_pad, ctx->W, ctx->n_pad,
-                           ctx->sc, ctx->q, ncols, b, se, status, ctx->stream, ctx->W32, tc::shift_of(ctx->tcs),
-                           ctx->st, ctx->num_sms, tc::xt_reduce_map(ctx->tcs), ctx->t));
+    if (const float* red = tc::partials(ctx->tcs))  // the sums were formed inside the solve
+      CK(launch_partials_solve(red, tc::partial_groups(ctx->tcs), tc::partial_ld(ctx->tcs), ctx->sc, ctx->q, ctx->t,
+                               ncols, b, se, status, tc::shift_of(ctx->tcs), ctx->stream));
+    else
+      CK(launch_reduce_solve(tc::xt_f32(ctx->tcs), XT_F32, tc::xt_ld(ctx->tcs), ctx->n_pad, ctx->W, ctx->n_pad,
+                             ctx->sc, ctx->q, ncols, b, se, status, ctx->stream, ctx->W32, tc::shift_of(ctx->tcs),
+                             ctx->st, ctx->num_sms, tc::xt_reduce_map(ctx->tcs), ctx->t));
   }
   ctx->launches += 1;
   return GWAS_OK;
@@ -367,8 +371,7 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
       cfg.precision < GWAS_FP64 || cfg.precision > GWAS_F16X2 ||
       (cfg.precision == GWAS_F16X2 && cfg.tile_mode != GWAS_TILES_AUTO && cfg.tile_mode != GWAS_TILES_INVERSE))
     return GWAS_ERR_ARG;
-  for (int r : cfg.reserved)
-    if (r != 0) return GWAS_ERR_ARG;
+  if (cfg.separate_sums != 0 && cfg.separate_sums != 1) return GWAS_ERR_ARG;
   const int traits = cfg.traits == 0 ? 1 : cfg.traits;
   if (traits < 1 || traits > TMAX || p - 1 + traits > QMAX + 1) return GWAS_ERR_ARG;
 
@@ -504,6 +507,7 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
       CK(dmalloc(&ctx->W32, sizeof(float) * np * w32_stride(nw - 1)));
       CK(launch_make_w32(ctx->W, ctx->n_pad, ctx->n_pad, nw - 1, ctx->W32, ctx->stream));
       CK(prepare_reduce_solve());
+      if (!cfg.separate_sums) CK(tc::set_reductions(ctx->tcs, ctx->W32, w32_stride(nw - 1), nw));
       ctx->launches += 1;
     }
 
@@ -1176,9 +1180,13 @@ int batch_capture(gwas_batch* B, const std::vector<int>& cols, int order, int gr
   for (int i = 0; i < B->ns && e == cudaSuccess; ++i) {
     gwas_ctx* c = B->ctx[i];
     if (cols[i] == 0) continue;
-    e = launch_reduce_solve(tc::xt_f32(c->tcs), XT_F32, tc::xt_ld(c->tcs), c->n_pad, c->W, c->n_pad, c->sc, c->q,
-                            cols[i], B->d_b[i], B->d_se[i], B->d_st[i], B->stream, c->W32, tc::shift_of(c->tcs),
-                            c->st, c->num_sms, tc::xt_reduce_map(c->tcs));
+    if (const float* red = tc::partials(c->tcs))
+      e = launch_partials_solve(red, tc::partial_groups(c->tcs), tc::partial_ld(c->tcs), c->sc, c->q, 1, cols[i],
+                                B->d_b[i], B->d_se[i], B->d_st[i], tc::shift_of(c->tcs), B->stream);
+    else
+      e = launch_reduce_solve(tc::xt_f32(c->tcs), XT_F32, tc::xt_ld(c->tcs), c->n_pad, c->W, c->n_pad, c->sc, c->q,
+                              cols[i], B->d_b[i], B->d_se[i], B->d_st[i], B->stream, c->W32, tc::shift_of(c->tcs),
+                              c->st, c->num_sms, tc::xt_reduce_map(c->tcs));
     ++nl;
   }
   cudaGraph_t g = nullptr;

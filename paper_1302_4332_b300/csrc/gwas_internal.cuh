@@ -137,6 +137,11 @@ cudaError_t launch_reduce_solve(const void* Xt, XtKind kind, int64_t ldt, int ro
 // launch_reduce_solve streams X~ through it: one persistent block per SM,
 // bounded waits reporting into st.
 constexpr int RED_BOX_ROWS = 256, RED_BOX_COLS = 32;
+// The per-SNP sums formed by the inverse form's epilogue (tc::partials): their
+// FP64 totals over the row groups, then the solve (q + t <= 8).
+cudaError_t launch_partials_solve(const float* red, int ngroups, int64_t ldr, const SolveConsts* sc, int q, int t,
+                                  int ncols, double* b, double* se, int* status, const int8_t* shift,
+                                  cudaStream_t s, int64_t bstride = 0);
 cudaError_t prepare_reduce_solve();
 int w32_stride(int q);  // q + 1 columns (pass q + t - 1 for t phenotypes)
 cudaError_t launch_make_w32(const double* W, int64_t ldw, int rows, int q, float* W32, cudaStream_t s);

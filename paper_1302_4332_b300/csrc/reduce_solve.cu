@@ -118,12 +118,12 @@ __device__ __forceinline__ void solve_store(const double (&acc)[QM + 2], const S
   double l[QM > 0 ? QM : 1];
   double ll = 0.0;
 #pragma unroll
-  for (int i = 0; i < QM; ++i) {
-    if (i >= q) break;
+  for (int i = 0; i < QM; ++i) {  // compile-time indices keep l and g in registers
     double v = 0.0;
+#pragma unroll
     for (int u = 0; u <= i; ++u) v = fma(sc->Cinv[i + u * QMAX], acc[u], v);
-    l[i] = v;
-    ll = fma(v, v, ll);
+    l[i] = i < q ? v : 0.0;
+    ll = fma(l[i], l[i], ll);
   }
   const double d2 = sbr - ll;
   double* so = se ? se + (int64_t)col * p : nullptr;
@@ -136,31 +136,31 @@ __device__ __forceinline__ void solve_store(const double (&acc)[QM + 2], const S
     if (status) status[col] = GWAS_SNP_SINGULAR;
     return;
   }
-  double g[QM > 0 ? QM : 1];  // g = C^-T l (+ c e_0: the shift)
+  const double rd2 = 1.0 / d2;  // one division: the chain of FP64 operations per SNP is the solve's latency
+  double g[QM > 0 ? QM : 1];    // g = C^-T l (+ c e_0: the shift)
 #pragma unroll
   for (int j = 0; j < QM; ++j) {
-    if (j >= q) break;
     double v = 0.0;
-    for (int i = j; i < q; ++i) v = fma(sc->Cinv[i + j * QMAX], l[i], v);
+#pragma unroll
+    for (int i = j; i < QM; ++i) v = fma(sc->Cinv[i + j * QMAX], l[i], v);  // l[i] = 0 for i >= q
     if (j == 0) v += c;
     g[j] = v;
-    if (so) so[j] = sqrt(sc->dSTL[j] + v * v / d2);
+    if (so && j < q) so[j] = sqrt(sc->dSTL[j] + v * v * rd2);
   }
-  if (so) so[q] = sqrt(1.0 / d2);
+  if (so) so[q] = sqrt(rd2);
   for (int k = 0; k < t; ++k) {
     double lz = 0.0;
 #pragma unroll
-    for (int i = 0; i < QM; ++i) {
-      if (i >= q) break;
-      lz = fma(l[i], sc->zT[k][i], lz);
-    }
-    const double bp = (acc[q + k] - lz) / d2;
+    for (int i = 0; i < QM; ++i) lz = fma(l[i], sc->zT[k][i], lz);
+    double rb = 0.0;  // acc[q + k] without a run-time index (which would put acc in local memory)
+#pragma unroll
+    for (int a = 0; a <= QM; ++a)
+      if (a == q + k) rb = acc[a];
+    const double bp = (rb - lz) * rd2;
     double* bo = b + k * bstride + (int64_t)col * p;
 #pragma unroll
-    for (int j = 0; j < QM; ++j) {
-      if (j >= q) break;
-      bo[j] = sc->b0[k][j] - bp * g[j];
-    }
+    for (int j = 0; j < QM; ++j)
+      if (j < q) bo[j] = sc->b0[k][j] - bp * g[j];
     bo[q] = bp;
   }
   if (status) status[col] = GWAS_SNP_OK;
@@ -518,6 +518,80 @@ cudaError_t launch_reduce_solve(const void* Xt, XtKind kind, int64_t ldt, int ro
   else
     reduce_solve_f32_kernel<QMAX, 16, 8><<<g32, 256, 0, s>>>(X, ldt, rows, W32, sc, q, ncols, b, se, status, shift,
                                                              t, bstride);
+  return cudaGetLastError();
+}
+
+// The second half of the sums formed by the inverse form's epilogue: per SNP
+// column, the total of the 32-row FP32 partials over all row groups, then the
+// p x p solve.  A block takes 16 columns (64-byte plane rows) in 32 slices of
+// row groups, four groups in flight per thread; every sum is a double-FP32
+// pair (B300's FP64 pipe is too narrow for a few million FP64 adds per block):
+// each slice over its groups, then the slices pairwise in a fixed tree, so
+// the result does not depend on scheduling.  FP64 from the column totals on.
+constexpr int PS_COLS = 16, PS_SLICES = 32;
+
+template <int QM>
+__global__ void __launch_bounds__(PS_COLS * PS_SLICES)
+    partials_solve_kernel(const float* __restrict__ red, int ngroups, int nw, int64_t ldr,
+                          const SolveConsts* __restrict__ sc, int q, int ncols, double* __restrict__ b,
+                          double* __restrict__ se, int* __restrict__ status, const int8_t* __restrict__ shift, int t,
+                          int64_t bstride) {
+  __shared__ float2 part[PS_SLICES][QM + 2][PS_COLS];
+  __shared__ SolveConsts scs;  // the solves' constants next to the solving threads
+  for (int i = threadIdx.x; i < (int)(sizeof(SolveConsts) / 4); i += blockDim.x)
+    reinterpret_cast<int*>(&scs)[i] = reinterpret_cast<const int*>(sc)[i];
+  const int cl = threadIdx.x % PS_COLS, slice = threadIdx.x / PS_COLS;
+  const int col = blockIdx.x * PS_COLS + cl;
+  const int64_t group = (int64_t)(nw + 1) * ldr;
+  float hi[QM + 2], lo[QM + 2];
+#pragma unroll
+  for (int a = 0; a < QM + 2; ++a) hi[a] = lo[a] = 0.f;
+  if (col < ncols) {
+#pragma unroll 4
+    for (int g = slice; g < ngroups; g += PS_SLICES) {
+      const float* r = red + g * group + col;
+      float v[QM + 2];
+#pragma unroll
+      for (int a = 0; a <= QM; ++a) v[a] = a < nw ? __ldcs(r + a * ldr) : 0.f;  // W's columns: X~_L, then Y~
+      v[QM + 1] = __ldcs(r + nw * ldr);                                         // x~ . x~
+#pragma unroll
+      for (int a = 0; a < QM + 2; ++a) ptx::df_add(hi[a], lo[a], v[a], 0.f);
+    }
+  }
+#pragma unroll
+  for (int a = 0; a < QM + 2; ++a) part[slice][a][cl] = make_float2(hi[a], lo[a]);
+  for (int w = PS_SLICES / 2; w >= 1; w >>= 1) {
+    __syncthreads();
+    if (slice < w) {
+#pragma unroll
+      for (int a = 0; a < QM + 2; ++a) {
+        const float2 o = part[slice + w][a][cl];
+        ptx::df_add(hi[a], lo[a], o.x, o.y);
+        part[slice][a][cl] = make_float2(hi[a], lo[a]);
+      }
+    }
+  }
+  if (slice != 0 || col >= ncols) return;
+  double acc[QM + 2];
+#pragma unroll
+  for (int a = 0; a < QM + 2; ++a) acc[a] = (double)hi[a] + (double)lo[a];
+  solve_store<QM>(acc, &scs, q, col, b, se, status, shift ? (double)shift[col] : 0.0, t, bstride);
+}
+
+cudaError_t launch_partials_solve(const float* red, int ngroups, int64_t ldr, const SolveConsts* sc, int q, int t,
+                                  int ncols, double* b, double* se, int* status, const int8_t* shift,
+                                  cudaStream_t s, int64_t bstride) {
+  if (ncols <= 0) return cudaSuccess;
+  const int nw = q + t;
+  if (t < 1 || nw > 8) return cudaErrorInvalidValue;
+  if (bstride == 0) bstride = (int64_t)(q + 1) * ncols;
+  const int grid = (ncols + PS_COLS - 1) / PS_COLS;
+  if (nw <= 4)
+    partials_solve_kernel<3><<<grid, PS_COLS * PS_SLICES, 0, s>>>(red, ngroups, nw, ldr, sc, q, ncols, b, se, status,
+                                                                  shift, t, bstride);
+  else
+    partials_solve_kernel<7><<<grid, PS_COLS * PS_SLICES, 0, s>>>(red, ngroups, nw, ldr, sc, q, ncols, b, se, status,
+                                                                  shift, t, bstride);
   return cudaGetLastError();
 }
 

@@ -1049,6 +1049,109 @@ __global__ void __launch_bounds__(THREADS, 1)
 // longest first.  B comes by TMA from the cast copy of the block
 // (cast_shift_kernel: x - c_i as BF16/FP32), so TMA alone fills every stage.
 namespace inv2 {
+// Fused sums: the staging of one epilogue warp (4 KB) holds a transposition
+// buffer for 32 rows x 16 columns and, from FS_W_OFF, the warp's 32 rows of W.
+// Rows 0..15 sit at row * 20 floats, rows 16..31 at 336 + (row - 16) * 20:
+// a row's 16 floats go in as four 16-byte stores (8 lanes per phase on 32
+// distinct banks) and a column comes out with lanes 0..15 on rows 0..15 and
+// lanes 16..31 on rows 16..31 (banks c and 16 + c).
+constexpr int FS_W_OFF = 2688;
+__device__ __forceinline__ int fs_idx(int row, int col) { return (row & 15) * 20 + (row >> 4) * 336 + col; }
+static_assert((336 + 15 * 20 + 16) * 4 <= FS_W_OFF && FS_W_OFF + 32 * 8 * 4 <= 4096, "fused-sum staging");
+
+// The per-SNP sums of Listing 1 over one CTA's 128 rows of a tile, formed in
+// place of storing X~: per SNP column, x~ . W[:, a] (a < nw) and x~ . x~.
+// master holds this lane's row (the epilogue warp's 32 rows x 128 columns)
+// before its scale rs (the FP16 form's power of two; else 1).  16 columns at
+// a time go through the warp's transposition buffer; lane (ci, h) sums rows
+// 16h .. 16h+15 of column ci in FP32 FMAs and one shuffle adds the halves.
+// WS = 4 (nw <= 4): the four row quarters (warps lq = 0..3 of the same column
+// half) then add their 32-row sums through shared memory in a fixed order and
+// write one plane per (row panel k, quantity a): red[(k (nw+1) + a) ldr + j].
+// WS = 8: each warp writes its 32-row sums, plane ((4k + lq)(nw+1) + a).
+// `grp` is the staging of warp lq = 0 of this column half (warp lq's at
+// grp + 4 KB lq); named barrier 2 + chalf holds the half's 4 warps.
+template <int WS>
+__device__ __forceinline__ void tile_sums(const float (&master)[EPI_COLS], float rs, uint8_t* grp, int lq, int chalf,
+                                          float* red, int64_t ldr, int k, int nw, int lane, int cols_left) {
+  const int ci = lane & 15, h = lane >> 4;
+  uint8_t* stg = grp + lq * 2 * 2048;
+  float* sm = reinterpret_cast<float*>(stg);
+  const float* wsm = reinterpret_cast<const float*>(stg + FS_W_OFF);
+  const int nq = nw + 1;
+  float keep[4][WS + 1];  // WS = 4: this lane's half of the chunks' sums (chunks 4h .. 4h+3)
+#pragma unroll
+  for (int q = 0; q < EPI_COLS / 16; ++q) {
+    float4* dst = reinterpret_cast<float4*>(sm + fs_idx(lane, 0));
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+      dst[j] = make_float4(master[q * 16 + 4 * j] * rs, master[q * 16 + 4 * j + 1] * rs,
+                           master[q * 16 + 4 * j + 2] * rs, master[q * 16 + 4 * j + 3] * rs);
+    __syncwarp();
+    float acc[WS + 1];
+#pragma unroll
+    for (int a = 0; a <= WS; ++a) acc[a] = 0.f;
+#pragma unroll 2
+    for (int r = 0; r < 16; ++r) {
+      const float x = sm[fs_idx(16 * h + r, ci)];
+      const float4* wr = reinterpret_cast<const float4*>(wsm + (16 * h + r) * WS);
+#pragma unroll
+      for (int v = 0; v < WS / 4; ++v) {
+        const float4 w = wr[v];
+        acc[4 * v] = fmaf(x, w.x, acc[4 * v]);
+        acc[4 * v + 1] = fmaf(x, w.y, acc[4 * v + 1]);
+        acc[4 * v + 2] = fmaf(x, w.z, acc[4 * v + 2]);
+        acc[4 * v + 3] = fmaf(x, w.w, acc[4 * v + 3]);
+      }
+      acc[WS] = fmaf(x, x, acc[WS]);
+    }
+#pragma unroll
+    for (int a = 0; a <= WS; ++a) acc[a] += __shfl_xor_sync(0xffffffffu, acc[a], 16);
+    if constexpr (WS == 4) {
+#pragma unroll
+      for (int a = 0; a <= WS; ++a) keep[q & 3][a] = (h == (q >> 2)) ? acc[a] : keep[q & 3][a];
+    } else {
+      float* out = red + (int64_t)(4 * k + lq) * nq * ldr + q * 16 + ci;
+      if (h == 0 && q * 16 + ci < cols_left) {
+#pragma unroll
+        for (int a = 0; a < WS; ++a)
+          if (a < nw) out[a * ldr] = acc[a];
+        out[nw * ldr] = acc[WS];
+      }
+    }
+    __syncwarp();
+  }
+  if constexpr (WS == 4) {
+    // exchange: this warp's sums at [chunk][a][column] in its transposition
+    // buffer (8 x 5 x 16 floats), then warp lq adds chunks 2lq, 2lq+1 over the
+    // four row quarters in order 0..3 and writes the panel's plane
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int a = 0; a <= WS; ++a) sm[((4 * h + j) * (WS + 1) + a) * 16 + ci] = keep[j][a];
+    auto half_bar = [&] {  // the 4 warps of this column half
+      if (chalf == 0)
+        ptx::named_bar(2, 128);
+      else
+        ptx::named_bar(3, 128);
+    };
+    half_bar();
+    const int q = 2 * lq + h;
+    if (q * 16 + ci < cols_left) {
+      float* out = red + (int64_t)k * nq * ldr + q * 16 + ci;
+#pragma unroll
+      for (int a = 0; a <= WS; ++a) {
+        float v = 0.f;
+#pragma unroll
+        for (int w = 0; w < 4; ++w) v += reinterpret_cast<const float*>(grp + w * 2 * 2048)[(q * (WS + 1) + a) * 16 + ci];
+        if (a < nw) out[a * ldr] = v;
+        if (a == WS) out[nw * ldr] = v;
+      }
+    }
+    half_bar();  // the buffers are free for the next tile
+  }
+}
+
 // UP: the transposed product X^ = L^-T X~ of the adjoint form (upper
 // triangular A, B the split pieces of X~: two B pieces a stage, six stages)
 template <bool TF32, bool UP = false>
@@ -1067,6 +1170,7 @@ struct Cfg {
   static constexpr int NBARS = 2 * STAGES + 4 + 3 * TRING + 1;
   static constexpr int SMEM = 1024 + BAR_OFF + NBARS * 8 + TRING * 4 + 16;
   static_assert(SMEM <= 232448, "shared memory per CTA");
+  static_assert(CHUNK_BYTES == 2048, "the fused sums take 4 KB of staging per epilogue warp");
 };
 }  // namespace inv2
 
@@ -1280,6 +1384,19 @@ __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_co
       const pair2::Unit u = pair2::make_unit(row, S);
       const bool has = leader || u.paired;  // this CTA has a tile
       const int k = u.k0 + (int)rank;
+      uint8_t* stg = smem + K::STG_OFF + e * 2 * K::CHUNK_BYTES;  // this warp's 4 KB of staging
+      if (!UP && S.red && has) {
+        // fused sums: this warp's 32 rows of W into its staging (read at the
+        // tile's end; the copies land while the partials are added)
+        if (gq > 0) {  // stores of an earlier tile still reading the staging buffers
+          if (lane == 0) ptx::bulk_wait_read<0>();
+          __syncwarp();
+        }
+        const float* wsrc = S.w32 + (int64_t)(k * TB + 32 * lq + lane) * S.ws;
+        float* wdst = reinterpret_cast<float*>(stg + inv2::FS_W_OFF) + lane * S.ws;
+        for (int v = 0; v < S.ws; v += 4) ptx::cp_async16(wdst + v, wsrc + v);
+        ptx::cp_async_commit();
+      }
 #pragma unroll
       for (int i = 0; i < EPI_COLS; ++i) master[i] = 0.f;
       bool ok = true;
@@ -1309,11 +1426,22 @@ __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_co
       // X~ of this CTA's tile to HBM by TMA stores of shared-memory chunks (and,
       // for the transpose solve of the adjoint form, its hi/lo pieces)
       const TcMaps& M = b.maps[sidx];
-      uint8_t* stg = smem + K::STG_OFF + e * 2 * K::CHUNK_BYTES;
       const int r0 = k * TB + 32 * lq;
       const int c0 = c * TN + chalf * EPI_COLS;
-      if constexpr (F16) {  // this thread's row back to the scale of L^-1 (exact: a power of two)
-        const float rs = __ldg(S.rscale + r0 + lane);
+      // F16: this thread's row back to the scale of L^-1 (exact: a power of two)
+      const float rs = F16 ? __ldg(S.rscale + r0 + lane) : 1.f;
+      if (!UP && S.red) {
+        // the per-SNP sums of Listing 1 in place of the store
+        ptx::cp_async_wait_all();  // this lane's W row
+        __syncwarp();
+        uint8_t* grp = smem + K::STG_OFF + 4 * chalf * 2 * K::CHUNK_BYTES;
+        if (S.ws == 4)
+          inv2::tile_sums<4>(master, rs, grp, lq, chalf, S.red + c0, S.ldr, k, S.nw, lane, S.ncols - c0);
+        else
+          inv2::tile_sums<8>(master, rs, grp, lq, chalf, S.red + c0, S.ldr, k, S.nw, lane, S.ncols - c0);
+        continue;
+      }
+      if constexpr (F16) {
 #pragma unroll
         for (int i = 0; i < EPI_COLS; ++i) master[i] *= rs;
       }

@@ -74,6 +74,18 @@ const float* xhat_f32(const TcState* t);
 const CUtensorMap* xhat_reduce_map(const TcState* t);  // xhat_f32() as the reduction's tiled map
 
 const float* xt_f32(const TcState* t);
+// Inverse form: the per-SNP sums of x~ with W = [X~_L | Y~] (FP32, row-major,
+// row stride ws = 4 or 8, nw <= 8 columns) and of x~ with itself formed by the
+// solve's epilogue, which then stores no X~ (a block solved for the adjoint
+// still stores it).  Other modes or sizes: no change (the sums stay a separate
+// pass over xt_f32()).
+cudaError_t set_reductions(TcState* t, const float* w32, int ws, int nw);
+// The last block's partial sums, or null when the block stored X~ instead:
+// partial_groups(t) row groups x (nw + 1) quantities, each a plane of
+// partial_ld(t) floats with SNP column j at offset j.
+const float* partials(const TcState* t);
+int partial_groups(const TcState* t);
+int64_t partial_ld(const TcState* t);
 const CUtensorMap* xt_reduce_map(const TcState* t);  // xt_f32() as the reduction's tiled map
 const int8_t* shift_of(const TcState* t);  // per-SNP shifts of the last block, or null
 int64_t xt_ld(const TcState* t);

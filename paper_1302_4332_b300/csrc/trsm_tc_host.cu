@@ -423,6 +423,11 @@ struct TcState {
   void* xc = nullptr;  // inverse form: the cast block x - c_i (n_pad x bs, BF16, FP32 or FP16)
   bool f16 = false;           // inverse form with FP16 pieces of L^-1 (row-scaled) and an FP16 cast block
   float* rscale = nullptr;    // f16: per-row scale of L^-1 (n_pad)
+  // inverse form: the per-SNP sums fused into the launch (set_reductions)
+  const float* w32 = nullptr;  // W in FP32, row-major, row stride ws
+  int ws = 0, nw = 0;
+  float* red = nullptr;        // partials: P (ws 4) or 4P (ws 8) groups of nw + 1 planes of bs floats
+  bool red_last = false;       // the last block's sums are in red
   EncodeTiledFn encode = nullptr;
 };
 
@@ -641,6 +646,11 @@ static cudaError_t prepare_study(TcState* t, const int8_t* X, int64_t ldx, int n
   S->blo = t->blo;
   S->ldt = t->ldt;
   S->rscale = t->f16 ? t->rscale : nullptr;
+  S->w32 = t->w32;
+  S->red = t->red;
+  S->ws = t->ws;
+  S->nw = t->nw;
+  S->ldr = t->bs;
   return cudaSuccess;
 }
 
@@ -673,6 +683,8 @@ cudaError_t run_block(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaS
   b.counter = t->sched;
   b.st = t->st;
   b.pieces = pieces ? 1 : 0;
+  if (pieces) b.s0.red = nullptr;  // the adjoint reads X~ itself
+  t->red_last = b.s0.red != nullptr;
   const bool inv = t->mode == TILES_INVERSE;
   if (inv || (t->strip_group > 0 && t->strip_group < b.s0.C)) {
     if (t->order_C != b.s0.C) {  // (re)build the order for this strip count
@@ -907,6 +919,19 @@ cudaError_t run_transpose(TcState* t, int ncols, cudaStream_t s, int64_t* launch
 
 const float* xhat_f32(const TcState* t) { return t->xh32; }
 
+cudaError_t set_reductions(TcState* t, const float* w32, int ws, int nw) {
+  if (t->red || t->mode != TILES_INVERSE || nw < 1 || nw > 8 || (ws != 4 && ws != 8) || ws < nw) return cudaSuccess;
+  cudaError_t e = cudaMalloc(&t->red, sizeof(float) * (size_t)t->P * 4 * (nw + 1) * t->bs);
+  if (e != cudaSuccess) return e;
+  t->w32 = w32;
+  t->ws = ws;
+  t->nw = nw;
+  return cudaSuccess;
+}
+const float* partials(const TcState* t) { return t->red_last ? t->red : nullptr; }
+int partial_groups(const TcState* t) { return t->ws == 4 ? t->P : 4 * t->P; }  // row panels or their quarters
+int64_t partial_ld(const TcState* t) { return t->bs; }
+
 // ------------------------------------------------------------- batched launch
 struct TcBatchState {
   int nstudies = 0;
@@ -995,6 +1020,12 @@ cudaError_t batch_plan(TcBatchState* B, TcState* const* ts, const int8_t* const*
     S[i].blo = t->blo;
     S[i].ldt = t->ldt;
     S[i].rscale = t->f16 ? t->rscale : nullptr;
+    S[i].w32 = t->w32;
+    S[i].red = t->red;
+    S[i].ws = t->ws;
+    S[i].nw = t->nw;
+    S[i].ldr = t->bs;
+    t->red_last = ncols[i] > 0 && t->red != nullptr;
     pmax = unit_rows(t) > pmax ? unit_rows(t) : pmax;
     total += unit_rows(t) * S[i].C;
   }
@@ -1104,6 +1135,7 @@ void destroy(TcState* t) {
   cudaFree(t->ahiT);
   cudaFree(t->aloT);
   cudaFree(t->xh32);
+  cudaFree(t->red);
   cudaFree(t->xhhi);
   cudaFree(t->xhlo);
   cudaFree(t->ahi);

@@ -51,6 +51,16 @@ struct TcStudy {
   void* blo;            // lo piece of X~ (BF16 or FP32)
   int64_t ldt;
   const float* rscale;  // inverse form with FP16 pieces: row r of L^-1 was split scaled by 1 / rscale[r]
+  // inverse form, per-SNP sums formed by the epilogue in place of storing X~
+  // (red null: X~ is stored for a separate reduction pass): W = [X~_L | Y~] in
+  // FP32, row-major, row stride ws (4 or 8), nw <= ws columns; the partial
+  // sums for SNP column j, a < nw: x~ . W[:, a], a = nw: x~ . x~, over the 128
+  // rows of row panel k at red[(k (nw + 1) + a) ldr + j] (ws 4), or over the
+  // 32 rows of its quarter g at red[((4k + g)(nw + 1) + a) ldr + j] (ws 8)
+  const float* w32;
+  float* red;
+  int ws, nw;
+  int64_t ldr;
 };
 
 // The tensor maps of one study: block operator hi/lo, X~ hi/lo, int8 block.
