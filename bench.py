@@ -354,7 +354,8 @@ def run_ours(args, rank, world, local_rank, dist):
             prods = 2 if mode == "inverse" else 3
             pk = base / prods
             roof = dict(bound="tensor", achieved=achieved, peak=pk, unit="TFLOP/s", frac=achieved / pk,
-                        traffic=kernel_traffic(path, mode),
+                        traffic=kernel_traffic(path, mode + ("_separate_sums" if args.separate_sums and
+                                                             mode == "inverse" else "")),
                         peak_basis=(f"{'tf32' if path == 'tf32x3' else 'bf16'} dense tensor peak (of measured, "
                                     f"burst) / {prods}: {prods} split products per algorithmic product "
                                     f"({mode} tile mode)"))

@@ -538,11 +538,19 @@ __global__ void __launch_bounds__(PS_COLS * PS_SLICES)
                           int64_t bstride) {
   __shared__ float2 part[PS_SLICES][QM + 2][PS_COLS];
   __shared__ SolveConsts scs;  // the solves' constants next to the solving threads
-  for (int i = threadIdx.x; i < (int)(sizeof(SolveConsts) / 4); i += blockDim.x)
-    reinterpret_cast<int*>(&scs)[i] = reinterpret_cast<const int*>(sc)[i];
   const int cl = threadIdx.x % PS_COLS, slice = threadIdx.x / PS_COLS;
   const int col = blockIdx.x * PS_COLS + cl;
   const int64_t group = (int64_t)(nw + 1) * ldr;
+  // every global load is issued before the first use of any (one round trip):
+  // this thread's share of the constants, the SNP's shift, its partials
+  constexpr int NW = (int)(sizeof(SolveConsts) / 4), NT = PS_COLS * PS_SLICES, SCW = (NW + NT - 1) / NT;
+  int scw[SCW];
+#pragma unroll
+  for (int j = 0; j < SCW; ++j) {
+    const int i = (int)threadIdx.x + j * NT;
+    scw[j] = i < NW ? __ldg(reinterpret_cast<const int*>(sc) + i) : 0;
+  }
+  const double cshift = (slice == 0 && col < ncols && shift) ? (double)__ldg(shift + col) : 0.0;
   float hi[QM + 2], lo[QM + 2];
 #pragma unroll
   for (int a = 0; a < QM + 2; ++a) hi[a] = lo[a] = 0.f;
@@ -560,7 +568,12 @@ __global__ void __launch_bounds__(PS_COLS * PS_SLICES)
   }
 #pragma unroll
   for (int a = 0; a < QM + 2; ++a) part[slice][a][cl] = make_float2(hi[a], lo[a]);
-  for (int w = PS_SLICES / 2; w >= 1; w >>= 1) {
+#pragma unroll
+  for (int j = 0; j < SCW; ++j) {
+    const int i = (int)threadIdx.x + j * NT;
+    if (i < NW) reinterpret_cast<int*>(&scs)[i] = scw[j];
+  }
+  for (int w = PS_SLICES / 2; w >= 1; w >>= 1) {  // the first barrier also publishes scs
     __syncthreads();
     if (slice < w) {
 #pragma unroll
@@ -575,7 +588,7 @@ __global__ void __launch_bounds__(PS_COLS * PS_SLICES)
   double acc[QM + 2];
 #pragma unroll
   for (int a = 0; a < QM + 2; ++a) acc[a] = (double)hi[a] + (double)lo[a];
-  solve_store<QM>(acc, &scs, q, col, b, se, status, shift ? (double)shift[col] : 0.0, t, bstride);
+  solve_store<QM>(acc, &scs, q, col, b, se, status, cshift, t, bstride);
 }
 
 cudaError_t launch_partials_solve(const float* red, int ngroups, int64_t ldr, const SolveConsts* sc, int q, int t,

@@ -238,6 +238,37 @@ def test_several_phenotypes(prec, n, p, m, t):
         assert e["b_norm"] <= tol and e["se_rel"] <= tol, (prec, k, e)
 
 
+@pytest.mark.parametrize("prec", SPLITS)
+@pytest.mark.parametrize("n,p,m,t", [(1000, 4, 1000, 1), (300, 2, 257, 3), (640, 4, 300, 5), (129, 2, 65, 1)])
+def test_fused_and_separate_sums(prec, n, p, m, t):
+    """Inverse form: the per-SNP sums formed in the solve's epilogue (the
+    default; one plane per row panel when p - 1 + t <= 4, per row quarter up to
+    8) against the separate pass over a stored X~: both at the oracle's bar, and
+    equal to each other up to summation order.  A block solved for the adjoint
+    (which stores X~) in between leaves the next block's fused sums intact."""
+    s, X, L, _ = _case(n, p, 2 * n, 0.5, sigma2=1.3, m=m)
+    Y = _phenotypes(s, t) if t > 1 else s["y"]
+    XL = s["XL"] if p > 1 else None
+    out = {}
+    for sep in (False, True):
+        with gw.GLS(s["Phi"], XL, Y, 0.5, 1.3, precision=prec, bs=m, tiles="inverse", separate_sums=sep) as g:
+            out[sep] = g.solve_block(X)
+            if t == 1 and p > 1:
+                g.adjoint_block(X[:, : m // 2])
+                again = g.solve_block(X)
+                assert all(np.array_equal(a, c) for a, c in zip(out[sep], again))
+    for k in range(t):
+        yk = Y[:, k] if t > 1 else Y
+        r, se, _, st = oracle.gls(L, s["XL"], yk, X)
+        for sep in (False, True):
+            b = out[sep][0][:, :, k] if t > 1 else out[sep][0]
+            e = compare(b, out[sep][1], out[sep][2], r, se, st)
+            assert e["b_norm"] <= TOL_SPLIT and e["se_rel"] <= TOL_SPLIT, (prec, sep, k, e)
+    assert np.array_equal(out[False][2], out[True][2])
+    ok = out[True][2] == 0
+    assert np.allclose(out[False][1][:, ok], out[True][1][:, ok], rtol=1e-6, atol=0)
+
+
 def test_several_phenotypes_device_outputs_and_limits():
     import torch
     s, X, L, _ = _case(300, 4, 600, 0.5, m=64)
