@@ -343,8 +343,10 @@ int gwas_copy_factor(gwas_ctx *ctx, double *L, int64_t ld);
 /* Stage timing with CUDA events recorded around each stage on the stream the
  * stage runs on; for measurement only (a few microseconds per event pair).
  * Stages: GWAS_STAGE_H2D (block copy in), GWAS_STAGE_TRSM (the blocked
- * triangular solve), GWAS_STAGE_REDUCE (reductions + p x p solves),
- * GWAS_STAGE_D2H (results out).  gwas_timing_enable(ctx, 1) clears and starts
+ * triangular solve, with the split paths' cast or shift pre-pass),
+ * GWAS_STAGE_REDUCE (reductions + p x p solves), GWAS_STAGE_D2H (results
+ * out), GWAS_STAGE_SOLVE (the solve kernel's launch alone, inside
+ * GWAS_STAGE_TRSM).  gwas_timing_enable(ctx, 1) clears and starts
  * the accumulators, 0 stops them.  gwas_timing_read waits for the recorded
  * events and writes the summed milliseconds and the number of timed launches
  * per stage into ms[GWAS_NSTAGES] and count[GWAS_NSTAGES]. */
@@ -352,7 +354,8 @@ int gwas_copy_factor(gwas_ctx *ctx, double *L, int64_t ld);
 #define GWAS_STAGE_TRSM 1
 #define GWAS_STAGE_REDUCE 2
 #define GWAS_STAGE_D2H 3
-#define GWAS_NSTAGES 4
+#define GWAS_STAGE_SOLVE 4
+#define GWAS_NSTAGES 5
 int gwas_timing_enable(gwas_ctx *ctx, int enable);
 int gwas_timing_read(gwas_ctx *ctx, double *ms, int64_t *count);
 

@@ -44,7 +44,7 @@ EXPORTS = (
     "gwas_reader_release", "gwas_reader_error_detail", "gwas_reader_close",
 )
 GWAS_RESUME = 1
-STAGES = ("h2d", "trsm", "reduce", "d2h")
+STAGES = ("h2d", "trsm", "reduce", "d2h", "solve")
 
 
 class GwasError(RuntimeError):
@@ -463,9 +463,10 @@ class GLS:
         self._check(load().gwas_timing_enable(self._ctx, int(bool(enable))))
 
     def timing_read(self) -> dict:
-        """{stage: (total ms, timed launches)} for h2d, trsm, reduce, d2h."""
-        ms = (ctypes.c_double * 4)()
-        cnt = (ctypes.c_int64 * 4)()
+        """{stage: (total ms, timed launches)} for h2d, trsm, reduce, d2h, and
+        solve (the solve kernel alone, inside trsm)."""
+        ms = (ctypes.c_double * len(STAGES))()
+        cnt = (ctypes.c_int64 * len(STAGES))()
         self._check(load().gwas_timing_read(self._ctx, ms, cnt))
         return {name: (ms[i], int(cnt[i])) for i, name in enumerate(STAGES)}
 

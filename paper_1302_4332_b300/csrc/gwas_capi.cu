@@ -223,6 +223,7 @@ int run_block(gwas_ctx* ctx, const void* X, bool int8_input, int64_t ldx, int nc
     a.sched = ctx->sched; a.st = ctx->st;
     {
       StageMark m(ctx, GWAS_STAGE_TRSM, ctx->stream);
+      StageMark k(ctx, GWAS_STAGE_SOLVE, ctx->stream);
       CK(launch_trsm_f64(a, int8_input, ctx->stream, ctx->num_sms));
     }
     ctx->launches += 1;
@@ -245,7 +246,14 @@ int run_block(gwas_ctx* ctx, const void* X, bool int8_input, int64_t ldx, int nc
   {
     StageMark m(ctx, GWAS_STAGE_TRSM, ctx->stream);
     int64_t nl = 0;
-    cudaError_t e = tc::run_block(ctx->tcs, X8, ldx, ncols, ctx->stream, &nl);
+    cudaEvent_t k0 = ctx->timing ? pool_event(ctx) : nullptr, k1 = ctx->timing ? pool_event(ctx) : nullptr;
+    cudaError_t e = tc::run_block(ctx->tcs, X8, ldx, ncols, ctx->stream, &nl, false, k0, k1);
+    if (ctx->timing && e == cudaSuccess) {
+      ctx->marks.push_back({GWAS_STAGE_SOLVE, k0, k1});
+    } else if (ctx->timing) {
+      ctx->event_pool.push_back(k0);
+      ctx->event_pool.push_back(k1);
+    }
     ctx->launches += nl;
     if (e != cudaSuccess) return fail(ctx, GWAS_ERR_CUDA, "split-precision solve: %s", cudaGetErrorString(e));
   }

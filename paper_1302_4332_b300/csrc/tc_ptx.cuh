@@ -433,6 +433,17 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl)
   lo = l - (hi - s);
 }
 
+// d0 += a * b0 and d1 += a * b1 as one packed instruction (two FP32 FMAs,
+// each rounded to nearest: the same results as two fmaf).
+__device__ __forceinline__ void fma2(float& d0, float& d1, float a, float b0, float b1) {
+  uint64_t d, av, bv;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(d) : "f"(d0), "f"(d1));
+  asm("mov.b64 %0, {%1, %1};" : "=l"(av) : "f"(a));
+  asm("mov.b64 %0, {%1, %2};" : "=l"(bv) : "f"(b0), "f"(b1));
+  asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(d) : "l"(av), "l"(bv));
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(d0), "=f"(d1) : "l"(d));
+}
+
 // After a failed (timed-out or aborted) wait: 2 ms for bulk copies already in
 // flight to land, so that none writes shared memory of a retired block.
 __device__ __forceinline__ void settle() {

@@ -1064,7 +1064,8 @@ static_assert((336 + 15 * 20 + 16) * 4 <= FS_W_OFF && FS_W_OFF + 32 * 8 * 4 <= 4
 // master holds this lane's row (the epilogue warp's 32 rows x 128 columns)
 // before its scale rs (the FP16 form's power of two; else 1).  16 columns at
 // a time go through the warp's transposition buffer; lane (ci, h) sums rows
-// 16h .. 16h+15 of column ci in FP32 FMAs and one shuffle adds the halves.
+// 16h .. 16h+15 of column ci in FP32 FMAs (packed in pairs) and one shuffle
+// adds the halves.
 // WS = 4 (nw <= 4): the four row quarters (warps lq = 0..3 of the same column
 // half) then add their 32-row sums through shared memory in a fixed order and
 // write one plane per (row panel k, quantity a): red[(k (nw+1) + a) ldr + j].
@@ -1098,10 +1099,8 @@ __device__ __forceinline__ void tile_sums(const float (&master)[EPI_COLS], float
 #pragma unroll
       for (int v = 0; v < WS / 4; ++v) {
         const float4 w = wr[v];
-        acc[4 * v] = fmaf(x, w.x, acc[4 * v]);
-        acc[4 * v + 1] = fmaf(x, w.y, acc[4 * v + 1]);
-        acc[4 * v + 2] = fmaf(x, w.z, acc[4 * v + 2]);
-        acc[4 * v + 3] = fmaf(x, w.w, acc[4 * v + 3]);
+        ptx::fma2(acc[4 * v], acc[4 * v + 1], x, w.x, w.y);
+        ptx::fma2(acc[4 * v + 2], acc[4 * v + 3], x, w.z, w.w);
       }
       acc[WS] = fmaf(x, x, acc[WS]);
     }

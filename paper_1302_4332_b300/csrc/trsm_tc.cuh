@@ -45,8 +45,9 @@ cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_p
 // pieces: the hi/lo pieces of X~ are also stored (the substitution modes
 // always store them; the inverse form only when asked: the transpose solve
 // of the adjoint form reads them).
+// ev0 / ev1 (optional): recorded on s right before and after the solve kernel.
 cudaError_t run_block(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaStream_t s, int64_t* launches,
-                      bool pieces = false);
+                      bool pieces = false, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
 
 // The batching form: one persistent launch over several studies (each with its
 // own operator and buffers; all BF16 or all TF32).  ts[i] solves ncols[i]

@@ -662,7 +662,7 @@ static cudaError_t launch_kernel(bool tf32, TileMode mode, const TcBatch& b, int
 }
 
 cudaError_t run_block(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaStream_t s, int64_t* launches,
-                      bool pieces) {
+                      bool pieces, cudaEvent_t ev0, cudaEvent_t ev1) {
   if (ncols <= 0) return cudaSuccess;
   TcBatch b;
   memset(&b, 0, sizeof b);
@@ -704,7 +704,10 @@ cudaError_t run_block(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaS
     }
     b.order = t->order;  // the study descriptor stays b.s0 (studies null)
   }
-  return launch_kernel(t->tf32, t->mode, b, t->num_sms, t->max_clusters, s, launches, t->f16);
+  if (ev0 && (e = cudaEventRecord(ev0, s)) != cudaSuccess) return e;
+  if ((e = launch_kernel(t->tf32, t->mode, b, t->num_sms, t->max_clusters, s, launches, t->f16)) != cudaSuccess)
+    return e;
+  return ev1 ? cudaEventRecord(ev1, s) : cudaSuccess;
 }
 
 // Inverse form set-up: L^-1 = the substitution applied to the identity, on

@@ -427,3 +427,19 @@ def test_full_size_sampled(paper_scale, prec, tiles):
             assert e["b_norm"] <= tb and e["se_rel"] <= ts, (prec, e)
             if prec != "fp64":  # significant components, one by one (see COMP_TOL)
                 assert e["b_comp_max"] <= COMP_TOL[prec], (prec, e)
+
+
+@pytest.mark.parametrize("prec", ("fp64", "f16x2"))
+def test_stage_timing(small_study, prec):
+    """Per-stage CUDA-event timers: the solve kernel's launches are timed on
+    their own (inside the trsm stage, which also holds the split pre-pass)."""
+    s, X, L, _ = small_study
+    with gw.GLS(s["Phi"], s["XL"], s["y"], s["h"], s["sigma2"], precision=prec, bs=512) as g:
+        g.timing(True)
+        for c0 in (0, 512):
+            g.solve_block(X[:, c0:c0 + 512])
+        st = g.timing_read()
+        g.timing(False)
+    assert set(st) == {"h2d", "trsm", "reduce", "d2h", "solve"}
+    assert st["trsm"][1] == st["solve"][1] == st["reduce"][1] == 2
+    assert 0.0 < st["solve"][0] <= st["trsm"][0] and st["reduce"][0] > 0.0
