@@ -605,6 +605,28 @@ def error_report(res_path, oracle_out, blocks_h, s, w):
     return compare(b, se, st, r, se_o, st_o)
 
 
+def storage_precision_study(oracle_out, blocks_h, s, w, errors):
+    """Whether single precision is enough to store the operator: b and se of
+    the sampled SNPs against the FP64 oracle with L^-1 held as its split pair
+    (the split paths as measured) and as its hi piece alone (one BF16, TF32
+    or row-scaled FP16 rounding: `single_piece`), next to the FP64 path."""
+    import paper_1302_4332_b300 as gw
+    import oracle
+    from oracle.metrics import compare
+    X = np.asfortranarray(blocks_h[0][:, :64])
+    r, se_o, _, st_o = oracle.gls(oracle_out[0], s["XL"], s["y"], X)
+    study = {"sample": "first 64 SNPs of block 0, n=%d, p=%d" % (w["n"], w["p"]),
+             "fp64": errors.get("fp64")}
+    for path in ("bf16x3", "tf32x3", "f16x2"):
+        if path not in gw.BUILT_PRECISIONS:
+            continue
+        with gw.GLS(s["Phi"], s["XL"], s["y"], w["h"], w["sigma2"], precision=path, bs=64,
+                    single_piece=True) as g:
+            b, se, st = g.solve_block(X)
+        study[path] = {"split_pair": errors.get(path), "single_piece": compare(b, se, st, r, se_o, st_o)}
+    return study
+
+
 def main():
     args = parse_args()
     world = int(os.environ.get("WORLD_SIZE", "1"))
@@ -647,6 +669,12 @@ def main():
                 errors[path] = error_report(res, oracle_out, out["blocks_h"], out["s"], w)
             except Exception as e:  # report, do not hide
                 errors[path] = {"error": repr(e)}
+    storage = None
+    if oracle_out is not None:
+        try:
+            storage = storage_precision_study(oracle_out, out["blocks_h"], out["s"], w, errors)
+        except Exception as e:  # report, do not hide
+            storage = {"error": repr(e)}
 
     split = [pp for pp in SPLIT_PATHS if pp in results]
     head = max(split, key=lambda pp: results[pp]["snps_per_s"]) if split else "fp64"
@@ -683,6 +711,7 @@ def main():
         "roofline": hr["roofline"], "path_roofline": path_roofline, "e2e": hr.get("e2e"),
         "gpu_launches": hr["gpu_launches"],
         "clocks": hr["clocks"], "cpu_baseline": cpu, "paths": paths_out, "forms": forms,
+        "storage_precision": storage,
         "peaks": {"measured_file": {k: out["peaks"].get(k) for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained")},
                   "measured_here": out["extra"]},
     }

@@ -109,10 +109,13 @@ typedef struct {
                       b + k p ncols.  Batches, the adjoint, REML and gwas_solve_block_static take t = 1
                       (else GWAS_ERR_UNSUPPORTED) */
   int separate_sums; /* inverse tile mode (with p - 1 + t <= 8): 0 (default) forms the per-SNP sums
-                        x~ . [X~_L | Y~] and x~ . x~ inside the solve's launch (two idle warps per SM read
-                        each stored tile back from L2; the launch leaves FP32 hi/lo partial sums per row
-                        panel that a small pass adds in FP64); 1 keeps them a separate pass over X~.
+                        x~ . [X~_L | Y~] and x~ . x~ in the solve's epilogue, which then stores no X~
+                        (FP32 partial sums per row panel, added by a small pass as double-FP32 pairs
+                        before the FP64 p x p solves); 1 stores X~ and sums it in a separate pass.
                         Other modes and sizes always use the separate pass */
+  int single_piece;  /* precision studies only (inverse tile mode): 1 keeps L^-1 as its hi piece alone
+                        (its lo piece zeroed: one BF16, TF32 or row-scaled FP16 rounding of L^-1);
+                        b and se then carry that rounding, far above the split forms' 1e-5 */
 } gwas_config;
 
 enum {

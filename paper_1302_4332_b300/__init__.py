@@ -63,7 +63,8 @@ class NotSPDError(GwasError):
 class _Config(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("bs", ctypes.c_int), ("ring_depth", ctypes.c_int),
                 ("device", ctypes.c_int), ("strip_group", ctypes.c_int), ("tile_mode", ctypes.c_int),
-                ("traits", ctypes.c_int), ("separate_sums", ctypes.c_int)]
+                ("traits", ctypes.c_int), ("separate_sums", ctypes.c_int),
+                ("single_piece", ctypes.c_int)]
 
 
 _lib = None
@@ -276,7 +277,8 @@ class GLS:
 
     def __init__(self, phi_or_L, XL, y, h: float, sigma2: float = 1.0, *, precision: str = "fp64",
                  bs: int = 4096, ring_depth: int = 3, is_L: bool = False, device: int = -1, stream=None,
-                 strip_group: int = 0, tiles: str = "auto", separate_sums: bool = False):
+                 strip_group: int = 0, tiles: str = "auto", separate_sums: bool = False,
+                 single_piece: bool = False):
         lib = load()
         n = int(np.shape(y)[0]) if not _is_torch(y) else int(y.shape[0])
         q = 0 if XL is None else (int(XL.shape[1]) if np.ndim(XL) == 2 or _is_torch(XL) else 1)
@@ -301,6 +303,7 @@ class GLS:
         cfg.tile_mode = TILE_MODES[tiles]
         cfg.traits = self.t
         cfg.separate_sums = int(bool(separate_sums))
+        cfg.single_piece = int(bool(single_piece))
         self.precision, self.bs = precision, int(bs)
         stream_p = None
         if stream is not None:

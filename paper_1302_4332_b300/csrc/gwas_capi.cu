@@ -380,6 +380,10 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
       (cfg.precision == GWAS_F16X2 && cfg.tile_mode != GWAS_TILES_AUTO && cfg.tile_mode != GWAS_TILES_INVERSE))
     return GWAS_ERR_ARG;
   if (cfg.separate_sums != 0 && cfg.separate_sums != 1) return GWAS_ERR_ARG;
+  if (cfg.single_piece != 0 && cfg.single_piece != 1) return GWAS_ERR_ARG;
+  if (cfg.single_piece && (cfg.precision == GWAS_FP64 ||
+                           (cfg.tile_mode != GWAS_TILES_AUTO && cfg.tile_mode != GWAS_TILES_INVERSE)))
+    return GWAS_ERR_ARG;
   const int traits = cfg.traits == 0 ? 1 : cfg.traits;
   if (traits < 1 || traits > TMAX || p - 1 + traits > QMAX + 1) return GWAS_ERR_ARG;
 
@@ -516,6 +520,7 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
       CK(launch_make_w32(ctx->W, ctx->n_pad, ctx->n_pad, nw - 1, ctx->W32, ctx->stream));
       CK(prepare_reduce_solve());
       if (!cfg.separate_sums) CK(tc::set_reductions(ctx->tcs, ctx->W32, w32_stride(nw - 1), nw));
+      if (cfg.single_piece) CK(tc::drop_lo_piece(ctx->tcs, ctx->stream));
       ctx->launches += 1;
     }
 

@@ -81,6 +81,9 @@ const float* xt_f32(const TcState* t);
 // still stores it).  Other modes or sizes: no change (the sums stay a separate
 // pass over xt_f32()).
 cudaError_t set_reductions(TcState* t, const float* w32, int ws, int nw);
+// Precision studies (inverse form): zeroes the lo piece of L^-1, so that the
+// solve multiplies by its hi piece alone.  Other modes: cudaErrorInvalidValue.
+cudaError_t drop_lo_piece(TcState* t, cudaStream_t s);
 // The last block's partial sums, or null when the block stored X~ instead:
 // partial_groups(t) row groups x (nw + 1) quantities, each a plane of
 // partial_ld(t) floats with SNP column j at offset j.

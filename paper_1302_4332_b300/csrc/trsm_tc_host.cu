@@ -931,6 +931,11 @@ cudaError_t set_reductions(TcState* t, const float* w32, int ws, int nw) {
   t->nw = nw;
   return cudaSuccess;
 }
+cudaError_t drop_lo_piece(TcState* t, cudaStream_t s) {
+  if (t->mode != TILES_INVERSE || t->ahiT) return cudaErrorInvalidValue;
+  const size_t esz = t->tf32 ? 4 : 2;
+  return cudaMemsetAsync(t->alo, 0, esz * (size_t)t->n_pad * t->n_pad, s);
+}
 const float* partials(const TcState* t) { return t->red_last ? t->red : nullptr; }
 int partial_groups(const TcState* t) { return t->ws == 4 ? t->P : 4 * t->P; }  // row panels or their quarters
 int64_t partial_ld(const TcState* t) { return t->bs; }

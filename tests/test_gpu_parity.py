@@ -443,3 +443,27 @@ def test_stage_timing(small_study, prec):
     assert set(st) == {"h2d", "trsm", "reduce", "d2h", "solve"}
     assert st["trsm"][1] == st["solve"][1] == st["reduce"][1] == 2
     assert 0.0 < st["solve"][0] <= st["trsm"][0] and st["reduce"][0] > 0.0
+
+
+@pytest.mark.parametrize("prec", SPLITS)
+def test_single_piece_study_switch(small_study, prec):
+    """The precision-study switch keeps L^-1 as its hi piece alone: results
+    stay finite with the same statuses, their error against the oracle grows
+    by orders of magnitude over the split pair's, and the switch is refused
+    outside the inverse form."""
+    s, X, L, (r, se, st) = small_study
+    Xs = X[:, :256]
+    e = {}
+    for single in (False, True):
+        with gw.GLS(s["Phi"], s["XL"], s["y"], s["h"], s["sigma2"], precision=prec, bs=256,
+                    single_piece=single) as g:
+            b, se_g, st_g = g.solve_block(Xs)
+        assert np.array_equal(st_g, st[:256]) and np.all(np.isfinite(b[:, st_g == 0]))
+        e[single] = compare(b, se_g, st_g, r[:, :256], se[:, :256], st[:256])
+    assert e[False]["b_norm"] <= TOL_SPLIT
+    assert e[True]["b_norm"] > 10 * e[False]["b_norm"], e
+    for bad in (dict(precision="fp64"), dict(precision=prec, tiles="pair_mma")):
+        if bad.get("tiles") and prec == "f16x2":
+            continue
+        with pytest.raises(gw.GwasError):
+            gw.GLS(s["Phi"], s["XL"], s["y"], s["h"], s["sigma2"], bs=256, single_piece=True, **bad)
