@@ -1327,14 +1327,20 @@ __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_co
         const pair2::Unit u = pair2::make_unit(row, S);
         const int nkb = UP ? S.P - u.k0 : u.nkb;
         bool ok = true;
+        int a = 0;
+        uint32_t d = 0, accumulate = 0;
         for (int j = 0; j < nkb && ok; ++j) {
-          // every K-block into a fresh partial (promoted by the epilogue)
-          const int a = kb & 1;
-          if (!ptx::mbar_wait(&part_empty[a], ((kb >> 1) & 1) ^ 1, st)) { ok = false; break; }
-          ++kb;
-          ptx::tc_fence_after();
-          const uint32_t d = tmem_base + a * TN;
-          uint32_t accumulate = 0;
+          // K-blocks 0 and 1 of a unit into one partial, every later K-block
+          // into a fresh one (promoted by the epilogue): three K-blocks of work
+          // before the epilogue must take a partial, to cover its tile-end sums
+          if (j != 1) {
+            a = kb & 1;
+            if (!ptx::mbar_wait(&part_empty[a], ((kb >> 1) & 1) ^ 1, st)) { ok = false; break; }
+            ++kb;
+            ptx::tc_fence_after();
+            d = tmem_base + a * TN;
+            accumulate = 0;
+          }
           for (int h = 0; h < K::CPB; ++h, ++cnt) {
             const int s = cnt % ST;
             const uint32_t r = cnt / ST;
@@ -1355,7 +1361,7 @@ __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_co
             ptx::mma_commit_pair(&empty[s], BOTH);
           }
           if (!ok) break;
-          ptx::mma_commit_pair(&part_full[a], BOTH);
+          if (j != 0 || nkb == 1) ptx::mma_commit_pair(&part_full[a], BOTH);
         }
         if (!ok) break;
       }
@@ -1400,7 +1406,8 @@ __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_co
       for (int i = 0; i < EPI_COLS; ++i) master[i] = 0.f;
       bool ok = true;
       const int nkb = UP ? S.P - u.k0 : u.nkb;
-      for (int pp = 0; pp < nkb && ok; ++pp) {
+      const int nparts = nkb > 1 ? nkb - 1 : 1;  // K-blocks 0 and 1 share a partial
+      for (int pp = 0; pp < nparts && ok; ++pp) {
         const int a = kb & 1;
         if (!ptx::group_and(1, NT, ptx::mbar_wait(&part_full[a], (kb >> 1) & 1, st))) { ok = false; break; }
         ptx::tc_fence_after();

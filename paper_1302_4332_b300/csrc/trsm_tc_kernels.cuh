@@ -21,7 +21,8 @@ constexpr int THREADS = 32 * (4 + EPI_WARPS);
 constexpr int EPI_COLS = TN / 2;  // SNP columns per epilogue warp
 // K-blocks accumulated in one TMEM partial before the epilogue promotes it:
 // one (two measured no faster and raised the error of se up to tenfold); with
-// one, all tile modes give the same results bit for bit
+// one, the substitution's tile modes give the same results bit for bit.  (The
+// inverse form puts the first two K-blocks of a unit into one partial.)
 constexpr int PROMOTE = 1;
 
 template <bool TF32>
