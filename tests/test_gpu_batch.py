@@ -61,6 +61,36 @@ def test_batch_matches_single_and_oracle(prec, tiles):
             g.close()
 
 
+@pytest.mark.parametrize("prec", ("bf16x3", "f16x2"))
+def test_batch_studies_of_different_p(prec):
+    """Studies with p = 2, 4, 6, 8 in one launch: their per-SNP sums take both
+    widths of W in the solve's epilogue (4 and 8 columns; per row panel or per
+    row quarter) side by side.  Each equals its own context's block solve bit
+    for bit and the oracle within the split bar."""
+    ps, ns = (2, 4, 6, 8), (300, 520, 129, 700)
+    studies = []
+    for i, (n, p) in enumerate(zip(ns, ps)):
+        s = gwas_synth.study(n, p, 2 * n, 0.5, 1.0, seed=31, study_id=i)
+        studies.append((s, gw.GLS(s["Phi"], s["XL"], s["y"], 0.5, 1.0, precision=prec, bs=256)))
+    gls = [g for _, g in studies]
+    try:
+        with gw.GLSBatch(gls) as B:
+            blocks = [gwas_synth.dosages(s["n"], 0, m, seed=31, study=i)
+                      for i, ((s, _), m) in enumerate(zip(studies, (256, 200, 97, 256)))]
+            outs = B.solve(blocks)
+            for i, ((s, g), X, (b, se, st)) in enumerate(zip(studies, blocks, outs)):
+                assert b.shape == (ps[i], X.shape[1])
+                b1, se1, st1 = g.solve_block(X)
+                assert np.array_equal(b, b1) and np.array_equal(se, se1) and np.array_equal(st, st1), (prec, i)
+                L = oracle.potrf(oracle.form_m(s["Phi"], 0.5, 1.0))
+                r, se_o, _, st_o = oracle.gls(L, s["XL"], s["y"], X)
+                e = compare(b, se, st, r, se_o, st_o)
+                assert e["b_norm"] <= 1e-5 and e["se_rel"] <= 1e-5, (prec, i, e)
+    finally:
+        for g in gls:
+            g.close()
+
+
 def test_batch_autotune_and_skipped_study():
     studies = _studies("bf16x3", bs=1024)
     gls = [g for _, g in studies]
