@@ -542,7 +542,9 @@ __global__ void __launch_bounds__(PS_COLS * PS_SLICES)
   const int col = blockIdx.x * PS_COLS + cl;
   const int64_t group = (int64_t)(nw + 1) * ldr;
   // every global load is issued before the first use of any (one round trip):
-  // this thread's share of the constants, the SNP's shift, its partials
+  // this thread's share of the constants (set at init: read before the solve
+  // kernel this one depends on has finished), then the SNP's shift and its
+  // partials
   constexpr int NW = (int)(sizeof(SolveConsts) / 4), NT = PS_COLS * PS_SLICES, SCW = (NW + NT - 1) / NT;
   int scw[SCW];
 #pragma unroll
@@ -550,7 +552,8 @@ __global__ void __launch_bounds__(PS_COLS * PS_SLICES)
     const int i = (int)threadIdx.x + j * NT;
     scw[j] = i < NW ? __ldg(reinterpret_cast<const int*>(sc) + i) : 0;
   }
-  const double cshift = (slice == 0 && col < ncols && shift) ? (double)__ldg(shift + col) : 0.0;
+  ptx::griddep_wait();  // a programmatic dependent of the solve kernel that wrote the partials
+  const double cshift = (slice == 0 && col < ncols && shift) ? (double)shift[col] : 0.0;
   float hi[QM + 2], lo[QM + 2];
 #pragma unroll
   for (int a = 0; a < QM + 2; ++a) hi[a] = lo[a] = 0.f;
@@ -598,14 +601,23 @@ cudaError_t launch_partials_solve(const float* red, int ngroups, int64_t ldr, co
   const int nw = q + t;
   if (t < 1 || nw > 8) return cudaErrorInvalidValue;
   if (bstride == 0) bstride = (int64_t)(q + 1) * ncols;
-  const int grid = (ncols + PS_COLS - 1) / PS_COLS;
-  if (nw <= 4)
-    partials_solve_kernel<3><<<grid, PS_COLS * PS_SLICES, 0, s>>>(red, ngroups, nw, ldr, sc, q, ncols, b, se, status,
-                                                                  shift, t, bstride);
-  else
-    partials_solve_kernel<7><<<grid, PS_COLS * PS_SLICES, 0, s>>>(red, ngroups, nw, ldr, sc, q, ncols, b, se, status,
-                                                                  shift, t, bstride);
-  return cudaGetLastError();
+  // launched as a programmatic dependent of the solve kernel: its blocks start
+  // as the solve's CTAs retire and wait (griddep_wait) for all of its stores
+  cudaLaunchConfig_t cfg;
+  memset(&cfg, 0, sizeof cfg);
+  cfg.gridDim = dim3((ncols + PS_COLS - 1) / PS_COLS);
+  cfg.blockDim = dim3(PS_COLS * PS_SLICES);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  cudaError_t e = nw <= 4 ? cudaLaunchKernelEx(&cfg, partials_solve_kernel<3>, red, ngroups, nw, ldr, sc, q, ncols, b,
+                                               se, status, shift, t, bstride)
+                          : cudaLaunchKernelEx(&cfg, partials_solve_kernel<7>, red, ngroups, nw, ldr, sc, q, ncols, b,
+                                               se, status, shift, t, bstride);
+  return e != cudaSuccess ? e : cudaGetLastError();
 }
 
 // W32 = W in FP32, row-major with row stride w32_stride(q) (zero-padded).

@@ -433,6 +433,14 @@ __device__ __forceinline__ void df_add(float& hi, float& lo, float bh, float bl)
   lo = l - (hi - s);
 }
 
+// Programmatic dependent launch: a kernel launched with programmatic stream
+// serialization may start while the kernel before it still runs; griddep_wait
+// blocks until that kernel has completed and its memory is visible.
+// griddep_launch lets the next such kernel start once every block of this one
+// has issued it (or exited).  Both are no-ops for ordinary launches.
+__device__ __forceinline__ void griddep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void griddep_launch() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // d0 += a * b0 and d1 += a * b1 as one packed instruction (two FP32 FMAs,
 // each rounded to nearest: the same results as two fmaf).
 __device__ __forceinline__ void fma2(float& d0, float& d1, float a, float b0, float b1) {

@@ -1248,6 +1248,9 @@ __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_co
   ptx::tc_fence_after();
   ptx::cluster_sync();  // both CTAs' barriers and tensor memory exist before any remote access
   const uint32_t tmem_base = *tmem_slot;
+  // launched as a dependent of the cast pre-pass: set-up above overlaps its
+  // tail; no global memory is touched before it has completed
+  ptx::griddep_wait();
 
   if (warp == 0) {
     // ------------------------------------------------ scheduler + TMA producer
@@ -1271,7 +1274,10 @@ __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_co
           if (!ptx::mbar_wait_s<true>(&tile_full[slot], use & 1, st)) break;
           t = tile_ring[slot];
         }
-        if (t >= ntiles) break;
+        if (t >= ntiles) {
+          ptx::griddep_launch();  // no more units for this CTA: the sums' kernel may launch
+          break;
+        }
         int sidx, row, c;
         TcStudy S;
         decode_tile(b, t, sidx, row, c, S);
@@ -1588,8 +1594,13 @@ cudaError_t query_clusters(bool tf32, TileMode mode, int num_sms, int* out, bool
 template <bool TF32>
 static cudaError_t launch_pair(const TcBatch& b, int max_clusters, cudaStream_t s, TileMode mode, bool f16) {
   const int ncl = b.ntiles < max_clusters ? b.ntiles : max_clusters;
-  cudaLaunchAttribute attr[1];
+  cudaLaunchAttribute attr[2];
   cudaLaunchConfig_t cfg = pair_config<TF32>(attr, 2 * ncl, s, mode);
+  if (mode == TILES_INVERSE) {  // a programmatic dependent of the cast pre-pass (the kernel waits for it)
+    attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[1].val.programmaticStreamSerializationAllowed = 1;
+    cfg.numAttrs = 2;
+  }
   if (mode == TILES_INVERSE && f16 && !TF32) return cudaLaunchKernelEx(&cfg, trsm_tc_inv_kernel<false, true>, b);
   if (mode == TILES_INVERSE) return cudaLaunchKernelEx(&cfg, trsm_tc_inv_kernel<TF32>, b);
   if (mode == TILES_PAIR_MMA) return cudaLaunchKernelEx(&cfg, trsm_tc_pair_mma_kernel<TF32>, b);

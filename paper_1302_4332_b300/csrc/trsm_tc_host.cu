@@ -12,6 +12,7 @@
 #include <cstring>
 #include <vector>
 
+#include "tc_ptx.cuh"
 #include "trsm_tc_kernels.cuh"
 
 namespace gwas {
@@ -80,6 +81,7 @@ template <int OUT, int NV>
 __global__ void __launch_bounds__(256) cast_shift_reg_kernel(const int8_t* __restrict__ X, int64_t ldx, int n,
                                                              int n_pad, int ncols, int8_t* __restrict__ shift,
                                                              void* __restrict__ xc) {
+  ptx::griddep_launch();  // the solve kernel may start its set-up
   const int lane = threadIdx.x & 31;
   const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (col >= ncols) return;
@@ -132,6 +134,7 @@ __global__ void __launch_bounds__(256) cast_shift_reg_kernel(const int8_t* __res
 template <int OUT>
 __global__ void cast_shift_kernel(const int8_t* __restrict__ X, int64_t ldx, int n, int n_pad, int ncols,
                                   int8_t* __restrict__ shift, void* __restrict__ xc) {
+  ptx::griddep_launch();  // the solve kernel may start its set-up
   const int lane = threadIdx.x & 31;
   const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (col >= ncols) return;
