@@ -362,6 +362,16 @@ int gwas_copy_factor(gwas_ctx *ctx, double *L, int64_t ld);
 int gwas_timing_enable(gwas_ctx *ctx, int enable);
 int gwas_timing_read(gwas_ctx *ctx, double *ms, int64_t *count);
 
+/* Diagnostic of the device-side failure detection: one thread waits, bounded
+ * by limit_us microseconds (1 .. 1,000,000) of %globaltimer, for something
+ * that never happens -- kind 0: a device flag that nothing sets, kind 1: a
+ * shared-memory mbarrier that nothing arrives on -- with the same bounded
+ * wait, error word and abort flag as the solve kernels.  Returns
+ * GWAS_ERR_TIMEOUT (the expected outcome: the wait ran out, the device
+ * recorded it and the host read and cleared it) and leaves the context
+ * usable; GWAS_ERR_ARG for a bad kind or limit. */
+int gwas_check_timeout(gwas_ctx *ctx, int kind, int limit_us);
+
 /* Kernel launches the context issued since it was created (all kinds). */
 int64_t gwas_kernel_launches(const gwas_ctx *ctx);
 

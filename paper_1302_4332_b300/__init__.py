@@ -41,7 +41,7 @@ EXPORTS = (
     "gwas_batch_set_order", "gwas_batch_autotune", "gwas_batch_solve_files", "gwas_batch_kernel_launches",
     "gwas_batch_last_error_detail",
     "gwas_batch_destroy", "gwas_solve_file", "gwas_solve_file_out", "gwas_reader_open", "gwas_reader_next",
-    "gwas_reader_release", "gwas_reader_error_detail", "gwas_reader_close",
+    "gwas_reader_release", "gwas_reader_error_detail", "gwas_reader_close", "gwas_check_timeout",
 )
 GWAS_RESUME = 1
 STAGES = ("h2d", "trsm", "reduce", "d2h", "solve")
@@ -93,6 +93,8 @@ def load(path: str | None = None):
     lib.gwas_solve_stream.restype = c_int
     lib.gwas_synchronize.argtypes = [vp]
     lib.gwas_synchronize.restype = c_int
+    lib.gwas_check_timeout.argtypes = [vp, c_int, c_int]
+    lib.gwas_check_timeout.restype = c_int
     lib.gwas_set_stream.argtypes = [vp, vp]
     lib.gwas_set_stream.restype = c_int
     lib.gwas_get_info.argtypes = [vp] + [ctypes.POINTER(c_int)] * 5
@@ -450,6 +452,12 @@ class GLS:
 
     def synchronize(self):
         self._check(load().gwas_synchronize(self._ctx))
+
+    def check_timeout(self, kind: int = 0, limit_us: int = 20000) -> int:
+        """Diagnostic: a device-side wait on something that never happens,
+        bounded by limit_us; returns the library's code (GWAS_ERR_TIMEOUT is
+        the expected outcome) and leaves the context usable."""
+        return int(load().gwas_check_timeout(self._ctx, int(kind), int(limit_us)))
 
     def set_stream(self, stream):
         sp = stream.cuda_stream if hasattr(stream, "cuda_stream") else stream

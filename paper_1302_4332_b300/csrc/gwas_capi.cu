@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "gwas_internal.cuh"
+#include "tc_ptx.cuh"
 #include "trsm_tc.cuh"
 
 using namespace gwas;
@@ -1465,6 +1466,45 @@ int gwas_batch_solve_files(gwas_batch* B, const char* const* paths, const int64_
 int64_t gwas_batch_kernel_launches(const gwas_batch* B) { return B ? B->launches : 0; }
 const char* gwas_batch_last_error_detail(const gwas_batch* B) { return B ? B->detail.c_str() : ""; }
 void gwas_batch_destroy(gwas_batch* B) { batch_free(B); }
+
+}  // extern "C"
+
+namespace {
+__device__ int g_never_set = 0;  // a flag no code writes
+
+// One thread waits for a flag or an mbarrier phase that never comes, bounded
+// like the solve kernels' waits (here by limit_ns): the error word and the
+// abort flag are raised on expiry and the kernel returns.
+__global__ void check_timeout_kernel(int kind, long long limit_ns, gwas::DevStatus* st) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x != 0) return;
+  if (kind == 1) {
+    gwas::ptx::mbar_init(&bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  const long long t0 = gwas::ptx::globaltimer();
+  while (true) {
+    if (kind == 0 ? *reinterpret_cast<volatile const int*>(&g_never_set) != 0 : gwas::ptx::mbar_try_wait(&bar, 0))
+      return;
+    if (gwas::ptx::aborting(st)) return;
+    if (gwas::ptx::globaltimer() - t0 > limit_ns) {
+      gwas::ptx::raise_timeout(st);
+      return;
+    }
+  }
+}
+}  // namespace
+
+extern "C" {
+
+int gwas_check_timeout(gwas_ctx* ctx, int kind, int limit_us) {
+  if (!ctx || (kind != 0 && kind != 1) || limit_us < 1 || limit_us > 1000000) return GWAS_ERR_ARG;
+  CK(cudaSetDevice(ctx->dev));
+  check_timeout_kernel<<<1, 32, 0, ctx->stream>>>(kind, 1000LL * limit_us, ctx->st);
+  CK(cudaGetLastError());
+  ctx->launches += 1;
+  return check_device_status(ctx);
+}
 
 int gwas_synchronize(gwas_ctx* ctx) {
   if (!ctx) return GWAS_ERR_ARG;
