@@ -603,8 +603,7 @@ cudaError_t launch_partials_solve(const float* red, int ngroups, int64_t ldr, co
   if (bstride == 0) bstride = (int64_t)(q + 1) * ncols;
   // launched as a programmatic dependent of the solve kernel: its blocks start
   // as the solve's CTAs retire and wait (griddep_wait) for all of its stores
-  cudaLaunchConfig_t cfg;
-  memset(&cfg, 0, sizeof cfg);
+  cudaLaunchConfig_t cfg = {};
   cfg.gridDim = dim3((ncols + PS_COLS - 1) / PS_COLS);
   cfg.blockDim = dim3(PS_COLS * PS_SLICES);
   cfg.stream = s;
