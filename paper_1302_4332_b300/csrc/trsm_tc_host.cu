@@ -78,13 +78,9 @@ __device__ __forceinline__ void store_cast16(void* xc, int64_t off, const float 
 // NV 16-byte pieces of the column in registers between the sum and the
 // cast (all of them in flight at once).
 template <int OUT, int NV>
-__global__ void __launch_bounds__(256) cast_shift_reg_kernel(const int8_t* __restrict__ X, int64_t ldx, int n,
-                                                             int n_pad, int ncols, int8_t* __restrict__ shift,
-                                                             void* __restrict__ xc) {
-  ptx::griddep_launch();  // the solve kernel may start its set-up
+__device__ __forceinline__ void cast_column_reg(const int8_t* __restrict__ X, int64_t ldx, int n, int n_pad,
+                                                int col, int8_t* __restrict__ shift, void* __restrict__ xc) {
   const int lane = threadIdx.x & 31;
-  const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (col >= ncols) return;
   const int8_t* x = X + (int64_t)col * ldx;  // 16-byte aligned (checked by the caller)
   int4 v[NV];
 #pragma unroll
@@ -126,18 +122,34 @@ __global__ void __launch_bounds__(256) cast_shift_reg_kernel(const int8_t* __res
   }
 }
 
+// Launch order of a block (inverse form): this cast, then the solve as its
+// programmatic dependent, then the sums' kernel as the solve's.  The cast may
+// itself start as a dependent of the previous block's sums' kernel (which
+// lets it go once the previous solve has completed): it zeroes the solve's
+// unit counter, writes the cast block and this block's shift slot (the
+// previous sums read the other slot), and waits for that kernel only at its
+// end, so that the solve's own wait covers the previous sums' reads of the
+// partials the solve is about to overwrite.
+template <int OUT, int NV>
+__global__ void __launch_bounds__(256) cast_shift_reg_kernel(const int8_t* __restrict__ X, int64_t ldx, int n,
+                                                             int n_pad, int ncols, int8_t* __restrict__ shift,
+                                                             void* __restrict__ xc, unsigned int* counter) {
+  ptx::griddep_launch();  // the solve kernel may start its set-up
+  if (counter && blockIdx.x == 0 && threadIdx.x == 0) *counter = 0;
+  const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (col < ncols) cast_column_reg<OUT, NV>(X, ldx, n, n_pad, col, shift, xc);
+  ptx::griddep_wait();
+}
+
 // B operand of the inverse form: x'_ri = x_ri - c_i on rows < n and 0 on rows
 // n..n_pad-1, as BF16, FP32 (read as TF32 by the tensor cores) or FP16,
 // column-major with leading dimension n_pad.  c_i is computed here as in
 // column_shift_kernel when `shift` is given (and stored there), else 0.  One
 // warp per SNP column.
 template <int OUT>
-__global__ void cast_shift_kernel(const int8_t* __restrict__ X, int64_t ldx, int n, int n_pad, int ncols,
-                                  int8_t* __restrict__ shift, void* __restrict__ xc) {
-  ptx::griddep_launch();  // the solve kernel may start its set-up
+__device__ __forceinline__ void cast_column(const int8_t* __restrict__ X, int64_t ldx, int n, int n_pad, int col,
+                                            int8_t* __restrict__ shift, void* __restrict__ xc) {
   const int lane = threadIdx.x & 31;
-  const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (col >= ncols) return;
   const int8_t* x = X + (int64_t)col * ldx;  // 16-byte aligned (checked by the caller)
   const int n16 = n & ~15;
   int c = 0;
@@ -183,28 +195,42 @@ __global__ void cast_shift_kernel(const int8_t* __restrict__ X, int64_t ldx, int
   }
 }
 
-// The cast pre-pass of the inverse form: one read per column while it fits
-// the registers (n <= 16384), else two.
 template <int OUT>
-static void launch_cast_t(const int8_t* X, int64_t ldx, int n, int n_pad, int ncols, int8_t* shift, void* xc,
-                          cudaStream_t s) {
-  const int grid = (ncols + 7) / 8;
-  if (n <= 512 * 20)
-    cast_shift_reg_kernel<OUT, 20><<<grid, 256, 0, s>>>(X, ldx, n, n_pad, ncols, shift, xc);
-  else if (n <= 512 * 32)
-    cast_shift_reg_kernel<OUT, 32><<<grid, 256, 0, s>>>(X, ldx, n, n_pad, ncols, shift, xc);
-  else
-    cast_shift_kernel<OUT><<<grid, 256, 0, s>>>(X, ldx, n, n_pad, ncols, shift, xc);
+__global__ void cast_shift_kernel(const int8_t* __restrict__ X, int64_t ldx, int n, int n_pad, int ncols,
+                                  int8_t* __restrict__ shift, void* __restrict__ xc, unsigned int* counter) {
+  ptx::griddep_launch();  // the solve kernel may start its set-up
+  if (counter && blockIdx.x == 0 && threadIdx.x == 0) *counter = 0;
+  const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (col < ncols) cast_column<OUT>(X, ldx, n, n_pad, col, shift, xc);
+  ptx::griddep_wait();
 }
 
-static void launch_cast(int out, const int8_t* X, int64_t ldx, int n, int n_pad, int ncols, int8_t* shift,
-                        void* xc, cudaStream_t s) {
-  if (out == OUT_F32)
-    launch_cast_t<OUT_F32>(X, ldx, n, n_pad, ncols, shift, xc, s);
-  else if (out == OUT_F16)
-    launch_cast_t<OUT_F16>(X, ldx, n, n_pad, ncols, shift, xc, s);
-  else
-    launch_cast_t<OUT_BF16>(X, ldx, n, n_pad, ncols, shift, xc, s);
+// The cast pre-pass of the inverse form: one read per column while it fits
+// the registers (n <= 16384), else two.  A programmatic dependent of the
+// kernel before it (see cast_shift_reg_kernel); counter: the solve's unit
+// counter to zero, or null when the caller clears it.
+template <int OUT>
+static cudaError_t launch_cast_t(const int8_t* X, int64_t ldx, int n, int n_pad, int ncols, int8_t* shift, void* xc,
+                                 unsigned int* counter, cudaStream_t s) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3((ncols + 7) / 8);
+  cfg.blockDim = dim3(256);
+  cfg.stream = s;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (n <= 512 * 20) return cudaLaunchKernelEx(&cfg, cast_shift_reg_kernel<OUT, 20>, X, ldx, n, n_pad, ncols, shift, xc, counter);
+  if (n <= 512 * 32) return cudaLaunchKernelEx(&cfg, cast_shift_reg_kernel<OUT, 32>, X, ldx, n, n_pad, ncols, shift, xc, counter);
+  return cudaLaunchKernelEx(&cfg, cast_shift_kernel<OUT>, X, ldx, n, n_pad, ncols, shift, xc, counter);
+}
+
+static cudaError_t launch_cast(int out, const int8_t* X, int64_t ldx, int n, int n_pad, int ncols, int8_t* shift,
+                               void* xc, unsigned int* counter, cudaStream_t s) {
+  if (out == OUT_F32) return launch_cast_t<OUT_F32>(X, ldx, n, n_pad, ncols, shift, xc, counter, s);
+  if (out == OUT_F16) return launch_cast_t<OUT_F16>(X, ldx, n, n_pad, ncols, shift, xc, counter, s);
+  return launch_cast_t<OUT_BF16>(X, ldx, n, n_pad, ncols, shift, xc, counter, s);
 }
 
 // Columns c0.. c0+ncols-1 of the n_pad x n_pad identity as int8, column-major
@@ -400,7 +426,9 @@ struct TcState {
   void* bhi = nullptr;
   void* blo = nullptr;
   int64_t ldt = 0;
-  int8_t* shift = nullptr;        // per-SNP integer shift (bs)
+  int8_t* shift = nullptr;        // per-SNP integer shift (bs) of the last block: one of shift_buf
+  int8_t* shift_buf[2] = {nullptr, nullptr};  // inverse form: alternate blocks, so that a block's cast
+  int shift_slot = 0;                         // may run while the previous block's sums read theirs
   bool center = false;            // X_L[:, 0] is the intercept: shift SNP columns
   int strip_group = 0;            // tile order over groups of column strips (0: all)
   TileMode mode = TILES_SINGLE;    // how tiles map onto CTAs
@@ -496,7 +524,9 @@ cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_p
   TRY(cudaMalloc(&t->xt32, sizeof(float) * (size_t)n_pad * bs));
   if (!t->tf32) TRY(cudaMalloc(&t->bhi, 2 * (size_t)n_pad * bs));
   TRY(cudaMalloc(&t->blo, esz * (size_t)n_pad * bs));
-  TRY(cudaMalloc(&t->shift, (size_t)bs));
+  TRY(cudaMalloc(&t->shift_buf[0], 2 * (size_t)bs));
+  t->shift_buf[1] = t->shift_buf[0] + bs;
+  t->shift = t->shift_buf[0];
   t->center = center;
   t->strip_group = strip_group;
   // measured at n = 1e4 with 4096-column blocks: the inverse form is the
@@ -607,9 +637,13 @@ static cudaError_t prepare_cast(TcState* t, const int8_t* X, int64_t ldx, int nc
   cudaError_t e = make_map(t->encode, mXcH, dt, t->xc, (uint64_t)t->n_pad, (uint64_t)ncols, esz * t->n_pad, kch,
                            TN / 2, true);
   if (e != cudaSuccess) return e;
+  if (t->center) {  // this block's shift slot (the previous block's sums may still read the other)
+    t->shift_slot ^= 1;
+    t->shift = t->shift_buf[t->shift_slot];
+  }
   int8_t* sh = t->center ? t->shift : nullptr;
-  launch_cast(cast_out(t), X, ldx, t->n, t->n_pad, ncols, sh, t->xc, s);
   ++*launches;
+  if ((e = launch_cast(cast_out(t), X, ldx, t->n, t->n_pad, ncols, sh, t->xc, t->sched, s)) != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -629,8 +663,12 @@ static cudaError_t prepare_study(TcState* t, const int8_t* X, int64_t ldx, int n
     if (e != cudaSuccess) return e;
   }
   const int C = (ncols + TN - 1) / TN;
-  e = cudaMemsetAsync(t->sched, 0, 128 + sizeof(int) * (size_t)t->P * C, s);
-  if (e != cudaSuccess) return e;
+  // the substitution's counter and tile flags; the inverse form uses the
+  // counter alone, which its cast zeroes (no stream operation between the
+  // previous block's kernels and this cast)
+  if (t->mode != TILES_INVERSE && (e = cudaMemsetAsync(t->sched, 0, 128 + sizeof(int) * (size_t)t->P * C, s)) !=
+                                      cudaSuccess)
+    return e;
   if (t->mode == TILES_INVERSE) {
     if ((e = prepare_cast(t, X, ldx, ncols, s, launches, mXcH)) != cudaSuccess) return e;
   } else if (t->center) {
@@ -1084,8 +1122,10 @@ cudaError_t batch_launch(TcBatchState* B, TcState* const* ts, cudaStream_t s, in
     if ((e = cudaMemsetAsync(t->sched, 0, 128 + sizeof(int) * (size_t)t->P * B->S[i].C, s)) != cudaSuccess) return e;
     if (t->mode == TILES_INVERSE) {
       int8_t* sh = t->center ? t->shift : nullptr;
-      launch_cast(cast_out(t), B->X[i], B->ldx[i], t->n, t->n_pad, B->S[i].ncols, sh, t->xc, s);
       ++*launches;
+      if ((e = launch_cast(cast_out(t), B->X[i], B->ldx[i], t->n, t->n_pad, B->S[i].ncols, sh, t->xc, nullptr, s)) !=
+          cudaSuccess)
+        return e;
       if ((e = cudaGetLastError()) != cudaSuccess) return e;
     } else if (t->center) {
       column_shift_kernel<<<(B->S[i].ncols + 7) / 8, 256, 0, s>>>(B->X[i], B->ldx[i], t->n, B->S[i].ncols, t->shift);
@@ -1157,7 +1197,7 @@ void destroy(TcState* t) {
   cudaFree(t->xc);
   cudaFree(t->rscale);
   cudaFree(t->sched);
-  cudaFree(t->shift);
+  cudaFree(t->shift_buf[0]);
   cudaFree(t->order);
   delete t;
 }
