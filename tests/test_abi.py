@@ -45,8 +45,26 @@ def test_strerror_and_defaults(lib):
     assert (cfg.precision, cfg.bs, cfg.ring_depth, cfg.device) == (0, 4096, 3, -1)
 
 
+def test_config_struct_matches_the_header(lib):
+    """gwas_config_default writes exactly the C struct: as many bytes as the
+    binding's _Config holds (a guard region after it stays untouched), and the
+    fields the header lists, in its order, are the binding's."""
+    size = ctypes.sizeof(gw._Config)
+    buf = (ctypes.c_ubyte * (size + 64))(*([0xA5] * (size + 64)))
+    lib.gwas_config_default(ctypes.cast(buf, ctypes.POINTER(gw._Config)))
+    assert all(b == 0xA5 for b in bytes(buf)[size:]), "the C struct is larger than the binding's"
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "gwas_b300.h")).read(), flags=re.S)
+    body = re.search(r"typedef struct \{(.*?)\} gwas_config;", text, flags=re.S).group(1)
+    fields = re.findall(r"\bint\s+([a-z_0-9]+)\s*;", body)
+    assert fields == [name for name, _ in gw._Config._fields_]
+    zeros = gw._Config()
+    lib.gwas_config_default(ctypes.byref(zeros))
+    assert zeros.separate_sums == 0 and zeros.single_piece == 0 and zeros.traits == 0
+
+
 def test_null_context_is_an_argument_error(lib):
     assert lib.gwas_synchronize(None) == -1
+    assert lib.gwas_check_timeout(None, 0, 1000) == -1
     assert lib.gwas_solve_block(None, None, 0, 0, None, None, None) == -1
     lib.gwas_destroy(None)
 
