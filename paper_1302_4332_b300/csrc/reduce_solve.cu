@@ -553,8 +553,6 @@ __global__ void __launch_bounds__(PS_COLS * PS_SLICES)
     scw[j] = i < NW ? __ldg(reinterpret_cast<const int*>(sc) + i) : 0;
   }
   ptx::griddep_wait();  // a programmatic dependent of the solve kernel that wrote the partials
-  ptx::griddep_launch();  // the solve has completed: the next block's cast may start (it writes the
-                          // cast block and the other shift slot, and waits for this kernel at its end)
   const double cshift = (slice == 0 && col < ncols && shift) ? (double)shift[col] : 0.0;
   float hi[QM + 2], lo[QM + 2];
 #pragma unroll

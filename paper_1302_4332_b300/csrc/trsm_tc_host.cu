@@ -122,14 +122,11 @@ __device__ __forceinline__ void cast_column_reg(const int8_t* __restrict__ X, in
   }
 }
 
-// Launch order of a block (inverse form): this cast, then the solve as its
-// programmatic dependent, then the sums' kernel as the solve's.  The cast may
-// itself start as a dependent of the previous block's sums' kernel (which
-// lets it go once the previous solve has completed): it zeroes the solve's
-// unit counter, writes the cast block and this block's shift slot (the
-// previous sums read the other slot), and waits for that kernel only at its
-// end, so that the solve's own wait covers the previous sums' reads of the
-// partials the solve is about to overwrite.
+// Launch order of a block (inverse form): this cast (an ordinary launch: its
+// input may come from any kernel before it), then the solve as its
+// programmatic dependent, then the sums' kernel as the solve's.  The cast
+// zeroes the solve's unit counter (no stream operation between it and the
+// solve) and writes the cast block and this block's shift slot.
 template <int OUT, int NV>
 __global__ void __launch_bounds__(256) cast_shift_reg_kernel(const int8_t* __restrict__ X, int64_t ldx, int n,
                                                              int n_pad, int ncols, int8_t* __restrict__ shift,
@@ -138,7 +135,6 @@ __global__ void __launch_bounds__(256) cast_shift_reg_kernel(const int8_t* __res
   if (counter && blockIdx.x == 0 && threadIdx.x == 0) *counter = 0;
   const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (col < ncols) cast_column_reg<OUT, NV>(X, ldx, n, n_pad, col, shift, xc);
-  ptx::griddep_wait();
 }
 
 // B operand of the inverse form: x'_ri = x_ri - c_i on rows < n and 0 on rows
@@ -202,28 +198,22 @@ __global__ void cast_shift_kernel(const int8_t* __restrict__ X, int64_t ldx, int
   if (counter && blockIdx.x == 0 && threadIdx.x == 0) *counter = 0;
   const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (col < ncols) cast_column<OUT>(X, ldx, n, n_pad, col, shift, xc);
-  ptx::griddep_wait();
 }
 
 // The cast pre-pass of the inverse form: one read per column while it fits
-// the registers (n <= 16384), else two.  A programmatic dependent of the
-// kernel before it (see cast_shift_reg_kernel); counter: the solve's unit
-// counter to zero, or null when the caller clears it.
+// the registers (n <= 16384), else two.  counter: the solve's unit counter to
+// zero, or null when the caller clears it.
 template <int OUT>
 static cudaError_t launch_cast_t(const int8_t* X, int64_t ldx, int n, int n_pad, int ncols, int8_t* shift, void* xc,
                                  unsigned int* counter, cudaStream_t s) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3((ncols + 7) / 8);
-  cfg.blockDim = dim3(256);
-  cfg.stream = s;
-  cudaLaunchAttribute attr[1];
-  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  attr[0].val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = attr;
-  cfg.numAttrs = 1;
-  if (n <= 512 * 20) return cudaLaunchKernelEx(&cfg, cast_shift_reg_kernel<OUT, 20>, X, ldx, n, n_pad, ncols, shift, xc, counter);
-  if (n <= 512 * 32) return cudaLaunchKernelEx(&cfg, cast_shift_reg_kernel<OUT, 32>, X, ldx, n, n_pad, ncols, shift, xc, counter);
-  return cudaLaunchKernelEx(&cfg, cast_shift_kernel<OUT>, X, ldx, n, n_pad, ncols, shift, xc, counter);
+  const int grid = (ncols + 7) / 8;
+  if (n <= 512 * 20)
+    cast_shift_reg_kernel<OUT, 20><<<grid, 256, 0, s>>>(X, ldx, n, n_pad, ncols, shift, xc, counter);
+  else if (n <= 512 * 32)
+    cast_shift_reg_kernel<OUT, 32><<<grid, 256, 0, s>>>(X, ldx, n, n_pad, ncols, shift, xc, counter);
+  else
+    cast_shift_kernel<OUT><<<grid, 256, 0, s>>>(X, ldx, n, n_pad, ncols, shift, xc, counter);
+  return cudaGetLastError();
 }
 
 static cudaError_t launch_cast(int out, const int8_t* X, int64_t ldx, int n, int n_pad, int ncols, int8_t* shift,
@@ -427,8 +417,8 @@ struct TcState {
   void* blo = nullptr;
   int64_t ldt = 0;
   int8_t* shift = nullptr;        // per-SNP integer shift (bs) of the last block: one of shift_buf
-  int8_t* shift_buf[2] = {nullptr, nullptr};  // inverse form: alternate blocks, so that a block's cast
-  int shift_slot = 0;                         // may run while the previous block's sums read theirs
+  int8_t* shift_buf[2] = {nullptr, nullptr};  // inverse form: alternate blocks (a block's shifts stay
+  int shift_slot = 0;                         // intact while the next block is cast)
   bool center = false;            // X_L[:, 0] is the intercept: shift SNP columns
   int strip_group = 0;            // tile order over groups of column strips (0: all)
   TileMode mode = TILES_SINGLE;    // how tiles map onto CTAs
@@ -637,7 +627,7 @@ static cudaError_t prepare_cast(TcState* t, const int8_t* X, int64_t ldx, int nc
   cudaError_t e = make_map(t->encode, mXcH, dt, t->xc, (uint64_t)t->n_pad, (uint64_t)ncols, esz * t->n_pad, kch,
                            TN / 2, true);
   if (e != cudaSuccess) return e;
-  if (t->center) {  // this block's shift slot (the previous block's sums may still read the other)
+  if (t->center) {  // this block's shift slot
     t->shift_slot ^= 1;
     t->shift = t->shift_buf[t->shift_slot];
   }
