@@ -62,11 +62,10 @@ def parse_args():
     ap.add_argument("--no-forms", action="store_true", help="skip the batch / disk / adjoint / REML measurements")
     ap.add_argument("--strip-group", type=int, default=None,
                     help="split paths: column strips per tile-order group (0 = all; default: the measured best)")
-    ap.add_argument("--tiles", choices=("auto", "single", "pair_multicast", "pair_mma", "inverse"), default="auto",
+    ap.add_argument("--tiles", choices=("auto", "single", "pair_mma", "inverse"), default="auto",
                     help="split paths: tiles on SMs (auto: the measured fastest; single: one 128-row tile per SM; "
-                         "pair_multicast: row-panel pairs per 2-SM cluster with shared loads; pair_mma: pairs as "
-                         "one 256-row product per cluster; inverse: the triangular product with L^-1 formed at "
-                         "set-up, row-panel pairs per cluster)")
+                         "pair_mma: row-panel pairs as one 256-row product per 2-SM cluster; inverse: the "
+                         "triangular product with L^-1 formed at set-up, row-panel pairs per cluster)")
     ap.add_argument("--no-substitution", action="store_true",
                     help="with --tiles auto: skip the kernel-only measurement of the blocked substitution (pair_mma)")
     ap.add_argument("--separate-sums", action="store_true",
@@ -238,10 +237,7 @@ def kernel_traffic(path: str, tiles: str = ""):
 
 
 # ------------------------------------------------------------------ sharding
-def shard_block_starts(rank: int, world: int, nb: int, bs: int) -> list[int]:
-    """First SNP column of each of this rank's nb resident blocks: rank r owns
-    blocks r*nb .. r*nb + nb - 1 of the study, so ranks never share a SNP."""
-    return [(rank * nb + i) * bs for i in range(nb)]
+from paper_1302_4332_b300.shard import shard_block_starts  # noqa: E402  (rank r owns blocks r*nb ..)
 
 
 def max_over_ranks(x: float, dist, device=None) -> float:
@@ -330,8 +326,9 @@ def run_ours(args, rank, world, local_rank, dist):
         # the kernels would also stop the solve and sums kernels from starting
         # early as programmatic dependents): one more pass over the blocks
         g.timing(True)
-        for i in (range(NB) if path != "fp64" else (NB - 1,)):  # ends on the block the error report reads
-            g.solve_block(blocks_d[i], b, se, st)
+        steps_t = steps if path != "fp64" else 1
+        for i in (range(steps_t * NB) if path != "fp64" else (NB - 1,)):  # ends on the block the error report reads
+            g.solve_block(blocks_d[i % NB], b, se, st)
         g.synchronize()
         stages = g.timing_read()
         g.timing(False)
@@ -368,11 +365,11 @@ def run_ours(args, rank, world, local_rank, dist):
                         peak_basis=(f"{'tf32' if path == 'tf32x3' else 'bf16'} dense tensor peak (of measured, "
                                     f"burst) / {prods}: {prods} split products per algorithmic product "
                                     f"({mode} tile mode)"))
-            sus = peaks.get("bf16_tflops_sustained")
-            if path in ("bf16x3", "f16x2") and sus:  # a long timed region runs under the power cap
-                roof["frac_of_sustained"] = achieved / (sus / prods)
         roof["kernel_ms"] = kernel_ms
-        roof["timed"] = "mean CUDA-event duration of the solve kernel's launches in the timed region"
+        roof["timed"] = (f"mean CUDA-event duration of the solve kernel's {st_solve[1]} launches in a second timed "
+                         f"region of the same {steps_t} steps right after the first, with the library's per-launch "
+                         "events recorded on the kernel's stream (the first region has none: events between the "
+                         "kernels stop the programmatic dependent launches from starting early)")
         res["roofline"] = roof
         res["trsm_ms_per_launch"] = stages["trsm"][0] / max(stages["trsm"][1], 1)  # with the pre-pass
         res["solve_kernel_ms_per_launch"] = kernel_ms
@@ -734,7 +731,9 @@ def run_reference(args, world):
     w = workload(args)
     n, p, bs = w["n"], w["p"], w["bs"]
     s = gwas_synth.study(n, p, w["k"], w["h"], w["sigma2"])
-    per_step = 64 if n >= 5000 else 512
+    # the oracle parallelises over groups of 16 SNPs (one L stream per group): one group per thread
+    threads = oracle.num_threads()
+    per_step = 16 * threads * (1 if n >= 5000 else 8)
     X = gwas_synth.dosages(n, 0, per_step * (args.warmup + args.steps))
     L = oracle.potrf(oracle.form_m(s["Phi"], w["h"], w["sigma2"]))
     for i in range(args.warmup):
@@ -744,14 +743,16 @@ def run_reference(args, world):
         oracle.gls(L, s["XL"], s["y"], X[:, i * per_step:(i + 1) * per_step])
     dt = time.time() - t0
     v = args.steps * per_step / dt
-    sample = f"{per_step} SNPs per step at n={n}, p={p} (one bs={bs} block would take {bs / v:.0f} s); Cholesky excluded"
+    sample = (f"{per_step} SNPs per step = {per_step // 16} groups of 16 on {threads} threads, at n={n}, p={p} "
+              f"(one bs={bs} block would take {bs / v:.0f} s); Cholesky excluded")
     line = {
         "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
         "ms_per_step": 1e3 * dt / args.steps, "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
         "dtype": "f64", "data": "synthetic", "impl": "reference",
         "config": {"workload": WORKLOAD, "n": n, "p": p, "bs": bs, "snps_per_step": per_step,
                    "headline_path": "oracle-fp64-cpu", "parallelism": "host cores"},
-        "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle", "sample": sample},
+        "cpu_baseline": {"value": v, "unit": UNIT, "cores": threads, "kind": "oracle", "sample": sample,
+                         "snp_groups_per_step": per_step // 16},
         "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)

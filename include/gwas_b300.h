@@ -91,9 +91,7 @@ typedef struct {
   int tile_mode;   /* split modes, how the solve's tiles map onto the SMs:
                       GWAS_TILES_AUTO (0, default): the measured fastest of the others for the split;
                       GWAS_TILES_SINGLE (1): every 128-row tile on its own SM;
-                      GWAS_TILES_PAIR_MULTICAST (2): the row panels 2u and 2u+1 of a column strip on
-                        the two SMs of a thread-block cluster, each with its own product, the solved
-                        blocks both need fetched once;
+                      (2 is not a mode: GWAS_ERR_ARG)
                       GWAS_TILES_PAIR_MMA (3): panels 2u and 2u+1 as one 256-row tensor-core product
                         on the two SMs of a cluster;
                       GWAS_TILES_INVERSE (4): L^-1 is formed once at gwas_init (on the tensor cores,
@@ -121,7 +119,6 @@ typedef struct {
 enum {
   GWAS_TILES_AUTO = 0,
   GWAS_TILES_SINGLE = 1,
-  GWAS_TILES_PAIR_MULTICAST = 2,
   GWAS_TILES_PAIR_MMA = 3,
   GWAS_TILES_INVERSE = 4
 };
@@ -185,16 +182,20 @@ int gwas_solve_stream(gwas_ctx *ctx, const int8_t *XR_host, int64_t ldx, int64_t
  *   layouts and outputs as gwas_solve_block; asynchronous on the context's
  *   stream (device-side errors surface at gwas_synchronize).
  * Scratch: one fixed device array of GWAS_STATIC_SCRATCH_BYTES inside the
- * library (CUDA sets it aside when the library's device code is loaded on a
- * device and keeps it until the process exits).  A call needs
+ * library.  gwas_init, with the context's device current, looks the array's
+ * device address up (cudaGetSymbolAddress) and keeps it in the context; that
+ * lookup loads the array's module, which is when CUDA sets the array aside on
+ * the device (it stays until the process exits), and gwas_init also loads the
+ * kernels this call launches -- so every context holds its device's share of
+ * the array from gwas_init on, and the call itself needs no device memory even
+ * when the device's memory is full.  A call needs
  *   256-byte-rounded (128 + 4 * ceil(n/128) * ceil(ncols/64)) + 8 * n_pad * ncols
  * bytes, n_pad = n rounded up to 128 (at n = 10,000: up to 414 columns); a
- * larger call returns GWAS_ERR_ARG.  Every call uses the same array and it
- * keeps the previous call's contents (the call clears what must start at
- * zero): calls whose GPU work overlaps -- two streams, or two contexts at
- * once -- race on it and give wrong results.  The first call on a device looks
- * the array's device address up (cudaGetSymbolAddress); make that first call
- * before any stream capture.
+ * larger call returns GWAS_ERR_ARG before anything is launched.  Every call
+ * uses the same array and it keeps the previous call's contents (the call
+ * clears what must start at zero): calls whose GPU work overlaps -- two
+ * streams, or two contexts at once -- race on it and give wrong results.
+ * The call runs the FP64 solve whatever the context's precision.
  * Errors: GWAS_ERR_ARG, GWAS_ERR_CUDA. */
 #define GWAS_STATIC_SCRATCH_BYTES (32u * 1024u * 1024u)
 int gwas_solve_block_static(gwas_ctx *ctx, const int8_t *XR, int64_t ldx, int ncols, double *b, double *se,

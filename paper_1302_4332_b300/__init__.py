@@ -25,9 +25,11 @@ ERRORS = {
     -1: "GWAS_ERR_ARG", -2: "GWAS_ERR_NOT_SPD", -3: "GWAS_ERR_CUDA", -4: "GWAS_ERR_TIMEOUT",
     -5: "GWAS_ERR_IO", -6: "GWAS_ERR_NOMEM", -7: "GWAS_ERR_UNSUPPORTED",
 }
+GWAS_ERR_ARG, GWAS_ERR_NOT_SPD, GWAS_ERR_CUDA, GWAS_ERR_TIMEOUT = -1, -2, -3, -4
+GWAS_ERR_IO, GWAS_ERR_NOMEM, GWAS_ERR_UNSUPPORTED = -5, -6, -7
 PRECISIONS = {"fp64": 0, "tf32x3": 1, "bf16x3": 2, "f16x2": 3}
 # split modes: how the solve's tiles map onto SMs (gwas_config.tile_mode)
-TILE_MODES = {"auto": 0, "single": 1, "pair_multicast": 2, "pair_mma": 3, "inverse": 4}
+TILE_MODES = {"auto": 0, "single": 1, "pair_mma": 3, "inverse": 4}
 BUILT_PRECISIONS = ("fp64", "bf16x3", "tf32x3", "f16x2")
 SNP_OK, SNP_SINGULAR = 0, 1
 

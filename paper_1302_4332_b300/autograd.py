@@ -12,7 +12,15 @@ from . import GLS
 
 class WaldChi2Sum(torch.autograd.Function):
     """loss = sum_i chi2_i(h, y) over the SNP blocks; d loss/dh and d loss/dy
-    come from one adjoint pass per block (computed during forward)."""
+    come from one adjoint pass per block (computed during forward).
+
+    Every forward call sets the study up afresh for its (h, y): M and its
+    Cholesky factor depend on h, and y~, r_T and the solve constants on y, so
+    a call pays gwas_init (the FP64 Cholesky, n^3/3 flop, plus in the split
+    precisions the formation of L^-1 on the tensor cores) before its blocks:
+    about 0.1-0.5 s at n = 5,000-10,000, against milliseconds per block.  A fit
+    that moves h re-factors M at every step anyway; callers that evaluate many
+    blocks at one (h, y) should pass them all in one call."""
 
     @staticmethod
     def forward(ctx, h, y, phi, XL, blocks, sigma2=1.0, bs=4096, precision="fp64"):

@@ -67,6 +67,7 @@ struct gwas_ctx {
   double* h_se = nullptr;
   int* h_status = nullptr;
   double* f64_in = nullptr;  // n x bs FP64 staging for gwas_solve_block_f64 with host input
+  void* static_scratch = nullptr;  // device address of the fixed scratch array (gwas_solve_block_static)
   int64_t launches = 0;
   int64_t not_spd_index = -1;
   std::string detail;
@@ -279,7 +280,8 @@ int solve_common(gwas_ctx* ctx, const void* XR, bool int8_input, int64_t ldx, in
     return fail(ctx, GWAS_ERR_ARG, "bad arguments: XR=%p b=%p ncols=%d (bs %d) ldx=%lld (n %d)", XR, (void*)b,
                 ncols, ctx->bs, (long long)ldx, ctx->n);
   if (ncols == 0) return GWAS_OK;
-  CK(cudaSetDevice(ctx->dev));
+  DeviceScope dscope_(ctx->dev);
+  CK(dscope_.status());
   const bool dev_in = is_device_ptr(XR);
   const bool dev_out = is_device_ptr(b) && (!se || is_device_ptr(se)) && (!status || is_device_ptr(status));
   const void* xin = XR;
@@ -320,7 +322,7 @@ int solve_common(gwas_ctx* ctx, const void* XR, bool int8_input, int64_t ldx, in
 
 void free_all(gwas_ctx* c) {
   if (!c) return;
-  cudaSetDevice(c->dev);
+  DeviceScope dscope_(c->dev);
   cudaStreamSynchronize(c->stream);
   if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
   for (auto* p : c->ring) cudaFree(p);
@@ -377,6 +379,7 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
   if (cfg_in) cfg = *cfg_in;
   if (n < 1 || p < 1 || p > QMAX + 1 || !phi_or_L || !y || (p > 1 && !XL) || !(h >= 0.0 && h <= 1.0) ||
       !(sigma2 > 0.0) || cfg.bs < 1 || cfg.ring_depth < 2 || cfg.strip_group < 0 || cfg.tile_mode < GWAS_TILES_AUTO || cfg.tile_mode > GWAS_TILES_INVERSE ||
+      cfg.tile_mode == 2 /* not a mode */ ||
       cfg.precision < GWAS_FP64 || cfg.precision > GWAS_F16X2 ||
       (cfg.precision == GWAS_F16X2 && cfg.tile_mode != GWAS_TILES_AUTO && cfg.tile_mode != GWAS_TILES_INVERSE))
     return GWAS_ERR_ARG;
@@ -398,9 +401,11 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
     }
   }
   ctx->dev = dev;
-  {
-    cudaError_t e = cudaSetDevice(dev);
-    if (e != cudaSuccess) { cudaGetLastError(); free_all(ctx); return GWAS_ERR_CUDA; }
+  DeviceScope dscope_(dev);
+  if (dscope_.status() != cudaSuccess) {
+    cudaGetLastError();
+    free_all(ctx);
+    return GWAS_ERR_CUDA;
   }
   int rc = [&]() -> int {
     cudaDeviceProp prop;
@@ -543,6 +548,8 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
       for (auto& ev : *v) CK(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
     }
     CK(cudaStreamSynchronize(ctx->stream));
+    // the no-allocation block solve: its scratch array's address and its kernels, loaded now
+    CK(static_scratch_setup(&ctx->static_scratch));
     return GWAS_OK;
   }();
   if (rc != GWAS_OK) {
@@ -573,7 +580,8 @@ int gwas_solve_stream(gwas_ctx* ctx, const int8_t* XR_host, int64_t ldx, int64_t
   if (!XR_host || !b_host || m < 0 || ldx < ctx->n)
     return fail(ctx, GWAS_ERR_ARG, "bad arguments to gwas_solve_stream");
   if (m == 0) return GWAS_OK;
-  CK(cudaSetDevice(ctx->dev));
+  DeviceScope dscope_(ctx->dev);
+  CK(dscope_.status());
   const int R = ctx->ring_depth, bs = ctx->bs, p = ctx->p, T = ctx->t;
   const int64_t nblk = (m + bs - 1) / bs;
   auto cols_of = [&](int64_t blk) { return (int)std::min<int64_t>(bs, m - blk * bs); };
@@ -656,7 +664,8 @@ int gwas_solve_stream(gwas_ctx* ctx, const int8_t* XR_host, int64_t ldx, int64_t
 template <typename Sink>
 static int solve_file_impl(gwas_ctx* ctx, const char* path, int64_t header_bytes, int64_t ldx, int64_t col0, int64_t m,
                            bool want_se, bool want_status, Sink&& sink) {
-  CK(cudaSetDevice(ctx->dev));
+  DeviceScope dscope_(ctx->dev);
+  CK(dscope_.status());
   const int R = ctx->ring_depth, bs = ctx->bs, p = ctx->p;
   const int64_t nblk = (m + bs - 1) / bs;
   auto cols_of = [&](int64_t blk) { return (int)std::min<int64_t>(bs, m - blk * bs); };
@@ -880,7 +889,8 @@ int gwas_adjoint_block(gwas_ctx* ctx, const int8_t* XR, int64_t ldx, int ncols, 
   if (!(ctx->h > 0.0)) return fail(ctx, GWAS_ERR_ARG, "the adjoint needs h > 0");
   if (ctx->t != 1) return fail(ctx, GWAS_ERR_UNSUPPORTED, "the adjoint takes one phenotype");
   if (ncols == 0) return GWAS_OK;
-  CK(cudaSetDevice(ctx->dev));
+  DeviceScope dscope_(ctx->dev);
+  CK(dscope_.status());
   int rc = ensure_adjoint(ctx);
   if (rc != GWAS_OK) return rc;
   const int p = ctx->p, bs = ctx->bs, n = ctx->n;
@@ -991,6 +1001,8 @@ static int reml_eval_impl(const double* phi, int n, int q, const double* XL, con
   int rc = gwas_init(&ctx, n, q + 1, phi, 0, XL, y, h, 1.0, &c, stream);
   if (rc != GWAS_OK) return rc;
   rc = [&]() -> int {
+    DeviceScope dscope_(ctx->dev);
+    CK(dscope_.status());
     rc = ensure_adjoint(ctx);
     if (rc != GWAS_OK) return rc;
     const int nc = q + 1, np = ctx->n_pad;
@@ -1161,7 +1173,7 @@ int bfail(gwas_batch* B, int code, const char* msg, cudaError_t e = cudaSuccess)
 
 void batch_free(gwas_batch* B) {
   if (!B) return;
-  cudaSetDevice(B->dev);
+  DeviceScope dscope_(B->dev);
   if (B->stream) cudaStreamSynchronize(B->stream);
   if (B->exec) cudaGraphExecDestroy(B->exec);
   if (B->graph) cudaGraphDestroy(B->graph);
@@ -1231,8 +1243,9 @@ int gwas_batch_create(gwas_batch** out, gwas_ctx* const* studies, int nstudies, 
   gwas_batch* B = new gwas_batch;
   B->ns = nstudies;
   B->dev = studies[0]->dev;
+  DeviceScope dscope_(B->dev);
   int rc = [&]() -> int {
-    BCK(cudaSetDevice(B->dev), "set device");
+    BCK(dscope_.status(), "set device");
     if (stream) {
       B->stream = static_cast<cudaStream_t>(stream);
     } else {
@@ -1286,7 +1299,8 @@ int gwas_batch_solve(gwas_batch* B, const int8_t* const* XR, const int64_t* ldx,
       return bfail(B, GWAS_ERR_ARG, "bad arguments to gwas_batch_solve");
     cols[i] = ncols[i];
   }
-  BCK(cudaSetDevice(B->dev), "set device");
+  DeviceScope dscope_(B->dev);
+  BCK(dscope_.status(), "set device");
   for (int i = 0; i < B->ns; ++i) {
     if (cols[i] == 0) continue;
     gwas_ctx* c = B->ctx[i];
@@ -1328,7 +1342,8 @@ int gwas_batch_solve(gwas_batch* B, const int8_t* const* XR, const int64_t* ldx,
 
 int gwas_batch_synchronize(gwas_batch* B) {
   if (!B) return GWAS_ERR_ARG;
-  BCK(cudaSetDevice(B->dev), "set device");
+  DeviceScope dscope_(B->dev);
+  BCK(dscope_.status(), "set device");
   BCK(cudaStreamSynchronize(B->stream), "sync");
   for (int i = 0; i < B->ns; ++i) {
     int rc = check_device_status(B->ctx[i]);
@@ -1339,7 +1354,8 @@ int gwas_batch_synchronize(gwas_batch* B) {
 
 int gwas_batch_autotune(gwas_batch* B, int reps, int* cols_out, int* order_out, double* snps_per_s_out) {
   if (!B || !cols_out || reps < 1) return GWAS_ERR_ARG;
-  BCK(cudaSetDevice(B->dev), "set device");
+  DeviceScope dscope_(B->dev);
+  BCK(dscope_.status(), "set device");
   int maxc = 1 << 30;
   for (auto* c : B->ctx) maxc = std::min(maxc, c->bs);
   // synthetic dosages: any values cost the same; fill the slots with 1
@@ -1396,6 +1412,8 @@ int gwas_batch_solve_files(gwas_batch* B, const char* const* paths, const int64_
         (m[i] > 0 && !b_host[i]))
       return bfail(B, GWAS_ERR_ARG, "bad arguments to gwas_batch_solve_files");
   }
+  DeviceScope dscope_(B->dev);
+  BCK(dscope_.status(), "set device");
   std::vector<int64_t> nblk(ns);
   int64_t steps = 0;
   for (int i = 0; i < ns; ++i) {
@@ -1499,7 +1517,8 @@ extern "C" {
 
 int gwas_check_timeout(gwas_ctx* ctx, int kind, int limit_us) {
   if (!ctx || (kind != 0 && kind != 1) || limit_us < 1 || limit_us > 1000000) return GWAS_ERR_ARG;
-  CK(cudaSetDevice(ctx->dev));
+  DeviceScope dscope_(ctx->dev);
+  CK(dscope_.status());
   check_timeout_kernel<<<1, 32, 0, ctx->stream>>>(kind, 1000LL * limit_us, ctx->st);
   CK(cudaGetLastError());
   ctx->launches += 1;
@@ -1508,7 +1527,8 @@ int gwas_check_timeout(gwas_ctx* ctx, int kind, int limit_us) {
 
 int gwas_synchronize(gwas_ctx* ctx) {
   if (!ctx) return GWAS_ERR_ARG;
-  CK(cudaSetDevice(ctx->dev));
+  DeviceScope dscope_(ctx->dev);
+  CK(dscope_.status());
   CK(cudaStreamSynchronize(ctx->stream));
   return check_device_status(ctx);
 }
@@ -1531,7 +1551,8 @@ int gwas_get_info(const gwas_ctx* ctx, int* n, int* p, int* n_pad, int* precisio
 
 int gwas_solve_shape(const gwas_ctx* ctx, int* ctas, int* cluster_size, int* tile_mode) {
   if (!ctx) return GWAS_ERR_ARG;
-  if (cudaSetDevice(ctx->dev) != cudaSuccess) {
+  DeviceScope dscope_(ctx->dev);
+  if (dscope_.status() != cudaSuccess) {
     cudaGetLastError();
     return GWAS_ERR_CUDA;
   }
@@ -1554,7 +1575,8 @@ int64_t gwas_not_spd_index(const gwas_ctx* ctx) { return ctx ? ctx->not_spd_inde
 
 int gwas_copy_factor(gwas_ctx* ctx, double* L, int64_t ld) {
   if (!ctx || !L || ld < ctx->n) return GWAS_ERR_ARG;
-  CK(cudaSetDevice(ctx->dev));
+  DeviceScope dscope_(ctx->dev);
+  CK(dscope_.status());
   CK(cudaMemcpy2DAsync(L, sizeof(double) * (size_t)ld, ctx->L, sizeof(double) * (size_t)ctx->n_pad,
                        sizeof(double) * (size_t)ctx->n, (size_t)ctx->n, cudaMemcpyDefault, ctx->stream));
   CK(cudaStreamSynchronize(ctx->stream));
@@ -1563,7 +1585,8 @@ int gwas_copy_factor(gwas_ctx* ctx, double* L, int64_t ld) {
 
 int gwas_timing_enable(gwas_ctx* ctx, int enable) {
   if (!ctx) return GWAS_ERR_ARG;
-  CK(cudaSetDevice(ctx->dev));
+  DeviceScope dscope_(ctx->dev);
+  CK(dscope_.status());
   CK(cudaStreamSynchronize(ctx->stream));
   CK(cudaStreamSynchronize(ctx->copy_stream));
   for (auto& mk : ctx->marks) {
@@ -1577,7 +1600,8 @@ int gwas_timing_enable(gwas_ctx* ctx, int enable) {
 
 int gwas_timing_read(gwas_ctx* ctx, double* ms, int64_t* count) {
   if (!ctx || !ms || !count) return GWAS_ERR_ARG;
-  CK(cudaSetDevice(ctx->dev));
+  DeviceScope dscope_(ctx->dev);
+  CK(dscope_.status());
   for (int i = 0; i < GWAS_NSTAGES; ++i) { ms[i] = 0.0; count[i] = 0; }
   for (auto& mk : ctx->marks) {
     CK(cudaEventSynchronize(mk.b));
@@ -1610,5 +1634,6 @@ bool gwas::ctx_view(gwas_ctx* ctx, CtxView* v) {
   v->sc = ctx->sc;
   v->st = ctx->st;
   v->launches = &ctx->launches;
+  v->static_scratch = ctx->static_scratch;
   return true;
 }

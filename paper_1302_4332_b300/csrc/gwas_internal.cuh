@@ -186,8 +186,45 @@ struct CtxView {
   const SolveConsts* sc;
   DevStatus* st;
   int64_t* launches;
+  void* static_scratch;  // device address of the library's fixed scratch array on this device
 };
 bool ctx_view(gwas_ctx* ctx, CtxView* v);
+
+// Set-up of the no-allocation block solve (static_scratch.cu), run by
+// gwas_init with the context's device current: looks up the device address
+// of the fixed scratch array (which loads its module, so the array is set
+// aside now, not at the first solve) and loads the kernels that solve uses.
+cudaError_t static_scratch_setup(void** addr);
+// Load the FP64 solve's int8 kernel and the FP64 reduction kernel (lazy
+// module loading would otherwise load them, allocating device memory for
+// their code, at their first launch).
+cudaError_t preload_trsm_f64_int8();
+cudaError_t preload_reduce_solve_f64();
+
+// Makes `dev` the calling thread's current device for the scope and gives the
+// caller's device back on exit, so that a library call never leaves the
+// calling thread on another device.
+class DeviceScope {
+ public:
+  explicit DeviceScope(int dev) {
+    if (cudaGetDevice(&prev_) != cudaSuccess) {
+      cudaGetLastError();
+      prev_ = -1;
+    }
+    err_ = prev_ == dev ? cudaSuccess : cudaSetDevice(dev);
+  }
+  ~DeviceScope() {
+    int cur = -1;
+    if (prev_ >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev_) cudaSetDevice(prev_);
+  }
+  DeviceScope(const DeviceScope&) = delete;
+  DeviceScope& operator=(const DeviceScope&) = delete;
+  cudaError_t status() const { return err_; }
+
+ private:
+  int prev_ = -1;
+  cudaError_t err_ = cudaSuccess;
+};
 
 // The file reader over caller-owned pinned buffers (host_reader.cu).
 int reader_open_with(gwas_reader** out, const char* path, int64_t offset, int64_t block_bytes, int64_t nblocks,

@@ -468,6 +468,14 @@ __global__ void __launch_bounds__(32 * (BCW + 1), 1) reduce_solve_bulk_kernel(
   }
 }
 
+cudaError_t preload_reduce_solve_f64() {
+  cudaFuncAttributes fa;
+  cudaError_t e = cudaFuncGetAttributes(&fa, reduce_solve_kernel<3>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, reduce_solve_kernel<7>);
+  if (e == cudaSuccess) e = cudaFuncGetAttributes(&fa, reduce_solve_kernel<QMAX>);
+  return e;
+}
+
 cudaError_t prepare_reduce_solve() {
   cudaError_t e = cudaFuncSetAttribute(reduce_solve_bulk_kernel<3, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        BulkCfg<4>::SMEM);

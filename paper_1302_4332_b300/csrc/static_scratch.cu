@@ -10,13 +10,18 @@
 //
 // The scratch is one file-scope __device__ array of GWAS_STATIC_SCRATCH_BYTES.
 // Host code may not use the array's name as a device address (on the host it
-// names a host-side shadow), so the entry point looks the address up with
-// cudaGetSymbolAddress once per device, with that device current, and passes
-// that pointer to the kernels.
+// names a host-side shadow), so gwas_init, with the context's device current,
+// looks the address up with cudaGetSymbolAddress (static_scratch_setup) and
+// keeps it in the context; the entry point passes that pointer to the kernels.
+// The lookup also loads this file's module, which is when CUDA sets the array
+// aside, and the set-up loads the kernels the call launches: with CUDA's lazy
+// loading both would otherwise happen at the first call, which would then
+// need device memory.  The address belongs to the CUDA context that was
+// current at gwas_init; a context destroyed by cudaDeviceReset takes every
+// gwas context of that device with it.
 #include <cuda_runtime.h>
 
 #include <cstdint>
-#include <mutex>
 
 #include "gwas_internal.cuh"
 
@@ -24,27 +29,9 @@ namespace {
 
 constexpr size_t kScratchBytes = GWAS_STATIC_SCRATCH_BYTES;
 constexpr size_t kSchedBytes = 128;  // scheduler counter, then the tile flags
-constexpr int kMaxDevices = 64;
 
 // Per-call scratch: [scheduler counter | tile flags | padding to 256 B | X~ block (FP64)].
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];
-
-std::mutex g_mu;
-void* g_addr[kMaxDevices] = {};
-
-// The device address of g_scratch on device `dev` (which must be current).
-cudaError_t scratch_address(int dev, void** out) {
-  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_addr[dev]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess) return e;
-    g_addr[dev] = p;
-  }
-  *out = g_addr[dev];
-  return cudaSuccess;
-}
 
 bool is_device(const void* p) {
   if (!p) return false;
@@ -58,6 +45,21 @@ bool is_device(const void* p) {
 
 }  // namespace
 
+namespace gwas {
+
+cudaError_t static_scratch_setup(void** addr) {
+  *addr = nullptr;
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+  if (e != cudaSuccess) return e;
+  if ((e = preload_trsm_f64_int8()) != cudaSuccess) return e;
+  if ((e = preload_reduce_solve_f64()) != cudaSuccess) return e;
+  *addr = p;
+  return cudaSuccess;
+}
+
+}  // namespace gwas
+
 extern "C" int gwas_solve_block_static(gwas_ctx* ctx, const int8_t* XR, int64_t ldx, int ncols, double* b,
                                        double* se, int* status) {
   using namespace gwas;
@@ -66,18 +68,18 @@ extern "C" int gwas_solve_block_static(gwas_ctx* ctx, const int8_t* XR, int64_t 
   if (v.t != 1) return GWAS_ERR_UNSUPPORTED;  // one phenotype
   if (ncols < 0 || ldx < v.n || !XR || !b) return GWAS_ERR_ARG;
   if (ncols == 0) return GWAS_OK;
-  if (!is_device(XR) || !is_device(b) || (se && !is_device(se)) || (status && !is_device(status)))
-    return GWAS_ERR_ARG;
   const int C = (ncols + F64_TN - 1) / F64_TN;
   const size_t flags_bytes = sizeof(int) * (size_t)v.P * C;
   const size_t xt_off = (kSchedBytes + flags_bytes + 255) / 256 * 256;
   const size_t need = xt_off + sizeof(double) * (size_t)v.n_pad * ncols;
   if (need > kScratchBytes) return GWAS_ERR_ARG;  // beyond the fixed scratch: use gwas_solve_block
+  if (!v.static_scratch) return GWAS_ERR_CUDA;
 
-  if (cudaSetDevice(v.dev) != cudaSuccess) return GWAS_ERR_CUDA;
-  void* base = nullptr;
-  if (scratch_address(v.dev, &base) != cudaSuccess) return GWAS_ERR_CUDA;
-  unsigned char* sp = static_cast<unsigned char*>(base);
+  DeviceScope scope(v.dev);
+  if (scope.status() != cudaSuccess) return GWAS_ERR_CUDA;
+  if (!is_device(XR) || !is_device(b) || (se && !is_device(se)) || (status && !is_device(status)))
+    return GWAS_ERR_ARG;
+  unsigned char* sp = static_cast<unsigned char*>(v.static_scratch);
   Sched* sched = reinterpret_cast<Sched*>(sp);
   double* Xt = reinterpret_cast<double*>(sp + xt_off);
 

@@ -161,6 +161,11 @@ int trsm_f64_grid(int num_sms) {
   return num_sms * (per_sm < 1 ? 1 : per_sm);
 }
 
+cudaError_t preload_trsm_f64_int8() {
+  cudaFuncAttributes fa;
+  return cudaFuncGetAttributes(&fa, trsm_f64_kernel<int8_t, false>);
+}
+
 cudaError_t launch_trsm_f64(const TrsmF64Args& a, bool int8_input, cudaStream_t s, int num_sms, bool upper) {
   if (a.ncols <= 0) return cudaSuccess;
   int per_sm = 0;

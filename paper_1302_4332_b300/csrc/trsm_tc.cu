@@ -1,7 +1,7 @@
 // a6, split-precision modes: the blocked triangular solve X~ = L^-1 X on the
 // 5th-generation tensor cores (tcgen05), operands brought in by TMA,
 // accumulators in tensor memory (TMEM).  This file holds the solve kernels --
-// the substitution (single CTAs, pair with multicast, pair product) and the
+// the substitution (single CTAs, pair product) and the
 // inverse form (the product with a precomputed L^-1, further below) -- and
 // their launch entries; per-study state, set-up and pre-passes are in
 // trsm_tc_host.cu.
@@ -94,75 +94,50 @@ __device__ __forceinline__ void store_tile(const float (&master)[EPI_COLS], cons
 // K-block kinds of a work unit's stage sequence.
 enum KbKind : int {
   KB_DIAG = 0,    // j == k: Aop hi/lo by TMA, B = the int8 block cast in shared memory
-  KB_SHARED = 1,  // pair mode, j < 2u: each CTA loads its own Aop and half of X~_jc for both
-  KB_LOCAL = 2,   // Aop and all of X~_jc by this CTA alone
-  KB_NULL = 3,    // no loads, no MMA: keeps the two CTAs' stage rings in step
+  KB_LOCAL = 2,   // Aop and all of X~_jc by this CTA
   KB_DIAG_IN = 4  // transpose solve, j == k: B = the forward solve's X~ pieces by TMA (3 products)
 };
 
-// A work unit.  Single mode: the tile (k, c).  Pair mode: the tiles (2u, c)
-// and (2u+1, c) on the two CTAs of a cluster (rank r takes row panel 2u + r).
+// A work unit: the tile (k, c).
 struct Unit {
-  int k;        // this CTA's row panel
-  bool has;     // this CTA has a tile (the last unit of an odd P has one)
-  bool paired;  // both CTAs have a tile
-  int nkb;      // K-blocks in the unit's stage sequence (the same on both CTAs)
+  int k;    // row panel
+  int nkb;  // K-blocks in the unit's stage sequence
 };
 
-// UPPER (transpose solve X^ = L^-T X~, single CTAs): row panels from the
-// last one up; tile (k, c) walks j = k (its own X~ input), then P-1 .. k+1.
-template <bool PAIR, bool UPPER = false>
-__device__ __forceinline__ Unit make_unit(int row, const TcStudy& S, uint32_t rank) {
+// UPPER (transpose solve X^ = L^-T X~): row panels from the last one up;
+// tile (k, c) walks j = k (its own X~ input), then P-1 .. k+1.
+template <bool UPPER = false>
+__device__ __forceinline__ Unit make_unit(int row, const TcStudy& S) {
   Unit u;
   if (UPPER) {
     u.k = S.P - 1 - row;
-    u.has = true;
-    u.paired = false;
     u.nkb = S.P - u.k;
-  } else if (PAIR) {
-    u.k = 2 * row + (int)rank;
-    u.has = u.k < S.P;
-    u.paired = 2 * row + 1 < S.P;
-    u.nkb = 2 * row + (u.paired ? 2 : 1);
   } else {
     u.k = row;
-    u.has = true;
-    u.paired = false;
     u.nkb = row + 1;
   }
   return u;
 }
 
-// K-block jj of a unit: its kind, and j, the block column of Aop it multiplies.
-// Pair mode, both tiles present: rank 0 runs [diag 2u, shared 0..2u-1, null],
-// rank 1 [diag 2u+1, shared 0..2u-1, local 2u] (X~ of rank 0's own tile).
-template <bool PAIR, bool UPPER = false>
-__device__ __forceinline__ KbKind kb_kind(const Unit& u, int row, uint32_t rank, int jj, int& j) {
+// K-block jj of a unit: its kind, and j, the block column of Aop it multiplies
+// (forward: the diagonal block first, then 0 .. k-1).
+template <bool UPPER = false>
+__device__ __forceinline__ KbKind kb_kind(const Unit& u, int jj, int& j) {
   if (UPPER) {
     j = jj == 0 ? u.k : u.k + u.nkb - jj;  // k, then P-1 .. k+1
     return jj == 0 ? KB_DIAG_IN : KB_LOCAL;
   }
   if (jj == 0) {
     j = u.k;
-    return u.has ? KB_DIAG : KB_NULL;
+    return KB_DIAG;
   }
-  if (!PAIR) {
-    j = jj - 1;
-    return KB_LOCAL;
-  }
-  if (jj <= 2 * row) {
-    j = jj - 1;
-    if (u.paired) return KB_SHARED;
-    return rank == 0 ? KB_LOCAL : KB_NULL;
-  }
-  j = 2 * row;
-  return rank == 1 ? KB_LOCAL : KB_NULL;
+  j = jj - 1;
+  return KB_LOCAL;
 }
 
-template <bool TF32, bool PAIR, bool UPPER = false>
+template <bool TF32, bool UPPER = false>
 __global__ void __launch_bounds__(THREADS, 1)
     trsm_tc_kernel(const __grid_constant__ TcBatch b) {
-  static_assert(!(PAIR && UPPER), "the transpose solve runs on single CTAs");
   using K = Cfg<TF32>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -177,20 +152,18 @@ __global__ void __launch_bounds__(THREADS, 1)
   uint64_t* x8_full = tile_empty + TRING;
   uint64_t* x8_empty = x8_full + 1;
   uint64_t* drain = x8_empty + 1;
-  uint64_t* peer_free = drain + 1;  // pair mode, rank 0: rank 1 is done with a tile-ring slot
+  uint64_t* peer_free = drain + 1;  // unused (kept so the barrier block keeps its size)
   int* tile_ring = reinterpret_cast<int*>(peer_free + TRING);
   uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tile_ring + TRING);
 
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int ntiles = b.ntiles;  // work units
   DevStatus* st = b.st;
-  const uint32_t rank = PAIR ? ptx::cluster_ctarank() : 0u;
-  constexpr uint16_t BOTH = 3;  // multicast mask: both CTAs of the pair
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
-      ptx::mbar_init(&full[s], 2);             // producer (+tx) and producer-or-cast
-      ptx::mbar_init(&empty[s], PAIR ? 2 : 1);  // the MMA commit of every CTA that reads the stage
+      ptx::mbar_init(&full[s], 2);   // producer (+tx) and producer-or-cast
+      ptx::mbar_init(&empty[s], 1);  // the MMA commit
     }
     for (int a = 0; a < 2; ++a) {
       ptx::mbar_init(&part_full[a], 1);           // MMA commit
@@ -199,7 +172,6 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int i = 0; i < TRING; ++i) {
       ptx::mbar_init(&tile_full[i], 1);
       ptx::mbar_init(&tile_empty[i], 1 + 2 + EPI_WARPS);  // MMA + cast warps + epilogue warps
-      ptx::mbar_init(&peer_free[i], 1);
     }
     ptx::mbar_init(x8_full, 1);
     ptx::mbar_init(x8_empty, 1);
@@ -211,10 +183,6 @@ __global__ void __launch_bounds__(THREADS, 1)
       ptx::prefetch_tensormap(&b.maps[q].Bhi);
       ptx::prefetch_tensormap(&b.maps[q].Blo);
       ptx::prefetch_tensormap(&b.maps[q].X8);
-      if (PAIR) {
-        ptx::prefetch_tensormap(&b.maps[q].BhiH);
-        ptx::prefetch_tensormap(&b.maps[q].BloH);
-      }
     }
   }
   if (warp == 2) {
@@ -224,7 +192,6 @@ __global__ void __launch_bounds__(THREADS, 1)
   ptx::tc_fence_before();
   __syncthreads();
   ptx::tc_fence_after();
-  if (PAIR) ptx::cluster_sync();  // the peer's barriers exist before any remote access
   const uint32_t tmem_base = *tmem_slot;
 
   if (warp == 0) {
@@ -235,29 +202,17 @@ __global__ void __launch_bounds__(THREADS, 1)
         const int slot = it % TRING;
         const uint32_t use = it / TRING;
         if (!ptx::mbar_wait(&tile_empty[slot], (use & 1) ^ 1, st)) break;
-        int t;
-        if (!PAIR || rank == 0) {
-          // pair mode: rank 0 takes the unit for both CTAs and writes it into
-          // rank 1's ring as well, once rank 1 has released the slot
-          if (PAIR && !ptx::mbar_wait(&peer_free[slot], use & 1, st)) break;
-          t = ptx::aborting(st) ? ntiles : (int)atomicAdd(b.counter, 1u);
-          if (t > ntiles) t = ntiles;
-          tile_ring[slot] = t;
-          if (PAIR) ptx::st_peer_u32(ptx::peer_addr(&tile_ring[slot], 1), (uint32_t)t);
-          ptx::mbar_arrive(&tile_full[slot]);
-          if (PAIR) ptx::mbar_arrive_peer(ptx::peer_addr(&tile_full[slot], 1));
-        } else {
-          ptx::mbar_arrive_peer(ptx::peer_addr(&peer_free[slot], 0));
-          if (!ptx::mbar_wait_s<true>(&tile_full[slot], use & 1, st)) break;
-          t = tile_ring[slot];
-        }
+        int t = ptx::aborting(st) ? ntiles : (int)atomicAdd(b.counter, 1u);
+        if (t > ntiles) t = ntiles;
+        tile_ring[slot] = t;
+        ptx::mbar_arrive(&tile_full[slot]);
         if (t >= ntiles) break;
         int sidx, row, c;
         TcStudy S;
         decode_tile(b, t, sidx, row, c, S);
         const TcMaps& M = b.maps[sidx];
-        const Unit u = make_unit<PAIR, UPPER>(row, S, rank);
-        if (u.has && !UPPER) {
+        const Unit u = make_unit<UPPER>(row, S);
+        if (!UPPER) {
           if (!ptx::mbar_wait(x8_empty, (x8n & 1) ^ 1, st)) break;
           ptx::mbar_arrive_expect_tx(x8_full, K::X8_BYTES);
           ptx::tma_load_2d(x8, &M.X8, x8_full, u.k * TB, c * TN);
@@ -266,8 +221,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         bool ok = true;
         for (int jj = 0; jj < u.nkb && ok; ++jj) {
           int j;
-          const KbKind kind = kb_kind<PAIR, UPPER>(u, row, rank, jj, j);
-          if (kind == KB_SHARED || kind == KB_LOCAL) {
+          const KbKind kind = kb_kind<UPPER>(u, jj, j);
+          if (kind == KB_LOCAL) {
             if (!ptx::wait_flag(&S.flags[j * S.C + c], st)) { ok = false; break; }
             ptx::fence_proxy_async_global();
           }
@@ -277,10 +232,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             if (!ptx::mbar_wait(&empty[s], (r & 1) ^ 1, st)) { ok = false; break; }
             uint8_t* sb = smem + s * K::STAGE_BYTES;
             const int kx = j * TB + h * K::KCH;
-            if (kind == KB_NULL) {
-              ptx::mbar_arrive(&full[s]);
-              ptx::mbar_arrive(&full[s]);
-            } else if (kind == KB_DIAG) {
+            if (kind == KB_DIAG) {
               ptx::mbar_arrive_expect_tx(&full[s], 2 * K::A_BYTES);
               ptx::tma_load_2d(sb, &M.Ahi, &full[s], kx, u.k * TB);
               ptx::tma_load_2d(sb + K::A_BYTES, &M.Alo, &full[s], kx, u.k * TB);
@@ -288,15 +240,7 @@ __global__ void __launch_bounds__(THREADS, 1)
               ptx::mbar_arrive_expect_tx(&full[s], 2 * K::A_BYTES + 2 * K::B_BYTES);
               ptx::tma_load_2d(sb, &M.Ahi, &full[s], kx, u.k * TB);
               ptx::tma_load_2d(sb + K::A_BYTES, &M.Alo, &full[s], kx, u.k * TB);
-              if (PAIR && kind == KB_SHARED) {
-                // this CTA's half of the strip's columns, into both CTAs (the
-                // peer sends the other half); the 8 KB offset keeps the
-                // 512-byte swizzle atoms of a full-width load
-                constexpr int HB = K::B_BYTES / 2;
-                const int y = c * TN + (int)rank * (TN / 2);
-                ptx::tma_load_2d_mc(sb + 2 * K::A_BYTES + rank * HB, &M.BhiH, &full[s], kx, y, BOTH);
-                ptx::tma_load_2d_mc(sb + 2 * K::A_BYTES + K::B_BYTES + rank * HB, &M.BloH, &full[s], kx, y, BOTH);
-              } else if (UPPER && kind == KB_DIAG_IN) {
+              if (UPPER && kind == KB_DIAG_IN) {
                 ptx::tma_load_2d(sb + 2 * K::A_BYTES, &M.BinHi, &full[s], kx, c * TN);
                 ptx::tma_load_2d(sb + 2 * K::A_BYTES + K::B_BYTES, &M.BinLo, &full[s], kx, c * TN);
               } else {
@@ -315,39 +259,25 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (lane == 0) {
       constexpr uint32_t idesc = ptx::idesc_f32acc<TF32>(TB, TN);
       uint32_t cnt = 0, kb = 0;
-      // a consumed stage is released to every CTA that writes it
-      auto release = [&](int s) {
-        if (PAIR)
-          ptx::mma_commit_mc(&empty[s], BOTH);
-        else
-          ptx::mma_commit(&empty[s]);
-      };
+      auto release = [&](int s) { ptx::mma_commit(&empty[s]); };  // a consumed stage goes back to the producer
       for (int it = 0;; ++it) {
         const int slot = it % TRING;
         const uint32_t use = it / TRING;
-        if (!ptx::mbar_wait_s<PAIR>(&tile_full[slot], use & 1, st)) break;
+        if (!ptx::mbar_wait(&tile_full[slot], use & 1, st)) break;
         const int t = tile_ring[slot];
         ptx::mbar_arrive(&tile_empty[slot]);
         if (t >= ntiles) break;
         int sidx, row, c;
         TcStudy S;
         decode_tile(b, t, sidx, row, c, S);
-        const Unit u = make_unit<PAIR, UPPER>(row, S, rank);
+        const Unit u = make_unit<UPPER>(row, S);
         bool ok = true;
-        int q = 0;  // K-blocks of this CTA's tile issued so far (k + 1 in all)
+        int q = 0;  // K-blocks of the tile issued so far
         int a = 0;
         uint32_t d = 0, accumulate = 0;
         for (int jj = 0; jj < u.nkb && ok; ++jj) {
           int j;
-          const KbKind kind = kb_kind<PAIR, UPPER>(u, row, rank, jj, j);
-          if (kind == KB_NULL) {
-            for (int h = 0; h < K::CPB; ++h, ++cnt) {
-              const int s = cnt % STAGES;
-              if (!ptx::mbar_wait(&full[s], (cnt / STAGES) & 1, st)) { ok = false; break; }
-              release(s);
-            }
-            continue;
-          }
+          const KbKind kind = kb_kind<UPPER>(u, jj, j);
           if (q % PROMOTE == 0) {
             // a fresh partial every PROMOTE K-blocks, alternating between the two TMEM buffers
             a = kb & 1;
@@ -394,7 +324,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int it = 0;; ++it) {
       const int slot = it % TRING;
       const uint32_t use = it / TRING;
-      if (!ptx::group_and(2, 64, ptx::mbar_wait_s<PAIR>(&tile_full[slot], use & 1, st))) break;
+      if (!ptx::group_and(2, 64, ptx::mbar_wait(&tile_full[slot], use & 1, st))) break;
       const int t = tile_ring[slot];
       ptx::named_bar(2, 64);
       if (lane == 0) ptx::mbar_arrive(&tile_empty[slot]);
@@ -402,8 +332,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       int sidx, row, ctile;
       TcStudy S;
       decode_tile(b, t, sidx, row, ctile, S);
-      const Unit u = make_unit<PAIR, UPPER>(row, S, rank);
-      if (u.has && !UPPER) {
+      const Unit u = make_unit<UPPER>(row, S);
+      if (!UPPER) {
         const int k = u.k;
         if (!ptx::group_and(2, 64, ptx::mbar_wait(x8_full, x8n & 1, st))) break;
         bool ok = true;
@@ -471,7 +401,7 @@ __global__ void __launch_bounds__(THREADS, 1)
     for (int it = 0;; ++it) {
       const int slot = it % TRING;
       const uint32_t use = it / TRING;
-      if (!ptx::group_and(1, NT, ptx::mbar_wait_s<PAIR>(&tile_full[slot], use & 1, st))) break;
+      if (!ptx::group_and(1, NT, ptx::mbar_wait(&tile_full[slot], use & 1, st))) break;
       const int t = tile_ring[slot];
       ptx::named_bar(1, NT);
       if (lane == 0) ptx::mbar_arrive(&tile_empty[slot]);
@@ -479,8 +409,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       int sidx, row, c;
       TcStudy S;
       decode_tile(b, t, sidx, row, c, S);
-      const Unit u = make_unit<PAIR, UPPER>(row, S, rank);
-      if (!u.has) continue;
+      const Unit u = make_unit<UPPER>(row, S);
       const int k = u.k;
 #pragma unroll
       for (int i = 0; i < EPI_COLS; ++i) master[i] = 0.f;
@@ -528,9 +457,6 @@ __global__ void __launch_bounds__(THREADS, 1)
     while (ptx::globaltimer() - t0 < 2000000LL) {
     }
   }
-  // pair mode: neither CTA retires while the other may still write its shared
-  // memory or arrive on its barriers
-  if (PAIR) ptx::cluster_sync();
   ptx::tc_fence_before();
   __syncthreads();
   ptx::tc_fence_after();
@@ -1538,9 +1464,7 @@ static cudaLaunchConfig_t pair_config(cudaLaunchAttribute* attr, int grid, cudaS
   memset(&cfg, 0, sizeof cfg);
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(THREADS);
-  cfg.dynamicSmemBytes = mode == TILES_INVERSE    ? inv2::Cfg<TF32>::SMEM
-                         : mode == TILES_PAIR_MMA ? pair2::Cfg<TF32>::SMEM
-                                                  : Cfg<TF32>::SMEM;
+  cfg.dynamicSmemBytes = mode == TILES_INVERSE ? inv2::Cfg<TF32>::SMEM : pair2::Cfg<TF32>::SMEM;
   cfg.stream = s;
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = 2;
@@ -1554,9 +1478,8 @@ static cudaLaunchConfig_t pair_config(cudaLaunchAttribute* attr, int grid, cudaS
 template <bool TF32>
 static cudaError_t set_attrs(bool clusters) {
   constexpr cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t e = cudaFuncSetAttribute(trsm_tc_kernel<TF32, false>, A, Cfg<TF32>::SMEM);
+  cudaError_t e = cudaFuncSetAttribute(trsm_tc_kernel<TF32>, A, Cfg<TF32>::SMEM);
   if (e != cudaSuccess || !clusters) return e;
-  if ((e = cudaFuncSetAttribute(trsm_tc_kernel<TF32, true>, A, Cfg<TF32>::SMEM)) != cudaSuccess) return e;
   if ((e = cudaFuncSetAttribute(trsm_tc_pair_mma_kernel<TF32>, A, pair2::Cfg<TF32>::SMEM)) != cudaSuccess) return e;
   if (!TF32 && (e = cudaFuncSetAttribute(trsm_tc_inv_kernel<false, true>, A, inv2::Cfg<false>::SMEM)) != cudaSuccess)
     return e;
@@ -1572,18 +1495,17 @@ cudaError_t set_kernel_attrs(bool tf32, bool clusters) {
 
 cudaError_t set_upper_attr(bool tf32) {
   constexpr cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  return tf32 ? cudaFuncSetAttribute(trsm_tc_kernel<true, false, true>, A, Cfg<true>::SMEM)
-              : cudaFuncSetAttribute(trsm_tc_kernel<false, false, true>, A, Cfg<false>::SMEM);
+  return tf32 ? cudaFuncSetAttribute(trsm_tc_kernel<true, true>, A, Cfg<true>::SMEM)
+              : cudaFuncSetAttribute(trsm_tc_kernel<false, true>, A, Cfg<false>::SMEM);
 }
 
 template <bool TF32>
 static cudaError_t clusters_of(int num_sms, TileMode mode, int* out, bool f16) {
   cudaLaunchAttribute attr[1];
   cudaLaunchConfig_t cfg = pair_config<TF32>(attr, 2 * (num_sms / 2), nullptr, mode);
-  const void* fn = mode == TILES_INVERSE    ? (f16 ? (const void*)trsm_tc_inv_kernel<false, true>
-                                                   : (const void*)trsm_tc_inv_kernel<TF32>)
-                   : mode == TILES_PAIR_MMA ? (const void*)trsm_tc_pair_mma_kernel<TF32>
-                                            : (const void*)trsm_tc_kernel<TF32, true>;
+  const void* fn = mode == TILES_INVERSE ? (f16 ? (const void*)trsm_tc_inv_kernel<false, true>
+                                                : (const void*)trsm_tc_inv_kernel<TF32>)
+                                         : (const void*)trsm_tc_pair_mma_kernel<TF32>;
   return cudaOccupancyMaxActiveClusters(out, fn, &cfg);
 }
 
@@ -1603,13 +1525,13 @@ static cudaError_t launch_pair(const TcBatch& b, int max_clusters, cudaStream_t 
   }
   if (mode == TILES_INVERSE && f16 && !TF32) return cudaLaunchKernelEx(&cfg, trsm_tc_inv_kernel<false, true>, b);
   if (mode == TILES_INVERSE) return cudaLaunchKernelEx(&cfg, trsm_tc_inv_kernel<TF32>, b);
-  if (mode == TILES_PAIR_MMA) return cudaLaunchKernelEx(&cfg, trsm_tc_pair_mma_kernel<TF32>, b);
-  return cudaLaunchKernelEx(&cfg, trsm_tc_kernel<TF32, true>, b);
+  return cudaLaunchKernelEx(&cfg, trsm_tc_pair_mma_kernel<TF32>, b);
 }
 
 cudaError_t launch_solve(bool tf32, TileMode mode, const TcBatch& b, int num_sms, int max_clusters,
                          cudaStream_t s, bool f16) {
   if (f16 && (tf32 || mode != TILES_INVERSE)) return cudaErrorInvalidValue;
+  if (mode != TILES_SINGLE && mode != TILES_PAIR_MMA && mode != TILES_INVERSE) return cudaErrorInvalidValue;
   if (mode != TILES_SINGLE) {
     const cudaError_t e = tf32 ? launch_pair<true>(b, max_clusters, s, mode, false)
                                : launch_pair<false>(b, max_clusters, s, mode, f16);
@@ -1617,9 +1539,9 @@ cudaError_t launch_solve(bool tf32, TileMode mode, const TcBatch& b, int num_sms
   }
   const int grid = b.ntiles < num_sms ? b.ntiles : num_sms;
   if (tf32)
-    trsm_tc_kernel<true, false><<<grid, THREADS, Cfg<true>::SMEM, s>>>(b);
+    trsm_tc_kernel<true><<<grid, THREADS, Cfg<true>::SMEM, s>>>(b);
   else
-    trsm_tc_kernel<false, false><<<grid, THREADS, Cfg<false>::SMEM, s>>>(b);
+    trsm_tc_kernel<false><<<grid, THREADS, Cfg<false>::SMEM, s>>>(b);
   return cudaGetLastError();
 }
 
@@ -1639,9 +1561,9 @@ cudaError_t launch_inverse_upper(bool tf32, const TcBatch& b, int max_clusters, 
 
 cudaError_t launch_upper(bool tf32, const TcBatch& b, int grid, cudaStream_t s) {
   if (tf32)
-    trsm_tc_kernel<true, false, true><<<grid, THREADS, Cfg<true>::SMEM, s>>>(b);
+    trsm_tc_kernel<true, true><<<grid, THREADS, Cfg<true>::SMEM, s>>>(b);
   else
-    trsm_tc_kernel<false, false, true><<<grid, THREADS, Cfg<false>::SMEM, s>>>(b);
+    trsm_tc_kernel<false, true><<<grid, THREADS, Cfg<false>::SMEM, s>>>(b);
   return cudaGetLastError();
 }
 

@@ -18,7 +18,7 @@ enum Split : int { SPLIT_BF16 = 0, SPLIT_TF32 = 1, SPLIT_F16 = 2 };
 enum TileMode : int {
   TILES_AUTO = 0,            // the measured fastest for the split (resolved by create)
   TILES_SINGLE = 1,          // every tile on its own CTA
-  TILES_PAIR_MULTICAST = 2,  // panels 2u, 2u+1 on a 2-CTA cluster, shared X~ loads by TMA multicast
+                             // (2 is not a mode)
   TILES_PAIR_MMA = 3,        // panels 2u, 2u+1: one M = 256 product on a 2-CTA cluster (cta_group::2)
   TILES_INVERSE = 4,         // L^-1 formed at set-up; a block is the triangular product L^-1 X, row-panel
                              // pairs as M = 256 products on 2-CTA clusters, no dependency between tiles

@@ -485,6 +485,8 @@ static cudaError_t build_inverse(TcState* t, const double* Aop, cudaStream_t s, 
 cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_pad, int bs, int num_sms,
                    bool center, DevStatus* st, cudaStream_t s, int64_t* launches, int strip_group, TileMode mode) {
   *out = nullptr;
+  if (mode != TILES_AUTO && mode != TILES_SINGLE && mode != TILES_PAIR_MMA && mode != TILES_INVERSE)
+    return cudaErrorInvalidValue;
   if (split == SPLIT_F16 && mode != TILES_AUTO && mode != TILES_INVERSE) return cudaErrorInvalidValue;
   TcState* t = new TcState;
   t->tf32 = (split == SPLIT_TF32);

@@ -34,13 +34,13 @@ def _case(n, p, k, h, sigma2=1.0, m=64, seed=11, c0=0):
 
 @pytest.fixture(scope="module")
 def small_study():
-    """n = 1000, p = 4, h = 0.6: the small FP64-dosage workload (first 2000 SNPs here)."""
-    return _case(1000, 4, 2000, 0.6, m=2000)
+    """n = 1000, p = 4, h = 0.6: the small FP64-dosage workload, all of its m = 10,000 SNPs."""
+    return _case(1000, 4, 2000, 0.6, m=10000)
 
 
 def test_fp64_dosages_full_parity(small_study):
     s, X, L, (r, se, st) = small_study
-    with gw.GLS(s["Phi"], s["XL"], s["y"], s["h"], s["sigma2"], bs=4096) as g:
+    with gw.GLS(s["Phi"], s["XL"], s["y"], s["h"], s["sigma2"], bs=X.shape[1]) as g:
         b, se_g, st_g = g.solve_block_f64(X.astype(np.float64))
     e = compare(b, se_g, st_g, r, se, st)
     assert e["b_norm"] <= TOL64 and e["se_rel"] <= TOL64, e
@@ -125,7 +125,7 @@ def test_device_tensors_async(small_study):
     import torch
     s, X, L, (r, se, st) = small_study
     Xd = torch.from_numpy(np.ascontiguousarray(X.T)).cuda().T  # n x m, column-major on the device
-    with gw.GLS(s["Phi"], s["XL"], s["y"], s["h"], s["sigma2"], bs=2000) as g:
+    with gw.GLS(s["Phi"], s["XL"], s["y"], s["h"], s["sigma2"], bs=X.shape[1]) as g:
         b, se_g, st_g = g.solve_block(Xd)
         g.synchronize()
         e = compare(b.cpu().numpy(), se_g.cpu().numpy(), st_g.cpu().numpy(), r, se, st)
@@ -147,7 +147,7 @@ SPLITS = ("bf16x3", "tf32x3", "f16x2")
 # how the tensor-core solve's tiles map onto SMs: one per SM, row-panel pairs on
 # a 2-SM cluster with shared loads, row-panel pairs as one 256-row product (the
 # substitution), and the product with L^-1 formed at set-up
-TILES = ("single", "pair_multicast", "pair_mma", "inverse")
+TILES = ("single", "pair_mma", "inverse")
 # f16x2 exists in the inverse form only
 SPLIT_TILES = [(p, t) for p in SPLITS for t in TILES if p != "f16x2" or t == "inverse"]
 FULL_CASES = [("fp64", "auto")] + [(p, t) for p in SPLITS for t in ("auto",) + TILES
@@ -287,7 +287,7 @@ def test_several_phenotypes_device_outputs_and_limits():
         gw.GLS(s["Phi"], s["XL"], _phenotypes(s, 14), 0.5, 1.0, bs=64)
 
 
-@pytest.mark.parametrize("tiles", ("single", "pair_multicast", "pair_mma"))
+@pytest.mark.parametrize("tiles", ("single", "pair_mma"))
 def test_f16x2_needs_the_inverse_form(small_study, tiles):
     s, *_ = small_study
     with pytest.raises(gw.GwasError):

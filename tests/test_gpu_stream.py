@@ -6,7 +6,9 @@ import numpy as np
 import pytest
 
 import gwas_synth
+import oracle
 import paper_1302_4332_b300 as gw
+from oracle.metrics import compare
 
 pytestmark = pytest.mark.gpu
 
@@ -33,23 +35,45 @@ def dosage_file(tmp_path_factory):
     return str(path), n, m, ld, header, X
 
 
+TOL = {"fp64": 1e-10, "bf16x3": 1e-5, "f16x2": 1e-5}
+
+
+@pytest.fixture(scope="module")
+def oracle_results(dosage_file):
+    """The FP64 oracle over every column of the file (b, se, status)."""
+    path, n, m, ld, header, X = dosage_file
+    s = gwas_synth.study(n, 4, 2000, 0.6, seed=40)
+    L = oracle.potrf(oracle.form_m(s["Phi"], 0.6, 1.0))
+    r, se, _, st = oracle.gls(L, s["XL"], s["y"], X)
+    return r, se, st
+
+
+def _check_oracle(b, se, st, ref, cols, prec):
+    """Columns `cols` of the file against the oracle; b, se, st hold those columns in order."""
+    r, se_o, st_o = ref
+    e = compare(b, se, st, r[:, cols], se_o[:, cols], st_o[cols])
+    assert e["b_norm"] <= TOL[prec] and e["se_rel"] <= TOL[prec], (prec, e)
+
+
 @pytest.mark.parametrize("prec", ["fp64", "bf16x3"])
-def test_solve_file_matches_blocks_and_resumes(dosage_file, prec):
+def test_solve_file_matches_blocks_and_resumes(dosage_file, oracle_results, prec):
     path, n, m, ld, header, X = dosage_file
     s = gwas_synth.study(n, 4, 2000, 0.6, seed=40)
     with gw.GLS(s["Phi"], s["XL"], s["y"], 0.6, 1.0, precision=prec, bs=512) as g:
         b, se, st = g.solve_file(path, m, ldx=ld, header_bytes=header)
+        _check_oracle(b, se, st, oracle_results, np.arange(m), prec)  # every column, first and last of each block
         ref = [g.solve_block(X[:, c0:c0 + 512]) for c0 in range(0, m, 512)]
         b_ref = np.concatenate([r[0] for r in ref], axis=1)
         st_ref = np.concatenate([r[2] for r in ref])
         assert np.array_equal(b, b_ref) and np.array_equal(st, st_ref)
         # resume from a column cursor
         b2, se2, st2 = g.solve_file(path, m - 1100, ldx=ld, col0=1100, header_bytes=header)
+        _check_oracle(b2, se2, st2, oracle_results, np.arange(1100, m), prec)
         assert np.array_equal(b2, b_ref[:, 1100:]) and np.array_equal(se2, se[:, 1100:])
 
 
 @pytest.mark.parametrize("prec", ["fp64", "f16x2"])
-def test_solve_file_out_writes_results_and_resumes(dosage_file, tmp_path, prec):
+def test_solve_file_out_writes_results_and_resumes(dosage_file, oracle_results, tmp_path, prec):
     """Disk to disk: the result file holds exactly what the in-memory stream
     returns; a run resumed from a checkpoint recomputes what follows it and
     ends with the same file."""
@@ -62,6 +86,7 @@ def test_solve_file_out_writes_results_and_resumes(dosage_file, tmp_path, prec):
         assert done == m - 300
         head, b2, se2, st2 = gw.read_results(out)
         assert head == dict(p=4, n=n, col0=300, m=m - 300, record_bytes=72, precision=gw.PRECISIONS[prec])
+        _check_oracle(b2, se2, st2, oracle_results, np.arange(300, m), prec)
         assert np.array_equal(b, b2) and np.array_equal(se, se2) and np.array_equal(st, st2)
         full = open(out, "rb").read()
         # an interrupted run: the checkpoint says 2 blocks, the records after them are garbage
@@ -74,6 +99,8 @@ def test_solve_file_out_writes_results_and_resumes(dosage_file, tmp_path, prec):
             f.write(b"\xee" * (72 * 500))
         assert g.solve_file_out(path, m - 300, out, ldx=ld, col0=300, header_bytes=header, resume=True) == m - 300
         assert open(out, "rb").read() == full
+        _, b3, se3, st3 = gw.read_results(out)  # the resumed range against the oracle as well
+        _check_oracle(b3[:, 256:], se3[:, 256:], st3[256:], oracle_results, np.arange(300 + 256, m), prec)
         # a checkpoint of another run is refused
         with pytest.raises(gw.GwasError) as e:
             g.solve_file_out(path, m - 301, out, ldx=ld, col0=300, header_bytes=header, resume=True)
