@@ -17,6 +17,8 @@
 // sums of x^ against [X^_L | y^] and itself, exactly like the forward sums.
 // The y-gradient sums over SNPs: sum_i c_i W a_i = X^_L (sum_i c_i v_T,i)
 // + sum_i c_i v_p,i x^_i,  c_i = 2 b_p / s.
+#include <cuda_fp16.h>
+
 #include "gwas_internal.cuh"
 #include "tc_ptx.cuh"
 
@@ -123,23 +125,126 @@ __global__ void __launch_bounds__(256) adjoint_snp_kernel(const double* __restri
   adjoint_store<QM>(af, ah, sc, GH, q, col, h, sigma2, chi2, dh, wv);
 }
 
+// The split precisions' adjoint from the exact products C = A x' of
+// adjoint_exact.cu (A: three slabs of RS rows, slab k = slice k of W's rows,
+// then slices k and k + 3 of the ne = 2(q+1) appended rows [X^_L | y^ |
+// W X^_L | W y^]^T): one warp per SNP column.  Over W's rows r < n, with the
+// integers x'_r and c_k = C[k RS + r]:
+//   P_k = sum_r x'_r c_k  (int64, exact),  S_BR = x'^T W x' = (P_1 + 2^-10 P_2 + 2^-20 P_3) / s_W,
+//   ||x^'||^2 = sum_r u_r^2 / s_W^2,  u_r = c_1 + 2^-10 c_2 + 2^-20 c_3  (exact; the sum of squares too
+//   for dosage-sized values -- its relative error reaches the gradient amplified by the cancellation
+//   in ||W a||^2, so an FP32 sum would not do),
+// and appended row e gives sum_k 2^-10k C[...] / s_e (six slices), the
+// forward sums x'^T [X^_L | y^] and the transpose sums x^'^T [X^_L | y^].
+// Then the p x p adjoint as in the FP64 path.
+template <int QM>
+__global__ void __launch_bounds__(256) exact_adjoint_kernel(
+    const int32_t* __restrict__ C, int64_t ldc, int RS, const __half* __restrict__ xc, int64_t ldx, int n, int n_pad,
+    int ne, const double* __restrict__ inv_scale, const SolveConsts* __restrict__ sc, const double* __restrict__ GH,
+    int q, int ncols, double h, double sigma2, const int* __restrict__ xmax, double* __restrict__ chi2,
+    double* __restrict__ dh, double* __restrict__ wv) {
+  const int lane = threadIdx.x & 31;
+  const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (col >= ncols) return;
+  const bool small44 = 512LL * (*xmax) * n_pad <= (1LL << 24);
+  const int32_t* cc = C + (int64_t)col * ldc;
+  const __half* x = xc + (int64_t)col * ldx;
+  // P_k: exact in int64 (|x'_r c_k| < 2^39).  ||x^'||^2 = 2^-40 sum_r T_r^2 with
+  // T_r = 2^20 c_1 + 2^10 c_2 + c_3 (an integer): when |T_r| < 2^44 (small44:
+  // 512 * max|x'| * n_pad <= 2^24, e.g. dosages and n <= 16,384), exact as
+  // T = 2^22 t_h + t_l, T^2 = 2^44 t_h^2 + 2^23 t_h t_l + t_l^2, each part an
+  // int64 sum; otherwise T_r^2 summed in FP64.
+  long long p1 = 0, p2 = 0, p3 = 0, shh = 0, shl = 0, sll = 0;
+  double qq = 0.0;
+#pragma unroll 4
+  for (int r = lane; r < n; r += 32) {
+    const int xi = __half2int_rn(x[r]);
+    const int a1 = __ldcs(cc + r), a2 = __ldcs(cc + RS + r), a3 = __ldcs(cc + 2 * RS + r);
+    p1 += (long long)xi * a1;
+    p2 += (long long)xi * a2;
+    p3 += (long long)xi * a3;
+    const long long T = ((long long)a1 << 20) + ((long long)a2 << 10) + a3;
+    if (small44) {  // |t_h| <= 2^23, 0 <= t_l < 2^22: 32 x 32 -> 64-bit products
+      const int th = (int)(T >> 22), tl = (int)(T & 0x3FFFFF);
+      shh += (long long)th * th;
+      shl += (long long)th * tl;
+      sll += (long long)tl * tl;
+    } else {
+      const double u = (double)T;
+      qq = fma(u, u, qq);
+    }
+  }
+#pragma unroll
+  for (int o = 16; o; o >>= 1) {
+    p1 += __shfl_xor_sync(0xffffffffu, p1, o);
+    p2 += __shfl_xor_sync(0xffffffffu, p2, o);
+    p3 += __shfl_xor_sync(0xffffffffu, p3, o);
+    if (small44) {
+      shh += __shfl_xor_sync(0xffffffffu, shh, o);
+      shl += __shfl_xor_sync(0xffffffffu, shl, o);
+      sll += __shfl_xor_sync(0xffffffffu, sll, o);
+    } else {
+      qq += __shfl_xor_sync(0xffffffffu, qq, o);
+    }
+  }
+  if (small44) qq = fma((double)shh, 0x1p44, fma((double)shl, 0x1p23, (double)sll));
+  qq *= 0x1p-40;
+  // appended row `lane` (< ne): six slices, the smallest first
+  double ev = 0.0;
+  if (lane < ne) {
+    const int r0 = n_pad + lane, r1 = n_pad + ne + lane;
+    double v = 0.0;
+    v = fma((double)cc[2 * RS + r1], 0x1p-50, v);
+    v = fma((double)cc[RS + r1], 0x1p-40, v);
+    v = fma((double)cc[r1], 0x1p-30, v);
+    v = fma((double)cc[2 * RS + r0], 0x1p-20, v);
+    v = fma((double)cc[RS + r0], 0x1p-10, v);
+    ev = ((double)cc[r0] + v) * inv_scale[1 + lane];
+  }
+  double evs[2 * (QM + 1)];
+#pragma unroll
+  for (int e = 0; e < 2 * (QM + 1); ++e) evs[e] = __shfl_sync(0xffffffffu, ev, e < 32 ? e : 0);
+  if (lane != 0) return;
+  const double is = inv_scale[0];
+  double af[QM + 2], ah[QM + 2];
+#pragma unroll
+  for (int a = 0; a < QM + 2; ++a) af[a] = ah[a] = 0.0;
+  for (int a = 0; a <= q; ++a) {
+    af[a] = evs[a];          // x'^T X^_L, x'^T y^
+    ah[a] = evs[q + 1 + a];  // x^'^T X^_L, x^'^T y^
+  }
+  af[QM + 1] = fma((double)p3, 0x1p-20, fma((double)p2, 0x1p-10, (double)p1)) * is;
+  ah[QM + 1] = qq * is * is;
+  adjoint_store<QM>(af, ah, sc, GH, q, col, h, sigma2, chi2, dh, wv);
+}
+
 // One block: dh_sum += sum_i dh_i and uT[a] = sum_i w_i[a] (a < q), in a fixed order.
-__global__ void adjoint_sum_kernel(const double* __restrict__ dh, const double* __restrict__ wv, int q, int ncols,
-                                   double* __restrict__ dh_accum, double* __restrict__ uT) {
-  __shared__ double red[QMAX + 1][32];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;  // warp a < q: uT[a]; warp q: dh
-  if (warp > q) return;
-  double s = 0.0;
-  for (int i = lane; i < ncols; i += 32) s += (warp == q) ? dh[i] : wv[(int64_t)i * (q + 1) + warp];
-  red[warp][lane] = s;
-  __syncwarp();
-  if (lane == 0) {
-    double t = 0.0;
-    for (int l = 0; l < 32; ++l) t += red[warp][l];
-    if (warp == q)
-      *dh_accum += t;
+// Block a (< q + 1): quantity a over the SNPs -- uT[a] for a < q, the block's
+// d chi2/dh (added to *dh_accum) for a = q -- 256 threads each over a strided
+// slice, then a fixed tree in shared memory (deterministic).
+__global__ void __launch_bounds__(256) adjoint_sum_kernel(const double* __restrict__ dh, const double* __restrict__ wv,
+                                                          int q, int ncols, double* __restrict__ dh_accum,
+                                                          double* __restrict__ uT) {
+  __shared__ double red[256];
+  const int a = blockIdx.x;
+  double s0 = 0.0, s1 = 0.0;
+  int i = threadIdx.x;
+  for (; i + 256 < ncols; i += 512) {  // two loads in flight per thread
+    s0 += (a == q) ? dh[i] : wv[(int64_t)i * (q + 1) + a];
+    s1 += (a == q) ? dh[i + 256] : wv[(int64_t)(i + 256) * (q + 1) + a];
+  }
+  if (i < ncols) s0 += (a == q) ? dh[i] : wv[(int64_t)i * (q + 1) + a];
+  red[threadIdx.x] = s0 + s1;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (threadIdx.x < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    if (a == q)
+      *dh_accum += red[0];
     else
-      uT[warp] = t;
+      uT[a] = red[0];
   }
 }
 
@@ -394,12 +499,35 @@ cudaError_t launch_adjoint(const double* Xt, const double* Xh, int64_t ldt, int 
                                                   wv);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  adjoint_sum_kernel<<<1, 32 * (q + 1), 0, s>>>(dh, wv, q, ncols, dh_accum, uT);
+  adjoint_sum_kernel<<<q + 1, 256, 0, s>>>(dh, wv, q, ncols, dh_accum, uT);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int nchunks = adjoint_dy_chunks(ncols);
   adjoint_dy_part_kernel<<<dim3((n + 255) / 256, nchunks), 256, 0, s>>>(Xh, ldt, wv, q, n, ncols, dy_part);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   adjoint_dy_sum_kernel<<<(n + 255) / 256, 256, 0, s>>>(Wh, ldw, uT, q, n, nchunks, dy_part, dy_accum);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_exact_adjoint_sums(const int32_t* C, int64_t ldc, int RS, const __half* xc, int64_t ldx, int n,
+                                      int n_pad, int ne, const double* inv_scale, const SolveConsts* sc,
+                                      const double* GH, int q, int ncols, double h, double sigma2, const int* xmax,
+                                      double* chi2, double* dh, double* wv, double* dh_accum, double* uT,
+                                      cudaStream_t s) {
+  if (ncols <= 0) return cudaSuccess;
+  if (ne != 2 * (q + 1) || ne > 32) return cudaErrorInvalidValue;
+  const int grid = (ncols + 7) / 8;
+  if (q <= 3)
+    exact_adjoint_kernel<3><<<grid, 256, 0, s>>>(C, ldc, RS, xc, ldx, n, n_pad, ne, inv_scale, sc, GH, q, ncols, h,
+                                                 sigma2, xmax, chi2, dh, wv);
+  else if (q <= 7)
+    exact_adjoint_kernel<7><<<grid, 256, 0, s>>>(C, ldc, RS, xc, ldx, n, n_pad, ne, inv_scale, sc, GH, q, ncols, h,
+                                                 sigma2, xmax, chi2, dh, wv);
+  else
+    exact_adjoint_kernel<QMAX><<<grid, 256, 0, s>>>(C, ldc, RS, xc, ldx, n, n_pad, ne, inv_scale, sc, GH, q, ncols,
+                                                    h, sigma2, xmax, chi2, dh, wv);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  adjoint_sum_kernel<<<q + 1, 256, 0, s>>>(dh, wv, q, ncols, dh_accum, uT);
   return cudaGetLastError();
 }
 
@@ -420,7 +548,7 @@ cudaError_t launch_adjoint_f32(const CUtensorMap* xtmap, const CUtensorMap* xhma
         *xtmap, *xhmap, rows, W32, Wh32, G, GH, sc, shift, q, ncols, h, sigma2, chi2, dh, wv, st);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  adjoint_sum_kernel<<<1, 32 * (q + 1), 0, s>>>(dh, wv, q, ncols, dh_accum, uT);
+  adjoint_sum_kernel<<<q + 1, 256, 0, s>>>(dh, wv, q, ncols, dh_accum, uT);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   const int nchunks = adjoint_dy_chunks(ncols);
   adjoint_dy_part_f32_kernel<<<dim3((n + 255) / 256, nchunks), 256, 0, s>>>(Xh32, ldt, Wh, shift, wv, q, n, ncols,

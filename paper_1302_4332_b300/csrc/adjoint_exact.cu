@@ -1,0 +1,729 @@
+// a11 in the split precisions: the adjoint from exact integer products on the
+// tensor cores (the M^-1 form).
+//
+// With W = M^-1 (symmetric), X^_L = W X_L, y^ = W y and x' = x - c 1 (the SNP
+// column shifted by the integer nearest its mean when X_L[:, 0] is the
+// intercept: [X_L | x'] spans the same space, so the Wald statistic and its
+// gradient do not change), every per-SNP input of the adjoint is a product
+// of a fixed FP64 matrix with the small integers x':
+//   forward sums    x~^T X~_L = x'^T X^_L,  x~^T y~ = x'^T y^,  x~^T x~ = x'^T (W x'),
+//   transpose sums  x^^T X^_L = x'^T (W X^_L),  x^^T y^ = x'^T (W y^),  ||x^||^2 = ||W x'||^2,
+// (x~ = L^-1 x', x^ = L^-T x~ = W x').  So one product per block, A x' with
+//   A = [ W ; X^_L^T ; y^T ; (W X^_L)^T ; (W y^)^T ]   ((n_pad + 2(q+1)) x n_pad),
+// gives all of them; the adjoint arithmetic (adjoint.cu) stays FP64.
+//
+// Exact slices.  Each row of A, scaled by a power of two s (one s for all of
+// W's rows, one per appended row) so that its largest entry is at most 512 in
+// magnitude, is written as a_1 + a_2 2^-10 + a_3 2^-20 + ..., every a_k an
+// integer in [-512, 512] (exact in FP16).  W's rows keep three slices (30
+// bits), the appended rows six: their dot products with a centred x' can
+// cancel, and three slices left ~1e-7 relative error in the gradient where
+// six leave ~4e-9 (a CPU emulation of this scheme at n = 300..3000).  A slice
+// times the integer dosages, accumulated by the tensor cores in FP32, is
+// exact while every partial sum stays below 2^24: at most 256 / max|x'|
+// K-blocks of 128 go into one TMEM partial (every K-block of a dosage block
+// up to n = 16,384 with |x'| <= 2), and the epilogue adds the partials as
+// int32.  The products leave as int32 and are combined per SNP in FP64 and
+// int64 (adjoint.cu), so the only error left is the slices' representation.
+//
+// Layout: A holds three slabs of RS rows (RS = 256 ceil((P + 1) / 2)), slab k
+// = slice k of W's n_pad rows, then slice k of the 2(q+1) appended rows, then
+// their slice k + 3, then zero rows; FP16, row-major (K contiguous).  The
+// product C = A x' is 3 RS x ncols int32, column-major (leading dimension 3 RS).
+#include <cuda.h>
+#include <cuda_fp16.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "gwas_internal.cuh"
+#include "tc_ptx.cuh"
+#include "trsm_tc_kernels.cuh"
+
+namespace gwas {
+
+using tc::EPI_COLS;
+using tc::EPI_WARPS;
+using tc::THREADS;
+using tc::TN;
+using tc::TRING;
+
+namespace ex3 {
+constexpr int KCH = 32;                              // FP16 K per stage: one 64-byte swizzle row
+constexpr int KMMA = 16;                             // K per tcgen05.mma (kind::f16)
+constexpr int CPB = TB / KCH;                        // stages per 128-wide K-block
+constexpr int A_BYTES = TB * 64;                     // this CTA's 128 rows of a slice: 8 KB
+constexpr int B_BYTES = (TN / 2) * 64;               // this CTA's 128 SNP columns: 8 KB
+constexpr int STAGE_BYTES = A_BYTES + B_BYTES;       // 16 KB
+constexpr int STAGES = 10;
+constexpr int CHUNK_BYTES = 2048;                    // epilogue store chunk: 32 rows x 16 int32
+constexpr int ST_COLS = 16;
+constexpr int STG_OFF = STAGES * STAGE_BYTES;
+constexpr int BAR_OFF = STG_OFF + EPI_WARPS * 2 * CHUNK_BYTES;
+constexpr int NBARS = 2 * STAGES + 4 + 3 * TRING + 1;
+constexpr int SMEM = 1024 + BAR_OFF + NBARS * 8 + TRING * 4 + 16;
+static_assert(SMEM <= 232448, "shared memory per CTA");
+constexpr int SLABS = 3;
+
+struct Params {
+  CUtensorMap A;  // the stacked slices: dims {n_pad, 3 RS}, box {32, 128}, 64-byte swizzle, FP16
+  CUtensorMap B;  // x' (FP16): dims {n_pad, bs}, box {32, 128}, 64-byte swizzle
+  CUtensorMap C;  // the int32 product: dims {3 RS, bs}, box {32, 16}
+  int P;          // K-blocks of 128 (n_pad / 128)
+  int U;          // row-panel pairs per slab (RS / 256)
+  int RS;         // rows per slab
+  int Cs;         // 256-column strips of the block
+  int ntiles;     // work units: SLABS * U * Cs
+  const int* xmax;         // largest |x'| of the block (set by the cast)
+  unsigned int* counter;   // unit counter (zeroed by the cast)
+  DevStatus* st;
+};
+
+// K-blocks per TMEM partial so that every partial sum is an integer below
+// 2^24 in magnitude: 512 * xmax * 128 * G <= 2^24.
+__device__ __forceinline__ int partial_span(int xmax, int P) {
+  if (xmax <= 0) return P;
+  const int g = 256 / xmax;
+  return g < 1 ? 1 : (g > P ? P : g);
+}
+
+// The int32 totals hold 512 * xmax * n_pad at most: beyond 2^31 the block is refused.
+__device__ __forceinline__ bool in_range(int xmax, int P) {
+  return 512LL * xmax * (long long)TB * P < (1LL << 31);
+}
+
+__global__ void __launch_bounds__(THREADS, 1) exact_product_kernel(const __grid_constant__ Params b) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + BAR_OFF);
+  uint64_t* full = bars;                 // CTA 0: both CTAs' loads of a stage
+  uint64_t* empty = full + STAGES;       // CTA 0's commit: the stage's MMAs are done
+  uint64_t* part_full = empty + STAGES;  // CTA 0's commit: a partial is complete
+  uint64_t* part_empty = part_full + 2;  // CTA 0: both CTAs' epilogues are done with a partial
+  uint64_t* tile_full = part_empty + 2;
+  uint64_t* tile_empty = tile_full + TRING;
+  uint64_t* peer_free = tile_empty + TRING;
+  uint64_t* drain = peer_free + TRING;
+  int* tile_ring = reinterpret_cast<int*>(drain + 1);
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(tile_ring + TRING);
+
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  DevStatus* st = b.st;
+  const uint32_t rank = ptx::cluster_ctarank();
+  const bool leader = rank == 0;
+  constexpr uint16_t BOTH = 3;
+  auto lead_addr = [&](uint64_t* bar) -> uint32_t { return leader ? ptx::smem_u32(bar) : ptx::peer_addr(bar, 0); };
+  auto count_lead = [&](uint64_t* bar) {
+    if (leader)
+      ptx::mbar_arrive(bar);
+    else
+      ptx::mbar_arrive_peer_count(ptx::peer_addr(bar, 0));
+  };
+  const int xmax = *b.xmax;  // written by the cast, an ordinary launch before this one
+  const bool ok_range = in_range(xmax, b.P);
+  if (!ok_range && blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&st->err, DEV_OK, DEV_ERR_RANGE);
+  const int ntiles = ok_range ? b.ntiles : 0;
+  const int G = partial_span(xmax, b.P);
+  const int nparts = (b.P + G - 1) / G;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      ptx::mbar_init(&full[s], 2);   // one arrival from each CTA's producer (+ the bytes of both)
+      ptx::mbar_init(&empty[s], 1);  // CTA 0's commit
+    }
+    for (int a = 0; a < 2; ++a) {
+      ptx::mbar_init(&part_full[a], 1);
+      ptx::mbar_init(&part_empty[a], 2 * EPI_WARPS);
+    }
+    for (int i = 0; i < TRING; ++i) {
+      ptx::mbar_init(&tile_full[i], 1);
+      ptx::mbar_init(&tile_empty[i], 1 + EPI_WARPS);
+      ptx::mbar_init(&peer_free[i], 1);
+    }
+    ptx::mbar_init(drain, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    ptx::prefetch_tensormap(&b.A);
+    ptx::prefetch_tensormap(&b.B);
+    ptx::prefetch_tensormap(&b.C);
+  }
+  if (warp == 2) {
+    ptx::tmem_alloc_pair(tmem_slot, 2 * TN);
+    ptx::tmem_relinquish_pair();
+  }
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  ptx::cluster_sync();  // both CTAs' barriers and tensor memory exist before any remote access
+  const uint32_t tmem_base = *tmem_slot;
+
+  auto decode = [&](int t, int& slab, int& u, int& c) {
+    const int per = b.U * b.Cs;
+    slab = t / per;
+    const int rem = t - slab * per;
+    u = rem / b.Cs;
+    c = rem - u * b.Cs;
+  };
+
+  if (warp == 0) {
+    // ------------------------------------------------ scheduler + TMA producer
+    if (lane == 0) {
+      uint32_t cnt = 0;
+      for (int it = 0;; ++it) {
+        const int slot = it % TRING;
+        const uint32_t use = it / TRING;
+        if (!ptx::mbar_wait(&tile_empty[slot], (use & 1) ^ 1, st)) break;
+        int t;
+        if (leader) {
+          if (!ptx::mbar_wait(&peer_free[slot], use & 1, st)) break;
+          t = (ptx::aborting(st) || ntiles == 0) ? ntiles : (int)atomicAdd(b.counter, 1u);
+          if (t > ntiles) t = ntiles;
+          tile_ring[slot] = t;
+          ptx::st_peer_u32(ptx::peer_addr(&tile_ring[slot], 1), (uint32_t)t);
+          ptx::mbar_arrive(&tile_full[slot]);
+          ptx::mbar_arrive_peer(ptx::peer_addr(&tile_full[slot], 1));
+        } else {
+          ptx::mbar_arrive_peer(ptx::peer_addr(&peer_free[slot], 0));
+          if (!ptx::mbar_wait_s<true>(&tile_full[slot], use & 1, st)) break;
+          t = tile_ring[slot];
+        }
+        if (t >= ntiles) break;
+        int slab, u, c;
+        decode(t, slab, u, c);
+        const int arow = slab * b.RS + (2 * u + (int)rank) * TB;  // this CTA's 128 rows of A
+        const int ycol = c * TN + (int)rank * (TN / 2);           // this CTA's 128 SNP columns
+        bool ok = true;
+        for (int j = 0; j < b.P && ok; ++j) {
+          for (int h = 0; h < CPB; ++h, ++cnt) {
+            const int s = cnt % STAGES;
+            const uint32_t r = cnt / STAGES;
+            if (!ptx::mbar_wait(&empty[s], (r & 1) ^ 1, st)) { ok = false; break; }
+            uint8_t* sb = smem + s * STAGE_BYTES;
+            const int kx = j * TB + h * KCH;
+            const uint32_t fb = lead_addr(&full[s]);
+            if (leader)
+              ptx::mbar_arrive_expect_tx(&full[s], 2 * STAGE_BYTES);
+            else
+              ptx::mbar_arrive_peer_count(fb);
+            ptx::tma_load_2d_pair(sb, &b.A, fb, kx, arow);
+            ptx::tma_load_2d_pair(sb + A_BYTES, &b.B, fb, kx, ycol);
+          }
+        }
+        if (!ok) break;
+      }
+    }
+  } else if (warp == 1) {
+    // ------------------------------------------------- MMA issuer (CTA 0 only)
+    if (lane == 0) {
+      constexpr uint32_t idesc = ptx::idesc_f32acc_f16(2 * TB, TN);
+      uint32_t cnt = 0, kb = 0;
+      for (int it = 0;; ++it) {
+        const int slot = it % TRING;
+        const uint32_t use = it / TRING;
+        if (!ptx::mbar_wait_s<true>(&tile_full[slot], use & 1, st)) break;
+        const int t = tile_ring[slot];
+        ptx::mbar_arrive(&tile_empty[slot]);
+        if (t >= ntiles) break;
+        if (!leader) continue;
+        bool ok = true;
+        int a = 0;
+        uint32_t d = 0, accumulate = 0;
+        for (int j = 0; j < b.P && ok; ++j) {
+          if (j % G == 0) {  // a fresh partial every G K-blocks, alternating between the two buffers
+            a = kb & 1;
+            if (!ptx::mbar_wait(&part_empty[a], ((kb >> 1) & 1) ^ 1, st)) { ok = false; break; }
+            ++kb;
+            ptx::tc_fence_after();
+            d = tmem_base + a * TN;
+            accumulate = 0;
+          }
+          for (int h = 0; h < CPB; ++h, ++cnt) {
+            const int s = cnt % STAGES;
+            const uint32_t r = cnt / STAGES;
+            if (!ptx::mbar_wait(&full[s], r & 1, st)) { ok = false; break; }
+            ptx::tc_fence_after();
+            const uint32_t base = ptx::smem_u32(smem + s * STAGE_BYTES);
+#pragma unroll
+            for (int kk = 0; kk < KCH / KMMA; ++kk) {
+              const uint32_t off = kk * KMMA * 2;
+              ptx::mma_pair<false>(d, ptx::sdesc_k64(base + off), ptx::sdesc_k64(base + A_BYTES + off), idesc,
+                                   accumulate);
+              accumulate = 1;
+            }
+            ptx::mma_commit_pair(&empty[s], BOTH);
+          }
+          if (!ok) break;
+          if (j % G == G - 1 || j == b.P - 1) ptx::mma_commit_pair(&part_full[a], BOTH);
+        }
+        if (!ok) break;
+      }
+    }
+  } else if (warp >= 4) {
+    // ----------------------------------------------------------------- epilogue
+    constexpr int NT = 32 * EPI_WARPS;
+    const int e = warp - 4;
+    const int lq = e & 3;     // TMEM lanes (rows) 32 lq ..
+    const int chalf = e >> 2;  // SNP columns chalf * 128 ..
+    uint8_t* stg = smem + STG_OFF + e * 2 * CHUNK_BYTES;
+    uint32_t kb = 0, gq = 0;
+    int master[EPI_COLS];
+    for (int it = 0;; ++it) {
+      const int slot = it % TRING;
+      const uint32_t use = it / TRING;
+      if (!ptx::group_and(1, NT, ptx::mbar_wait_s<true>(&tile_full[slot], use & 1, st))) break;
+      const int t = tile_ring[slot];
+      ptx::named_bar(1, NT);
+      if (lane == 0) ptx::mbar_arrive(&tile_empty[slot]);
+      if (t >= ntiles) break;
+      int slab, u, c;
+      decode(t, slab, u, c);
+#pragma unroll
+      for (int i = 0; i < EPI_COLS; ++i) master[i] = 0;
+      bool ok = true;
+      for (int pp = 0; pp < nparts && ok; ++pp) {
+        const int a = kb & 1;
+        if (!ptx::group_and(1, NT, ptx::mbar_wait(&part_full[a], (kb >> 1) & 1, st))) { ok = false; break; }
+        ptx::tc_fence_after();
+        const uint32_t tb = tmem_base + (static_cast<uint32_t>(32 * lq) << 16) + a * TN + chalf * EPI_COLS;
+#pragma unroll
+        for (int ch = 0; ch < EPI_COLS / 16; ++ch) {
+          uint32_t v[16];
+          ptx::tmem_ld_32x32b_x16(tb + ch * 16, v);
+          ptx::tmem_ld_wait();
+#pragma unroll
+          for (int i = 0; i < 16; ++i) master[ch * 16 + i] += __float2int_rn(__uint_as_float(v[i]));  // exact
+        }
+        ptx::tc_fence_before();
+        __syncwarp();
+        if (lane == 0) count_lead(&part_empty[a]);
+        ++kb;
+      }
+      if (!ok) break;
+      // the tile's int32 products to HBM through TMA stores of 2 KB chunks
+      const int r0 = slab * b.RS + (2 * u + (int)rank) * TB + 32 * lq;
+      const int c0 = c * TN + chalf * EPI_COLS;
+#pragma unroll
+      for (int q = 0; q < EPI_COLS / ST_COLS; ++q) {
+        uint8_t* buf = stg + (gq & 1) * CHUNK_BYTES;
+        if (gq >= 2) {
+          if (lane == 0) ptx::bulk_wait_read<1>();
+          __syncwarp();
+        }
+        ++gq;
+#pragma unroll
+        for (int i = 0; i < ST_COLS; ++i) reinterpret_cast<int*>(buf)[i * 32 + lane] = master[q * ST_COLS + i];
+        ptx::fence_proxy_async_shared();
+        __syncwarp();
+        if (lane == 0) {
+          ptx::tma_store_2d(&b.C, buf, r0, c0 + q * ST_COLS);
+          ptx::bulk_commit();
+        }
+      }
+    }
+    if (lane == 0) ptx::bulk_wait_all();  // the last stores have read the staging buffers
+  }
+
+  // ---------------------------------------------------------------- teardown
+  if (warp == 1 && lane == 0 && leader) {
+    ptx::mma_commit_pair(drain, 1);  // every MMA of the pair has completed before TMEM is released
+    const long long t0 = ptx::globaltimer();
+    while (!ptx::mbar_try_wait(drain, 0) && ptx::globaltimer() - t0 < 100000000LL) {
+    }
+  }
+  if (ptx::aborting(st)) {
+    const long long t0 = ptx::globaltimer();
+    while (ptx::globaltimer() - t0 < 2000000LL) {
+    }
+  }
+  ptx::cluster_sync();
+  ptx::tc_fence_before();
+  __syncthreads();
+  ptx::tc_fence_after();
+  if (warp == 2) ptx::tmem_dealloc_pair(tmem_base, 2 * TN);
+}
+}  // namespace ex3
+
+// ----------------------------------------------------------- set-up kernels
+// Largest |value| of each column of a column-major rows x ncols matrix (as the
+// bits of a non-negative double, whose order is the integers').
+__global__ void col_absmax_kernel(const double* __restrict__ X, int64_t ld, int rows, int ncols,
+                                  unsigned long long* __restrict__ out) {
+  const int col = blockIdx.y;
+  if (col >= ncols) return;
+  double m = 0.0;
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x)
+    m = fmax(m, fabs(X[r + (int64_t)col * ld]));
+  for (int o = 16; o; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out + col, (unsigned long long)__double_as_longlong(m));
+}
+
+// Slice k (0-based) of v s: a_0 = rint(v s), a_k = rint(2^10 (remainder after a_0 .. a_{k-1})).
+// Every step is exact in FP64 (a power-of-two scale, an integer subtracted).
+__device__ __forceinline__ double slice_of(double v, double s, int k) {
+  double r = v * s, a = rint(r);
+  for (int i = 0; i < k; ++i) {
+    r = (r - a) * 1024.0;
+    a = rint(r);
+  }
+  return a;
+}
+
+// The stacked slices A (3 slabs of RS rows, row-major, n_pad columns, FP16).
+// Row R of a slab: R < n_pad: W's row R (W symmetric: read as its column, so
+// that the threads of a block read consecutive entries); n_pad <= R < n_pad +
+// 2 ne: appended row e = (R - n_pad) % ne of [X^_L | y^ | W X^_L | W y^] (the
+// columns of Ex, n_pad x ne), slice k for the first ne rows, k + 3 for the
+// next; further rows zero.
+__global__ void slice_rows_kernel(const double* __restrict__ W, const double* __restrict__ Ex, int n_pad, int ne,
+                                  int RS, const double* __restrict__ scale, __half* __restrict__ A) {
+  const int R = blockIdx.y;
+  const int col = blockIdx.x * blockDim.x + threadIdx.x;
+  if (col >= n_pad) return;
+  double v = 0.0, s = 1.0;
+  int k0 = 0;
+  if (R < n_pad) {
+    v = W[col + (int64_t)R * n_pad];
+    s = scale[0];
+  } else if (R < n_pad + 2 * ne) {
+    const int e = (R - n_pad) % ne;
+    k0 = (R - n_pad) / ne * 3;
+    v = Ex[col + (int64_t)e * n_pad];
+    s = scale[1 + e];
+  }
+  for (int k = 0; k < ex3::SLABS; ++k) {
+    const double a = (R < n_pad + 2 * ne) ? slice_of(v, s, k0 + k) : 0.0;
+    A[((int64_t)k * RS + R) * n_pad + col] = __float2half_rn((float)a);  // an integer in [-512, 512]: exact
+  }
+}
+
+// x' = x - c (c the SNP's integer shift, 0 without intercept) as FP16 on rows
+// < n, 0 on rows n .. n_pad - 1; c stored in shift[col]; the largest |x'| of
+// the block into *xmax.  One warp per SNP column; the block's first thread
+// also zeroes the product's unit counter.
+__global__ void cast_exact_kernel(const int8_t* __restrict__ X, int64_t ldx, int n, int n_pad, int ncols, int center,
+                                  int8_t* __restrict__ shift, __half* __restrict__ xc, int* __restrict__ xmax,
+                                  unsigned int* __restrict__ counter) {
+  if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0;
+  const int lane = threadIdx.x & 31;
+  const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (col >= ncols) return;
+  const int8_t* x = X + (int64_t)col * ldx;
+  int c = 0;
+  if (center) {
+    int sum = 0;
+    for (int r = lane; r < n; r += 32) sum += x[r];
+    for (int o = 16; o; o >>= 1) sum += __shfl_xor_sync(0xffffffffu, sum, o);
+    const long long num = 2LL * sum + n, den = 2LL * n;  // round half up of sum / n
+    long long cc = num >= 0 ? num / den : -((-num + den - 1) / den);
+    c = (int)(cc > 127 ? 127 : (cc < -127 ? -127 : cc));
+  }
+  if (lane == 0) shift[col] = (int8_t)c;
+  int m = 0;
+  __half* o = xc + (int64_t)col * n_pad;
+  for (int r = lane; r < n_pad; r += 32) {
+    const int v = r < n ? (int)x[r] - c : 0;
+    m = max(m, abs(v));
+    o[r] = __int2half_rn(v);
+  }
+  for (int k = 16; k; k >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, k));
+  if (lane == 0) atomicMax(xmax, m);
+}
+
+// y-gradient, first half: part[k][r] = sum over SNP chunk k of wp_i x'_ri,
+// wp_i = wv[i p + p - 1] (the weight of the SNP column in W a_i), in
+// double-FP32: wp_i = h_i + l_i (FP32 pieces), x' h_i exactly as the pair
+// (p, fma(x', h_i, -p)) and the running sum as (s, c) with TwoSum steps --
+// about 2^-44 relative, on the FP32 pipes instead of B300's narrow FP64 one.
+constexpr int EX_DY_CHUNK = 128;
+__global__ void __launch_bounds__(256) exact_dy_part_kernel(const __half* __restrict__ xc, int64_t ldc,
+                                                            const double* __restrict__ wv, int p, int n, int ncols,
+                                                            double* __restrict__ part) {
+  __shared__ float wh[EX_DY_CHUNK], wl[EX_DY_CHUNK];
+  const int i0 = blockIdx.y * EX_DY_CHUNK, i1 = min(i0 + EX_DY_CHUNK, ncols);
+  for (int i = threadIdx.x; i < i1 - i0; i += blockDim.x) {
+    const double w = wv[(int64_t)(i0 + i) * p + p - 1];
+    const float h = (float)w;
+    wh[i] = h;
+    wl[i] = (float)(w - (double)h);
+  }
+  __syncthreads();
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n) return;
+  const __half* x = xc + r + (int64_t)i0 * ldc;
+  float sh = 0.f, sl = 0.f;
+#pragma unroll 4
+  for (int i = 0; i < i1 - i0; ++i) {
+    const float xv = __half2float(x[(int64_t)i * ldc]);
+    const float pr = xv * wh[i];
+    const float pe = fmaf(xv, wh[i], -pr);  // exact error of the product
+    const float t = sh + pr;                // TwoSum(sh, pr)
+    const float bv = t - sh;
+    const float err = (sh - (t - bv)) + (pr - bv);
+    sh = t;
+    sl += err + pe + xv * wl[i];
+  }
+  part[(int64_t)blockIdx.y * n + r] = (double)sh + (double)sl;
+}
+
+// z = the chunk sums in order (rows < n; rows n .. n_pad - 1 zero)
+__global__ void exact_dy_z_kernel(const double* __restrict__ part, int nchunks, int n, int n_pad,
+                                  double* __restrict__ z) {
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
+  if (r >= n_pad) return;
+  double s = 0.0;
+  if (r < n)
+    for (int k = 0; k < nchunks; ++k) s += part[(int64_t)k * n + r];
+  z[r] = s;
+}
+
+// dy[r] += sum_c W[r, c] z[c] + sum_a uT[a] X^_L[r, a]   (one warp per row,
+// W symmetric: its row r is its column; 16-byte loads, four running sums)
+__global__ void __launch_bounds__(256) exact_dy_apply_kernel(const double* __restrict__ W, int n_pad, int n,
+                                                             const double* __restrict__ z,
+                                                             const double* __restrict__ What,
+                                                             const double* __restrict__ uT, int q,
+                                                             double* __restrict__ dy) {
+  const int lane = threadIdx.x & 31;
+  const int r = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (r >= n) return;
+  const double2* w = reinterpret_cast<const double2*>(W + (int64_t)r * n_pad);  // n_pad even, rows 16-byte aligned
+  const double2* zz = reinterpret_cast<const double2*>(z);
+  double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+  const int n2 = n_pad / 2;  // z is zero past n
+  int c = lane;
+  for (; c + 96 < n2; c += 128) {  // four 16-byte loads in flight per lane
+    double2 a[4], b[4];
+#pragma unroll
+    for (int k = 0; k < 4; ++k) a[k] = __ldcs(w + c + 32 * k);
+#pragma unroll
+    for (int k = 0; k < 4; ++k) b[k] = zz[c + 32 * k];
+    s0 = fma(a[0].x, b[0].x, s0);
+    s1 = fma(a[0].y, b[0].y, s1);
+    s2 = fma(a[1].x, b[1].x, s2);
+    s3 = fma(a[1].y, b[1].y, s3);
+    s0 = fma(a[2].x, b[2].x, s0);
+    s1 = fma(a[2].y, b[2].y, s1);
+    s2 = fma(a[3].x, b[3].x, s2);
+    s3 = fma(a[3].y, b[3].y, s3);
+  }
+  for (; c < n2; c += 32) {
+    const double2 a = __ldcs(w + c), za = zz[c];
+    s0 = fma(a.x, za.x, s0);
+    s1 = fma(a.y, za.y, s1);
+  }
+  double s = (s0 + s1) + (s2 + s3);
+  for (int o = 16; o; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) {
+    for (int a = 0; a < q; ++a) s = fma(uT[a], What[r + (int64_t)a * n_pad], s);
+    dy[r] += s;
+  }
+}
+
+// ------------------------------------------------------------------- host side
+struct ExactAdjoint {
+  int n = 0, n_pad = 0, q = 0, bs = 0, P = 0, U = 0, RS = 0, ne = 0;
+  bool center = false;
+  int max_clusters = 0;
+  double* W = nullptr;          // n_pad x n_pad FP64 (owned)
+  __half* A = nullptr;          // 3 RS x n_pad FP16 slices
+  __half* xc = nullptr;         // n_pad x bs FP16 x'
+  int32_t* C = nullptr;         // 3 RS x bs int32 products
+  int8_t* shift = nullptr;      // bs
+  int* xmax = nullptr;          // [0] largest |x'|; [1..] the unit counter
+  double* inv_scale = nullptr;  // [0] 1 / s_W, [1 + e] 1 / s_e
+  double* part = nullptr;       // y-gradient chunk partials
+  double* z = nullptr;          // n_pad
+  ex3::Params prm;
+};
+
+void exact_adjoint_destroy(ExactAdjoint* E) {
+  if (!E) return;
+  cudaFree(E->W);
+  cudaFree(E->A);
+  cudaFree(E->xc);
+  cudaFree(E->C);
+  cudaFree(E->shift);
+  cudaFree(E->xmax);
+  cudaFree(E->inv_scale);
+  cudaFree(E->part);
+  cudaFree(E->z);
+  delete E;
+}
+
+static double pow2_scale(double mx) {  // 2^e with mx 2^e <= 512 < mx 2^(e+1); 1 for a zero row
+  if (!(mx > 0.0) || !std::isfinite(mx)) return 1.0;
+  int e = (int)std::floor(std::log2(512.0 / mx));
+  while (std::ldexp(mx, e) > 512.0) --e;
+  while (std::ldexp(mx, e + 1) <= 512.0) ++e;
+  return std::ldexp(1.0, e);
+}
+
+cudaError_t exact_adjoint_create(ExactAdjoint** out, double* W, const double* What, const double* W2, int n,
+                                 int n_pad, int q, int bs, bool center, int num_sms, cudaStream_t s,
+                                 int64_t* launches) {
+  *out = nullptr;
+  ExactAdjoint* E = new ExactAdjoint;
+  E->W = W;
+  E->n = n;
+  E->n_pad = n_pad;
+  E->q = q;
+  E->bs = bs;
+  E->P = n_pad / TB;
+  E->U = (E->P + 2) / 2;  // row-panel pairs over W's P panels and one panel of appended rows
+  E->RS = 2 * E->U * TB;
+  E->ne = 2 * (q + 1);
+  E->center = center;
+  const int ne = E->ne;
+  cudaError_t e;
+#define TRY(x)                   \
+  do {                           \
+    e = (x);                     \
+    if (e != cudaSuccess) {      \
+      exact_adjoint_destroy(E);  \
+      return e;                  \
+    }                            \
+  } while (0)
+  const size_t rows = (size_t)ex3::SLABS * E->RS;
+  TRY(cudaMalloc(&E->A, sizeof(__half) * rows * n_pad));
+  TRY(cudaMalloc(&E->xc, sizeof(__half) * (size_t)n_pad * bs));
+  TRY(cudaMalloc(&E->C, sizeof(int32_t) * rows * bs));
+  TRY(cudaMalloc(&E->shift, (size_t)bs));
+  TRY(cudaMalloc(&E->xmax, 64));
+  TRY(cudaMalloc(&E->inv_scale, sizeof(double) * (1 + ne)));
+  const int nchunks = (bs + EX_DY_CHUNK - 1) / EX_DY_CHUNK;
+  TRY(cudaMalloc(&E->part, sizeof(double) * (size_t)nchunks * n));
+  TRY(cudaMalloc(&E->z, sizeof(double) * (size_t)n_pad));
+  TRY(cudaMemsetAsync(E->xc, 0, sizeof(__half) * (size_t)n_pad * bs, s));
+  // the appended columns [X^_L | y^ | W X^_L | W y^] side by side
+  double* Ex = nullptr;
+  TRY(cudaMallocAsync(&Ex, sizeof(double) * (size_t)n_pad * ne, s));
+  TRY(cudaMemcpyAsync(Ex, What, sizeof(double) * (size_t)n_pad * (q + 1), cudaMemcpyDeviceToDevice, s));
+  TRY(cudaMemcpyAsync(Ex + (size_t)n_pad * (q + 1), W2, sizeof(double) * (size_t)n_pad * (q + 1),
+                      cudaMemcpyDeviceToDevice, s));
+  // scales: the largest entry of W and of every appended row
+  unsigned long long* mx = nullptr;
+  TRY(cudaMallocAsync(&mx, sizeof(unsigned long long) * (size_t)(n_pad + ne), s));
+  TRY(cudaMemsetAsync(mx, 0, sizeof(unsigned long long) * (size_t)(n_pad + ne), s));
+  col_absmax_kernel<<<dim3(8, n_pad), 256, 0, s>>>(W, n_pad, n_pad, n_pad, mx);
+  col_absmax_kernel<<<dim3(8, ne), 256, 0, s>>>(Ex, n_pad, n_pad, ne, mx + n_pad);
+  *launches += 2;
+  TRY(cudaGetLastError());
+  std::vector<unsigned long long> hm((size_t)n_pad + ne);
+  TRY(cudaMemcpyAsync(hm.data(), mx, sizeof(unsigned long long) * hm.size(), cudaMemcpyDeviceToHost, s));
+  TRY(cudaStreamSynchronize(s));
+  double wmax = 0.0;
+  for (int i = 0; i < n_pad; ++i) {
+    double v;
+    std::memcpy(&v, &hm[i], sizeof v);
+    wmax = std::max(wmax, v);
+  }
+  std::vector<double> sc(1 + ne), inv(1 + ne);
+  sc[0] = pow2_scale(wmax);
+  for (int i = 0; i < ne; ++i) {
+    double v;
+    std::memcpy(&v, &hm[(size_t)n_pad + i], sizeof v);
+    sc[1 + i] = pow2_scale(v);
+  }
+  for (int i = 0; i <= ne; ++i) inv[i] = 1.0 / sc[i];  // powers of two: exact
+  double* dsc = nullptr;
+  TRY(cudaMallocAsync(&dsc, sizeof(double) * (1 + ne), s));
+  TRY(cudaMemcpyAsync(dsc, sc.data(), sizeof(double) * (1 + ne), cudaMemcpyHostToDevice, s));
+  TRY(cudaMemcpyAsync(E->inv_scale, inv.data(), sizeof(double) * (1 + ne), cudaMemcpyHostToDevice, s));
+  slice_rows_kernel<<<dim3((n_pad + 255) / 256, E->RS), 256, 0, s>>>(W, Ex, n_pad, ne, E->RS, dsc, E->A);
+  *launches += 1;
+  TRY(cudaGetLastError());
+  TRY(cudaFreeAsync(Ex, s));
+  TRY(cudaFreeAsync(mx, s));
+  TRY(cudaFreeAsync(dsc, s));
+  // tensor maps and the launch parameters (the block width fixed at bs; a
+  // shorter block covers only its strips)
+  tc::EncodeTiledFn enc = nullptr;
+  TRY(tc::get_encode(&enc));
+  ex3::Params& p = E->prm;
+  std::memset(&p, 0, sizeof p);
+  TRY(tc::make_map(enc, &p.A, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, E->A, n_pad, rows, 2 * (size_t)n_pad, ex3::KCH, TB,
+                   true));
+  TRY(tc::make_map(enc, &p.B, CU_TENSOR_MAP_DATA_TYPE_FLOAT16, E->xc, n_pad, bs, 2 * (size_t)n_pad, ex3::KCH, TN / 2,
+                   true));
+  TRY(tc::make_map(enc, &p.C, CU_TENSOR_MAP_DATA_TYPE_INT32, E->C, rows, bs, 4 * rows, 32, ex3::ST_COLS, false));
+  p.P = E->P;
+  p.U = E->U;
+  p.RS = E->RS;
+  p.xmax = E->xmax;
+  p.counter = reinterpret_cast<unsigned int*>(E->xmax + 1);
+  TRY(cudaFuncSetAttribute(ex3::exact_product_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, ex3::SMEM));
+  {
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof cfg);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2 * (num_sms / 2));
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = ex3::SMEM;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    TRY(cudaOccupancyMaxActiveClusters(&E->max_clusters, ex3::exact_product_kernel, &cfg));
+    if (E->max_clusters < 1) TRY(cudaErrorLaunchOutOfResources);
+  }
+  TRY(cudaStreamSynchronize(s));
+#undef TRY
+  *out = E;
+  return cudaSuccess;
+}
+
+cudaError_t exact_adjoint_block(ExactAdjoint* E, const int8_t* X, int64_t ldx, int ncols, const SolveConsts* sc,
+                                const double* GH, const double* What, double h, double sigma2, double* chi2,
+                                double* dh, double* wv, double* uT, double* dh_accum, double* dy_accum,
+                                DevStatus* st, cudaStream_t s, int64_t* launches) {
+  if (ncols <= 0) return cudaSuccess;
+  if (ncols > E->bs) return cudaErrorInvalidValue;
+  cudaError_t e;
+  if ((e = cudaMemsetAsync(E->xmax, 0, sizeof(int), s)) != cudaSuccess) return e;
+  // the last strip's columns past ncols: zeros, not an earlier block's values
+  const int cover = std::min(E->bs, (ncols + TN - 1) / TN * TN);
+  if (cover > ncols &&
+      (e = cudaMemsetAsync(E->xc + (size_t)ncols * E->n_pad, 0, sizeof(__half) * (size_t)(cover - ncols) * E->n_pad,
+                           s)) != cudaSuccess)
+    return e;
+  cast_exact_kernel<<<(ncols + 7) / 8, 256, 0, s>>>(X, ldx, E->n, E->n_pad, ncols, E->center ? 1 : 0, E->shift,
+                                                    E->xc, E->xmax, reinterpret_cast<unsigned int*>(E->xmax + 1));
+  if ((e = cudaGetLastError()) != cudaSuccess) return e;
+  ex3::Params p = E->prm;
+  p.Cs = (ncols + TN - 1) / TN;
+  p.ntiles = ex3::SLABS * p.U * p.Cs;
+  p.st = st;
+  {
+    const int ncl = std::min(p.ntiles, E->max_clusters);
+    cudaLaunchConfig_t cfg;
+    std::memset(&cfg, 0, sizeof cfg);
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.gridDim = dim3(2 * ncl);
+    cfg.blockDim = dim3(THREADS);
+    cfg.dynamicSmemBytes = ex3::SMEM;
+    cfg.stream = s;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if ((e = cudaLaunchKernelEx(&cfg, ex3::exact_product_kernel, p)) != cudaSuccess) return e;
+  }
+  const int64_t ldc = (int64_t)ex3::SLABS * E->RS;
+  if ((e = launch_exact_adjoint_sums(E->C, ldc, E->RS, E->xc, E->n_pad, E->n, E->n_pad, E->ne, E->inv_scale, sc, GH,
+                                     E->q, ncols, h, sigma2, E->xmax, chi2, dh, wv, dh_accum, uT, s)) != cudaSuccess)
+    return e;
+  const int p1 = E->q + 1, nchunks = (ncols + EX_DY_CHUNK - 1) / EX_DY_CHUNK;
+  exact_dy_part_kernel<<<dim3((E->n + 255) / 256, nchunks), 256, 0, s>>>(E->xc, E->n_pad, wv, p1, E->n, ncols,
+                                                                         E->part);
+  exact_dy_z_kernel<<<(E->n_pad + 255) / 256, 256, 0, s>>>(E->part, nchunks, E->n, E->n_pad, E->z);
+  exact_dy_apply_kernel<<<(E->n + 7) / 8, 256, 0, s>>>(E->W, E->n_pad, E->n, E->z, What, uT, E->q, dy_accum);
+  *launches += 7;
+  return cudaGetLastError();
+}
+
+}  // namespace gwas

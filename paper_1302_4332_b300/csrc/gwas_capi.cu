@@ -54,6 +54,7 @@ struct gwas_ctx {
   float* Wh32 = nullptr;       // split contexts: What in FP32, row-major (row stride w32_stride(q))
   double* adj = nullptr;       // per-SNP chi2 (bs), dh (bs), y-weights (bs x p), uT (q), dh/dy staging (1 + n),
                                // the y-gradient's chunk partials (adjoint_dy_chunks(bs) x n)
+  ExactAdjoint* exact = nullptr;  // split precisions: the adjoint's exact products (built on first use)
   // pinned host buffers of the file reader, kept across gwas_solve_file calls
   std::vector<void*> file_buf;
   int64_t file_buf_bytes = 0;
@@ -162,6 +163,9 @@ int check_device_status(gwas_ctx* ctx) {
     clean.not_spd = hs.not_spd;
     clean.sc_err = hs.sc_err;
     CK(cudaMemcpy(ctx->st, &clean, sizeof clean, cudaMemcpyHostToDevice));
+    if (hs.err == DEV_ERR_RANGE)
+      return fail(ctx, GWAS_ERR_ARG, "SNP values too large for the split adjoint's exact products "
+                                     "(largest |x - c| times 512 n_pad reaches 2^31)");
     return fail(ctx, GWAS_ERR_TIMEOUT, "a bounded device-side wait ran out (device code %d)", hs.err);
   }
   return GWAS_OK;
@@ -209,6 +213,46 @@ int ensure_adjoint(gwas_ctx* ctx) {
     ctx->launches += 1;
   }
   return GWAS_OK;
+}
+
+// The split precisions' adjoint set-up: W = M^-1 = L^-T L^-1 in FP64 (the
+// FP64 solves of the identity, bs columns at a time), W [X^_L | y^] likewise,
+// then the exact slices of both (exact_adjoint_create).
+int ensure_exact_adjoint(gwas_ctx* ctx) {
+  if (ctx->exact) return GWAS_OK;
+  int rc = ensure_adjoint(ctx);
+  if (rc != GWAS_OK) return rc;
+  const size_t np = (size_t)ctx->n_pad;
+  const int n = ctx->n, nc = ctx->q + 1;
+  double *W = nullptr, *E = nullptr, *W2 = nullptr;
+  auto release = [&] {
+    cudaFree(W);
+    cudaFree(E);
+    cudaFree(W2);
+  };
+  rc = [&]() -> int {
+    CK(dmalloc(&W, sizeof(double) * np * np));
+    CK(cudaMemsetAsync(W, 0, sizeof(double) * np * np, ctx->stream));
+    CK(dmalloc(&E, sizeof(double) * (size_t)n * std::min(ctx->bs, n)));
+    CK(dmalloc(&W2, sizeof(double) * np * nc));
+    for (int c0 = 0; c0 < n; c0 += ctx->bs) {
+      const int ncc = std::min(ctx->bs, n - c0);
+      CK(launch_identity_cols(E, n, c0, ncc, ctx->stream));
+      ctx->launches += 1;
+      int r = solve_f64_cols(ctx, E, n, n, ncc, ctx->Xt, false);
+      if (r == GWAS_OK) r = solve_f64_cols(ctx, ctx->Xt, ctx->n_pad, ctx->n_pad, ncc, W + (size_t)c0 * np, true);
+      if (r != GWAS_OK) return r;
+    }
+    int r = solve_f64_cols(ctx, ctx->What, ctx->n_pad, ctx->n_pad, nc, ctx->Xt, false);
+    if (r == GWAS_OK) r = solve_f64_cols(ctx, ctx->Xt, ctx->n_pad, ctx->n_pad, nc, W2, true);
+    if (r != GWAS_OK) return r;
+    CK(exact_adjoint_create(&ctx->exact, W, ctx->What, W2, n, ctx->n_pad, ctx->q, ctx->bs, ctx->intercept,
+                            ctx->num_sms, ctx->stream, &ctx->launches));
+    W = nullptr;  // owned by the exact state now
+    return check_device_status(ctx);
+  }();
+  release();
+  return rc;
 }
 
 // X~ = L^-1 X for one block (FP64 or split precision), then reductions + solve.
@@ -336,6 +380,7 @@ void free_all(gwas_ctx* c) {
   cudaFree(c->AopT); cudaFree(c->Xhat); cudaFree(c->What); cudaFree(c->GH); cudaFree(c->adj); cudaFree(c->Wh32);
   cudaFreeHost(c->h_b); cudaFreeHost(c->h_se); cudaFreeHost(c->h_status);
   if (c->tcs) tc::destroy(c->tcs);
+  exact_adjoint_destroy(c->exact);
   for (auto* p : c->file_buf) cudaFreeHost(p);
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   delete c;
@@ -917,40 +962,21 @@ int gwas_adjoint_block(gwas_ctx* ctx, const int8_t* XR, int64_t ldx, int ncols, 
     xin = ctx->ring[0];
     ld_in = ctx->n_pad;
   }
-  bool f32_sums = false;
   if (split) {
-    // the split adjoint: X~ and X^ = L^-T X~ on the tensor cores (both on the
-    // integer-shifted SNP columns).  Their sums come straight from FP32 (the
-    // shift undone exactly through the Gram matrices) when q <= 7; otherwise
-    // they are widened to FP64 with the shift undone.  The per-SNP adjoint
-    // arithmetic stays FP64.
+    // the split adjoint: every per-SNP input from one exact integer product
+    // of the sliced [W ; X^_L^T ; y^T ; (W X^_L)^T ; (W y^)^T] with the block's
+    // shifted dosages on the tensor cores (adjoint_exact.cu); the per-SNP
+    // adjoint arithmetic and the y-gradient in FP64
+    if ((rc = ensure_exact_adjoint(ctx)) != GWAS_OK) return rc;
     int64_t nl = 0;
     cudaError_t e;
     {
       StageMark m(ctx, GWAS_STAGE_TRSM, ctx->stream);
-      e = tc::run_block(ctx->tcs, static_cast<const int8_t*>(xin), ld_in, ncols, ctx->stream, &nl, true);
-      if (e == cudaSuccess) e = tc::ensure_transpose(ctx->tcs, ctx->AopT, ctx->stream, &nl);
-      if (e == cudaSuccess) e = tc::run_transpose(ctx->tcs, ncols, ctx->stream, &nl);
+      e = exact_adjoint_block(ctx->exact, static_cast<const int8_t*>(xin), ld_in, ncols, ctx->sc, ctx->GH, ctx->What,
+                              ctx->h, ctx->sigma2, d_chi2, d_dh, d_w, d_uT, acc_dh, acc_dy, ctx->st, ctx->stream, &nl);
     }
     ctx->launches += nl;
-    if (e != cudaSuccess) return fail(ctx, GWAS_ERR_CUDA, "split adjoint solves: %s", cudaGetErrorString(e));
-    const int8_t* sh = tc::shift_of(ctx->tcs);
-    f32_sums = ctx->Wh32 != nullptr && ctx->n_pad % 128 == 0 &&
-               (ncols + std::min(ncols, ctx->num_sms) - 1) / std::min(ncols, ctx->num_sms) <= 128;
-    if (f32_sums) {
-      StageMark m(ctx, GWAS_STAGE_REDUCE, ctx->stream);
-      CK(launch_adjoint_f32(tc::xt_reduce_map(ctx->tcs), tc::xhat_reduce_map(ctx->tcs), tc::xhat_f32(ctx->tcs),
-                            tc::xt_ld(ctx->tcs), ctx->n_pad, n, ctx->W32, ctx->Wh32, ctx->G, ctx->What, ctx->n_pad,
-                            ctx->GH, ctx->sc, sh, ctx->q, ncols, ctx->h, ctx->sigma2, d_chi2, d_dh, d_w, d_uT, acc_dh,
-                            acc_dy, d_dypart, ctx->st, ctx->num_sms, ctx->stream));
-      ctx->launches += 4;
-    } else {
-      CK(launch_widen(tc::xt_f32(ctx->tcs), tc::xt_ld(ctx->tcs), ctx->Xt, ctx->n_pad, ctx->n_pad, ncols, sh, ctx->W,
-                      ctx->stream));
-      CK(launch_widen(tc::xhat_f32(ctx->tcs), tc::xt_ld(ctx->tcs), ctx->Xhat, ctx->n_pad, ctx->n_pad, ncols, sh,
-                      ctx->What, ctx->stream));
-      ctx->launches += 2;
-    }
+    if (e != cudaSuccess) return fail(ctx, GWAS_ERR_CUDA, "split adjoint: %s", cudaGetErrorString(e));
   } else {
     const int C64 = (ncols + F64_TN - 1) / F64_TN;
     CK(cudaMemsetAsync(ctx->sched, 0, sizeof(Sched) + sizeof(int) * (size_t)ctx->P * C64, ctx->stream));
@@ -969,7 +995,7 @@ int gwas_adjoint_block(gwas_ctx* ctx, const int8_t* XR, int64_t ldx, int ncols, 
     StageMark m(ctx, GWAS_STAGE_TRSM, ctx->stream);
     if ((rc = solve_f64_cols(ctx, ctx->Xt, ctx->n_pad, ctx->n_pad, ncols, ctx->Xhat, true)) != GWAS_OK) return rc;
   }
-  if (!f32_sums) {
+  if (!split) {
     StageMark m(ctx, GWAS_STAGE_REDUCE, ctx->stream);
     CK(launch_adjoint(ctx->Xt, ctx->Xhat, ctx->n_pad, ctx->n_pad, n, ctx->W, ctx->What, ctx->n_pad, ctx->sc, ctx->GH,
                       ctx->q, ncols, ctx->h, ctx->sigma2, d_chi2, d_dh, d_w, d_uT, acc_dh, acc_dy, d_dypart,

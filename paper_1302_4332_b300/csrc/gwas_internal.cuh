@@ -16,6 +16,7 @@
 #pragma once
 
 #include <cuda.h>
+#include <cuda_fp16.h>
 #include <cuda_runtime.h>
 
 #include <cstdint>
@@ -31,7 +32,9 @@ constexpr double SINGULAR_TAU = 1e-7;
 constexpr long long WAIT_LIMIT_NS = 8000000000LL;  // bounded device-side waits: 8 s
 
 // Codes the kernels write into DevStatus::err.
-enum : int { DEV_OK = 0, DEV_ERR_TIMEOUT = 1 };
+// DEV_ERR_RANGE: the split adjoint's exact products refused a block whose
+// largest |x - c| times 512 n_pad reaches 2^31 (never for dosages 0..2).
+enum : int { DEV_OK = 0, DEV_ERR_TIMEOUT = 1, DEV_ERR_RANGE = 2 };
 
 // Device-resident status block of a context.
 struct DevStatus {
@@ -169,6 +172,30 @@ cudaError_t launch_adjoint_f32(const CUtensorMap* xtmap, const CUtensorMap* xhma
                                double* dh, double* wv, double* uT, double* dh_accum, double* dy_accum,
                                double* dy_part, DevStatus* st, int num_sms, cudaStream_t s);
 cudaError_t prepare_adjoint_f32();
+// The split precisions' adjoint in its M^-1 form with exact integer products
+// (adjoint_exact.cu).  Set-up: W = M^-1 (n_pad x n_pad FP64, symmetric, zero
+// on the padding; the state takes ownership), What = [X^_L | y^] and W2 = W
+// What (n_pad x (q+1) each, read during set-up only); center: X_L[:, 0] is
+// the intercept (SNP columns are shifted by their integer mean).
+struct ExactAdjoint;
+cudaError_t exact_adjoint_create(ExactAdjoint** out, double* W, const double* What, const double* W2, int n,
+                                 int n_pad, int q, int bs, bool center, int num_sms, cudaStream_t s,
+                                 int64_t* launches);
+// One block of ncols <= bs int8 SNP columns (device, any alignment): chi2 and
+// d chi2/dh per SNP, wv (p per SNP), dh_accum += the block's sum of d chi2/dh,
+// uT = the block's sums of wv[0..q-1], dy_accum += the block's y-gradient.
+cudaError_t exact_adjoint_block(ExactAdjoint* E, const int8_t* X, int64_t ldx, int ncols, const SolveConsts* sc,
+                                const double* GH, const double* What, double h, double sigma2, double* chi2,
+                                double* dh, double* wv, double* uT, double* dh_accum, double* dy_accum,
+                                DevStatus* st, cudaStream_t s, int64_t* launches);
+void exact_adjoint_destroy(ExactAdjoint* E);
+// The per-SNP sums and adjoint from the exact products (adjoint.cu), then the
+// block's sums of d chi2/dh (added to dh_accum) and of wv[0..q-1] (into uT).
+cudaError_t launch_exact_adjoint_sums(const int32_t* C, int64_t ldc, int RS, const __half* xc, int64_t ldx, int n,
+                                      int n_pad, int ne, const double* inv_scale, const SolveConsts* sc,
+                                      const double* GH, int q, int ncols, double h, double sigma2, const int* xmax,
+                                      double* chi2, double* dh, double* wv, double* dh_accum, double* uT,
+                                      cudaStream_t s);
 cudaError_t launch_log_diag(const double* L, int64_t ld, int n, double* out, cudaStream_t s);
 cudaError_t launch_col_sumsq(const double* X, int64_t ld, int n, int ncols, double* out, cudaStream_t s);
 cudaError_t launch_identity_cols(double* E, int n, int c0, int ncols, cudaStream_t s);

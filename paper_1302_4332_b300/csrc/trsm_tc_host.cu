@@ -403,9 +403,6 @@ __global__ void split_aop_kernel(const double* __restrict__ A, int64_t count, vo
 }
 
 // ------------------------------------------------------------------- host side
-typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
-                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
-                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
 
 struct TcState {
   bool tf32 = false;
@@ -455,7 +452,7 @@ struct TcState {
 // Row entries of the tile order: row panels, or row-panel pairs in pair mode.
 static int unit_rows(const TcState* t) { return t->mode == TILES_SINGLE ? t->P : (t->P + 1) / 2; }
 
-static cudaError_t get_encode(EncodeTiledFn* fn) {
+cudaError_t get_encode(EncodeTiledFn* fn) {
   void* f = nullptr;
   cudaDriverEntryPointQueryResult q;
   cudaError_t e = cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q);
@@ -467,7 +464,7 @@ static cudaError_t get_encode(EncodeTiledFn* fn) {
 
 // 2D tiled map: dims {inner, outer}, outer stride in bytes, box {bi, bo};
 // swz: the 64-byte swizzle of the operand stages (box inner extent 64 bytes).
-static cudaError_t make_map(EncodeTiledFn enc, CUtensorMap* m, CUtensorMapDataType dt, const void* base,
+cudaError_t make_map(EncodeTiledFn enc, CUtensorMap* m, CUtensorMapDataType dt, const void* base,
                             uint64_t inner, uint64_t outer, uint64_t stride_bytes, uint32_t bi, uint32_t bo,
                             bool swz) {
   cuuint64_t dims[2] = {inner, outer};

@@ -100,6 +100,16 @@ namespace inv2 {
 constexpr int ST_COLS = 16;  // SNP columns per inverse-form store chunk (32 rows x 16 FP32 = 2 KB)
 }  // namespace inv2
 
+// cuTensorMapEncodeTiled through the runtime's driver entry point, and a 2D
+// tiled map: dims {inner, outer}, outer stride in bytes, box {bi, bo};
+// swz: the 64-byte swizzle of the operand stages (box inner extent 64 bytes).
+typedef CUresult (*EncodeTiledFn)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                  const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+cudaError_t get_encode(EncodeTiledFn* fn);
+cudaError_t make_map(EncodeTiledFn enc, CUtensorMap* m, CUtensorMapDataType dt, const void* base, uint64_t inner,
+                     uint64_t outer, uint64_t stride_bytes, uint32_t bi, uint32_t bo, bool swz);
+
 // Launch entry points of the kernels (trsm_tc.cu).
 // Opt-in shared memory of the forward kernels (clusters: also the pair and
 // inverse-form kernels) and of the transpose solve.
