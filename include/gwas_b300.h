@@ -76,8 +76,7 @@ extern "C" {
  *                 GWAS_ERR_ARG): each row of L^-1 is scaled by a power of two so its
  *                 largest entry lies in [2^13, 2^14), then split into FP16 hi + lo
  *                 (11 + 11 significant bits against BF16's 8 + 8), the dosages exact
- *                 in FP16: two products at the BF16 rate; results scaled back exactly.
- *                 The adjoint's transpose solve of such a context runs in BF16x3. */
+ *                 in FP16: two products at the BF16 rate; results scaled back exactly. */
 typedef enum { GWAS_FP64 = 0, GWAS_TF32X3 = 1, GWAS_BF16X3 = 2, GWAS_F16X2 = 3 } gwas_precision;
 
 typedef struct {
@@ -203,14 +202,23 @@ int gwas_solve_block_static(gwas_ctx *ctx, const int8_t *XR, int64_t ldx, int nc
 
 /* The differentiation form (not in the paper): for one block of SNPs, the
  * Wald statistic chi2_i = b_{p-1}^2 / (S^-1)_{p-1,p-1} of every SNP and the
- * gradient of their sum with respect to h and y.  FP64 (forward solve
- * X~ = L^-1 X and transpose solve X^ = L^-T X~ = M^-1 X, then per-SNP p x p
- * adjoints); needs 0 < h <= 1 (it uses dM/dh = (M - sigma2 I) / h).
+ * gradient of their sum with respect to h and y; needs 0 < h <= 1 (it uses
+ * dM/dh = (M - sigma2 I) / h).
+ *   GWAS_FP64 contexts: forward solve X~ = L^-1 X and transpose solve
+ *     X^ = L^-T X~ = M^-1 X in FP64, then per-SNP p x p adjoints.  The first
+ *     call builds the transpose operator (8 n^2 bytes).
+ *   Split contexts (any precision and tile mode): every per-SNP input from one
+ *     exact integer product on the tensor cores -- M^-1 (formed in FP64 at the
+ *     first call, 8 n^2 bytes, plus three FP16 slices of it, 6 n^2 bytes) and
+ *     the solved covariates and phenotype, sliced into 10-bit integer pieces,
+ *     times the block's int8 dosages with FP32 accumulation kept below 2^24 --
+ *     then the same FP64 adjoint arithmetic: results agree with the FP64 path
+ *     to ~1e-8.  A block whose largest |x - c| times 512 n_pad reaches 2^31
+ *     (never for dosages 0..2 below n = 2,000,000) is refused: GWAS_ERR_ARG.
  *   chi2, dchi2_dh  ncols each, may be NULL (a collinear SNP: NaN and 0)
  *   dh_accum        one double; the block's sum of d chi2/dh is ADDED to it
  *   dy_accum        n doubles; the block's d(sum chi2)/dy is ADDED to it
- * Host or device pointers.  The first call builds the transpose operator
- * (8 n^2 bytes).  Errors: GWAS_ERR_ARG, GWAS_ERR_CUDA, GWAS_ERR_TIMEOUT. */
+ * Host or device pointers.  Errors: GWAS_ERR_ARG, GWAS_ERR_CUDA, GWAS_ERR_TIMEOUT. */
 int gwas_adjoint_block(gwas_ctx *ctx, const int8_t *XR, int64_t ldx, int ncols, double *chi2, double *dchi2_dh,
                        double *dh_accum, double *dy_accum);
 

@@ -218,7 +218,6 @@ __global__ void __launch_bounds__(256) exact_adjoint_kernel(
   adjoint_store<QM>(af, ah, sc, GH, q, col, h, sigma2, chi2, dh, wv);
 }
 
-// One block: dh_sum += sum_i dh_i and uT[a] = sum_i w_i[a] (a < q), in a fixed order.
 // Block a (< q + 1): quantity a over the SNPs -- uT[a] for a < q, the block's
 // d chi2/dh (added to *dh_accum) for a = q -- 256 threads each over a strided
 // slice, then a fixed tree in shared memory (deterministic).
@@ -276,211 +275,6 @@ __global__ void adjoint_dy_sum_kernel(const double* __restrict__ Wh, int64_t ldw
 
 int adjoint_dy_chunks(int bs) { return (bs + DY_CHUNK - 1) / DY_CHUNK; }
 
-// The split paths' adjoint sums from the FP32 X~ and X^ of the tensor-core
-// solves, without widening them to FP64: a persistent block per SM over a
-// contiguous range of SNP columns (groups of 32), a producer thread streaming
-// 256-row chunks of both (two tiled TMA loads of 256 rows x 32 SNPs) with the
-// chunk's rows of W32 and Wh32 (FP32 [X~_L | y~] and [X^_L | y^]) into
-// shared-memory stages; 16 consumer warps take two SNP columns each.  Sums as
-// in the forward reductions: FP32 per chunk, Kahan across chunks, a
-// double-FP32 butterfly across lanes.  The solves ran on the shifted columns
-// x - c 1: with X~ = X~' + c X~_L[:, 0] and X^ = X^' + c X^_L[:, 0], the sums
-// of the unshifted column follow exactly from the Gram matrices G = W^T W and
-// GH = What^T What (FP64).  Then the FP64 per-SNP adjoint, one lane per SNP.
-constexpr int AB_CW = 16, AB_G = 2 * AB_CW, AB_CH = RED_BOX_ROWS, AB_MAXC = 128;
-
-template <int WS>
-struct AdjBulkCfg {
-  static constexpr int BOX = AB_G * AB_CH * 4;             // one tiled load: 32 KB
-  static constexpr int WB = AB_CH * WS * 4;                // a chunk's W32 rows: 4 or 8 KB
-  static constexpr int STAGE = 2 * BOX + 2 * WB;           // 72 or 80 KB
-  static constexpr int ST = WS == 4 ? 3 : 2;
-  static constexpr int SMEM = 128 + ST * STAGE + 2 * ST * 8;
-};
-
-template <int QM, int WS>
-__global__ void __launch_bounds__(32 * (AB_CW + 1), 1) adjoint_snp_bulk_kernel(
-    const __grid_constant__ CUtensorMap xtmap, const __grid_constant__ CUtensorMap xhmap, int rows,
-    const float* __restrict__ W32, const float* __restrict__ Wh32, const double* __restrict__ G,
-    const double* __restrict__ GH, const SolveConsts* __restrict__ sc, const int8_t* __restrict__ shift, int q,
-    int ncols, double h, double sigma2, double* __restrict__ chi2, double* __restrict__ dh,
-    double* __restrict__ wv, DevStatus* st) {
-  using K = AdjBulkCfg<WS>;
-  constexpr int NA = QM + 2, NW4 = WS / 4, BST = K::ST;
-  extern __shared__ __align__(128) uint8_t smem_raw[];
-  __shared__ double cf[AB_MAXC][NA], chs[AB_MAXC][NA];  // the block's column totals, forward and transpose
-  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 127) & ~uintptr_t(127));
-  uint64_t* full = reinterpret_cast<uint64_t*>(smem + BST * K::STAGE);
-  uint64_t* empty = full + BST;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int c_begin = (int)((int64_t)blockIdx.x * ncols / gridDim.x);
-  const int c_end = (int)((int64_t)(blockIdx.x + 1) * ncols / gridDim.x);
-  const int nch = (rows + AB_CH - 1) / AB_CH;
-  if (threadIdx.x == 0) {
-    for (int s = 0; s < BST; ++s) {
-      ptx::mbar_init(&full[s], 1);
-      ptx::mbar_init(&empty[s], AB_CW);
-    }
-    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-    ptx::prefetch_tensormap(&xtmap);
-    ptx::prefetch_tensormap(&xhmap);
-  }
-  __syncthreads();
-  if (warp == AB_CW) {
-    // ------------------------------------------------------------ producer
-    if (lane == 0) {
-      uint32_t it = 0;
-      for (int g0 = c_begin; g0 < c_end; g0 += AB_G)
-        for (int t = 0; t < nch; ++t, ++it) {
-          const int s = it % BST;
-          const uint32_t r = it / BST;
-          if (!ptx::mbar_wait(&empty[s], (r & 1) ^ 1, st)) {
-            ptx::settle();
-            return;
-          }
-          const int rt = rows - t * AB_CH < AB_CH ? rows - t * AB_CH : AB_CH;
-          uint8_t* sb = smem + s * K::STAGE;
-          ptx::mbar_arrive_expect_tx(&full[s], (uint32_t)(2 * K::BOX + 2 * rt * WS * 4));
-          ptx::tma_load_2d(sb, &xtmap, &full[s], t * AB_CH, g0);
-          ptx::tma_load_2d(sb + K::BOX, &xhmap, &full[s], t * AB_CH, g0);
-          ptx::bulk_load(sb + 2 * K::BOX, W32 + (int64_t)t * AB_CH * WS, rt * WS * 4, &full[s]);
-          ptx::bulk_load(sb + 2 * K::BOX + K::WB, Wh32 + (int64_t)t * AB_CH * WS, rt * WS * 4, &full[s]);
-        }
-    }
-    return;
-  }
-  // ------------------------------------------------------------ consumers
-  uint32_t it = 0;
-  bool ok = true;
-  for (int g0 = c_begin; g0 < c_end && ok; g0 += AB_G) {
-    const int ca = g0 + 2 * warp;  // this warp's columns ca, ca + 1
-    float ks[4][NA], kc[4][NA];   // [x~ of ca, x~ of ca+1, x^ of ca, x^ of ca+1]
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-      for (int a = 0; a < NA; ++a) ks[u][a] = kc[u][a] = 0.f;
-    for (int t = 0; t < nch; ++t, ++it) {
-      const int s = it % BST;
-      const uint32_t r = it / BST;
-      if (!__all_sync(0xffffffffu, ptx::mbar_wait(&full[s], r & 1, st))) {
-        ok = false;
-        break;
-      }
-      if (ca < c_end) {
-        const uint8_t* sb = smem + s * K::STAGE;
-        const float* xt = reinterpret_cast<const float*>(sb) + (2 * warp) * AB_CH;
-        const float* xh = reinterpret_cast<const float*>(sb + K::BOX) + (2 * warp) * AB_CH;
-        const float4* sw = reinterpret_cast<const float4*>(sb + 2 * K::BOX);
-        const float4* swh = reinterpret_cast<const float4*>(sb + 2 * K::BOX + K::WB);
-        const int rt = rows - t * AB_CH < AB_CH ? rows - t * AB_CH : AB_CH;
-        float p[4][NA];
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int a = 0; a < NA; ++a) p[u][a] = 0.f;
-        for (int i = 0; i < rt / 128; ++i) {
-#pragma unroll
-          for (int rr = 0; rr < 4; ++rr) {
-            const int row = i * 128 + rr * 32 + lane;
-            const float x[4] = {xt[row], xt[AB_CH + row], xh[row], xh[AB_CH + row]};
-#pragma unroll
-            for (int v4 = 0; v4 < NW4; ++v4) {
-              const float4 w = sw[row * NW4 + v4], wh = swh[row * NW4 + v4];
-              const float wr[4] = {w.x, w.y, w.z, w.w}, whr[4] = {wh.x, wh.y, wh.z, wh.w};
-#pragma unroll
-              for (int e = 0; e < 4; ++e)
-                if (4 * v4 + e <= QM) {
-                  p[0][4 * v4 + e] = fmaf(x[0], wr[e], p[0][4 * v4 + e]);
-                  p[1][4 * v4 + e] = fmaf(x[1], wr[e], p[1][4 * v4 + e]);
-                  p[2][4 * v4 + e] = fmaf(x[2], whr[e], p[2][4 * v4 + e]);
-                  p[3][4 * v4 + e] = fmaf(x[3], whr[e], p[3][4 * v4 + e]);
-                }
-            }
-#pragma unroll
-            for (int u = 0; u < 4; ++u) p[u][QM + 1] = fmaf(x[u], x[u], p[u][QM + 1]);
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-          for (int a = 0; a < NA; ++a) {
-            const float y = p[u][a] - kc[u][a];
-            const float s2 = ks[u][a] + y;
-            kc[u][a] = (s2 - ks[u][a]) - y;
-            ks[u][a] = s2;
-          }
-      }
-      __syncwarp();
-      if (lane == 0) ptx::mbar_arrive(&empty[s]);
-    }
-    if (ok) {
-#pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int col = ca + (u & 1);
-        if (col >= c_end) continue;
-#pragma unroll
-        for (int a = 0; a < NA; ++a) {
-          float hi = ks[u][a], lo = -kc[u][a];
-#pragma unroll
-          for (int o = 16; o; o >>= 1)
-            ptx::df_add(hi, lo, __shfl_xor_sync(0xffffffffu, hi, o), __shfl_xor_sync(0xffffffffu, lo, o));
-          if (lane == 0) (u < 2 ? cf : chs)[col - c_begin][a] = (double)hi + (double)lo;
-        }
-      }
-    }
-  }
-  if (!ptx::group_and(1, 32 * AB_CW, ok)) {
-    ptx::settle();
-    return;
-  }
-  const int nc = q + 1;
-  for (int j = threadIdx.x; j < c_end - c_begin; j += 32 * AB_CW) {
-    const int col = c_begin + j;
-    const double c = shift ? (double)shift[col] : 0.0;
-    double af[NA], ah[NA];
-#pragma unroll
-    for (int a = 0; a < NA; ++a) {
-      af[a] = cf[j][a];
-      ah[a] = chs[j][a];
-    }
-    if (c != 0.0) {  // the unshifted column's sums (x~' and x^' before af[0], ah[0] change)
-      af[QM + 1] += c * (2.0 * af[0] + c * G[0]);
-      ah[QM + 1] += c * (2.0 * ah[0] + c * GH[0]);
-#pragma unroll
-      for (int a = 0; a <= QM; ++a)
-        if (a < nc) {
-          af[a] += c * G[a * nc];
-          ah[a] += c * GH[a * nc];
-        }
-    }
-    adjoint_store<QM>(af, ah, sc, GH, q, col, h, sigma2, chi2, dh, wv);
-  }
-}
-
-// The y-gradient's chunk partials from the FP32 X^ of the shifted columns:
-// x^_i = x^'_i + c_i X^_L[:, 0].
-__global__ void adjoint_dy_part_f32_kernel(const float* __restrict__ Xh, int64_t ldt, const double* __restrict__ Wh,
-                                           const int8_t* __restrict__ shift, const double* __restrict__ wv, int q,
-                                           int n, int ncols, double* __restrict__ part) {
-  const int r = blockIdx.x * blockDim.x + threadIdx.x;
-  if (r >= n) return;
-  const int i0 = blockIdx.y * DY_CHUNK, i1 = i0 + DY_CHUNK < ncols ? i0 + DY_CHUNK : ncols;
-  const double w0 = Wh[r];
-  double s = 0.0;
-  for (int i = i0; i < i1; ++i) {
-    const double x = (double)Xh[r + (int64_t)i * ldt] + (shift ? (double)shift[i] * w0 : 0.0);
-    s = fma(wv[(int64_t)i * (q + 1) + q], x, s);
-  }
-  part[(int64_t)blockIdx.y * n + r] = s;
-}
-
-cudaError_t prepare_adjoint_f32() {
-  cudaError_t e = cudaFuncSetAttribute(adjoint_snp_bulk_kernel<3, 4>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       AdjBulkCfg<4>::SMEM);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(adjoint_snp_bulk_kernel<7, 8>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                              AdjBulkCfg<8>::SMEM);
-}
 
 
 
@@ -528,33 +322,6 @@ cudaError_t launch_exact_adjoint_sums(const int32_t* C, int64_t ldc, int RS, con
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   adjoint_sum_kernel<<<q + 1, 256, 0, s>>>(dh, wv, q, ncols, dh_accum, uT);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_adjoint_f32(const CUtensorMap* xtmap, const CUtensorMap* xhmap, const float* Xh32, int64_t ldt,
-                               int rows, int n, const float* W32, const float* Wh32, const double* G,
-                               const double* Wh, int64_t ldw, const double* GH, const SolveConsts* sc,
-                               const int8_t* shift, int q, int ncols, double h, double sigma2, double* chi2,
-                               double* dh, double* wv, double* uT, double* dh_accum, double* dy_accum,
-                               double* dy_part, DevStatus* st, int num_sms, cudaStream_t s) {
-  if (ncols <= 0) return cudaSuccess;
-  const int gb = ncols < num_sms ? ncols : num_sms;
-  if (q > 7 || rows % 128 != 0 || (ncols + gb - 1) / gb > AB_MAXC) return cudaErrorInvalidValue;
-  if (q <= 3)
-    adjoint_snp_bulk_kernel<3, 4><<<gb, 32 * (AB_CW + 1), AdjBulkCfg<4>::SMEM, s>>>(
-        *xtmap, *xhmap, rows, W32, Wh32, G, GH, sc, shift, q, ncols, h, sigma2, chi2, dh, wv, st);
-  else
-    adjoint_snp_bulk_kernel<7, 8><<<gb, 32 * (AB_CW + 1), AdjBulkCfg<8>::SMEM, s>>>(
-        *xtmap, *xhmap, rows, W32, Wh32, G, GH, sc, shift, q, ncols, h, sigma2, chi2, dh, wv, st);
-  cudaError_t e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
-  adjoint_sum_kernel<<<q + 1, 256, 0, s>>>(dh, wv, q, ncols, dh_accum, uT);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const int nchunks = adjoint_dy_chunks(ncols);
-  adjoint_dy_part_f32_kernel<<<dim3((n + 255) / 256, nchunks), 256, 0, s>>>(Xh32, ldt, Wh, shift, wv, q, n, ncols,
-                                                                            dy_part);
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  adjoint_dy_sum_kernel<<<(n + 255) / 256, 256, 0, s>>>(Wh, ldw, uT, q, n, nchunks, dy_part, dy_accum);
   return cudaGetLastError();
 }
 
@@ -623,28 +390,6 @@ cudaError_t launch_identity_cols(double* E, int n, int c0, int ncols, cudaStream
 cudaError_t launch_null_residual(const double* W, int64_t ldw, int rows, int q, const SolveConsts* sc, double* R,
                                  cudaStream_t s) {
   null_residual_kernel<<<(rows + 255) / 256, 256, 0, s>>>(W, ldw, rows, q, sc, R);
-  return cudaGetLastError();
-}
-
-// The split adjoint's hand-over to the FP64 adjoint kernels: dst = (double)src
-// over rows x ncols, plus shift[c] * col0 on column c when the solve ran on the
-// integer-shifted SNP column x - c*1 (exact undo: L^-1 and L^-T are linear and
-// col0 is the solved intercept column).
-__global__ void widen_kernel(const float* __restrict__ src, int64_t lds, double* __restrict__ dst, int64_t ldd,
-                             int rows, int ncols, const int8_t* __restrict__ shift, const double* __restrict__ col0) {
-  const int64_t total = (int64_t)rows * ncols;
-  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
-    const int c = (int)(e / rows), r = (int)(e % rows);
-    double v = (double)src[(int64_t)c * lds + r];
-    if (shift) v = fma((double)shift[c], col0[r], v);
-    dst[(int64_t)c * ldd + r] = v;
-  }
-}
-
-cudaError_t launch_widen(const float* src, int64_t lds, double* dst, int64_t ldd, int rows, int ncols,
-                         const int8_t* shift, const double* col0, cudaStream_t s) {
-  if (rows <= 0 || ncols <= 0) return cudaSuccess;
-  widen_kernel<<<1184, 256, 0, s>>>(src, lds, dst, ldd, rows, ncols, shift, col0);
   return cudaGetLastError();
 }
 

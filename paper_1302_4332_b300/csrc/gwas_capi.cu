@@ -51,7 +51,6 @@ struct gwas_ctx {
   double* Xhat = nullptr;      // n_pad x bs: X^ = L^-T X~
   double* What = nullptr;      // n_pad x (q+1): [X^_L | y^]
   double* GH = nullptr;        // (q+1)^2 Gram of What
-  float* Wh32 = nullptr;       // split contexts: What in FP32, row-major (row stride w32_stride(q))
   double* adj = nullptr;       // per-SNP chi2 (bs), dh (bs), y-weights (bs x p), uT (q), dh/dy staging (1 + n),
                                // the y-gradient's chunk partials (adjoint_dy_chunks(bs) x n)
   ExactAdjoint* exact = nullptr;  // split precisions: the adjoint's exact products (built on first use)
@@ -206,12 +205,6 @@ int ensure_adjoint(gwas_ctx* ctx) {
   if (rc != GWAS_OK) return rc;
   CK(launch_gram(ctx->What, ctx->n_pad, ctx->n_pad, nc, ctx->GH, ctx->stream));
   ctx->launches += 1;
-  if (ctx->prec != GWAS_FP64 && ctx->q <= 7) {  // the FP32 adjoint sums of the split paths
-    CK(dmalloc(&ctx->Wh32, sizeof(float) * np * w32_stride(ctx->q)));
-    CK(launch_make_w32(ctx->What, ctx->n_pad, ctx->n_pad, ctx->q, ctx->Wh32, ctx->stream));
-    CK(prepare_adjoint_f32());
-    ctx->launches += 1;
-  }
   return GWAS_OK;
 }
 
@@ -293,7 +286,7 @@ int run_block(gwas_ctx* ctx, const void* X, bool int8_input, int64_t ldx, int nc
     StageMark m(ctx, GWAS_STAGE_TRSM, ctx->stream);
     int64_t nl = 0;
     cudaEvent_t k0 = ctx->timing ? pool_event(ctx) : nullptr, k1 = ctx->timing ? pool_event(ctx) : nullptr;
-    cudaError_t e = tc::run_block(ctx->tcs, X8, ldx, ncols, ctx->stream, &nl, false, k0, k1);
+    cudaError_t e = tc::run_block(ctx->tcs, X8, ldx, ncols, ctx->stream, &nl, k0, k1);
     if (ctx->timing && e == cudaSuccess) {
       ctx->marks.push_back({GWAS_STAGE_SOLVE, k0, k1});
     } else if (ctx->timing) {
@@ -377,7 +370,7 @@ void free_all(gwas_ctx* c) {
   cudaFree(c->L); cudaFree(c->Dinv); cudaFree(c->Aop); cudaFree(c->W); cudaFree(c->G);
   cudaFree(c->sc); cudaFree(c->st); cudaFree(c->Xt); cudaFree(c->sched);
   cudaFree(c->d_b); cudaFree(c->d_se); cudaFree(c->d_status); cudaFree(c->f64_in); cudaFree(c->W32);
-  cudaFree(c->AopT); cudaFree(c->Xhat); cudaFree(c->What); cudaFree(c->GH); cudaFree(c->adj); cudaFree(c->Wh32);
+  cudaFree(c->AopT); cudaFree(c->Xhat); cudaFree(c->What); cudaFree(c->GH); cudaFree(c->adj);
   cudaFreeHost(c->h_b); cudaFreeHost(c->h_se); cudaFreeHost(c->h_status);
   if (c->tcs) tc::destroy(c->tcs);
   exact_adjoint_destroy(c->exact);

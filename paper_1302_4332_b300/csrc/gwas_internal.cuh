@@ -151,27 +151,12 @@ cudaError_t launch_make_w32(const double* W, int64_t ldw, int rows, int q, float
 
 // a11: per-SNP adjoint (chi2, d chi2/dh, y-weights), their sums over SNPs and
 // the y-gradient; FP64.  GH = What^T What, What = [X^_L | y^] = L^-T W.
-// FP32 -> FP64 with the integer shift undone (shift[c] * col0 added to column c; shift may be null).
-cudaError_t launch_widen(const float* src, int64_t lds, double* dst, int64_t ldd, int rows, int ncols,
-                         const int8_t* shift, const double* col0, cudaStream_t s);
 cudaError_t launch_adjoint(const double* Xt, const double* Xh, int64_t ldt, int rows, int n, const double* W,
                            const double* Wh, int64_t ldw, const SolveConsts* sc, const double* GH, int q,
                            int ncols, double h, double sigma2, double* chi2, double* dh, double* wv, double* uT,
                            double* dh_accum, double* dy_accum, double* dy_part, cudaStream_t s);
 // Scratch of the y-gradient: adjoint_dy_chunks(bs) x n doubles (dy_part).
 int adjoint_dy_chunks(int bs);
-// The same from the split solves' FP32 X~ and X^ of the integer-shifted SNP
-// columns (tiled maps of both with box {RED_BOX_ROWS, RED_BOX_COLS}; Xh32 the
-// X^ buffer itself), W32 / Wh32 the FP32 row-major copies of W and What
-// (row stride w32_stride(q)), G and GH their FP64 Gram matrices, shift the
-// per-SNP shifts (or null).  q <= 7; one persistent block per SM.
-cudaError_t launch_adjoint_f32(const CUtensorMap* xtmap, const CUtensorMap* xhmap, const float* Xh32, int64_t ldt,
-                               int rows, int n, const float* W32, const float* Wh32, const double* G,
-                               const double* Wh, int64_t ldw, const double* GH, const SolveConsts* sc,
-                               const int8_t* shift, int q, int ncols, double h, double sigma2, double* chi2,
-                               double* dh, double* wv, double* uT, double* dh_accum, double* dy_accum,
-                               double* dy_part, DevStatus* st, int num_sms, cudaStream_t s);
-cudaError_t prepare_adjoint_f32();
 // The split precisions' adjoint in its M^-1 form with exact integer products
 // (adjoint_exact.cu).  Set-up: W = M^-1 (n_pad x n_pad FP64, symmetric, zero
 // on the padding; the state takes ownership), What = [X^_L | y^] and W2 = W

@@ -94,8 +94,7 @@ __device__ __forceinline__ void store_tile(const float (&master)[EPI_COLS], cons
 // K-block kinds of a work unit's stage sequence.
 enum KbKind : int {
   KB_DIAG = 0,    // j == k: Aop hi/lo by TMA, B = the int8 block cast in shared memory
-  KB_LOCAL = 2,   // Aop and all of X~_jc by this CTA
-  KB_DIAG_IN = 4  // transpose solve, j == k: B = the forward solve's X~ pieces by TMA (3 products)
+  KB_LOCAL = 2    // Aop and all of X~_jc by this CTA
 };
 
 // A work unit: the tile (k, c).
@@ -104,29 +103,16 @@ struct Unit {
   int nkb;  // K-blocks in the unit's stage sequence
 };
 
-// UPPER (transpose solve X^ = L^-T X~): row panels from the last one up;
-// tile (k, c) walks j = k (its own X~ input), then P-1 .. k+1.
-template <bool UPPER = false>
-__device__ __forceinline__ Unit make_unit(int row, const TcStudy& S) {
+__device__ __forceinline__ Unit make_unit(int row) {
   Unit u;
-  if (UPPER) {
-    u.k = S.P - 1 - row;
-    u.nkb = S.P - u.k;
-  } else {
-    u.k = row;
-    u.nkb = row + 1;
-  }
+  u.k = row;
+  u.nkb = row + 1;
   return u;
 }
 
 // K-block jj of a unit: its kind, and j, the block column of Aop it multiplies
 // (forward: the diagonal block first, then 0 .. k-1).
-template <bool UPPER = false>
 __device__ __forceinline__ KbKind kb_kind(const Unit& u, int jj, int& j) {
-  if (UPPER) {
-    j = jj == 0 ? u.k : u.k + u.nkb - jj;  // k, then P-1 .. k+1
-    return jj == 0 ? KB_DIAG_IN : KB_LOCAL;
-  }
   if (jj == 0) {
     j = u.k;
     return KB_DIAG;
@@ -135,7 +121,7 @@ __device__ __forceinline__ KbKind kb_kind(const Unit& u, int jj, int& j) {
   return KB_LOCAL;
 }
 
-template <bool TF32, bool UPPER = false>
+template <bool TF32>
 __global__ void __launch_bounds__(THREADS, 1)
     trsm_tc_kernel(const __grid_constant__ TcBatch b) {
   using K = Cfg<TF32>;
@@ -211,8 +197,8 @@ __global__ void __launch_bounds__(THREADS, 1)
         TcStudy S;
         decode_tile(b, t, sidx, row, c, S);
         const TcMaps& M = b.maps[sidx];
-        const Unit u = make_unit<UPPER>(row, S);
-        if (!UPPER) {
+        const Unit u = make_unit(row);
+        {
           if (!ptx::mbar_wait(x8_empty, (x8n & 1) ^ 1, st)) break;
           ptx::mbar_arrive_expect_tx(x8_full, K::X8_BYTES);
           ptx::tma_load_2d(x8, &M.X8, x8_full, u.k * TB, c * TN);
@@ -221,7 +207,7 @@ __global__ void __launch_bounds__(THREADS, 1)
         bool ok = true;
         for (int jj = 0; jj < u.nkb && ok; ++jj) {
           int j;
-          const KbKind kind = kb_kind<UPPER>(u, jj, j);
+          const KbKind kind = kb_kind(u, jj, j);
           if (kind == KB_LOCAL) {
             if (!ptx::wait_flag(&S.flags[j * S.C + c], st)) { ok = false; break; }
             ptx::fence_proxy_async_global();
@@ -240,13 +226,8 @@ __global__ void __launch_bounds__(THREADS, 1)
               ptx::mbar_arrive_expect_tx(&full[s], 2 * K::A_BYTES + 2 * K::B_BYTES);
               ptx::tma_load_2d(sb, &M.Ahi, &full[s], kx, u.k * TB);
               ptx::tma_load_2d(sb + K::A_BYTES, &M.Alo, &full[s], kx, u.k * TB);
-              if (UPPER && kind == KB_DIAG_IN) {
-                ptx::tma_load_2d(sb + 2 * K::A_BYTES, &M.BinHi, &full[s], kx, c * TN);
-                ptx::tma_load_2d(sb + 2 * K::A_BYTES + K::B_BYTES, &M.BinLo, &full[s], kx, c * TN);
-              } else {
-                ptx::tma_load_2d(sb + 2 * K::A_BYTES, &M.Bhi, &full[s], kx, c * TN);
-                ptx::tma_load_2d(sb + 2 * K::A_BYTES + K::B_BYTES, &M.Blo, &full[s], kx, c * TN);
-              }
+              ptx::tma_load_2d(sb + 2 * K::A_BYTES, &M.Bhi, &full[s], kx, c * TN);
+              ptx::tma_load_2d(sb + 2 * K::A_BYTES + K::B_BYTES, &M.Blo, &full[s], kx, c * TN);
               ptx::mbar_arrive(&full[s]);
             }
           }
@@ -270,14 +251,14 @@ __global__ void __launch_bounds__(THREADS, 1)
         int sidx, row, c;
         TcStudy S;
         decode_tile(b, t, sidx, row, c, S);
-        const Unit u = make_unit<UPPER>(row, S);
+        const Unit u = make_unit(row);
         bool ok = true;
         int q = 0;  // K-blocks of the tile issued so far
         int a = 0;
         uint32_t d = 0, accumulate = 0;
         for (int jj = 0; jj < u.nkb && ok; ++jj) {
           int j;
-          const KbKind kind = kb_kind<UPPER>(u, jj, j);
+          const KbKind kind = kb_kind(u, jj, j);
           if (q % PROMOTE == 0) {
             // a fresh partial every PROMOTE K-blocks, alternating between the two TMEM buffers
             a = kb & 1;
@@ -308,7 +289,7 @@ __global__ void __launch_bounds__(THREADS, 1)
             release(s);
           }
           if (!ok) break;
-          const int nk = UPPER ? u.nkb : u.k + 1;  // the tile's K-blocks
+          const int nk = u.k + 1;  // the tile's K-blocks
           if (q % PROMOTE == PROMOTE - 1 || q == nk - 1) ptx::mma_commit(&part_full[a]);
           ++q;
         }
@@ -332,8 +313,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       int sidx, row, ctile;
       TcStudy S;
       decode_tile(b, t, sidx, row, ctile, S);
-      const Unit u = make_unit<UPPER>(row, S);
-      if (!UPPER) {
+      const Unit u = make_unit(row);
+      {
         const int k = u.k;
         if (!ptx::group_and(2, 64, ptx::mbar_wait(x8_full, x8n & 1, st))) break;
         bool ok = true;
@@ -409,12 +390,12 @@ __global__ void __launch_bounds__(THREADS, 1)
       int sidx, row, c;
       TcStudy S;
       decode_tile(b, t, sidx, row, c, S);
-      const Unit u = make_unit<UPPER>(row, S);
+      const Unit u = make_unit(row);
       const int k = u.k;
 #pragma unroll
       for (int i = 0; i < EPI_COLS; ++i) master[i] = 0.f;
       bool ok = true;
-      const int nk = UPPER ? u.nkb : k + 1;  // the tile's K-blocks
+      const int nk = k + 1;  // the tile's K-blocks
       const int npart = (nk + PROMOTE - 1) / PROMOTE;
       for (int jp = 0; jp < npart; ++jp, ++kb) {
         const int a = kb & 1;
@@ -1077,18 +1058,16 @@ __device__ __forceinline__ void tile_sums(const float (&master)[EPI_COLS], float
   }
 }
 
-// UP: the transposed product X^ = L^-T X~ of the adjoint form (upper
-// triangular A, B the split pieces of X~: two B pieces a stage, six stages)
-template <bool TF32, bool UP = false>
+template <bool TF32>
 struct Cfg {
-  static constexpr int STAGES = UP ? 6 : 8;
+  static constexpr int STAGES = 8;
   static constexpr int ESZ = TF32 ? 4 : 2;
   static constexpr int KCH = 64 / ESZ;
   static constexpr int KMMA = TF32 ? 8 : 16;
   static constexpr int CPB = TB / KCH;
   static constexpr int A_BYTES = TB * 64;                    // one piece of this CTA's L^-1 rows: 8 KB
   static constexpr int B_BYTES = (TN / 2) * 64;              // this CTA's half of the SNP columns: 8 KB
-  static constexpr int STAGE_BYTES = 2 * A_BYTES + (UP ? 2 : 1) * B_BYTES;  // 24 KB (32 KB)
+  static constexpr int STAGE_BYTES = 2 * A_BYTES + B_BYTES;  // 24 KB
   static constexpr int CHUNK_BYTES = 2048;
   static constexpr int STG_OFF = STAGES * STAGE_BYTES;
   static constexpr int BAR_OFF = STG_OFF + EPI_WARPS * 2 * CHUNK_BYTES;
@@ -1102,13 +1081,9 @@ struct Cfg {
 // F16 (with TF32 false): L^-1 pieces and the cast block are FP16; row r of
 // L^-1 was scaled by 1 / rscale[r] (a power of two) before the split, so the
 // epilogue multiplies its results back by rscale[r].
-// UP: the adjoint's X^ = L^-T X~ with the split pieces of L^-T (upper
-// triangular: pair row u multiplies K-blocks 2u .. P-1) and B the hi/lo
-// pieces of the forward X~ (BhiH, BloH): three products a K-step; the
-// FP32 X^ goes out through the StX map the launch sets.
-template <bool TF32, bool F16 = false, bool UP = false>
+template <bool TF32, bool F16 = false>
 __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_constant__ TcBatch b) {
-  using K = inv2::Cfg<TF32, UP>;
+  using K = inv2::Cfg<TF32>;
   constexpr int ST = K::STAGES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -1157,12 +1132,7 @@ __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_co
     for (int q = 0; q < b.nstudies; ++q) {
       ptx::prefetch_tensormap(&b.maps[q].Ahi);
       ptx::prefetch_tensormap(&b.maps[q].Alo);
-      if (UP) {
-        ptx::prefetch_tensormap(&b.maps[q].BhiH);
-        ptx::prefetch_tensormap(&b.maps[q].BloH);
-      } else {
-        ptx::prefetch_tensormap(&b.maps[q].XcH);
-      }
+      ptx::prefetch_tensormap(&b.maps[q].XcH);
     }
   }
   if (warp == 2) {
@@ -1211,11 +1181,10 @@ __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_co
         const pair2::Unit u = pair2::make_unit(row, S);
         const int arow = rank == 0 ? u.k0 : (u.paired ? u.k0 + 1 : -1);  // this CTA's row panel
         const int ycol = c * TN + (int)rank * (TN / 2);                   // this CTA's SNP columns
-        const int j0 = UP ? u.k0 : 0, j1 = UP ? S.P : u.nkb;              // the unit's K-blocks
         bool ok = true;
-        for (int j = j0; j < j1 && ok; ++j) {
-          // a block outside the triangle, or no rows: a box wholly outside reads zeros
-          const int ay = (arow >= 0 && (UP ? j >= arow : j <= arow)) ? arow * TB : -TB;
+        for (int j = 0; j < u.nkb && ok; ++j) {  // the unit's K-blocks
+          // a block above the diagonal, or no rows: a box wholly outside reads zeros
+          const int ay = (arow >= 0 && j <= arow) ? arow * TB : -TB;
           for (int h = 0; h < K::CPB; ++h, ++cnt) {
             const int s = cnt % ST;
             const uint32_t r = cnt / ST;
@@ -1229,12 +1198,7 @@ __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_co
               ptx::mbar_arrive_peer_count(fb);
             ptx::tma_load_2d_pair(sb, &M.Ahi, fb, kx, ay);
             ptx::tma_load_2d_pair(sb + K::A_BYTES, &M.Alo, fb, kx, ay);
-            if (UP) {
-              ptx::tma_load_2d_pair(sb + 2 * K::A_BYTES, &M.BhiH, fb, kx, ycol);
-              ptx::tma_load_2d_pair(sb + 2 * K::A_BYTES + K::B_BYTES, &M.BloH, fb, kx, ycol);
-            } else {
-              ptx::tma_load_2d_pair(sb + 2 * K::A_BYTES, &M.XcH, fb, kx, ycol);
-            }
+            ptx::tma_load_2d_pair(sb + 2 * K::A_BYTES, &M.XcH, fb, kx, ycol);
           }
         }
         if (!ok) break;
@@ -1257,7 +1221,7 @@ __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_co
         TcStudy S;
         decode_tile(b, t, sidx, row, c, S);
         const pair2::Unit u = pair2::make_unit(row, S);
-        const int nkb = UP ? S.P - u.k0 : u.nkb;
+        const int nkb = u.nkb;
         bool ok = true;
         int a = 0;
         uint32_t d = 0, accumulate = 0;
@@ -1284,10 +1248,9 @@ __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_co
               const uint32_t off = kk * K::KMMA * K::ESZ;
               const uint64_t ahi = ptx::sdesc_k64(base + off);
               const uint64_t alo = ptx::sdesc_k64(base + K::A_BYTES + off);
-              const uint64_t bx = ptx::sdesc_k64(base + 2 * K::A_BYTES + off);  // B, or B's hi piece
+              const uint64_t bx = ptx::sdesc_k64(base + 2 * K::A_BYTES + off);
               ptx::mma_pair<TF32>(d, alo, bx, idesc, accumulate);
               accumulate = 1;
-              if (UP) ptx::mma_pair<TF32>(d, ahi, ptx::sdesc_k64(base + 2 * K::A_BYTES + K::B_BYTES + off), idesc, 1);
               ptx::mma_pair<TF32>(d, ahi, bx, idesc, 1);
             }
             ptx::mma_commit_pair(&empty[s], BOTH);
@@ -1322,7 +1285,7 @@ __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_co
       const bool has = leader || u.paired;  // this CTA has a tile
       const int k = u.k0 + (int)rank;
       uint8_t* stg = smem + K::STG_OFF + e * 2 * K::CHUNK_BYTES;  // this warp's 4 KB of staging
-      if (!UP && S.red && has) {
+      if (S.red && has) {
         // fused sums: this warp's 32 rows of W into its staging (read at the
         // tile's end; the copies land while the partials are added)
         if (gq > 0) {  // stores of an earlier tile still reading the staging buffers
@@ -1337,7 +1300,7 @@ __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_co
 #pragma unroll
       for (int i = 0; i < EPI_COLS; ++i) master[i] = 0.f;
       bool ok = true;
-      const int nkb = UP ? S.P - u.k0 : u.nkb;
+      const int nkb = u.nkb;
       const int nparts = nkb > 1 ? nkb - 1 : 1;  // K-blocks 0 and 1 share a partial
       for (int pp = 0; pp < nparts && ok; ++pp) {
         const int a = kb & 1;
@@ -1361,14 +1324,13 @@ __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_co
       }
       if (!ok) break;
       if (!has) continue;
-      // X~ of this CTA's tile to HBM by TMA stores of shared-memory chunks (and,
-      // for the transpose solve of the adjoint form, its hi/lo pieces)
+      // X~ of this CTA's tile to HBM by TMA stores of shared-memory chunks
       const TcMaps& M = b.maps[sidx];
       const int r0 = k * TB + 32 * lq;
       const int c0 = c * TN + chalf * EPI_COLS;
       // F16: this thread's row back to the scale of L^-1 (exact: a power of two)
       const float rs = F16 ? __ldg(S.rscale + r0 + lane) : 1.f;
-      if (!UP && S.red) {
+      if (S.red) {
         // the per-SNP sums of Listing 1 in place of the store
         ptx::cp_async_wait_all();  // this lane's W row
         __syncwarp();
@@ -1402,35 +1364,6 @@ __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_co
         if (lane == 0) {
           ptx::tma_store_2d(&M.StX, buf, r0, c0 + q * CC);
           ptx::bulk_commit();
-        }
-      }
-      if (b.pieces) {
-#pragma unroll
-        for (int q = 0; q < EPI_COLS / CC; ++q) {
-          uint8_t* buf = next_buf();
-#pragma unroll
-          for (int i = 0; i < CC; ++i) {
-            const float x = master[q * CC + i];
-            if constexpr (TF32) {
-              reinterpret_cast<float*>(buf)[i * 32 + lane] = x - __uint_as_float(tf32_trunc_bits(x));
-            } else {
-              const __nv_bfloat16 hi = __float2bfloat16_rn(x);
-              reinterpret_cast<__nv_bfloat16*>(buf)[i * 32 + lane] = hi;
-              reinterpret_cast<__nv_bfloat16*>(buf + 1024)[i * 32 + lane] =
-                  __float2bfloat16_rn(x - __bfloat162float(hi));
-            }
-          }
-          ptx::fence_proxy_async_shared();
-          __syncwarp();
-          if (lane == 0) {
-            if constexpr (TF32) {
-              ptx::tma_store_2d(&M.StLo, buf, r0, c0 + q * CC);
-            } else {
-              ptx::tma_store_2d(&M.StHi, buf, r0, c0 + q * CC);
-              ptx::tma_store_2d(&M.StLo, buf + 1024, r0, c0 + q * CC);
-            }
-            ptx::bulk_commit();
-          }
         }
       }
     }
@@ -1483,20 +1416,11 @@ static cudaError_t set_attrs(bool clusters) {
   if ((e = cudaFuncSetAttribute(trsm_tc_pair_mma_kernel<TF32>, A, pair2::Cfg<TF32>::SMEM)) != cudaSuccess) return e;
   if (!TF32 && (e = cudaFuncSetAttribute(trsm_tc_inv_kernel<false, true>, A, inv2::Cfg<false>::SMEM)) != cudaSuccess)
     return e;
-  if ((e = cudaFuncSetAttribute(trsm_tc_inv_kernel<TF32, false, true>, A, inv2::Cfg<TF32, true>::SMEM)) !=
-      cudaSuccess)
-    return e;
   return cudaFuncSetAttribute(trsm_tc_inv_kernel<TF32>, A, inv2::Cfg<TF32>::SMEM);
 }
 
 cudaError_t set_kernel_attrs(bool tf32, bool clusters) {
   return tf32 ? set_attrs<true>(clusters) : set_attrs<false>(clusters);
-}
-
-cudaError_t set_upper_attr(bool tf32) {
-  constexpr cudaFuncAttribute A = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  return tf32 ? cudaFuncSetAttribute(trsm_tc_kernel<true, true>, A, Cfg<true>::SMEM)
-              : cudaFuncSetAttribute(trsm_tc_kernel<false, true>, A, Cfg<false>::SMEM);
 }
 
 template <bool TF32>
@@ -1542,28 +1466,6 @@ cudaError_t launch_solve(bool tf32, TileMode mode, const TcBatch& b, int num_sms
     trsm_tc_kernel<true><<<grid, THREADS, Cfg<true>::SMEM, s>>>(b);
   else
     trsm_tc_kernel<false><<<grid, THREADS, Cfg<false>::SMEM, s>>>(b);
-  return cudaGetLastError();
-}
-
-template <bool TF32>
-static cudaError_t launch_inv_up(const TcBatch& b, int max_clusters, cudaStream_t s) {
-  const int ncl = b.ntiles < max_clusters ? b.ntiles : max_clusters;
-  cudaLaunchAttribute attr[1];
-  cudaLaunchConfig_t cfg = pair_config<TF32>(attr, 2 * ncl, s, TILES_INVERSE);
-  cfg.dynamicSmemBytes = inv2::Cfg<TF32, true>::SMEM;
-  return cudaLaunchKernelEx(&cfg, trsm_tc_inv_kernel<TF32, false, true>, b);
-}
-
-cudaError_t launch_inverse_upper(bool tf32, const TcBatch& b, int max_clusters, cudaStream_t s) {
-  const cudaError_t e = tf32 ? launch_inv_up<true>(b, max_clusters, s) : launch_inv_up<false>(b, max_clusters, s);
-  return e != cudaSuccess ? e : cudaGetLastError();
-}
-
-cudaError_t launch_upper(bool tf32, const TcBatch& b, int grid, cudaStream_t s) {
-  if (tf32)
-    trsm_tc_kernel<true, true><<<grid, THREADS, Cfg<true>::SMEM, s>>>(b);
-  else
-    trsm_tc_kernel<false, true><<<grid, THREADS, Cfg<false>::SMEM, s>>>(b);
   return cudaGetLastError();
 }
 

@@ -41,13 +41,11 @@ cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_p
                    TileMode mode = TILES_AUTO);
 
 // X~ = L^-1 X for ncols <= bs int8 columns (X 16-byte aligned, ldx % 16 == 0).
-// The FP32 result is left in xt_f32() with leading dimension xt_ld().
-// pieces: the hi/lo pieces of X~ are also stored (the substitution modes
-// always store them; the inverse form only when asked: the transpose solve
-// of the adjoint form reads them).
+// The FP32 result is left in xt_f32() with leading dimension xt_ld() (the
+// inverse form with the sums in its epilogue leaves partials() instead).
 // ev0 / ev1 (optional): recorded on s right before and after the solve kernel.
 cudaError_t run_block(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaStream_t s, int64_t* launches,
-                      bool pieces = false, cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
+                      cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
 
 // The batching form: one persistent launch over several studies (each with its
 // own operator and buffers; all BF16 or all TF32).  ts[i] solves ncols[i]
@@ -64,22 +62,11 @@ cudaError_t batch_launch(TcBatchState* B, TcState* const* ts, cudaStream_t s, in
 void batch_destroy(TcBatchState* B);
 constexpr int kMaxBatchStudies = 8;
 
-// The transpose solve of the adjoint form: X^ = L^-T X~ on the tensor cores,
-// X~ being the last run_block's result (its FP32 value and split pieces).
-// ensure_transpose splits the FP64 transpose block operator AopT (row panel k
-// = [D_k^-T at block k | -D_k^-T L_jk^T for j > k], row-major) once; the
-// result lands in xhat_f32() (leading dimension xt_ld()).
-cudaError_t ensure_transpose(TcState* t, const double* AopT, cudaStream_t s, int64_t* launches);
-cudaError_t run_transpose(TcState* t, int ncols, cudaStream_t s, int64_t* launches);
-const float* xhat_f32(const TcState* t);
-const CUtensorMap* xhat_reduce_map(const TcState* t);  // xhat_f32() as the reduction's tiled map
-
 const float* xt_f32(const TcState* t);
 // Inverse form: the per-SNP sums of x~ with W = [X~_L | Y~] (FP32, row-major,
 // row stride ws = 4 or 8, nw <= 8 columns) and of x~ with itself formed by the
-// solve's epilogue, which then stores no X~ (a block solved for the adjoint
-// still stores it).  Other modes or sizes: no change (the sums stay a separate
-// pass over xt_f32()).
+// solve's epilogue, which then stores no X~.  Other modes or sizes: no change
+// (the sums stay a separate pass over xt_f32()).
 cudaError_t set_reductions(TcState* t, const float* w32, int ws, int nw);
 // Precision studies (inverse form): zeroes the lo piece of L^-1, so that the
 // solve multiplies by its hi piece alone.  Other modes: cudaErrorInvalidValue.

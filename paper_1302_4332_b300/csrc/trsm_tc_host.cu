@@ -1,5 +1,5 @@
 // Host side of the split-precision solve (a4 split copies, a6, a10's batched
-// launch, a11's transpose solve): per-study state, set-up (the split block
+// launch): per-study state, set-up (the split block
 // operator, the pair form, L^-1 for the inverse form), tensor maps, tile
 // orders, and the small set-up and pre-pass kernels.  The solve kernels
 // themselves are in trsm_tc.cu.
@@ -428,16 +428,6 @@ struct TcState {
   CUtensorMap mAhi, mAlo, mBhi, mBlo, mBhiH, mBloH;
   CUtensorMap mStX, mStHi, mStLo;  // pair product's epilogue stores
   CUtensorMap mRed;                // the reduction's view of the FP32 X~ (box RED_BOX_ROWS x RED_BOX_COLS)
-  CUtensorMap mRedH;               // the same over the transpose solve's X^
-  // transpose solve (the adjoint form): the transpose block operator split hi/lo,
-  // X^ = L^-T X~ in FP32 + pieces, and their maps
-  void* ahiT = nullptr;
-  void* aloT = nullptr;
-  float* xh32 = nullptr;
-  void* xhhi = nullptr;
-  void* xhlo = nullptr;
-  CUtensorMap mAhiT, mAloT, mBhiT, mBloT;
-  CUtensorMap mStXh;  // inverse form: the FP32 X^ by the epilogue's store chunks
   void* xc = nullptr;  // inverse form: the cast block x - c_i (n_pad x bs, BF16, FP32 or FP16)
   bool f16 = false;           // inverse form with FP16 pieces of L^-1 (row-scaled) and an FP16 cast block
   float* rscale = nullptr;    // f16: per-row scale of L^-1 (n_pad)
@@ -487,7 +477,7 @@ cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_p
   if (split == SPLIT_F16 && mode != TILES_AUTO && mode != TILES_INVERSE) return cudaErrorInvalidValue;
   TcState* t = new TcState;
   t->tf32 = (split == SPLIT_TF32);
-  t->f16 = (split == SPLIT_F16);  // otherwise BF16 (the transpose solve of an FP16 context runs in BF16)
+  t->f16 = (split == SPLIT_F16);  // otherwise BF16
   t->n = n;
   t->n_pad = n_pad;
   t->bs = bs;
@@ -692,7 +682,7 @@ static cudaError_t launch_kernel(bool tf32, TileMode mode, const TcBatch& b, int
 }
 
 cudaError_t run_block(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaStream_t s, int64_t* launches,
-                      bool pieces, cudaEvent_t ev0, cudaEvent_t ev1) {
+                      cudaEvent_t ev0, cudaEvent_t ev1) {
   if (ncols <= 0) return cudaSuccess;
   TcBatch b;
   memset(&b, 0, sizeof b);
@@ -712,8 +702,6 @@ cudaError_t run_block(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaS
   b.ntiles = unit_rows(t) * b.s0.C;
   b.counter = t->sched;
   b.st = t->st;
-  b.pieces = pieces ? 1 : 0;
-  if (pieces) b.s0.red = nullptr;  // the adjoint reads X~ itself
   t->red_last = b.s0.red != nullptr;
   const bool inv = t->mode == TILES_INVERSE;
   if (inv || (t->strip_group > 0 && t->strip_group < b.s0.C)) {
@@ -789,169 +777,6 @@ static cudaError_t build_inverse(TcState* t, const double* Aop, cudaStream_t s, 
   return e;
 }
 
-// ------------------------------------------------------ transpose solve (adjoint)
-// The inverse form's transpose product reads L^-T: the pieces of L^-1, transposed
-// (a split commutes with the transpose).  32 x 32 tiles through shared memory.
-template <typename T>
-__global__ void transpose_square_kernel(const T* __restrict__ src, T* __restrict__ dst, int n) {
-  __shared__ T tile[32][33];
-  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) tile[ty + 8 * i][tx] = src[(int64_t)(r0 + ty + 8 * i) * n + c0 + tx];
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < 4; ++i) dst[(int64_t)(c0 + ty + 8 * i) * n + r0 + tx] = tile[tx][ty + 8 * i];
-}
-
-// The FP16 form's row-scaled pieces back to values (rscale[r] (hi + lo): exact
-// in FP32), transposed and split again as BF16 hi + lo: the operand pieces of
-// the transpose product, which takes the forward solve's BF16 X~ pieces as B.
-__global__ void transpose_resplit_f16_kernel(const __half* __restrict__ hi, const __half* __restrict__ lo,
-                                             const float* __restrict__ rscale, __nv_bfloat16* __restrict__ thi,
-                                             __nv_bfloat16* __restrict__ tlo, int n) {
-  __shared__ float tile[32][33];
-  const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
-  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const int r = r0 + ty + 8 * i;
-    const int64_t idx = (int64_t)r * n + c0 + tx;
-    tile[ty + 8 * i][tx] = __ldg(rscale + r) * (__half2float(hi[idx]) + __half2float(lo[idx]));
-  }
-  __syncthreads();
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    const float v = tile[tx][ty + 8 * i];
-    const __nv_bfloat16 h = __float2bfloat16_rn(v);
-    const int64_t idx = (int64_t)(c0 + ty + 8 * i) * n + r0 + tx;
-    thi[idx] = h;
-    tlo[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
-  }
-}
-
-cudaError_t ensure_transpose(TcState* t, const double* AopT, cudaStream_t s, int64_t* launches) {
-  if (t->ahiT) return cudaSuccess;
-  const size_t esz = t->tf32 ? 4 : 2;
-  const size_t np = (size_t)t->n_pad, n2 = np * np;
-  cudaError_t e;
-  if (t->mode == TILES_INVERSE) {
-    // X^ = L^-T X~ as a product with the transposed pieces of L^-1 (BF16 ones
-    // for the FP16 form: the forward X~ pieces are BF16)
-    if ((e = cudaMalloc(&t->ahiT, esz * n2)) != cudaSuccess || (e = cudaMalloc(&t->aloT, esz * n2)) != cudaSuccess ||
-        (e = cudaMalloc(&t->xh32, sizeof(float) * np * t->bs)) != cudaSuccess)
-      return e;
-    const dim3 grid((unsigned)(np / 32), (unsigned)(np / 32));
-    int nl = 2;
-    if (t->f16) {
-      transpose_resplit_f16_kernel<<<grid, dim3(32, 8), 0, s>>>(
-          static_cast<const __half*>(t->ahi), static_cast<const __half*>(t->alo), t->rscale,
-          static_cast<__nv_bfloat16*>(t->ahiT), static_cast<__nv_bfloat16*>(t->aloT), (int)np);
-      nl = 1;
-    } else if (t->tf32) {
-      transpose_square_kernel<float><<<grid, dim3(32, 8), 0, s>>>(static_cast<const float*>(t->ahi),
-                                                                  static_cast<float*>(t->ahiT), (int)np);
-      transpose_square_kernel<float><<<grid, dim3(32, 8), 0, s>>>(static_cast<const float*>(t->alo),
-                                                                  static_cast<float*>(t->aloT), (int)np);
-    } else {
-      transpose_square_kernel<uint16_t><<<grid, dim3(32, 8), 0, s>>>(static_cast<const uint16_t*>(t->ahi),
-                                                                     static_cast<uint16_t*>(t->ahiT), (int)np);
-      transpose_square_kernel<uint16_t><<<grid, dim3(32, 8), 0, s>>>(static_cast<const uint16_t*>(t->alo),
-                                                                     static_cast<uint16_t*>(t->aloT), (int)np);
-    }
-    *launches += nl;
-    if ((e = cudaGetLastError()) != cudaSuccess) return e;
-    const CUtensorMapDataType dt = t->tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-    const uint32_t kch = t->tf32 ? Cfg<true>::KCH : Cfg<false>::KCH;
-    if ((e = make_map(t->encode, &t->mAhiT, dt, t->ahiT, np, np, esz * np, kch, TB, true)) != cudaSuccess ||
-        (e = make_map(t->encode, &t->mAloT, dt, t->aloT, np, np, esz * np, kch, TB, true)) != cudaSuccess ||
-        (e = make_map(t->encode, &t->mStXh, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, t->xh32, np, t->bs, 4 * np, 32,
-                      inv2::ST_COLS, false)) != cudaSuccess ||
-        (e = make_map(t->encode, &t->mRedH, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, t->xh32, np, t->bs, 4 * np,
-                      RED_BOX_ROWS, RED_BOX_COLS, false)) != cudaSuccess)
-      return e;
-    return cudaSuccess;
-  }
-  if ((e = cudaMalloc(&t->ahiT, esz * n2)) != cudaSuccess || (e = cudaMalloc(&t->aloT, esz * n2)) != cudaSuccess ||
-      (e = cudaMalloc(&t->xh32, sizeof(float) * np * t->bs)) != cudaSuccess ||
-      (!t->tf32 && (e = cudaMalloc(&t->xhhi, 2 * np * t->bs)) != cudaSuccess) ||
-      (e = cudaMalloc(&t->xhlo, esz * np * t->bs)) != cudaSuccess)
-    return e;
-  if (t->tf32)
-    split_aop_kernel<true><<<1184, 256, 0, s>>>(AopT, (int64_t)n2, t->ahiT, t->aloT);
-  else
-    split_aop_kernel<false><<<1184, 256, 0, s>>>(AopT, (int64_t)n2, t->ahiT, t->aloT);
-  ++*launches;
-  if ((e = cudaGetLastError()) != cudaSuccess) return e;
-  const CUtensorMapDataType dt = t->tf32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_BFLOAT16;
-  const uint32_t kch = t->tf32 ? Cfg<true>::KCH : Cfg<false>::KCH;
-  const void* bhi = t->tf32 ? static_cast<const void*>(t->xh32) : t->xhhi;
-  if ((e = make_map(t->encode, &t->mAhiT, dt, t->ahiT, np, np, esz * np, kch, TB, true)) != cudaSuccess ||
-      (e = make_map(t->encode, &t->mAloT, dt, t->aloT, np, np, esz * np, kch, TB, true)) != cudaSuccess ||
-      (e = make_map(t->encode, &t->mBhiT, dt, bhi, np, t->bs, esz * np, kch, TN, true)) != cudaSuccess ||
-      (e = make_map(t->encode, &t->mBloT, dt, t->xhlo, np, t->bs, esz * np, kch, TN, true)) != cudaSuccess ||
-      (e = make_map(t->encode, &t->mRedH, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, t->xh32, np, t->bs, 4 * np, RED_BOX_ROWS,
-                    RED_BOX_COLS, false)) != cudaSuccess)
-    return e;
-  return set_upper_attr(t->tf32);
-}
-
-cudaError_t run_transpose(TcState* t, int ncols, cudaStream_t s, int64_t* launches) {
-  if (ncols <= 0) return cudaSuccess;
-  if (!t->ahiT || ncols > t->bs) return cudaErrorInvalidValue;
-  TcBatch b;
-  memset(&b, 0, sizeof b);
-  const int C = (ncols + TN - 1) / TN;
-  cudaError_t e = cudaMemsetAsync(t->sched, 0, 128 + sizeof(int) * (size_t)t->P * C, s);
-  if (e != cudaSuccess) return e;
-  if (t->mode == TILES_INVERSE) {
-    // row-panel pairs in their natural order: pair row 0 (P K-blocks) is the longest
-    TcStudy& S = b.s0;
-    S.P = t->P;
-    S.C = C;
-    S.ncols = ncols;
-    S.n = t->n;
-    S.ldt = t->ldt;
-    b.maps[0].Ahi = t->mAhiT;
-    b.maps[0].Alo = t->mAloT;
-    b.maps[0].BhiH = t->mBhiH;  // the forward solve's X~ pieces
-    b.maps[0].BloH = t->mBloH;
-    b.maps[0].StX = t->mStXh;
-    b.nstudies = 1;
-    b.ntiles = unit_rows(t) * C;
-    b.counter = t->sched;
-    b.st = t->st;
-    ++*launches;
-    return launch_inverse_upper(t->tf32, b, t->max_clusters, s);
-  }
-  TcStudy& S = b.s0;
-  S.P = t->P;
-  S.C = C;
-  S.ncols = ncols;
-  S.n = t->n;
-  S.shift = nullptr;
-  S.flags = reinterpret_cast<int*>(t->sched + 32);
-  S.xt32 = t->xh32;
-  S.bhi = t->xhhi;
-  S.blo = t->xhlo;
-  S.ldt = t->ldt;
-  b.maps[0].Ahi = t->mAhiT;
-  b.maps[0].Alo = t->mAloT;
-  b.maps[0].Bhi = t->mBhiT;
-  b.maps[0].Blo = t->mBloT;
-  b.maps[0].BinHi = t->mBhi;  // the forward solve's X~ pieces
-  b.maps[0].BinLo = t->mBlo;
-  b.nstudies = 1;
-  b.ntiles = t->P * C;
-  b.counter = t->sched;
-  b.st = t->st;
-  const int grid = b.ntiles < t->num_sms ? b.ntiles : t->num_sms;
-  ++*launches;
-  return launch_upper(t->tf32, b, grid, s);
-}
-
-const float* xhat_f32(const TcState* t) { return t->xh32; }
-
 cudaError_t set_reductions(TcState* t, const float* w32, int ws, int nw) {
   if (t->red || t->mode != TILES_INVERSE || nw < 1 || nw > 8 || (ws != 4 && ws != 8) || ws < nw) return cudaSuccess;
   cudaError_t e = cudaMalloc(&t->red, sizeof(float) * (size_t)t->P * 4 * (nw + 1) * t->bs);
@@ -962,7 +787,7 @@ cudaError_t set_reductions(TcState* t, const float* w32, int ws, int nw) {
   return cudaSuccess;
 }
 cudaError_t drop_lo_piece(TcState* t, cudaStream_t s) {
-  if (t->mode != TILES_INVERSE || t->ahiT) return cudaErrorInvalidValue;
+  if (t->mode != TILES_INVERSE) return cudaErrorInvalidValue;
   const size_t esz = t->tf32 ? 4 : 2;
   return cudaMemsetAsync(t->alo, 0, esz * (size_t)t->n_pad * t->n_pad, s);
 }
@@ -1154,7 +979,6 @@ void batch_destroy(TcBatchState* B) {
 
 const float* xt_f32(const TcState* t) { return t->xt32; }
 const CUtensorMap* xt_reduce_map(const TcState* t) { return &t->mRed; }
-const CUtensorMap* xhat_reduce_map(const TcState* t) { return &t->mRedH; }
 const int8_t* shift_of(const TcState* t) { return t->center ? t->shift : nullptr; }
 int64_t xt_ld(const TcState* t) { return t->ldt; }
 TileMode tile_mode(const TcState* t) { return t->mode; }
@@ -1172,12 +996,7 @@ void launch_shape(const TcState* t, int* ctas, int* cluster_size) {
 
 void destroy(TcState* t) {
   if (!t) return;
-  cudaFree(t->ahiT);
-  cudaFree(t->aloT);
-  cudaFree(t->xh32);
   cudaFree(t->red);
-  cudaFree(t->xhhi);
-  cudaFree(t->xhlo);
   cudaFree(t->ahi);
   cudaFree(t->alo);
   cudaFree(t->xt32);

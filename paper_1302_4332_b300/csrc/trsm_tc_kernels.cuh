@@ -69,7 +69,6 @@ struct TcMaps {
   CUtensorMap Ahi, Alo, Bhi, Blo, X8;
   CUtensorMap BhiH, BloH, X8H;  // half-width boxes (128 SNP columns) for the pair modes
   CUtensorMap StX, StHi, StLo;  // pair product's epilogue stores: FP32 X~, hi piece (BF16), lo piece
-  CUtensorMap BinHi, BinLo;     // transpose solve: X~ pieces of the forward solve (its diagonal-block input)
   CUtensorMap XcH;              // inverse form: the cast block x - c_i (BF16/FP32), half-width boxes
 };
 
@@ -83,7 +82,6 @@ struct TcBatch {
   const TcStudy* studies;     // device copies of the studies when order != null (null: s0 alone)
   const uint32_t* order;      // tile t -> (study << 28) | (k << 14) | c
   int nstudies, ntiles;
-  int pieces;                 // inverse form: also store the hi/lo pieces of X~ (the adjoint's input)
   unsigned int* counter;
   DevStatus* st;
 };
@@ -112,20 +110,14 @@ cudaError_t make_map(EncodeTiledFn enc, CUtensorMap* m, CUtensorMapDataType dt, 
 
 // Launch entry points of the kernels (trsm_tc.cu).
 // Opt-in shared memory of the forward kernels (clusters: also the pair and
-// inverse-form kernels) and of the transpose solve.
-// f16: the inverse form's FP16 variant (TILES_INVERSE only, tf32 false).
+// inverse-form kernels).  f16: the inverse form's FP16 variant (TILES_INVERSE
+// only, tf32 false).
 cudaError_t set_kernel_attrs(bool tf32, bool clusters);
-cudaError_t set_upper_attr(bool tf32);
 // Co-resident 2-CTA clusters of a cluster-mode kernel (one CTA per SM).
 cudaError_t query_clusters(bool tf32, TileMode mode, int num_sms, int* out, bool f16 = false);
 // One launch over b.ntiles work units (tiles, or row-panel pairs of a strip).
 cudaError_t launch_solve(bool tf32, TileMode mode, const TcBatch& b, int num_sms, int max_clusters,
                          cudaStream_t s, bool f16 = false);
-// The transpose solve of the adjoint form (single CTAs, grid CTAs).
-cudaError_t launch_upper(bool tf32, const TcBatch& b, int grid, cudaStream_t s);
-// The same as the product with the split L^-T (inverse form; 2-CTA clusters
-// over row-panel pairs, units handed out in the order of b.order).
-cudaError_t launch_inverse_upper(bool tf32, const TcBatch& b, int max_clusters, cudaStream_t s);
 
 }  // namespace tc
 }  // namespace gwas
