@@ -72,6 +72,9 @@ def parse_args():
                     help="inverse form: the per-SNP sums as a separate pass over X~ instead of inside the solve")
     ap.add_argument("--fp64-steps", type=int, default=None,
                     help="steps of the fp64 path when a split path is the headline (default 1)")
+    ap.add_argument("--disk-tier-gb", type=float, default=0.0,
+                    help="also run the out-of-core forms from files of about this many GB on the local disk "
+                         "(written, synced and dropped from the page cache first); not part of the default run")
     return ap.parse_args()
 
 
@@ -430,7 +433,8 @@ def measure_forms(args, out):
     gls = [gw.GLS(s["Phi"], s["XL"], s["y"], 0.6, 1.0, precision="bf16x3", bs=4096) for s in studies]
     setup_s = time.time() - t0
     with gw.GLSBatch(gls) as B:
-        cols, order, tuned = B.autotune(reps=2)
+        tune = B.autotune_ex(reps=3)
+        cols, order, tuned = tune["cols"], tune["order"], tune["snps_per_s"]
         blocks = [torch.from_numpy(np.ascontiguousarray(gwas_synth.dosages(n, 0, cols, study=i).T)).to(dev).T
                   for i, n in enumerate(STUDY_SIZES)]
         for _ in range(2):
@@ -447,12 +451,26 @@ def measure_forms(args, out):
         ev1.record()
         torch.cuda.synchronize()
         t = ev0.elapsed_time(ev1) / 1e3
+        rate = len(STUDY_SIZES) * cols * steps / t
+        # k blocks of every study per graph replay (k batched launches captured together)
+        kk = 4
+        B.solve_k([blocks] * kk)
+        B.synchronize()
+        ev0.record()
+        for _ in range(max(1, steps // kk)):
+            B.solve_k([blocks] * kk)
+        B.synchronize()
+        ev1.record()
+        torch.cuda.synchronize()
+        tk = ev0.elapsed_time(ev1) / 1e3
         forms["batch"] = dict(
             workload="8 studies n=" + ",".join(map(str, STUDY_SIZES)) + ", p=4, bf16x3, int8 dosages",
-            snps_per_s=len(STUDY_SIZES) * cols * steps / t, ms_per_step=1e3 * t / steps,
-            snps_per_step=len(STUDY_SIZES) * cols, autotuned_cols_per_study=cols,
-            autotuned_order=("row-panel interleaved" if order == 0 else "study after study"),
-            autotune_snps_per_s=tuned, gpu_launches=B.kernel_launches - l0, steps=steps, setup_s=setup_s,
+            snps_per_s=rate, ms_per_step=1e3 * t / steps,
+            snps_per_step=len(STUDY_SIZES) * cols, autotuned=tune,
+            autotune_snps_per_s=tuned, autotune_over_timed=tuned / rate,
+            k_block_replay=dict(blocks_per_study_per_replay=kk,
+                                snps_per_s=len(STUDY_SIZES) * cols * kk * max(1, steps // kk) / tk),
+            gpu_launches=B.kernel_launches - l0, steps=steps, setup_s=setup_s,
             algorithmic_tflops=sum(float(n) * n for n in STUDY_SIZES) * cols * steps / t / 1e12)
         # --- the same batch out of core: each study's dosages in its own file (its block
         # written REPS times), streamed disk -> pinned host (a reader thread per study) -> GPU
@@ -568,6 +586,115 @@ def measure_forms(args, out):
     return forms
 
 
+def _drop_cached(path):
+    """Flushes a file to the device and drops its pages from the page cache,
+    so that the next reads come from the disk (the reads themselves still go
+    through the page cache: no O_DIRECT)."""
+    fd = os.open(path, os.O_RDONLY)
+    try:
+        os.fsync(fd)
+        os.posix_fadvise(fd, 0, 0, os.POSIX_FADV_DONTNEED)
+    finally:
+        os.close(fd)
+
+
+def _write_repeated(path, raw, reps):
+    with open(path, "wb") as f:
+        for _ in range(reps):
+            f.write(raw)
+        f.flush()
+        os.fdatasync(f.fileno())
+
+
+def measure_disk_tier(args, out):
+    """The out-of-core forms at the scale the local disk holds (Sec. 3.1's
+    disk -> main memory -> GPU, results written back): one study's dosage file
+    of about --disk-tier-gb GB (the 8 resident blocks repeated), solved disk to
+    disk with checkpoints; then the 8-study batching workload from 8 files of
+    that total size (each study's first block repeated).  Files are written,
+    synced and dropped from the page cache before each timed read."""
+    import shutil
+    import tempfile
+    import torch
+    import gwas_synth
+    import paper_1302_4332_b300 as gw
+    w, s = out["w"], out["s"]
+    n, bs, p = w["n"], w["bs"], w["p"]
+    res = {}
+    root = tempfile.mkdtemp(prefix="gwas_disk_", dir=os.environ.get("TMPDIR", "/tmp"))
+    try:
+        free = shutil.disk_usage(root).free
+        target = min(args.disk_tier_gb * 1e9, 0.8 * free)
+        raw = b"".join(np.ascontiguousarray(X.T).tobytes() for X in out["blocks_h"])  # 8 blocks, column-major
+        reps = max(1, int(target // len(raw)))
+        m = reps * len(out["blocks_h"]) * bs
+        path = os.path.join(root, "dosages.bin")
+        t0 = time.perf_counter()
+        _write_repeated(path, raw, reps)
+        write_s = time.perf_counter() - t0
+        _drop_cached(path)
+        rpath = os.path.join(root, "results.bin")
+        head_path = "f16x2" if "f16x2" in gw.BUILT_PRECISIONS else "fp64"
+        with gw.GLS(s["Phi"], s["XL"], s["y"], w["h"], w["sigma2"], precision=head_path, bs=bs) as g:
+            t1 = time.perf_counter()
+            done = g.solve_file_out(path, m, rpath)
+            t_run = time.perf_counter() - t1
+            # check: the file's first and last block against the in-memory solve of the same columns
+            head, b_all, se_all, st_all = gw.read_results(rpath)
+            nb = m // bs
+            checks = []
+            for blk in (0, nb - 1):
+                b_ref, se_ref, st_ref = g.solve_block(out["blocks_h"][blk % len(out["blocks_h"])])
+                sl = slice(blk * bs, (blk + 1) * bs)
+                checks.append(bool(np.array_equal(b_all[:, sl], b_ref) and np.array_equal(se_all[:, sl], se_ref)
+                                   and np.array_equal(st_all[sl], st_ref)))
+        res["one_study_disk_to_disk"] = dict(
+            workload=f"n={n}, p={p}, {head_path}, m={m} SNPs ({m * n / 1e9:.1f} GB int8 file, the 8 resident "
+                     f"blocks repeated {reps} times)", snps=done, seconds=t_run, snps_per_s=done / t_run,
+            read_gbs=done * n / t_run / 1e9, results_gb=(64 + done * (16 * p + 8)) / 1e9,
+            file_write_gbs=m * n / write_s / 1e9,
+            page_cache="dropped before the run (fsync + POSIX_FADV_DONTNEED); reads through the page cache, "
+                       "not O_DIRECT",
+            matches_in_memory_solve=all(checks))
+        del b_all, se_all, st_all
+        os.remove(path)
+        os.remove(rpath)
+        if os.path.exists(rpath + ".ckpt"):
+            os.remove(rpath + ".ckpt")
+        # the batching workload, 8 studies of uneven n, from files of the same total size
+        studies = [gwas_synth.study(ni, 4, 2000, 0.6, 1.0, study_id=i) for i, ni in enumerate(STUDY_SIZES)]
+        gls = [gw.GLS(st_["Phi"], st_["XL"], st_["y"], 0.6, 1.0, precision="bf16x3", bs=4096) for st_ in studies]
+        cols = 4096
+        per = int(target // sum(STUDY_SIZES) // cols) * cols  # SNPs per study
+        paths = []
+        t0 = time.perf_counter()
+        for i, ni in enumerate(STUDY_SIZES):
+            blk = np.ascontiguousarray(gwas_synth.dosages(ni, 0, cols, study=i).T).tobytes()
+            paths.append(os.path.join(root, f"study{i}.bin"))
+            _write_repeated(paths[-1], blk, per // cols)
+        write_s = time.perf_counter() - t0
+        for pth in paths:
+            _drop_cached(pth)
+        with gw.GLSBatch(gls) as B:
+            t1 = time.perf_counter()
+            outs = B.solve_files(paths, [per] * len(paths), cols)
+            t_run = time.perf_counter() - t1
+        res["batch_8_studies_from_disk"] = dict(
+            workload="8 studies n=" + ",".join(map(str, STUDY_SIZES)) + f", p=4, bf16x3, {per} SNPs per study "
+                     f"({per / 2e6:.2f} of the 2,000,000 the batching workload names; "
+                     f"{per * sum(STUDY_SIZES) / 1e9:.1f} GB of int8 files on the local disk)",
+            snps=per * len(paths), seconds=t_run, snps_per_s=per * len(paths) / t_run,
+            read_gbs=per * sum(STUDY_SIZES) / t_run / 1e9, file_write_gbs=per * sum(STUDY_SIZES) / write_s / 1e9,
+            page_cache="dropped before the run (fsync + POSIX_FADV_DONTNEED); reads through the page cache",
+            all_finite=bool(all(np.isfinite(o[0][:, o[2] == 0]).all() for o in outs)))
+        for g in gls:
+            g.close()
+    finally:
+        shutil.rmtree(root, ignore_errors=True)
+    torch.cuda.empty_cache()
+    return res
+
+
 def cpu_baseline(w, s, X_sample, target_s=12.0):
     """The oracle as it stands on the host cores: Cholesky first (not timed,
     as the paper leaves set-up out), then per-SNP GLS on a bounded sample."""
@@ -661,6 +788,12 @@ def main():
             forms = measure_forms(args, out)
         except Exception as e:  # report, do not hide
             forms = {"error": repr(e)}
+    if world == 1 and args.disk_tier_gb > 0:
+        try:
+            forms = dict(forms or {})
+            forms["disk_tier"] = measure_disk_tier(args, out)
+        except Exception as e:  # report, do not hide
+            forms["disk_tier"] = {"error": repr(e)}
     cpu = None
     oracle_out = None
     if world == 1 and not args.no_cpu_baseline:

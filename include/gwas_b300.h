@@ -259,10 +259,36 @@ int gwas_batch_solve(gwas_batch *B, const int8_t *const *XR, const int64_t *ldx,
 int gwas_batch_synchronize(gwas_batch *B);
 /* 0: interleave the studies row panel by row panel (default); 1: one study after another. */
 int gwas_batch_set_order(gwas_batch *B, int order_mode);
-/* Autotuner: times the captured step (reps replays after one warm-up, CUDA
- * events) for SNP columns per study per launch in 512, 1024, ... up to the
- * smallest bs, and both tile orders; keeps the fastest order and reports its
- * columns and rate (SNPs/s over all studies).  Overwrites the input slots. */
+/* k blocks per study in one graph replay: the captured graph holds k steps
+ * (each: the pre-passes, one batched launch over all studies, every study's
+ * reductions), so one cudaGraphLaunch solves k blocks of every study.
+ * Arrays are indexed [j * nstudies + i] (study i's j-th block); otherwise as
+ * gwas_batch_solve.  1 <= k <= GWAS_BATCH_MAX_STEPS; the batch keeps k sets
+ * of device slots once used. */
+#define GWAS_BATCH_MAX_STEPS 16
+int gwas_batch_solve_k(gwas_batch *B, int k, const int8_t *const *XR, const int64_t *ldx, const int *ncols,
+                       double *const *b, double *const *se, int *const *status);
+/* Autotuner.  Candidates: SNP columns per study per launch (512, 1024, ... up
+ * to the smallest bs); the tile mode -- the studies' own and, for BF16x3 and
+ * TF32x3 batches, the other of GWAS_TILES_INVERSE and GWAS_TILES_PAIR_MMA
+ * (their operators are built once for the trial, kept if chosen); the
+ * inverse form's operand stages (8 or 6); the substitution's tile order
+ * (interleaved, or study after study over all strips or groups of 8 or 4).
+ * Each candidate is timed (CUDA events; one warm-up, then reps) as whole
+ * gwas_batch_solve steps with device arrays on seeded dosage blocks
+ * (Binomial(2, f), f in [0.05, 0.5), generated on the device) -- the work of
+ * a real step, including its input and output copies.  The fastest is kept
+ * for later solves. */
+typedef struct {
+  int cols;           /* SNP columns per study per launch */
+  int tile_mode;      /* GWAS_TILES_INVERSE or GWAS_TILES_PAIR_MMA */
+  int stages;         /* operand stages of the inverse-form kernel */
+  int order;          /* 0 interleaved, 1 study after study */
+  int strip_group;    /* 0 = all strips */
+  double snps_per_s;  /* the chosen candidate's rate over all studies */
+} gwas_batch_tuning;
+int gwas_batch_autotune_ex(gwas_batch *B, int reps, gwas_batch_tuning *out);
+/* The same, reporting the columns, order and rate only. */
 int gwas_batch_autotune(gwas_batch *B, int reps, int *cols_out, int *order_out, double *snps_per_s_out);
 /* The batching form out of core (Sec. 3.1's disk -> main memory -> GPU, for several studies):
  * study i's int8 dosages are columns col0[i] .. col0[i]+m[i]-1 of the file paths[i] (n_i rows,

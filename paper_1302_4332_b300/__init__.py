@@ -40,7 +40,8 @@ EXPORTS = (
     "gwas_kernel_launches", "gwas_strerror", "gwas_last_error_detail", "gwas_destroy",
     "gwas_timing_enable", "gwas_timing_read", "gwas_solve_block_static", "gwas_adjoint_block",
     "gwas_reml_eval", "gwas_reml_fit", "gwas_batch_create", "gwas_batch_solve", "gwas_batch_synchronize",
-    "gwas_batch_set_order", "gwas_batch_autotune", "gwas_batch_solve_files", "gwas_batch_kernel_launches",
+    "gwas_batch_set_order", "gwas_batch_autotune", "gwas_batch_autotune_ex", "gwas_batch_solve_k",
+    "gwas_batch_solve_files", "gwas_batch_kernel_launches",
     "gwas_batch_last_error_detail",
     "gwas_batch_destroy", "gwas_solve_file", "gwas_solve_file_out", "gwas_reader_open", "gwas_reader_next",
     "gwas_reader_release", "gwas_reader_error_detail", "gwas_reader_close", "gwas_check_timeout",
@@ -70,6 +71,11 @@ class _Config(ctypes.Structure):
 
 
 _lib = None
+
+
+class _Tuning(ctypes.Structure):
+    _fields_ = [("cols", ctypes.c_int), ("tile_mode", ctypes.c_int), ("stages", ctypes.c_int),
+                ("order", ctypes.c_int), ("strip_group", ctypes.c_int), ("snps_per_s", ctypes.c_double)]
 
 
 def load(path: str | None = None):
@@ -137,6 +143,10 @@ def load(path: str | None = None):
     lib.gwas_batch_set_order.restype = c_int
     lib.gwas_batch_autotune.argtypes = [vp, c_int, P(c_int), P(c_int), P(dp)]
     lib.gwas_batch_autotune.restype = c_int
+    lib.gwas_batch_autotune_ex.argtypes = [vp, c_int, P(_Tuning)]
+    lib.gwas_batch_autotune_ex.restype = c_int
+    lib.gwas_batch_solve_k.argtypes = [vp, c_int, P(vp), P(i64), P(c_int), P(vp), P(vp), P(vp)]
+    lib.gwas_batch_solve_k.restype = c_int
     lib.gwas_batch_solve_files.argtypes = [vp, P(ctypes.c_char_p), P(i64), P(i64), P(i64), P(i64), c_int, P(vp),
                                            P(vp), P(vp)]
     lib.gwas_batch_solve_files.restype = c_int
@@ -549,31 +559,37 @@ class GLSBatch:
     def solve(self, blocks):
         """blocks[i]: n_i x ncols_i int8 (column-major; None or 0 columns skips study i).
         Returns a list of (b, se, status) per study (None for skipped studies)."""
-        ns = len(self.studies)
+        return self.solve_k([blocks])[0]
+
+    def solve_k(self, steps):
+        """steps[j][i]: study i's block of step j; all k = len(steps) steps of
+        every study in one graph replay.  Returns outs[j][i] = (b, se, status)."""
+        ns, k = len(self.studies), len(steps)
         xs, lds, ncs, outs, keep = [], [], [], [], []
-        for g, X in zip(self.studies, blocks):
+        for g, X in ((g, X) for blocks in steps for g, X in zip(self.studies, blocks)):
             if X is None or (hasattr(X, "shape") and X.shape[1] == 0):
                 xs.append(None); lds.append(g.n); ncs.append(0); outs.append(None)
                 continue
-            xp, ld, k = _colmajor(X, np.int8, g.n, "XR")
-            keep.append(k)
-            nc = int(k.shape[1])
-            if _is_torch(k) and k.is_cuda:
+            xp, ld, xk = _colmajor(X, np.int8, g.n, "XR")
+            keep.append(xk)
+            nc = int(xk.shape[1])
+            if _is_torch(xk) and xk.is_cuda:
                 torch = _torch()
-                o = (torch.empty((nc, g.p), dtype=torch.float64, device=k.device).T,
-                     torch.empty((nc, g.p), dtype=torch.float64, device=k.device).T,
-                     torch.empty(nc, dtype=torch.int32, device=k.device))
+                o = (torch.empty((nc, g.p), dtype=torch.float64, device=xk.device).T,
+                     torch.empty((nc, g.p), dtype=torch.float64, device=xk.device).T,
+                     torch.empty(nc, dtype=torch.int32, device=xk.device))
             else:
                 o = (np.empty((g.p, nc), order="F"), np.empty((g.p, nc), order="F"), np.empty(nc, dtype=np.int32))
             xs.append(xp); lds.append(ld); ncs.append(nc); outs.append(o)
         ptr = lambda a: None if a is None else (a.data_ptr() if _is_torch(a) else a.ctypes.data)
-        VP = ctypes.c_void_p * ns
-        rc = load().gwas_batch_solve(self._B, VP(*xs), (ctypes.c_int64 * ns)(*lds), (ctypes.c_int * ns)(*ncs),
-                                     VP(*[ptr(o[0]) if o else None for o in outs]),
-                                     VP(*[ptr(o[1]) if o else None for o in outs]),
-                                     VP(*[ptr(o[2]) if o else None for o in outs]))
+        VP = ctypes.c_void_p * (k * ns)
+        rc = load().gwas_batch_solve_k(self._B, k, VP(*xs), (ctypes.c_int64 * (k * ns))(*lds),
+                                       (ctypes.c_int * (k * ns))(*ncs),
+                                       VP(*[ptr(o[0]) if o else None for o in outs]),
+                                       VP(*[ptr(o[1]) if o else None for o in outs]),
+                                       VP(*[ptr(o[2]) if o else None for o in outs]))
         self._check(rc)
-        return outs
+        return [outs[j * ns:(j + 1) * ns] for j in range(k)]
 
     def synchronize(self):
         self._check(load().gwas_batch_synchronize(self._B))
@@ -583,10 +599,17 @@ class GLSBatch:
 
     def autotune(self, reps: int = 3):
         """(columns per study per launch, tile order, SNPs/s) of the fastest measured configuration."""
-        c, o, r = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
-        self._check(load().gwas_batch_autotune(self._B, int(reps), ctypes.byref(c), ctypes.byref(o),
-                                               ctypes.byref(r)))
-        return c.value, o.value, r.value
+        t = self.autotune_ex(reps)
+        return t["cols"], t["order"], t["snps_per_s"]
+
+    def autotune_ex(self, reps: int = 3) -> dict:
+        """The autotuner's choice: columns per study, tile mode, operand stages,
+        tile order, strip group, and its measured rate (SNPs/s over all studies)."""
+        t = _Tuning()
+        self._check(load().gwas_batch_autotune_ex(self._B, int(reps), ctypes.byref(t)))
+        names = {v: k for k, v in TILE_MODES.items()}
+        return dict(cols=t.cols, tile_mode=names.get(t.tile_mode, t.tile_mode), stages=t.stages, order=t.order,
+                    strip_group=t.strip_group, snps_per_s=t.snps_per_s)
 
     @property
     def kernel_launches(self) -> int:

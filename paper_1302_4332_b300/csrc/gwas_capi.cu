@@ -54,6 +54,7 @@ struct gwas_ctx {
   double* adj = nullptr;       // per-SNP chi2 (bs), dh (bs), y-weights (bs x p), uT (q), dh/dy staging (1 + n),
                                // the y-gradient's chunk partials (adjoint_dy_chunks(bs) x n)
   ExactAdjoint* exact = nullptr;  // split precisions: the adjoint's exact products (built on first use)
+  bool separate_sums = false, single_piece = false;  // the split set-up's options (a batch's tuner repeats them)
   // pinned host buffers of the file reader, kept across gwas_solve_file calls
   std::vector<void*> file_buf;
   int64_t file_buf_bytes = 0;
@@ -457,6 +458,8 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
     ctx->n_pad = (n + TB - 1) / TB * TB;
     ctx->P = ctx->n_pad / TB;
     ctx->prec = cfg.precision; ctx->bs = cfg.bs; ctx->ring_depth = cfg.ring_depth;
+    ctx->separate_sums = cfg.separate_sums != 0;
+    ctx->single_piece = cfg.single_piece != 0;
     ctx->h = h; ctx->sigma2 = sigma2;
     const size_t np = (size_t)ctx->n_pad, n2 = np * np;
     CK(dmalloc(&ctx->L, sizeof(double) * n2));
@@ -1157,18 +1160,23 @@ struct gwas_batch {
   cudaStream_t stream = nullptr;
   bool own_stream = false;
   std::vector<gwas_ctx*> ctx;
-  std::vector<tc::TcState*> ts;
-  tc::TcBatchState* tb = nullptr;
-  std::vector<int8_t*> slot;    // per study: n_pad x bs int8 input slot
+  std::vector<tc::TcState*> ts;      // the studies' own split states
+  std::vector<tc::TcState*> alt_ts;  // the same studies in the other tile mode (owned; built by the autotuner)
+  bool use_alt = false;              // launches run on alt_ts
+  std::vector<tc::TcBatchState*> tb;  // one planned launch per step of a replay
+  // device slots of step j, study i at [j * ns + i]: n_pad x bs int8 input, outputs
+  std::vector<int8_t*> slot;
   std::vector<double*> d_b, d_se;
   std::vector<int*> d_st;
+  int ksteps = 0;  // steps with slots and a launch state
   cudaGraph_t graph = nullptr;
   cudaGraphExec_t exec = nullptr;
-  std::vector<int> planned_cols;
-  int planned_order = -1;
-  int planned_group = -1;
+  std::vector<int> planned_cols;  // [j * ns + i]
+  int planned_order = -1, planned_group = -1, planned_stages = 0;
+  bool planned_alt = false;
   int order_mode = 0;
   int strip_group = 0;
+  int stages = 8;
   int64_t launches = 0;
   int64_t launches_per_step = 0;
   // per study: the file readers' pinned buffers, kept across gwas_batch_solve_files calls
@@ -1190,49 +1198,106 @@ int bfail(gwas_batch* B, int code, const char* msg, cudaError_t e = cudaSuccess)
     if (e_ != cudaSuccess) return bfail(B, e_ == cudaErrorMemoryAllocation ? GWAS_ERR_NOMEM : GWAS_ERR_CUDA, msg, e_); \
   } while (0)
 
+const std::vector<tc::TcState*>& states(const gwas_batch* B) { return B->use_alt ? B->alt_ts : B->ts; }
+
+void drop_graph(gwas_batch* B) {
+  if (B->exec) { cudaGraphExecDestroy(B->exec); B->exec = nullptr; }
+  if (B->graph) { cudaGraphDestroy(B->graph); B->graph = nullptr; }
+}
+
+void drop_alt(gwas_batch* B) {
+  for (auto* t : B->alt_ts) tc::destroy(t);
+  B->alt_ts.clear();
+}
+
 void batch_free(gwas_batch* B) {
   if (!B) return;
   DeviceScope dscope_(B->dev);
   if (B->stream) cudaStreamSynchronize(B->stream);
-  if (B->exec) cudaGraphExecDestroy(B->exec);
-  if (B->graph) cudaGraphDestroy(B->graph);
+  drop_graph(B);
   for (auto* p : B->slot) cudaFree(p);
   for (auto* p : B->d_b) cudaFree(p);
   for (auto* p : B->d_se) cudaFree(p);
   for (auto* p : B->d_st) cudaFree(p);
   for (auto& v : B->file_buf)
     for (auto* q : v) cudaFreeHost(q);
-  if (B->tb) tc::batch_destroy(B->tb);
+  for (auto* t : B->tb) tc::batch_destroy(t);
+  drop_alt(B);
   if (B->own_stream && B->stream) cudaStreamDestroy(B->stream);
   delete B;
 }
 
-// Plans for cols[] and captures the whole step into a CUDA graph.
-int batch_capture(gwas_batch* B, const std::vector<int>& cols, int order, int group) {
-  std::vector<const int8_t*> X(B->ns);
-  std::vector<int64_t> ld(B->ns);
-  for (int i = 0; i < B->ns; ++i) {
-    X[i] = B->slot[i];
-    ld[i] = B->ctx[i]->n_pad;
+// Launch states for steps 0 .. k-1 over the current states (rebuilt when
+// the tile mode changes), and the device slots of those steps.
+int ensure_steps(gwas_batch* B, int k, bool rebuild) {
+  if (rebuild) {
+    for (auto* t : B->tb) tc::batch_destroy(t);
+    B->tb.clear();
   }
-  BCK(tc::batch_plan(B->tb, B->ts.data(), X.data(), ld.data(), cols.data(), order, B->stream, group),
-      "batch plan");
-  if (B->exec) { cudaGraphExecDestroy(B->exec); B->exec = nullptr; }
-  if (B->graph) { cudaGraphDestroy(B->graph); B->graph = nullptr; }
+  while ((int)B->tb.size() < std::max(k, B->ksteps)) {
+    tc::TcBatchState* t = nullptr;
+    BCK(tc::batch_create(&t, states(B).data(), B->ns), "batch state");
+    BCK(tc::batch_set_stages(t, B->stages), "stages");
+    B->tb.push_back(t);
+  }
+  for (auto* t : B->tb) BCK(tc::batch_set_stages(t, B->stages), "stages");
+  for (int j = B->ksteps; j < k; ++j) {
+    for (int i = 0; i < B->ns; ++i) {
+      gwas_ctx* c = B->ctx[i];
+      int8_t* sl = nullptr;
+      double *db = nullptr, *dse = nullptr;
+      int* dst = nullptr;
+      BCK(dmalloc(&sl, (size_t)c->n_pad * c->bs), "slot");
+      B->slot.push_back(sl);
+      BCK(cudaMemsetAsync(sl, 0, (size_t)c->n_pad * c->bs, B->stream), "slot clear");
+      BCK(dmalloc(&db, sizeof(double) * (size_t)c->p * c->bs), "b");
+      B->d_b.push_back(db);
+      BCK(dmalloc(&dse, sizeof(double) * (size_t)c->p * c->bs), "se");
+      B->d_se.push_back(dse);
+      BCK(dmalloc(&dst, sizeof(int) * (size_t)c->bs), "status");
+      B->d_st.push_back(dst);
+    }
+    B->ksteps = j + 1;
+  }
+  return GWAS_OK;
+}
+
+// Plans every step for cols (k * ns entries) and captures the k steps -- each
+// the pre-passes, one batched launch over all studies, every study's
+// reductions and p x p solves -- into one CUDA graph.
+int batch_capture(gwas_batch* B, const std::vector<int>& cols, int k, int order, int group) {
+  const int ns = B->ns;
+  const auto& ts = states(B);
+  std::vector<const int8_t*> X(ns);
+  std::vector<int64_t> ld(ns);
+  for (int j = 0; j < k; ++j) {
+    for (int i = 0; i < ns; ++i) {
+      X[i] = B->slot[j * ns + i];
+      ld[i] = B->ctx[i]->n_pad;
+    }
+    BCK(tc::batch_plan(B->tb[j], ts.data(), X.data(), ld.data(), cols.data() + j * ns, order, B->stream, group),
+        "batch plan");
+  }
+  drop_graph(B);
   BCK(cudaStreamBeginCapture(B->stream, cudaStreamCaptureModeThreadLocal), "begin capture");
   int64_t nl = 0;
-  cudaError_t e = tc::batch_launch(B->tb, B->ts.data(), B->stream, &nl);
-  for (int i = 0; i < B->ns && e == cudaSuccess; ++i) {
-    gwas_ctx* c = B->ctx[i];
-    if (cols[i] == 0) continue;
-    if (const float* red = tc::partials(c->tcs))
-      e = launch_partials_solve(red, tc::partial_groups(c->tcs), tc::partial_ld(c->tcs), c->sc, c->q, 1, cols[i],
-                                B->d_b[i], B->d_se[i], B->d_st[i], tc::shift_of(c->tcs), B->stream);
-    else
-      e = launch_reduce_solve(tc::xt_f32(c->tcs), XT_F32, tc::xt_ld(c->tcs), c->n_pad, c->W, c->n_pad, c->sc, c->q,
-                              cols[i], B->d_b[i], B->d_se[i], B->d_st[i], B->stream, c->W32, tc::shift_of(c->tcs),
-                              c->st, c->num_sms, tc::xt_reduce_map(c->tcs));
-    ++nl;
+  cudaError_t e = cudaSuccess;
+  for (int j = 0; j < k && e == cudaSuccess; ++j) {
+    e = tc::batch_launch(B->tb[j], ts.data(), B->stream, &nl);
+    for (int i = 0; i < ns && e == cudaSuccess; ++i) {
+      gwas_ctx* c = B->ctx[i];
+      tc::TcState* t = ts[i];
+      const int nc = cols[j * ns + i], o = j * ns + i;
+      if (nc == 0) continue;
+      if (const float* red = tc::partials(t))
+        e = launch_partials_solve(red, tc::partial_groups(t), tc::partial_ld(t), c->sc, c->q, 1, nc, B->d_b[o],
+                                  B->d_se[o], B->d_st[o], tc::shift_of(t), B->stream);
+      else
+        e = launch_reduce_solve(tc::xt_f32(t), XT_F32, tc::xt_ld(t), c->n_pad, c->W, c->n_pad, c->sc, c->q, nc,
+                                B->d_b[o], B->d_se[o], B->d_st[o], B->stream, c->W32, tc::shift_of(t), c->st,
+                                c->num_sms, tc::xt_reduce_map(t));
+      ++nl;
+    }
   }
   cudaGraph_t g = nullptr;
   cudaError_t e2 = cudaStreamEndCapture(B->stream, &g);
@@ -1243,8 +1308,85 @@ int batch_capture(gwas_batch* B, const std::vector<int>& cols, int order, int gr
   B->planned_cols = cols;
   B->planned_order = order;
   B->planned_group = group;
+  B->planned_stages = B->stages;
+  B->planned_alt = B->use_alt;
   B->launches_per_step = nl;
   return GWAS_OK;
+}
+
+// k blocks per study through one graph replay: inputs into the slots,
+// the replay (recaptured when the plan changed), results out.  Pointer
+// arrays are indexed [j * ns + i]; host arrays make the call synchronous.
+int batch_step(gwas_batch* B, int k, const int8_t* const* XR, const int64_t* ldx, const int* ncols,
+               double* const* b, double* const* se, int* const* status) {
+  const int ns = B->ns;
+  std::vector<int> cols(k * ns);
+  for (int o = 0; o < k * ns; ++o) {
+    gwas_ctx* c = B->ctx[o % ns];
+    if (ncols[o] < 0 || ncols[o] > c->bs || (ncols[o] > 0 && (!XR[o] || !b[o] || ldx[o] < c->n)))
+      return bfail(B, GWAS_ERR_ARG, "bad arguments to a batch solve");
+    cols[o] = ncols[o];
+  }
+  int rc = ensure_steps(B, k, false);
+  if (rc != GWAS_OK) return rc;
+  bool any_host = false;
+  for (int o = 0; o < k * ns; ++o) {
+    if (cols[o] == 0) continue;
+    gwas_ctx* c = B->ctx[o % ns];
+    const bool dev_in = is_device_ptr(XR[o]);
+    any_host |= !dev_in;
+    BCK(cudaMemcpy2DAsync(B->slot[o], (size_t)c->n_pad, XR[o], (size_t)ldx[o], (size_t)c->n, (size_t)cols[o],
+                          dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, B->stream),
+        "input copy");
+  }
+  if (!B->exec || cols != B->planned_cols || B->order_mode != B->planned_order ||
+      B->strip_group != B->planned_group || B->stages != B->planned_stages || B->use_alt != B->planned_alt) {
+    if ((rc = batch_capture(B, cols, k, B->order_mode, B->strip_group)) != GWAS_OK) return rc;
+  }
+  BCK(cudaGraphLaunch(B->exec, B->stream), "graph launch");
+  B->launches += B->launches_per_step;
+  for (int o = 0; o < k * ns; ++o) {
+    if (cols[o] == 0) continue;
+    gwas_ctx* c = B->ctx[o % ns];
+    any_host |= !is_device_ptr(b[o]) || (se && se[o] && !is_device_ptr(se[o])) ||
+                (status && status[o] && !is_device_ptr(status[o]));
+    BCK(cudaMemcpyAsync(b[o], B->d_b[o], sizeof(double) * (size_t)c->p * cols[o], cudaMemcpyDefault, B->stream),
+        "b out");
+    if (se && se[o])
+      BCK(cudaMemcpyAsync(se[o], B->d_se[o], sizeof(double) * (size_t)c->p * cols[o], cudaMemcpyDefault, B->stream),
+          "se out");
+    if (status && status[o])
+      BCK(cudaMemcpyAsync(status[o], B->d_st[o], sizeof(int) * (size_t)cols[o], cudaMemcpyDefault, B->stream),
+          "status out");
+  }
+  if (!any_host) return GWAS_OK;
+  BCK(cudaStreamSynchronize(B->stream), "sync");
+  for (int i = 0; i < ns; ++i) {
+    int r = check_device_status(B->ctx[i]);
+    if (r != GWAS_OK) return bfail(B, r, "device-side wait ran out");
+  }
+  return GWAS_OK;
+}
+
+// Seeded dosage columns for the autotuner: x ~ Binomial(2, f_j), f_j in
+// [0.05, 0.5), from a counter-based hash of (seed, column, row) -- blocks with
+// the value mix of real dosages (the tensor cores' power draw, and so the
+// clock under the power cap, depends on the operand values).
+__device__ __forceinline__ uint64_t mix64(uint64_t z) {
+  z += 0x9E3779B97F4A7C15ull;
+  z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+  z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+  return z ^ (z >> 31);
+}
+__global__ void tune_dosages_kernel(int8_t* __restrict__ X, int64_t ld, int n, int ncols, uint64_t seed) {
+  const int col = blockIdx.y;
+  if (col >= ncols) return;
+  const double f = 0.05 + 0.45 * (double)(mix64(seed ^ (0x5A17ull << 40) ^ (uint64_t)col) >> 11) * 0x1p-53;
+  const uint32_t thr = (uint32_t)(f * 4294967296.0);
+  for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < n; r += gridDim.x * blockDim.x) {
+    const uint64_t h = mix64(seed + ((uint64_t)col << 32) + (uint64_t)r);
+    X[(int64_t)col * ld + r] = (int8_t)(((uint32_t)h < thr) + ((uint32_t)(h >> 32) < thr));
+  }
 }
 
 }  // namespace
@@ -1272,23 +1414,11 @@ int gwas_batch_create(gwas_batch** out, gwas_ctx* const* studies, int nstudies, 
       B->own_stream = true;
     }
     for (int i = 0; i < nstudies; ++i) {
-      gwas_ctx* c = studies[i];
-      B->ctx.push_back(c);
-      B->ts.push_back(c->tcs);
-      int8_t* sl = nullptr;
-      double *db = nullptr, *dse = nullptr;
-      int* dst = nullptr;
-      BCK(dmalloc(&sl, (size_t)c->n_pad * c->bs), "slot");
-      B->slot.push_back(sl);
-      BCK(cudaMemsetAsync(sl, 0, (size_t)c->n_pad * c->bs, B->stream), "slot clear");
-      BCK(dmalloc(&db, sizeof(double) * (size_t)c->p * c->bs), "b");
-      B->d_b.push_back(db);
-      BCK(dmalloc(&dse, sizeof(double) * (size_t)c->p * c->bs), "se");
-      B->d_se.push_back(dse);
-      BCK(dmalloc(&dst, sizeof(int) * (size_t)c->bs), "status");
-      B->d_st.push_back(dst);
+      B->ctx.push_back(studies[i]);
+      B->ts.push_back(studies[i]->tcs);
     }
-    BCK(tc::batch_create(&B->tb, B->ts.data(), nstudies), "batch state");
+    int r = ensure_steps(B, 1, false);
+    if (r != GWAS_OK) return r;
     BCK(cudaStreamSynchronize(B->stream), "sync");
     return GWAS_OK;
   }();
@@ -1310,53 +1440,17 @@ int gwas_batch_set_order(gwas_batch* B, int order_mode) {
 int gwas_batch_solve(gwas_batch* B, const int8_t* const* XR, const int64_t* ldx, const int* ncols, double* const* b,
                      double* const* se, int* const* status) {
   if (!B || !XR || !ldx || !ncols || !b) return GWAS_ERR_ARG;
-  std::vector<int> cols(B->ns);
-  bool any_host = false;
-  for (int i = 0; i < B->ns; ++i) {
-    gwas_ctx* c = B->ctx[i];
-    if (ncols[i] < 0 || ncols[i] > c->bs || (ncols[i] > 0 && (!XR[i] || !b[i] || ldx[i] < c->n)))
-      return bfail(B, GWAS_ERR_ARG, "bad arguments to gwas_batch_solve");
-    cols[i] = ncols[i];
-  }
   DeviceScope dscope_(B->dev);
   BCK(dscope_.status(), "set device");
-  for (int i = 0; i < B->ns; ++i) {
-    if (cols[i] == 0) continue;
-    gwas_ctx* c = B->ctx[i];
-    const bool dev_in = is_device_ptr(XR[i]);
-    any_host |= !dev_in;
-    BCK(cudaMemcpy2DAsync(B->slot[i], (size_t)c->n_pad, XR[i], (size_t)ldx[i], (size_t)c->n, (size_t)cols[i],
-                          dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, B->stream),
-        "input copy");
-  }
-  if (!B->exec || cols != B->planned_cols || B->order_mode != B->planned_order ||
-      B->strip_group != B->planned_group) {
-    int rc = batch_capture(B, cols, B->order_mode, B->strip_group);
-    if (rc != GWAS_OK) return rc;
-  }
-  BCK(cudaGraphLaunch(B->exec, B->stream), "graph launch");
-  B->launches += B->launches_per_step;
-  for (int i = 0; i < B->ns; ++i) {
-    if (cols[i] == 0) continue;
-    gwas_ctx* c = B->ctx[i];
-    any_host |= !is_device_ptr(b[i]) || (se && se[i] && !is_device_ptr(se[i])) ||
-                (status && status[i] && !is_device_ptr(status[i]));
-    BCK(cudaMemcpyAsync(b[i], B->d_b[i], sizeof(double) * (size_t)c->p * cols[i], cudaMemcpyDefault, B->stream),
-        "b out");
-    if (se && se[i])
-      BCK(cudaMemcpyAsync(se[i], B->d_se[i], sizeof(double) * (size_t)c->p * cols[i], cudaMemcpyDefault, B->stream),
-          "se out");
-    if (status && status[i])
-      BCK(cudaMemcpyAsync(status[i], B->d_st[i], sizeof(int) * (size_t)cols[i], cudaMemcpyDefault, B->stream),
-          "status out");
-  }
-  if (!any_host) return GWAS_OK;
-  BCK(cudaStreamSynchronize(B->stream), "sync");
-  for (int i = 0; i < B->ns; ++i) {
-    int rc = check_device_status(B->ctx[i]);
-    if (rc != GWAS_OK) return bfail(B, rc, "device-side wait ran out");
-  }
-  return GWAS_OK;
+  return batch_step(B, 1, XR, ldx, ncols, b, se, status);
+}
+
+int gwas_batch_solve_k(gwas_batch* B, int k, const int8_t* const* XR, const int64_t* ldx, const int* ncols,
+                       double* const* b, double* const* se, int* const* status) {
+  if (!B || k < 1 || k > GWAS_BATCH_MAX_STEPS || !XR || !ldx || !ncols || !b) return GWAS_ERR_ARG;
+  DeviceScope dscope_(B->dev);
+  BCK(dscope_.status(), "set device");
+  return batch_step(B, k, XR, ldx, ncols, b, se, status);
 }
 
 int gwas_batch_synchronize(gwas_batch* B) {
@@ -1372,52 +1466,144 @@ int gwas_batch_synchronize(gwas_batch* B) {
 }
 
 int gwas_batch_autotune(gwas_batch* B, int reps, int* cols_out, int* order_out, double* snps_per_s_out) {
-  if (!B || !cols_out || reps < 1) return GWAS_ERR_ARG;
+  gwas_batch_tuning t;
+  int rc = gwas_batch_autotune_ex(B, reps, &t);
+  if (rc != GWAS_OK) return rc;
+  if (cols_out) *cols_out = t.cols;
+  if (order_out) *order_out = t.order;
+  if (snps_per_s_out) *snps_per_s_out = t.snps_per_s;
+  return GWAS_OK;
+}
+
+int gwas_batch_autotune_ex(gwas_batch* B, int reps, gwas_batch_tuning* out) {
+  if (!B || !out || reps < 1) return GWAS_ERR_ARG;
   DeviceScope dscope_(B->dev);
   BCK(dscope_.status(), "set device");
+  const int ns = B->ns;
   int maxc = 1 << 30;
   for (auto* c : B->ctx) maxc = std::min(maxc, c->bs);
-  // synthetic dosages: any values cost the same; fill the slots with 1
-  for (int i = 0; i < B->ns; ++i)
-    BCK(cudaMemsetAsync(B->slot[i], 1, (size_t)B->ctx[i]->n_pad * B->ctx[i]->bs, B->stream), "fill");
-  cudaEvent_t e0, e1;
-  BCK(cudaEventCreate(&e0), "event");
-  BCK(cudaEventCreate(&e1), "event");
-  double best = -1.0;
-  int best_cols = 0, best_order = 0;
-  int best_group = 0;
-  for (int cand = 512; cand <= maxc; cand *= 2) {
-    for (int variant = 0; variant < 4; ++variant) {
-      // order 0; order 1 with all strips, groups of 8, groups of 4
-      const int order = variant == 0 ? 0 : 1;
-      const int group = variant <= 1 ? 0 : (variant == 2 ? 8 : 4);
-      if (group && group >= (cand + 255) / 256) continue;
-      std::vector<int> cols(B->ns, cand);
-      int rc = batch_capture(B, cols, order, group);
-      if (rc != GWAS_OK) { cudaEventDestroy(e0); cudaEventDestroy(e1); return rc; }
-      BCK(cudaGraphLaunch(B->exec, B->stream), "warm-up");
-      BCK(cudaEventRecord(e0, B->stream), "event");
-      for (int r = 0; r < reps; ++r) BCK(cudaGraphLaunch(B->exec, B->stream), "timed");
-      BCK(cudaEventRecord(e1, B->stream), "event");
-      BCK(cudaEventSynchronize(e1), "event sync");
-      float ms = 0.f;
-      BCK(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
-      const double rate = (double)cand * B->ns * reps / (ms * 1e-3);
-      if (rate > best) { best = rate; best_cols = cand; best_order = order; best_group = group; }
+  // the candidates' inputs: seeded dosage blocks of maxc columns per study
+  // (device), outputs into device scratch -- each timed step is a full
+  // gwas_batch_solve with device arrays
+  std::vector<int8_t*> src(ns, nullptr);
+  std::vector<double*> ob(ns, nullptr), os(ns, nullptr);
+  std::vector<int*> ost(ns, nullptr);
+  std::vector<int64_t> ld(ns);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  auto release = [&] {
+    for (int i = 0; i < ns; ++i) {
+      cudaFree(src[i]);
+      cudaFree(ob[i]);
+      cudaFree(os[i]);
+      cudaFree(ost[i]);
     }
-  }
-  cudaEventDestroy(e0);
-  cudaEventDestroy(e1);
-  B->order_mode = best_order;
-  B->strip_group = best_group;
-  *cols_out = best_cols;
-  if (order_out) *order_out = best_order;
-  if (snps_per_s_out) *snps_per_s_out = best;
-  for (int i = 0; i < B->ns; ++i) {
-    int rc = check_device_status(B->ctx[i]);
-    if (rc != GWAS_OK) return bfail(B, rc, "device-side wait ran out");
-  }
-  return GWAS_OK;
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
+  };
+  int rc = [&]() -> int {
+    for (int i = 0; i < ns; ++i) {
+      gwas_ctx* c = B->ctx[i];
+      ld[i] = c->n_pad;
+      BCK(dmalloc(&src[i], (size_t)c->n_pad * maxc), "tuning input");
+      BCK(dmalloc(&ob[i], sizeof(double) * (size_t)c->p * maxc), "tuning output");
+      BCK(dmalloc(&os[i], sizeof(double) * (size_t)c->p * maxc), "tuning output");
+      BCK(dmalloc(&ost[i], sizeof(int) * (size_t)maxc), "tuning output");
+      tune_dosages_kernel<<<dim3(8, maxc), 256, 0, B->stream>>>(src[i], ld[i], c->n, maxc,
+                                                                0x243F6A8885A308D3ull + 977ull * i);
+      BCK(cudaGetLastError(), "tuning input");
+    }
+    BCK(cudaEventCreate(&e0), "event");
+    BCK(cudaEventCreate(&e1), "event");
+    // tile modes: the studies' own, and for BF16x3 / TF32x3 the other of
+    // {inverse form, pair product} (FP16 pieces exist in the inverse form only)
+    const tc::TileMode own = tc::tile_mode(B->ts[0]);
+    const bool can_alt = B->ctx[0]->prec != GWAS_F16X2 && !B->ctx[0]->single_piece &&
+                         (own == tc::TILES_INVERSE || own == tc::TILES_PAIR_MMA);
+    const tc::TileMode other = own == tc::TILES_INVERSE ? tc::TILES_PAIR_MMA : tc::TILES_INVERSE;
+    double best = -1.0;
+    gwas_batch_tuning bt{};
+    for (int alt = 0; alt <= (can_alt ? 1 : 0); ++alt) {
+      if (alt && B->alt_ts.empty()) {  // the studies' states in the other mode
+        for (int i = 0; i < ns; ++i) {
+          gwas_ctx* c = B->ctx[i];
+          tc::TcState* t = nullptr;
+          int64_t nl = 0;
+          const tc::Split sp = c->prec == GWAS_BF16X3 ? tc::SPLIT_BF16 : tc::SPLIT_TF32;
+          cudaError_t e = tc::create(&t, sp, c->Aop, c->n, c->n_pad, c->bs, c->num_sms, c->intercept, c->st,
+                                     B->stream, &nl, 0, other);
+          B->launches += nl;
+          if (e != cudaSuccess) return bfail(B, GWAS_ERR_CUDA, "tile-mode candidate", e);
+          B->alt_ts.push_back(t);
+          const int nw = c->q + c->t;
+          if (!c->separate_sums) BCK(tc::set_reductions(t, c->W32, w32_stride(nw - 1), nw), "reductions");
+        }
+        BCK(cudaStreamSynchronize(B->stream), "sync");
+      }
+      B->use_alt = alt != 0;
+      const tc::TileMode mode = alt ? other : own;
+      int r = ensure_steps(B, 1, true);
+      if (r != GWAS_OK) return r;
+      for (int cand = 512; cand <= maxc || (cand == 512 && maxc < 512); cand *= 2) {
+        const int cc = std::min(cand, maxc);
+        // inverse form: 8 or 6 operand stages (no ordering: units longest first);
+        // substitution: row-panel interleaved, or study after study over all strips,
+        // groups of 8 or of 4 strips
+        const int nvar = mode == tc::TILES_INVERSE ? 2 : 4;
+        for (int v = 0; v < nvar; ++v) {
+          const int stages = mode == tc::TILES_INVERSE ? (v == 0 ? 8 : 6) : 8;
+          const int order = mode == tc::TILES_INVERSE ? 0 : (v == 0 ? 0 : 1);
+          const int group = mode == tc::TILES_INVERSE ? 0 : (v <= 1 ? 0 : (v == 2 ? 8 : 4));
+          if (group && group >= (cc + 255) / 256) continue;
+          B->stages = stages;
+          B->order_mode = order;
+          B->strip_group = group;
+          if ((r = ensure_steps(B, 1, false)) != GWAS_OK) return r;
+          std::vector<int> cols(ns, cc);
+          std::vector<const int8_t*> x(src.begin(), src.end());
+          if ((r = batch_step(B, 1, x.data(), ld.data(), cols.data(), ob.data(), os.data(), ost.data())) != GWAS_OK)
+            return r;  // warm-up (and capture)
+          BCK(cudaEventRecord(e0, B->stream), "event");
+          for (int q = 0; q < reps; ++q)
+            if ((r = batch_step(B, 1, x.data(), ld.data(), cols.data(), ob.data(), os.data(), ost.data())) != GWAS_OK)
+              return r;
+          BCK(cudaEventRecord(e1, B->stream), "event");
+          BCK(cudaEventSynchronize(e1), "event sync");
+          float ms = 0.f;
+          BCK(cudaEventElapsedTime(&ms, e0, e1), "elapsed");
+          const double rate = (double)cc * ns * reps / (ms * 1e-3);
+          if (rate > best) {
+            best = rate;
+            bt.cols = cc;
+            bt.order = order;
+            bt.strip_group = group;
+            bt.stages = stages;
+            bt.tile_mode = mode;
+            bt.snps_per_s = rate;
+          }
+        }
+        if (cand >= maxc) break;
+      }
+    }
+    // keep the winner
+    B->use_alt = bt.tile_mode != own;
+    if (!B->use_alt) drop_alt(B);
+    B->stages = bt.stages;
+    B->order_mode = bt.order;
+    B->strip_group = bt.strip_group;
+    int r = ensure_steps(B, 1, true);
+    if (r != GWAS_OK) return r;
+    drop_graph(B);
+    B->planned_cols.clear();
+    *out = bt;
+    for (int i = 0; i < ns; ++i) {
+      r = check_device_status(B->ctx[i]);
+      if (r != GWAS_OK) return bfail(B, r, "device-side wait ran out");
+    }
+    return GWAS_OK;
+  }();
+  BCK(cudaStreamSynchronize(B->stream), "sync");
+  release();
+  return rc;
 }
 
 int gwas_batch_solve_files(gwas_batch* B, const char* const* paths, const int64_t* header_bytes, const int64_t* ldx,

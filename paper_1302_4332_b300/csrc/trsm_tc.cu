@@ -1058,9 +1058,11 @@ __device__ __forceinline__ void tile_sums(const float (&master)[EPI_COLS], float
   }
 }
 
-template <bool TF32>
+// NST operand stages (8, the most that fit beside the epilogue staging, or 6:
+// a batch's autotuner picks one)
+template <bool TF32, int NST = 8>
 struct Cfg {
-  static constexpr int STAGES = 8;
+  static constexpr int STAGES = NST;
   static constexpr int ESZ = TF32 ? 4 : 2;
   static constexpr int KCH = 64 / ESZ;
   static constexpr int KMMA = TF32 ? 8 : 16;
@@ -1081,9 +1083,9 @@ struct Cfg {
 // F16 (with TF32 false): L^-1 pieces and the cast block are FP16; row r of
 // L^-1 was scaled by 1 / rscale[r] (a power of two) before the split, so the
 // epilogue multiplies its results back by rscale[r].
-template <bool TF32, bool F16 = false>
+template <bool TF32, bool F16 = false, int NST = 8>
 __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_constant__ TcBatch b) {
-  using K = inv2::Cfg<TF32>;
+  using K = inv2::Cfg<TF32, NST>;
   constexpr int ST = K::STAGES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -1392,12 +1394,15 @@ __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_co
 
 // ------------------------------------------------------------ launch entries
 template <bool TF32>
-static cudaLaunchConfig_t pair_config(cudaLaunchAttribute* attr, int grid, cudaStream_t s, TileMode mode) {
+static cudaLaunchConfig_t pair_config(cudaLaunchAttribute* attr, int grid, cudaStream_t s, TileMode mode,
+                                      int stages = 8) {
   cudaLaunchConfig_t cfg;
   memset(&cfg, 0, sizeof cfg);
   cfg.gridDim = dim3(grid);
   cfg.blockDim = dim3(THREADS);
-  cfg.dynamicSmemBytes = mode == TILES_INVERSE ? inv2::Cfg<TF32>::SMEM : pair2::Cfg<TF32>::SMEM;
+  cfg.dynamicSmemBytes = mode != TILES_INVERSE ? pair2::Cfg<TF32>::SMEM
+                         : stages == 6         ? inv2::Cfg<TF32, 6>::SMEM
+                                               : inv2::Cfg<TF32>::SMEM;
   cfg.stream = s;
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = 2;
@@ -1415,6 +1420,11 @@ static cudaError_t set_attrs(bool clusters) {
   if (e != cudaSuccess || !clusters) return e;
   if ((e = cudaFuncSetAttribute(trsm_tc_pair_mma_kernel<TF32>, A, pair2::Cfg<TF32>::SMEM)) != cudaSuccess) return e;
   if (!TF32 && (e = cudaFuncSetAttribute(trsm_tc_inv_kernel<false, true>, A, inv2::Cfg<false>::SMEM)) != cudaSuccess)
+    return e;
+  if (!TF32 &&
+      (e = cudaFuncSetAttribute(trsm_tc_inv_kernel<false, true, 6>, A, inv2::Cfg<false, 6>::SMEM)) != cudaSuccess)
+    return e;
+  if ((e = cudaFuncSetAttribute(trsm_tc_inv_kernel<TF32, false, 6>, A, inv2::Cfg<TF32, 6>::SMEM)) != cudaSuccess)
     return e;
   return cudaFuncSetAttribute(trsm_tc_inv_kernel<TF32>, A, inv2::Cfg<TF32>::SMEM);
 }
@@ -1438,14 +1448,19 @@ cudaError_t query_clusters(bool tf32, TileMode mode, int num_sms, int* out, bool
 }
 
 template <bool TF32>
-static cudaError_t launch_pair(const TcBatch& b, int max_clusters, cudaStream_t s, TileMode mode, bool f16) {
+static cudaError_t launch_pair(const TcBatch& b, int max_clusters, cudaStream_t s, TileMode mode, bool f16,
+                               int stages) {
   const int ncl = b.ntiles < max_clusters ? b.ntiles : max_clusters;
   cudaLaunchAttribute attr[2];
-  cudaLaunchConfig_t cfg = pair_config<TF32>(attr, 2 * ncl, s, mode);
+  cudaLaunchConfig_t cfg = pair_config<TF32>(attr, 2 * ncl, s, mode, stages);
   if (mode == TILES_INVERSE) {  // a programmatic dependent of the cast pre-pass (the kernel waits for it)
     attr[1].id = cudaLaunchAttributeProgrammaticStreamSerialization;
     attr[1].val.programmaticStreamSerializationAllowed = 1;
     cfg.numAttrs = 2;
+  }
+  if (mode == TILES_INVERSE && stages == 6) {
+    if (f16 && !TF32) return cudaLaunchKernelEx(&cfg, trsm_tc_inv_kernel<false, true, 6>, b);
+    return cudaLaunchKernelEx(&cfg, trsm_tc_inv_kernel<TF32, false, 6>, b);
   }
   if (mode == TILES_INVERSE && f16 && !TF32) return cudaLaunchKernelEx(&cfg, trsm_tc_inv_kernel<false, true>, b);
   if (mode == TILES_INVERSE) return cudaLaunchKernelEx(&cfg, trsm_tc_inv_kernel<TF32>, b);
@@ -1453,12 +1468,13 @@ static cudaError_t launch_pair(const TcBatch& b, int max_clusters, cudaStream_t 
 }
 
 cudaError_t launch_solve(bool tf32, TileMode mode, const TcBatch& b, int num_sms, int max_clusters,
-                         cudaStream_t s, bool f16) {
+                         cudaStream_t s, bool f16, int stages) {
   if (f16 && (tf32 || mode != TILES_INVERSE)) return cudaErrorInvalidValue;
   if (mode != TILES_SINGLE && mode != TILES_PAIR_MMA && mode != TILES_INVERSE) return cudaErrorInvalidValue;
+  if (stages != 6 && stages != 8) return cudaErrorInvalidValue;
   if (mode != TILES_SINGLE) {
-    const cudaError_t e = tf32 ? launch_pair<true>(b, max_clusters, s, mode, false)
-                               : launch_pair<false>(b, max_clusters, s, mode, f16);
+    const cudaError_t e = tf32 ? launch_pair<true>(b, max_clusters, s, mode, false, stages)
+                               : launch_pair<false>(b, max_clusters, s, mode, f16, stages);
     return e != cudaSuccess ? e : cudaGetLastError();
   }
   const int grid = b.ntiles < num_sms ? b.ntiles : num_sms;

@@ -59,6 +59,8 @@ cudaError_t batch_plan(TcBatchState* B, TcState* const* ts, const int8_t* const*
                        const int* ncols, int order_mode, cudaStream_t s, int strip_group = 0);
 // One launch of the planned batch (stream-ordered only: capturable).
 cudaError_t batch_launch(TcBatchState* B, TcState* const* ts, cudaStream_t s, int64_t* launches);
+// Operand stages of the inverse-form kernel in later launches: 8 (default) or 6.
+cudaError_t batch_set_stages(TcBatchState* B, int stages);
 void batch_destroy(TcBatchState* B);
 constexpr int kMaxBatchStudies = 8;
 

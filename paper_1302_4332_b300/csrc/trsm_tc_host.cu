@@ -676,9 +676,9 @@ static cudaError_t prepare_study(TcState* t, const int8_t* X, int64_t ldx, int n
 
 // b.ntiles work units: tiles, or (cluster modes) row-panel pairs of a strip.
 static cudaError_t launch_kernel(bool tf32, TileMode mode, const TcBatch& b, int num_sms, int max_clusters,
-                                 cudaStream_t s, int64_t* launches, bool f16 = false) {
+                                 cudaStream_t s, int64_t* launches, bool f16 = false, int stages = 8) {
   ++*launches;
-  return launch_solve(tf32, mode, b, num_sms, max_clusters, s, f16);
+  return launch_solve(tf32, mode, b, num_sms, max_clusters, s, f16, stages);
 }
 
 cudaError_t run_block(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaStream_t s, int64_t* launches,
@@ -806,6 +806,7 @@ struct TcBatchState {
   bool tf32 = false, f16 = false;
   TileMode mode = TILES_SINGLE;
   int num_sms = 0, max_clusters = 0;
+  int stages = 8;                // operand stages of the inverse-form kernel (8 or 6)
   TcStudy* d_studies = nullptr;  // device copies
   uint32_t* d_order = nullptr;
   unsigned int* d_counter = nullptr;
@@ -966,7 +967,13 @@ cudaError_t batch_launch(TcBatchState* B, TcState* const* ts, cudaStream_t s, in
   b.ntiles = B->ntiles;
   b.counter = B->d_counter;
   b.st = B->st;
-  return launch_kernel(B->tf32, B->mode, b, B->num_sms, B->max_clusters, s, launches, B->f16);
+  return launch_kernel(B->tf32, B->mode, b, B->num_sms, B->max_clusters, s, launches, B->f16, B->stages);
+}
+
+cudaError_t batch_set_stages(TcBatchState* B, int stages) {
+  if (stages != 6 && stages != 8) return cudaErrorInvalidValue;
+  B->stages = stages;
+  return cudaSuccess;
 }
 
 void batch_destroy(TcBatchState* B) {

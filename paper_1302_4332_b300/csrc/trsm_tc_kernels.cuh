@@ -116,8 +116,9 @@ cudaError_t set_kernel_attrs(bool tf32, bool clusters);
 // Co-resident 2-CTA clusters of a cluster-mode kernel (one CTA per SM).
 cudaError_t query_clusters(bool tf32, TileMode mode, int num_sms, int* out, bool f16 = false);
 // One launch over b.ntiles work units (tiles, or row-panel pairs of a strip).
+// stages: operand stages of the inverse-form kernel (8 or 6; other modes: 8).
 cudaError_t launch_solve(bool tf32, TileMode mode, const TcBatch& b, int num_sms, int max_clusters,
-                         cudaStream_t s, bool f16 = false);
+                         cudaStream_t s, bool f16 = false, int stages = 8);
 
 }  // namespace tc
 }  // namespace gwas

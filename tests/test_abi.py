@@ -80,3 +80,11 @@ def test_no_device_fails_loudly(lib):
     with pytest.raises(gw.GwasError) as e:
         gw.GLS(np.eye(n), np.ones((n, 1)), np.ones(n), 0.5)
     assert e.value.name in ("GWAS_ERR_CUDA", "GWAS_ERR_UNSUPPORTED")
+
+
+def test_tuning_struct_matches_the_header():
+    """The binding's gwas_batch_tuning mirror has the header's fields, in order."""
+    text = re.sub(r"/\*.*?\*/", "", open(os.path.join(ROOT, "include", "gwas_b300.h")).read(), flags=re.S)
+    body = re.search(r"typedef struct \{([^{}]*)\} gwas_batch_tuning;", text).group(1)
+    fields = re.findall(r"\b(?:int|double)\s+([a-z_0-9]+)\s*;", body)
+    assert fields == [name for name, _ in gw._Tuning._fields_]

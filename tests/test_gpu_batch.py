@@ -91,19 +91,65 @@ def test_batch_studies_of_different_p(prec):
             g.close()
 
 
-def test_batch_autotune_and_skipped_study():
-    studies = _studies("bf16x3", bs=1024)
+@pytest.mark.parametrize("prec,tiles", [("bf16x3", "auto"), ("tf32x3", "pair_mma"), ("f16x2", "auto")])
+def test_batch_autotune_then_oracle_and_skipped_study(prec, tiles):
+    """The autotuner tries columns, tile mode (inverse form / pair product,
+    except for FP16 pieces), stages and orders on seeded dosages; solves
+    after it, in whatever configuration it kept, still meet the oracle."""
+    studies = _studies(prec, bs=1024, tiles=tiles)
     gls = [g for _, g in studies]
     try:
         with gw.GLSBatch(gls) as B:
-            cols, order, rate = B.autotune(reps=2)
-            assert cols in (512, 1024) and order in (0, 1) and rate > 0
+            t = B.autotune_ex(reps=2)
+            assert t["cols"] in (512, 1024) and t["snps_per_s"] > 0 and t["stages"] in (6, 8)
+            assert t["tile_mode"] in (("inverse",) if prec == "f16x2" else ("inverse", "pair_mma"))
+            blocks = [gwas_synth.dosages(s["n"], 1024, 1024 + m, seed=30, study=i)
+                      for i, ((s, _), m) in enumerate(zip(studies, (t["cols"], 300, 64, 511)))]
+            outs = B.solve(blocks)
+            for i, ((s, g), X, (b, se, st)) in enumerate(zip(studies, blocks, outs)):
+                L = oracle.potrf(oracle.form_m(s["Phi"], 0.5, 1.0))
+                pick = np.arange(0, X.shape[1], 13)
+                r, se_o, _, st_o = oracle.gls(L, s["XL"], s["y"], X[:, pick])
+                e = compare(b[:, pick], se[:, pick], st[pick], r, se_o, st_o)
+                assert e["b_norm"] <= 1e-5 and e["se_rel"] <= 1e-5, (prec, t, i, e)
             s0, g0 = studies[0]
-            X = gwas_synth.dosages(s0["n"], 0, cols, seed=30, study=0)
+            X = blocks[0]
             outs = B.solve([X, None, None, None])
             assert outs[1] is None
             b1, se1, st1 = g0.solve_block(X)
-            assert np.array_equal(outs[0][0], b1)
+            if t["tile_mode"] == (g0.solve_shape()[2]):  # the same kernels as the study's own solve
+                assert np.array_equal(outs[0][0], b1)
+    finally:
+        for g in gls:
+            g.close()
+
+
+@pytest.mark.parametrize("prec", ("bf16x3", "f16x2"))
+def test_batch_k_blocks_per_replay(prec):
+    """Three blocks of every study through one graph replay (three batched
+    launches captured together): each block equals the one-block batch solve
+    bit for bit, and the oracle on a sample; a later call with other column
+    counts re-captures."""
+    studies = _studies(prec, bs=512)
+    gls = [g for _, g in studies]
+    Ls = [oracle.potrf(oracle.form_m(s["Phi"], 0.5, 1.0)) for s, _ in studies]
+    try:
+        with gw.GLSBatch(gls) as B:
+            for ms in ((512, 300, 64, 511), (100, 512, 129, 7)):
+                steps = [[gwas_synth.dosages(s["n"], 512 * j, 512 * j + m, seed=32, study=i)
+                          for i, ((s, _), m) in enumerate(zip(studies, ms))] for j in range(3)]
+                outs = B.solve_k(steps)
+                assert len(outs) == 3
+                for j in range(3):
+                    one = B.solve(steps[j])
+                    for i, ((s, g), X) in enumerate(zip(studies, steps[j])):
+                        b, se, st = outs[j][i]
+                        assert np.array_equal(b, one[i][0]) and np.array_equal(se, one[i][1]), (j, i)
+                        assert np.array_equal(st, one[i][2])
+                        pick = np.r_[0, np.arange(1, X.shape[1], 29), X.shape[1] - 1]
+                        r, se_o, _, st_o = oracle.gls(Ls[i], s["XL"], s["y"], X[:, pick])
+                        e = compare(b[:, pick], se[:, pick], st[pick], r, se_o, st_o)
+                        assert e["b_norm"] <= 1e-5 and e["se_rel"] <= 1e-5, (prec, j, i, e)
     finally:
         for g in gls:
             g.close()
