@@ -51,13 +51,14 @@ using tc::TN;
 using tc::TRING;
 
 namespace ex3 {
-constexpr int KCH = 32;                              // FP16 K per stage: one 64-byte swizzle row
+constexpr int KCH = 32;                              // FP16 K per sub-chunk: one 64-byte swizzle row
+constexpr int SUB = 2;                               // sub-chunks per stage (64 K a stage, four MMAs)
 constexpr int KMMA = 16;                             // K per tcgen05.mma (kind::f16)
-constexpr int CPB = TB / KCH;                        // stages per 128-wide K-block
-constexpr int A_BYTES = TB * 64;                     // this CTA's 128 rows of a slice: 8 KB
-constexpr int B_BYTES = (TN / 2) * 64;               // this CTA's 128 SNP columns: 8 KB
-constexpr int STAGE_BYTES = A_BYTES + B_BYTES;       // 16 KB
-constexpr int STAGES = 10;
+constexpr int CPB = TB / (KCH * SUB);                // stages per 128-wide K-block
+constexpr int A_BYTES = TB * 64;                     // this CTA's 128 rows of a slice, one sub-chunk: 8 KB
+constexpr int B_BYTES = (TN / 2) * 64;               // this CTA's 128 SNP columns, one sub-chunk: 8 KB
+constexpr int STAGE_BYTES = SUB * (A_BYTES + B_BYTES);  // 32 KB: [A_0 | A_1 | B_0 | B_1]
+constexpr int STAGES = 6;
 constexpr int CHUNK_BYTES = 2048;                    // epilogue store chunk: 32 rows x 16 int32
 constexpr int ST_COLS = 16;
 constexpr int STG_OFF = STAGES * STAGE_BYTES;
@@ -200,14 +201,17 @@ __global__ void __launch_bounds__(THREADS, 1) exact_product_kernel(const __grid_
             const uint32_t r = cnt / STAGES;
             if (!ptx::mbar_wait(&empty[s], (r & 1) ^ 1, st)) { ok = false; break; }
             uint8_t* sb = smem + s * STAGE_BYTES;
-            const int kx = j * TB + h * KCH;
+            const int kx = j * TB + h * KCH * SUB;
             const uint32_t fb = lead_addr(&full[s]);
             if (leader)
               ptx::mbar_arrive_expect_tx(&full[s], 2 * STAGE_BYTES);
             else
               ptx::mbar_arrive_peer_count(fb);
-            ptx::tma_load_2d_pair(sb, &b.A, fb, kx, arow);
-            ptx::tma_load_2d_pair(sb + A_BYTES, &b.B, fb, kx, ycol);
+#pragma unroll
+            for (int u2 = 0; u2 < SUB; ++u2) {
+              ptx::tma_load_2d_pair(sb + u2 * A_BYTES, &b.A, fb, kx + u2 * KCH, arow);
+              ptx::tma_load_2d_pair(sb + SUB * A_BYTES + u2 * B_BYTES, &b.B, fb, kx + u2 * KCH, ycol);
+            }
           }
         }
         if (!ok) break;
@@ -245,12 +249,14 @@ __global__ void __launch_bounds__(THREADS, 1) exact_product_kernel(const __grid_
             ptx::tc_fence_after();
             const uint32_t base = ptx::smem_u32(smem + s * STAGE_BYTES);
 #pragma unroll
-            for (int kk = 0; kk < KCH / KMMA; ++kk) {
-              const uint32_t off = kk * KMMA * 2;
-              ptx::mma_pair<false>(d, ptx::sdesc_k64(base + off), ptx::sdesc_k64(base + A_BYTES + off), idesc,
-                                   accumulate);
-              accumulate = 1;
-            }
+            for (int u2 = 0; u2 < SUB; ++u2)
+#pragma unroll
+              for (int kk = 0; kk < KCH / KMMA; ++kk) {
+                const uint32_t off = kk * KMMA * 2;
+                ptx::mma_pair<false>(d, ptx::sdesc_k64(base + u2 * A_BYTES + off),
+                                     ptx::sdesc_k64(base + SUB * A_BYTES + u2 * B_BYTES + off), idesc, accumulate);
+                accumulate = 1;
+              }
             ptx::mma_commit_pair(&empty[s], BOTH);
           }
           if (!ok) break;
@@ -421,10 +427,31 @@ __global__ void cast_exact_kernel(const int8_t* __restrict__ X, int64_t ldx, int
   if (lane == 0) shift[col] = (int8_t)c;
   int m = 0;
   __half* o = xc + (int64_t)col * n_pad;
-  for (int r = lane; r < n_pad; r += 32) {
-    const int v = r < n ? (int)x[r] - c : 0;
-    m = max(m, abs(v));
-    o[r] = __int2half_rn(v);
+  if ((reinterpret_cast<uintptr_t>(x) & 15) == 0) {  // 16 values a lane per step (n_pad: a multiple of 128)
+    for (int r = lane * 16; r < n_pad; r += 32 * 16) {
+      int8_t v8[16];
+      if (r + 16 <= n) {
+        *reinterpret_cast<int4*>(v8) = __ldg(reinterpret_cast<const int4*>(x + r));
+      } else {
+#pragma unroll
+        for (int i = 0; i < 16; ++i) v8[i] = r + i < n ? x[r + i] : 0;
+      }
+      __half2 h[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int a = r + 2 * i < n ? (int)v8[2 * i] - c : 0, b2 = r + 2 * i + 1 < n ? (int)v8[2 * i + 1] - c : 0;
+        m = max(m, max(abs(a), abs(b2)));
+        h[i] = __halves2half2(__int2half_rn(a), __int2half_rn(b2));
+      }
+      *reinterpret_cast<int4*>(o + r) = *reinterpret_cast<const int4*>(h);
+      *reinterpret_cast<int4*>(o + r + 8) = *reinterpret_cast<const int4*>(h + 4);
+    }
+  } else {
+    for (int r = lane; r < n_pad; r += 32) {
+      const int v = r < n ? (int)x[r] - c : 0;
+      m = max(m, abs(v));
+      o[r] = __int2half_rn(v);
+    }
   }
   for (int k = 16; k; k >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, k));
   if (lane == 0) atomicMax(xmax, m);
