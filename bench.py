@@ -16,9 +16,11 @@ as in the paper's measurements (Sec. 4).
           step copies its 8 blocks host->device from pinned memory and their
           b / se / status back, overlapped by the library's block ring.
 
-Paths: "fp64" (all-FP64 solve, DFMA) and, when built, the split-precision
+Paths: "fp64" (all-FP64 solve, DFMA), "sliced64" (the FP64 bar from exact
+integer products of a sliced M^-1 on the tensor cores) and the split-precision
 tensor-core paths.  The headline `value` is the fastest split path when one is
-built, else fp64; every path's numbers are in "paths".
+built, else fp64; every path's numbers are in "paths", the two paths held to
+the FP64 bar side by side in "fp64_class".
 
 python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 Multi-GPU: launched by torchrun, one rank per GPU; SNP blocks are sharded
@@ -43,6 +45,7 @@ METRIC = "GLS solves/sec (SNPs/s) at n=10k,p=4: split-prec vs FP64 path, % roofl
 UNIT = "SNPs/s"
 WORKLOAD = "n10k_p4_m1M_int8"
 SPLIT_PATHS = ("bf16x3", "tf32x3", "f16x2")
+SLICED_SLABS = 4  # the sliced path's 10-bit slices of M^-1's triangle
 E2E_REPEATS = 4  # the end-to-end step streams the resident blocks this many times over
 STRIP_GROUP = 0  # tile order of the split paths: strips per group (0 = all)
 N_RESIDENT_BLOCKS = 8
@@ -299,9 +302,11 @@ def run_ours(args, rank, world, local_rank, dist):
             steps, warm_blocks = (args.fp64_steps or 1), args.warmup
         t_init = time.time()
         sg = STRIP_GROUP if args.strip_group is None else args.strip_group
+        tc_split = path in SPLIT_PATHS  # the tile options apply to the split paths only
         g = gw.GLS(s["Phi"], s["XL"], s["y"], w["h"], w["sigma2"], precision=path, bs=bs,
-                   strip_group=sg if path != "fp64" else 0, tiles=tiles if path != "f16x2" or tiles == "auto"
-                   else "inverse", separate_sums=args.separate_sums)
+                   strip_group=sg if tc_split else 0,
+                   tiles=(tiles if path != "f16x2" or tiles == "auto" else "inverse") if tc_split else "auto",
+                   separate_sums=args.separate_sums and tc_split)
         init_s = time.time() - t_init
         b = torch.empty((bs, p), dtype=torch.float64, device=dev).T
         se = torch.empty((bs, p), dtype=torch.float64, device=dev).T
@@ -337,7 +342,7 @@ def run_ours(args, rank, world, local_rank, dist):
         g.timing(False)
         res = dict(snps_per_s=job_rate(world, steps * step_snps, elapsed), ms_per_step=1e3 * elapsed / steps, steps=steps,
                    warmup_blocks=warm_blocks, snps_per_step=step_snps, init_s=init_s, gpu_launches=launches,
-                   strip_group=(sg if path != "fp64" else None),
+                   strip_group=(sg if tc_split else None),
                    solve_shape=dict(zip(("ctas", "cluster", "tiles"), g.solve_shape())),
                    clocks=clk.summary(),
                    stage_ms_per_block={k: v[0] / max(v[1], 1) for k, v in stages.items() if v[1]})
@@ -348,7 +353,16 @@ def run_ours(args, rank, world, local_rank, dist):
         alg_tflop = float(n) * n * bs / 1e12  # n^2 flops per SNP column (Sec. 2.2's trsm)
         achieved = alg_tflop / (kernel_ms / 1e3)
         mode = res["solve_shape"]["tiles"]
-        if path == "fp64":
+        if path == "sliced64":
+            # four FP16 products of M^-1's triangle (10-bit slices) per algorithmic
+            # product; FP16 runs at the BF16 rate
+            pk = (peaks.get("bf16_tflops") or 1800.0) / SLICED_SLABS
+            roof = dict(bound="tensor", achieved=achieved, peak=pk, unit="TFLOP/s", frac=achieved / pk,
+                        traffic=kernel_traffic(path, "sliced"),
+                        peak_basis=(f"bf16 dense tensor peak (of measured, burst; FP16 runs at that rate) / "
+                                    f"{SLICED_SLABS}: {SLICED_SLABS} exact FP16 products of the sliced triangle of "
+                                    "M^-1 per algorithmic product"))
+        elif path == "fp64":
             pk = extra.get("fp64_tflops_cublas")
             roof = dict(bound="alu", achieved=achieved, peak=pk, unit="TFLOP/s",
                         frac=achieved / pk if pk else None, traffic=kernel_traffic(path),
@@ -835,6 +849,14 @@ def main():
                      "frac": hr["snps_per_s"] / (slower * world) if slower else None,
                      "e2e_frac": (hr["e2e"]["value"] / (slower * world)) if slower and hr.get("e2e") else None,
                      "basis": "per GPU: n^2 flop/SNP at the roofline peak; n B/SNP over the measured pinned H2D link"}
+    # the FP64 bar two ways: the FP64 ALU path and the sliced tensor-core path
+    fp64_class = None
+    if "fp64" in results and "sliced64" in results:
+        f, sl = results["fp64"], results["sliced64"]
+        fp64_class = {"fp64_snps_per_s": f["snps_per_s"], "sliced64_snps_per_s": sl["snps_per_s"],
+                      "sliced64_over_fp64": sl["snps_per_s"] / f["snps_per_s"],
+                      "sliced64_e2e": sl.get("e2e"), "sliced64_roofline": sl["roofline"],
+                      "error_vs_oracle": {"fp64": errors.get("fp64"), "sliced64": errors.get("sliced64")}}
     line = {
         "metric": METRIC, "value": hr["snps_per_s"], "unit": UNIT, "n_gpus": world, "steps": hr["steps"],
         "warmup": args.warmup, "ms_per_step": hr["ms_per_step"], "higher_is_better": True, "scaling": "weak",
@@ -846,7 +868,7 @@ def main():
                    "l2": "inputs larger than L2: 8 resident int8 blocks (328 MB) per step plus the n x n operator (split L^-1 or block operator, 204 MB) streamed every block"},
         "roofline": hr["roofline"], "path_roofline": path_roofline, "e2e": hr.get("e2e"),
         "gpu_launches": hr["gpu_launches"],
-        "clocks": hr["clocks"], "cpu_baseline": cpu, "paths": paths_out, "forms": forms,
+        "clocks": hr["clocks"], "cpu_baseline": cpu, "fp64_class": fp64_class, "paths": paths_out, "forms": forms,
         "storage_precision": storage,
         "peaks": {"measured_file": {k: out["peaks"].get(k) for k in ("hbm_gbs", "bf16_tflops", "bf16_tflops_sustained")},
                   "measured_here": out["extra"]},

@@ -76,8 +76,23 @@ extern "C" {
  *                 GWAS_ERR_ARG): each row of L^-1 is scaled by a power of two so its
  *                 largest entry lies in [2^13, 2^14), then split into FP16 hi + lo
  *                 (11 + 11 significant bits against BF16's 8 + 8), the dosages exact
- *                 in FP16: two products at the BF16 rate; results scaled back exactly. */
-typedef enum { GWAS_FP64 = 0, GWAS_TF32X3 = 1, GWAS_BF16X3 = 2, GWAS_F16X2 = 3 } gwas_precision;
+ *                 in FP16: two products at the BF16 rate; results scaled back exactly.
+ *   GWAS_SLICED64 : FP64-class results (the FP64 path's tolerance) from the tensor cores.
+ *                 Eq. 1's X_i^T M^-1 X_i and X_i^T M^-1 y are formed with W = M^-1 made
+ *                 explicit once in FP64 (L^-T L^-1, at gwas_init): per SNP, with x' the
+ *                 int8 column shifted by its integer mean, x'^T [X^_L | y^] (X^_L = W X_L,
+ *                 y^ = W y) and x'^T W x' = 2 x'^T T x' (T = W's lower triangle, diagonal
+ *                 halved).  T's rows (one power-of-two scale) are cut into four 10-bit
+ *                 integer slices and [X^_L | y^]'s columns into six, each exact in FP16;
+ *                 every slice times the int8 dosages is an exact integer (FP16 products,
+ *                 FP32 accumulation kept below 2^24), so the only error is T's 40-bit
+ *                 representation.  Four triangular FP16 products per block.  Tile modes,
+ *                 strip_group, separate_sums and single_piece do not apply (GWAS_ERR_ARG
+ *                 if set); batches take split contexts only.  A block whose largest
+ *                 |x - c| * 512 * n_pad reaches 2^31 is refused (GWAS_ERR_ARG; never for
+ *                 dosages 0..2 below n = 2,000,000).  Set-up holds 8 n_pad^2 bytes of W
+ *                 and up to 8 n_pad^2 (slices) + 16 n_pad bs (products) bytes. */
+typedef enum { GWAS_FP64 = 0, GWAS_TF32X3 = 1, GWAS_BF16X3 = 2, GWAS_F16X2 = 3, GWAS_SLICED64 = 4 } gwas_precision;
 
 typedef struct {
   int precision;   /* gwas_precision */
@@ -368,7 +383,8 @@ int gwas_get_info(const gwas_ctx *ctx, int *n, int *p, int *n_pad, int *precisio
 /* Launch shape of the blocked triangular solve for a full block: *ctas thread blocks (one per SM),
    in clusters of *cluster_size (2 in the pair tile modes, else 1), and *tile_mode, the resolved
    gwas_config.tile_mode (never GWAS_TILES_AUTO).  FP64 contexts report the occupancy-bound grid of
-   the FP64 solve, 1 and GWAS_TILES_SINGLE.  Any output pointer may be NULL. */
+   the FP64 solve, 1 and GWAS_TILES_SINGLE; GWAS_SLICED64 contexts the exact product kernel's CTAs,
+   2 and GWAS_TILES_AUTO (no tile mode applies).  Any output pointer may be NULL. */
 int gwas_solve_shape(const gwas_ctx *ctx, int *ctas, int *cluster_size, int *tile_mode);
 
 /* Index of the first failing Cholesky pivot after GWAS_ERR_NOT_SPD, else -1. */

@@ -27,10 +27,12 @@ ERRORS = {
 }
 GWAS_ERR_ARG, GWAS_ERR_NOT_SPD, GWAS_ERR_CUDA, GWAS_ERR_TIMEOUT = -1, -2, -3, -4
 GWAS_ERR_IO, GWAS_ERR_NOMEM, GWAS_ERR_UNSUPPORTED = -5, -6, -7
-PRECISIONS = {"fp64": 0, "tf32x3": 1, "bf16x3": 2, "f16x2": 3}
+PRECISIONS = {"fp64": 0, "tf32x3": 1, "bf16x3": 2, "f16x2": 3, "sliced64": 4}
 # split modes: how the solve's tiles map onto SMs (gwas_config.tile_mode)
 TILE_MODES = {"auto": 0, "single": 1, "pair_mma": 3, "inverse": 4}
-BUILT_PRECISIONS = ("fp64", "bf16x3", "tf32x3", "f16x2")
+BUILT_PRECISIONS = ("fp64", "bf16x3", "tf32x3", "f16x2", "sliced64")
+# the split precisions (tensor-core solves to the 1e-5 bar; batches take these)
+SPLIT_PRECISIONS = ("bf16x3", "tf32x3", "f16x2")
 SNP_OK, SNP_SINGULAR = 0, 1
 
 # Every symbol the header declares (checked by the CPU test suite).
@@ -286,7 +288,9 @@ class GLS:
     phi_or_L: n x n kinship Phi (or, with is_L=True, the lower factor L of M).
     XL: n x (p-1) covariates; y: n phenotypes; M = sigma2 (h Phi + (1-h) I).
     precision: "fp64", "tf32x3", "bf16x3" or "f16x2" (the inverse tile mode's
-    row-scaled FP16 pieces of L^-1) for the blocked triangular solve.
+    row-scaled FP16 pieces of L^-1) for the blocked triangular solve, or
+    "sliced64" (FP64-class results from exact integer products of a sliced
+    M^-1 on the tensor cores; tile options do not apply).
     """
 
     def __init__(self, phi_or_L, XL, y, h: float, sigma2: float = 1.0, *, precision: str = "fp64",

@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(256) adjoint_snp_kernel(const double* __restri
 }
 
 // The split precisions' adjoint from the exact products C = A x' of
-// adjoint_exact.cu (A: three slabs of RS rows, slab k = slice k of W's rows,
+// exact_products.cu (A: three slabs of RS rows, slab k = slice k of W's rows,
 // then slices k and k + 3 of the ne = 2(q+1) appended rows [X^_L | y^ |
 // W X^_L | W y^]^T): one warp per SNP column.  Over W's rows r < n, with the
 // integers x'_r and c_k = C[k RS + r]:

@@ -66,17 +66,21 @@ constexpr int BAR_OFF = STG_OFF + EPI_WARPS * 2 * CHUNK_BYTES;
 constexpr int NBARS = 2 * STAGES + 4 + 3 * TRING + 1;
 constexpr int SMEM = 1024 + BAR_OFF + NBARS * 8 + TRING * 4 + 16;
 static_assert(SMEM <= 232448, "shared memory per CTA");
-constexpr int SLABS = 3;
+constexpr int SLABS = 3;        // the adjoint: three 10-bit slices of W (30 bits)
+constexpr int SOLVE_SLABS = 4;  // the sliced solve: four slices of W's triangle (40 bits)
 
 struct Params {
-  CUtensorMap A;  // the stacked slices: dims {n_pad, 3 RS}, box {32, 128}, 64-byte swizzle, FP16
+  CUtensorMap A;  // the stacked slices: dims {n_pad, slabs RS}, box {32, 128}, 64-byte swizzle, FP16
   CUtensorMap B;  // x' (FP16): dims {n_pad, bs}, box {32, 128}, 64-byte swizzle
-  CUtensorMap C;  // the int32 product: dims {3 RS, bs}, box {32, 16}
+  CUtensorMap C;  // the int32 product: dims {slabs RS, bs}, box {32, 16}
   int P;          // K-blocks of 128 (n_pad / 128)
   int U;          // row-panel pairs per slab (RS / 256)
   int RS;         // rows per slab
+  int slabs;      // slices of the square part (3: the adjoint's W; 4: the solve's triangle)
+  int tri;        // 1: the square part is lower triangular (rows < 256 (u + 1) of pair u need
+                  // K-blocks < 2u + 2 only) and units go out longest first
   int Cs;         // 256-column strips of the block
-  int ntiles;     // work units: SLABS * U * Cs
+  int ntiles;     // work units: slabs * U * Cs
   const int* xmax;         // largest |x'| of the block (set by the cast)
   unsigned int* counter;   // unit counter (zeroed by the cast)
   DevStatus* st;
@@ -93,6 +97,32 @@ __device__ __forceinline__ int partial_span(int xmax, int P) {
 // The int32 totals hold 512 * xmax * n_pad at most: beyond 2^31 the block is refused.
 __device__ __forceinline__ bool in_range(int xmax, int P) {
   return 512LL * xmax * (long long)TB * P < (1LL << 31);
+}
+
+// Work unit t -> (slab, row-panel pair u, 256-column strip c) and its K-blocks.
+// Dense: slab by slab.  Triangular: pair rows from the longest (all K-blocks)
+// to the shortest over every slab and strip, so the launch ends on short units.
+struct Unit {
+  int slab, u, c, kend;
+};
+__device__ __forceinline__ Unit unit_of(const Params& b, int t) {
+  Unit v;
+  if (b.tri) {
+    const int per = b.slabs * b.Cs;
+    v.u = b.U - 1 - t / per;
+    const int rem = t - (b.U - 1 - v.u) * per;
+    v.slab = rem / b.Cs;
+    v.c = rem - v.slab * b.Cs;
+    v.kend = 2 * v.u + 2 <= b.P ? 2 * v.u + 2 : b.P;  // a pair of the triangle, or one holding appended rows
+  } else {
+    const int per = b.U * b.Cs;
+    v.slab = t / per;
+    const int rem = t - v.slab * per;
+    v.u = rem / b.Cs;
+    v.c = rem - v.u * b.Cs;
+    v.kend = b.P;
+  }
+  return v;
 }
 
 __global__ void __launch_bounds__(THREADS, 1) exact_product_kernel(const __grid_constant__ Params b) {
@@ -127,7 +157,6 @@ __global__ void __launch_bounds__(THREADS, 1) exact_product_kernel(const __grid_
   if (!ok_range && blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&st->err, DEV_OK, DEV_ERR_RANGE);
   const int ntiles = ok_range ? b.ntiles : 0;
   const int G = partial_span(xmax, b.P);
-  const int nparts = (b.P + G - 1) / G;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -159,14 +188,6 @@ __global__ void __launch_bounds__(THREADS, 1) exact_product_kernel(const __grid_
   ptx::cluster_sync();  // both CTAs' barriers and tensor memory exist before any remote access
   const uint32_t tmem_base = *tmem_slot;
 
-  auto decode = [&](int t, int& slab, int& u, int& c) {
-    const int per = b.U * b.Cs;
-    slab = t / per;
-    const int rem = t - slab * per;
-    u = rem / b.Cs;
-    c = rem - u * b.Cs;
-  };
-
   if (warp == 0) {
     // ------------------------------------------------ scheduler + TMA producer
     if (lane == 0) {
@@ -190,12 +211,11 @@ __global__ void __launch_bounds__(THREADS, 1) exact_product_kernel(const __grid_
           t = tile_ring[slot];
         }
         if (t >= ntiles) break;
-        int slab, u, c;
-        decode(t, slab, u, c);
-        const int arow = slab * b.RS + (2 * u + (int)rank) * TB;  // this CTA's 128 rows of A
-        const int ycol = c * TN + (int)rank * (TN / 2);           // this CTA's 128 SNP columns
+        const Unit un = unit_of(b, t);
+        const int arow = un.slab * b.RS + (2 * un.u + (int)rank) * TB;  // this CTA's 128 rows of A
+        const int ycol = un.c * TN + (int)rank * (TN / 2);              // this CTA's 128 SNP columns
         bool ok = true;
-        for (int j = 0; j < b.P && ok; ++j) {
+        for (int j = 0; j < un.kend && ok; ++j) {
           for (int h = 0; h < CPB; ++h, ++cnt) {
             const int s = cnt % STAGES;
             const uint32_t r = cnt / STAGES;
@@ -230,10 +250,11 @@ __global__ void __launch_bounds__(THREADS, 1) exact_product_kernel(const __grid_
         ptx::mbar_arrive(&tile_empty[slot]);
         if (t >= ntiles) break;
         if (!leader) continue;
+        const int kend = unit_of(b, t).kend;
         bool ok = true;
         int a = 0;
         uint32_t d = 0, accumulate = 0;
-        for (int j = 0; j < b.P && ok; ++j) {
+        for (int j = 0; j < kend && ok; ++j) {
           if (j % G == 0) {  // a fresh partial every G K-blocks, alternating between the two buffers
             a = kb & 1;
             if (!ptx::mbar_wait(&part_empty[a], ((kb >> 1) & 1) ^ 1, st)) { ok = false; break; }
@@ -260,7 +281,7 @@ __global__ void __launch_bounds__(THREADS, 1) exact_product_kernel(const __grid_
             ptx::mma_commit_pair(&empty[s], BOTH);
           }
           if (!ok) break;
-          if (j % G == G - 1 || j == b.P - 1) ptx::mma_commit_pair(&part_full[a], BOTH);
+          if (j % G == G - 1 || j == kend - 1) ptx::mma_commit_pair(&part_full[a], BOTH);
         }
         if (!ok) break;
       }
@@ -282,8 +303,8 @@ __global__ void __launch_bounds__(THREADS, 1) exact_product_kernel(const __grid_
       ptx::named_bar(1, NT);
       if (lane == 0) ptx::mbar_arrive(&tile_empty[slot]);
       if (t >= ntiles) break;
-      int slab, u, c;
-      decode(t, slab, u, c);
+      const Unit un = unit_of(b, t);
+      const int nparts = (un.kend + G - 1) / G;
 #pragma unroll
       for (int i = 0; i < EPI_COLS; ++i) master[i] = 0;
       bool ok = true;
@@ -307,8 +328,8 @@ __global__ void __launch_bounds__(THREADS, 1) exact_product_kernel(const __grid_
       }
       if (!ok) break;
       // the tile's int32 products to HBM through TMA stores of 2 KB chunks
-      const int r0 = slab * b.RS + (2 * u + (int)rank) * TB + 32 * lq;
-      const int c0 = c * TN + chalf * EPI_COLS;
+      const int r0 = un.slab * b.RS + (2 * un.u + (int)rank) * TB + 32 * lq;
+      const int c0 = un.c * TN + chalf * EPI_COLS;
 #pragma unroll
       for (int q = 0; q < EPI_COLS / ST_COLS; ++q) {
         uint8_t* buf = stg + (gq & 1) * CHUNK_BYTES;
@@ -375,30 +396,36 @@ __device__ __forceinline__ double slice_of(double v, double s, int k) {
   return a;
 }
 
-// The stacked slices A (3 slabs of RS rows, row-major, n_pad columns, FP16).
-// Row R of a slab: R < n_pad: W's row R (W symmetric: read as its column, so
-// that the threads of a block read consecutive entries); n_pad <= R < n_pad +
-// 2 ne: appended row e = (R - n_pad) % ne of [X^_L | y^ | W X^_L | W y^] (the
-// columns of Ex, n_pad x ne), slice k for the first ne rows, k + 3 for the
-// next; further rows zero.
+// The stacked slices A (slabs of RS rows, row-major, n_pad columns, FP16).
+// Row R of slab k: R < n_pad: row R of the square part, W itself or (tri)
+// its lower triangle with the diagonal halved, T (x'^T W x' = 2 x'^T T x');
+// W is symmetric, so its row R is read as its column and the threads of a
+// block read consecutive entries.  n_pad <= R < n_pad + 2 ne: appended row
+// e = (R - n_pad) % ne (the columns of Ex, n_pad x ne), slice k for the first
+// ne rows, slice k + 3 for the next, in slabs 0..2 (zero in later slabs).
+// Further rows zero.
 __global__ void slice_rows_kernel(const double* __restrict__ W, const double* __restrict__ Ex, int n_pad, int ne,
-                                  int RS, const double* __restrict__ scale, __half* __restrict__ A) {
+                                  int RS, int slabs, int tri, const double* __restrict__ scale,
+                                  __half* __restrict__ A) {
   const int R = blockIdx.y;
   const int col = blockIdx.x * blockDim.x + threadIdx.x;
   if (col >= n_pad) return;
   double v = 0.0, s = 1.0;
-  int k0 = 0;
+  int k0 = 0, kind = 0;  // 1: square part, 2: appended row
   if (R < n_pad) {
     v = W[col + (int64_t)R * n_pad];
+    if (tri) v = col < R ? v : (col == R ? 0.5 * v : 0.0);  // halving is exact
     s = scale[0];
+    kind = 1;
   } else if (R < n_pad + 2 * ne) {
     const int e = (R - n_pad) % ne;
     k0 = (R - n_pad) / ne * 3;
     v = Ex[col + (int64_t)e * n_pad];
     s = scale[1 + e];
+    kind = 2;
   }
-  for (int k = 0; k < ex3::SLABS; ++k) {
-    const double a = (R < n_pad + 2 * ne) ? slice_of(v, s, k0 + k) : 0.0;
+  for (int k = 0; k < slabs; ++k) {
+    const double a = kind == 1 ? slice_of(v, s, k) : (kind == 2 && k < 3) ? slice_of(v, s, k0 + k) : 0.0;
     A[((int64_t)k * RS + R) * n_pad + col] = __float2half_rn((float)a);  // an integer in [-512, 512]: exact
   }
 }
@@ -548,23 +575,26 @@ __global__ void __launch_bounds__(256) exact_dy_apply_kernel(const double* __res
 }
 
 // ------------------------------------------------------------------- host side
-struct ExactAdjoint {
-  int n = 0, n_pad = 0, q = 0, bs = 0, P = 0, U = 0, RS = 0, ne = 0;
-  bool center = false;
+// One state serves both uses of the exact products: the adjoint (W dense in 3
+// slabs; appended rows [X^_L | y^ | W X^_L | W y^]) and the sliced solve (W's
+// triangle T in 4 slabs; appended rows [X^_L | Y^]).
+struct ExactProducts {
+  int n = 0, n_pad = 0, q = 0, bs = 0, P = 0, U = 0, RS = 0, ne = 0, slabs = 0;
+  bool tri = false, center = false;
   int max_clusters = 0;
-  double* W = nullptr;          // n_pad x n_pad FP64 (owned)
-  __half* A = nullptr;          // 3 RS x n_pad FP16 slices
+  double* W = nullptr;          // n_pad x n_pad FP64 (owned; kept by the adjoint for its y-gradient)
+  __half* A = nullptr;          // slabs RS x n_pad FP16 slices
   __half* xc = nullptr;         // n_pad x bs FP16 x'
-  int32_t* C = nullptr;         // 3 RS x bs int32 products
+  int32_t* C = nullptr;         // slabs RS x bs int32 products
   int8_t* shift = nullptr;      // bs
   int* xmax = nullptr;          // [0] largest |x'|; [1..] the unit counter
   double* inv_scale = nullptr;  // [0] 1 / s_W, [1 + e] 1 / s_e
-  double* part = nullptr;       // y-gradient chunk partials
-  double* z = nullptr;          // n_pad
+  double* part = nullptr;       // the adjoint's y-gradient chunk partials
+  double* z = nullptr;          // n_pad (adjoint)
   ex3::Params prm;
 };
 
-void exact_adjoint_destroy(ExactAdjoint* E) {
+void exact_destroy(ExactProducts* E) {
   if (!E) return;
   cudaFree(E->W);
   cudaFree(E->A);
@@ -586,11 +616,12 @@ static double pow2_scale(double mx) {  // 2^e with mx 2^e <= 512 < mx 2^(e+1); 1
   return std::ldexp(1.0, e);
 }
 
-cudaError_t exact_adjoint_create(ExactAdjoint** out, double* W, const double* What, const double* W2, int n,
-                                 int n_pad, int q, int bs, bool center, int num_sms, cudaStream_t s,
-                                 int64_t* launches) {
+// W (taken over), Ex = the ne appended columns (n_pad x ne, read here only).
+static cudaError_t exact_create(ExactProducts** out, double* W, const double* Ex, int ne, int slabs, bool tri,
+                                bool keep_w, int n, int n_pad, int q, int bs, bool center, int num_sms,
+                                cudaStream_t s, int64_t* launches) {
   *out = nullptr;
-  ExactAdjoint* E = new ExactAdjoint;
+  ExactProducts* E = new ExactProducts;
   E->W = W;
   E->n = n;
   E->n_pad = n_pad;
@@ -599,36 +630,33 @@ cudaError_t exact_adjoint_create(ExactAdjoint** out, double* W, const double* Wh
   E->P = n_pad / TB;
   E->U = (E->P + 2) / 2;  // row-panel pairs over W's P panels and one panel of appended rows
   E->RS = 2 * E->U * TB;
-  E->ne = 2 * (q + 1);
+  E->ne = ne;
+  E->slabs = slabs;
+  E->tri = tri;
   E->center = center;
-  const int ne = E->ne;
   cudaError_t e;
-#define TRY(x)                   \
-  do {                           \
-    e = (x);                     \
-    if (e != cudaSuccess) {      \
-      exact_adjoint_destroy(E);  \
-      return e;                  \
-    }                            \
+#define TRY(x)            \
+  do {                    \
+    e = (x);              \
+    if (e != cudaSuccess) { \
+      exact_destroy(E);   \
+      return e;           \
+    }                     \
   } while (0)
-  const size_t rows = (size_t)ex3::SLABS * E->RS;
+  const size_t rows = (size_t)slabs * E->RS;
   TRY(cudaMalloc(&E->A, sizeof(__half) * rows * n_pad));
   TRY(cudaMalloc(&E->xc, sizeof(__half) * (size_t)n_pad * bs));
   TRY(cudaMalloc(&E->C, sizeof(int32_t) * rows * bs));
   TRY(cudaMalloc(&E->shift, (size_t)bs));
   TRY(cudaMalloc(&E->xmax, 64));
   TRY(cudaMalloc(&E->inv_scale, sizeof(double) * (1 + ne)));
-  const int nchunks = (bs + EX_DY_CHUNK - 1) / EX_DY_CHUNK;
-  TRY(cudaMalloc(&E->part, sizeof(double) * (size_t)nchunks * n));
-  TRY(cudaMalloc(&E->z, sizeof(double) * (size_t)n_pad));
+  if (keep_w) {
+    const int nchunks = (bs + EX_DY_CHUNK - 1) / EX_DY_CHUNK;
+    TRY(cudaMalloc(&E->part, sizeof(double) * (size_t)nchunks * n));
+    TRY(cudaMalloc(&E->z, sizeof(double) * (size_t)n_pad));
+  }
   TRY(cudaMemsetAsync(E->xc, 0, sizeof(__half) * (size_t)n_pad * bs, s));
-  // the appended columns [X^_L | y^ | W X^_L | W y^] side by side
-  double* Ex = nullptr;
-  TRY(cudaMallocAsync(&Ex, sizeof(double) * (size_t)n_pad * ne, s));
-  TRY(cudaMemcpyAsync(Ex, What, sizeof(double) * (size_t)n_pad * (q + 1), cudaMemcpyDeviceToDevice, s));
-  TRY(cudaMemcpyAsync(Ex + (size_t)n_pad * (q + 1), W2, sizeof(double) * (size_t)n_pad * (q + 1),
-                      cudaMemcpyDeviceToDevice, s));
-  // scales: the largest entry of W and of every appended row
+  // scales: the largest entry of W (bounds T's too) and of every appended row
   unsigned long long* mx = nullptr;
   TRY(cudaMallocAsync(&mx, sizeof(unsigned long long) * (size_t)(n_pad + ne), s));
   TRY(cudaMemsetAsync(mx, 0, sizeof(unsigned long long) * (size_t)(n_pad + ne), s));
@@ -657,12 +685,17 @@ cudaError_t exact_adjoint_create(ExactAdjoint** out, double* W, const double* Wh
   TRY(cudaMallocAsync(&dsc, sizeof(double) * (1 + ne), s));
   TRY(cudaMemcpyAsync(dsc, sc.data(), sizeof(double) * (1 + ne), cudaMemcpyHostToDevice, s));
   TRY(cudaMemcpyAsync(E->inv_scale, inv.data(), sizeof(double) * (1 + ne), cudaMemcpyHostToDevice, s));
-  slice_rows_kernel<<<dim3((n_pad + 255) / 256, E->RS), 256, 0, s>>>(W, Ex, n_pad, ne, E->RS, dsc, E->A);
+  slice_rows_kernel<<<dim3((n_pad + 255) / 256, E->RS), 256, 0, s>>>(W, Ex, n_pad, ne, E->RS, slabs, tri ? 1 : 0,
+                                                                     dsc, E->A);
   *launches += 1;
   TRY(cudaGetLastError());
-  TRY(cudaFreeAsync(Ex, s));
   TRY(cudaFreeAsync(mx, s));
   TRY(cudaFreeAsync(dsc, s));
+  TRY(cudaStreamSynchronize(s));
+  if (!keep_w) {
+    cudaFree(E->W);
+    E->W = nullptr;
+  }
   // tensor maps and the launch parameters (the block width fixed at bs; a
   // shorter block covers only its strips)
   tc::EncodeTiledFn enc = nullptr;
@@ -677,6 +710,8 @@ cudaError_t exact_adjoint_create(ExactAdjoint** out, double* W, const double* Wh
   p.P = E->P;
   p.U = E->U;
   p.RS = E->RS;
+  p.slabs = slabs;
+  p.tri = tri ? 1 : 0;
   p.xmax = E->xmax;
   p.counter = reinterpret_cast<unsigned int*>(E->xmax + 1);
   TRY(cudaFuncSetAttribute(ex3::exact_product_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, ex3::SMEM));
@@ -696,18 +731,42 @@ cudaError_t exact_adjoint_create(ExactAdjoint** out, double* W, const double* Wh
     TRY(cudaOccupancyMaxActiveClusters(&E->max_clusters, ex3::exact_product_kernel, &cfg));
     if (E->max_clusters < 1) TRY(cudaErrorLaunchOutOfResources);
   }
-  TRY(cudaStreamSynchronize(s));
 #undef TRY
   *out = E;
   return cudaSuccess;
 }
 
-cudaError_t exact_adjoint_block(ExactAdjoint* E, const int8_t* X, int64_t ldx, int ncols, const SolveConsts* sc,
-                                const double* GH, const double* What, double h, double sigma2, double* chi2,
-                                double* dh, double* wv, double* uT, double* dh_accum, double* dy_accum,
-                                DevStatus* st, cudaStream_t s, int64_t* launches) {
-  if (ncols <= 0) return cudaSuccess;
-  if (ncols > E->bs) return cudaErrorInvalidValue;
+cudaError_t exact_adjoint_create(ExactProducts** out, double* W, const double* What, const double* W2, int n,
+                                 int n_pad, int q, int bs, bool center, int num_sms, cudaStream_t s,
+                                 int64_t* launches) {
+  *out = nullptr;
+  const int ne = 2 * (q + 1);
+  double* Ex = nullptr;  // the appended columns [X^_L | y^ | W X^_L | W y^] side by side
+  cudaError_t e = cudaMallocAsync(&Ex, sizeof(double) * (size_t)n_pad * ne, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(Ex, What, sizeof(double) * (size_t)n_pad * (q + 1), cudaMemcpyDeviceToDevice, s);
+  if (e == cudaSuccess)
+    e = cudaMemcpyAsync(Ex + (size_t)n_pad * (q + 1), W2, sizeof(double) * (size_t)n_pad * (q + 1),
+                        cudaMemcpyDeviceToDevice, s);
+  if (e != cudaSuccess) {
+    if (Ex) cudaFreeAsync(Ex, s);
+    cudaFree(W);
+    return e;
+  }
+  e = exact_create(out, W, Ex, ne, ex3::SLABS, false, true, n, n_pad, q, bs, center, num_sms, s, launches);
+  cudaFreeAsync(Ex, s);
+  return e;
+}
+
+cudaError_t exact_solve_create(ExactProducts** out, double* W, const double* Wh, int nw, int n, int n_pad, int q,
+                               int bs, bool center, int num_sms, cudaStream_t s, int64_t* launches) {
+  return exact_create(out, W, Wh, nw, ex3::SOLVE_SLABS, true, false, n, n_pad, q, bs, center, num_sms, s, launches);
+}
+
+// x' of a block into the FP16 operand (columns past ncols of the last strip
+// zeroed), then the product C = A x' over the block's strips.
+static cudaError_t exact_cast_product(ExactProducts* E, const int8_t* X, int64_t ldx, int ncols, DevStatus* st,
+                                      cudaStream_t s, cudaEvent_t k0, cudaEvent_t k1) {
   cudaError_t e;
   if ((e = cudaMemsetAsync(E->xmax, 0, sizeof(int), s)) != cudaSuccess) return e;
   // the last strip's columns past ncols: zeros, not an earlier block's values
@@ -721,26 +780,37 @@ cudaError_t exact_adjoint_block(ExactAdjoint* E, const int8_t* X, int64_t ldx, i
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   ex3::Params p = E->prm;
   p.Cs = (ncols + TN - 1) / TN;
-  p.ntiles = ex3::SLABS * p.U * p.Cs;
+  p.ntiles = E->slabs * p.U * p.Cs;
   p.st = st;
-  {
-    const int ncl = std::min(p.ntiles, E->max_clusters);
-    cudaLaunchConfig_t cfg;
-    std::memset(&cfg, 0, sizeof cfg);
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeClusterDimension;
-    attr[0].val.clusterDim.x = 2;
-    attr[0].val.clusterDim.y = 1;
-    attr[0].val.clusterDim.z = 1;
-    cfg.gridDim = dim3(2 * ncl);
-    cfg.blockDim = dim3(THREADS);
-    cfg.dynamicSmemBytes = ex3::SMEM;
-    cfg.stream = s;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    if ((e = cudaLaunchKernelEx(&cfg, ex3::exact_product_kernel, p)) != cudaSuccess) return e;
-  }
-  const int64_t ldc = (int64_t)ex3::SLABS * E->RS;
+  const int ncl = std::min(p.ntiles, E->max_clusters);
+  cudaLaunchConfig_t cfg;
+  std::memset(&cfg, 0, sizeof cfg);
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = 2;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(2 * ncl);
+  cfg.blockDim = dim3(THREADS);
+  cfg.dynamicSmemBytes = ex3::SMEM;
+  cfg.stream = s;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  if (k0 && (e = cudaEventRecord(k0, s)) != cudaSuccess) return e;
+  if ((e = cudaLaunchKernelEx(&cfg, ex3::exact_product_kernel, p)) != cudaSuccess) return e;
+  if (k1 && (e = cudaEventRecord(k1, s)) != cudaSuccess) return e;
+  return cudaSuccess;
+}
+
+cudaError_t exact_adjoint_block(ExactProducts* E, const int8_t* X, int64_t ldx, int ncols, const SolveConsts* sc,
+                                const double* GH, const double* What, double h, double sigma2, double* chi2,
+                                double* dh, double* wv, double* uT, double* dh_accum, double* dy_accum,
+                                DevStatus* st, cudaStream_t s, int64_t* launches) {
+  if (ncols <= 0) return cudaSuccess;
+  if (ncols > E->bs || E->tri || !E->W) return cudaErrorInvalidValue;
+  cudaError_t e;
+  if ((e = exact_cast_product(E, X, ldx, ncols, st, s, nullptr, nullptr)) != cudaSuccess) return e;
+  const int64_t ldc = (int64_t)E->slabs * E->RS;
   if ((e = launch_exact_adjoint_sums(E->C, ldc, E->RS, E->xc, E->n_pad, E->n, E->n_pad, E->ne, E->inv_scale, sc, GH,
                                      E->q, ncols, h, sigma2, E->xmax, chi2, dh, wv, dh_accum, uT, s)) != cudaSuccess)
     return e;
@@ -751,6 +821,23 @@ cudaError_t exact_adjoint_block(ExactAdjoint* E, const int8_t* X, int64_t ldx, i
   exact_dy_apply_kernel<<<(E->n + 7) / 8, 256, 0, s>>>(E->W, E->n_pad, E->n, E->z, What, uT, E->q, dy_accum);
   *launches += 7;
   return cudaGetLastError();
+}
+
+int exact_max_ctas(const ExactProducts* E) { return E ? 2 * E->max_clusters : 0; }
+
+cudaError_t exact_solve_product(ExactProducts* E, const int8_t* X, int64_t ldx, int ncols, DevStatus* st,
+                                cudaStream_t s, cudaEvent_t k0, cudaEvent_t k1) {
+  if (ncols <= 0) return cudaSuccess;
+  if (ncols > E->bs || !E->tri) return cudaErrorInvalidValue;
+  return exact_cast_product(E, X, ldx, ncols, st, s, k0, k1);
+}
+
+cudaError_t exact_solve_sums(ExactProducts* E, int ncols, const SolveConsts* sc, int t, double* b, double* se,
+                             int* status, cudaStream_t s) {
+  if (ncols <= 0) return cudaSuccess;
+  if (ncols > E->bs || !E->tri) return cudaErrorInvalidValue;
+  return launch_sliced_solve(E->C, (int64_t)E->slabs * E->RS, E->RS, E->xc, E->n_pad, E->n, E->ne, E->inv_scale, sc,
+                             E->q, t, ncols, b, se, status, E->center ? E->shift : nullptr, s);
 }
 
 }  // namespace gwas

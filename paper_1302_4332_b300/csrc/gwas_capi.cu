@@ -53,7 +53,8 @@ struct gwas_ctx {
   double* GH = nullptr;        // (q+1)^2 Gram of What
   double* adj = nullptr;       // per-SNP chi2 (bs), dh (bs), y-weights (bs x p), uT (q), dh/dy staging (1 + n),
                                // the y-gradient's chunk partials (adjoint_dy_chunks(bs) x n)
-  ExactAdjoint* exact = nullptr;  // split precisions: the adjoint's exact products (built on first use)
+  ExactProducts* exact = nullptr;   // split precisions: the adjoint's exact products (built on first use)
+  ExactProducts* sliced = nullptr;  // GWAS_SLICED64: the solve's exact products (built at gwas_init)
   bool separate_sums = false, single_piece = false;  // the split set-up's options (a batch's tuner repeats them)
   // pinned host buffers of the file reader, kept across gwas_solve_file calls
   std::vector<void*> file_buf;
@@ -189,14 +190,56 @@ int solve_f64_cols(gwas_ctx* ctx, const double* X, int64_t ldx, int rows, int nc
   return GWAS_OK;
 }
 
-// The adjoint's loop-invariant part: the transpose operator, X^_L and y^, their Gram.
-int ensure_adjoint(gwas_ctx* ctx) {
+// The transpose block operator (for L^-T solves).
+int ensure_aop_t(gwas_ctx* ctx) {
   if (ctx->AopT) return GWAS_OK;
   const size_t np = (size_t)ctx->n_pad;
-  const int nc = ctx->q + 1;
   CK(dmalloc(&ctx->AopT, sizeof(double) * np * np));
   CK(cudaMemsetAsync(ctx->AopT, 0, sizeof(double) * np * np, ctx->stream));
   CK(launch_build_aop_t(ctx->L, ctx->Dinv, ctx->n_pad, ctx->AopT, ctx->stream, &ctx->launches));
+  return GWAS_OK;
+}
+
+// W = M^-1 = L^-T L^-1 in FP64 (n_pad x n_pad, zero on the padding): the FP64
+// solves of the identity, bs columns at a time.  *out receives the device array.
+int form_inverse(gwas_ctx* ctx, double** out) {
+  *out = nullptr;
+  int rc = ensure_aop_t(ctx);
+  if (rc != GWAS_OK) return rc;
+  const size_t np = (size_t)ctx->n_pad;
+  const int n = ctx->n;
+  double *W = nullptr, *E = nullptr;
+  rc = [&]() -> int {
+    CK(dmalloc(&W, sizeof(double) * np * np));
+    CK(cudaMemsetAsync(W, 0, sizeof(double) * np * np, ctx->stream));
+    CK(dmalloc(&E, sizeof(double) * (size_t)n * std::min(ctx->bs, n)));
+    for (int c0 = 0; c0 < n; c0 += ctx->bs) {
+      const int ncc = std::min(ctx->bs, n - c0);
+      CK(launch_identity_cols(E, n, c0, ncc, ctx->stream));
+      ctx->launches += 1;
+      int r = solve_f64_cols(ctx, E, n, n, ncc, ctx->Xt, false);
+      if (r == GWAS_OK) r = solve_f64_cols(ctx, ctx->Xt, ctx->n_pad, ctx->n_pad, ncc, W + (size_t)c0 * np, true);
+      if (r != GWAS_OK) return r;
+    }
+    CK(cudaStreamSynchronize(ctx->stream));
+    return GWAS_OK;
+  }();
+  cudaFree(E);
+  if (rc != GWAS_OK) {
+    cudaFree(W);
+    return rc;
+  }
+  *out = W;
+  return GWAS_OK;
+}
+
+// The adjoint's loop-invariant part: the transpose operator, X^_L and y^, their Gram.
+int ensure_adjoint(gwas_ctx* ctx) {
+  if (ctx->What) return GWAS_OK;
+  const size_t np = (size_t)ctx->n_pad;
+  const int nc = ctx->q + 1;
+  int rc0 = ensure_aop_t(ctx);
+  if (rc0 != GWAS_OK) return rc0;
   CK(dmalloc(&ctx->Xhat, sizeof(double) * np * std::max(ctx->bs, nc)));
   CK(dmalloc(&ctx->What, sizeof(double) * np * nc));
   CK(dmalloc(&ctx->GH, sizeof(double) * nc * nc));
@@ -209,40 +252,30 @@ int ensure_adjoint(gwas_ctx* ctx) {
   return GWAS_OK;
 }
 
-// The split precisions' adjoint set-up: W = M^-1 = L^-T L^-1 in FP64 (the
-// FP64 solves of the identity, bs columns at a time), W [X^_L | y^] likewise,
-// then the exact slices of both (exact_adjoint_create).
+// The split precisions' adjoint set-up: W = M^-1 (form_inverse), W [X^_L | y^]
+// by the FP64 solves, then the exact slices of both (exact_adjoint_create).
 int ensure_exact_adjoint(gwas_ctx* ctx) {
   if (ctx->exact) return GWAS_OK;
   int rc = ensure_adjoint(ctx);
   if (rc != GWAS_OK) return rc;
   const size_t np = (size_t)ctx->n_pad;
   const int n = ctx->n, nc = ctx->q + 1;
-  double *W = nullptr, *E = nullptr, *W2 = nullptr;
+  double *W = nullptr, *W2 = nullptr;
   auto release = [&] {
     cudaFree(W);
-    cudaFree(E);
     cudaFree(W2);
   };
   rc = [&]() -> int {
-    CK(dmalloc(&W, sizeof(double) * np * np));
-    CK(cudaMemsetAsync(W, 0, sizeof(double) * np * np, ctx->stream));
-    CK(dmalloc(&E, sizeof(double) * (size_t)n * std::min(ctx->bs, n)));
+    int r = form_inverse(ctx, &W);
+    if (r != GWAS_OK) return r;
     CK(dmalloc(&W2, sizeof(double) * np * nc));
-    for (int c0 = 0; c0 < n; c0 += ctx->bs) {
-      const int ncc = std::min(ctx->bs, n - c0);
-      CK(launch_identity_cols(E, n, c0, ncc, ctx->stream));
-      ctx->launches += 1;
-      int r = solve_f64_cols(ctx, E, n, n, ncc, ctx->Xt, false);
-      if (r == GWAS_OK) r = solve_f64_cols(ctx, ctx->Xt, ctx->n_pad, ctx->n_pad, ncc, W + (size_t)c0 * np, true);
-      if (r != GWAS_OK) return r;
-    }
-    int r = solve_f64_cols(ctx, ctx->What, ctx->n_pad, ctx->n_pad, nc, ctx->Xt, false);
+    r = solve_f64_cols(ctx, ctx->What, ctx->n_pad, ctx->n_pad, nc, ctx->Xt, false);
     if (r == GWAS_OK) r = solve_f64_cols(ctx, ctx->Xt, ctx->n_pad, ctx->n_pad, nc, W2, true);
     if (r != GWAS_OK) return r;
-    CK(exact_adjoint_create(&ctx->exact, W, ctx->What, W2, n, ctx->n_pad, ctx->q, ctx->bs, ctx->intercept,
+    double* Wt = W;
+    W = nullptr;  // owned by the exact state from here on, failures included
+    CK(exact_adjoint_create(&ctx->exact, Wt, ctx->What, W2, n, ctx->n_pad, ctx->q, ctx->bs, ctx->intercept,
                             ctx->num_sms, ctx->stream, &ctx->launches));
-    W = nullptr;  // owned by the exact state now
     return check_device_status(ctx);
   }();
   release();
@@ -273,6 +306,30 @@ int run_block(gwas_ctx* ctx, const void* X, bool int8_input, int64_t ldx, int nc
                              b, se, status, ctx->stream, nullptr, nullptr, nullptr, 0, nullptr, ctx->t));
     }
     ctx->launches += 1;
+    return GWAS_OK;
+  }
+  if (ctx->prec == GWAS_SLICED64) {  // exact products of the sliced M^-1 (any alignment of X)
+    int64_t nl = 0;
+    {
+      StageMark m(ctx, GWAS_STAGE_TRSM, ctx->stream);
+      cudaEvent_t k0 = ctx->timing ? pool_event(ctx) : nullptr, k1 = ctx->timing ? pool_event(ctx) : nullptr;
+      cudaError_t e = exact_solve_product(ctx->sliced, static_cast<const int8_t*>(X), ldx, ncols, ctx->st,
+                                          ctx->stream, k0, k1);
+      if (ctx->timing && e == cudaSuccess) {
+        ctx->marks.push_back({GWAS_STAGE_SOLVE, k0, k1});
+      } else if (ctx->timing) {
+        ctx->event_pool.push_back(k0);
+        ctx->event_pool.push_back(k1);
+      }
+      if (e != cudaSuccess) return fail(ctx, GWAS_ERR_CUDA, "sliced solve: %s", cudaGetErrorString(e));
+      nl += 2;
+    }
+    {
+      StageMark m(ctx, GWAS_STAGE_REDUCE, ctx->stream);
+      CK(exact_solve_sums(ctx->sliced, ncols, ctx->sc, ctx->t, b, se, status, ctx->stream));
+      nl += 1;
+    }
+    ctx->launches += nl;
     return GWAS_OK;
   }
   // split precision: the TMA map of X needs a 16-byte aligned base and leading dimension
@@ -374,7 +431,8 @@ void free_all(gwas_ctx* c) {
   cudaFree(c->AopT); cudaFree(c->Xhat); cudaFree(c->What); cudaFree(c->GH); cudaFree(c->adj);
   cudaFreeHost(c->h_b); cudaFreeHost(c->h_se); cudaFreeHost(c->h_status);
   if (c->tcs) tc::destroy(c->tcs);
-  exact_adjoint_destroy(c->exact);
+  exact_destroy(c->exact);
+  exact_destroy(c->sliced);
   for (auto* p : c->file_buf) cudaFreeHost(p);
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
   delete c;
@@ -419,10 +477,13 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
   if (n < 1 || p < 1 || p > QMAX + 1 || !phi_or_L || !y || (p > 1 && !XL) || !(h >= 0.0 && h <= 1.0) ||
       !(sigma2 > 0.0) || cfg.bs < 1 || cfg.ring_depth < 2 || cfg.strip_group < 0 || cfg.tile_mode < GWAS_TILES_AUTO || cfg.tile_mode > GWAS_TILES_INVERSE ||
       cfg.tile_mode == 2 /* not a mode */ ||
-      cfg.precision < GWAS_FP64 || cfg.precision > GWAS_F16X2 ||
+      cfg.precision < GWAS_FP64 || cfg.precision > GWAS_SLICED64 ||
       (cfg.precision == GWAS_F16X2 && cfg.tile_mode != GWAS_TILES_AUTO && cfg.tile_mode != GWAS_TILES_INVERSE))
     return GWAS_ERR_ARG;
   if (cfg.separate_sums != 0 && cfg.separate_sums != 1) return GWAS_ERR_ARG;
+  if (cfg.precision == GWAS_SLICED64 &&
+      (cfg.tile_mode != GWAS_TILES_AUTO || cfg.strip_group != 0 || cfg.separate_sums != 0 || cfg.single_piece != 0))
+    return GWAS_ERR_ARG;
   if (cfg.single_piece != 0 && cfg.single_piece != 1) return GWAS_ERR_ARG;
   if (cfg.single_piece && (cfg.precision == GWAS_FP64 ||
                            (cfg.tile_mode != GWAS_TILES_AUTO && cfg.tile_mode != GWAS_TILES_INVERSE)))
@@ -550,8 +611,36 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
     if (hs.err != DEV_OK) return fail(ctx, GWAS_ERR_TIMEOUT, "set-up solve timed out");
     if (hs.sc_err) return fail(ctx, GWAS_ERR_NOT_SPD, "S_TL = X~_L^T X~_L is singular (collinear covariates)");
 
+    // the sliced solve: W = M^-1, Wh = W [X_L | Y] = L^-T [X~_L | Y~], their slices
+    if (ctx->prec == GWAS_SLICED64) {
+      int rc0;
+      double* Wm = nullptr;
+      if ((rc0 = form_inverse(ctx, &Wm)) != GWAS_OK) return rc0;
+      double* Wh = nullptr;
+      if (dmalloc(&Wh, sizeof(double) * np * nw) != cudaSuccess) {
+        cudaFree(Wm);
+        return fail(ctx, GWAS_ERR_NOMEM, "sliced set-up: out of device memory");
+      }
+      rc0 = solve_f64_cols(ctx, ctx->W, ctx->n_pad, ctx->n_pad, nw, Wh, true);
+      cudaError_t e = cudaSuccess;
+      if (rc0 == GWAS_OK)  // Wm is taken over by the state, on failure too
+        e = exact_solve_create(&ctx->sliced, Wm, Wh, nw, ctx->n, ctx->n_pad, ctx->q, cfg.bs, ctx->intercept,
+                               ctx->num_sms, ctx->stream, &ctx->launches);
+      else
+        cudaFree(Wm);
+      cudaStreamSynchronize(ctx->stream);
+      cudaFree(Wh);
+      if (rc0 != GWAS_OK) return rc0;
+      if (e != cudaSuccess)
+        return fail(ctx, e == cudaErrorMemoryAllocation ? GWAS_ERR_NOMEM : GWAS_ERR_CUDA, "sliced set-up: %s",
+                    cudaGetErrorString(e));
+      if ((rc0 = check_device_status(ctx)) != GWAS_OK) return rc0;
+      cudaFree(ctx->AopT);  // needed again only by the adjoint, which rebuilds it
+      ctx->AopT = nullptr;
+    }
+
     // split-precision operands: hi + lo copies of the block operator
-    if (ctx->prec != GWAS_FP64) {
+    if (ctx->prec != GWAS_FP64 && ctx->prec != GWAS_SLICED64) {
       int64_t nl = 0;
       const tc::Split sp = ctx->prec == GWAS_BF16X3 ? tc::SPLIT_BF16
                            : ctx->prec == GWAS_F16X2 ? tc::SPLIT_F16
@@ -961,7 +1050,7 @@ int gwas_adjoint_block(gwas_ctx* ctx, const int8_t* XR, int64_t ldx, int ncols, 
   if (split) {
     // the split adjoint: every per-SNP input from one exact integer product
     // of the sliced [W ; X^_L^T ; y^T ; (W X^_L)^T ; (W y^)^T] with the block's
-    // shifted dosages on the tensor cores (adjoint_exact.cu); the per-SNP
+    // shifted dosages on the tensor cores (exact_products.cu); the per-SNP
     // adjoint arithmetic and the y-gradient in FP64
     if ((rc = ensure_exact_adjoint(ctx)) != GWAS_OK) return rc;
     int64_t nl = 0;
@@ -1765,6 +1854,10 @@ int gwas_solve_shape(const gwas_ctx* ctx, int* ctas, int* cluster_size, int* til
   if (ctx->tcs) {
     tc::launch_shape(ctx->tcs, &g, &cl);
     mode = static_cast<int>(tc::tile_mode(ctx->tcs));
+  } else if (ctx->sliced) {
+    g = exact_max_ctas(ctx->sliced);
+    cl = 2;
+    mode = GWAS_TILES_AUTO;
   } else {
     const int tiles = (ctx->n_pad / TB) * ((ctx->bs + F64_TN - 1) / F64_TN);
     g = trsm_f64_grid(ctx->num_sms);

@@ -157,23 +157,45 @@ cudaError_t launch_adjoint(const double* Xt, const double* Xh, int64_t ldt, int 
                            double* dh_accum, double* dy_accum, double* dy_part, cudaStream_t s);
 // Scratch of the y-gradient: adjoint_dy_chunks(bs) x n doubles (dy_part).
 int adjoint_dy_chunks(int bs);
-// The split precisions' adjoint in its M^-1 form with exact integer products
-// (adjoint_exact.cu).  Set-up: W = M^-1 (n_pad x n_pad FP64, symmetric, zero
-// on the padding; the state takes ownership), What = [X^_L | y^] and W2 = W
-// What (n_pad x (q+1) each, read during set-up only); center: X_L[:, 0] is
-// the intercept (SNP columns are shifted by their integer mean).
-struct ExactAdjoint;
-cudaError_t exact_adjoint_create(ExactAdjoint** out, double* W, const double* What, const double* W2, int n,
+// Exact integer products of sliced M^-1 on the tensor cores (exact_products.cu),
+// in two uses.  The split precisions' adjoint in its M^-1 form: W = M^-1
+// (n_pad x n_pad FP64, symmetric, zero on the padding; the state takes
+// ownership), What = [X^_L | y^] and W2 = W What (n_pad x (q+1) each, read
+// during set-up only).  The sliced solve (GWAS_SLICED64): W (taken over and
+// freed once sliced) and Wh = [X^_L | Y^] (n_pad x nw, nw = q + t, read during
+// set-up only).  center: X_L[:, 0] is the intercept (SNP columns are shifted
+// by their integer mean).
+struct ExactProducts;
+cudaError_t exact_adjoint_create(ExactProducts** out, double* W, const double* What, const double* W2, int n,
                                  int n_pad, int q, int bs, bool center, int num_sms, cudaStream_t s,
                                  int64_t* launches);
+cudaError_t exact_solve_create(ExactProducts** out, double* W, const double* Wh, int nw, int n, int n_pad, int q,
+                               int bs, bool center, int num_sms, cudaStream_t s, int64_t* launches);
 // One block of ncols <= bs int8 SNP columns (device, any alignment): chi2 and
 // d chi2/dh per SNP, wv (p per SNP), dh_accum += the block's sum of d chi2/dh,
 // uT = the block's sums of wv[0..q-1], dy_accum += the block's y-gradient.
-cudaError_t exact_adjoint_block(ExactAdjoint* E, const int8_t* X, int64_t ldx, int ncols, const SolveConsts* sc,
+cudaError_t exact_adjoint_block(ExactProducts* E, const int8_t* X, int64_t ldx, int ncols, const SolveConsts* sc,
                                 const double* GH, const double* What, double h, double sigma2, double* chi2,
                                 double* dh, double* wv, double* uT, double* dh_accum, double* dy_accum,
                                 DevStatus* st, cudaStream_t s, int64_t* launches);
-void exact_adjoint_destroy(ExactAdjoint* E);
+// One block of the sliced solve in two steps: the cast of x' and the exact
+// product (two launches; k0/k1, may be null, recorded around the product
+// kernel), then the per-SNP sums and solve: b (t blocks of p x ncols), se,
+// status.
+cudaError_t exact_solve_product(ExactProducts* E, const int8_t* X, int64_t ldx, int ncols, DevStatus* st,
+                                cudaStream_t s, cudaEvent_t k0, cudaEvent_t k1);
+cudaError_t exact_solve_sums(ExactProducts* E, int ncols, const SolveConsts* sc, int t, double* b, double* se,
+                             int* status, cudaStream_t s);
+void exact_destroy(ExactProducts* E);
+// CTAs of a full launch of the exact product kernel (2-SM clusters).
+int exact_max_ctas(const ExactProducts* E);
+// The sliced solve's per-SNP sums from the exact products and the FP64 p x p
+// solve (reduce_solve.cu).  C: slabs x RS rows per SNP (leading dimension
+// ldc), xc: x' in FP16 (leading dimension ldx = n_pad), ne = q + t appended rows.
+cudaError_t launch_sliced_solve(const int32_t* C, int64_t ldc, int RS, const __half* xc, int64_t ldx, int n,
+                                int ne, const double* inv_scale, const SolveConsts* sc, int q, int t, int ncols,
+                                double* b, double* se, int* status, const int8_t* shift, cudaStream_t s,
+                                int64_t bstride = 0);
 // The per-SNP sums and adjoint from the exact products (adjoint.cu), then the
 // block's sums of d chi2/dh (added to dh_accum) and of wv[0..q-1] (into uT).
 cudaError_t launch_exact_adjoint_sums(const int32_t* C, int64_t ldc, int RS, const __half* xc, int64_t ldx, int n,

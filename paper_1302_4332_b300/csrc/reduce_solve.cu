@@ -627,6 +627,84 @@ cudaError_t launch_partials_solve(const float* red, int ngroups, int64_t ldr, co
   return e != cudaSuccess ? e : cudaGetLastError();
 }
 
+// ------------------------------------------- sliced solve: sums from exact products
+// The per-SNP inputs of the solve as products of x' (the shifted int8 column)
+// with fixed FP64 data (W = M^-1, W^ = [X^_L | Y^] = W [X_L | Y]):
+//     S_BL = x~^T X~_L = x'^T X^_L,   r_B = x~^T y~ = x'^T y^,   S_BR = x~^T x~ = x'^T W x' = 2 x'^T T x',
+// T = W's lower triangle with its diagonal halved.  C holds, per SNP, the
+// exact int32 products of x' with SL = 4 slabs of 10-bit slices: slab k row r
+// (r < n_pad) = slice k of (T x')_r in units of 2^-10k / s_T; rows n_pad + e
+// and n_pad + ne + e of slabs 0..2 = slices k and k + 3 of W^[:, e]^T x'.
+// Here: sum_r x'_r C_k[r] exactly in int64 (|x'_r C| < 2^39), the four slabs
+// and the six slices combined in FP64 (smallest first), then the FP64 solve.
+constexpr int SOLVE_SL = 4;
+
+template <int QM>
+__global__ void __launch_bounds__(256) sliced_solve_kernel(
+    const int32_t* __restrict__ C, int64_t ldc, int RS, const __half* __restrict__ xc, int64_t ldx, int n, int n_pad,
+    int ne, const double* __restrict__ inv_scale, const SolveConsts* __restrict__ sc, int q, int t, int ncols,
+    double* __restrict__ b, double* __restrict__ se, int* __restrict__ status, const int8_t* __restrict__ shift,
+    int64_t bstride) {
+  const int lane = threadIdx.x & 31;
+  const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (col >= ncols) return;
+  const int32_t* cc = C + (int64_t)col * ldc;
+  const __half* x = xc + (int64_t)col * ldx;
+  long long pk[SOLVE_SL] = {0, 0, 0, 0};
+#pragma unroll 4
+  for (int r = lane; r < n; r += 32) {
+    const int xi = __half2int_rn(x[r]);
+#pragma unroll
+    for (int k = 0; k < SOLVE_SL; ++k) pk[k] += (long long)xi * __ldcs(cc + k * RS + r);
+  }
+#pragma unroll
+  for (int k = 0; k < SOLVE_SL; ++k)
+#pragma unroll
+    for (int o = 16; o; o >>= 1) pk[k] += __shfl_xor_sync(0xffffffffu, pk[k], o);
+  // appended row `lane` (< ne): six slices, the smallest first
+  double ev = 0.0;
+  if (lane < ne) {
+    const int r0 = n_pad + lane, r1 = n_pad + ne + lane;
+    double v = 0.0;
+    v = fma((double)cc[2 * RS + r1], 0x1p-50, v);
+    v = fma((double)cc[RS + r1], 0x1p-40, v);
+    v = fma((double)cc[r1], 0x1p-30, v);
+    v = fma((double)cc[2 * RS + r0], 0x1p-20, v);
+    v = fma((double)cc[RS + r0], 0x1p-10, v);
+    ev = ((double)cc[r0] + v) * inv_scale[1 + lane];
+  }
+  double acc[QM + 2];
+#pragma unroll
+  for (int a = 0; a <= QM; ++a) acc[a] = __shfl_sync(0xffffffffu, ev, a);
+  if (lane != 0) return;
+  double v = (double)pk[3] * 0x1p-30;  // |pk| < 2^53: exact conversions
+  v = fma((double)pk[2], 0x1p-20, v);
+  v = fma((double)pk[1], 0x1p-10, v);
+  acc[QM + 1] = 2.0 * ((double)pk[0] + v) * inv_scale[0];
+  solve_store<QM>(acc, sc, q, col, b, se, status, shift ? (double)shift[col] : 0.0, t, bstride);
+}
+
+cudaError_t launch_sliced_solve(const int32_t* C, int64_t ldc, int RS, const __half* xc, int64_t ldx, int n,
+                                int ne, const double* inv_scale, const SolveConsts* sc, int q, int t, int ncols,
+                                double* b, double* se, int* status, const int8_t* shift, cudaStream_t s,
+                                int64_t bstride) {
+  if (ncols <= 0) return cudaSuccess;
+  if (t < 1 || ne != q + t || ne > QMAX + 1) return cudaErrorInvalidValue;
+  if (bstride == 0) bstride = (int64_t)(q + 1) * ncols;
+  const int n_pad = (int)ldx;
+  const int grid = (ncols + 7) / 8;
+  if (ne <= 4)
+    sliced_solve_kernel<3><<<grid, 256, 0, s>>>(C, ldc, RS, xc, ldx, n, n_pad, ne, inv_scale, sc, q, t, ncols, b, se,
+                                                status, shift, bstride);
+  else if (ne <= 8)
+    sliced_solve_kernel<7><<<grid, 256, 0, s>>>(C, ldc, RS, xc, ldx, n, n_pad, ne, inv_scale, sc, q, t, ncols, b, se,
+                                                status, shift, bstride);
+  else
+    sliced_solve_kernel<QMAX><<<grid, 256, 0, s>>>(C, ldc, RS, xc, ldx, n, n_pad, ne, inv_scale, sc, q, t, ncols, b,
+                                                   se, status, shift, bstride);
+  return cudaGetLastError();
+}
+
 // W32 = W in FP32, row-major with row stride w32_stride(q) (zero-padded).
 __global__ void make_w32_kernel(const double* __restrict__ W, int64_t ldw, int rows, int nc, int ws,
                                 float* __restrict__ W32) {

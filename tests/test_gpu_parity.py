@@ -150,8 +150,8 @@ SPLITS = ("bf16x3", "tf32x3", "f16x2")
 TILES = ("single", "pair_mma", "inverse")
 # f16x2 exists in the inverse form only
 SPLIT_TILES = [(p, t) for p in SPLITS for t in TILES if p != "f16x2" or t == "inverse"]
-FULL_CASES = [("fp64", "auto")] + [(p, t) for p in SPLITS for t in ("auto",) + TILES
-                                   if p != "f16x2" or t in ("auto", "inverse")]
+FULL_CASES = [("fp64", "auto"), ("sliced64", "auto")] + [(p, t) for p in SPLITS for t in ("auto",) + TILES
+                                                          if p != "f16x2" or t in ("auto", "inverse")]
 
 
 @pytest.mark.parametrize("prec,tiles", SPLIT_TILES)
@@ -219,14 +219,14 @@ def _phenotypes(s, t, seed=5):
     return np.asfortranarray(np.column_stack(cols))
 
 
-@pytest.mark.parametrize("prec", ("fp64",) + SPLITS)
+@pytest.mark.parametrize("prec", ("fp64", "sliced64") + SPLITS)
 @pytest.mark.parametrize("n,p,m,t", [(640, 4, 300, 5), (300, 2, 130, 3), (257, 6, 65, 11)])
 def test_several_phenotypes(prec, n, p, m, t):
     """t phenotypes sharing one study: b of each equals its own single-phenotype
     GLS (the oracle run per column of Y); se and status are shared."""
     s, X, L, _ = _case(n, p, 2 * n, 0.5, m=m)
     Y = _phenotypes(s, t)
-    tol = TOL64 if prec == "fp64" else TOL_SPLIT
+    tol = TOL64 if prec in ("fp64", "sliced64") else TOL_SPLIT
     with gw.GLS(s["Phi"], s["XL"] if p > 1 else None, Y, 0.5, 1.0, precision=prec, bs=m) as g:
         b, se_g, st_g = g.solve_block(X)
         b_s, se_s, st_s = g.solve_stream(np.asfortranarray(X))
@@ -407,8 +407,10 @@ def test_full_size_seeded_sample(paper_scale, paper_scale_sample, prec, tiles):
 
 # b: per-SNP normwise relative error (the stated bar: 1e-10 FP64, 1e-5 split);
 # se: component-wise relative error, same bars.
-FULL_TOL = {"fp64": (1e-10, 1e-10), "bf16x3": (1e-5, 1e-5), "tf32x3": (1e-5, 1e-5), "f16x2": (1e-5, 1e-5)}
-COMP_TOL = {"bf16x3": 2e-5, "tf32x3": 1e-5, "f16x2": 1e-5}
+FULL_TOL = {"fp64": (1e-10, 1e-10), "sliced64": (1e-10, 1e-10), "bf16x3": (1e-5, 1e-5), "tf32x3": (1e-5, 1e-5),
+            "f16x2": (1e-5, 1e-5)}
+# the sliced path carries the FP64 bar component by component too
+COMP_TOL = {"sliced64": 1e-10, "bf16x3": 2e-5, "tf32x3": 1e-5, "f16x2": 1e-5}
 
 
 @pytest.mark.parametrize("prec,tiles", FULL_CASES)
