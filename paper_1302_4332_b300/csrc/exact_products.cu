@@ -1,35 +1,42 @@
-// a11 in the split precisions: the adjoint from exact integer products on the
-// tensor cores (the M^-1 form).
+// Exact integer products of a sliced M^-1 on the tensor cores, in two uses:
+// the split precisions' adjoint (a11) and the sliced solve (GWAS_SLICED64, the
+// FP64 bar from the tensor cores).
 //
 // With W = M^-1 (symmetric), X^_L = W X_L, y^ = W y and x' = x - c 1 (the SNP
 // column shifted by the integer nearest its mean when X_L[:, 0] is the
-// intercept: [X_L | x'] spans the same space, so the Wald statistic and its
-// gradient do not change), every per-SNP input of the adjoint is a product
-// of a fixed FP64 matrix with the small integers x':
+// intercept: [X_L | x'] spans the same space, so b_p, its se, the Wald
+// statistic and its gradient do not change, and b_0 maps back exactly), the
+// per-SNP inputs are products of fixed FP64 data with the small integers x':
 //   forward sums    x~^T X~_L = x'^T X^_L,  x~^T y~ = x'^T y^,  x~^T x~ = x'^T (W x'),
 //   transpose sums  x^^T X^_L = x'^T (W X^_L),  x^^T y^ = x'^T (W y^),  ||x^||^2 = ||W x'||^2,
-// (x~ = L^-1 x', x^ = L^-T x~ = W x').  So one product per block, A x' with
-//   A = [ W ; X^_L^T ; y^T ; (W X^_L)^T ; (W y^)^T ]   ((n_pad + 2(q+1)) x n_pad),
-// gives all of them; the adjoint arithmetic (adjoint.cu) stays FP64.
+// (x~ = L^-1 x', x^ = L^-T x~ = W x': Eq. 1's X_i^T M^-1 X_i and X_i^T M^-1 y
+// with M^-1 explicit).  So one product per block, A x':
+//   adjoint   A = [ W ; X^_L^T ; y^T ; (W X^_L)^T ; (W y^)^T ],
+//   solve     A = [ T ; X^_L^T ; Y^^T ],  T = W's lower triangle with its diagonal
+//             halved (x'^T W x' = 2 x'^T T x'), so that the product skips the
+//             K-blocks above each row pair's diagonal;
+// the arithmetic after the product (adjoint.cu, reduce_solve.cu) is FP64.
 //
 // Exact slices.  Each row of A, scaled by a power of two s (one s for all of
-// W's rows, one per appended row) so that its largest entry is at most 512 in
-// magnitude, is written as a_1 + a_2 2^-10 + a_3 2^-20 + ..., every a_k an
-// integer in [-512, 512] (exact in FP16).  W's rows keep three slices (30
-// bits), the appended rows six: their dot products with a centred x' can
-// cancel, and three slices left ~1e-7 relative error in the gradient where
-// six leave ~4e-9 (a CPU emulation of this scheme at n = 300..3000).  A slice
-// times the integer dosages, accumulated by the tensor cores in FP32, is
-// exact while every partial sum stays below 2^24: at most 256 / max|x'|
-// K-blocks of 128 go into one TMEM partial (every K-block of a dosage block
-// up to n = 16,384 with |x'| <= 2), and the epilogue adds the partials as
-// int32.  The products leave as int32 and are combined per SNP in FP64 and
-// int64 (adjoint.cu), so the only error left is the slices' representation.
+// the square part's rows, one per appended row) so that its largest entry is
+// at most 512 in magnitude, is written as a_1 + a_2 2^-10 + a_3 2^-20 + ...,
+// every a_k an integer in [-512, 512] (exact in FP16).  The square part keeps
+// three slices in the adjoint (30 bits) and four in the solve (40 bits: the
+// FP64 bar on b and se), the appended rows six: their dot products with a
+// centred x' can cancel, and three slices left ~1e-7 relative error in the
+// gradient where six leave ~4e-9 (a CPU emulation of this scheme at n =
+// 300..3000).  A slice times the integer dosages, accumulated by the tensor
+// cores in FP32, is exact while every partial sum stays below 2^24: at most
+// 256 / max|x'| K-blocks of 128 go into one TMEM partial (every K-block of a
+// dosage block up to n = 16,384 with |x'| <= 2), and the epilogue adds the
+// partials as int32.  The products leave as int32 and are combined per SNP in
+// FP64 and int64, so the only error left is the slices' representation.
 //
-// Layout: A holds three slabs of RS rows (RS = 256 ceil((P + 1) / 2)), slab k
-// = slice k of W's n_pad rows, then slice k of the 2(q+1) appended rows, then
-// their slice k + 3, then zero rows; FP16, row-major (K contiguous).  The
-// product C = A x' is 3 RS x ncols int32, column-major (leading dimension 3 RS).
+// Layout: A holds `slabs` slabs of RS rows (RS = 256 ceil((P + 1) / 2)), slab
+// k = slice k of the square part's n_pad rows, then (slabs 0..2) slice k of
+// the ne appended rows and their slice k + 3, then zero rows; FP16, row-major
+// (K contiguous).  The product C = A x' is slabs RS x ncols int32,
+// column-major (leading dimension slabs RS).
 #include <cuda.h>
 #include <cuda_fp16.h>
 
