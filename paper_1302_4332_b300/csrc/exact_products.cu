@@ -21,8 +21,9 @@
 // the square part's rows, one per appended row) so that its largest entry is
 // at most 512 in magnitude, is written as a_1 + a_2 2^-10 + a_3 2^-20 + ...,
 // every a_k an integer in [-512, 512] (exact in FP16).  The square part keeps
-// three slices in the adjoint (30 bits) and four in the solve (40 bits: the
-// FP64 bar on b and se), the appended rows six: their dot products with a
+// three slices in the adjoint (30 bits) and five in the solve (50 bits: b and
+// se at the FP64 path's accuracy even where z-scores reach 1e5), the appended
+// rows six: their dot products with a
 // centred x' can cancel, and three slices left ~1e-7 relative error in the
 // gradient where six leave ~4e-9 (a CPU emulation of this scheme at n =
 // 300..3000).  A slice times the integer dosages, accumulated by the tensor
@@ -74,7 +75,7 @@ constexpr int NBARS = 2 * STAGES + 4 + 3 * TRING + 1;
 constexpr int SMEM = 1024 + BAR_OFF + NBARS * 8 + TRING * 4 + 16;
 static_assert(SMEM <= 232448, "shared memory per CTA");
 constexpr int SLABS = 3;        // the adjoint: three 10-bit slices of W (30 bits)
-constexpr int SOLVE_SLABS = 4;  // the sliced solve: four slices of W's triangle (40 bits)
+constexpr int SOLVE_SLABS = 5;  // the sliced solve: five slices of W's triangle (50 bits)
 
 struct Params {
   CUtensorMap A;  // the stacked slices: dims {n_pad, slabs RS}, box {32, 128}, 64-byte swizzle, FP16

@@ -632,12 +632,12 @@ cudaError_t launch_partials_solve(const float* red, int ngroups, int64_t ldr, co
 // with fixed FP64 data (W = M^-1, W^ = [X^_L | Y^] = W [X_L | Y]):
 //     S_BL = x~^T X~_L = x'^T X^_L,   r_B = x~^T y~ = x'^T y^,   S_BR = x~^T x~ = x'^T W x' = 2 x'^T T x',
 // T = W's lower triangle with its diagonal halved.  C holds, per SNP, the
-// exact int32 products of x' with SL = 4 slabs of 10-bit slices: slab k row r
+// exact int32 products of x' with SOLVE_SL = 5 slabs of 10-bit slices: slab k row r
 // (r < n_pad) = slice k of (T x')_r in units of 2^-10k / s_T; rows n_pad + e
 // and n_pad + ne + e of slabs 0..2 = slices k and k + 3 of W^[:, e]^T x'.
-// Here: sum_r x'_r C_k[r] exactly in int64 (|x'_r C| < 2^39), the four slabs
+// Here: sum_r x'_r C_k[r] exactly in int64 (|x'_r C| < 2^39), the five slabs
 // and the six slices combined in FP64 (smallest first), then the FP64 solve.
-constexpr int SOLVE_SL = 4;
+constexpr int SOLVE_SL = 5;
 
 template <int QM>
 __global__ void __launch_bounds__(256) sliced_solve_kernel(
@@ -650,7 +650,7 @@ __global__ void __launch_bounds__(256) sliced_solve_kernel(
   if (col >= ncols) return;
   const int32_t* cc = C + (int64_t)col * ldc;
   const __half* x = xc + (int64_t)col * ldx;
-  long long pk[SOLVE_SL] = {0, 0, 0, 0};
+  long long pk[SOLVE_SL] = {0, 0, 0, 0, 0};
 #pragma unroll 4
   for (int r = lane; r < n; r += 32) {
     const int xi = __half2int_rn(x[r]);
@@ -677,7 +677,8 @@ __global__ void __launch_bounds__(256) sliced_solve_kernel(
 #pragma unroll
   for (int a = 0; a <= QM; ++a) acc[a] = __shfl_sync(0xffffffffu, ev, a);
   if (lane != 0) return;
-  double v = (double)pk[3] * 0x1p-30;  // |pk| < 2^53: exact conversions
+  double v = (double)pk[4] * 0x1p-40;  // |pk| < 2^53: exact conversions
+  v = fma((double)pk[3], 0x1p-30, v);
   v = fma((double)pk[2], 0x1p-20, v);
   v = fma((double)pk[1], 0x1p-10, v);
   acc[QM + 1] = 2.0 * ((double)pk[0] + v) * inv_scale[0];
