@@ -88,10 +88,19 @@ struct Params {
   int tri;        // 1: the square part is lower triangular (rows < 256 (u + 1) of pair u need
                   // K-blocks < 2u + 2 only) and units go out longest first
   int Cs;         // 256-column strips of the block
+  int ncols;      // SNP columns of the block (the last strip may be partial)
   int ntiles;     // work units: slabs * U * Cs
   const int* xmax;         // largest |x'| of the block (set by the cast)
   unsigned int* counter;   // unit counter (zeroed by the cast)
   DevStatus* st;
+  // the sliced solve (tri) only, else null: the epilogue of every pair wholly
+  // inside the triangle forms sum_r x'_r (T_k x')_r over its rows and adds it to
+  // acc[k * ldacc + column] (int64, exact: integer additions in any order) instead
+  // of storing its rows of C; x' read from xc (FP16, leading dimension ldx)
+  long long* acc;
+  int ldacc;
+  const __half* xc;
+  int ldx;
 };
 
 // K-blocks per TMEM partial so that every partial sum is an integer below
@@ -335,6 +344,35 @@ __global__ void __launch_bounds__(THREADS, 1) exact_product_kernel(const __grid_
         ++kb;
       }
       if (!ok) break;
+      if (b.acc != nullptr && 2 * un.u + 2 <= b.P) {
+        // x'^T (T_k x') over this warp's 32 rows, column by column: the int64
+        // product of each lane split at bit 20 (|x' C| < 2^39, so both parts sum
+        // over 32 lanes inside an int32), one warp reduction each, one atomic
+        // Columns past the block's ncols (a partial last strip) are neither read
+        // nor added: x' and acc hold the block's columns only.
+        const int rr = (2 * un.u + (int)rank) * TB + 32 * lq + lane;  // the row of T: x' row too
+        const int cb = un.c * TN + chalf * EPI_COLS;
+        const int nv = b.ncols - cb;  // valid columns of this warp's 128 (may be <= 0)
+        const __half* xr = b.xc + rr;
+        unsigned long long* ac = reinterpret_cast<unsigned long long*>(b.acc) + (size_t)un.slab * b.ldacc + cb;
+#pragma unroll
+        for (int q = 0; q < EPI_COLS / 8; ++q) {
+          if (q * 8 >= nv) break;  // uniform over the warp
+          int xv[8];
+#pragma unroll
+          for (int i = 0; i < 8; ++i)
+            xv[i] = q * 8 + i < nv ? __half2int_rn(xr[(size_t)(cb + q * 8 + i) * b.ldx]) : 0;
+#pragma unroll
+          for (int i = 0; i < 8; ++i) {
+            const long long pr = (long long)xv[i] * master[q * 8 + i];
+            const unsigned lo = __reduce_add_sync(0xffffffffu, (unsigned)(pr & 0xFFFFF));
+            const int hi = __reduce_add_sync(0xffffffffu, (int)(pr >> 20));
+            if (lane == ((q * 8 + i) & 31) && q * 8 + i < nv)
+              atomicAdd(ac + q * 8 + i, (unsigned long long)(((long long)hi << 20) + (long long)lo));
+          }
+        }
+        continue;
+      }
       // the tile's int32 products to HBM through TMA stores of 2 KB chunks
       const int r0 = un.slab * b.RS + (2 * un.u + (int)rank) * TB + 32 * lq;
       const int c0 = un.c * TN + chalf * EPI_COLS;
@@ -441,14 +479,17 @@ __global__ void slice_rows_kernel(const double* __restrict__ W, const double* __
 // x' = x - c (c the SNP's integer shift, 0 without intercept) as FP16 on rows
 // < n, 0 on rows n .. n_pad - 1; c stored in shift[col]; the largest |x'| of
 // the block into *xmax.  One warp per SNP column; the block's first thread
-// also zeroes the product's unit counter.
+// also zeroes the product's unit counter; acc (if not null): the fused sums
+// of the sliced solve, slabs x ldacc, zeroed for the block's columns.
 __global__ void cast_exact_kernel(const int8_t* __restrict__ X, int64_t ldx, int n, int n_pad, int ncols, int center,
                                   int8_t* __restrict__ shift, __half* __restrict__ xc, int* __restrict__ xmax,
-                                  unsigned int* __restrict__ counter) {
+                                  unsigned int* __restrict__ counter, long long* __restrict__ acc, int ldacc,
+                                  int slabs) {
   if (blockIdx.x == 0 && threadIdx.x == 0) *counter = 0;
   const int lane = threadIdx.x & 31;
   const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
   if (col >= ncols) return;
+  if (acc && lane < slabs) acc[(int64_t)lane * ldacc + col] = 0;
   const int8_t* x = X + (int64_t)col * ldx;
   int c = 0;
   if (center) {
@@ -599,6 +640,7 @@ struct ExactProducts {
   double* inv_scale = nullptr;  // [0] 1 / s_W, [1 + e] 1 / s_e
   double* part = nullptr;       // the adjoint's y-gradient chunk partials
   double* z = nullptr;          // n_pad (adjoint)
+  long long* acc = nullptr;     // the sliced solve's fused sums: slabs x bs int64
   ex3::Params prm;
 };
 
@@ -613,6 +655,7 @@ void exact_destroy(ExactProducts* E) {
   cudaFree(E->inv_scale);
   cudaFree(E->part);
   cudaFree(E->z);
+  cudaFree(E->acc);
   delete E;
 }
 
@@ -658,6 +701,7 @@ static cudaError_t exact_create(ExactProducts** out, double* W, const double* Ex
   TRY(cudaMalloc(&E->shift, (size_t)bs));
   TRY(cudaMalloc(&E->xmax, 64));
   TRY(cudaMalloc(&E->inv_scale, sizeof(double) * (1 + ne)));
+  if (tri) TRY(cudaMalloc(&E->acc, sizeof(long long) * (size_t)slabs * bs));
   if (keep_w) {
     const int nchunks = (bs + EX_DY_CHUNK - 1) / EX_DY_CHUNK;
     TRY(cudaMalloc(&E->part, sizeof(double) * (size_t)nchunks * n));
@@ -722,6 +766,10 @@ static cudaError_t exact_create(ExactProducts** out, double* W, const double* Ex
   p.tri = tri ? 1 : 0;
   p.xmax = E->xmax;
   p.counter = reinterpret_cast<unsigned int*>(E->xmax + 1);
+  p.acc = E->acc;
+  p.ldacc = bs;
+  p.xc = E->xc;
+  p.ldx = n_pad;
   TRY(cudaFuncSetAttribute(ex3::exact_product_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, ex3::SMEM));
   {
     cudaLaunchConfig_t cfg;
@@ -784,10 +832,12 @@ static cudaError_t exact_cast_product(ExactProducts* E, const int8_t* X, int64_t
                            s)) != cudaSuccess)
     return e;
   cast_exact_kernel<<<(ncols + 7) / 8, 256, 0, s>>>(X, ldx, E->n, E->n_pad, ncols, E->center ? 1 : 0, E->shift,
-                                                    E->xc, E->xmax, reinterpret_cast<unsigned int*>(E->xmax + 1));
+                                                    E->xc, E->xmax, reinterpret_cast<unsigned int*>(E->xmax + 1),
+                                                    E->acc, E->bs, E->slabs);
   if ((e = cudaGetLastError()) != cudaSuccess) return e;
   ex3::Params p = E->prm;
   p.Cs = (ncols + TN - 1) / TN;
+  p.ncols = ncols;
   p.ntiles = E->slabs * p.U * p.Cs;
   p.st = st;
   const int ncl = std::min(p.ntiles, E->max_clusters);
@@ -844,8 +894,10 @@ cudaError_t exact_solve_sums(ExactProducts* E, int ncols, const SolveConsts* sc,
                              int* status, cudaStream_t s) {
   if (ncols <= 0) return cudaSuccess;
   if (ncols > E->bs || !E->tri) return cudaErrorInvalidValue;
-  return launch_sliced_solve(E->C, (int64_t)E->slabs * E->RS, E->RS, E->xc, E->n_pad, E->n, E->ne, E->inv_scale, sc,
-                             E->q, t, ncols, b, se, status, E->center ? E->shift : nullptr, s);
+  // rows of T stored as products: those of the last row-panel pair (it also holds the appended rows)
+  const int r_lo = 2 * (E->U - 1) * TB;
+  return launch_sliced_solve(E->C, (int64_t)E->slabs * E->RS, E->RS, E->acc, E->bs, r_lo, E->xc, E->n_pad, E->n,
+                             E->ne, E->inv_scale, sc, E->q, t, ncols, b, se, status, E->center ? E->shift : nullptr, s);
 }
 
 }  // namespace gwas

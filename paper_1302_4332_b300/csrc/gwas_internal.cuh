@@ -191,9 +191,11 @@ void exact_destroy(ExactProducts* E);
 int exact_max_ctas(const ExactProducts* E);
 // The sliced solve's per-SNP sums from the exact products and the FP64 p x p
 // solve (reduce_solve.cu).  C: slabs x RS rows per SNP (leading dimension
-// ldc), xc: x' in FP16 (leading dimension ldx = n_pad), ne = q + t appended rows.
-cudaError_t launch_sliced_solve(const int32_t* C, int64_t ldc, int RS, const __half* xc, int64_t ldx, int n,
-                                int ne, const double* inv_scale, const SolveConsts* sc, int q, int t, int ncols,
+// ldc; only rows >= r_lo of the square part and the appended rows are read),
+// acc: the product kernel's sums over the rows below r_lo (slabs x ldacc
+// int64), xc: x' in FP16 (leading dimension ldx = n_pad), ne = q + t appended rows.
+cudaError_t launch_sliced_solve(const int32_t* C, int64_t ldc, int RS, const long long* acc, int ldacc, int r_lo,
+                                const __half* xc, int64_t ldx, int n, int ne, const double* inv_scale, const SolveConsts* sc, int q, int t, int ncols,
                                 double* b, double* se, int* status, const int8_t* shift, cudaStream_t s,
                                 int64_t bstride = 0);
 // The per-SNP sums and adjoint from the exact products (adjoint.cu), then the

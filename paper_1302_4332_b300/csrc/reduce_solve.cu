@@ -635,14 +635,16 @@ cudaError_t launch_partials_solve(const float* red, int ngroups, int64_t ldr, co
 // exact int32 products of x' with SOLVE_SL = 5 slabs of 10-bit slices: slab k row r
 // (r < n_pad) = slice k of (T x')_r in units of 2^-10k / s_T; rows n_pad + e
 // and n_pad + ne + e of slabs 0..2 = slices k and k + 3 of W^[:, e]^T x'.
-// Here: sum_r x'_r C_k[r] exactly in int64 (|x'_r C| < 2^39), the five slabs
-// and the six slices combined in FP64 (smallest first), then the FP64 solve.
+// sum_r x'_r C_k[r] is exact in int64 (|x'_r C| < 2^39): the product kernel
+// added it over the rows below r_lo into acc[k][col]; the rows r_lo .. n - 1
+// (stored in C) are added here.  The five slabs and the six slices are then
+// combined in FP64 (smallest first), then the FP64 solve.
 constexpr int SOLVE_SL = 5;
 
 template <int QM>
 __global__ void __launch_bounds__(256) sliced_solve_kernel(
-    const int32_t* __restrict__ C, int64_t ldc, int RS, const __half* __restrict__ xc, int64_t ldx, int n, int n_pad,
-    int ne, const double* __restrict__ inv_scale, const SolveConsts* __restrict__ sc, int q, int t, int ncols,
+    const int32_t* __restrict__ C, int64_t ldc, int RS, const long long* __restrict__ fused, int ldacc, int r_lo,
+    const __half* __restrict__ xc, int64_t ldx, int n, int n_pad, int ne, const double* __restrict__ inv_scale, const SolveConsts* __restrict__ sc, int q, int t, int ncols,
     double* __restrict__ b, double* __restrict__ se, int* __restrict__ status, const int8_t* __restrict__ shift,
     int64_t bstride) {
   const int lane = threadIdx.x & 31;
@@ -650,9 +652,11 @@ __global__ void __launch_bounds__(256) sliced_solve_kernel(
   if (col >= ncols) return;
   const int32_t* cc = C + (int64_t)col * ldc;
   const __half* x = xc + (int64_t)col * ldx;
-  long long pk[SOLVE_SL] = {0, 0, 0, 0, 0};
+  long long pk[SOLVE_SL];
+#pragma unroll
+  for (int k = 0; k < SOLVE_SL; ++k) pk[k] = lane == 0 ? fused[(int64_t)k * ldacc + col] : 0;
 #pragma unroll 4
-  for (int r = lane; r < n; r += 32) {
+  for (int r = r_lo + lane; r < n; r += 32) {
     const int xi = __half2int_rn(x[r]);
 #pragma unroll
     for (int k = 0; k < SOLVE_SL; ++k) pk[k] += (long long)xi * __ldcs(cc + k * RS + r);
@@ -685,8 +689,8 @@ __global__ void __launch_bounds__(256) sliced_solve_kernel(
   solve_store<QM>(acc, sc, q, col, b, se, status, shift ? (double)shift[col] : 0.0, t, bstride);
 }
 
-cudaError_t launch_sliced_solve(const int32_t* C, int64_t ldc, int RS, const __half* xc, int64_t ldx, int n,
-                                int ne, const double* inv_scale, const SolveConsts* sc, int q, int t, int ncols,
+cudaError_t launch_sliced_solve(const int32_t* C, int64_t ldc, int RS, const long long* acc, int ldacc, int r_lo,
+                                const __half* xc, int64_t ldx, int n, int ne, const double* inv_scale, const SolveConsts* sc, int q, int t, int ncols,
                                 double* b, double* se, int* status, const int8_t* shift, cudaStream_t s,
                                 int64_t bstride) {
   if (ncols <= 0) return cudaSuccess;
@@ -695,13 +699,13 @@ cudaError_t launch_sliced_solve(const int32_t* C, int64_t ldc, int RS, const __h
   const int n_pad = (int)ldx;
   const int grid = (ncols + 7) / 8;
   if (ne <= 4)
-    sliced_solve_kernel<3><<<grid, 256, 0, s>>>(C, ldc, RS, xc, ldx, n, n_pad, ne, inv_scale, sc, q, t, ncols, b, se,
+    sliced_solve_kernel<3><<<grid, 256, 0, s>>>(C, ldc, RS, acc, ldacc, r_lo, xc, ldx, n, n_pad, ne, inv_scale, sc, q, t, ncols, b, se,
                                                 status, shift, bstride);
   else if (ne <= 8)
-    sliced_solve_kernel<7><<<grid, 256, 0, s>>>(C, ldc, RS, xc, ldx, n, n_pad, ne, inv_scale, sc, q, t, ncols, b, se,
+    sliced_solve_kernel<7><<<grid, 256, 0, s>>>(C, ldc, RS, acc, ldacc, r_lo, xc, ldx, n, n_pad, ne, inv_scale, sc, q, t, ncols, b, se,
                                                 status, shift, bstride);
   else
-    sliced_solve_kernel<QMAX><<<grid, 256, 0, s>>>(C, ldc, RS, xc, ldx, n, n_pad, ne, inv_scale, sc, q, t, ncols, b,
+    sliced_solve_kernel<QMAX><<<grid, 256, 0, s>>>(C, ldc, RS, acc, ldacc, r_lo, xc, ldx, n, n_pad, ne, inv_scale, sc, q, t, ncols, b,
                                                    se, status, shift, bstride);
   return cudaGetLastError();
 }

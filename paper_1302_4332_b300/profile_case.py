@@ -23,7 +23,7 @@ if ROOT not in sys.path:
 
 def main(argv=None):
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
-    ap.add_argument("--path", default="f16x2", choices=("fp64", "bf16x3", "tf32x3", "f16x2"))
+    ap.add_argument("--path", default="f16x2", choices=("fp64", "bf16x3", "tf32x3", "f16x2", "sliced64"))
     ap.add_argument("--tiles", default="auto", choices=("auto", "single", "pair_mma", "inverse"))
     ap.add_argument("--n", type=int, default=10000)
     ap.add_argument("--bs", type=int, default=4096)
