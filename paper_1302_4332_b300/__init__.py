@@ -47,6 +47,7 @@ EXPORTS = (
     "gwas_batch_last_error_detail",
     "gwas_batch_destroy", "gwas_solve_file", "gwas_solve_file_out", "gwas_reader_open", "gwas_reader_next",
     "gwas_reader_release", "gwas_reader_error_detail", "gwas_reader_close", "gwas_check_timeout",
+    "gwas_pack_dosages2", "gwas_h2d_bytes",
 )
 GWAS_RESUME = 1
 STAGES = ("h2d", "trsm", "reduce", "d2h", "solve")
@@ -69,7 +70,7 @@ class _Config(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("bs", ctypes.c_int), ("ring_depth", ctypes.c_int),
                 ("device", ctypes.c_int), ("strip_group", ctypes.c_int), ("tile_mode", ctypes.c_int),
                 ("traits", ctypes.c_int), ("separate_sums", ctypes.c_int),
-                ("single_piece", ctypes.c_int)]
+                ("single_piece", ctypes.c_int), ("stream_pack", ctypes.c_int)]
 
 
 _lib = None
@@ -117,6 +118,10 @@ def load(path: str | None = None):
     lib.gwas_copy_factor.restype = c_int
     lib.gwas_kernel_launches.argtypes = [vp]
     lib.gwas_kernel_launches.restype = i64
+    lib.gwas_h2d_bytes.argtypes = [vp]
+    lib.gwas_h2d_bytes.restype = i64
+    lib.gwas_pack_dosages2.argtypes = [vp, i64, c_int, c_int, vp, i64]
+    lib.gwas_pack_dosages2.restype = c_int
     lib.gwas_strerror.argtypes = [c_int]
     lib.gwas_strerror.restype = ctypes.c_char_p
     lib.gwas_last_error_detail.argtypes = [vp]
@@ -260,6 +265,23 @@ def _colmajor(a, dtype, rows: int, name: str, allow_none=False):
     return arr.ctypes.data, rows, arr
 
 
+def pack_dosages2(X) -> np.ndarray:
+    """The 2-bit encoding of gwas_solve_stream's transport (gwas_pack_dosages2):
+    X n x m int8 with values 0..3 -> ceil(n/4) x m uint8 (column-major), row
+    4k + i of a column in bits 2i .. 2i+1 of its byte k.  Raises GwasError
+    (GWAS_ERR_ARG) for any other value."""
+    x = np.asfortranarray(X, dtype=np.int8)
+    if x.ndim == 1:
+        x = x.reshape(-1, 1, order="F")
+    n, m = x.shape
+    ldp = (n + 3) // 4
+    out = np.zeros((ldp, m), dtype=np.uint8, order="F")
+    rc = load().gwas_pack_dosages2(x.ctypes.data, n, n, m, out.ctypes.data, ldp)
+    if rc != GWAS_OK:
+        raise GwasError(rc, "values outside 0..3")
+    return out
+
+
 def read_results(path: str):
     """A result file of GLS.solve_file_out: (header dict, b, se p x m, status m);
     b is p x m, or p x m x t for t phenotypes."""
@@ -296,7 +318,7 @@ class GLS:
     def __init__(self, phi_or_L, XL, y, h: float, sigma2: float = 1.0, *, precision: str = "fp64",
                  bs: int = 4096, ring_depth: int = 3, is_L: bool = False, device: int = -1, stream=None,
                  strip_group: int = 0, tiles: str = "auto", separate_sums: bool = False,
-                 single_piece: bool = False):
+                 single_piece: bool = False, stream_pack: bool = True):
         lib = load()
         n = int(np.shape(y)[0]) if not _is_torch(y) else int(y.shape[0])
         q = 0 if XL is None else (int(XL.shape[1]) if np.ndim(XL) == 2 or _is_torch(XL) else 1)
@@ -322,6 +344,7 @@ class GLS:
         cfg.traits = self.t
         cfg.separate_sums = int(bool(separate_sums))
         cfg.single_piece = int(bool(single_piece))
+        cfg.stream_pack = int(bool(stream_pack))
         self.precision, self.bs = precision, int(bs)
         stream_p = None
         if stream is not None:
@@ -500,6 +523,11 @@ class GLS:
     @property
     def kernel_launches(self) -> int:
         return int(load().gwas_kernel_launches(self._ctx))
+
+    @property
+    def h2d_bytes(self) -> int:
+        """SNP-block bytes this context has copied host -> device (packed blocks count packed bytes)."""
+        return int(load().gwas_h2d_bytes(self._ctx))
 
     def close(self):
         if getattr(self, "_ctx", None):

@@ -69,6 +69,14 @@ struct gwas_ctx {
   double* h_se = nullptr;
   int* h_status = nullptr;
   double* f64_in = nullptr;  // n x bs FP64 staging for gwas_solve_block_f64 with host input
+  // the 2-bit transport of gwas_solve_stream (set up on its first packed call)
+  bool stream_pack = false;
+  PackPool* pack_pool = nullptr;
+  int64_t ldp = 0;                   // packed bytes per column (ceil(n/4) rounded up to 16)
+  std::vector<uint8_t*> hpack;       // ring_depth pinned host slots of ldp x bs bytes
+  std::vector<uint8_t*> dpack;       // ring_depth device slots of ldp x bs bytes
+  std::vector<cudaEvent_t> ev_staged;  // the H2D copy out of hpack[slot] is done
+  int64_t h2d_bytes = 0;             // SNP-block bytes copied host -> device
   void* static_scratch = nullptr;  // device address of the fixed scratch array (gwas_solve_block_static)
   int64_t launches = 0;
   int64_t not_spd_index = -1;
@@ -386,12 +394,14 @@ int solve_common(gwas_ctx* ctx, const void* XR, bool int8_input, int64_t ldx, in
     if (int8_input) {
       CK(cudaMemcpy2DAsync(ctx->ring[0], (size_t)ctx->n_pad, XR, (size_t)ldx, (size_t)ctx->n, (size_t)ncols,
                            cudaMemcpyHostToDevice, ctx->stream));
+      ctx->h2d_bytes += (int64_t)ctx->n * ncols;
       xin = ctx->ring[0];
       ld_in = ctx->n_pad;
     } else {
       if (!ctx->f64_in) CK(dmalloc(&ctx->f64_in, sizeof(double) * (size_t)ctx->n * ctx->bs));
       CK(cudaMemcpy2DAsync(ctx->f64_in, sizeof(double) * (size_t)ctx->n, XR, sizeof(double) * (size_t)ldx,
                            sizeof(double) * (size_t)ctx->n, (size_t)ncols, cudaMemcpyHostToDevice, ctx->stream));
+      ctx->h2d_bytes += (int64_t)sizeof(double) * ctx->n * ncols;
       xin = ctx->f64_in;
       ld_in = ctx->n;
     }
@@ -430,6 +440,10 @@ void free_all(gwas_ctx* c) {
   cudaFree(c->d_b); cudaFree(c->d_se); cudaFree(c->d_status); cudaFree(c->f64_in); cudaFree(c->W32);
   cudaFree(c->AopT); cudaFree(c->Xhat); cudaFree(c->What); cudaFree(c->GH); cudaFree(c->adj);
   cudaFreeHost(c->h_b); cudaFreeHost(c->h_se); cudaFreeHost(c->h_status);
+  for (auto* p : c->hpack) cudaFreeHost(p);
+  for (auto* p : c->dpack) cudaFree(p);
+  for (auto ev : c->ev_staged) cudaEventDestroy(ev);
+  pack_pool_destroy(c->pack_pool);
   if (c->tcs) tc::destroy(c->tcs);
   exact_destroy(c->exact);
   exact_destroy(c->sliced);
@@ -449,6 +463,7 @@ void gwas_config_default(gwas_config* cfg) {
   cfg->bs = 4096;
   cfg->ring_depth = 3;
   cfg->device = -1;
+  cfg->stream_pack = 1;
 }
 
 const char* gwas_strerror(int code) {
@@ -481,6 +496,7 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
       (cfg.precision == GWAS_F16X2 && cfg.tile_mode != GWAS_TILES_AUTO && cfg.tile_mode != GWAS_TILES_INVERSE))
     return GWAS_ERR_ARG;
   if (cfg.separate_sums != 0 && cfg.separate_sums != 1) return GWAS_ERR_ARG;
+  if (cfg.stream_pack != 0 && cfg.stream_pack != 1) return GWAS_ERR_ARG;
   if (cfg.precision == GWAS_SLICED64 &&
       (cfg.tile_mode != GWAS_TILES_AUTO || cfg.strip_group != 0 || cfg.separate_sums != 0 || cfg.single_piece != 0))
     return GWAS_ERR_ARG;
@@ -521,6 +537,7 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
     ctx->prec = cfg.precision; ctx->bs = cfg.bs; ctx->ring_depth = cfg.ring_depth;
     ctx->separate_sums = cfg.separate_sums != 0;
     ctx->single_piece = cfg.single_piece != 0;
+    ctx->stream_pack = cfg.stream_pack != 0;
     ctx->h = h; ctx->sigma2 = sigma2;
     const size_t np = (size_t)ctx->n_pad, n2 = np * np;
     CK(dmalloc(&ctx->L, sizeof(double) * n2));
@@ -736,16 +753,51 @@ int gwas_solve_stream(gwas_ctx* ctx, const int8_t* XR_host, int64_t ldx, int64_t
   // columns are repacked to the slot's stride n_pad by a pitched copy.
   const bool flat = (ldx % 16) == 0 && ldx <= ctx->n_pad;
   const int64_t ld_dev = flat ? ldx : ctx->n_pad;
+  // The 2-bit transport: pinned host and device slots of ldp x bs bytes and the
+  // packing threads, set up on the first packed call.
+  if (ctx->stream_pack && ctx->hpack.empty()) {
+    ctx->ldp = ((ctx->n + 3) / 4 + 15) / 16 * 16;
+    ctx->hpack.assign(R, nullptr);
+    ctx->dpack.assign(R, nullptr);
+    ctx->ev_staged.assign(R, nullptr);
+    for (int s2 = 0; s2 < R; ++s2) {
+      CK(cudaMallocHost(&ctx->hpack[s2], (size_t)ctx->ldp * bs));
+      CK(dmalloc(&ctx->dpack[s2], (size_t)ctx->ldp * bs));
+      CK(cudaEventCreateWithFlags(&ctx->ev_staged[s2], cudaEventDisableTiming));
+    }
+    ctx->pack_pool = pack_pool_create();
+  }
+  std::vector<char> packed(R, 0);        // block in slot s crossed the link packed
+  std::vector<int64_t> sld(R, ld_dev);   // leading dimension of the block in ring slot s
   auto enqueue_copy = [&](int64_t blk) -> int {
     const int slot = (int)(blk % R), nc = cols_of(blk);
+    const int8_t* src = XR_host + blk * bs * ldx;
+    bool pk = false;
+    if (ctx->stream_pack) {
+      // hpack[slot] last left for the device R blocks ago; packed while earlier blocks solve
+      CK(cudaEventSynchronize(ctx->ev_staged[slot]));
+      pk = pack_pool_run(ctx->pack_pool, src, ldx, ctx->n, nc, ctx->hpack[slot], ctx->ldp);
+    }
     CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_free[slot], 0));
     StageMark mk(ctx, GWAS_STAGE_H2D, ctx->copy_stream);
-    if (flat)  // the last column ends after its n-th byte
-      CK(cudaMemcpyAsync(ctx->ring[slot], XR_host + blk * bs * ldx, (size_t)((nc - 1) * ldx + ctx->n),
-                         cudaMemcpyHostToDevice, ctx->copy_stream));
-    else
-      CK(cudaMemcpy2DAsync(ctx->ring[slot], (size_t)ctx->n_pad, XR_host + blk * bs * ldx, (size_t)ldx,
-                           (size_t)ctx->n, (size_t)nc, cudaMemcpyHostToDevice, ctx->copy_stream));
+    if (pk) {
+      CK(cudaMemcpyAsync(ctx->dpack[slot], ctx->hpack[slot], (size_t)ctx->ldp * nc, cudaMemcpyHostToDevice,
+                         ctx->copy_stream));
+      CK(cudaEventRecord(ctx->ev_staged[slot], ctx->copy_stream));
+      ctx->h2d_bytes += ctx->ldp * nc;
+      sld[slot] = ctx->n_pad;
+    } else if (flat) {  // the last column ends after its n-th byte
+      CK(cudaMemcpyAsync(ctx->ring[slot], src, (size_t)((nc - 1) * ldx + ctx->n), cudaMemcpyHostToDevice,
+                         ctx->copy_stream));
+      ctx->h2d_bytes += (nc - 1) * ldx + ctx->n;
+      sld[slot] = ld_dev;
+    } else {
+      CK(cudaMemcpy2DAsync(ctx->ring[slot], (size_t)ctx->n_pad, src, (size_t)ldx, (size_t)ctx->n, (size_t)nc,
+                           cudaMemcpyHostToDevice, ctx->copy_stream));
+      ctx->h2d_bytes += (int64_t)ctx->n * nc;
+      sld[slot] = ld_dev;
+    }
+    packed[slot] = pk;
     CK(cudaEventRecord(ctx->ev_copied[slot], ctx->copy_stream));
     return GWAS_OK;
   };
@@ -758,10 +810,15 @@ int gwas_solve_stream(gwas_ctx* ctx, const int8_t* XR_host, int64_t ldx, int64_t
   for (int64_t blk = 0; blk < nblk; ++blk) {
     const int slot = (int)(blk % R), nc = cols_of(blk);
     CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_copied[slot], 0));
+    if (packed[slot]) {  // the 2-bit codes into the ring slot, int8 as the copy would have left them
+      StageMark mk(ctx, GWAS_STAGE_H2D, ctx->stream);
+      CK(launch_unpack2(ctx->dpack[slot], ctx->ldp, ctx->n, nc, ctx->ring[slot], ctx->n_pad, ctx->stream));
+      ctx->launches += 1;
+    }
     double* ob = ctx->d_b + (size_t)slot * T * p * bs;
     double* ose = ctx->d_se + (size_t)slot * p * bs;
     int* ost = ctx->d_status + (size_t)slot * bs;
-    if ((rc = run_block(ctx, ctx->ring[slot], true, ld_dev, nc, ob, ose, ost)) != GWAS_OK) return rc;
+    if ((rc = run_block(ctx, ctx->ring[slot], true, sld[slot], nc, ob, ose, ost)) != GWAS_OK) return rc;
     CK(cudaEventRecord(ctx->ev_free[slot], ctx->stream));
     {
     StageMark mk(ctx, GWAS_STAGE_D2H, ctx->stream);
@@ -1912,6 +1969,8 @@ int gwas_timing_read(gwas_ctx* ctx, double* ms, int64_t* count) {
 }
 
 int64_t gwas_kernel_launches(const gwas_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+int64_t gwas_h2d_bytes(const gwas_ctx* ctx) { return ctx ? ctx->h2d_bytes : 0; }
 
 void gwas_destroy(gwas_ctx* ctx) { free_all(ctx); }
 

@@ -1,0 +1,183 @@
+// The 2-bit transport of gwas_solve_stream: hard-called genotypes (values
+// 0..3) cross the host link four to a byte.  The link, not the solve, bounds
+// the whole-study stream from host memory (n int8 bytes per SNP at ~56 GB/s
+// against ~7.6 M SNPs/s of solves at n = 10^4); packing on the host cores and
+// unpacking in HBM moves a quarter of the bytes.
+//
+// Encoding (gwas_pack_dosages2): column c occupies ceil(n/4) bytes at P + c ldp;
+// byte k holds rows 4k .. 4k+3, row 4k + i in bits 2i .. 2i+1; rows past n are 0.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <atomic>
+#include <condition_variable>
+#include <cstdint>
+#include <cstring>
+#include <functional>
+#include <mutex>
+#include <thread>
+#include <vector>
+
+#include "gwas_internal.cuh"
+
+namespace gwas {
+
+// ---------------------------------------------------------------- packing
+// Eight rows a step: bytes b0..b7 of a little-endian word (each 0..3) fold to
+// the two packed bytes (b0 | b1 << 2 | b2 << 4 | b3 << 6) and the same of b4..b7.
+static inline uint16_t pack8(uint64_t w) {
+  uint64_t v = (w | (w >> 6)) & 0x000F000F000F000Full;  // nibbles b0|b1<<2 at bits 0, 16, 32, 48
+  v = (v | (v >> 12)) & 0x000000FF000000FFull;          // bytes at bits 0 and 32
+  return (uint16_t)(v | (v >> 24));
+}
+
+bool pack2_columns(const int8_t* X, int64_t ldx, int n, int c0, int c1, uint8_t* P, int64_t ldp) {
+  const int nb = (n + 3) / 4;
+  for (int c = c0; c < c1; ++c) {
+    const uint8_t* x = reinterpret_cast<const uint8_t*>(X + (int64_t)c * ldx);
+    uint8_t* o = P + (int64_t)c * ldp;
+    uint64_t bad = 0;
+    int r = 0;
+    for (; r + 8 <= n; r += 8) {
+      uint64_t w;
+      std::memcpy(&w, x + r, 8);
+      bad |= w;
+      const uint16_t h = pack8(w);
+      std::memcpy(o + r / 4, &h, 2);
+    }
+    if (r < n) {  // the ragged end: rows past n count as 0
+      uint8_t t[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      std::memcpy(t, x + r, (size_t)(n - r));
+      uint64_t w;
+      std::memcpy(&w, t, 8);
+      bad |= w;
+      const uint16_t h = pack8(w);
+      const int left = nb - r / 4;  // 1 or 2 bytes of this column remain
+      std::memcpy(o + r / 4, &h, (size_t)left);
+    }
+    if (bad & 0xFCFCFCFCFCFCFCFCull) return false;  // a value outside 0..3
+  }
+  return true;
+}
+
+// ---------------------------------------------------------- thread pool
+// Persistent workers for pack2 over column ranges: run() hands out chunks of
+// columns through an atomic cursor; the calling thread works too and returns
+// when every chunk is done.
+struct PackPool {
+  std::vector<std::thread> th;
+  std::mutex mu;
+  std::condition_variable cv_go, cv_done;
+  uint64_t gen = 0;
+  bool quit = false;
+  // the current job
+  const int8_t* X = nullptr;
+  int64_t ldx = 0, ldp = 0;
+  int n = 0, ncols = 0, chunk = 1;
+  uint8_t* P = nullptr;
+  std::atomic<int> cursor{0}, pending{0};
+  std::atomic<bool> ok{true};
+
+  void work() {
+    for (;;) {
+      const int c = cursor.fetch_add(chunk);
+      if (c >= ncols) break;
+      const int c1 = std::min(ncols, c + chunk);
+      if (!pack2_columns(X, ldx, n, c, c1, P, ldp)) ok.store(false);
+    }
+  }
+  void loop() {
+    uint64_t seen = 0;
+    for (;;) {
+      {
+        std::unique_lock<std::mutex> lk(mu);
+        cv_go.wait(lk, [&] { return quit || gen != seen; });
+        if (quit) return;
+        seen = gen;
+      }
+      work();
+      if (pending.fetch_sub(1) == 1) {
+        std::lock_guard<std::mutex> lk(mu);
+        cv_done.notify_all();
+      }
+    }
+  }
+  bool run(const int8_t* X_, int64_t ldx_, int n_, int ncols_, uint8_t* P_, int64_t ldp_) {
+    {
+      std::lock_guard<std::mutex> lk(mu);
+      X = X_, ldx = ldx_, n = n_, ncols = ncols_, P = P_, ldp = ldp_;
+      chunk = std::max(1, ncols_ / (8 * ((int)th.size() + 1)));
+      cursor.store(0);
+      ok.store(true);
+      pending.store((int)th.size());
+      ++gen;
+    }
+    cv_go.notify_all();
+    work();
+    std::unique_lock<std::mutex> lk(mu);
+    cv_done.wait(lk, [&] { return pending.load() == 0; });
+    return ok.load();
+  }
+};
+
+PackPool* pack_pool_create() {
+  PackPool* p = new PackPool;
+  const unsigned hc = std::thread::hardware_concurrency();
+  const int nw = std::max(0, std::min(15, (int)(hc ? hc : 2) - 1));
+  for (int k = 0; k < nw; ++k) p->th.emplace_back([p] { p->loop(); });
+  return p;
+}
+
+bool pack_pool_run(PackPool* p, const int8_t* X, int64_t ldx, int n, int ncols, uint8_t* P, int64_t ldp) {
+  return p->run(X, ldx, n, ncols, P, ldp);
+}
+
+void pack_pool_destroy(PackPool* p) {
+  if (!p) return;
+  {
+    std::lock_guard<std::mutex> lk(p->mu);
+    p->quit = true;
+  }
+  p->cv_go.notify_all();
+  for (auto& t : p->th) t.join();
+  delete p;
+}
+
+// --------------------------------------------------------------- unpacking
+// One thread per 4 packed bytes (16 rows of a column): a 16-byte store of
+// the int8 values.  X rows 16 t .. 16 t + 15 < ceil(n / 16) 16 <= n_pad; rows
+// past n come out 0 (the packed padding), as the slot holds them.
+__global__ void unpack2_kernel(const uint8_t* __restrict__ P, int64_t ldp, int n, int ncols, int8_t* __restrict__ X,
+                               int64_t ldx) {
+  const int col = blockIdx.y;
+  const int g = blockIdx.x * blockDim.x + threadIdx.x;  // group of 16 rows
+  if (col >= ncols || 16 * g >= n) return;
+  const uint8_t* p = P + (int64_t)col * ldp + 4 * g;
+  const int nb = (n + 3) / 4;  // packed bytes of the column
+  uint32_t v = 0;
+#pragma unroll
+  for (int k = 0; k < 4; ++k)
+    if (4 * g + k < nb) v |= (uint32_t)p[k] << (8 * k);
+  uint32_t w[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t b = (v >> (8 * k)) & 0xFFu;  // rows 16g + 4k .. +3
+    w[k] = (b & 3u) | ((b & 0xCu) << 6) | ((b & 0x30u) << 12) | ((b & 0xC0u) << 18);
+  }
+  *reinterpret_cast<uint4*>(X + (int64_t)col * ldx + 16 * g) = make_uint4(w[0], w[1], w[2], w[3]);
+}
+
+cudaError_t launch_unpack2(const uint8_t* P, int64_t ldp, int n, int ncols, int8_t* X, int64_t ldx, cudaStream_t s) {
+  if (ncols <= 0) return cudaSuccess;
+  if ((ldx & 15) || (reinterpret_cast<uintptr_t>(X) & 15) || ldx < (n + 15) / 16 * 16) return cudaErrorInvalidValue;
+  const int groups = (n + 15) / 16;
+  unpack2_kernel<<<dim3((groups + 127) / 128, ncols), 128, 0, s>>>(P, ldp, n, ncols, X, ldx);
+  return cudaGetLastError();
+}
+
+}  // namespace gwas
+
+extern "C" int gwas_pack_dosages2(const int8_t* X, int64_t ldx, int n, int ncols, uint8_t* P, int64_t ldp) {
+  if (!X || !P || n < 1 || ncols < 0 || ldx < n || ldp < (n + 3) / 4) return GWAS_ERR_ARG;
+  return gwas::pack2_columns(X, ldx, n, 0, ncols, P, ldp) ? GWAS_OK : GWAS_ERR_ARG;
+}

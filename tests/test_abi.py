@@ -88,3 +88,42 @@ def test_tuning_struct_matches_the_header():
     body = re.search(r"typedef struct \{([^{}]*)\} gwas_batch_tuning;", text).group(1)
     fields = re.findall(r"\b(?:int|double)\s+([a-z_0-9]+)\s*;", body)
     assert fields == [name for name, _ in gw._Tuning._fields_]
+
+
+def _pack_reference(X):
+    """The 2-bit encoding written out: byte k of a column = sum_i X[4k + i] 4^i."""
+    n, m = X.shape
+    nb = (n + 3) // 4
+    Xp = np.zeros((4 * nb, m), dtype=np.int64)
+    Xp[:n] = X
+    return (Xp[0::4] + 4 * Xp[1::4] + 16 * Xp[2::4] + 64 * Xp[3::4]).astype(np.uint8)
+
+
+@pytest.mark.parametrize("n", [1, 3, 4, 5, 7, 8, 9, 15, 16, 17, 129, 1000, 10001])
+def test_pack_dosages2_encoding(lib, n):
+    """The stream transport's host packing (host code, no device needed) against
+    the encoding written out, on ragged n, values 0..3 (3 included)."""
+    rng = np.random.default_rng(n)
+    X = np.asfortranarray(rng.integers(0, 4, size=(n, 37)).astype(np.int8))
+    P = gw.pack_dosages2(X)
+    assert P.shape == ((n + 3) // 4, 37)
+    np.testing.assert_array_equal(P, _pack_reference(X))
+
+
+@pytest.mark.parametrize("bad", [4, -1, 127, -128])
+def test_pack_dosages2_refuses_other_values(lib, bad):
+    X = np.zeros((50, 5), dtype=np.int8, order="F")
+    X[49, 3] = bad  # the last row of one column: the ragged end is checked too
+    with pytest.raises(gw.GwasError) as e:
+        gw.pack_dosages2(X)
+    assert e.value.name == "GWAS_ERR_ARG"
+    X[49, 3] = 2
+    X[0, 4] = bad
+    with pytest.raises(gw.GwasError):
+        gw.pack_dosages2(X)
+
+
+def test_stream_pack_is_on_by_default(lib):
+    cfg = gw._Config()
+    lib.gwas_config_default(ctypes.byref(cfg))
+    assert cfg.stream_pack == 1

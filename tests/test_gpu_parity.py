@@ -141,6 +141,51 @@ def test_stream_matches_blocks(small_study):
     assert e["b_norm"] <= TOL64 and e["se_rel"] <= TOL64, e
 
 
+@pytest.mark.parametrize("prec", ("fp64", "f16x2", "sliced64"))
+def test_stream_2bit_transport(small_study, prec):
+    """gwas_solve_stream's 2-bit transport: blocks of values 0..3 cross the
+    link as 2-bit codes; results bit for bit those of the int8 transport, a
+    quarter of the bytes copied; a block holding another value (here a 5)
+    crosses as int8; an input leading dimension that is not the device slot's
+    (ldx = n + 3) goes through the same unpacking."""
+    s, X, L, (r, se, st) = small_study
+    n, m, bs = X.shape[0], 1100, 256
+    Xh = np.asfortranarray(X[:, :m])
+    Xw = np.zeros((n + 3, m), dtype=np.int8, order="F")  # ldx = n + 3 (neither 16-aligned nor n_pad)
+    Xw[:n] = Xh
+    out = {}
+    for pack in (False, True):
+        with gw.GLS(s["Phi"], s["XL"], s["y"], s["h"], s["sigma2"], precision=prec, bs=bs,
+                    stream_pack=pack) as g:
+            h0 = g.h2d_bytes
+            out[pack] = g.solve_stream(Xh)
+            moved = g.h2d_bytes - h0
+            out[(pack, "w")] = g.solve_stream(Xw[:n])
+        ldp = ((n + 3) // 4 + 15) // 16 * 16
+        assert moved == (ldp * m if pack else n * m), (pack, moved)
+    for a, b_ in zip(out[False], out[True]):
+        assert np.array_equal(a, b_, equal_nan=True)
+    for a, b_ in zip(out[False], out[(True, "w")]):
+        assert np.array_equal(a, b_, equal_nan=True)
+    tol = TOL64 if prec in ("fp64", "sliced64") else 1e-5
+    e = compare(*out[True], r[:, :m], se[:, :m], st[:m])
+    assert e["b_norm"] <= tol and e["se_rel"] <= tol, e
+    # a 5 in the third block: that block goes as int8, the others packed
+    Xm = Xh.copy()
+    Xm[17, 2 * bs + 9] = 5
+    rm, sem, _, stm = oracle.gls(L, s["XL"], s["y"], Xm)
+    with gw.GLS(s["Phi"], s["XL"], s["y"], s["h"], s["sigma2"], precision=prec, bs=bs) as g:
+        h0 = g.h2d_bytes
+        bm, sem_g, stm_g = g.solve_stream(Xm)
+        moved = g.h2d_bytes - h0
+    nblk = (m + bs - 1) // bs
+    cols3 = min(bs, m - 2 * bs)
+    assert moved == ldp * (m - cols3) + n * cols3, moved
+    e = compare(bm, sem_g, stm_g, rm, sem, stm)
+    assert e["b_norm"] <= tol and e["se_rel"] <= tol, e
+    assert nblk == 5
+
+
 # ---------------------------------------------------------------- split precision
 TOL_SPLIT = 1e-5
 SPLITS = ("bf16x3", "tf32x3", "f16x2")
