@@ -404,32 +404,39 @@ def run_ours(args, rank, world, local_rank, dist):
             bh = torch.empty((e2e_snps, p), dtype=torch.float64, pin_memory=True)
             seh = torch.empty((e2e_snps, p), dtype=torch.float64, pin_memory=True)
             sth = torch.empty(e2e_snps, dtype=torch.int32, pin_memory=True)
-            def e2e_run(gg):
-                gg.solve_stream(Xh_np[:bs].T, bh.numpy()[:bs].T, seh.numpy()[:bs].T, sth.numpy()[:bs])  # warm
-                if dist:
-                    dist.barrier()
+            g.solve_stream(Xh_np[:bs].T, bh.numpy()[:bs].T, seh.numpy()[:bs].T, sth.numpy()[:bs])  # warm
+            if dist:
+                dist.barrier()
+            torch.cuda.synchronize()
+            h0 = g.h2d_bytes
+            t1 = time.perf_counter()
+            for _ in range(steps):
+                g.solve_stream(Xh_np.T, bh.numpy().T, seh.numpy().T, sth.numpy())
+            e2e_s = max_over_ranks(time.perf_counter() - t1, dist, dev)
+            res["e2e"] = dict(value=job_rate(world, steps * e2e_snps, e2e_s), unit=UNIT,
+                              h2d_bytes_per_step=(g.h2d_bytes - h0) // steps,
+                              d2h_bytes_per_step=e2e_snps * (2 * p * 8 + 4), snps_per_step=e2e_snps,
+                              step=f"one gwas_solve_stream call over {reps} x the {NB} resident blocks "
+                                   "(pinned host memory, int8, one contiguous copy per block)")
+            if path in SPLIT_PATHS or path == "sliced64":
+                # the same SNPs held 2-bit packed in pinned host memory (hard calls
+                # 0..3, four to a byte): the link carries ceil(n/4) bytes per SNP
+                nbp = (n + 3) // 4
+                Ph = torch.zeros((e2e_snps, (nbp + 15) // 16 * 16), dtype=torch.uint8, pin_memory=True)
+                Ph.numpy()[:, :nbp] = gw.pack_dosages2(Xh_np.T).T  # columns 16-byte aligned: one copy a block
+                g.solve_stream_packed(Ph.T[:, :bs], bh.numpy()[:bs].T, seh.numpy()[:bs].T, sth.numpy()[:bs])
                 torch.cuda.synchronize()
-                h0 = gg.h2d_bytes
+                h0 = g.h2d_bytes
                 t1 = time.perf_counter()
                 for _ in range(steps):
-                    gg.solve_stream(Xh_np.T, bh.numpy().T, seh.numpy().T, sth.numpy())
-                dt = max_over_ranks(time.perf_counter() - t1, dist, dev)
-                return dt, (gg.h2d_bytes - h0) // steps
-            # the default transport: blocks of values 0..3 cross the link as 2-bit codes
-            e2e_s, moved = e2e_run(g)
-            res["e2e"] = dict(value=job_rate(world, steps * e2e_snps, e2e_s), unit=UNIT,
-                              h2d_bytes_per_step=moved, d2h_bytes_per_step=e2e_snps * (2 * p * 8 + 4),
-                              snps_per_step=e2e_snps, transport="2-bit codes (stream_pack, the default)",
-                              step=f"one gwas_solve_stream call over {reps} x the {NB} resident int8 blocks "
-                                   "(pinned host memory; packed by the library's host threads, unpacked on "
-                                   "the GPU)")
-            if path in SPLIT_PATHS or path == "sliced64":
-                # the same call with the int8 transport (one copy of n bytes per SNP)
-                with gw.GLS(s["Phi"], s["XL"], s["y"], w["h"], w["sigma2"], precision=path, bs=bs,
-                            stream_pack=False) as g8:
-                    e2e8_s, moved8 = e2e_run(g8)
-                res["e2e_int8_transport"] = dict(value=job_rate(world, steps * e2e_snps, e2e8_s), unit=UNIT,
-                                                 h2d_bytes_per_step=moved8)
+                    g.solve_stream_packed(Ph.T, bh.numpy().T, seh.numpy().T, sth.numpy())
+                ep_s = max_over_ranks(time.perf_counter() - t1, dist, dev)
+                res["e2e_packed_input"] = dict(
+                    value=job_rate(world, steps * e2e_snps, ep_s), unit=UNIT,
+                    h2d_bytes_per_step=(g.h2d_bytes - h0) // steps, snps_per_step=e2e_snps,
+                    step="one gwas_solve_stream_packed call over the same SNPs held 2-bit packed in pinned "
+                         "host memory (unpacked on the GPU)")
+                del Ph
             del Xh, bh, seh, sth
         # keep a few results for the error report against the oracle
         res["_sample"] = (b[:, :64].cpu().numpy().copy(), se[:, :64].cpu().numpy().copy(),
@@ -849,25 +856,26 @@ def main():
             r["error_vs_oracle"] = errors[path]
         paths_out[path] = r
     # the path's roofline: the slower of the solve's flops at the path's peak
-    # (n^2 algorithmic flop per SNP) and the SNP's bytes over the measured
-    # pinned host->device link -- as the e2e call moved them (2-bit codes by
-    # default), and for reference as n int8 bytes
+    # (n^2 algorithmic flop per SNP) and the SNP's n int8 bytes over the
+    # measured pinned host->device link (beside it: the link term of 2-bit
+    # packed input, ceil(n/4) bytes per SNP)
     n_ = float(w["n"])
     trsm_bound = hr["roofline"]["peak"] * 1e12 / (n_ * n_) if hr["roofline"].get("peak") else None
     h2d = out["extra"].get("h2d_gbs_pinned")
-    e2e_h = hr.get("e2e") or {}
-    bps = (e2e_h["h2d_bytes_per_step"] / e2e_h["snps_per_step"]) if e2e_h.get("h2d_bytes_per_step") else n_
-    h2d_bound = h2d * 1e9 / bps if h2d else None
-    h2d_int8_bound = h2d * 1e9 / n_ if h2d else None
+    h2d_bound = h2d * 1e9 / n_ if h2d else None
     terms = [t for t in (trsm_bound, h2d_bound) if t]
     slower = min(terms) if terms else None
-    path_roofline = {"trsm_snps_per_s": trsm_bound, "h2d_snps_per_s": h2d_bound, "h2d_bytes_per_snp": bps,
-                     "h2d_int8_snps_per_s": h2d_int8_bound,
+    path_roofline = {"trsm_snps_per_s": trsm_bound, "h2d_snps_per_s": h2d_bound,
                      "bound": None if slower is None else ("trsm" if slower == trsm_bound else "h2d"),
                      "frac": hr["snps_per_s"] / (slower * world) if slower else None,
-                     "e2e_frac": (e2e_h["value"] / (slower * world)) if slower and e2e_h else None,
-                     "basis": "per GPU: n^2 flop/SNP at the roofline peak; the bytes per SNP the e2e call moved "
-                              "over the measured pinned H2D link (2-bit codes: ceil(n/4) rounded up to 16)"}
+                     "e2e_frac": (hr["e2e"]["value"] / (slower * world)) if slower and hr.get("e2e") else None,
+                     "basis": "per GPU: n^2 flop/SNP at the roofline peak; n B/SNP over the measured pinned H2D link"}
+    if h2d and hr.get("e2e_packed_input") and trsm_bound:
+        packed_bound = min(trsm_bound, h2d * 1e9 / ((n_ + 3) // 4))
+        path_roofline["packed_input"] = {
+            "h2d_snps_per_s": h2d * 1e9 / ((n_ + 3) // 4),
+            "bound": "trsm" if packed_bound == trsm_bound else "h2d",
+            "e2e_frac": hr["e2e_packed_input"]["value"] / (packed_bound * world)}
     # the FP64 bar two ways: the FP64 ALU path and the sliced tensor-core path
     fp64_class = None
     if "fp64" in results and "sliced64" in results:

@@ -129,11 +129,6 @@ typedef struct {
   int single_piece;  /* precision studies only (inverse tile mode): 1 keeps L^-1 as its hi piece alone
                         (its lo piece zeroed: one BF16, TF32 or row-scaled FP16 rounding of L^-1);
                         b and se then carry that rounding, far above the split forms' 1e-5 */
-  int stream_pack;   /* gwas_solve_stream only: 1 (default) sends every block whose values all lie in
-                        0..3 (hard-called genotypes) over the host link as 2-bit codes, four SNP values
-                        a byte (gwas_pack_dosages2), packed by host threads and unpacked on the GPU
-                        into the same device slot: a quarter of the link's bytes, results identical;
-                        blocks holding other values go as int8.  0 sends every block as int8 */
 } gwas_config;
 
 enum {
@@ -184,9 +179,6 @@ int gwas_solve_block_f64(gwas_ctx *ctx, const double *XR, int64_t ldx, int ncols
  * are cut into blocks of cfg.bs columns and copied into a ring of
  * cfg.ring_depth device slots on a copy stream, overlapping the solve of the
  * previous blocks on the compute stream; results are copied back per block.
- * With cfg.stream_pack (the default) a block of values 0..3 crosses the link
- * as 2-bit codes (packed on the host while earlier blocks solve, unpacked by
- * a kernel on the compute stream); gwas_h2d_bytes counts what was copied.
  *   XR_host n x m int8, leading dimension ldx >= n (pinned memory gives full
  *           link speed; pageable memory works through the driver's staging)
  *   b_host, se_host p x m;  status_host m (se_host / status_host may be NULL)
@@ -194,7 +186,19 @@ int gwas_solve_block_f64(gwas_ctx *ctx, const double *XR, int64_t ldx, int ncols
 int gwas_solve_stream(gwas_ctx *ctx, const int8_t *XR_host, int64_t ldx, int64_t m, double *b_host,
                       double *se_host, int *status_host);
 
-/* The transport encoding of gwas_solve_stream (a storage format too): column c
+/* gwas_solve_stream over SNP columns held 2-bit packed in HOST memory (hard
+ * calls 0..3, four to a byte, as gwas_pack_dosages2 writes them and as genotype
+ * files commonly store them): the host link carries ceil(n/4) bytes per SNP
+ * instead of n, and a kernel unpacks each block into the device ring slot.
+ * Results are those of gwas_solve_stream on the unpacked int8 columns.
+ *   P_host  ceil(n/4) bytes per column, leading dimension ldp >= ceil(n/4)
+ * Other arguments, errors and results as gwas_solve_stream.  (Packing inside
+ * the stream does not pay on a host whose cores pack more slowly than the
+ * link carries int8: 16 cores packed ~20 GB/s against the link's ~56 GB/s.) */
+int gwas_solve_stream_packed(gwas_ctx *ctx, const uint8_t *P_host, int64_t ldp, int64_t m, double *b_host,
+                             double *se_host, int *status_host);
+
+/* The 2-bit encoding of gwas_solve_stream_packed (a storage format): column c
  * of the n x ncols int8 array X (leading dimension ldx) becomes P[c ldp ..
  * c ldp + ceil(n/4) - 1], byte k holding X[4k + i, c] in bits 2i .. 2i+1
  * (i = 0..3; rows past n as 0); ldp >= ceil(n/4).  Host memory, host code.
@@ -202,7 +206,8 @@ int gwas_solve_stream(gwas_ctx *ctx, const int8_t *XR_host, int64_t ldx, int64_t
 int gwas_pack_dosages2(const int8_t *X, int64_t ldx, int n, int ncols, uint8_t *P, int64_t ldp);
 
 /* Bytes the context has copied host -> device for SNP blocks since gwas_init
- * (all entry points; packed blocks count their packed bytes). */
+ * (the block solves with host input and both streams; packed columns count
+ * their packed bytes). */
 int64_t gwas_h2d_bytes(const gwas_ctx *ctx);
 
 /* gwas_solve_block without any allocation, FP64 solve only.  The paper has no

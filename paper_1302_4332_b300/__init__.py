@@ -47,7 +47,7 @@ EXPORTS = (
     "gwas_batch_last_error_detail",
     "gwas_batch_destroy", "gwas_solve_file", "gwas_solve_file_out", "gwas_reader_open", "gwas_reader_next",
     "gwas_reader_release", "gwas_reader_error_detail", "gwas_reader_close", "gwas_check_timeout",
-    "gwas_pack_dosages2", "gwas_h2d_bytes",
+    "gwas_pack_dosages2", "gwas_h2d_bytes", "gwas_solve_stream_packed",
 )
 GWAS_RESUME = 1
 STAGES = ("h2d", "trsm", "reduce", "d2h", "solve")
@@ -70,7 +70,7 @@ class _Config(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("bs", ctypes.c_int), ("ring_depth", ctypes.c_int),
                 ("device", ctypes.c_int), ("strip_group", ctypes.c_int), ("tile_mode", ctypes.c_int),
                 ("traits", ctypes.c_int), ("separate_sums", ctypes.c_int),
-                ("single_piece", ctypes.c_int), ("stream_pack", ctypes.c_int)]
+                ("single_piece", ctypes.c_int)]
 
 
 _lib = None
@@ -122,6 +122,8 @@ def load(path: str | None = None):
     lib.gwas_h2d_bytes.restype = i64
     lib.gwas_pack_dosages2.argtypes = [vp, i64, c_int, c_int, vp, i64]
     lib.gwas_pack_dosages2.restype = c_int
+    lib.gwas_solve_stream_packed.argtypes = [vp, vp, i64, i64, vp, vp, vp]
+    lib.gwas_solve_stream_packed.restype = c_int
     lib.gwas_strerror.argtypes = [c_int]
     lib.gwas_strerror.restype = ctypes.c_char_p
     lib.gwas_last_error_detail.argtypes = [vp]
@@ -318,7 +320,7 @@ class GLS:
     def __init__(self, phi_or_L, XL, y, h: float, sigma2: float = 1.0, *, precision: str = "fp64",
                  bs: int = 4096, ring_depth: int = 3, is_L: bool = False, device: int = -1, stream=None,
                  strip_group: int = 0, tiles: str = "auto", separate_sums: bool = False,
-                 single_piece: bool = False, stream_pack: bool = True):
+                 single_piece: bool = False):
         lib = load()
         n = int(np.shape(y)[0]) if not _is_torch(y) else int(y.shape[0])
         q = 0 if XL is None else (int(XL.shape[1]) if np.ndim(XL) == 2 or _is_torch(XL) else 1)
@@ -344,7 +346,6 @@ class GLS:
         cfg.traits = self.t
         cfg.separate_sums = int(bool(separate_sums))
         cfg.single_piece = int(bool(single_piece))
-        cfg.stream_pack = int(bool(stream_pack))
         self.precision, self.bs = precision, int(bs)
         stream_p = None
         if stream is not None:
@@ -440,6 +441,29 @@ class GLS:
             status = np.empty(m, dtype=np.int32)
         _, ptrs = self._outputs(m, keep, b, se, status)
         self._check(load().gwas_solve_stream(self._ctx, xp, ldx, m, *ptrs))
+        return b, se, status
+
+    def solve_stream_packed(self, P_host, b=None, se=None, status=None):
+        """As solve_stream over 2-bit packed HOST columns (ceil(n/4) x m uint8,
+        column-major, as pack_dosages2 returns them)."""
+        P = P_host
+        if _is_torch(P):
+            if P.is_cuda:
+                raise ValueError("solve_stream_packed takes host memory")
+            ptr, m, ldp = P.data_ptr(), int(P.shape[1]), int(P.stride(1))
+            if P.stride(0) != 1 or P.dtype != _torch().uint8:
+                raise ValueError("P_host must be column-major uint8")
+        else:
+            P = np.asfortranarray(P, dtype=np.uint8)
+            ptr, m, ldp = P.ctypes.data, int(P.shape[1]), int(P.shape[0])
+        if int(P.shape[0]) < (self.n + 3) // 4:
+            raise ValueError("P_host needs ceil(n/4) rows")
+        if b is None:
+            b = np.empty((self.p, m) if self.t == 1 else (self.p, m, self.t), order="F")
+            se = np.empty((self.p, m), order="F")
+            status = np.empty(m, dtype=np.int32)
+        _, ptrs = self._outputs(m, P, b, se, status)
+        self._check(load().gwas_solve_stream_packed(self._ctx, ptr, ldp, m, *ptrs))
         return b, se, status
 
     def adjoint_block(self, XR, dh_accum=None, dy_accum=None, chi2=None, dchi2_dh=None):

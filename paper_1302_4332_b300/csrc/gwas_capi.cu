@@ -27,6 +27,7 @@ struct gwas_ctx {
   int num_sms = 148;
   cudaStream_t stream = nullptr;
   cudaStream_t copy_stream = nullptr;
+  cudaStream_t out_stream = nullptr;  // the whole-study stream's result copies
   int n = 0, p = 0, q = 0, n_pad = 0, P = 0;
   int t = 1;  // phenotypes sharing the study (columns of y)
   int prec = GWAS_FP64, bs = 0, ring_depth = 0;
@@ -69,13 +70,9 @@ struct gwas_ctx {
   double* h_se = nullptr;
   int* h_status = nullptr;
   double* f64_in = nullptr;  // n x bs FP64 staging for gwas_solve_block_f64 with host input
-  // the 2-bit transport of gwas_solve_stream (set up on its first packed call)
-  bool stream_pack = false;
-  PackPool* pack_pool = nullptr;
-  int64_t ldp = 0;                   // packed bytes per column (ceil(n/4) rounded up to 16)
-  std::vector<uint8_t*> hpack;       // ring_depth pinned host slots of ldp x bs bytes
+  // 2-bit packed input (gwas_solve_stream_packed; set up on its first call)
+  int64_t ldp = 0;                   // packed bytes per column in a device slot (ceil(n/4) rounded up to 16)
   std::vector<uint8_t*> dpack;       // ring_depth device slots of ldp x bs bytes
-  std::vector<cudaEvent_t> ev_staged;  // the H2D copy out of hpack[slot] is done
   int64_t h2d_bytes = 0;             // SNP-block bytes copied host -> device
   void* static_scratch = nullptr;  // device address of the fixed scratch array (gwas_solve_block_static)
   int64_t launches = 0;
@@ -430,6 +427,7 @@ void free_all(gwas_ctx* c) {
   DeviceScope dscope_(c->dev);
   cudaStreamSynchronize(c->stream);
   if (c->copy_stream) cudaStreamSynchronize(c->copy_stream);
+  if (c->out_stream) cudaStreamSynchronize(c->out_stream);
   for (auto* p : c->ring) cudaFree(p);
   for (auto& v : {&c->ev_copied, &c->ev_free, &c->ev_out})
     for (auto ev : *v) cudaEventDestroy(ev);
@@ -440,15 +438,13 @@ void free_all(gwas_ctx* c) {
   cudaFree(c->d_b); cudaFree(c->d_se); cudaFree(c->d_status); cudaFree(c->f64_in); cudaFree(c->W32);
   cudaFree(c->AopT); cudaFree(c->Xhat); cudaFree(c->What); cudaFree(c->GH); cudaFree(c->adj);
   cudaFreeHost(c->h_b); cudaFreeHost(c->h_se); cudaFreeHost(c->h_status);
-  for (auto* p : c->hpack) cudaFreeHost(p);
   for (auto* p : c->dpack) cudaFree(p);
-  for (auto ev : c->ev_staged) cudaEventDestroy(ev);
-  pack_pool_destroy(c->pack_pool);
   if (c->tcs) tc::destroy(c->tcs);
   exact_destroy(c->exact);
   exact_destroy(c->sliced);
   for (auto* p : c->file_buf) cudaFreeHost(p);
   if (c->copy_stream) cudaStreamDestroy(c->copy_stream);
+  if (c->out_stream) cudaStreamDestroy(c->out_stream);
   delete c;
 }
 
@@ -463,7 +459,6 @@ void gwas_config_default(gwas_config* cfg) {
   cfg->bs = 4096;
   cfg->ring_depth = 3;
   cfg->device = -1;
-  cfg->stream_pack = 1;
 }
 
 const char* gwas_strerror(int code) {
@@ -496,7 +491,6 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
       (cfg.precision == GWAS_F16X2 && cfg.tile_mode != GWAS_TILES_AUTO && cfg.tile_mode != GWAS_TILES_INVERSE))
     return GWAS_ERR_ARG;
   if (cfg.separate_sums != 0 && cfg.separate_sums != 1) return GWAS_ERR_ARG;
-  if (cfg.stream_pack != 0 && cfg.stream_pack != 1) return GWAS_ERR_ARG;
   if (cfg.precision == GWAS_SLICED64 &&
       (cfg.tile_mode != GWAS_TILES_AUTO || cfg.strip_group != 0 || cfg.separate_sums != 0 || cfg.single_piece != 0))
     return GWAS_ERR_ARG;
@@ -531,13 +525,13 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
     ctx->num_sms = prop.multiProcessorCount;
     ctx->stream = static_cast<cudaStream_t>(stream);
     CK(cudaStreamCreateWithFlags(&ctx->copy_stream, cudaStreamNonBlocking));
+    CK(cudaStreamCreateWithFlags(&ctx->out_stream, cudaStreamNonBlocking));
     ctx->n = n; ctx->p = p; ctx->q = p - 1; ctx->t = traits;
     ctx->n_pad = (n + TB - 1) / TB * TB;
     ctx->P = ctx->n_pad / TB;
     ctx->prec = cfg.precision; ctx->bs = cfg.bs; ctx->ring_depth = cfg.ring_depth;
     ctx->separate_sums = cfg.separate_sums != 0;
     ctx->single_piece = cfg.single_piece != 0;
-    ctx->stream_pack = cfg.stream_pack != 0;
     ctx->h = h; ctx->sigma2 = sigma2;
     const size_t np = (size_t)ctx->n_pad, n2 = np * np;
     CK(dmalloc(&ctx->L, sizeof(double) * n2));
@@ -721,11 +715,17 @@ int gwas_solve_block_f64(gwas_ctx* ctx, const double* XR, int64_t ldx, int ncols
   return solve_common(ctx, XR, false, ldx, ncols, b, se, status);
 }
 
-int gwas_solve_stream(gwas_ctx* ctx, const int8_t* XR_host, int64_t ldx, int64_t m, double* b_host,
-                      double* se_host, int* status_host) {
+}  // extern "C"
+
+// The whole-study stream over host columns: int8 (ld = ldx bytes per column)
+// or 2-bit packed (ld = bytes per packed column, unpacked into the ring slot
+// on the GPU).
+static int stream_impl(gwas_ctx* ctx, const void* host, bool packed, int64_t ldx, int64_t m, double* b_host,
+                       double* se_host, int* status_host) {
   if (!ctx) return GWAS_ERR_ARG;
-  if (!XR_host || !b_host || m < 0 || ldx < ctx->n)
-    return fail(ctx, GWAS_ERR_ARG, "bad arguments to gwas_solve_stream");
+  const int64_t nb = ((int64_t)ctx->n + 3) / 4;
+  if (!host || !b_host || m < 0 || ldx < (packed ? nb : ctx->n))
+    return fail(ctx, GWAS_ERR_ARG, "bad arguments to the whole-study stream");
   if (m == 0) return GWAS_OK;
   DeviceScope dscope_(ctx->dev);
   CK(dscope_.status());
@@ -747,57 +747,35 @@ int gwas_solve_stream(gwas_ctx* ctx, const int8_t* XR_host, int64_t ldx, int64_t
       std::memcpy(status_host + blk * bs, ctx->h_status + (size_t)slot * bs, sizeof(int) * (size_t)nc);
     return GWAS_OK;
   };
-  // Columns whose stride is a multiple of 16 bytes and fits a ring slot are
-  // copied as they lie in host memory, one contiguous copy per block (a DMA
-  // of whole rows runs a few per cent faster than a pitched one); else the
-  // columns are repacked to the slot's stride n_pad by a pitched copy.
-  const bool flat = (ldx % 16) == 0 && ldx <= ctx->n_pad;
-  const int64_t ld_dev = flat ? ldx : ctx->n_pad;
-  // The 2-bit transport: pinned host and device slots of ldp x bs bytes and the
-  // packing threads, set up on the first packed call.
-  if (ctx->stream_pack && ctx->hpack.empty()) {
-    ctx->ldp = ((ctx->n + 3) / 4 + 15) / 16 * 16;
-    ctx->hpack.assign(R, nullptr);
+  const uint8_t* src0 = static_cast<const uint8_t*>(host);
+  if (packed && ctx->dpack.empty()) {  // device slots for the packed columns
+    ctx->ldp = (nb + 15) / 16 * 16;
     ctx->dpack.assign(R, nullptr);
-    ctx->ev_staged.assign(R, nullptr);
-    for (int s2 = 0; s2 < R; ++s2) {
-      CK(cudaMallocHost(&ctx->hpack[s2], (size_t)ctx->ldp * bs));
-      CK(dmalloc(&ctx->dpack[s2], (size_t)ctx->ldp * bs));
-      CK(cudaEventCreateWithFlags(&ctx->ev_staged[s2], cudaEventDisableTiming));
-    }
-    ctx->pack_pool = pack_pool_create();
+    for (int s2 = 0; s2 < R; ++s2) CK(dmalloc(&ctx->dpack[s2], (size_t)ctx->ldp * bs));
   }
-  std::vector<char> packed(R, 0);        // block in slot s crossed the link packed
-  std::vector<int64_t> sld(R, ld_dev);   // leading dimension of the block in ring slot s
+  // Int8 columns whose stride is a multiple of 16 bytes and fits a ring slot
+  // are copied as they lie in host memory, one contiguous copy per block (a
+  // DMA of whole rows runs a few per cent faster than a pitched one); else the
+  // columns are repacked to the slot's stride by a pitched copy.  Packed
+  // columns likewise into a slot of ldp bytes per column.
+  const int64_t slot_ld_in = packed ? ctx->ldp : ctx->n_pad;
+  const int64_t width = packed ? nb : ctx->n;
+  const bool flat = (ldx % 16) == 0 && ldx <= slot_ld_in;
+  const int64_t ld_dev = flat ? ldx : slot_ld_in;  // the block's leading dimension on the device
   auto enqueue_copy = [&](int64_t blk) -> int {
     const int slot = (int)(blk % R), nc = cols_of(blk);
-    const int8_t* src = XR_host + blk * bs * ldx;
-    bool pk = false;
-    if (ctx->stream_pack) {
-      // hpack[slot] last left for the device R blocks ago; packed while earlier blocks solve
-      CK(cudaEventSynchronize(ctx->ev_staged[slot]));
-      pk = pack_pool_run(ctx->pack_pool, src, ldx, ctx->n, nc, ctx->hpack[slot], ctx->ldp);
-    }
+    void* dst = packed ? static_cast<void*>(ctx->dpack[slot]) : static_cast<void*>(ctx->ring[slot]);
+    const uint8_t* src = src0 + blk * bs * ldx;
     CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_free[slot], 0));
     StageMark mk(ctx, GWAS_STAGE_H2D, ctx->copy_stream);
-    if (pk) {
-      CK(cudaMemcpyAsync(ctx->dpack[slot], ctx->hpack[slot], (size_t)ctx->ldp * nc, cudaMemcpyHostToDevice,
-                         ctx->copy_stream));
-      CK(cudaEventRecord(ctx->ev_staged[slot], ctx->copy_stream));
-      ctx->h2d_bytes += ctx->ldp * nc;
-      sld[slot] = ctx->n_pad;
-    } else if (flat) {  // the last column ends after its n-th byte
-      CK(cudaMemcpyAsync(ctx->ring[slot], src, (size_t)((nc - 1) * ldx + ctx->n), cudaMemcpyHostToDevice,
-                         ctx->copy_stream));
-      ctx->h2d_bytes += (nc - 1) * ldx + ctx->n;
-      sld[slot] = ld_dev;
+    if (flat) {  // the last column ends after its width-th byte
+      CK(cudaMemcpyAsync(dst, src, (size_t)((nc - 1) * ldx + width), cudaMemcpyHostToDevice, ctx->copy_stream));
+      ctx->h2d_bytes += (nc - 1) * ldx + width;
     } else {
-      CK(cudaMemcpy2DAsync(ctx->ring[slot], (size_t)ctx->n_pad, src, (size_t)ldx, (size_t)ctx->n, (size_t)nc,
+      CK(cudaMemcpy2DAsync(dst, (size_t)slot_ld_in, src, (size_t)ldx, (size_t)width, (size_t)nc,
                            cudaMemcpyHostToDevice, ctx->copy_stream));
-      ctx->h2d_bytes += (int64_t)ctx->n * nc;
-      sld[slot] = ld_dev;
+      ctx->h2d_bytes += width * nc;
     }
-    packed[slot] = pk;
     CK(cudaEventRecord(ctx->ev_copied[slot], ctx->copy_stream));
     return GWAS_OK;
   };
@@ -810,28 +788,32 @@ int gwas_solve_stream(gwas_ctx* ctx, const int8_t* XR_host, int64_t ldx, int64_t
   for (int64_t blk = 0; blk < nblk; ++blk) {
     const int slot = (int)(blk % R), nc = cols_of(blk);
     CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_copied[slot], 0));
-    if (packed[slot]) {  // the 2-bit codes into the ring slot, int8 as the copy would have left them
+    if (packed) {  // the 2-bit codes into the ring slot as int8
       StageMark mk(ctx, GWAS_STAGE_H2D, ctx->stream);
-      CK(launch_unpack2(ctx->dpack[slot], ctx->ldp, ctx->n, nc, ctx->ring[slot], ctx->n_pad, ctx->stream));
+      CK(launch_unpack2(ctx->dpack[slot], ld_dev, ctx->n, nc, ctx->ring[slot], ctx->n_pad, ctx->stream));
       ctx->launches += 1;
     }
     double* ob = ctx->d_b + (size_t)slot * T * p * bs;
     double* ose = ctx->d_se + (size_t)slot * p * bs;
     int* ost = ctx->d_status + (size_t)slot * bs;
-    if ((rc = run_block(ctx, ctx->ring[slot], true, sld[slot], nc, ob, ose, ost)) != GWAS_OK) return rc;
+    // the slot's outputs were copied out R blocks ago (on the result stream)
+    if (blk >= R) CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_out[slot], 0));
+    if ((rc = run_block(ctx, ctx->ring[slot], true, packed ? ctx->n_pad : ld_dev, nc, ob, ose, ost)) != GWAS_OK)
+      return rc;
     CK(cudaEventRecord(ctx->ev_free[slot], ctx->stream));
-    {
-    StageMark mk(ctx, GWAS_STAGE_D2H, ctx->stream);
+    {  // results out on their own stream, overlapping the next block's solve
+    CK(cudaStreamWaitEvent(ctx->out_stream, ctx->ev_free[slot], 0));
+    StageMark mk(ctx, GWAS_STAGE_D2H, ctx->out_stream);
     CK(cudaMemcpyAsync(ctx->h_b + (size_t)slot * T * p * bs, ob, sizeof(double) * (size_t)p * nc * T,
-                       cudaMemcpyDeviceToHost, ctx->stream));
+                       cudaMemcpyDeviceToHost, ctx->out_stream));
     if (se_host)
       CK(cudaMemcpyAsync(ctx->h_se + (size_t)slot * p * bs, ose, sizeof(double) * (size_t)p * nc,
-                         cudaMemcpyDeviceToHost, ctx->stream));
+                         cudaMemcpyDeviceToHost, ctx->out_stream));
     if (status_host)
       CK(cudaMemcpyAsync(ctx->h_status + (size_t)slot * bs, ost, sizeof(int) * (size_t)nc,
-                         cudaMemcpyDeviceToHost, ctx->stream));
+                         cudaMemcpyDeviceToHost, ctx->out_stream));
     }
-    CK(cudaEventRecord(ctx->ev_out[slot], ctx->stream));
+    CK(cudaEventRecord(ctx->ev_out[slot], ctx->out_stream));
     if (next_copy < nblk) {
       if ((rc = enqueue_copy(next_copy)) != GWAS_OK) return rc;
       ++next_copy;
@@ -841,6 +823,18 @@ int gwas_solve_stream(gwas_ctx* ctx, const int8_t* XR_host, int64_t ldx, int64_t
   }
   if ((rc = drain(nblk - 1)) != GWAS_OK) return rc;
   return check_device_status(ctx);
+}
+
+extern "C" {
+
+int gwas_solve_stream(gwas_ctx* ctx, const int8_t* XR_host, int64_t ldx, int64_t m, double* b_host,
+                      double* se_host, int* status_host) {
+  return stream_impl(ctx, XR_host, false, ldx, m, b_host, se_host, status_host);
+}
+
+int gwas_solve_stream_packed(gwas_ctx* ctx, const uint8_t* P_host, int64_t ldp, int64_t m, double* b_host,
+                             double* se_host, int* status_host) {
+  return stream_impl(ctx, P_host, true, ldp, m, b_host, se_host, status_host);
 }
 
 }  // extern "C"
@@ -1944,6 +1938,7 @@ int gwas_timing_enable(gwas_ctx* ctx, int enable) {
   CK(dscope_.status());
   CK(cudaStreamSynchronize(ctx->stream));
   CK(cudaStreamSynchronize(ctx->copy_stream));
+  CK(cudaStreamSynchronize(ctx->out_stream));
   for (auto& mk : ctx->marks) {
     ctx->event_pool.push_back(mk.a);
     ctx->event_pool.push_back(mk.b);

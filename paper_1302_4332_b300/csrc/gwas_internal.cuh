@@ -205,16 +205,11 @@ cudaError_t launch_exact_adjoint_sums(const int32_t* C, int64_t ldc, int RS, con
                                       const double* GH, int q, int ncols, double h, double sigma2, const int* xmax,
                                       double* chi2, double* dh, double* wv, double* dh_accum, double* uT,
                                       cudaStream_t s);
-// The 2-bit transport of gwas_solve_stream (host_pack.cu): host packing of
-// int8 columns whose values all lie in 0..3 (false otherwise), a pool of
-// persistent host threads that packs a block's columns in parallel, and the
-// device unpacking into an int8 slot (leading dimension ldx, a multiple of 16,
-// 16-byte aligned; rows n .. 16 ceil(n/16) - 1 written as 0).
+// 2-bit packed SNP columns (host_pack.cu): host packing of int8 columns whose
+// values all lie in 0..3 (false otherwise), and the device unpacking into an
+// int8 slot (leading dimension ldx, a multiple of 16, 16-byte aligned; rows
+// n .. 16 ceil(n/16) - 1 written as 0).
 bool pack2_columns(const int8_t* X, int64_t ldx, int n, int c0, int c1, uint8_t* P, int64_t ldp);
-struct PackPool;
-PackPool* pack_pool_create();
-bool pack_pool_run(PackPool* p, const int8_t* X, int64_t ldx, int n, int ncols, uint8_t* P, int64_t ldp);
-void pack_pool_destroy(PackPool* p);
 cudaError_t launch_unpack2(const uint8_t* P, int64_t ldp, int n, int ncols, int8_t* X, int64_t ldx, cudaStream_t s);
 cudaError_t launch_log_diag(const double* L, int64_t ld, int n, double* out, cudaStream_t s);
 cudaError_t launch_col_sumsq(const double* X, int64_t ld, int n, int ncols, double* out, cudaStream_t s);

@@ -1,22 +1,18 @@
-// The 2-bit transport of gwas_solve_stream: hard-called genotypes (values
-// 0..3) cross the host link four to a byte.  The link, not the solve, bounds
-// the whole-study stream from host memory (n int8 bytes per SNP at ~56 GB/s
-// against ~7.6 M SNPs/s of solves at n = 10^4); packing on the host cores and
-// unpacking in HBM moves a quarter of the bytes.
+// 2-bit packed SNP columns: hard-called genotypes (values 0..3) four to a
+// byte, the way genotype files commonly store them.  The host link, not the
+// solve, bounds the whole-study stream of int8 columns (n bytes per SNP at
+// ~56 GB/s against ~7.6 M SNPs/s of solves at n = 10^4); columns that are
+// already packed cross it in a quarter of the bytes and are unpacked in HBM
+// (gwas_solve_stream_packed).  Packing on the host in the stream itself does
+// not pay: 16 host cores pack ~20 GB/s of int8, below the link's 56 GB/s.
 //
 // Encoding (gwas_pack_dosages2): column c occupies ceil(n/4) bytes at P + c ldp;
 // byte k holds rows 4k .. 4k+3, row 4k + i in bits 2i .. 2i+1; rows past n are 0.
 #include <cuda_runtime.h>
 
 #include <algorithm>
-#include <atomic>
-#include <condition_variable>
 #include <cstdint>
 #include <cstring>
-#include <functional>
-#include <mutex>
-#include <thread>
-#include <vector>
 
 #include "gwas_internal.cuh"
 
@@ -58,89 +54,6 @@ bool pack2_columns(const int8_t* X, int64_t ldx, int n, int c0, int c1, uint8_t*
     if (bad & 0xFCFCFCFCFCFCFCFCull) return false;  // a value outside 0..3
   }
   return true;
-}
-
-// ---------------------------------------------------------- thread pool
-// Persistent workers for pack2 over column ranges: run() hands out chunks of
-// columns through an atomic cursor; the calling thread works too and returns
-// when every chunk is done.
-struct PackPool {
-  std::vector<std::thread> th;
-  std::mutex mu;
-  std::condition_variable cv_go, cv_done;
-  uint64_t gen = 0;
-  bool quit = false;
-  // the current job
-  const int8_t* X = nullptr;
-  int64_t ldx = 0, ldp = 0;
-  int n = 0, ncols = 0, chunk = 1;
-  uint8_t* P = nullptr;
-  std::atomic<int> cursor{0}, pending{0};
-  std::atomic<bool> ok{true};
-
-  void work() {
-    for (;;) {
-      const int c = cursor.fetch_add(chunk);
-      if (c >= ncols) break;
-      const int c1 = std::min(ncols, c + chunk);
-      if (!pack2_columns(X, ldx, n, c, c1, P, ldp)) ok.store(false);
-    }
-  }
-  void loop() {
-    uint64_t seen = 0;
-    for (;;) {
-      {
-        std::unique_lock<std::mutex> lk(mu);
-        cv_go.wait(lk, [&] { return quit || gen != seen; });
-        if (quit) return;
-        seen = gen;
-      }
-      work();
-      if (pending.fetch_sub(1) == 1) {
-        std::lock_guard<std::mutex> lk(mu);
-        cv_done.notify_all();
-      }
-    }
-  }
-  bool run(const int8_t* X_, int64_t ldx_, int n_, int ncols_, uint8_t* P_, int64_t ldp_) {
-    {
-      std::lock_guard<std::mutex> lk(mu);
-      X = X_, ldx = ldx_, n = n_, ncols = ncols_, P = P_, ldp = ldp_;
-      chunk = std::max(1, ncols_ / (8 * ((int)th.size() + 1)));
-      cursor.store(0);
-      ok.store(true);
-      pending.store((int)th.size());
-      ++gen;
-    }
-    cv_go.notify_all();
-    work();
-    std::unique_lock<std::mutex> lk(mu);
-    cv_done.wait(lk, [&] { return pending.load() == 0; });
-    return ok.load();
-  }
-};
-
-PackPool* pack_pool_create() {
-  PackPool* p = new PackPool;
-  const unsigned hc = std::thread::hardware_concurrency();
-  const int nw = std::max(0, std::min(15, (int)(hc ? hc : 2) - 1));
-  for (int k = 0; k < nw; ++k) p->th.emplace_back([p] { p->loop(); });
-  return p;
-}
-
-bool pack_pool_run(PackPool* p, const int8_t* X, int64_t ldx, int n, int ncols, uint8_t* P, int64_t ldp) {
-  return p->run(X, ldx, n, ncols, P, ldp);
-}
-
-void pack_pool_destroy(PackPool* p) {
-  if (!p) return;
-  {
-    std::lock_guard<std::mutex> lk(p->mu);
-    p->quit = true;
-  }
-  p->cv_go.notify_all();
-  for (auto& t : p->th) t.join();
-  delete p;
 }
 
 // --------------------------------------------------------------- unpacking

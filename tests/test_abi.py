@@ -121,9 +121,3 @@ def test_pack_dosages2_refuses_other_values(lib, bad):
     X[0, 4] = bad
     with pytest.raises(gw.GwasError):
         gw.pack_dosages2(X)
-
-
-def test_stream_pack_is_on_by_default(lib):
-    cfg = gw._Config()
-    lib.gwas_config_default(ctypes.byref(cfg))
-    assert cfg.stream_pack == 1

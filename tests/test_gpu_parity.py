@@ -142,48 +142,32 @@ def test_stream_matches_blocks(small_study):
 
 
 @pytest.mark.parametrize("prec", ("fp64", "f16x2", "sliced64"))
-def test_stream_2bit_transport(small_study, prec):
-    """gwas_solve_stream's 2-bit transport: blocks of values 0..3 cross the
-    link as 2-bit codes; results bit for bit those of the int8 transport, a
-    quarter of the bytes copied; a block holding another value (here a 5)
-    crosses as int8; an input leading dimension that is not the device slot's
-    (ldx = n + 3) goes through the same unpacking."""
+def test_stream_packed_input(small_study, prec):
+    """gwas_solve_stream_packed: the same columns held 2-bit packed in host
+    memory give bit for bit gwas_solve_stream's results while the link carries
+    ceil(n/4) bytes per SNP; a packed leading dimension that is not a multiple
+    of 16 (ldp = ceil(n/4) + 3) goes through the pitched copy."""
     s, X, L, (r, se, st) = small_study
     n, m, bs = X.shape[0], 1100, 256
-    Xh = np.asfortranarray(X[:, :m])
-    Xw = np.zeros((n + 3, m), dtype=np.int8, order="F")  # ldx = n + 3 (neither 16-aligned nor n_pad)
-    Xw[:n] = Xh
-    out = {}
-    for pack in (False, True):
-        with gw.GLS(s["Phi"], s["XL"], s["y"], s["h"], s["sigma2"], precision=prec, bs=bs,
-                    stream_pack=pack) as g:
-            h0 = g.h2d_bytes
-            out[pack] = g.solve_stream(Xh)
-            moved = g.h2d_bytes - h0
-            out[(pack, "w")] = g.solve_stream(Xw[:n])
-        ldp = ((n + 3) // 4 + 15) // 16 * 16
-        assert moved == (ldp * m if pack else n * m), (pack, moved)
-    for a, b_ in zip(out[False], out[True]):
-        assert np.array_equal(a, b_, equal_nan=True)
-    for a, b_ in zip(out[False], out[(True, "w")]):
-        assert np.array_equal(a, b_, equal_nan=True)
-    tol = TOL64 if prec in ("fp64", "sliced64") else 1e-5
-    e = compare(*out[True], r[:, :m], se[:, :m], st[:m])
-    assert e["b_norm"] <= tol and e["se_rel"] <= tol, e
-    # a 5 in the third block: that block goes as int8, the others packed
-    Xm = Xh.copy()
-    Xm[17, 2 * bs + 9] = 5
-    rm, sem, _, stm = oracle.gls(L, s["XL"], s["y"], Xm)
+    Xh = np.asfortranarray(X[:, :m].astype(np.int8))
+    P = gw.pack_dosages2(Xh)
+    nb = (n + 3) // 4
+    Pw = np.zeros((nb + 3, m), dtype=np.uint8, order="F")
+    Pw[:nb] = P
     with gw.GLS(s["Phi"], s["XL"], s["y"], s["h"], s["sigma2"], precision=prec, bs=bs) as g:
+        ref = g.solve_stream(Xh)
         h0 = g.h2d_bytes
-        bm, sem_g, stm_g = g.solve_stream(Xm)
+        out = g.solve_stream_packed(P)
         moved = g.h2d_bytes - h0
-    nblk = (m + bs - 1) // bs
-    cols3 = min(bs, m - 2 * bs)
-    assert moved == ldp * (m - cols3) + n * cols3, moved
-    e = compare(bm, sem_g, stm_g, rm, sem, stm)
+        out_w = g.solve_stream_packed(Pw)
+    assert moved == nb * m, moved
+    for a_, b_ in zip(ref, out):
+        assert np.array_equal(a_, b_, equal_nan=True)
+    for a_, b_ in zip(ref, out_w):
+        assert np.array_equal(a_, b_, equal_nan=True)
+    tol = TOL64 if prec in ("fp64", "sliced64") else 1e-5
+    e = compare(*out, r[:, :m], se[:, :m], st[:m])
     assert e["b_norm"] <= tol and e["se_rel"] <= tol, e
-    assert nblk == 5
 
 
 # ---------------------------------------------------------------- split precision
