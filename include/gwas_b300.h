@@ -368,6 +368,9 @@ int gwas_solve_file(gwas_ctx *ctx, const char *path, int64_t header_bytes, int64
  * A checkpoint file out_path + ".ckpt" (the same header with magic "GWASCKP\0"
  * and, at byte 48, uint64 done) advances every 16 blocks and at the end, each
  * time after the records it covers were flushed to disk (fdatasync).  With
+ * flags & GWAS_PACKED_INPUT: the input columns are 2-bit packed (the encoding
+ * of gwas_pack_dosages2, ldx >= ceil(n/4) bytes per column): a quarter of the
+ * bytes from disk and over the link, unpacked on the GPU; results identical.
  * flags & GWAS_RESUME the run continues from the checkpoint's `done` column
  * (rewriting at most the blocks after it; a missing checkpoint starts at 0); a
  * checkpoint of another run (p, n, col0, m, precision) is GWAS_ERR_ARG.
@@ -375,6 +378,7 @@ int gwas_solve_file(gwas_ctx *ctx, const char *path, int64_t header_bytes, int64
  * Errors: GWAS_ERR_IO (the input as in gwas_solve_file; creating or writing the
  * output or checkpoint), and those of gwas_solve_file. */
 #define GWAS_RESUME 1
+#define GWAS_PACKED_INPUT 2
 #define GWAS_RESULT_RECORD_BYTES(p) (16 * (p) + 8)
 /* With t phenotypes a record holds double b[t][p] (phenotype-major), se[p], status, 0; the header
  * stores t at byte 56 (uint64). */

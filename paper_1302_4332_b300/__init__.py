@@ -50,6 +50,7 @@ EXPORTS = (
     "gwas_pack_dosages2", "gwas_h2d_bytes", "gwas_solve_stream_packed",
 )
 GWAS_RESUME = 1
+GWAS_PACKED_INPUT = 2
 STAGES = ("h2d", "trsm", "reduce", "d2h", "solve")
 
 
@@ -502,15 +503,17 @@ class GLS:
         return b, se, st
 
     def solve_file_out(self, path: str, m: int, out_path: str, ldx: int | None = None, col0: int = 0,
-                       header_bytes: int = 0, resume: bool = False) -> int:
+                       header_bytes: int = 0, resume: bool = False, packed: bool = False) -> int:
         """Columns col0 .. col0+m-1 of the dosage file, disk to disk: results
         written to out_path (read them with read_results), with a checkpoint
-        beside it; resume=True continues an interrupted run.  Returns the
-        number of columns on disk."""
+        beside it; resume=True continues an interrupted run; packed=True reads
+        2-bit packed columns (pack_dosages2's encoding, ldx default ceil(n/4)).
+        Returns the number of columns on disk."""
         done = ctypes.c_int64(0)
-        self._check(load().gwas_solve_file_out(self._ctx, os.fsencode(path), int(header_bytes), int(ldx or self.n),
-                                               int(col0), int(m), os.fsencode(out_path),
-                                               GWAS_RESUME if resume else 0, ctypes.byref(done)))
+        ld = int(ldx or ((self.n + 3) // 4 if packed else self.n))
+        flags = (GWAS_RESUME if resume else 0) | (GWAS_PACKED_INPUT if packed else 0)
+        self._check(load().gwas_solve_file_out(self._ctx, os.fsencode(path), int(header_bytes), ld, int(col0),
+                                               int(m), os.fsencode(out_path), flags, ctypes.byref(done)))
         return done.value
 
     def synchronize(self):

@@ -717,6 +717,16 @@ int gwas_solve_block_f64(gwas_ctx* ctx, const double* XR, int64_t ldx, int ncols
 
 }  // extern "C"
 
+// Device slots for 2-bit packed columns (ldp = ceil(n/4) rounded up to 16
+// bytes per column), allocated on first use.
+static int ensure_packed_slots(gwas_ctx* ctx) {
+  if (!ctx->dpack.empty()) return GWAS_OK;
+  ctx->ldp = ((ctx->n + 3) / 4 + 15) / 16 * 16;
+  ctx->dpack.assign(ctx->ring_depth, nullptr);
+  for (auto& d : ctx->dpack) CK(dmalloc(&d, (size_t)ctx->ldp * ctx->bs));
+  return GWAS_OK;
+}
+
 // The whole-study stream over host columns: int8 (ld = ldx bytes per column)
 // or 2-bit packed (ld = bytes per packed column, unpacked into the ring slot
 // on the GPU).
@@ -748,10 +758,9 @@ static int stream_impl(gwas_ctx* ctx, const void* host, bool packed, int64_t ldx
     return GWAS_OK;
   };
   const uint8_t* src0 = static_cast<const uint8_t*>(host);
-  if (packed && ctx->dpack.empty()) {  // device slots for the packed columns
-    ctx->ldp = (nb + 15) / 16 * 16;
-    ctx->dpack.assign(R, nullptr);
-    for (int s2 = 0; s2 < R; ++s2) CK(dmalloc(&ctx->dpack[s2], (size_t)ctx->ldp * bs));
+  if (packed) {
+    const int rc0 = ensure_packed_slots(ctx);
+    if (rc0 != GWAS_OK) return rc0;
   }
   // Int8 columns whose stride is a multiple of 16 bytes and fits a ring slot
   // are copied as they lie in host memory, one contiguous copy per block (a
@@ -844,10 +853,17 @@ int gwas_solve_stream_packed(gwas_ctx* ctx, const uint8_t* P_host, int64_t ldp, 
 // column order, while the GPU works on later blocks.
 template <typename Sink>
 static int solve_file_impl(gwas_ctx* ctx, const char* path, int64_t header_bytes, int64_t ldx, int64_t col0, int64_t m,
-                           bool want_se, bool want_status, Sink&& sink) {
+                           bool packed, bool want_se, bool want_status, Sink&& sink) {
   DeviceScope dscope_(ctx->dev);
   CK(dscope_.status());
   const int R = ctx->ring_depth, bs = ctx->bs, p = ctx->p;
+  // packed columns (2-bit codes, ceil(n/4) bytes) land in a device slot of
+  // ldp bytes per column and are unpacked into the ring slot
+  const int64_t width = packed ? ((int64_t)ctx->n + 3) / 4 : ctx->n;
+  if (packed) {
+    const int r0 = ensure_packed_slots(ctx);
+    if (r0 != GWAS_OK) return r0;
+  }
   const int64_t nblk = (m + bs - 1) / bs;
   auto cols_of = [&](int64_t blk) { return (int)std::min<int64_t>(bs, m - blk * bs); };
   if (ctx->file_buf_bytes < ldx * bs) {
@@ -878,11 +894,21 @@ static int solve_file_impl(gwas_ctx* ctx, const char* path, int64_t header_bytes
       CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_free[slot], 0));
       {
         StageMark mk(ctx, GWAS_STAGE_H2D, ctx->copy_stream);
-        CK(cudaMemcpy2DAsync(ctx->ring[slot], (size_t)ctx->n_pad, hb, (size_t)ldx, (size_t)ctx->n, (size_t)nc,
-                             cudaMemcpyHostToDevice, ctx->copy_stream));
+        if (packed)
+          CK(cudaMemcpy2DAsync(ctx->dpack[slot], (size_t)ctx->ldp, hb, (size_t)ldx, (size_t)width, (size_t)nc,
+                               cudaMemcpyHostToDevice, ctx->copy_stream));
+        else
+          CK(cudaMemcpy2DAsync(ctx->ring[slot], (size_t)ctx->n_pad, hb, (size_t)ldx, (size_t)ctx->n, (size_t)nc,
+                               cudaMemcpyHostToDevice, ctx->copy_stream));
+        ctx->h2d_bytes += width * nc;
       }
       CK(cudaEventRecord(ctx->ev_copied[slot], ctx->copy_stream));
       CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_copied[slot], 0));
+      if (packed) {
+        StageMark mk(ctx, GWAS_STAGE_H2D, ctx->stream);
+        CK(launch_unpack2(ctx->dpack[slot], ctx->ldp, ctx->n, nc, ctx->ring[slot], ctx->n_pad, ctx->stream));
+        ctx->launches += 1;
+      }
       double* ob = ctx->d_b + (size_t)slot * ctx->t * p * bs;
       double* ose = ctx->d_se + (size_t)slot * p * bs;
       int* ost = ctx->d_status + (size_t)slot * bs;
@@ -965,7 +991,7 @@ int gwas_solve_file(gwas_ctx* ctx, const char* path, int64_t header_bytes, int64
     return fail(ctx, GWAS_ERR_ARG, "bad arguments to gwas_solve_file");
   if (m == 0) return GWAS_OK;
   const int p = ctx->p, bs = ctx->bs;
-  return solve_file_impl(ctx, path, header_bytes, ldx, col0, m, se_host != nullptr, status_host != nullptr,
+  return solve_file_impl(ctx, path, header_bytes, ldx, col0, m, false, se_host != nullptr, status_host != nullptr,
                          [&](int64_t blk, int nc, const double* hb, const double* hse, const int* hst) -> int {
                            for (int k = 0; k < ctx->t; ++k)  // phenotype k: p x nc at hb + k p nc
                              std::memcpy(b_host + (k * m + blk * bs) * p, hb + (size_t)k * p * nc,
@@ -979,7 +1005,9 @@ int gwas_solve_file(gwas_ctx* ctx, const char* path, int64_t header_bytes, int64
 int gwas_solve_file_out(gwas_ctx* ctx, const char* in_path, int64_t header_bytes, int64_t ldx, int64_t col0,
                         int64_t m, const char* out_path, int flags, int64_t* done_out) {
   if (!ctx) return GWAS_ERR_ARG;
-  if (!in_path || !out_path || header_bytes < 0 || ldx < ctx->n || col0 < 0 || m < 0 || (flags & ~GWAS_RESUME))
+  const bool packed_in = (flags & GWAS_PACKED_INPUT) != 0;
+  if (!in_path || !out_path || header_bytes < 0 || ldx < (packed_in ? ((int64_t)ctx->n + 3) / 4 : ctx->n) ||
+      col0 < 0 || m < 0 || (flags & ~(GWAS_RESUME | GWAS_PACKED_INPUT)))
     return fail(ctx, GWAS_ERR_ARG, "bad arguments to gwas_solve_file_out");
   const int p = ctx->p, bs = ctx->bs, T = ctx->t;
   const size_t rec = GWAS_RESULT_RECORD_BYTES_T(p, T);
@@ -1031,7 +1059,7 @@ int gwas_solve_file_out(gwas_ctx* ctx, const char* in_path, int64_t header_bytes
     std::vector<char> buf((size_t)bs * rec);
     const int64_t start = done;
     int64_t since_sync = 0;
-    rc = solve_file_impl(ctx, in_path, header_bytes, ldx, col0 + start, m - start, true, true,
+    rc = solve_file_impl(ctx, in_path, header_bytes, ldx, col0 + start, m - start, packed_in, true, true,
                          [&](int64_t blk, int nc, const double* hb, const double* hse, const int* hst) -> int {
                            for (int c = 0; c < nc; ++c) {
                              char* r = buf.data() + (size_t)c * rec;

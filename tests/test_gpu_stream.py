@@ -35,7 +35,7 @@ def dosage_file(tmp_path_factory):
     return str(path), n, m, ld, header, X
 
 
-TOL = {"fp64": 1e-10, "bf16x3": 1e-5, "f16x2": 1e-5}
+TOL = {"fp64": 1e-10, "sliced64": 1e-10, "bf16x3": 1e-5, "f16x2": 1e-5}
 
 
 @pytest.fixture(scope="module")
@@ -108,6 +108,46 @@ def test_solve_file_out_writes_results_and_resumes(dosage_file, oracle_results, 
         with pytest.raises(gw.GwasError) as e:
             g.solve_file_out(path, 10, str(tmp_path / "no_such_dir" / "r.bin"), ldx=ld, header_bytes=header)
         assert e.value.name == "GWAS_ERR_IO"
+
+
+@pytest.mark.parametrize("prec", ["fp64", "f16x2", "sliced64"])
+def test_solve_file_out_packed_input(dosage_file, oracle_results, tmp_path, prec):
+    """Disk to disk from a 2-bit packed file (GWAS_PACKED_INPUT; columns of
+    ceil(n/4) bytes at a stride of 257 bytes after a 64-byte header): the
+    result file equals the one from the int8 file byte for byte, a quarter of
+    the bytes crossed the link, and a packed run resumes from a checkpoint."""
+    path, n, m, ld, header, X = dosage_file
+    nb = (n + 3) // 4
+    ldp = nb + 7
+    raw = np.zeros((m, ldp), dtype=np.uint8)
+    raw[:, :nb] = gw.pack_dosages2(X).T
+    ppath = str(tmp_path / "dosages.2bit")
+    with open(ppath, "wb") as f:
+        f.write(b"\x5a" * 64)
+        f.write(raw.tobytes())
+    s = gwas_synth.study(n, 4, 2000, 0.6, seed=40)
+    out8, outp = str(tmp_path / "r8.bin"), str(tmp_path / "rp.bin")
+    with gw.GLS(s["Phi"], s["XL"], s["y"], 0.6, 1.0, precision=prec, bs=256) as g:
+        assert g.solve_file_out(path, m - 100, out8, ldx=ld, col0=100, header_bytes=header) == m - 100
+        h0 = g.h2d_bytes
+        assert g.solve_file_out(ppath, m - 100, outp, ldx=ldp, col0=100, header_bytes=64, packed=True) == m - 100
+        assert g.h2d_bytes - h0 == nb * (m - 100)
+        full = open(outp, "rb").read()
+        assert full == open(out8, "rb").read()
+        _, b2, se2, st2 = gw.read_results(outp)
+        _check_oracle(b2, se2, st2, oracle_results, np.arange(100, m), prec)
+        ck = bytearray(open(outp + ".ckpt", "rb").read())
+        ck[48:56] = (512).to_bytes(8, "little")
+        open(outp + ".ckpt", "wb").write(bytes(ck))
+        with open(outp, "r+b") as f:
+            f.seek(64 + 512 * 72)
+            f.write(b"\xee" * (72 * 300))
+        assert g.solve_file_out(ppath, m - 100, outp, ldx=ldp, col0=100, header_bytes=64, packed=True,
+                                resume=True) == m - 100
+        assert open(outp, "rb").read() == full
+        with pytest.raises(gw.GwasError) as e:  # a packed stride below ceil(n/4)
+            g.solve_file_out(ppath, 10, outp, ldx=nb - 1, header_bytes=64, packed=True)
+        assert e.value.name == "GWAS_ERR_ARG"
 
 
 def test_solve_file_several_phenotypes(dosage_file, tmp_path):
