@@ -721,9 +721,18 @@ int gwas_solve_block_f64(gwas_ctx* ctx, const double* XR, int64_t ldx, int ncols
 // bytes per column), allocated on first use.
 static int ensure_packed_slots(gwas_ctx* ctx) {
   if (!ctx->dpack.empty()) return GWAS_OK;
-  ctx->ldp = ((ctx->n + 3) / 4 + 15) / 16 * 16;
-  ctx->dpack.assign(ctx->ring_depth, nullptr);
-  for (auto& d : ctx->dpack) CK(dmalloc(&d, (size_t)ctx->ldp * ctx->bs));
+  const int64_t ldp = ((ctx->n + 3) / 4 + 15) / 16 * 16;
+  std::vector<uint8_t*> slots(ctx->ring_depth, nullptr);
+  for (auto& d : slots) {
+    const cudaError_t e = dmalloc(&d, (size_t)ldp * ctx->bs);
+    if (e != cudaSuccess) {  // nothing half-made stays behind: a later call retries
+      for (auto* q : slots) cudaFree(q);
+      return fail(ctx, e == cudaErrorMemoryAllocation ? GWAS_ERR_NOMEM : GWAS_ERR_CUDA,
+                  "packed input slots: %s", cudaGetErrorString(e));
+    }
+  }
+  ctx->ldp = ldp;
+  ctx->dpack = std::move(slots);
   return GWAS_OK;
 }
 
