@@ -52,6 +52,7 @@ struct gwas_ctx {
   double* Xhat = nullptr;      // n_pad x bs: X^ = L^-T X~
   double* What = nullptr;      // n_pad x (q+1): [X^_L | y^]
   double* GH = nullptr;        // (q+1)^2 Gram of What
+  bool adjoint_ready = false;  // the arrays below are made and What / GH hold their values
   double* adj = nullptr;       // per-SNP chi2 (bs), dh (bs), y-weights (bs x p), uT (q), dh/dy staging (1 + n),
                                // the y-gradient's chunk partials (adjoint_dy_chunks(bs) x n)
   ExactProducts* exact = nullptr;   // split precisions: the adjoint's exact products (built on first use)
@@ -240,20 +241,23 @@ int form_inverse(gwas_ctx* ctx, double** out) {
 
 // The adjoint's loop-invariant part: the transpose operator, X^_L and y^, their Gram.
 int ensure_adjoint(gwas_ctx* ctx) {
-  if (ctx->What) return GWAS_OK;
+  if (ctx->adjoint_ready) return GWAS_OK;
   const size_t np = (size_t)ctx->n_pad;
   const int nc = ctx->q + 1;
   int rc0 = ensure_aop_t(ctx);
   if (rc0 != GWAS_OK) return rc0;
-  CK(dmalloc(&ctx->Xhat, sizeof(double) * np * std::max(ctx->bs, nc)));
-  CK(dmalloc(&ctx->What, sizeof(double) * np * nc));
-  CK(dmalloc(&ctx->GH, sizeof(double) * nc * nc));
-  CK(dmalloc(&ctx->adj, sizeof(double) * ((size_t)ctx->bs * (2 + ctx->p) + QMAX + 1 + ctx->n +
-                                           (size_t)adjoint_dy_chunks(ctx->bs) * ctx->n)));
+  // each array once (a failed earlier attempt may have made some of them)
+  if (!ctx->Xhat) CK(dmalloc(&ctx->Xhat, sizeof(double) * np * std::max(ctx->bs, nc)));
+  if (!ctx->What) CK(dmalloc(&ctx->What, sizeof(double) * np * nc));
+  if (!ctx->GH) CK(dmalloc(&ctx->GH, sizeof(double) * nc * nc));
+  if (!ctx->adj)
+    CK(dmalloc(&ctx->adj, sizeof(double) * ((size_t)ctx->bs * (2 + ctx->p) + QMAX + 1 + ctx->n +
+                                             (size_t)adjoint_dy_chunks(ctx->bs) * ctx->n)));
   int rc = solve_f64_cols(ctx, ctx->W, ctx->n_pad, ctx->n_pad, nc, ctx->What, true);
   if (rc != GWAS_OK) return rc;
   CK(launch_gram(ctx->What, ctx->n_pad, ctx->n_pad, nc, ctx->GH, ctx->stream));
   ctx->launches += 1;
+  ctx->adjoint_ready = true;
   return GWAS_OK;
 }
 
