@@ -223,6 +223,47 @@ static cudaError_t launch_cast(int out, const int8_t* X, int64_t ldx, int n, int
   return launch_cast_t<OUT_BF16>(X, ldx, n, n_pad, ncols, shift, xc, counter, s);
 }
 
+// The batch's cast pre-passes in one launch: the columns of every study of a
+// step, one warp per column (the study found from its first column), each
+// cast as cast_shift_reg_kernel casts it; the batch's unit counter zeroed.
+// One launch instead of a memset and a cast per study keeps the gaps between
+// graph nodes out of the step, and the solve follows as its programmatic
+// dependent.
+struct CastJob {
+  const int8_t* X;
+  int64_t ldx;
+  int n, n_pad, col0, ncols;
+  int8_t* shift;
+  void* xc;
+};
+struct CastJobs {
+  CastJob j[MAX_STUDIES];
+  int njobs, total;
+  unsigned int* counter;
+};
+
+template <int OUT, int NV>
+__global__ void __launch_bounds__(256) cast_batch_kernel(const __grid_constant__ CastJobs J) {
+  ptx::griddep_launch();  // the solve kernel may start its set-up
+  if (blockIdx.x == 0 && threadIdx.x == 0) *J.counter = 0;
+  const int g = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+  if (g >= J.total) return;
+  int i = 0;
+  while (i + 1 < J.njobs && g >= J.j[i + 1].col0) ++i;
+  const CastJob& c = J.j[i];
+  cast_column_reg<OUT, NV>(c.X, c.ldx, c.n, c.n_pad, g - c.col0, c.shift, c.xc);
+}
+
+template <int OUT>
+static cudaError_t launch_cast_batch_t(const CastJobs& J, int nmax, cudaStream_t s) {
+  const int grid = (J.total + 7) / 8;
+  if (nmax <= 512 * 20)
+    cast_batch_kernel<OUT, 20><<<grid, 256, 0, s>>>(J);
+  else
+    cast_batch_kernel<OUT, 32><<<grid, 256, 0, s>>>(J);
+  return cudaGetLastError();
+}
+
 // Columns c0.. c0+ncols-1 of the n_pad x n_pad identity as int8, column-major
 // with leading dimension n_pad (the right-hand side that turns the
 // substitution into L^-1).
@@ -931,11 +972,25 @@ cudaError_t batch_launch(TcBatchState* B, TcState* const* ts, cudaStream_t s, in
   TcBatch b;
   memset(&b, 0, sizeof b);
   cudaError_t e;
+  // inverse form with every study at n <= 16384: the casts in one launch, which
+  // also zeroes the counter (the inverse form's tiles use no flags)
+  int nmax = 0;
+  for (int i = 0; i < B->nstudies; ++i)
+    if (B->S[i].ncols > 0) nmax = std::max(nmax, ts[i]->n);
+  const bool one_cast = B->mode == TILES_INVERSE && nmax <= 512 * 32;
+  CastJobs J;
+  memset(&J, 0, sizeof J);
+  J.counter = B->d_counter;
   for (int i = 0; i < B->nstudies; ++i) {
     if (B->S[i].ncols == 0) continue;
     TcState* t = ts[i];
-    if ((e = cudaMemsetAsync(t->sched, 0, 128 + sizeof(int) * (size_t)t->P * B->S[i].C, s)) != cudaSuccess) return e;
-    if (t->mode == TILES_INVERSE) {
+    if (one_cast) {  // cast below, with every study's columns
+      J.j[J.njobs++] = CastJob{B->X[i], B->ldx[i], t->n, t->n_pad, J.total, B->S[i].ncols,
+                               t->center ? t->shift : nullptr, t->xc};
+      J.total += B->S[i].ncols;
+    } else if ((e = cudaMemsetAsync(t->sched, 0, 128 + sizeof(int) * (size_t)t->P * B->S[i].C, s)) != cudaSuccess) {
+      return e;
+    } else if (t->mode == TILES_INVERSE) {
       int8_t* sh = t->center ? t->shift : nullptr;
       ++*launches;
       if ((e = launch_cast(cast_out(t), B->X[i], B->ldx[i], t->n, t->n_pad, B->S[i].ncols, sh, t->xc, nullptr, s)) !=
@@ -960,7 +1015,16 @@ cudaError_t batch_launch(TcBatchState* B, TcState* const* ts, cudaStream_t s, in
     b.maps[i].StHi = t->mStHi;
     b.maps[i].StLo = t->mStLo;
   }
-  if ((e = cudaMemsetAsync(B->d_counter, 0, 128, s)) != cudaSuccess) return e;
+  if (one_cast) {
+    const int out = cast_out(ts[0]);  // one split for the whole batch
+    e = out == OUT_F32   ? launch_cast_batch_t<OUT_F32>(J, nmax, s)
+        : out == OUT_F16 ? launch_cast_batch_t<OUT_F16>(J, nmax, s)
+                         : launch_cast_batch_t<OUT_BF16>(J, nmax, s);
+    if (e != cudaSuccess) return e;
+    ++*launches;
+  } else if ((e = cudaMemsetAsync(B->d_counter, 0, 128, s)) != cudaSuccess) {
+    return e;
+  }
   b.studies = B->d_studies;
   b.order = B->d_order;
   b.nstudies = B->nstudies;
