@@ -498,6 +498,25 @@ __device__ __forceinline__ Unit make_unit(int row, const TcStudy& S) {
   return u;
 }
 
+// The inverse form pairs panels (2u - o, 2u + 1 - o) with o = P mod 2: with an
+// odd panel count the lone panel is panel 0 (one K-block, the partner CTA's
+// half of its one MMA on zero rows) instead of the last one (P K-blocks).  The
+// substitution keeps pairs (2u, 2u + 1): its operator's pair form is built on them.
+__device__ __forceinline__ Unit make_unit_inv(int row, const TcStudy& S) {
+  Unit u;
+  const int o = S.P & 1;
+  if (o && row == 0) {
+    u.k0 = 0;
+    u.paired = false;
+    u.nkb = 1;
+    return u;
+  }
+  u.k0 = 2 * row - o;
+  u.paired = u.k0 + 1 < S.P;
+  u.nkb = u.k0 + (u.paired ? 2 : 1);
+  return u;
+}
+
 // K-block jj of a unit: its kind, the operator block column j, and the
 // operator row panel of this CTA's A rows (-1: zero rows).
 __device__ __forceinline__ Kind kind_of(const Unit& u, uint32_t rank, int jj, int& j, int& arow) {
@@ -1180,7 +1199,7 @@ __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_co
         TcStudy S;
         decode_tile(b, t, sidx, row, c, S);
         const TcMaps& M = b.maps[sidx];
-        const pair2::Unit u = pair2::make_unit(row, S);
+        const pair2::Unit u = pair2::make_unit_inv(row, S);
         const int arow = rank == 0 ? u.k0 : (u.paired ? u.k0 + 1 : -1);  // this CTA's row panel
         const int ycol = c * TN + (int)rank * (TN / 2);                   // this CTA's SNP columns
         bool ok = true;
@@ -1222,7 +1241,7 @@ __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_co
         int sidx, row, c;
         TcStudy S;
         decode_tile(b, t, sidx, row, c, S);
-        const pair2::Unit u = pair2::make_unit(row, S);
+        const pair2::Unit u = pair2::make_unit_inv(row, S);
         const int nkb = u.nkb;
         bool ok = true;
         int a = 0;
@@ -1283,7 +1302,7 @@ __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_co
       int sidx, row, c;
       TcStudy S;
       decode_tile(b, t, sidx, row, c, S);
-      const pair2::Unit u = pair2::make_unit(row, S);
+      const pair2::Unit u = pair2::make_unit_inv(row, S);
       const bool has = leader || u.paired;  // this CTA has a tile
       const int k = u.k0 + (int)rank;
       uint8_t* stg = smem + K::STG_OFF + e * 2 * K::CHUNK_BYTES;  // this warp's 4 KB of staging

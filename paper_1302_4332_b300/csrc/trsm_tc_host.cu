@@ -632,9 +632,13 @@ struct UnitKey {
   int len;
   uint32_t code;
 };
+// The inverse form's units with their K-block counts (the device's
+// pair2::make_unit_inv: with an odd P the lone panel is panel 0).
 static void append_units(std::vector<UnitKey>& v, int si, int P, int C) {
+  const int o = P & 1;
   for (int r = 0; r < (P + 1) / 2; ++r) {
-    const int len = 2 * r + (2 * r + 1 < P ? 2 : 1);
+    const int k0 = (o && r == 0) ? 0 : 2 * r - o;
+    const int len = (o && r == 0) ? 1 : k0 + (k0 + 1 < P ? 2 : 1);
     for (int c = 0; c < C; ++c) v.push_back({len, ((uint32_t)si << 28) | ((uint32_t)r << 14) | (uint32_t)c});
   }
 }
