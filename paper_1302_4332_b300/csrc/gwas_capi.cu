@@ -292,8 +292,12 @@ int ensure_exact_adjoint(gwas_ctx* ctx) {
 }
 
 // X~ = L^-1 X for one block (FP64 or split precision), then reductions + solve.
+// packed: X holds 2-bit packed columns (ldx bytes a column, 16-byte aligned),
+// which only the split inverse form reads as they are (tc::packed_ok).
 int run_block(gwas_ctx* ctx, const void* X, bool int8_input, int64_t ldx, int ncols, double* b, double* se,
-              int* status) {
+              int* status, bool packed = false) {
+  if (packed && !(ctx->tcs && tc::packed_ok(ctx->tcs)))
+    return fail(ctx, GWAS_ERR_ARG, "packed columns go to the split inverse form only");
   const int C64 = (ncols + F64_TN - 1) / F64_TN;
   if (ctx->prec == GWAS_FP64 || !int8_input) {
     CK(cudaMemsetAsync(ctx->sched, 0, sizeof(Sched) + sizeof(int) * (size_t)ctx->P * C64, ctx->stream));
@@ -343,7 +347,7 @@ int run_block(gwas_ctx* ctx, const void* X, bool int8_input, int64_t ldx, int nc
   }
   // split precision: the TMA map of X needs a 16-byte aligned base and leading dimension
   const int8_t* X8 = static_cast<const int8_t*>(X);
-  if ((reinterpret_cast<uintptr_t>(X8) & 15) || (ldx & 15)) {
+  if (!packed && ((reinterpret_cast<uintptr_t>(X8) & 15) || (ldx & 15))) {
     CK(cudaMemcpy2DAsync(ctx->ring[0], (size_t)ctx->n_pad, X8, (size_t)ldx, (size_t)ctx->n, (size_t)ncols,
                          cudaMemcpyDeviceToDevice, ctx->stream));
     X8 = ctx->ring[0];
@@ -353,7 +357,7 @@ int run_block(gwas_ctx* ctx, const void* X, bool int8_input, int64_t ldx, int nc
     StageMark m(ctx, GWAS_STAGE_TRSM, ctx->stream);
     int64_t nl = 0;
     cudaEvent_t k0 = ctx->timing ? pool_event(ctx) : nullptr, k1 = ctx->timing ? pool_event(ctx) : nullptr;
-    cudaError_t e = tc::run_block(ctx->tcs, X8, ldx, ncols, ctx->stream, &nl, k0, k1);
+    cudaError_t e = tc::run_block(ctx->tcs, X8, ldx, ncols, ctx->stream, &nl, k0, k1, packed);
     if (ctx->timing && e == cudaSuccess) {
       ctx->marks.push_back({GWAS_STAGE_SOLVE, k0, k1});
     } else if (ctx->timing) {
@@ -781,6 +785,8 @@ static int stream_impl(gwas_ctx* ctx, const void* host, bool packed, int64_t ldx
   // columns are repacked to the slot's stride by a pitched copy.  Packed
   // columns likewise into a slot of ldp bytes per column.
   const int64_t slot_ld_in = packed ? ctx->ldp : ctx->n_pad;
+  // the split inverse form's cast reads the packed columns themselves (no unpack kernel)
+  const bool fused = packed && ctx->tcs && tc::packed_ok(ctx->tcs);
   const int64_t width = packed ? nb : ctx->n;
   const bool flat = (ldx % 16) == 0 && ldx <= slot_ld_in;
   const int64_t ld_dev = flat ? ldx : slot_ld_in;  // the block's leading dimension on the device
@@ -810,7 +816,7 @@ static int stream_impl(gwas_ctx* ctx, const void* host, bool packed, int64_t ldx
   for (int64_t blk = 0; blk < nblk; ++blk) {
     const int slot = (int)(blk % R), nc = cols_of(blk);
     CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_copied[slot], 0));
-    if (packed) {  // the 2-bit codes into the ring slot as int8
+    if (packed && !fused) {  // the 2-bit codes into the ring slot as int8
       StageMark mk(ctx, GWAS_STAGE_H2D, ctx->stream);
       CK(launch_unpack2(ctx->dpack[slot], ld_dev, ctx->n, nc, ctx->ring[slot], ctx->n_pad, ctx->stream));
       ctx->launches += 1;
@@ -820,8 +826,9 @@ static int stream_impl(gwas_ctx* ctx, const void* host, bool packed, int64_t ldx
     int* ost = ctx->d_status + (size_t)slot * bs;
     // the slot's outputs were copied out R blocks ago (on the result stream)
     if (blk >= R) CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_out[slot], 0));
-    if ((rc = run_block(ctx, ctx->ring[slot], true, packed ? ctx->n_pad : ld_dev, nc, ob, ose, ost)) != GWAS_OK)
-      return rc;
+    rc = fused ? run_block(ctx, ctx->dpack[slot], true, ld_dev, nc, ob, ose, ost, true)
+               : run_block(ctx, ctx->ring[slot], true, packed ? ctx->n_pad : ld_dev, nc, ob, ose, ost);
+    if (rc != GWAS_OK) return rc;
     CK(cudaEventRecord(ctx->ev_free[slot], ctx->stream));
     {  // results out on their own stream, overlapping the next block's solve
     CK(cudaStreamWaitEvent(ctx->out_stream, ctx->ev_free[slot], 0));
@@ -873,6 +880,7 @@ static int solve_file_impl(gwas_ctx* ctx, const char* path, int64_t header_bytes
   // packed columns (2-bit codes, ceil(n/4) bytes) land in a device slot of
   // ldp bytes per column and are unpacked into the ring slot
   const int64_t width = packed ? ((int64_t)ctx->n + 3) / 4 : ctx->n;
+  const bool fused = packed && ctx->tcs && tc::packed_ok(ctx->tcs);  // the cast reads the packed columns
   if (packed) {
     const int r0 = ensure_packed_slots(ctx);
     if (r0 != GWAS_OK) return r0;
@@ -917,7 +925,7 @@ static int solve_file_impl(gwas_ctx* ctx, const char* path, int64_t header_bytes
       }
       CK(cudaEventRecord(ctx->ev_copied[slot], ctx->copy_stream));
       CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_copied[slot], 0));
-      if (packed) {
+      if (packed && !fused) {
         StageMark mk(ctx, GWAS_STAGE_H2D, ctx->stream);
         CK(launch_unpack2(ctx->dpack[slot], ctx->ldp, ctx->n, nc, ctx->ring[slot], ctx->n_pad, ctx->stream));
         ctx->launches += 1;
@@ -925,7 +933,9 @@ static int solve_file_impl(gwas_ctx* ctx, const char* path, int64_t header_bytes
       double* ob = ctx->d_b + (size_t)slot * ctx->t * p * bs;
       double* ose = ctx->d_se + (size_t)slot * p * bs;
       int* ost = ctx->d_status + (size_t)slot * bs;
-      if ((r2 = run_block(ctx, ctx->ring[slot], true, ctx->n_pad, nc, ob, ose, ost)) != GWAS_OK) return r2;
+      r2 = fused ? run_block(ctx, ctx->dpack[slot], true, ctx->ldp, nc, ob, ose, ost, true)
+                 : run_block(ctx, ctx->ring[slot], true, ctx->n_pad, nc, ob, ose, ost);
+      if (r2 != GWAS_OK) return r2;
       CK(cudaEventRecord(ctx->ev_free[slot], ctx->stream));
       {
         StageMark mk(ctx, GWAS_STAGE_D2H, ctx->stream);

@@ -59,7 +59,7 @@ bool pack2_columns(const int8_t* X, int64_t ldx, int n, int c0, int c1, uint8_t*
 // --------------------------------------------------------------- unpacking
 // One thread per 4 packed bytes (16 rows of a column): a 16-byte store of
 // the int8 values.  X rows 16 t .. 16 t + 15 < ceil(n / 16) 16 <= n_pad; rows
-// past n come out 0 (the packed padding), as the slot holds them.
+// past n come out 0, as the slot holds them.
 __global__ void unpack2_kernel(const uint8_t* __restrict__ P, int64_t ldp, int n, int ncols, int8_t* __restrict__ X,
                                int64_t ldx) {
   const int col = blockIdx.y;
@@ -77,6 +77,9 @@ __global__ void unpack2_kernel(const uint8_t* __restrict__ P, int64_t ldp, int n
     const uint32_t b = (v >> (8 * k)) & 0xFFu;  // rows 16g + 4k .. +3
     w[k] = (b & 3u) | ((b & 0xCu) << 6) | ((b & 0x30u) << 12) | ((b & 0xC0u) << 18);
   }
+  if (16 * g + 16 > n)  // rows past n as 0, whatever bits the packed padding holds
+    for (int i = 0; i < 16; ++i)
+      if (16 * g + i >= n) w[i >> 2] &= ~(0xFFu << (8 * (i & 3)));
   *reinterpret_cast<uint4*>(X + (int64_t)col * ldx + 16 * g) = make_uint4(w[0], w[1], w[2], w[3]);
 }
 

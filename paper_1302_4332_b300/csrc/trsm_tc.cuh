@@ -45,7 +45,10 @@ cudaError_t create(TcState** out, Split split, const double* Aop, int n, int n_p
 // inverse form with the sums in its epilogue leaves partials() instead).
 // ev0 / ev1 (optional): recorded on s right before and after the solve kernel.
 cudaError_t run_block(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaStream_t s, int64_t* launches,
-                      cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr);
+                      cudaEvent_t ev0 = nullptr, cudaEvent_t ev1 = nullptr, bool packed = false);
+// run_block takes 2-bit packed columns (packed = true, ldx >= ceil(n/4) bytes a
+// column, 16-byte aligned): the inverse form at n <= 16384, whose cast reads them.
+bool packed_ok(const TcState* t);
 
 // The batching form: one persistent launch over several studies (each with its
 // own operator and buffers; all BF16 or all TF32).  ts[i] solves ncols[i]

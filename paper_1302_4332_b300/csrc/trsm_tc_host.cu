@@ -74,10 +74,24 @@ __device__ __forceinline__ void store_cast16(void* xc, int64_t off, const float 
   }
 }
 
+// 16 rows of a 2-bit packed column (4 bytes, row 4k + i in bits 2i .. 2i+1 of
+// byte k) as the 16 int8 values of an int4.
+__device__ __forceinline__ int4 unpack16(uint32_t p) {
+  uint32_t w[4];
+#pragma unroll
+  for (int k = 0; k < 4; ++k) {
+    const uint32_t b = (p >> (8 * k)) & 0xFFu;
+    w[k] = (b & 3u) | ((b & 0xCu) << 6) | ((b & 0x30u) << 12) | ((b & 0xC0u) << 18);
+  }
+  return make_int4((int)w[0], (int)w[1], (int)w[2], (int)w[3]);
+}
+
 // The same in one read of the column: for n <= 512 * NV each lane holds its
-// NV 16-byte pieces of the column in registers between the sum and the
-// cast (all of them in flight at once).
-template <int OUT, int NV>
+// NV 16-row pieces of the column in registers between the sum and the cast
+// (all of them in flight at once).  PK: the column is 2-bit packed (ldx bytes
+// per column, ceil(n/4) of them used; 4 bytes a piece), as the packed input
+// forms carry hard-called genotypes -- no int8 copy of the block is made.
+template <int OUT, int NV, bool PK = false>
 __device__ __forceinline__ void cast_column_reg(const int8_t* __restrict__ X, int64_t ldx, int n, int n_pad,
                                                 int col, int8_t* __restrict__ shift, void* __restrict__ xc) {
   const int lane = threadIdx.x & 31;
@@ -86,7 +100,22 @@ __device__ __forceinline__ void cast_column_reg(const int8_t* __restrict__ X, in
 #pragma unroll
   for (int j = 0; j < NV; ++j) {
     const int r = j * 512 + lane * 16;
-    if (r + 16 <= n) {
+    if (PK) {
+      const int nb = (n + 3) / 4;  // packed bytes of the column; rows past n are 0 in them
+      const uint8_t* xb = reinterpret_cast<const uint8_t*>(x) + r / 4;
+      uint32_t p = 0;
+      if (r + 16 <= n) {
+        p = __ldg(reinterpret_cast<const uint32_t*>(xb));
+        v[j] = unpack16(p);
+      } else {  // the ragged piece: rows past n as 0 whatever their bits hold
+        for (int k = 0; r / 4 + k < nb && k < 4; ++k) p |= (uint32_t)xb[k] << (8 * k);
+        const int4 q = unpack16(p);
+        uint32_t w[4] = {(uint32_t)q.x, (uint32_t)q.y, (uint32_t)q.z, (uint32_t)q.w};
+        for (int i = 0; i < 16; ++i)
+          if (r + i >= n) w[i >> 2] &= ~(0xFFu << (8 * (i & 3)));
+        v[j] = make_int4((int)w[0], (int)w[1], (int)w[2], (int)w[3]);
+      }
+    } else if (r + 16 <= n) {
       v[j] = __ldg(reinterpret_cast<const int4*>(x + r));
     } else {  // the ragged piece (bytes past n read as 0)
       uint32_t w[4] = {0u, 0u, 0u, 0u};
@@ -127,14 +156,14 @@ __device__ __forceinline__ void cast_column_reg(const int8_t* __restrict__ X, in
 // programmatic dependent, then the sums' kernel as the solve's.  The cast
 // zeroes the solve's unit counter (no stream operation between it and the
 // solve) and writes the cast block and this block's shift slot.
-template <int OUT, int NV>
+template <int OUT, int NV, bool PK = false>
 __global__ void __launch_bounds__(256) cast_shift_reg_kernel(const int8_t* __restrict__ X, int64_t ldx, int n,
                                                              int n_pad, int ncols, int8_t* __restrict__ shift,
                                                              void* __restrict__ xc, unsigned int* counter) {
   ptx::griddep_launch();  // the solve kernel may start its set-up
   if (counter && blockIdx.x == 0 && threadIdx.x == 0) *counter = 0;
   const int col = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-  if (col < ncols) cast_column_reg<OUT, NV>(X, ldx, n, n_pad, col, shift, xc);
+  if (col < ncols) cast_column_reg<OUT, NV, PK>(X, ldx, n, n_pad, col, shift, xc);
 }
 
 // B operand of the inverse form: x'_ri = x_ri - c_i on rows < n and 0 on rows
@@ -205,8 +234,17 @@ __global__ void cast_shift_kernel(const int8_t* __restrict__ X, int64_t ldx, int
 // zero, or null when the caller clears it.
 template <int OUT>
 static cudaError_t launch_cast_t(const int8_t* X, int64_t ldx, int n, int n_pad, int ncols, int8_t* shift, void* xc,
-                                 unsigned int* counter, cudaStream_t s) {
+                                 unsigned int* counter, cudaStream_t s, bool packed = false) {
   const int grid = (ncols + 7) / 8;
+  if (packed) {  // 2-bit packed columns: the register form only
+    if (n <= 512 * 20)
+      cast_shift_reg_kernel<OUT, 20, true><<<grid, 256, 0, s>>>(X, ldx, n, n_pad, ncols, shift, xc, counter);
+    else if (n <= 512 * 32)
+      cast_shift_reg_kernel<OUT, 32, true><<<grid, 256, 0, s>>>(X, ldx, n, n_pad, ncols, shift, xc, counter);
+    else
+      return cudaErrorInvalidValue;
+    return cudaGetLastError();
+  }
   if (n <= 512 * 20)
     cast_shift_reg_kernel<OUT, 20><<<grid, 256, 0, s>>>(X, ldx, n, n_pad, ncols, shift, xc, counter);
   else if (n <= 512 * 32)
@@ -217,10 +255,10 @@ static cudaError_t launch_cast_t(const int8_t* X, int64_t ldx, int n, int n_pad,
 }
 
 static cudaError_t launch_cast(int out, const int8_t* X, int64_t ldx, int n, int n_pad, int ncols, int8_t* shift,
-                               void* xc, unsigned int* counter, cudaStream_t s) {
-  if (out == OUT_F32) return launch_cast_t<OUT_F32>(X, ldx, n, n_pad, ncols, shift, xc, counter, s);
-  if (out == OUT_F16) return launch_cast_t<OUT_F16>(X, ldx, n, n_pad, ncols, shift, xc, counter, s);
-  return launch_cast_t<OUT_BF16>(X, ldx, n, n_pad, ncols, shift, xc, counter, s);
+                               void* xc, unsigned int* counter, cudaStream_t s, bool packed = false) {
+  if (out == OUT_F32) return launch_cast_t<OUT_F32>(X, ldx, n, n_pad, ncols, shift, xc, counter, s, packed);
+  if (out == OUT_F16) return launch_cast_t<OUT_F16>(X, ldx, n, n_pad, ncols, shift, xc, counter, s, packed);
+  return launch_cast_t<OUT_BF16>(X, ldx, n, n_pad, ncols, shift, xc, counter, s, packed);
 }
 
 // The batch's cast pre-passes in one launch: the columns of every study of a
@@ -648,11 +686,12 @@ static void longest_first(std::vector<UnitKey>& v, std::vector<uint32_t>& order)
 }
 
 static int cast_out(const TcState* t) { return t->tf32 ? OUT_F32 : (t->f16 ? OUT_F16 : OUT_BF16); }
+bool packed_ok(const TcState* t);
 
 // Inverse form: the cast block's map (half-width boxes) and the cast
 // pre-pass (with the integer shifts when centering).
 static cudaError_t prepare_cast(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaStream_t s,
-                                int64_t* launches, CUtensorMap* mXcH) {
+                                int64_t* launches, CUtensorMap* mXcH, bool packed = false) {
   const size_t esz = t->tf32 ? 4 : 2;
   const CUtensorMapDataType dt = t->tf32  ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
                                  : t->f16 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT16
@@ -667,16 +706,18 @@ static cudaError_t prepare_cast(TcState* t, const int8_t* X, int64_t ldx, int nc
   }
   int8_t* sh = t->center ? t->shift : nullptr;
   ++*launches;
-  if ((e = launch_cast(cast_out(t), X, ldx, t->n, t->n_pad, ncols, sh, t->xc, t->sched, s)) != cudaSuccess) return e;
+  if ((e = launch_cast(cast_out(t), X, ldx, t->n, t->n_pad, ncols, sh, t->xc, t->sched, s, packed)) != cudaSuccess)
+    return e;
   return cudaGetLastError();
 }
 
 // The study part of one launch: int8 map, cleared flags, integer shifts.
 static cudaError_t prepare_study(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaStream_t s,
                                  int64_t* launches, TcStudy* S, CUtensorMap* mX8, CUtensorMap* mX8H,
-                                 CUtensorMap* mXcH) {
-  if (ncols > t->bs || (reinterpret_cast<uintptr_t>(X) & 15) || (ldx & 15) || ldx < t->n)
+                                 CUtensorMap* mXcH, bool packed = false) {
+  if (ncols > t->bs || (reinterpret_cast<uintptr_t>(X) & 15) || (ldx & 15) || ldx < (packed ? (t->n + 3) / 4 : t->n))
     return cudaErrorInvalidValue;
+  if (packed && !packed_ok(t)) return cudaErrorInvalidValue;
   cudaError_t e;
   if (t->mode != TILES_INVERSE) {
     e = make_map(t->encode, mX8, CU_TENSOR_MAP_DATA_TYPE_UINT8, X, (uint64_t)t->n, (uint64_t)ncols, (uint64_t)ldx, TB,
@@ -694,7 +735,7 @@ static cudaError_t prepare_study(TcState* t, const int8_t* X, int64_t ldx, int n
                                       cudaSuccess)
     return e;
   if (t->mode == TILES_INVERSE) {
-    if ((e = prepare_cast(t, X, ldx, ncols, s, launches, mXcH)) != cudaSuccess) return e;
+    if ((e = prepare_cast(t, X, ldx, ncols, s, launches, mXcH, packed)) != cudaSuccess) return e;
   } else if (t->center) {
     column_shift_kernel<<<(ncols + 7) / 8, 256, 0, s>>>(X, ldx, t->n, ncols, t->shift);
     ++*launches;
@@ -726,13 +767,15 @@ static cudaError_t launch_kernel(bool tf32, TileMode mode, const TcBatch& b, int
   return launch_solve(tf32, mode, b, num_sms, max_clusters, s, f16, stages);
 }
 
+bool packed_ok(const TcState* t) { return t->mode == TILES_INVERSE && t->n <= 512 * 32; }
+
 cudaError_t run_block(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaStream_t s, int64_t* launches,
-                      cudaEvent_t ev0, cudaEvent_t ev1) {
+                      cudaEvent_t ev0, cudaEvent_t ev1, bool packed) {
   if (ncols <= 0) return cudaSuccess;
   TcBatch b;
   memset(&b, 0, sizeof b);
-  cudaError_t e =
-      prepare_study(t, X, ldx, ncols, s, launches, &b.s0, &b.maps[0].X8, &b.maps[0].X8H, &b.maps[0].XcH);
+  cudaError_t e = prepare_study(t, X, ldx, ncols, s, launches, &b.s0, &b.maps[0].X8, &b.maps[0].X8H, &b.maps[0].XcH,
+                                packed);
   if (e != cudaSuccess) return e;
   b.maps[0].Ahi = t->mAhi;
   b.maps[0].Alo = t->mAlo;

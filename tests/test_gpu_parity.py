@@ -170,6 +170,24 @@ def test_stream_packed_input(small_study, prec):
     assert e["b_norm"] <= tol and e["se_rel"] <= tol, e
 
 
+@pytest.mark.parametrize("prec", ("fp64", "f16x2", "bf16x3", "sliced64"))
+def test_stream_packed_ragged_rows_and_padding_bits(prec):
+    """n = 301 (the last packed byte holds one row): packed columns whose
+    padding bits are set (rows past n) give the int8 stream's results bit for
+    bit -- the split inverse form reads the codes in its cast, the other
+    precisions unpack them; rows past n count as 0 either way."""
+    n, m = 301, 300
+    s = gwas_synth.study(n, 4, 600, 0.6, 1.0, seed=9)
+    X = np.asfortranarray(gwas_synth.dosages(n, 0, m, seed=9))
+    P = gw.pack_dosages2(X)
+    P[-1, :] |= 0xFC  # rows 301..303 of the last byte: garbage
+    with gw.GLS(s["Phi"], s["XL"], s["y"], 0.6, 1.0, precision=prec, bs=128) as g:
+        ref = g.solve_stream(X)
+        out = g.solve_stream_packed(P)
+    for a_, b_ in zip(ref, out):
+        assert np.array_equal(a_, b_, equal_nan=True)
+
+
 # ---------------------------------------------------------------- split precision
 TOL_SPLIT = 1e-5
 SPLITS = ("bf16x3", "tf32x3", "f16x2")
