@@ -189,8 +189,10 @@ int gwas_solve_stream(gwas_ctx *ctx, const int8_t *XR_host, int64_t ldx, int64_t
 /* gwas_solve_stream over SNP columns held 2-bit packed in HOST memory (hard
  * calls 0..3, four to a byte, as gwas_pack_dosages2 writes them and as genotype
  * files commonly store them): the host link carries ceil(n/4) bytes per SNP
- * instead of n, and a kernel unpacks each block into the device ring slot.
- * Results are those of gwas_solve_stream on the unpacked int8 columns.
+ * instead of n.  The split inverse form's cast pre-pass reads the codes as
+ * they are (n <= 16384); otherwise a kernel unpacks each block into the
+ * device ring slot first.  Results are those of gwas_solve_stream on the
+ * unpacked int8 columns; bits of rows past n are ignored.
  *   P_host  ceil(n/4) bytes per column, leading dimension ldp >= ceil(n/4)
  * Other arguments, errors and results as gwas_solve_stream.  (Packing inside
  * the stream does not pay on a host whose cores pack more slowly than the
