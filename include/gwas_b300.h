@@ -109,8 +109,8 @@ typedef struct {
                       (2 is not a mode: GWAS_ERR_ARG)
                       GWAS_TILES_PAIR_MMA (3): panels 2u and 2u+1 as one 256-row tensor-core product
                         on the two SMs of a cluster;
-                      GWAS_TILES_INVERSE (4): L^-1 is formed once at gwas_init (on the tensor cores,
-                        TF32x3 substitution of the identity) and split like the block operator; a
+                      GWAS_TILES_INVERSE (4): L^-1 is formed once at gwas_init (the FP64 blocked
+                        solve of the identity, n^3/3 flop) and split like the block operator; a
                         block is then the triangular product L^-1 X_R with no dependency between its
                         tiles (256-row products on 2-SM clusters, longest first).  Costs one
                         n_pad x bs cast copy of the block and, at set-up, up to 16 n_pad^2 bytes of

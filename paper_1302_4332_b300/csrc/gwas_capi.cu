@@ -179,7 +179,9 @@ int check_device_status(gwas_ctx* ctx) {
 }
 
 // out = L^-1 X (upper = false) or L^-T X (upper = true) for FP64 columns, FP64 solve.
-int solve_f64_cols(gwas_ctx* ctx, const double* X, int64_t ldx, int rows, int ncols, double* out, bool upper) {
+// tri_col0 >= 0 (lower): X holds identity columns tri_col0 .. (zero tiles skipped).
+int solve_f64_cols(gwas_ctx* ctx, const double* X, int64_t ldx, int rows, int ncols, double* out, bool upper,
+                   int64_t tri_col0 = -1) {
   for (int c0 = 0; c0 < ncols; c0 += ctx->bs) {
     const int nc = std::min(ctx->bs, ncols - c0);
     const int C64 = (nc + F64_TN - 1) / F64_TN;
@@ -190,6 +192,7 @@ int solve_f64_cols(gwas_ctx* ctx, const double* X, int64_t ldx, int rows, int nc
     a.Xt = out + (int64_t)c0 * ctx->n_pad; a.ldt = ctx->n_pad;
     a.P = ctx->P; a.ncols = nc; a.C = C64;
     a.sched = ctx->sched; a.st = ctx->st;
+    a.tri_col0 = (tri_col0 >= 0 && !upper) ? tri_col0 + c0 : -1;
     CK(launch_trsm_f64(a, false, ctx->stream, ctx->num_sms, upper));
     ctx->launches += 1;
   }
@@ -223,7 +226,7 @@ int form_inverse(gwas_ctx* ctx, double** out) {
       const int ncc = std::min(ctx->bs, n - c0);
       CK(launch_identity_cols(E, n, c0, ncc, ctx->stream));
       ctx->launches += 1;
-      int r = solve_f64_cols(ctx, E, n, n, ncc, ctx->Xt, false);
+      int r = solve_f64_cols(ctx, E, n, n, ncc, ctx->Xt, false, c0);
       if (r == GWAS_OK) r = solve_f64_cols(ctx, ctx->Xt, ctx->n_pad, ctx->n_pad, ncc, W + (size_t)c0 * np, true);
       if (r != GWAS_OK) return r;
     }

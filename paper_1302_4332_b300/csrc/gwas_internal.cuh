@@ -103,6 +103,10 @@ struct TrsmF64Args {
   int C;              // column tiles (of F64_TN)
   Sched* sched;
   DevStatus* st;
+  // >= 0 (lower solve only): X holds identity columns tri_col0 .. tri_col0 + ncols - 1,
+  // so rows above each column strip's first column are zero in X and X~: those
+  // tiles are written as zeros without the solve and later tiles skip them
+  int64_t tri_col0 = -1;
 };
 // upper = true: Xt = L^-T X with Aop the transpose block operator (FP64 input only).
 cudaError_t launch_trsm_f64(const TrsmF64Args& a, bool int8_input, cudaStream_t s, int num_sms,

@@ -53,6 +53,8 @@ constexpr int KC = 16;  // reduction chunk
 // UPPER: the transpose solve X^ = L^-T X with the transpose block operator
 // (row panel k = [D_k^-T at block k | -D_k^-T L_jk^T for j > k]); tiles are
 // handed out from the last row panel up and tile (k, c) walks j = P-1 .. k+1.
+// With identity columns (tri_col0 >= 0, lower) tile (k, c) walks j = jmin ..
+// k-1 only, jmin the panel of the strip's first column; tiles k < jmin are zero.
 template <typename TIn, bool UPPER>
 __global__ void __launch_bounds__(256, 2) trsm_f64_kernel(TrsmF64Args a) {
   __shared__ double As[KC][TB + 1];
@@ -75,7 +77,25 @@ __global__ void __launch_bounds__(256, 2) trsm_f64_kernel(TrsmF64Args a) {
     if (tile >= ntiles) return;
     const int k = UPPER ? a.P - 1 - tile / a.C : tile / a.C, c = tile % a.C;
     const int col0 = c * F64_TN;
-    const int nsteps = UPPER ? a.P - k : k + 1;
+    // identity columns: panels above the strip's first column are zero
+    const int jmin = (!UPPER && a.tri_col0 >= 0) ? (int)((a.tri_col0 + col0) / TB) : 0;
+    if (k < jmin) {  // a zero tile: stored and published without the solve
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int col = col0 + tx + 16 * q;
+        if (col < a.ncols) {
+#pragma unroll
+          for (int r = 0; r < 8; ++r) a.Xt[(int64_t)col * a.ldt + k * TB + ty + 16 * r] = 0.0;
+        }
+      }
+      __syncthreads();
+      if (tid == 0) {
+        __threadfence();
+        st_release(&flags[k * a.C + c], 1);
+      }
+      continue;
+    }
+    const int nsteps = UPPER ? a.P - k : k + 1 - jmin;
 
     double acc[8][4];
 #pragma unroll
@@ -86,7 +106,7 @@ __global__ void __launch_bounds__(256, 2) trsm_f64_kernel(TrsmF64Args a) {
     // j = k first (the diagonal inverse on this tile's own input), then the
     // finished panels, oldest first: 0..k-1 (lower) or P-1..k+1 (upper)
     for (int step = 0; step < nsteps; ++step) {
-      const int j = (step == 0) ? k : (UPPER ? a.P - step : step - 1);
+      const int j = (step == 0) ? k : (UPPER ? a.P - step : jmin + step - 1);
       if (j != k) {
         if (tid == 0) s_ok = wait_flag(&flags[j * a.C + c], a.st) ? 1 : 0;
         __syncthreads();

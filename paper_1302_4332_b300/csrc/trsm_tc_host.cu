@@ -313,39 +313,40 @@ __global__ void identity_i8_kernel(int8_t* __restrict__ I8, int n_pad, int c0, i
   }
 }
 
-// Columns c0.. of L^-1, solved into `xt` (FP32, column-major, leading
+// Columns c0.. of L^-1, solved in FP64 into `xt` (column-major, leading
 // dimension ldt), transposed into the row-major hi/lo pieces of the inverse
-// form's operator.  Entries above the diagonal and in the padding rows and
+// form's operator: hi = v rounded to BF16 / TF32, lo = (v - hi) rounded, both
+// from the FP64 value.  Entries above the diagonal and in the padding rows and
 // columns (index >= n) are set to zero.  32 x 32 tiles through shared memory.
 template <bool TF32>
-__global__ void linv_split_kernel(const float* __restrict__ xt, int64_t ldt, int n, int n_pad, int c0, int ncols,
+__global__ void linv_split_kernel(const double* __restrict__ xt, int64_t ldt, int n, int n_pad, int c0, int ncols,
                                   void* __restrict__ hi, void* __restrict__ lo) {
-  __shared__ float tile[32][33];
+  __shared__ double tile[32][33];
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
   const int q0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int q = q0 + ty + 8 * i;
-    tile[ty + 8 * i][tx] = q < ncols ? xt[(int64_t)q * ldt + r0 + tx] : 0.f;
+    tile[ty + 8 * i][tx] = q < ncols ? xt[(int64_t)q * ldt + r0 + tx] : 0.0;
   }
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int row = r0 + ty + 8 * i, q = q0 + tx, gcol = c0 + q;
     if (q >= ncols) continue;
-    float v = tile[tx][ty + 8 * i];
-    if (row >= n || gcol >= n || gcol > row) v = 0.f;
+    double v = tile[tx][ty + 8 * i];
+    if (row >= n || gcol >= n || gcol > row) v = 0.0;
     const int64_t idx = (int64_t)row * n_pad + gcol;
     if constexpr (TF32) {
       uint32_t hb;
-      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"(v));
+      asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(hb) : "f"((float)v));
       const float h = __uint_as_float(hb);
       static_cast<float*>(hi)[idx] = h;
-      static_cast<float*>(lo)[idx] = v - h;
+      static_cast<float*>(lo)[idx] = (float)(v - (double)h);
     } else {
-      const __nv_bfloat16 h = __float2bfloat16_rn(v);
+      const __nv_bfloat16 h = __float2bfloat16_rn((float)v);
       static_cast<__nv_bfloat16*>(hi)[idx] = h;
-      static_cast<__nv_bfloat16*>(lo)[idx] = __float2bfloat16_rn(v - __bfloat162float(h));
+      static_cast<__nv_bfloat16*>(lo)[idx] = __float2bfloat16_rn((float)(v - (double)__bfloat162float(h)));
     }
   }
 }
@@ -357,36 +358,36 @@ __global__ void linv_split_kernel(const float* __restrict__ xt, int64_t ldt, int
 // |s_r L^-1_rj| < 2^15, inside FP16's range with 11 significant bits for the
 // hi piece and 11 more for the lo piece, both exact FP32 operations), and
 // rscale[r] = 1 / s_r.
-__global__ void linv_rows_kernel(const float* __restrict__ xt, int64_t ldt, int n, int n_pad, int c0, int ncols,
-                                 float* __restrict__ rows32) {
-  __shared__ float tile[32][33];
+__global__ void linv_rows_kernel(const double* __restrict__ xt, int64_t ldt, int n, int n_pad, int c0, int ncols,
+                                 double* __restrict__ rows64) {
+  __shared__ double tile[32][33];
   const int tx = threadIdx.x, ty = threadIdx.y;  // 32 x 8
   const int q0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int q = q0 + ty + 8 * i;
-    tile[ty + 8 * i][tx] = q < ncols ? xt[(int64_t)q * ldt + r0 + tx] : 0.f;
+    tile[ty + 8 * i][tx] = q < ncols ? xt[(int64_t)q * ldt + r0 + tx] : 0.0;
   }
   __syncthreads();
 #pragma unroll
   for (int i = 0; i < 4; ++i) {
     const int row = r0 + ty + 8 * i, q = q0 + tx, gcol = c0 + q;
     if (q >= ncols) continue;
-    float v = tile[tx][ty + 8 * i];
-    if (row >= n || gcol >= n || gcol > row) v = 0.f;
-    rows32[(int64_t)row * n_pad + gcol] = v;
+    double v = tile[tx][ty + 8 * i];
+    if (row >= n || gcol >= n || gcol > row) v = 0.0;
+    rows64[(int64_t)row * n_pad + gcol] = v;
   }
 }
 
 // One block per row of L^-1: its scale, then its FP16 hi/lo pieces.
-__global__ void __launch_bounds__(256) linv_split_f16_kernel(const float* __restrict__ rows32, int n_pad,
+__global__ void __launch_bounds__(256) linv_split_f16_kernel(const double* __restrict__ rows64, int n_pad,
                                                              __half* __restrict__ hi, __half* __restrict__ lo,
                                                              float* __restrict__ rscale) {
   __shared__ float wmax[8];
   const int row = blockIdx.x;
-  const float* src = rows32 + (int64_t)row * n_pad;
+  const double* src = rows64 + (int64_t)row * n_pad;
   float m = 0.f;
-  for (int j = threadIdx.x; j <= row && j < n_pad; j += 256) m = fmaxf(m, fabsf(src[j]));
+  for (int j = threadIdx.x; j <= row && j < n_pad; j += 256) m = fmaxf(m, (float)fabs(src[j]));
 #pragma unroll
   for (int o = 16; o; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) wmax[threadIdx.x >> 5] = m;
@@ -399,10 +400,10 @@ __global__ void __launch_bounds__(256) linv_split_f16_kernel(const float* __rest
   const float sc = ldexpf(1.f, 14 - e);
   if (threadIdx.x == 0) rscale[row] = ldexpf(1.f, e - 14);
   for (int j = threadIdx.x; j < n_pad; j += 256) {
-    const float v = src[j] * sc;
-    const __half h = __float2half_rn(v);
+    const double v = src[j] * (double)sc;  // a power of two: exact
+    const __half h = __float2half_rn((float)v);
     hi[(int64_t)row * n_pad + j] = h;
-    lo[(int64_t)row * n_pad + j] = __float2half_rn(v - __half2float(h));
+    lo[(int64_t)row * n_pad + j] = __float2half_rn((float)(v - (double)__half2float(h)));
   }
 }
 
@@ -820,39 +821,61 @@ cudaError_t run_block(TcState* t, const int8_t* X, int64_t ldx, int ncols, cudaS
 // the tensor cores in TF32x3 (the pair product over Aop, 4096 identity
 // columns per launch, no centering), then transposed and split into the
 // row-major hi/lo pieces of t.  Synchronizes the stream.
+// L^-1 in FP64: the FP64 blocked solve of int8 identity columns, 4096 at a
+// time (tiles above each strip's first column are zero and skipped: n^3/3
+// flop in all), then its hi/lo pieces.
 static cudaError_t build_inverse(TcState* t, const double* Aop, cudaStream_t s, int64_t* launches) {
   const int np = t->n_pad;
   const int bsi = np < 4096 ? np : 4096;
-  TcState* g = nullptr;
-  cudaError_t e = create(&g, SPLIT_TF32, Aop, t->n, np, bsi, t->num_sms, false, t->st, s, launches, 0, TILES_PAIR_MMA);
-  if (e != cudaSuccess) return e;
+  const int C64 = (bsi + F64_TN - 1) / F64_TN;
+  const size_t sched_bytes = sizeof(Sched) + sizeof(int) * (size_t)t->P * C64;
   int8_t* eye = nullptr;
-  float* rows32 = nullptr;  // FP16 pieces: the whole FP32 L^-1, row-major, before the row scales are known
-  e = cudaMalloc(&eye, (size_t)np * bsi);
-  if (e == cudaSuccess && t->f16) e = cudaMalloc(&rows32, sizeof(float) * (size_t)np * np);
+  double* x64 = nullptr;     // the solved columns, n_pad x bsi
+  Sched* sch = nullptr;      // the FP64 solve's counter and tile flags
+  double* rows64 = nullptr;  // FP16 pieces: the whole L^-1, row-major, before the row scales are known
+  cudaError_t e = cudaMalloc(&eye, (size_t)np * bsi);
+  if (e == cudaSuccess) e = cudaMalloc(&x64, sizeof(double) * (size_t)np * bsi);
+  if (e == cudaSuccess) e = cudaMalloc(&sch, sched_bytes);
+  if (e == cudaSuccess && t->f16) e = cudaMalloc(&rows64, sizeof(double) * (size_t)np * np);
   for (int c0 = 0; e == cudaSuccess && c0 < np; c0 += bsi) {
     const int nc = np - c0 < bsi ? np - c0 : bsi;
     identity_i8_kernel<<<1184, 256, 0, s>>>(eye, np, c0, nc);
     ++*launches;
     if ((e = cudaGetLastError()) != cudaSuccess) break;
-    if ((e = run_block(g, eye, np, nc, s, launches)) != cudaSuccess) break;
+    if ((e = cudaMemsetAsync(sch, 0, sched_bytes, s)) != cudaSuccess) break;
+    TrsmF64Args a{};
+    a.Aop = Aop;
+    a.lda = np;
+    a.X = eye;
+    a.ldx = np;
+    a.n = t->n;
+    a.Xt = x64;
+    a.ldt = np;
+    a.P = t->P;
+    a.ncols = nc;
+    a.C = (nc + F64_TN - 1) / F64_TN;
+    a.sched = sch;
+    a.st = t->st;
+    a.tri_col0 = c0;
+    if ((e = launch_trsm_f64(a, true, s, t->num_sms)) != cudaSuccess) break;
+    ++*launches;
     const dim3 grid((nc + 31) / 32, np / 32);
     if (t->f16)
-      linv_rows_kernel<<<grid, dim3(32, 8), 0, s>>>(g->xt32, g->ldt, t->n, np, c0, nc, rows32);
+      linv_rows_kernel<<<grid, dim3(32, 8), 0, s>>>(x64, np, t->n, np, c0, nc, rows64);
     else if (t->tf32)
-      linv_split_kernel<true><<<grid, dim3(32, 8), 0, s>>>(g->xt32, g->ldt, t->n, np, c0, nc, t->ahi, t->alo);
+      linv_split_kernel<true><<<grid, dim3(32, 8), 0, s>>>(x64, np, t->n, np, c0, nc, t->ahi, t->alo);
     else
-      linv_split_kernel<false><<<grid, dim3(32, 8), 0, s>>>(g->xt32, g->ldt, t->n, np, c0, nc, t->ahi, t->alo);
+      linv_split_kernel<false><<<grid, dim3(32, 8), 0, s>>>(x64, np, t->n, np, c0, nc, t->ahi, t->alo);
     ++*launches;
     e = cudaGetLastError();
   }
   if (e == cudaSuccess && t->f16) {
-    linv_split_f16_kernel<<<np, 256, 0, s>>>(rows32, np, static_cast<__half*>(t->ahi), static_cast<__half*>(t->alo),
+    linv_split_f16_kernel<<<np, 256, 0, s>>>(rows64, np, static_cast<__half*>(t->ahi), static_cast<__half*>(t->alo),
                                               t->rscale);
     ++*launches;
     e = cudaGetLastError();
   }
-  const cudaError_t es = cudaStreamSynchronize(s);  // before g's buffers go
+  const cudaError_t es = cudaStreamSynchronize(s);  // before the buffers go
   if (e == cudaSuccess) e = es;
   if (e == cudaSuccess && t->st) {
     DevStatus h;
@@ -860,8 +883,9 @@ static cudaError_t build_inverse(TcState* t, const double* Aop, cudaStream_t s, 
       e = cudaErrorLaunchTimeout;  // a bounded wait of the solve expired
   }
   cudaFree(eye);
-  cudaFree(rows32);
-  destroy(g);
+  cudaFree(x64);
+  cudaFree(sch);
+  cudaFree(rows64);
   return e;
 }
 
