@@ -46,7 +46,7 @@ UNIT = "SNPs/s"
 WORKLOAD = "n10k_p4_m1M_int8"
 SPLIT_PATHS = ("bf16x3", "tf32x3", "f16x2")
 SLICED_SLABS = 5  # the sliced path's 10-bit slices of M^-1's triangle
-E2E_REPEATS = 4  # the end-to-end step streams the resident blocks this many times over
+E2E_REPEATS = 8  # the end-to-end step streams the resident blocks this many times over (64 blocks a call)
 STRIP_GROUP = 0  # tile order of the split paths: strips per group (0 = all)
 N_RESIDENT_BLOCKS = 8
 
