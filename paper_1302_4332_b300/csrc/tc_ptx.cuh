@@ -384,7 +384,7 @@ __host__ __device__ constexpr uint32_t idesc_f32acc_f16(int M, int N) {
 }
 
 // Barrier over `count` threads that also ANDs a predicate across them: every
-// thread of the group gets the same verdict, so a group never splits between
+// thread of the group gets the same outcome, so a group never splits between
 // "continue" and "give up" (which would leave the rest in a later barrier).
 __device__ __forceinline__ bool group_and(int id, int count, bool v) {
   uint32_t r;
