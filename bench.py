@@ -758,16 +758,19 @@ def cpu_baseline(w, s, X_sample, target_s=12.0):
     t0 = time.time()
     L = oracle.potrf(oracle.form_m(s["Phi"], w["h"], w["sigma2"]))
     chol_s = time.time() - t0
+    # calibrate on one group of 16 SNPs per thread (the oracle's unit of parallel
+    # work), then time a whole number of such rounds lasting about target_s
+    cores = oracle.num_threads()
+    grp = 16 * cores
     t1 = time.time()
-    oracle.gls(L, s["XL"], s["y"], X_sample[:, :16])
-    rate = 16 / max(time.time() - t1, 1e-9)
-    m = int(min(X_sample.shape[1], max(32, rate * target_s)))
-    m -= m % 16 if m > 16 else 0
+    oracle.gls(L, s["XL"], s["y"], X_sample[:, :grp])
+    rate = grp / max(time.time() - t1, 1e-9)
+    m = int(min(X_sample.shape[1], max(grp, rate * target_s)))
+    m -= m % grp if m > grp else 0
     t2 = time.time()
     r, se, _, st = oracle.gls(L, s["XL"], s["y"], X_sample[:, :m])
     dt = time.time() - t2
     # the same oracle on one core, on the first 16 SNPs of the sample
-    cores = oracle.num_threads()
     oracle.set_num_threads(1)
     try:
         t3 = time.time()
