@@ -938,9 +938,11 @@ def run_reference(args, world):
     w = workload(args)
     n, p, bs = w["n"], w["p"], w["bs"]
     s = gwas_synth.study(n, p, w["k"], w["h"], w["sigma2"])
-    # the oracle parallelises over groups of 16 SNPs (one L stream per group): one group per thread
+    # the oracle parallelises over groups of 16 SNPs (one L stream per group): eight rounds of one
+    # group per thread a step -- each call also solves X~_L and y~ (~0.34 s at n = 1e4, one
+    # thread), so a single round per call measured ~40 % below the steady rate, eight ~9 %
     threads = oracle.num_threads()
-    per_step = 16 * threads * (1 if n >= 5000 else 8)
+    per_step = 16 * threads * (8 if n >= 5000 else 64)
     X = gwas_synth.dosages(n, 0, per_step * (args.warmup + args.steps))
     L = oracle.potrf(oracle.form_m(s["Phi"], w["h"], w["sigma2"]))
     for i in range(args.warmup):
