@@ -743,6 +743,39 @@ def measure_disk_tier(args, out):
             read_gbs=per * sum(STUDY_SIZES) / t_run / 1e9, file_write_gbs=per * sum(STUDY_SIZES) / write_s / 1e9,
             page_cache="dropped before the run (fsync + POSIX_FADV_DONTNEED); reads through the page cache",
             all_finite=bool(all(np.isfinite(o[0][:, o[2] == 0]).all() for o in outs)))
+        for pth in paths:
+            os.remove(pth)
+        # the batching workload at its full 2,000,000 SNPs per study, from 2-bit packed files
+        # (a quarter of the int8 bytes: ~33.5 GB where int8 files need 134 GB)
+        nbp_all = sum((ni + 3) // 4 for ni in STUDY_SIZES)
+        per_p = min(2_000_000, int(0.8 * shutil.disk_usage(root).free // nbp_all // cols) * cols)
+        nblk_p = -(-per_p // cols)
+        ppaths = []
+        t0 = time.perf_counter()
+        for i, ni in enumerate(STUDY_SIZES):
+            blk = gw.pack_dosages2(gwas_synth.dosages(ni, 0, cols, study=i))
+            ppaths.append(os.path.join(root, f"study{i}.2bit"))
+            _write_repeated(ppaths[-1], np.ascontiguousarray(blk.T).tobytes(), nblk_p)
+        writep_s = time.perf_counter() - t0
+        for pth in ppaths:
+            _drop_cached(pth)
+        with gw.GLSBatch(gls) as B:
+            t1 = time.perf_counter()
+            outs_p = B.solve_files(ppaths, [per_p] * len(ppaths), cols, packed=True)
+            tp_run = time.perf_counter() - t1
+        k = min(per, per_p)  # the columns both runs solved (the same repeated block)
+        same = all(np.array_equal(a[0][:, :k], q[0][:, :k]) and np.array_equal(a[1][:, :k], q[1][:, :k])
+                   and np.array_equal(a[2][:k], q[2][:k]) for a, q in zip(outs, outs_p))
+        res["batch_8_studies_from_disk_packed"] = dict(
+            workload="8 studies n=" + ",".join(map(str, STUDY_SIZES)) + f", p=4, bf16x3, {per_p} SNPs per study "
+                     f"({per_p / 2e6:.2f} of the 2,000,000 the batching workload names; "
+                     f"{per_p * nbp_all / 1e9:.1f} GB of 2-bit packed files on the local disk)",
+            snps=per_p * len(ppaths), seconds=tp_run, snps_per_s=per_p * len(ppaths) / tp_run,
+            read_gbs=per_p * nbp_all / tp_run / 1e9, file_write_gbs=per_p * nbp_all / writep_s / 1e9,
+            page_cache="dropped before the run (fsync + POSIX_FADV_DONTNEED); reads through the page cache",
+            results_equal_int8_files_on_common_columns=bool(same),
+            all_finite=bool(all(np.isfinite(o[0][:, o[2] == 0]).all() for o in outs_p)))
+        del outs, outs_p
         for g in gls:
             g.close()
     finally:

@@ -344,6 +344,16 @@ int gwas_batch_autotune(gwas_batch *B, int reps, int *cols_out, int *order_out, 
 int gwas_batch_solve_files(gwas_batch *B, const char *const *paths, const int64_t *header_bytes, const int64_t *ldx,
                            const int64_t *col0, const int64_t *m, int cols, double *const *b_host,
                            double *const *se_host, int *const *status_host);
+/* The same over files of 2-bit packed columns (gwas_pack_dosages2's encoding: ceil(n_i/4) bytes a
+ * column, leading dimension ldp[i] >= ceil(n_i/4) bytes after header_bytes[i]): a quarter of the
+ * int8 file's bytes from disk and over the host link; each step's packed blocks are copied into a
+ * device staging area (ceil(n_i/4) rounded up to 16 bytes x bs per study, allocated on first use)
+ * and expanded into the batch's int8 slots on the GPU before the replay, so the results equal
+ * gwas_batch_solve_files on the int8 file bit for bit.  Bits of rows past n_i are ignored.
+ * Errors: those of gwas_batch_solve_files; GWAS_ERR_ARG also for ldp[i] < ceil(n_i/4). */
+int gwas_batch_solve_files_packed(gwas_batch *B, const char *const *paths, const int64_t *header_bytes,
+                                  const int64_t *ldp, const int64_t *col0, const int64_t *m, int cols,
+                                  double *const *b_host, double *const *se_host, int *const *status_host);
 int64_t gwas_batch_kernel_launches(const gwas_batch *B);
 const char *gwas_batch_last_error_detail(const gwas_batch *B);
 void gwas_batch_destroy(gwas_batch *B);

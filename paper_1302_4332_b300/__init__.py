@@ -43,7 +43,7 @@ EXPORTS = (
     "gwas_timing_enable", "gwas_timing_read", "gwas_solve_block_static", "gwas_adjoint_block",
     "gwas_reml_eval", "gwas_reml_fit", "gwas_batch_create", "gwas_batch_solve", "gwas_batch_synchronize",
     "gwas_batch_set_order", "gwas_batch_autotune", "gwas_batch_autotune_ex", "gwas_batch_solve_k",
-    "gwas_batch_solve_files", "gwas_batch_kernel_launches",
+    "gwas_batch_solve_files", "gwas_batch_solve_files_packed", "gwas_batch_kernel_launches",
     "gwas_batch_last_error_detail",
     "gwas_batch_destroy", "gwas_solve_file", "gwas_solve_file_out", "gwas_reader_open", "gwas_reader_next",
     "gwas_reader_release", "gwas_reader_error_detail", "gwas_reader_close", "gwas_check_timeout",
@@ -160,6 +160,8 @@ def load(path: str | None = None):
     lib.gwas_batch_solve_files.argtypes = [vp, P(ctypes.c_char_p), P(i64), P(i64), P(i64), P(i64), c_int, P(vp),
                                            P(vp), P(vp)]
     lib.gwas_batch_solve_files.restype = c_int
+    lib.gwas_batch_solve_files_packed.argtypes = lib.gwas_batch_solve_files.argtypes
+    lib.gwas_batch_solve_files_packed.restype = c_int
     lib.gwas_batch_kernel_launches.argtypes = [vp]
     lib.gwas_batch_kernel_launches.restype = i64
     lib.gwas_batch_last_error_detail.argtypes = [vp]
@@ -594,20 +596,23 @@ class GLSBatch:
         if rc != GWAS_OK:
             raise GwasError(rc, (load().gwas_batch_last_error_detail(self._B) or b"").decode())
 
-    def solve_files(self, paths, m, cols: int, ldx=None, col0=None, header_bytes=None):
+    def solve_files(self, paths, m, cols: int, ldx=None, col0=None, header_bytes=None, packed=False):
         """Out of core: study i's columns col0[i] .. col0[i]+m[i]-1 of the n_i x M int8
         column-major file paths[i] (leading dimension ldx[i] bytes, default n_i, after
         header_bytes[i]), streamed disk -> pinned host -> batched solves of `cols`
-        columns per study per step.  Returns a list of (b, se, status) per study."""
+        columns per study per step.  packed=True: the files hold 2-bit packed columns
+        (pack_dosages2's encoding; ldx default ceil(n_i/4)), expanded on the GPU.
+        Returns a list of (b, se, status) per study."""
         ns = len(self.studies)
         m = [int(v) for v in m]
-        ldx = [int(v) for v in (ldx or [g.n for g in self.studies])]
+        ldx = [int(v) for v in (ldx or [(g.n + 3) // 4 if packed else g.n for g in self.studies])]
         col0 = [int(v) for v in (col0 or [0] * ns)]
         header_bytes = [int(v) for v in (header_bytes or [0] * ns)]
         outs = [(np.empty((g.p, mi), order="F"), np.empty((g.p, mi), order="F"), np.empty(mi, dtype=np.int32))
                 for g, mi in zip(self.studies, m)]
         arr = lambda t, v: (t * ns)(*v)
-        rc = load().gwas_batch_solve_files(
+        fn = load().gwas_batch_solve_files_packed if packed else load().gwas_batch_solve_files
+        rc = fn(
             self._B, arr(ctypes.c_char_p, [os.fsencode(p) for p in paths]), arr(ctypes.c_int64, header_bytes),
             arr(ctypes.c_int64, ldx), arr(ctypes.c_int64, col0), arr(ctypes.c_int64, m), int(cols),
             arr(ctypes.c_void_p, [o[0].ctypes.data for o in outs]), arr(ctypes.c_void_p, [o[1].ctypes.data for o in outs]),

@@ -1360,6 +1360,10 @@ struct gwas_batch {
   std::vector<tc::TcBatchState*> tb;  // one planned launch per step of a replay
   // device slots of step j, study i at [j * ns + i]: n_pad x bs int8 input, outputs
   std::vector<int8_t*> slot;
+  // device staging of 2-bit packed host columns, [j * ns + i], allocated on
+  // first use: ceil(n_i / 4) rounded up to 16 bytes per column (pk_ld)
+  std::vector<uint8_t*> pk;
+  std::vector<int64_t> pk_ld;
   std::vector<double*> d_b, d_se;
   std::vector<int*> d_st;
   int ksteps = 0;  // steps with slots and a launch state
@@ -1410,6 +1414,7 @@ void batch_free(gwas_batch* B) {
   if (B->stream) cudaStreamSynchronize(B->stream);
   drop_graph(B);
   for (auto* p : B->slot) cudaFree(p);
+  for (auto* p : B->pk) cudaFree(p);
   for (auto* p : B->d_b) cudaFree(p);
   for (auto* p : B->d_se) cudaFree(p);
   for (auto* p : B->d_st) cudaFree(p);
@@ -1508,30 +1513,73 @@ int batch_capture(gwas_batch* B, const std::vector<int>& cols, int k, int order,
   return GWAS_OK;
 }
 
+// Device staging for the packed columns of steps 0 .. k-1 (nothing half-made
+// stays behind on failure: a later call retries).
+int ensure_pack_staging(gwas_batch* B, int k) {
+  const int need = k * B->ns;
+  if ((int)B->pk.size() >= need) return GWAS_OK;
+  std::vector<uint8_t*> add;
+  std::vector<int64_t> add_ld;
+  for (int o = (int)B->pk.size(); o < need; ++o) {
+    const gwas_ctx* c = B->ctx[o % B->ns];
+    const int64_t ld = (((int64_t)c->n + 3) / 4 + 15) / 16 * 16;
+    uint8_t* d = nullptr;
+    const cudaError_t e = dmalloc(&d, (size_t)ld * c->bs);
+    if (e != cudaSuccess) {
+      for (auto* q : add) cudaFree(q);
+      return bfail(B, e == cudaErrorMemoryAllocation ? GWAS_ERR_NOMEM : GWAS_ERR_CUDA, "packed staging", e);
+    }
+    add.push_back(d);
+    add_ld.push_back(ld);
+  }
+  B->pk.insert(B->pk.end(), add.begin(), add.end());
+  B->pk_ld.insert(B->pk_ld.end(), add_ld.begin(), add_ld.end());
+  return GWAS_OK;
+}
+
 // k blocks per study through one graph replay: inputs into the slots,
 // the replay (recaptured when the plan changed), results out.  Pointer
 // arrays are indexed [j * ns + i]; host arrays make the call synchronous.
-int batch_step(gwas_batch* B, int k, const int8_t* const* XR, const int64_t* ldx, const int* ncols,
-               double* const* b, double* const* se, int* const* status) {
+// packed: XR holds 2-bit packed columns (ldx bytes per column, at least
+// ceil(n_i / 4)), copied into the staging (host input) and unpacked into the
+// int8 slots on the GPU.
+int batch_step(gwas_batch* B, int k, const void* const* XR, const int64_t* ldx, const int* ncols,
+               double* const* b, double* const* se, int* const* status, bool packed = false) {
   const int ns = B->ns;
   std::vector<int> cols(k * ns);
   for (int o = 0; o < k * ns; ++o) {
     gwas_ctx* c = B->ctx[o % ns];
-    if (ncols[o] < 0 || ncols[o] > c->bs || (ncols[o] > 0 && (!XR[o] || !b[o] || ldx[o] < c->n)))
+    const int64_t width = packed ? ((int64_t)c->n + 3) / 4 : c->n;
+    if (ncols[o] < 0 || ncols[o] > c->bs || (ncols[o] > 0 && (!XR[o] || !b[o] || ldx[o] < width)))
       return bfail(B, GWAS_ERR_ARG, "bad arguments to a batch solve");
     cols[o] = ncols[o];
   }
   int rc = ensure_steps(B, k, false);
   if (rc != GWAS_OK) return rc;
+  if (packed && (rc = ensure_pack_staging(B, k)) != GWAS_OK) return rc;
   bool any_host = false;
   for (int o = 0; o < k * ns; ++o) {
     if (cols[o] == 0) continue;
     gwas_ctx* c = B->ctx[o % ns];
     const bool dev_in = is_device_ptr(XR[o]);
     any_host |= !dev_in;
-    BCK(cudaMemcpy2DAsync(B->slot[o], (size_t)c->n_pad, XR[o], (size_t)ldx[o], (size_t)c->n, (size_t)cols[o],
-                          dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, B->stream),
-        "input copy");
+    if (packed) {
+      const uint8_t* src = static_cast<const uint8_t*>(XR[o]);
+      int64_t ld = ldx[o];
+      if (!dev_in) {
+        BCK(cudaMemcpy2DAsync(B->pk[o], (size_t)B->pk_ld[o], src, (size_t)ldx[o], (size_t)((c->n + 3) / 4),
+                              (size_t)cols[o], cudaMemcpyHostToDevice, B->stream),
+            "packed input copy");
+        src = B->pk[o];
+        ld = B->pk_ld[o];
+      }
+      BCK(launch_unpack2(src, ld, c->n, cols[o], B->slot[o], c->n_pad, B->stream), "unpack");
+      B->launches += 1;
+    } else {
+      BCK(cudaMemcpy2DAsync(B->slot[o], (size_t)c->n_pad, XR[o], (size_t)ldx[o], (size_t)c->n, (size_t)cols[o],
+                            dev_in ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, B->stream),
+          "input copy");
+    }
   }
   if (!B->exec || cols != B->planned_cols || B->order_mode != B->planned_order ||
       B->strip_group != B->planned_group || B->stages != B->planned_stages || B->use_alt != B->planned_alt) {
@@ -1636,7 +1684,7 @@ int gwas_batch_solve(gwas_batch* B, const int8_t* const* XR, const int64_t* ldx,
   if (!B || !XR || !ldx || !ncols || !b) return GWAS_ERR_ARG;
   DeviceScope dscope_(B->dev);
   BCK(dscope_.status(), "set device");
-  return batch_step(B, 1, XR, ldx, ncols, b, se, status);
+  return batch_step(B, 1, reinterpret_cast<const void* const*>(XR), ldx, ncols, b, se, status);
 }
 
 int gwas_batch_solve_k(gwas_batch* B, int k, const int8_t* const* XR, const int64_t* ldx, const int* ncols,
@@ -1644,7 +1692,7 @@ int gwas_batch_solve_k(gwas_batch* B, int k, const int8_t* const* XR, const int6
   if (!B || k < 1 || k > GWAS_BATCH_MAX_STEPS || !XR || !ldx || !ncols || !b) return GWAS_ERR_ARG;
   DeviceScope dscope_(B->dev);
   BCK(dscope_.status(), "set device");
-  return batch_step(B, k, XR, ldx, ncols, b, se, status);
+  return batch_step(B, k, reinterpret_cast<const void* const*>(XR), ldx, ncols, b, se, status);
 }
 
 int gwas_batch_synchronize(gwas_batch* B) {
@@ -1753,7 +1801,7 @@ int gwas_batch_autotune_ex(gwas_batch* B, int reps, gwas_batch_tuning* out) {
           B->strip_group = group;
           if ((r = ensure_steps(B, 1, false)) != GWAS_OK) return r;
           std::vector<int> cols(ns, cc);
-          std::vector<const int8_t*> x(src.begin(), src.end());
+          std::vector<const void*> x(src.begin(), src.end());
           if ((r = batch_step(B, 1, x.data(), ld.data(), cols.data(), ob.data(), os.data(), ost.data())) != GWAS_OK)
             return r;  // warm-up (and capture)
           BCK(cudaEventRecord(e0, B->stream), "event");
@@ -1800,14 +1848,18 @@ int gwas_batch_autotune_ex(gwas_batch* B, int reps, gwas_batch_tuning* out) {
   return rc;
 }
 
-int gwas_batch_solve_files(gwas_batch* B, const char* const* paths, const int64_t* header_bytes, const int64_t* ldx,
-                           const int64_t* col0, const int64_t* m, int cols, double* const* b_host,
-                           double* const* se_host, int* const* status_host) {
+}  // extern "C"
+
+// The batch over files of int8 or 2-bit packed columns (ldx bytes per column).
+static int batch_files_impl(gwas_batch* B, const char* const* paths, const int64_t* header_bytes, const int64_t* ldx,
+                            const int64_t* col0, const int64_t* m, int cols, double* const* b_host,
+                            double* const* se_host, int* const* status_host, bool packed) {
   if (!B || !paths || !header_bytes || !ldx || !col0 || !m || !b_host || cols < 1) return GWAS_ERR_ARG;
   const int ns = B->ns;
   for (int i = 0; i < ns; ++i) {
     const gwas_ctx* c = B->ctx[i];
-    if (!paths[i] || header_bytes[i] < 0 || ldx[i] < c->n || col0[i] < 0 || m[i] < 0 || cols > c->bs ||
+    const int64_t width = packed ? ((int64_t)c->n + 3) / 4 : c->n;
+    if (!paths[i] || header_bytes[i] < 0 || ldx[i] < width || col0[i] < 0 || m[i] < 0 || cols > c->bs ||
         (m[i] > 0 && !b_host[i]))
       return bfail(B, GWAS_ERR_ARG, "bad arguments to gwas_batch_solve_files");
   }
@@ -1847,7 +1899,7 @@ int gwas_batch_solve_files(gwas_batch* B, const char* const* paths, const int64_
       return bfail(B, rc, "cannot open a study's dosage file");
     }
   }
-  std::vector<const int8_t*> xr(ns, nullptr);
+  std::vector<const void*> xr(ns, nullptr);
   std::vector<int> nc(ns, 0);
   std::vector<double*> bo(ns, nullptr), so(ns, nullptr);
   std::vector<int*> sto(ns, nullptr);
@@ -1865,19 +1917,33 @@ int gwas_batch_solve_files(gwas_batch* B, const char* const* paths, const int64_
         break;
       }
       const int p = B->ctx[i]->p;
-      xr[i] = static_cast<const int8_t*>(hb);
+      xr[i] = hb;
       bo[i] = b_host[i] + k * cols * p;
       so[i] = (se_host && se_host[i]) ? se_host[i] + k * cols * p : nullptr;
       sto[i] = (status_host && status_host[i]) ? status_host[i] + k * cols : nullptr;
     }
     if (rc != GWAS_OK) break;
     // host inputs and outputs: returns once the step's results are in host memory
-    rc = gwas_batch_solve(B, xr.data(), ldx, nc.data(), bo.data(), so.data(), sto.data());
+    rc = batch_step(B, 1, xr.data(), ldx, nc.data(), bo.data(), so.data(), sto.data(), packed);
     for (int i = 0; i < ns; ++i)
       if (nc[i] > 0) gwas_reader_release(rd[i]);
   }
   close_all();
   return rc;
+}
+
+extern "C" {
+
+int gwas_batch_solve_files(gwas_batch* B, const char* const* paths, const int64_t* header_bytes, const int64_t* ldx,
+                           const int64_t* col0, const int64_t* m, int cols, double* const* b_host,
+                           double* const* se_host, int* const* status_host) {
+  return batch_files_impl(B, paths, header_bytes, ldx, col0, m, cols, b_host, se_host, status_host, false);
+}
+
+int gwas_batch_solve_files_packed(gwas_batch* B, const char* const* paths, const int64_t* header_bytes,
+                                  const int64_t* ldp, const int64_t* col0, const int64_t* m, int cols,
+                                  double* const* b_host, double* const* se_host, int* const* status_host) {
+  return batch_files_impl(B, paths, header_bytes, ldp, col0, m, cols, b_host, se_host, status_host, true);
 }
 
 int64_t gwas_batch_kernel_launches(const gwas_batch* B) { return B ? B->launches : 0; }

@@ -207,3 +207,61 @@ def test_batch_solve_files_matches_in_memory(tmp_path):
     finally:
         for g in gls:
             g.close()
+
+
+def test_batch_solve_files_packed_equals_int8_files(tmp_path):
+    """The batch over files of 2-bit packed columns (own leading dimensions and
+    headers, junk in the padding bits past n): every study's results equal the
+    int8 files' bit for bit and the oracle on a sample; a leading dimension
+    below ceil(n/4) is refused, a short file is an IO error."""
+    studies = _studies("f16x2")
+    gls = [g for _, g in studies]
+    cols, ms = 256, (700, 1000, 300, 513)
+    p8, pp, ld8, ldp, heads, Xs = [], [], [], [], [], []
+    rng = np.random.default_rng(4)
+    for i, ((s, _), m) in enumerate(zip(studies, ms)):
+        n = s["n"]
+        X = gwas_synth.dosages(n, 0, m, seed=32, study=i)
+        X[::2, 5] = 3  # the largest hard call
+        X[:, 6] = 1  # a monomorphic SNP: singular, NaN outputs
+        head = 8 * i + 3
+        raw = np.ascontiguousarray(X.T)
+        P = gw.pack_dosages2(X)  # ceil(n/4) x m
+        nb = (n + 3) // 4
+        lp = nb + 1 + i
+        rawp = rng.integers(0, 256, size=(m, lp), dtype=np.uint8)  # junk beyond each column's bytes
+        rawp[:, :nb] = P.T
+        if n % 4:  # junk in the bits of rows past n in each column's last byte
+            keep = (1 << (2 * (n % 4))) - 1
+            rawp[:, nb - 1] = (rawp[:, nb - 1] & keep) | (rng.integers(0, 256, size=m, dtype=np.uint8) & ~np.uint8(keep))
+        for lst, data, tag in ((p8, raw, "bin"), (pp, rawp, "2bit")):
+            path = tmp_path / f"study{i}.{tag}"
+            with open(path, "wb") as f:
+                f.write(b"\xa5" * head)
+                f.write(data.tobytes())
+            lst.append(str(path))
+        ld8.append(n); ldp.append(lp); heads.append(head); Xs.append(X)
+    try:
+        with gw.GLSBatch(gls) as B:
+            o8 = B.solve_files(p8, ms, cols, ldx=ld8, header_bytes=heads)
+            op = B.solve_files(pp, ms, cols, ldx=ldp, header_bytes=heads, packed=True)
+            for i, (a, q) in enumerate(zip(o8, op)):
+                assert all(np.array_equal(u, v, equal_nan=True) for u, v in zip(a, q)), i
+                assert a[2][6] == 1 and np.isnan(q[0][:, 6]).all()
+            for i, ((s, _), X, (b, se, st)) in enumerate(zip(studies, Xs, op)):
+                L = oracle.potrf(oracle.form_m(s["Phi"], 0.5, 1.0))
+                pick = np.r_[np.arange(0, X.shape[1], 29), X.shape[1] - 1]
+                r, se_o, _, st_o = oracle.gls(L, s["XL"], s["y"], X[:, pick])
+                e = compare(b[:, pick], se[:, pick], st[pick], r, se_o, st_o)
+                assert e["b_norm"] <= 1e-5 and e["se_rel"] <= 1e-5, (i, e)
+            bad = list(ldp)
+            bad[2] = (NS[2] + 3) // 4 - 1
+            with pytest.raises(gw.GwasError) as err:
+                B.solve_files(pp, ms, cols, ldx=bad, header_bytes=heads, packed=True)
+            assert err.value.name == "GWAS_ERR_ARG"
+            with pytest.raises(gw.GwasError) as err:
+                B.solve_files(pp, [m + 300 for m in ms], cols, ldx=ldp, header_bytes=heads, packed=True)
+            assert err.value.name == "GWAS_ERR_IO"
+    finally:
+        for g in gls:
+            g.close()
