@@ -45,7 +45,7 @@ METRIC = "GLS solves/sec (SNPs/s) at n=10k,p=4: split-prec vs FP64 path, % roofl
 UNIT = "SNPs/s"
 WORKLOAD = "n10k_p4_m1M_int8"
 SPLIT_PATHS = ("bf16x3", "tf32x3", "f16x2")
-SLICED_SLABS = 5  # the sliced path's 10-bit slices of M^-1's triangle
+SLICED_SLABS = 4  # the sliced path's 11-bit slices of M^-1's triangle
 E2E_REPEATS = 8  # the end-to-end step streams the resident blocks this many times over (64 blocks a call)
 STRIP_GROUP = 0  # tile order of the split paths: strips per group (0 = all)
 N_RESIDENT_BLOCKS = 8
@@ -905,7 +905,9 @@ def main():
             storage = {"error": repr(e)}
 
     split = [pp for pp in SPLIT_PATHS if pp in results]
-    head = max(split, key=lambda pp: results[pp]["snps_per_s"]) if split else "fp64"
+    # the headline: the fastest split path; else the FP64 path; else whatever ran
+    head = max(split, key=lambda pp: results[pp]["snps_per_s"]) if split else ("fp64" if "fp64" in results
+                                                                             else next(iter(results)))
     hr = results[head]
     paths_out = {}
     for path, res in results.items():
@@ -945,7 +947,8 @@ def main():
     line = {
         "metric": METRIC, "value": hr["snps_per_s"], "unit": UNIT, "n_gpus": world, "steps": hr["steps"],
         "warmup": args.warmup, "ms_per_step": hr["ms_per_step"], "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": {"fp64": "f64", "bf16x3": "bf16x3", "tf32x3": "tf32x3", "f16x2": "f16x2"}[head],
+        "vs_baseline": None, "dtype": {"fp64": "f64", "bf16x3": "bf16x3", "tf32x3": "tf32x3", "f16x2": "f16x2",
+                                                                   "sliced64": "f16"}[head],
         "data": "synthetic (seeded kinship, covariates, phenotype and int8 dosages shaped like the paper's n=1e4, p=4 workload)",
         "config": {"workload": WORKLOAD, "n": w["n"], "p": w["p"], "bs": w["bs"],
                    "snps_per_step": N_RESIDENT_BLOCKS * w["bs"],

@@ -82,17 +82,18 @@ extern "C" {
  *                 explicit once in FP64 (L^-T L^-1, at gwas_init): per SNP, with x' the
  *                 int8 column shifted by its integer mean, x'^T [X^_L | y^] (X^_L = W X_L,
  *                 y^ = W y) and x'^T W x' = 2 x'^T T x' (T = W's lower triangle, diagonal
- *                 halved).  T's rows (one power-of-two scale) are cut into five 10-bit
- *                 integer slices and [X^_L | y^]'s columns into six, each exact in FP16;
- *                 every slice times the int8 dosages is an exact integer (FP16 products,
- *                 FP32 accumulation kept below 2^24), so the only error is T's 50-bit
- *                 representation.  Five triangular FP16 products per block.  Tile modes,
- *                 strip_group, separate_sums and single_piece do not apply (GWAS_ERR_ARG
- *                 if set); batches take split contexts only.  A block whose largest
- *                 |x - c| * 512 * n_pad reaches 2^31 is refused (GWAS_ERR_ARG; never for
- *                 dosages 0..2 below n = 2,000,000).  Set-up takes 16 n_pad^2 bytes for a
- *                 while (W and the transpose operator), the context keeps 10 n_pad^2
- *                 (slices) + 20 n_pad bs (products) bytes beside the FP64 study data. */
+ *                 halved).  T's rows (one power-of-two scale) are cut into four 11-bit
+ *                 integer slices (entries within +-1024) and [X^_L | y^]'s columns into
+ *                 six, each exact in FP16; every slice times the int8 dosages is an exact
+ *                 integer (FP16 products, FP32 accumulation kept at most 2^24), so the
+ *                 only error is T's 44-bit representation.  Four triangular FP16 products
+ *                 per block.  Tile modes, strip_group, separate_sums and single_piece do
+ *                 not apply (GWAS_ERR_ARG if set); batches take split contexts only.  A
+ *                 block whose largest |x - c| * 1024 * n_pad reaches 2^31 is refused
+ *                 (GWAS_ERR_ARG; never for dosages 0..2 below n = 1,000,000; any int8
+ *                 values up to n = 8,192).  Set-up takes 16 n_pad^2 bytes for a while (W
+ *                 and the transpose operator), the context keeps 8 n_pad^2 (slices) +
+ *                 16 n_pad bs (products) bytes beside the FP64 study data. */
 typedef enum { GWAS_FP64 = 0, GWAS_TF32X3 = 1, GWAS_BF16X3 = 2, GWAS_F16X2 = 3, GWAS_SLICED64 = 4 } gwas_precision;
 
 typedef struct {

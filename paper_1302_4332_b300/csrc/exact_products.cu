@@ -17,21 +17,22 @@
 //             K-blocks above each row pair's diagonal;
 // the arithmetic after the product (adjoint.cu, reduce_solve.cu) is FP64.
 //
-// Exact slices.  Each row of A, scaled by a power of two s (one s for all of
-// the square part's rows, one per appended row) so that its largest entry is
-// at most 512 in magnitude, is written as a_1 + a_2 2^-10 + a_3 2^-20 + ...,
-// every a_k an integer in [-512, 512] (exact in FP16).  The square part keeps
-// three slices in the adjoint (30 bits) and five in the solve (50 bits: b and
-// se at the FP64 path's accuracy even where z-scores reach 1e5), the appended
-// rows six: their dot products with a
-// centred x' can cancel, and three slices left ~1e-7 relative error in the
-// gradient where six leave ~4e-9 (a CPU emulation of this scheme at n =
-// 300..3000).  A slice times the integer dosages, accumulated by the tensor
-// cores in FP32, is exact while every partial sum stays below 2^24: at most
-// 256 / max|x'| K-blocks of 128 go into one TMEM partial (every K-block of a
-// dosage block up to n = 16,384 with |x'| <= 2), and the epilogue adds the
-// partials as int32.  The products leave as int32 and are combined per SNP in
-// FP64 and int64, so the only error left is the slices' representation.
+// Exact slices of B bits (B = 10 in the adjoint, 11 in the solve).  Each row
+// of A, scaled by a power of two s (one s for all of the square part's rows,
+// one per appended row) so that its largest entry is at most 2^(B-1) in
+// magnitude, is written as a_1 + a_2 2^-B + a_3 2^-2B + ..., every a_k an
+// integer in [-2^(B-1), 2^(B-1)] (exact in FP16).  The square part keeps three
+// 10-bit slices in the adjoint (30 bits) and four 11-bit slices in the solve
+// (44 bits), the appended rows six: their dot products with a centred x' can
+// cancel, and three slices left ~1e-7 relative error in the gradient where six
+// leave ~4e-9 (a CPU emulation of this scheme at n = 300..3000).  A slice times
+// the integer dosages, accumulated by the tensor cores in FP32, is exact while
+// every partial sum stays at most 2^24 in magnitude: one TMEM partial takes at
+// most 2^24 / (2^(B-1) max|x'| 64) operand stages of 64 K (dosages, |x'| <= 2:
+// 256 stages of 10-bit slices, 128 of 11-bit ones; any int8 values: at least
+// one), and the epilogue adds the partials as int32.  The products leave as
+// int32 and are combined per SNP in FP64 and int64, so the only error left is
+// the slices' representation.
 //
 // Layout: A holds `slabs` slabs of RS rows (RS = 256 ceil((P + 1) / 2)), slab
 // k = slice k of the square part's n_pad rows, then (slabs 0..2) slice k of
@@ -74,8 +75,10 @@ constexpr int BAR_OFF = STG_OFF + EPI_WARPS * 2 * CHUNK_BYTES;
 constexpr int NBARS = 2 * STAGES + 4 + 3 * TRING + 1;
 constexpr int SMEM = 1024 + BAR_OFF + NBARS * 8 + TRING * 4 + 16;
 static_assert(SMEM <= 232448, "shared memory per CTA");
-constexpr int SLABS = 3;        // the adjoint: three 10-bit slices of W (30 bits)
-constexpr int SOLVE_SLABS = 5;  // the sliced solve: five slices of W's triangle (50 bits)
+constexpr int SLABS = 3;       // the adjoint: three 10-bit slices of W (30 bits)
+constexpr int ADJ_BITS = 10;
+constexpr int SOLVE_SLABS = SLICED_SLABS;  // the sliced solve: four 11-bit slices of W's triangle (44 bits)
+constexpr int SOLVE_BITS = SLICED_BITS;
 
 struct Params {
   CUtensorMap A;  // the stacked slices: dims {n_pad, slabs RS}, box {32, 128}, 64-byte swizzle, FP16
@@ -85,6 +88,7 @@ struct Params {
   int U;          // row-panel pairs per slab (RS / 256)
   int RS;         // rows per slab
   int slabs;      // slices of the square part (3: the adjoint's W; 4: the solve's triangle)
+  int amax;       // bound on |slice entry|: 2^(B-1) for B-bit slices (512 or 1024)
   int tri;        // 1: the square part is lower triangular (rows < 256 (u + 1) of pair u need
                   // K-blocks < 2u + 2 only) and units go out longest first
   int Cs;         // 256-column strips of the block
@@ -103,17 +107,18 @@ struct Params {
   int ldx;
 };
 
-// K-blocks per TMEM partial so that every partial sum is an integer below
-// 2^24 in magnitude: 512 * xmax * 128 * G <= 2^24.
-__device__ __forceinline__ int partial_span(int xmax, int P) {
-  if (xmax <= 0) return P;
-  const int g = 256 / xmax;
-  return g < 1 ? 1 : (g > P ? P : g);
+// Operand stages (64 K each) per TMEM partial so that every partial sum is an
+// integer of magnitude at most 2^24: amax * xmax * 64 * G <= 2^24 (G >= 1 for
+// every int8 block: |x'| <= 255 and amax <= 1024).  `stages`: a unit's most.
+__device__ __forceinline__ int partial_stages(int xmax, int amax, int stages) {
+  if (xmax <= 0) return stages;
+  const long long g = (1LL << 24) / ((long long)amax * xmax * (KCH * SUB));
+  return g < 1 ? 1 : (g > stages ? stages : (int)g);
 }
 
-// The int32 totals hold 512 * xmax * n_pad at most: beyond 2^31 the block is refused.
-__device__ __forceinline__ bool in_range(int xmax, int P) {
-  return 512LL * xmax * (long long)TB * P < (1LL << 31);
+// The int32 totals hold amax * xmax * n_pad at most: beyond 2^31 the block is refused.
+__device__ __forceinline__ bool in_range(int xmax, int amax, int P) {
+  return (long long)amax * xmax * (long long)TB * P < (1LL << 31);
 }
 
 // Work unit t -> (slab, row-panel pair u, 256-column strip c) and its K-blocks.
@@ -170,10 +175,10 @@ __global__ void __launch_bounds__(THREADS, 1) exact_product_kernel(const __grid_
       ptx::mbar_arrive_peer_count(ptx::peer_addr(bar, 0));
   };
   const int xmax = *b.xmax;  // written by the cast, an ordinary launch before this one
-  const bool ok_range = in_range(xmax, b.P);
+  const bool ok_range = in_range(xmax, b.amax, b.P);
   if (!ok_range && blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&st->err, DEV_OK, DEV_ERR_RANGE);
   const int ntiles = ok_range ? b.ntiles : 0;
-  const int G = partial_span(xmax, b.P);
+  const int G = partial_stages(xmax, b.amax, b.P * CPB);  // operand stages per TMEM partial
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -267,12 +272,12 @@ __global__ void __launch_bounds__(THREADS, 1) exact_product_kernel(const __grid_
         ptx::mbar_arrive(&tile_empty[slot]);
         if (t >= ntiles) break;
         if (!leader) continue;
-        const int kend = unit_of(b, t).kend;
+        const int nst = unit_of(b, t).kend * CPB;  // the unit's operand stages
         bool ok = true;
         int a = 0;
         uint32_t d = 0, accumulate = 0;
-        for (int j = 0; j < kend && ok; ++j) {
-          if (j % G == 0) {  // a fresh partial every G K-blocks, alternating between the two buffers
+        for (int g = 0; g < nst; ++g, ++cnt) {
+          if (g % G == 0) {  // a fresh partial every G stages, alternating between the two buffers
             a = kb & 1;
             if (!ptx::mbar_wait(&part_empty[a], ((kb >> 1) & 1) ^ 1, st)) { ok = false; break; }
             ++kb;
@@ -280,25 +285,22 @@ __global__ void __launch_bounds__(THREADS, 1) exact_product_kernel(const __grid_
             d = tmem_base + a * TN;
             accumulate = 0;
           }
-          for (int h = 0; h < CPB; ++h, ++cnt) {
-            const int s = cnt % STAGES;
-            const uint32_t r = cnt / STAGES;
-            if (!ptx::mbar_wait(&full[s], r & 1, st)) { ok = false; break; }
-            ptx::tc_fence_after();
-            const uint32_t base = ptx::smem_u32(smem + s * STAGE_BYTES);
+          const int s = cnt % STAGES;
+          const uint32_t r = cnt / STAGES;
+          if (!ptx::mbar_wait(&full[s], r & 1, st)) { ok = false; break; }
+          ptx::tc_fence_after();
+          const uint32_t base = ptx::smem_u32(smem + s * STAGE_BYTES);
 #pragma unroll
-            for (int u2 = 0; u2 < SUB; ++u2)
+          for (int u2 = 0; u2 < SUB; ++u2)
 #pragma unroll
-              for (int kk = 0; kk < KCH / KMMA; ++kk) {
-                const uint32_t off = kk * KMMA * 2;
-                ptx::mma_pair<false>(d, ptx::sdesc_k64(base + u2 * A_BYTES + off),
-                                     ptx::sdesc_k64(base + SUB * A_BYTES + u2 * B_BYTES + off), idesc, accumulate);
-                accumulate = 1;
-              }
-            ptx::mma_commit_pair(&empty[s], BOTH);
-          }
-          if (!ok) break;
-          if (j % G == G - 1 || j == kend - 1) ptx::mma_commit_pair(&part_full[a], BOTH);
+            for (int kk = 0; kk < KCH / KMMA; ++kk) {
+              const uint32_t off = kk * KMMA * 2;
+              ptx::mma_pair<false>(d, ptx::sdesc_k64(base + u2 * A_BYTES + off),
+                                   ptx::sdesc_k64(base + SUB * A_BYTES + u2 * B_BYTES + off), idesc, accumulate);
+              accumulate = 1;
+            }
+          ptx::mma_commit_pair(&empty[s], BOTH);
+          if (g % G == G - 1 || g == nst - 1) ptx::mma_commit_pair(&part_full[a], BOTH);
         }
         if (!ok) break;
       }
@@ -321,7 +323,7 @@ __global__ void __launch_bounds__(THREADS, 1) exact_product_kernel(const __grid_
       if (lane == 0) ptx::mbar_arrive(&tile_empty[slot]);
       if (t >= ntiles) break;
       const Unit un = unit_of(b, t);
-      const int nparts = (un.kend + G - 1) / G;
+      const int nparts = (un.kend * CPB + G - 1) / G;
 #pragma unroll
       for (int i = 0; i < EPI_COLS; ++i) master[i] = 0;
       bool ok = true;
@@ -431,12 +433,13 @@ __global__ void col_absmax_kernel(const double* __restrict__ X, int64_t ld, int 
   if ((threadIdx.x & 31) == 0) atomicMax(out + col, (unsigned long long)__double_as_longlong(m));
 }
 
-// Slice k (0-based) of v s: a_0 = rint(v s), a_k = rint(2^10 (remainder after a_0 .. a_{k-1})).
-// Every step is exact in FP64 (a power-of-two scale, an integer subtracted).
-__device__ __forceinline__ double slice_of(double v, double s, int k) {
+// Slice k (0-based) of v s: a_0 = rint(v s), a_k = rint(2^B (remainder after
+// a_0 .. a_{k-1})), step = 2^B.  Every step is exact in FP64 (a power-of-two
+// scale, an integer subtracted); |remainder| <= 1/2, so |a_k| <= 2^(B-1).
+__device__ __forceinline__ double slice_of(double v, double s, int k, double step) {
   double r = v * s, a = rint(r);
   for (int i = 0; i < k; ++i) {
-    r = (r - a) * 1024.0;
+    r = (r - a) * step;
     a = rint(r);
   }
   return a;
@@ -451,7 +454,7 @@ __device__ __forceinline__ double slice_of(double v, double s, int k) {
 // ne rows, slice k + 3 for the next, in slabs 0..2 (zero in later slabs).
 // Further rows zero.
 __global__ void slice_rows_kernel(const double* __restrict__ W, const double* __restrict__ Ex, int n_pad, int ne,
-                                  int RS, int slabs, int tri, const double* __restrict__ scale,
+                                  int RS, int slabs, int tri, double step, const double* __restrict__ scale,
                                   __half* __restrict__ A) {
   const int R = blockIdx.y;
   const int col = blockIdx.x * blockDim.x + threadIdx.x;
@@ -471,8 +474,9 @@ __global__ void slice_rows_kernel(const double* __restrict__ W, const double* __
     kind = 2;
   }
   for (int k = 0; k < slabs; ++k) {
-    const double a = kind == 1 ? slice_of(v, s, k) : (kind == 2 && k < 3) ? slice_of(v, s, k0 + k) : 0.0;
-    A[((int64_t)k * RS + R) * n_pad + col] = __float2half_rn((float)a);  // an integer in [-512, 512]: exact
+    const double a =
+        kind == 1 ? slice_of(v, s, k, step) : (kind == 2 && k < 3) ? slice_of(v, s, k0 + k, step) : 0.0;
+    A[((int64_t)k * RS + R) * n_pad + col] = __float2half_rn((float)a);  // an integer in [-1024, 1024]: exact
   }
 }
 
@@ -629,6 +633,7 @@ __global__ void __launch_bounds__(256) exact_dy_apply_kernel(const double* __res
 // triangle T in 4 slabs; appended rows [X^_L | Y^]).
 struct ExactProducts {
   int n = 0, n_pad = 0, q = 0, bs = 0, P = 0, U = 0, RS = 0, ne = 0, slabs = 0;
+  int bits = 0;  // bits per slice
   bool tri = false, center = false;
   int max_clusters = 0;
   double* W = nullptr;          // n_pad x n_pad FP64 (owned; kept by the adjoint for its y-gradient)
@@ -659,17 +664,18 @@ void exact_destroy(ExactProducts* E) {
   delete E;
 }
 
-static double pow2_scale(double mx) {  // 2^e with mx 2^e <= 512 < mx 2^(e+1); 1 for a zero row
+// 2^e with mx 2^e <= bound < mx 2^(e+1); 1 for a zero row
+static double pow2_scale(double mx, double bound) {
   if (!(mx > 0.0) || !std::isfinite(mx)) return 1.0;
-  int e = (int)std::floor(std::log2(512.0 / mx));
-  while (std::ldexp(mx, e) > 512.0) --e;
-  while (std::ldexp(mx, e + 1) <= 512.0) ++e;
+  int e = (int)std::floor(std::log2(bound / mx));
+  while (std::ldexp(mx, e) > bound) --e;
+  while (std::ldexp(mx, e + 1) <= bound) ++e;
   return std::ldexp(1.0, e);
 }
 
 // W (taken over), Ex = the ne appended columns (n_pad x ne, read here only).
-static cudaError_t exact_create(ExactProducts** out, double* W, const double* Ex, int ne, int slabs, bool tri,
-                                bool keep_w, int n, int n_pad, int q, int bs, bool center, int num_sms,
+static cudaError_t exact_create(ExactProducts** out, double* W, const double* Ex, int ne, int slabs, int bits,
+                                bool tri, bool keep_w, int n, int n_pad, int q, int bs, bool center, int num_sms,
                                 cudaStream_t s, int64_t* launches) {
   *out = nullptr;
   ExactProducts* E = new ExactProducts;
@@ -683,6 +689,7 @@ static cudaError_t exact_create(ExactProducts** out, double* W, const double* Ex
   E->RS = 2 * E->U * TB;
   E->ne = ne;
   E->slabs = slabs;
+  E->bits = bits;
   E->tri = tri;
   E->center = center;
   cudaError_t e;
@@ -726,11 +733,12 @@ static cudaError_t exact_create(ExactProducts** out, double* W, const double* Ex
     wmax = std::max(wmax, v);
   }
   std::vector<double> sc(1 + ne), inv(1 + ne);
-  sc[0] = pow2_scale(wmax);
+  const double amax = std::ldexp(1.0, bits - 1);  // the largest |slice entry|
+  sc[0] = pow2_scale(wmax, amax);
   for (int i = 0; i < ne; ++i) {
     double v;
     std::memcpy(&v, &hm[(size_t)n_pad + i], sizeof v);
-    sc[1 + i] = pow2_scale(v);
+    sc[1 + i] = pow2_scale(v, amax);
   }
   for (int i = 0; i <= ne; ++i) inv[i] = 1.0 / sc[i];  // powers of two: exact
   double* dsc = nullptr;
@@ -738,7 +746,7 @@ static cudaError_t exact_create(ExactProducts** out, double* W, const double* Ex
   TRY(cudaMemcpyAsync(dsc, sc.data(), sizeof(double) * (1 + ne), cudaMemcpyHostToDevice, s));
   TRY(cudaMemcpyAsync(E->inv_scale, inv.data(), sizeof(double) * (1 + ne), cudaMemcpyHostToDevice, s));
   slice_rows_kernel<<<dim3((n_pad + 255) / 256, E->RS), 256, 0, s>>>(W, Ex, n_pad, ne, E->RS, slabs, tri ? 1 : 0,
-                                                                     dsc, E->A);
+                                                                     2.0 * amax, dsc, E->A);
   *launches += 1;
   TRY(cudaGetLastError());
   TRY(cudaFreeAsync(mx, s));
@@ -763,6 +771,7 @@ static cudaError_t exact_create(ExactProducts** out, double* W, const double* Ex
   p.U = E->U;
   p.RS = E->RS;
   p.slabs = slabs;
+  p.amax = 1 << (bits - 1);
   p.tri = tri ? 1 : 0;
   p.xmax = E->xmax;
   p.counter = reinterpret_cast<unsigned int*>(E->xmax + 1);
@@ -809,14 +818,16 @@ cudaError_t exact_adjoint_create(ExactProducts** out, double* W, const double* W
     cudaFree(W);
     return e;
   }
-  e = exact_create(out, W, Ex, ne, ex3::SLABS, false, true, n, n_pad, q, bs, center, num_sms, s, launches);
+  e = exact_create(out, W, Ex, ne, ex3::SLABS, ex3::ADJ_BITS, false, true, n, n_pad, q, bs, center, num_sms, s,
+                   launches);
   cudaFreeAsync(Ex, s);
   return e;
 }
 
 cudaError_t exact_solve_create(ExactProducts** out, double* W, const double* Wh, int nw, int n, int n_pad, int q,
                                int bs, bool center, int num_sms, cudaStream_t s, int64_t* launches) {
-  return exact_create(out, W, Wh, nw, ex3::SOLVE_SLABS, true, false, n, n_pad, q, bs, center, num_sms, s, launches);
+  return exact_create(out, W, Wh, nw, ex3::SOLVE_SLABS, ex3::SOLVE_BITS, true, false, n, n_pad, q, bs, center,
+                      num_sms, s, launches);
 }
 
 // x' of a block into the FP16 operand (columns past ncols of the last strip

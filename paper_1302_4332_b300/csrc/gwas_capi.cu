@@ -171,8 +171,9 @@ int check_device_status(gwas_ctx* ctx) {
     clean.sc_err = hs.sc_err;
     CK(cudaMemcpy(ctx->st, &clean, sizeof clean, cudaMemcpyHostToDevice));
     if (hs.err == DEV_ERR_RANGE)
-      return fail(ctx, GWAS_ERR_ARG, "SNP values too large for the split adjoint's exact products "
-                                     "(largest |x - c| times 512 n_pad reaches 2^31)");
+      return fail(ctx, GWAS_ERR_ARG, "SNP values too large for the exact products (largest |x - c| times "
+                                     "n_pad times the slice bound, 512 in the adjoint and 1024 in the sliced "
+                                     "solve, reaches 2^31)");
     return fail(ctx, GWAS_ERR_TIMEOUT, "a bounded device-side wait ran out (device code %d)", hs.err);
   }
   return GWAS_OK;

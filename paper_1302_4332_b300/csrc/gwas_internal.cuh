@@ -193,6 +193,12 @@ cudaError_t exact_solve_sums(ExactProducts* E, int ncols, const SolveConsts* sc,
 void exact_destroy(ExactProducts* E);
 // CTAs of a full launch of the exact product kernel (2-SM clusters).
 int exact_max_ctas(const ExactProducts* E);
+// The sliced solve's slices of T (the product kernel and the per-SNP sums must
+// agree): SLICED_SLABS integer slices of SLICED_BITS bits, every entry of a
+// slice within +-2^(SLICED_BITS - 1) (exact in FP16).  The adjoint's slices of
+// W are three of 10 bits (exact_products.cu, adjoint.cu).
+constexpr int SLICED_SLABS = 4;
+constexpr int SLICED_BITS = 11;
 // The sliced solve's per-SNP sums from the exact products and the FP64 p x p
 // solve (reduce_solve.cu).  C: slabs x RS rows per SNP (leading dimension
 // ldc; only rows >= r_lo of the square part and the appended rows are read),

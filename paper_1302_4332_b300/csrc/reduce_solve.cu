@@ -632,14 +632,16 @@ cudaError_t launch_partials_solve(const float* red, int ngroups, int64_t ldr, co
 // with fixed FP64 data (W = M^-1, W^ = [X^_L | Y^] = W [X_L | Y]):
 //     S_BL = x~^T X~_L = x'^T X^_L,   r_B = x~^T y~ = x'^T y^,   S_BR = x~^T x~ = x'^T W x' = 2 x'^T T x',
 // T = W's lower triangle with its diagonal halved.  C holds, per SNP, the
-// exact int32 products of x' with SOLVE_SL = 5 slabs of 10-bit slices: slab k row r
-// (r < n_pad) = slice k of (T x')_r in units of 2^-10k / s_T; rows n_pad + e
-// and n_pad + ne + e of slabs 0..2 = slices k and k + 3 of W^[:, e]^T x'.
-// sum_r x'_r C_k[r] is exact in int64 (|x'_r C| < 2^39): the product kernel
-// added it over the rows below r_lo into acc[k][col]; the rows r_lo .. n - 1
-// (stored in C) are added here.  The five slabs and the six slices are then
-// combined in FP64 (smallest first), then the FP64 solve.
-constexpr int SOLVE_SL = 5;
+// exact int32 products of x' with SOLVE_SL slabs of B-bit slices (B =
+// SLICED_BITS): slab k row r (r < n_pad) = slice k of (T x')_r in units of
+// 2^-Bk / s_T; rows n_pad + e and n_pad + ne + e of slabs 0..2 = slices k and
+// k + 3 of W^[:, e]^T x'.  sum_r x'_r C_k[r] is exact in int64 (|x'_r C| <
+// 2^39): the product kernel added it over the rows below r_lo into
+// acc[k][col]; the rows r_lo .. n - 1 (stored in C) are added here.  The slabs
+// and the six slices are then combined in FP64 (smallest first, every factor a
+// power of two), then the FP64 solve.
+constexpr int SOLVE_SL = SLICED_SLABS;
+constexpr double SL_UP = (double)(1 << SLICED_BITS);  // 2^B
 
 template <int QM>
 __global__ void __launch_bounds__(256) sliced_solve_kernel(
@@ -665,26 +667,25 @@ __global__ void __launch_bounds__(256) sliced_solve_kernel(
   for (int k = 0; k < SOLVE_SL; ++k)
 #pragma unroll
     for (int o = 16; o; o >>= 1) pk[k] += __shfl_xor_sync(0xffffffffu, pk[k], o);
-  // appended row `lane` (< ne): six slices, the smallest first
+  // appended row `lane` (< ne): six slices, the smallest first; slice k sits
+  // in slab k % 3, row r0 (k < 3) or r1 (k >= 3)
   double ev = 0.0;
   if (lane < ne) {
     const int r0 = n_pad + lane, r1 = n_pad + ne + lane;
-    double v = 0.0;
-    v = fma((double)cc[2 * RS + r1], 0x1p-50, v);
-    v = fma((double)cc[RS + r1], 0x1p-40, v);
-    v = fma((double)cc[r1], 0x1p-30, v);
-    v = fma((double)cc[2 * RS + r0], 0x1p-20, v);
-    v = fma((double)cc[RS + r0], 0x1p-10, v);
+    double v = 0.0, f = 1.0 / (SL_UP * SL_UP * SL_UP * SL_UP * SL_UP);  // 2^-5B
+#pragma unroll
+    for (int k = 5; k >= 1; --k, f *= SL_UP) v = fma((double)cc[(k % 3) * RS + (k < 3 ? r0 : r1)], f, v);
     ev = ((double)cc[r0] + v) * inv_scale[1 + lane];
   }
   double acc[QM + 2];
 #pragma unroll
   for (int a = 0; a <= QM; ++a) acc[a] = __shfl_sync(0xffffffffu, ev, a);
   if (lane != 0) return;
-  double v = (double)pk[4] * 0x1p-40;  // |pk| < 2^53: exact conversions
-  v = fma((double)pk[3], 0x1p-30, v);
-  v = fma((double)pk[2], 0x1p-20, v);
-  v = fma((double)pk[1], 0x1p-10, v);
+  double v = 0.0, f = 1.0;  // |pk| < 2^53: exact conversions
+#pragma unroll
+  for (int k = 1; k < SOLVE_SL; ++k) f /= SL_UP;  // 2^-B(SOLVE_SL - 1)
+#pragma unroll
+  for (int k = SOLVE_SL - 1; k >= 1; --k, f *= SL_UP) v = fma((double)pk[k], f, v);
   acc[QM + 1] = 2.0 * ((double)pk[0] + v) * inv_scale[0];
   solve_store<QM>(acc, sc, q, col, b, se, status, shift ? (double)shift[col] : 0.0, t, bstride);
 }

@@ -2,7 +2,7 @@
 
 Eq. 1's X_i^T M^-1 X_i and X_i^T M^-1 y from exact integer products of a
 sliced M^-1 with the shifted int8 dosages on the tensor cores; the only error
-is the 50-bit representation of M^-1's triangle, so every check here uses the
+is the 44-bit representation of M^-1's triangle, so every check here uses the
 FP64 path's tolerance: per-SNP normwise b, b in units of se, and se
 component-wise, all <= 1e-10, statuses identical."""
 import numpy as np
