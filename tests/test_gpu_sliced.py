@@ -165,3 +165,30 @@ def test_adjoint_on_a_sliced_context():
     assert np.linalg.norm(dch - dh_o) / np.linalg.norm(dh_o) <= 1e-6
     assert abs(dh_acc[0] - dh_o.sum()) / abs(dh_o.sum()) <= 1e-6
     assert np.linalg.norm(dy_acc - dy_o) / np.linalg.norm(dy_o) <= 1e-6
+
+
+def test_int8_range_limit():
+    """The int32 product totals bound max|x - c| * 1024 * n_pad below 2^31:
+    a column with |x - c| = 255 is solved exactly at n = 8,192 (n_pad = 8,192)
+    and refused with GWAS_ERR_ARG one row panel later (n_pad = 8,320), where
+    dosage columns still solve."""
+    for n, ok in ((8192, True), (8193, False)):
+        s = gwas_synth.study(n, 4, 256, 0.5, 1.0, seed=3)
+        X = np.asfortranarray(gwas_synth.dosages(n, 0, 6, seed=3))
+        Xw = X.copy(order="F")
+        Xw[:, 2] = 127
+        Xw[:10, 2] = -128  # shift 127: |x - c| = 255
+        with gw.GLS(s["Phi"], s["XL"], s["y"], 0.5, 1.0, precision="fp64", bs=8) as g:
+            b64, se64, st64 = g.solve_block(Xw)
+        with gw.GLS(s["Phi"], s["XL"], s["y"], 0.5, 1.0, precision="sliced64", bs=8) as g:
+            if ok:
+                b, se_g, st_g = g.solve_block(Xw)
+                _check(b, se_g, st_g, b64, se64, st64, ("int8 extremes", n))
+            else:
+                with pytest.raises(gw.GwasError) as e:
+                    g.solve_block(Xw)
+                assert e.value.name == "GWAS_ERR_ARG"
+                b, se_g, st_g = g.solve_block(X)  # the context stays usable
+                with gw.GLS(s["Phi"], s["XL"], s["y"], 0.5, 1.0, precision="fp64", bs=8) as g64:
+                    r, se, st = g64.solve_block(X)
+                _check(b, se_g, st_g, r, se, st, ("dosages", n))
