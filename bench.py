@@ -226,18 +226,38 @@ def measure_extra_peaks(torch, dev):
     return out
 
 
+def source_digest(name: str) -> str:
+    """sha256[:16] of a kernel source file and of every library header it
+    includes (directly or through another header), in a fixed order: a
+    traffic record holds for the kernel only while none of them changed."""
+    csrc = os.path.join(ROOT, "paper_1302_4332_b300", "csrc")
+    seen, todo = [], [name]
+    while todo:
+        f = todo.pop(0)
+        path = os.path.join(csrc, f)
+        if f in seen or not os.path.exists(path):
+            continue
+        seen.append(f)
+        for line in open(path, encoding="utf-8", errors="replace"):
+            t = line.strip()
+            if t.startswith("#include \""):
+                todo.append(t.split('"')[1])
+    h = hashlib.sha256()
+    for f in [seen[0]] + sorted(seen[1:]):
+        h.update(f.encode() + b"\0" + open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
 def kernel_traffic(path: str, tiles: str = ""):
     """DRAM bytes per launch of the path's solve kernel (split paths: keyed by
     precision and tile mode) from the committed ncu summary, if that summary
-    was taken on the current source."""
+    was taken on the current source (the kernel's file and its headers)."""
     try:
         with open(os.path.join(ROOT, "profiles", "traffic_per_launch.json")) as f:
             rec = json.load(f).get(f"{path}/{tiles}" if tiles else path)
         if not rec:
             return None
-        src = os.path.join(ROOT, "paper_1302_4332_b300", "csrc", rec["source"])
-        digest = hashlib.sha256(open(src, "rb").read()).hexdigest()[:16]
-        return rec["dram_bytes"] if digest == rec["sha256_16"] else None
+        return rec["dram_bytes"] if source_digest(rec["source"]) == rec["sha256_16"] else None
     except Exception:
         return None
 

@@ -274,16 +274,17 @@ __global__ void __launch_bounds__(THREADS, 1) exact_product_kernel(const __grid_
         if (!leader) continue;
         const int nst = unit_of(b, t).kend * CPB;  // the unit's operand stages
         bool ok = true;
-        int a = 0;
+        int a = 0, left = 0;  // stages left for the current partial (a counter: no division per stage)
         uint32_t d = 0, accumulate = 0;
         for (int g = 0; g < nst; ++g, ++cnt) {
-          if (g % G == 0) {  // a fresh partial every G stages, alternating between the two buffers
+          if (left == 0) {  // a fresh partial every G stages, alternating between the two buffers
             a = kb & 1;
             if (!ptx::mbar_wait(&part_empty[a], ((kb >> 1) & 1) ^ 1, st)) { ok = false; break; }
             ++kb;
             ptx::tc_fence_after();
             d = tmem_base + a * TN;
             accumulate = 0;
+            left = G;
           }
           const int s = cnt % STAGES;
           const uint32_t r = cnt / STAGES;
@@ -300,7 +301,7 @@ __global__ void __launch_bounds__(THREADS, 1) exact_product_kernel(const __grid_
               accumulate = 1;
             }
           ptx::mma_commit_pair(&empty[s], BOTH);
-          if (g % G == G - 1 || g == nst - 1) ptx::mma_commit_pair(&part_full[a], BOTH);
+          if (--left == 0 || g == nst - 1) ptx::mma_commit_pair(&part_full[a], BOTH);
         }
         if (!ok) break;
       }
@@ -350,8 +351,9 @@ __global__ void __launch_bounds__(THREADS, 1) exact_product_kernel(const __grid_
         // x'^T (T_k x') over this warp's 32 rows, column by column: the int64
         // product of each lane split at bit 20 (|x' C| < 2^39, so both parts sum
         // over 32 lanes inside an int32), one warp reduction each, one atomic
-        // Columns past the block's ncols (a partial last strip) are neither read
-        // nor added: x' and acc hold the block's columns only.
+        // add per column.  Columns past the block's ncols (a partial last
+        // strip) are neither read nor added: x' and acc hold the block's
+        // columns only.
         const int rr = (2 * un.u + (int)rank) * TB + 32 * lq + lane;  // the row of T: x' row too
         const int cb = un.c * TN + chalf * EPI_COLS;
         const int nv = b.ncols - cb;  // valid columns of this warp's 128 (may be <= 0)

@@ -1966,16 +1966,10 @@ __global__ void check_timeout_kernel(int kind, long long limit_ns, gwas::DevStat
     gwas::ptx::mbar_init(&bar, 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  const long long t0 = gwas::ptx::globaltimer();
-  while (true) {
-    if (kind == 0 ? *reinterpret_cast<volatile const int*>(&g_never_set) != 0 : gwas::ptx::mbar_try_wait(&bar, 0))
-      return;
-    if (gwas::ptx::aborting(st)) return;
-    if (gwas::ptx::globaltimer() - t0 > limit_ns) {
-      gwas::ptx::raise_timeout(st);
-      return;
-    }
-  }
+  if (kind == 0)
+    gwas::ptx::bounded_wait([&] { return *reinterpret_cast<volatile const int*>(&g_never_set) != 0; }, st, limit_ns);
+  else
+    gwas::ptx::bounded_wait([&] { return gwas::ptx::mbar_try_wait(&bar, 0); }, st, limit_ns);
 }
 }  // namespace
 

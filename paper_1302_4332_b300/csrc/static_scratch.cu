@@ -29,6 +29,7 @@ namespace {
 
 constexpr size_t kScratchBytes = GWAS_STATIC_SCRATCH_BYTES;
 constexpr size_t kSchedBytes = 128;  // scheduler counter, then the tile flags
+static_assert(sizeof(gwas::Sched) == kSchedBytes, "the tile flags follow the scheduler block");
 
 // Per-call scratch: [scheduler counter | tile flags | padding to 256 B | X~ block (FP64)].
 static __device__ __align__(256) unsigned char g_scratch[kScratchBytes];

@@ -60,19 +60,36 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
   return ok != 0;
 }
 
+// Polls between two looks at the abort flag and the clock in a bounded wait.
+// The abort flag is a global load (hundreds of cycles): read after every poll
+// it would delay the waiter's reaction to the event it waits for by that much
+// (measured: the exact product kernel's single MMA-issuing thread lost ~10 %).
+constexpr uint32_t WAIT_CHECK_EVERY = 32;
+
+// Polls `done` until it holds: true; false when the launch is aborting or after
+// limit_ns (the error word and the abort flag raised).  Every poll ends by
+// itself (an mbarrier try_wait returns after a bounded suspension, a flag poll
+// is a load), so the wait is bounded.
+template <typename Done>
+__device__ __forceinline__ bool bounded_wait(Done done, DevStatus* st, long long limit_ns = WAIT_LIMIT_NS) {
+  if (done()) return true;
+  const long long t0 = globaltimer();
+  for (uint32_t i = 1;; ++i) {
+    if (done()) return true;
+    if (i % WAIT_CHECK_EVERY == 0) {
+      if (aborting(st)) return false;
+      if (globaltimer() - t0 > limit_ns) {
+        raise_timeout(st);
+        return false;
+      }
+    }
+  }
+}
+
 // Waits for the phase with the given parity to complete.  False on timeout
 // or when the launch is aborting.
 __device__ __forceinline__ bool mbar_wait(uint64_t* bar, uint32_t parity, DevStatus* st) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const long long t0 = globaltimer();
-  while (true) {
-    if (mbar_try_wait(bar, parity)) return true;
-    if (aborting(st)) return false;
-    if (globaltimer() - t0 > WAIT_LIMIT_NS) {
-      raise_timeout(st);
-      return false;
-    }
-  }
+  return bounded_wait([&] { return mbar_try_wait(bar, parity); }, st);
 }
 
 // The same with cluster-scope acquire: for barriers that a peer CTA of the
@@ -92,17 +109,7 @@ __device__ __forceinline__ bool mbar_try_wait_cl(uint64_t* bar, uint32_t parity)
 
 template <bool CLUSTER>
 __device__ __forceinline__ bool mbar_wait_s(uint64_t* bar, uint32_t parity, DevStatus* st) {
-  auto poll = [&] { return CLUSTER ? mbar_try_wait_cl(bar, parity) : mbar_try_wait(bar, parity); };
-  if (poll()) return true;
-  const long long t0 = globaltimer();
-  while (true) {
-    if (poll()) return true;
-    if (aborting(st)) return false;
-    if (globaltimer() - t0 > WAIT_LIMIT_NS) {
-      raise_timeout(st);
-      return false;
-    }
-  }
+  return bounded_wait([&] { return CLUSTER ? mbar_try_wait_cl(bar, parity) : mbar_try_wait(bar, parity); }, st);
 }
 
 // ------------------------------------------------------------------ clusters
@@ -168,16 +175,12 @@ __device__ __forceinline__ void publish_flag(int* flag, bool who) {
 // Waits until *flag != 0 (another CTA finished a tile).  False on timeout/abort.
 __device__ __forceinline__ bool wait_flag(const int* flag, DevStatus* st) {
   if (ld_acquire(flag) != 0) return true;
-  const long long t0 = globaltimer();
-  while (true) {
-    __nanosleep(100);
-    if (ld_acquire(flag) != 0) return true;
-    if (aborting(st)) return false;
-    if (globaltimer() - t0 > WAIT_LIMIT_NS) {
-      raise_timeout(st);
-      return false;
-    }
-  }
+  return bounded_wait(
+      [&] {
+        __nanosleep(100);
+        return ld_acquire(flag) != 0;
+      },
+      st);
 }
 
 // Orders this thread's generic-proxy accesses of global memory with its
