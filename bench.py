@@ -633,6 +633,42 @@ def measure_forms(args, out):
         t = (time.perf_counter() - t1) / 5
     forms["adjoint_bf16x3"] = dict(workload="n=5000, p=4, 4096 SNPs per block", snps_per_s=4096 / t,
                                    ms_per_block=1e3 * t)
+    # the differentiation workload at its full size: d(sum chi2)/dh and d/dy over all m = 100,000
+    # SNPs (25 blocks, the last one ragged), split and FP64, the split result against the FP64 one
+    m4 = 100_000
+    blocks4 = [torch.from_numpy(np.ascontiguousarray(
+        gwas_synth.dosages(5000, c0, min(c0 + 4096, m4), study=4).T)).to(dev).T for c0 in range(0, m4, 4096)]
+
+    def full_adjoint(precision):
+        with gw.GLS(s4["Phi"], s4["XL"], s4["y"], 0.5, 1.0, bs=4096, precision=precision) as g:
+            dh_w = torch.zeros(1, dtype=torch.float64, device=dev)
+            dy_w = torch.zeros(5000, dtype=torch.float64, device=dev)
+            g.adjoint_block(blocks4[0], dh_w, dy_w, chi2, dch)  # set-up and warm-up
+            g.synchronize()
+            dh_f = torch.zeros(1, dtype=torch.float64, device=dev)
+            dy_f = torch.zeros(5000, dtype=torch.float64, device=dev)
+            c2 = [torch.empty(X.shape[1], dtype=torch.float64, device=dev) for X in blocks4]
+            dc = [torch.empty(X.shape[1], dtype=torch.float64, device=dev) for X in blocks4]
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            for X, a, d_ in zip(blocks4, c2, dc):
+                g.adjoint_block(X, dh_f, dy_f, a, d_)
+            g.synchronize()
+            return (time.perf_counter() - t1, float(dh_f[0]), dy_f.cpu().numpy(), torch.cat(c2).cpu().numpy(),
+                    torch.cat(dc).cpu().numpy())
+
+    ts, dhs, dys, c2s, dcs = full_adjoint("bf16x3")
+    t64, dh64, dy64, c264, dc64 = full_adjoint("fp64")
+    ok = np.isfinite(c264) & np.isfinite(c2s)
+    forms["adjoint_full_m100k"] = dict(
+        workload="n=5000, p=4, m=100,000 SNPs (25 blocks of 4096), loss = sum of the Wald chi2",
+        bf16x3_seconds=ts, bf16x3_snps_per_s=m4 / ts, fp64_seconds=t64, fp64_snps_per_s=m4 / t64,
+        dloss_dh=dhs, dloss_dh_fp64=dh64,
+        rel_err_vs_fp64={"dloss_dh": abs(dhs - dh64) / abs(dh64),
+                         "dloss_dy_norm": float(np.linalg.norm(dys - dy64) / np.linalg.norm(dy64)),
+                         "chi2_max": float(np.max(np.abs(c2s[ok] - c264[ok]) / np.abs(c264[ok]))),
+                         "dchi2_dh_norm": float(np.linalg.norm(dcs[ok] - dc64[ok]) / np.linalg.norm(dc64[ok]))})
+    del blocks4
     t1 = time.perf_counter()
     h_hat, ll, evals = gw.reml_fit(s4["Phi"], s4["XL"][:, :3], s4["y"], h0=0.2, tol=1e-8)
     forms["reml_fit"] = dict(workload="null model n=5000, q=3, true h=0.5, from h0=0.2", h_hat=h_hat,
