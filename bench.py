@@ -496,40 +496,47 @@ def measure_forms(args, out):
         cols, order, tuned = tune["cols"], tune["order"], tune["snps_per_s"]
         blocks = [torch.from_numpy(np.ascontiguousarray(gwas_synth.dosages(n, 0, cols, study=i).T)).to(dev).T
                   for i, n in enumerate(STUDY_SIZES)]
-        for _ in range(2):
-            B.solve(blocks)
+        kk = 4  # k blocks of every study per graph replay (k batched launches captured together)
+        steps = max(kk, args.steps // 2 // kk * kk)
+        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+        def timed(fn, reps):
+            fn()  # a switch between the two forms re-captures the graph: untimed
+            B.synchronize()
+            torch.cuda.synchronize()
+            ev0.record()
+            for _ in range(reps):
+                fn()
+            B.synchronize()
+            ev1.record()
+            torch.cuda.synchronize()
+            return ev0.elapsed_time(ev1) / 1e3
+
+        one = lambda: B.solve(blocks)
+        k_steps = lambda: B.solve_k([blocks] * kk)
+        one()
         B.synchronize()
         l0 = B.kernel_launches
-        steps = max(3, args.steps // 2)
-        ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        ev0.record()
-        for _ in range(steps):
-            B.solve(blocks)
+        one()
         B.synchronize()
-        ev1.record()
-        torch.cuda.synchronize()
-        t = ev0.elapsed_time(ev1) / 1e3
+        per_step = B.kernel_launches - l0  # kernels of one single-step replay
+        t_one = [timed(one, steps)]
+        t_k = []
+        for _ in range(2):  # the two forms in turn, the same number of block-steps each
+            t_k.append(timed(k_steps, steps // kk))
+            t_one.append(timed(one, steps))
+        t = float(np.median(t_one))
+        tk = float(np.median(t_k))
         rate = len(STUDY_SIZES) * cols * steps / t
-        # k blocks of every study per graph replay (k batched launches captured together)
-        kk = 4
-        B.solve_k([blocks] * kk)
-        B.synchronize()
-        ev0.record()
-        for _ in range(max(1, steps // kk)):
-            B.solve_k([blocks] * kk)
-        B.synchronize()
-        ev1.record()
-        torch.cuda.synchronize()
-        tk = ev0.elapsed_time(ev1) / 1e3
         forms["batch"] = dict(
             workload="8 studies n=" + ",".join(map(str, STUDY_SIZES)) + ", p=4, bf16x3, int8 dosages",
             snps_per_s=rate, ms_per_step=1e3 * t / steps,
             snps_per_step=len(STUDY_SIZES) * cols, autotuned=tune,
             autotune_snps_per_s=tuned, autotune_over_timed=tuned / rate,
-            k_block_replay=dict(blocks_per_study_per_replay=kk,
-                                snps_per_s=len(STUDY_SIZES) * cols * kk * max(1, steps // kk) / tk),
-            gpu_launches=B.kernel_launches - l0, steps=steps, setup_s=setup_s,
+            k_block_replay=dict(blocks_per_study_per_replay=kk, snps_per_s=len(STUDY_SIZES) * cols * steps / tk),
+            timing="median of 3 timed runs of single-step replays and of 2 of k-step replays, taken in turn "
+                   "(the same block-steps each; the re-capture after each switch untimed)",
+            gpu_launches=per_step * steps, steps=steps, setup_s=setup_s,
             algorithmic_tflops=sum(float(n) * n for n in STUDY_SIZES) * cols * steps / t / 1e12)
         # --- the same batch out of core: each study's dosages in its own file (its block
         # written REPS times), streamed disk -> pinned host (a reader thread per study) -> GPU
