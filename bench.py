@@ -474,6 +474,7 @@ def run_ours(args, rank, world, local_rank, dist):
 
 
 STUDY_SIZES = (2000, 3500, 5000, 7000, 9000, 11000, 13500, 16000)  # the multi-study batching workload
+BATCH_BS = 4096  # the most SNP columns of a study in one batched launch (the tuner's range: 512 .. BATCH_BS)
 
 
 def measure_forms(args, out):
@@ -489,7 +490,8 @@ def measure_forms(args, out):
     # --- batching: 8 studies of uneven n, one persistent graph-captured launch, autotuned
     t0 = time.time()
     studies = [gwas_synth.study(n, 4, 2000, 0.6, 1.0, study_id=i) for i, n in enumerate(STUDY_SIZES)]
-    gls = [gw.GLS(s["Phi"], s["XL"], s["y"], 0.6, 1.0, precision="bf16x3", bs=4096) for s in studies]
+    # each study's context holds up to BATCH_BS columns a launch; the tuner picks how many (512 .. BATCH_BS)
+    gls = [gw.GLS(s["Phi"], s["XL"], s["y"], 0.6, 1.0, precision="bf16x3", bs=BATCH_BS) for s in studies]
     setup_s = time.time() - t0
     with gw.GLSBatch(gls) as B:
         tune = B.autotune_ex(reps=3)
