@@ -99,7 +99,8 @@ def workload(args):
 
 # ------------------------------------------------------------------ clocks
 class ClockSampler:
-    """SM clock and throttle reasons sampled through NVML while running."""
+    """SM clock and throttle reasons sampled through NVML (or nvidia-smi)
+    while running."""
 
     REASONS = {
         0x1: "gpu_idle", 0x2: "applications_clocks_setting", 0x4: "sw_power_cap", 0x8: "hw_slowdown",
@@ -175,8 +176,9 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": self.max_mhz, "reasons": [], "samples": 0,
                     "error": getattr(self, "error", "no samples")}
         reasons = [name for bit, name in self.REASONS.items() if self.reasons & bit and bit != 0x1]
-        return {"sm_mhz": float(np.median(self.samples)), "sm_max_mhz": self.max_mhz, "reasons": reasons,
-                "samples": len(self.samples), "source": "nvml" if self._nvml else "nvidia-smi"}
+        out = {"sm_mhz": float(np.median(self.samples)), "sm_max_mhz": self.max_mhz, "reasons": reasons,
+               "samples": len(self.samples), "source": "nvml" if self._nvml else "nvidia-smi"}
+        return out
 
 
 # ------------------------------------------------------------------ peaks
@@ -540,6 +542,30 @@ def measure_forms(args, out):
                    "(the same block-steps each; the re-capture after each switch untimed)",
             gpu_launches=per_step * steps, steps=steps, setup_s=setup_s,
             algorithmic_tflops=sum(float(n) * n for n in STUDY_SIZES) * cols * steps / t / 1e12)
+        # roofline of the whole step (casts, the batched solve and every study's sums):
+        # n_i^2 flop per SNP of study i at the tuned tile mode's peak
+        prods = 2 if tune["tile_mode"] == "inverse" else 3
+        pk = (load_measured_peaks().get("bf16_tflops") or 1800.0) / prods
+        forms["batch"]["roofline"] = dict(
+            bound="tensor", achieved=forms["batch"]["algorithmic_tflops"], peak=pk, unit="TFLOP/s",
+            frac=forms["batch"]["algorithmic_tflops"] / pk,
+            peak_basis=f"bf16 dense tensor peak (of measured, burst) / {prods}; achieved over whole steps")
+        # every study's results of one step against the FP64 GPU path on its first 64 SNPs
+        outs = B.solve(blocks)
+        worst = {"b_norm": 0.0, "se_rel": 0.0}
+        for s_, X, o in zip(studies, blocks, outs):
+            with gw.GLS(s_["Phi"], s_["XL"], s_["y"], 0.6, 1.0, precision="fp64", bs=64) as g64:
+                b64, se64, st64 = g64.solve_block(X[:, :64])
+                g64.synchronize()
+            b64, se64 = b64.cpu().numpy(), se64.cpu().numpy()
+            bb, ss = o[0][:, :64].cpu().numpy(), o[1][:, :64].cpu().numpy()
+            okc = st64.cpu().numpy() == 0
+            worst["b_norm"] = max(worst["b_norm"], float(np.max(np.linalg.norm(bb[:, okc] - b64[:, okc], axis=0) /
+                                                                  np.linalg.norm(b64[:, okc], axis=0))))
+            worst["se_rel"] = max(worst["se_rel"], float(np.max(np.abs(ss[:, okc] - se64[:, okc]) / se64[:, okc])))
+        forms["batch"]["error_vs_fp64_path"] = dict(
+            worst, sample="first 64 SNPs of every study, one batched step against the FP64 GPU path "
+                          "(itself held to 1e-10 of the oracle by the tests)")
         # --- the same batch out of core: each study's dosages in its own file (its block
         # written REPS times), streamed disk -> pinned host (a reader thread per study) -> GPU
         reps_f = 4
