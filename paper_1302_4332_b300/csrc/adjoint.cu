@@ -156,10 +156,7 @@ __global__ void __launch_bounds__(256) exact_adjoint_kernel(
   // int64 sum; otherwise T_r^2 summed in FP64.
   long long p1 = 0, p2 = 0, p3 = 0, shh = 0, shl = 0, sll = 0;
   double qq = 0.0;
-#pragma unroll 4
-  for (int r = lane; r < n; r += 32) {
-    const int xi = __half2int_rn(x[r]);
-    const int a1 = __ldcs(cc + r), a2 = __ldcs(cc + RS + r), a3 = __ldcs(cc + 2 * RS + r);
+  auto row = [&](int xi, int a1, int a2, int a3) {
     p1 += (long long)xi * a1;
     p2 += (long long)xi * a2;
     p3 += (long long)xi * a3;
@@ -173,6 +170,25 @@ __global__ void __launch_bounds__(256) exact_adjoint_kernel(
       const double u = (double)T;
       qq = fma(u, u, qq);
     }
+  };
+  // four rows a lane per step: 16-byte loads of each slab's products and 8 of
+  // x' (C's rows are 16-byte aligned: ldc and RS are multiples of 256, and
+  // x''s of 8: ldx = n_pad).  Rows n .. n_pad - 1 add nothing: x' is 0 there
+  // and so are the products (W is zero on the padding).
+  const int4* c1 = reinterpret_cast<const int4*>(cc);
+  const int4* c2 = reinterpret_cast<const int4*>(cc + RS);
+  const int4* c3 = reinterpret_cast<const int4*>(cc + 2 * RS);
+  const uint2* x4 = reinterpret_cast<const uint2*>(x);
+#pragma unroll 2
+  for (int r4 = lane; r4 < (n_pad >> 2); r4 += 32) {
+    const int4 A1 = __ldcs(c1 + r4), A2 = __ldcs(c2 + r4), A3 = __ldcs(c3 + r4);
+    const uint2 xv = __ldg(x4 + r4);
+    const __half2 h01 = *reinterpret_cast<const __half2*>(&xv.x);
+    const __half2 h23 = *reinterpret_cast<const __half2*>(&xv.y);
+    row(__half2int_rn(__low2half(h01)), A1.x, A2.x, A3.x);
+    row(__half2int_rn(__high2half(h01)), A1.y, A2.y, A3.y);
+    row(__half2int_rn(__low2half(h23)), A1.z, A2.z, A3.z);
+    row(__half2int_rn(__high2half(h23)), A1.w, A2.w, A3.w);
   }
 #pragma unroll
   for (int o = 16; o; o >>= 1) {
