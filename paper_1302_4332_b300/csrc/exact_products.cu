@@ -557,29 +557,22 @@ __global__ void __launch_bounds__(256) exact_dy_part_kernel(const __half* __rest
     wl[i] = (float)(w - (double)h);
   }
   __syncthreads();
-  // two rows a thread (4-byte loads of x'; rows up to n_pad exist, x' = 0 past n)
-  const int r = 2 * (blockIdx.x * blockDim.x + threadIdx.x);
+  const int r = blockIdx.x * blockDim.x + threadIdx.x;
   if (r >= n) return;
-  const __half2* x = reinterpret_cast<const __half2*>(xc + r + (int64_t)i0 * ldc);
-  const int64_t ld2 = ldc / 2;
-  float sh0 = 0.f, sl0 = 0.f, sh1 = 0.f, sl1 = 0.f;
-  auto step = [](float& sh, float& sl, float xv, float h, float l) {
-    const float pr = xv * h;
-    const float pe = fmaf(xv, h, -pr);  // exact error of the product
-    const float t = sh + pr;            // TwoSum(sh, pr)
+  const __half* x = xc + r + (int64_t)i0 * ldc;
+  float sh = 0.f, sl = 0.f;
+#pragma unroll 4
+  for (int i = 0; i < i1 - i0; ++i) {
+    const float xv = __half2float(x[(int64_t)i * ldc]);
+    const float pr = xv * wh[i];
+    const float pe = fmaf(xv, wh[i], -pr);  // exact error of the product
+    const float t = sh + pr;                // TwoSum(sh, pr)
     const float bv = t - sh;
     const float err = (sh - (t - bv)) + (pr - bv);
     sh = t;
-    sl += err + pe + xv * l;
-  };
-#pragma unroll 4
-  for (int i = 0; i < i1 - i0; ++i) {
-    const float2 xv = __half22float2(x[(int64_t)i * ld2]);
-    step(sh0, sl0, xv.x, wh[i], wl[i]);
-    step(sh1, sl1, xv.y, wh[i], wl[i]);
+    sl += err + pe + xv * wl[i];
   }
-  part[(int64_t)blockIdx.y * n + r] = (double)sh0 + (double)sl0;
-  if (r + 1 < n) part[(int64_t)blockIdx.y * n + r + 1] = (double)sh1 + (double)sl1;
+  part[(int64_t)blockIdx.y * n + r] = (double)sh + (double)sl;
 }
 
 // z = the chunk sums in order (rows < n; rows n .. n_pad - 1 zero)
@@ -608,21 +601,7 @@ __global__ void __launch_bounds__(256) exact_dy_apply_kernel(const double* __res
   double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
   const int n2 = n_pad / 2;  // z is zero past n
   int c = lane;
-  for (; c + 224 < n2; c += 256) {  // eight 16-byte loads in flight per lane
-    double2 a[8], b[8];
-#pragma unroll
-    for (int k = 0; k < 8; ++k) a[k] = __ldcs(w + c + 32 * k);
-#pragma unroll
-    for (int k = 0; k < 8; ++k) b[k] = zz[c + 32 * k];
-#pragma unroll
-    for (int k = 0; k < 8; k += 2) {
-      s0 = fma(a[k].x, b[k].x, s0);
-      s1 = fma(a[k].y, b[k].y, s1);
-      s2 = fma(a[k + 1].x, b[k + 1].x, s2);
-      s3 = fma(a[k + 1].y, b[k + 1].y, s3);
-    }
-  }
-  for (; c + 96 < n2; c += 128) {  // four
+  for (; c + 96 < n2; c += 128) {  // four 16-byte loads in flight per lane
     double2 a[4], b[4];
 #pragma unroll
     for (int k = 0; k < 4; ++k) a[k] = __ldcs(w + c + 32 * k);
@@ -907,7 +886,7 @@ cudaError_t exact_adjoint_block(ExactProducts* E, const int8_t* X, int64_t ldx, 
                                      E->q, ncols, h, sigma2, E->xmax, chi2, dh, wv, dh_accum, uT, s)) != cudaSuccess)
     return e;
   const int p1 = E->q + 1, nchunks = (ncols + EX_DY_CHUNK - 1) / EX_DY_CHUNK;
-  exact_dy_part_kernel<<<dim3((E->n + 511) / 512, nchunks), 256, 0, s>>>(E->xc, E->n_pad, wv, p1, E->n, ncols,
+  exact_dy_part_kernel<<<dim3((E->n + 255) / 256, nchunks), 256, 0, s>>>(E->xc, E->n_pad, wv, p1, E->n, ncols,
                                                                          E->part);
   exact_dy_z_kernel<<<(E->n_pad + 255) / 256, 256, 0, s>>>(E->part, nchunks, E->n, E->n_pad, E->z);
   exact_dy_apply_kernel<<<(E->n + 7) / 8, 256, 0, s>>>(E->W, E->n_pad, E->n, E->z, What, uT, E->q, dy_accum);
