@@ -63,7 +63,8 @@ __device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
 // Polls between two looks at the abort flag and the clock in a bounded wait.
 // The abort flag is a global load (hundreds of cycles): read after every poll
 // it would delay the waiter's reaction to the event it waits for by that much
-// (measured: the exact product kernel's single MMA-issuing thread lost ~10 %).
+// (measured on the pair product, whose producer waits on tile flags: 0.986 ->
+// 0.969 ms a block with the flag read every 32 polls).
 constexpr uint32_t WAIT_CHECK_EVERY = 32;
 
 // Polls `done` until it holds: true; false when the launch is aborting or after
