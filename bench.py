@@ -330,10 +330,10 @@ def run_ours(args, rank, world, local_rank, dist):
         t_init = time.time()
         sg = STRIP_GROUP if args.strip_group is None else args.strip_group
         tc_split = path in SPLIT_PATHS  # the tile options apply to the split paths only
-        g = gw.GLS(s["Phi"], s["XL"], s["y"], w["h"], w["sigma2"], precision=path, bs=bs,
-                   strip_group=sg if tc_split else 0,
+        gkw = dict(precision=path, bs=bs, strip_group=sg if tc_split else 0,
                    tiles=(tiles if path != "f16x2" or tiles == "auto" else "inverse") if tc_split else "auto",
                    separate_sums=args.separate_sums and tc_split)
+        g = gw.GLS(s["Phi"], s["XL"], s["y"], w["h"], w["sigma2"], **gkw)
         init_s = time.time() - t_init
         b = torch.empty((bs, p), dtype=torch.float64, device=dev).T
         se = torch.empty((bs, p), dtype=torch.float64, device=dev).T
@@ -440,11 +440,31 @@ def run_ours(args, rank, world, local_rank, dist):
             for _ in range(steps):
                 g.solve_stream(Xh_np.T, bh.numpy().T, seh.numpy().T, sth.numpy())
             e2e_s = max_over_ranks(time.perf_counter() - t1, dist, dev)
+            h2d_step = (g.h2d_bytes - h0) // steps
+            host_packed = h2d_step < e2e_snps * n  # the library packed the blocks on the host
             res["e2e"] = dict(value=job_rate(world, steps * e2e_snps, e2e_s), unit=UNIT,
-                              h2d_bytes_per_step=(g.h2d_bytes - h0) // steps,
+                              h2d_bytes_per_step=h2d_step,
                               d2h_bytes_per_step=e2e_snps * (2 * p * 8 + 4), snps_per_step=e2e_snps,
                               step=f"one gwas_solve_stream call over {reps} x the {NB} resident blocks "
-                                   "(pinned host memory, int8, one contiguous copy per block)")
+                                   "(int8 dosages in pinned host memory; " +
+                                   ("each block packed to 2-bit codes by the library's host threads while "
+                                    "earlier blocks solve, and sent as such" if host_packed else
+                                    "sent as int8, one contiguous copy per block") + ")",
+                              transport="2-bit codes packed on the host" if host_packed else "int8")
+            if host_packed and (path in SPLIT_PATHS or path == "sliced64"):
+                # the same call with the int8 transport (stream_pack = 0), for comparison
+                with gw.GLS(s["Phi"], s["XL"], s["y"], w["h"], w["sigma2"], stream_pack=0, **gkw) as g8:
+                    g8.solve_stream(Xh_np[:bs].T, bh.numpy()[:bs].T, seh.numpy()[:bs].T, sth.numpy()[:bs])
+                    torch.cuda.synchronize()
+                    h0 = g8.h2d_bytes
+                    t1 = time.perf_counter()
+                    for _ in range(steps):
+                        g8.solve_stream(Xh_np.T, bh.numpy().T, seh.numpy().T, sth.numpy())
+                    e8_s = max_over_ranks(time.perf_counter() - t1, dist, dev)
+                    res["e2e_int8_transport"] = dict(
+                        value=job_rate(world, steps * e2e_snps, e8_s), unit=UNIT,
+                        h2d_bytes_per_step=(g8.h2d_bytes - h0) // steps, snps_per_step=e2e_snps,
+                        step="the same calls with gwas_config.stream_pack = 0 (int8 over the link)")
             if path in SPLIT_PATHS or path == "sliced64":
                 # the same SNPs held 2-bit packed in pinned host memory (hard calls
                 # 0..3, four to a byte): the link carries ceil(n/4) bytes per SNP
@@ -1100,6 +1120,14 @@ def main():
                      "frac": hr["snps_per_s"] / (slower * world) if slower else None,
                      "e2e_frac": (hr["e2e"]["value"] / (slower * world)) if slower and hr.get("e2e") else None,
                      "basis": "per GPU: n^2 flop/SNP at the roofline peak; n B/SNP over the measured pinned H2D link"}
+    if h2d and trsm_bound and hr.get("e2e", {}).get("transport", "int8") != "int8":
+        # the e2e call sent 2-bit codes packed on the host: its link term is ceil(n/4) B/SNP
+        link_p = h2d * 1e9 / ((n_ + 3) // 4)
+        e2e_bound = min(trsm_bound, link_p)
+        path_roofline["e2e_frac"] = hr["e2e"]["value"] / (e2e_bound * world)
+        path_roofline["e2e_bound"] = "trsm" if e2e_bound == trsm_bound else "h2d (2-bit codes)"
+        path_roofline["e2e_basis"] = ("the e2e call's blocks crossed the link as 2-bit codes packed on the host: "
+                                      "the slower of the solve term and ceil(n/4) B/SNP over the link")
     if h2d and hr.get("e2e_packed_input") and trsm_bound:
         packed_bound = min(trsm_bound, h2d * 1e9 / ((n_ + 3) // 4))
         path_roofline["packed_input"] = {

@@ -130,6 +130,15 @@ typedef struct {
   int single_piece;  /* precision studies only (inverse tile mode): 1 keeps L^-1 as its hi piece alone
                         (its lo piece zeroed: one BF16, TF32 or row-scaled FP16 rounding of L^-1);
                         b and se then carry that rounding, far above the split forms' 1e-5 */
+  int stream_pack;   /* how gwas_solve_stream moves int8 host columns to the device: -1 (default) packs
+                        each block whose values all lie in 0..3 into 2-bit codes on the host (the
+                        encoding of gwas_pack_dosages2; a quarter of the link's bytes, unpacked on the
+                        GPU) when the host CPU has AVX-512 (BW, VL), where a pool of host threads packs
+                        faster than the link carries int8, else copies int8; 0 always copies int8; 1
+                        packs wherever the values allow.  A block with any other value crosses as int8.
+                        Results are identical either way.  The pool (one thread per host core, created
+                        on the first packed call) and ring_depth pinned host slots of ceil(n/4)
+                        (rounded up to 16) x bs bytes belong to the context */
 } gwas_config;
 
 enum {

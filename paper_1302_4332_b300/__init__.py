@@ -71,7 +71,7 @@ class _Config(ctypes.Structure):
     _fields_ = [("precision", ctypes.c_int), ("bs", ctypes.c_int), ("ring_depth", ctypes.c_int),
                 ("device", ctypes.c_int), ("strip_group", ctypes.c_int), ("tile_mode", ctypes.c_int),
                 ("traits", ctypes.c_int), ("separate_sums", ctypes.c_int),
-                ("single_piece", ctypes.c_int)]
+                ("single_piece", ctypes.c_int), ("stream_pack", ctypes.c_int)]
 
 
 _lib = None
@@ -318,12 +318,15 @@ class GLS:
     row-scaled FP16 pieces of L^-1) for the blocked triangular solve, or
     "sliced64" (FP64-class results from exact integer products of a sliced
     M^-1 on the tensor cores; tile options do not apply).
+    stream_pack: how solve_stream moves int8 host columns (-1: 2-bit codes
+    packed by host threads when the CPU has AVX-512, 0: int8, 1: packed
+    wherever the values lie in 0..3); results are identical either way.
     """
 
     def __init__(self, phi_or_L, XL, y, h: float, sigma2: float = 1.0, *, precision: str = "fp64",
                  bs: int = 4096, ring_depth: int = 3, is_L: bool = False, device: int = -1, stream=None,
                  strip_group: int = 0, tiles: str = "auto", separate_sums: bool = False,
-                 single_piece: bool = False):
+                 single_piece: bool = False, stream_pack: int = -1):
         lib = load()
         n = int(np.shape(y)[0]) if not _is_torch(y) else int(y.shape[0])
         q = 0 if XL is None else (int(XL.shape[1]) if np.ndim(XL) == 2 or _is_torch(XL) else 1)
@@ -349,6 +352,7 @@ class GLS:
         cfg.traits = self.t
         cfg.separate_sums = int(bool(separate_sums))
         cfg.single_piece = int(bool(single_piece))
+        cfg.stream_pack = int(stream_pack)
         self.precision, self.bs = precision, int(bs)
         stream_p = None
         if stream is not None:

@@ -74,6 +74,12 @@ struct gwas_ctx {
   // 2-bit packed input (gwas_solve_stream_packed; set up on its first call)
   int64_t ldp = 0;                   // packed bytes per column in a device slot (ceil(n/4) rounded up to 16)
   std::vector<uint8_t*> dpack;       // ring_depth device slots of ldp x bs bytes
+  // int8 host columns packed by host threads in gwas_solve_stream (gwas_config.stream_pack;
+  // the pool and the pinned slots are made on the first packed call)
+  bool stream_pack = false;
+  PackPool* pack_pool = nullptr;
+  std::vector<uint8_t*> hpack;         // ring_depth pinned host slots of ldp x bs bytes
+  std::vector<cudaEvent_t> ev_staged;  // the copy out of hpack[slot] has finished
   int64_t h2d_bytes = 0;             // SNP-block bytes copied host -> device
   void* static_scratch = nullptr;  // device address of the fixed scratch array (gwas_solve_block_static)
   int64_t launches = 0;
@@ -451,6 +457,9 @@ void free_all(gwas_ctx* c) {
   cudaFree(c->AopT); cudaFree(c->Xhat); cudaFree(c->What); cudaFree(c->GH); cudaFree(c->adj);
   cudaFreeHost(c->h_b); cudaFreeHost(c->h_se); cudaFreeHost(c->h_status);
   for (auto* p : c->dpack) cudaFree(p);
+  for (auto* p : c->hpack) cudaFreeHost(p);
+  for (auto ev : c->ev_staged) cudaEventDestroy(ev);
+  pack_pool_destroy(c->pack_pool);
   if (c->tcs) tc::destroy(c->tcs);
   exact_destroy(c->exact);
   exact_destroy(c->sliced);
@@ -471,6 +480,7 @@ void gwas_config_default(gwas_config* cfg) {
   cfg->bs = 4096;
   cfg->ring_depth = 3;
   cfg->device = -1;
+  cfg->stream_pack = -1;
 }
 
 const char* gwas_strerror(int code) {
@@ -507,6 +517,7 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
       (cfg.tile_mode != GWAS_TILES_AUTO || cfg.strip_group != 0 || cfg.separate_sums != 0 || cfg.single_piece != 0))
     return GWAS_ERR_ARG;
   if (cfg.single_piece != 0 && cfg.single_piece != 1) return GWAS_ERR_ARG;
+  if (cfg.stream_pack < -1 || cfg.stream_pack > 1) return GWAS_ERR_ARG;
   if (cfg.single_piece && (cfg.precision == GWAS_FP64 ||
                            (cfg.tile_mode != GWAS_TILES_AUTO && cfg.tile_mode != GWAS_TILES_INVERSE)))
     return GWAS_ERR_ARG;
@@ -544,6 +555,7 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
     ctx->prec = cfg.precision; ctx->bs = cfg.bs; ctx->ring_depth = cfg.ring_depth;
     ctx->separate_sums = cfg.separate_sums != 0;
     ctx->single_piece = cfg.single_piece != 0;
+    ctx->stream_pack = cfg.stream_pack == 1 || (cfg.stream_pack == -1 && host_pack_fast());
     ctx->h = h; ctx->sigma2 = sigma2;
     const size_t np = (size_t)ctx->n_pad, n2 = np * np;
     CK(dmalloc(&ctx->L, sizeof(double) * n2));
@@ -748,9 +760,39 @@ static int ensure_packed_slots(gwas_ctx* ctx) {
   return GWAS_OK;
 }
 
+// The 2-bit transport's host side for int8 columns: pinned slots, their
+// events and the packing threads, made on the first packed call (nothing
+// half-made stays behind; a later call retries).
+static int ensure_host_pack(gwas_ctx* ctx) {
+  if (!ctx->hpack.empty()) return GWAS_OK;
+  const int R = ctx->ring_depth;
+  std::vector<uint8_t*> slots(R, nullptr);
+  std::vector<cudaEvent_t> evs(R, nullptr);
+  cudaError_t e = cudaSuccess;
+  for (int s = 0; s < R && e == cudaSuccess; ++s) {
+    e = cudaMallocHost(&slots[s], (size_t)ctx->ldp * ctx->bs);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&evs[s], cudaEventDisableTiming);
+  }
+  if (e != cudaSuccess) {
+    for (auto* q : slots)
+      if (q) cudaFreeHost(q);
+    for (auto ev : evs)
+      if (ev) cudaEventDestroy(ev);
+    return fail(ctx, e == cudaErrorMemoryAllocation ? GWAS_ERR_NOMEM : GWAS_ERR_CUDA, "host packing slots: %s",
+                cudaGetErrorString(e));
+  }
+  ctx->hpack = std::move(slots);
+  ctx->ev_staged = std::move(evs);
+  ctx->pack_pool = pack_pool_create();
+  return GWAS_OK;
+}
+
 // The whole-study stream over host columns: int8 (ld = ldx bytes per column)
-// or 2-bit packed (ld = bytes per packed column, unpacked into the ring slot
-// on the GPU).
+// or 2-bit packed (ld = bytes per packed column).  Int8 columns cross the link
+// as int8, or -- with gwas_config.stream_pack -- block by block as 2-bit codes
+// packed by host threads while the GPU solves earlier blocks (a block holding
+// any value outside 0..3 goes as int8).  Packed blocks are unpacked on the GPU
+// (into the ring slot, or by the split inverse form's cast itself).
 static int stream_impl(gwas_ctx* ctx, const void* host, bool packed, int64_t ldx, int64_t m, double* b_host,
                        double* se_host, int* status_host) {
   if (!ctx) return GWAS_ERR_ARG;
@@ -779,8 +821,13 @@ static int stream_impl(gwas_ctx* ctx, const void* host, bool packed, int64_t ldx
     return GWAS_OK;
   };
   const uint8_t* src0 = static_cast<const uint8_t*>(host);
-  if (packed) {
+  const bool host_pack = !packed && ctx->stream_pack;
+  if (packed || host_pack) {
     const int rc0 = ensure_packed_slots(ctx);
+    if (rc0 != GWAS_OK) return rc0;
+  }
+  if (host_pack) {
+    const int rc0 = ensure_host_pack(ctx);
     if (rc0 != GWAS_OK) return rc0;
   }
   // Int8 columns whose stride is a multiple of 16 bytes and fits a ring slot
@@ -789,25 +836,44 @@ static int stream_impl(gwas_ctx* ctx, const void* host, bool packed, int64_t ldx
   // columns are repacked to the slot's stride by a pitched copy.  Packed
   // columns likewise into a slot of ldp bytes per column.
   const int64_t slot_ld_in = packed ? ctx->ldp : ctx->n_pad;
-  // the split inverse form's cast reads the packed columns themselves (no unpack kernel)
-  const bool fused = packed && ctx->tcs && tc::packed_ok(ctx->tcs);
+  // the split inverse form's cast reads packed columns themselves (no unpack kernel)
+  const bool fused_ok = ctx->tcs && tc::packed_ok(ctx->tcs);
   const int64_t width = packed ? nb : ctx->n;
   const bool flat = (ldx % 16) == 0 && ldx <= slot_ld_in;
   const int64_t ld_dev = flat ? ldx : slot_ld_in;  // the block's leading dimension on the device
+  std::vector<char> pk(R, packed ? 1 : 0);          // the block in slot s crossed the link as 2-bit codes
+  std::vector<int64_t> ld_slot(R, ld_dev);          // and its leading dimension in its device slot
   auto enqueue_copy = [&](int64_t blk) -> int {
     const int slot = (int)(blk % R), nc = cols_of(blk);
-    void* dst = packed ? static_cast<void*>(ctx->dpack[slot]) : static_cast<void*>(ctx->ring[slot]);
     const uint8_t* src = src0 + blk * bs * ldx;
+    bool hp = false;
+    if (host_pack) {
+      // hpack[slot] last left for the device R blocks ago; packed while the GPU solves earlier blocks
+      CK(cudaEventSynchronize(ctx->ev_staged[slot]));
+      hp = pack_pool_run(ctx->pack_pool, reinterpret_cast<const int8_t*>(src), ldx, ctx->n, nc, ctx->hpack[slot],
+                         ctx->ldp);
+    }
     CK(cudaStreamWaitEvent(ctx->copy_stream, ctx->ev_free[slot], 0));
     StageMark mk(ctx, GWAS_STAGE_H2D, ctx->copy_stream);
-    if (flat) {  // the last column ends after its width-th byte
-      CK(cudaMemcpyAsync(dst, src, (size_t)((nc - 1) * ldx + width), cudaMemcpyHostToDevice, ctx->copy_stream));
-      ctx->h2d_bytes += (nc - 1) * ldx + width;
+    if (hp) {
+      CK(cudaMemcpyAsync(ctx->dpack[slot], ctx->hpack[slot], (size_t)(ctx->ldp * nc), cudaMemcpyHostToDevice,
+                         ctx->copy_stream));
+      CK(cudaEventRecord(ctx->ev_staged[slot], ctx->copy_stream));
+      ctx->h2d_bytes += ctx->ldp * nc;
+      ld_slot[slot] = ctx->ldp;
     } else {
-      CK(cudaMemcpy2DAsync(dst, (size_t)slot_ld_in, src, (size_t)ldx, (size_t)width, (size_t)nc,
-                           cudaMemcpyHostToDevice, ctx->copy_stream));
-      ctx->h2d_bytes += width * nc;
+      void* dst = packed ? static_cast<void*>(ctx->dpack[slot]) : static_cast<void*>(ctx->ring[slot]);
+      if (flat) {  // the last column ends after its width-th byte
+        CK(cudaMemcpyAsync(dst, src, (size_t)((nc - 1) * ldx + width), cudaMemcpyHostToDevice, ctx->copy_stream));
+        ctx->h2d_bytes += (nc - 1) * ldx + width;
+      } else {
+        CK(cudaMemcpy2DAsync(dst, (size_t)slot_ld_in, src, (size_t)ldx, (size_t)width, (size_t)nc,
+                             cudaMemcpyHostToDevice, ctx->copy_stream));
+        ctx->h2d_bytes += width * nc;
+      }
+      ld_slot[slot] = ld_dev;
     }
+    pk[slot] = packed || hp;
     CK(cudaEventRecord(ctx->ev_copied[slot], ctx->copy_stream));
     return GWAS_OK;
   };
@@ -815,14 +881,17 @@ static int stream_impl(gwas_ctx* ctx, const void* host, bool packed, int64_t ldx
   for (int s = 0; s < R; ++s) CK(cudaEventRecord(ctx->ev_free[s], ctx->stream));
   int rc;
   int64_t next_copy = 0;
-  for (; next_copy < std::min<int64_t>(R, nblk); ++next_copy)
+  // copies ahead of the first solve: the whole ring, or -- when the host packs
+  // each block first -- one block, so that the GPU starts after one packing
+  for (; next_copy < std::min<int64_t>(host_pack ? 1 : R, nblk); ++next_copy)
     if ((rc = enqueue_copy(next_copy)) != GWAS_OK) return rc;
   for (int64_t blk = 0; blk < nblk; ++blk) {
     const int slot = (int)(blk % R), nc = cols_of(blk);
     CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_copied[slot], 0));
-    if (packed && !fused) {  // the 2-bit codes into the ring slot as int8
+    const bool fused = pk[slot] && fused_ok;
+    if (pk[slot] && !fused) {  // the 2-bit codes into the ring slot as int8
       StageMark mk(ctx, GWAS_STAGE_H2D, ctx->stream);
-      CK(launch_unpack2(ctx->dpack[slot], ld_dev, ctx->n, nc, ctx->ring[slot], ctx->n_pad, ctx->stream));
+      CK(launch_unpack2(ctx->dpack[slot], ld_slot[slot], ctx->n, nc, ctx->ring[slot], ctx->n_pad, ctx->stream));
       ctx->launches += 1;
     }
     double* ob = ctx->d_b + (size_t)slot * T * p * bs;
@@ -830,8 +899,8 @@ static int stream_impl(gwas_ctx* ctx, const void* host, bool packed, int64_t ldx
     int* ost = ctx->d_status + (size_t)slot * bs;
     // the slot's outputs were copied out R blocks ago (on the result stream)
     if (blk >= R) CK(cudaStreamWaitEvent(ctx->stream, ctx->ev_out[slot], 0));
-    rc = fused ? run_block(ctx, ctx->dpack[slot], true, ld_dev, nc, ob, ose, ost, true)
-               : run_block(ctx, ctx->ring[slot], true, packed ? ctx->n_pad : ld_dev, nc, ob, ose, ost);
+    rc = fused ? run_block(ctx, ctx->dpack[slot], true, ld_slot[slot], nc, ob, ose, ost, true)
+               : run_block(ctx, ctx->ring[slot], true, pk[slot] ? ctx->n_pad : ld_slot[slot], nc, ob, ose, ost);
     if (rc != GWAS_OK) return rc;
     CK(cudaEventRecord(ctx->ev_free[slot], ctx->stream));
     {  // results out on their own stream, overlapping the next block's solve
@@ -847,10 +916,8 @@ static int stream_impl(gwas_ctx* ctx, const void* host, bool packed, int64_t ldx
                          cudaMemcpyDeviceToHost, ctx->out_stream));
     }
     CK(cudaEventRecord(ctx->ev_out[slot], ctx->out_stream));
-    if (next_copy < nblk) {
+    for (; next_copy < nblk && next_copy <= blk + R; ++next_copy)  // the ring refilled up to R blocks ahead
       if ((rc = enqueue_copy(next_copy)) != GWAS_OK) return rc;
-      ++next_copy;
-    }
     // results of the previous block: its copy-out overlaps this block's solve
     if (blk >= 1 && (rc = drain(blk - 1)) != GWAS_OK) return rc;
   }

@@ -220,6 +220,14 @@ cudaError_t launch_exact_adjoint_sums(const int32_t* C, int64_t ldc, int RS, con
 // int8 slot (leading dimension ldx, a multiple of 16, 16-byte aligned; rows
 // n .. 16 ceil(n/16) - 1 written as 0).
 bool pack2_columns(const int8_t* X, int64_t ldx, int n, int c0, int c1, uint8_t* P, int64_t ldp);
+// Whether this host packs with AVX-512 (BW, VL), fast enough to pay inside the
+// int8 stream; and a pool of persistent host threads (one per core with the
+// caller) packing a block's columns in parallel (false: a value outside 0..3).
+bool host_pack_fast();
+struct PackPool;
+PackPool* pack_pool_create();
+bool pack_pool_run(PackPool* p, const int8_t* X, int64_t ldx, int n, int ncols, uint8_t* P, int64_t ldp);
+void pack_pool_destroy(PackPool* p);
 cudaError_t launch_unpack2(const uint8_t* P, int64_t ldp, int n, int ncols, int8_t* X, int64_t ldx, cudaStream_t s);
 cudaError_t launch_log_diag(const double* L, int64_t ld, int n, double* out, cudaStream_t s);
 cudaError_t launch_col_sumsq(const double* X, int64_t ld, int n, int ncols, double* out, cudaStream_t s);

@@ -99,7 +99,7 @@ def _pack_reference(X):
     return (Xp[0::4] + 4 * Xp[1::4] + 16 * Xp[2::4] + 64 * Xp[3::4]).astype(np.uint8)
 
 
-@pytest.mark.parametrize("n", [1, 3, 4, 5, 7, 8, 9, 15, 16, 17, 129, 1000, 10001])
+@pytest.mark.parametrize("n", [1, 3, 4, 5, 7, 8, 9, 15, 16, 17, 63, 64, 65, 127, 128, 129, 1000, 10001])
 def test_pack_dosages2_encoding(lib, n):
     """The stream transport's host packing (host code, no device needed) against
     the encoding written out, on ragged n, values 0..3 (3 included)."""

@@ -154,8 +154,8 @@ def test_stream_packed_input(small_study, prec):
     nb = (n + 3) // 4
     Pw = np.zeros((nb + 3, m), dtype=np.uint8, order="F")
     Pw[:nb] = P
-    with gw.GLS(s["Phi"], s["XL"], s["y"], s["h"], s["sigma2"], precision=prec, bs=bs) as g:
-        ref = g.solve_stream(Xh)
+    with gw.GLS(s["Phi"], s["XL"], s["y"], s["h"], s["sigma2"], precision=prec, bs=bs, stream_pack=0) as g:
+        ref = g.solve_stream(Xh)  # int8 over the link
         h0 = g.h2d_bytes
         out = g.solve_stream_packed(P)
         moved = g.h2d_bytes - h0
@@ -181,7 +181,7 @@ def test_stream_packed_ragged_rows_and_padding_bits(prec):
     X = np.asfortranarray(gwas_synth.dosages(n, 0, m, seed=9))
     P = gw.pack_dosages2(X)
     P[-1, :] |= 0xFC  # rows 301..303 of the last byte: garbage
-    with gw.GLS(s["Phi"], s["XL"], s["y"], 0.6, 1.0, precision=prec, bs=128) as g:
+    with gw.GLS(s["Phi"], s["XL"], s["y"], 0.6, 1.0, precision=prec, bs=128, stream_pack=0) as g:
         ref = g.solve_stream(X)
         out = g.solve_stream_packed(P)
     for a_, b_ in zip(ref, out):
@@ -199,6 +199,37 @@ TILES = ("single", "pair_mma", "inverse")
 SPLIT_TILES = [(p, t) for p in SPLITS for t in TILES if p != "f16x2" or t == "inverse"]
 FULL_CASES = [("fp64", "auto"), ("sliced64", "auto")] + [(p, t) for p in SPLITS for t in ("auto",) + TILES
                                                           if p != "f16x2" or t in ("auto", "inverse")]
+
+
+@pytest.mark.parametrize("prec,tiles", [("fp64", "auto"), ("f16x2", "auto"), ("bf16x3", "auto"),
+                                        ("bf16x3", "pair_mma"), ("sliced64", "auto")])
+def test_stream_host_packing(prec, tiles):
+    """gwas_solve_stream with stream_pack = 1: int8 host blocks whose values lie
+    in 0..3 are packed by the host threads and cross the link as 2-bit codes
+    (the split inverse form reads them in its cast, the others unpack them);
+    a block holding another value crosses as int8.  Results bit for bit those
+    of the int8 transport; the link's bytes counted per block."""
+    n, bs = 1001, 256
+    m = 3 * bs + 77  # four blocks, the last ragged
+    s = gwas_synth.study(n, 4, 2 * n, 0.6, 1.0, seed=21)
+    X = np.asfortranarray(gwas_synth.dosages(n, 0, m, seed=21))
+    X[5, 300] = 3    # block 1: still packable
+    X[9, 600] = 5    # block 2: int8
+    nb, ldp = (n + 3) // 4, ((n + 3) // 4 + 15) // 16 * 16
+    outs, moved = {}, {}
+    for mode in (0, 1):
+        with gw.GLS(s["Phi"], s["XL"], s["y"], 0.6, 1.0, precision=prec, bs=bs, tiles=tiles,
+                    stream_pack=mode) as g:
+            h0 = g.h2d_bytes
+            outs[mode] = g.solve_stream(X)
+            moved[mode] = g.h2d_bytes - h0
+            again = g.solve_stream(X)  # the pool and slots reused
+            for a_, b_ in zip(outs[mode], again):
+                assert np.array_equal(a_, b_, equal_nan=True)
+    for a_, b_ in zip(outs[0], outs[1]):
+        assert np.array_equal(a_, b_, equal_nan=True)
+    assert moved[0] == n * m
+    assert moved[1] == ldp * (2 * bs + 77) + n * bs  # blocks 0, 1, 3 packed; block 2 as int8
 
 
 @pytest.mark.parametrize("prec,tiles", SPLIT_TILES)
