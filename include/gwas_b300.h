@@ -134,8 +134,9 @@ typedef struct {
                         each block whose values all lie in 0..3 into 2-bit codes on the host (the
                         encoding of gwas_pack_dosages2; a quarter of the link's bytes, unpacked on the
                         GPU) when the host CPU has AVX-512 (BW, VL), where a pool of host threads packs
-                        faster than the link carries int8, else copies int8; 0 always copies int8; 1
-                        packs wherever the values allow.  A block with any other value crosses as int8.
+                        faster than the link carries int8, and the solve outruns the int8 link (BF16x3
+                        and F16x2 in the inverse tile mode), else copies int8; 0 always copies int8;
+                        1 packs wherever the values allow.  A block with any other value crosses as int8.
                         Results are identical either way.  The pool (one thread per host core, created
                         on the first packed call) and ring_depth pinned host slots of ceil(n/4)
                         (rounded up to 16) x bs bytes belong to the context */

@@ -319,7 +319,8 @@ class GLS:
     "sliced64" (FP64-class results from exact integer products of a sliced
     M^-1 on the tensor cores; tile options do not apply).
     stream_pack: how solve_stream moves int8 host columns (-1: 2-bit codes
-    packed by host threads when the CPU has AVX-512, 0: int8, 1: packed
+    packed by host threads when the CPU has AVX-512 and the solve outruns the
+    int8 link, i.e. bf16x3 / f16x2 in the inverse form; 0: int8; 1: packed
     wherever the values lie in 0..3); results are identical either way.
     """
 

@@ -76,7 +76,7 @@ struct gwas_ctx {
   std::vector<uint8_t*> dpack;       // ring_depth device slots of ldp x bs bytes
   // int8 host columns packed by host threads in gwas_solve_stream (gwas_config.stream_pack;
   // the pool and the pinned slots are made on the first packed call)
-  bool stream_pack = false;
+  int stream_pack = 0;  // gwas_config.stream_pack: -1 auto, 0 off, 1 on
   PackPool* pack_pool = nullptr;
   std::vector<uint8_t*> hpack;         // ring_depth pinned host slots of ldp x bs bytes
   std::vector<cudaEvent_t> ev_staged;  // the copy out of hpack[slot] has finished
@@ -555,7 +555,7 @@ int gwas_init(gwas_ctx** out, int n, int p, const double* phi_or_L, int is_L, co
     ctx->prec = cfg.precision; ctx->bs = cfg.bs; ctx->ring_depth = cfg.ring_depth;
     ctx->separate_sums = cfg.separate_sums != 0;
     ctx->single_piece = cfg.single_piece != 0;
-    ctx->stream_pack = cfg.stream_pack == 1 || (cfg.stream_pack == -1 && host_pack_fast());
+    ctx->stream_pack = cfg.stream_pack;
     ctx->h = h; ctx->sigma2 = sigma2;
     const size_t np = (size_t)ctx->n_pad, n2 = np * np;
     CK(dmalloc(&ctx->L, sizeof(double) * n2));
@@ -821,7 +821,12 @@ static int stream_impl(gwas_ctx* ctx, const void* host, bool packed, int64_t ldx
     return GWAS_OK;
   };
   const uint8_t* src0 = static_cast<const uint8_t*>(host);
-  const bool host_pack = !packed && ctx->stream_pack;
+  // auto: where the host packs with AVX-512 and the solve outruns the int8
+  // link (BF16 / FP16 pieces in the inverse form, whose cast reads the codes)
+  const bool outruns_link = ctx->tcs && tc::packed_ok(ctx->tcs) &&
+                            (ctx->prec == GWAS_BF16X3 || ctx->prec == GWAS_F16X2);
+  const bool host_pack =
+      !packed && (ctx->stream_pack == 1 || (ctx->stream_pack == -1 && host_pack_fast() && outruns_link));
   if (packed || host_pack) {
     const int rc0 = ensure_packed_slots(ctx);
     if (rc0 != GWAS_OK) return rc0;
