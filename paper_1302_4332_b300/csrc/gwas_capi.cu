@@ -781,9 +781,15 @@ static int ensure_host_pack(gwas_ctx* ctx) {
     return fail(ctx, e == cudaErrorMemoryAllocation ? GWAS_ERR_NOMEM : GWAS_ERR_CUDA, "host packing slots: %s",
                 cudaGetErrorString(e));
   }
+  PackPool* pool = pack_pool_create();
+  if (!pool) {
+    for (auto* q : slots) cudaFreeHost(q);
+    for (auto ev : evs) cudaEventDestroy(ev);
+    return fail(ctx, GWAS_ERR_NOMEM, "host packing threads could not be started");
+  }
   ctx->hpack = std::move(slots);
   ctx->ev_staged = std::move(evs);
-  ctx->pack_pool = pack_pool_create();
+  ctx->pack_pool = pool;
   return GWAS_OK;
 }
 

@@ -19,6 +19,7 @@
 #include <cstdint>
 #include <cstring>
 #include <mutex>
+#include <new>
 #include <thread>
 #include <vector>
 
@@ -172,11 +173,20 @@ struct PackPool {
   }
 };
 
+void pack_pool_destroy(PackPool* p);
+
+// Null when the threads cannot be started (nothing is left running).
 PackPool* pack_pool_create() {
-  PackPool* p = new PackPool;
+  PackPool* p = new (std::nothrow) PackPool;
+  if (!p) return nullptr;
   const unsigned hc = std::thread::hardware_concurrency();
   const int nw = std::max(0, std::min(31, (int)(hc ? hc : 2) - 1));  // with the caller: one per core
-  for (int k = 0; k < nw; ++k) p->th.emplace_back([p] { p->loop(); });
+  try {
+    for (int k = 0; k < nw; ++k) p->th.emplace_back([p] { p->loop(); });
+  } catch (...) {
+    pack_pool_destroy(p);
+    return nullptr;
+  }
   return p;
 }
 
