@@ -190,9 +190,14 @@ int gwas_solve_block_f64(gwas_ctx *ctx, const double *XR, int64_t ldx, int ncols
  * are cut into blocks of cfg.bs columns and copied into a ring of
  * cfg.ring_depth device slots on a copy stream, overlapping the solve of the
  * previous blocks on the compute stream; results are copied back per block.
+ * With cfg.stream_pack (see gwas_config) a block whose values all lie in 0..3
+ * is packed to 2-bit codes by host threads and crosses the link in a quarter
+ * of the bytes; results are the same either way.
  *   XR_host n x m int8, leading dimension ldx >= n (pinned memory gives full
  *           link speed; pageable memory works through the driver's staging)
  *   b_host, se_host p x m;  status_host m (se_host / status_host may be NULL)
+ * Errors: GWAS_ERR_ARG, GWAS_ERR_CUDA, GWAS_ERR_TIMEOUT, GWAS_ERR_NOMEM (the
+ * packing slots or threads could not be made).
  * Returns when all results are in host memory. */
 int gwas_solve_stream(gwas_ctx *ctx, const int8_t *XR_host, int64_t ldx, int64_t m, double *b_host,
                       double *se_host, int *status_host);
@@ -206,8 +211,9 @@ int gwas_solve_stream(gwas_ctx *ctx, const int8_t *XR_host, int64_t ldx, int64_t
  * unpacked int8 columns; bits of rows past n are ignored.
  *   P_host  ceil(n/4) bytes per column, leading dimension ldp >= ceil(n/4)
  * Other arguments, errors and results as gwas_solve_stream.  (Packing inside
- * the stream does not pay on a host whose cores pack more slowly than the
- * link carries int8: 16 cores packed ~20 GB/s against the link's ~56 GB/s.) */
+ * the stream pays only on a host whose cores pack faster than the link carries
+ * int8: with AVX-512 16 cores pack ~73 GB/s, the scalar form ~20 GB/s, the
+ * link ~56 GB/s; gwas_config.stream_pack chooses.) */
 int gwas_solve_stream_packed(gwas_ctx *ctx, const uint8_t *P_host, int64_t ldp, int64_t m, double *b_host,
                              double *se_host, int *status_host);
 
