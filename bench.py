@@ -234,15 +234,17 @@ def measure_extra_peaks(torch, dev):
 
 
 def source_digest(name: str) -> str:
-    """sha256[:16] of a kernel source file and of every library header it
-    includes (directly or through another header), in a fixed order: a
-    traffic record holds for the kernel only while none of them changed."""
+    """sha256[:16] of a kernel source file and of every header of the library's
+    CUDA sources (csrc/) it includes, directly or through another header, in
+    a fixed order: a traffic record holds for the kernel only while none of
+    them changed.  The public C header (declarations and their documentation,
+    no device code) is not part of it."""
     csrc = os.path.join(ROOT, "paper_1302_4332_b300", "csrc")
     seen, todo = [], [name]
     while todo:
         f = todo.pop(0)
         path = os.path.join(csrc, f)
-        if f in seen or not os.path.exists(path):
+        if f in seen or "/" in f or not os.path.exists(path):
             continue
         seen.append(f)
         for line in open(path, encoding="utf-8", errors="replace"):
