@@ -220,12 +220,14 @@ __global__ void unpack2_kernel(const uint8_t* __restrict__ P, int64_t ldp, int n
 #pragma unroll
   for (int k = 0; k < 4; ++k)
     if (4 * g + k < nb) v |= (uint32_t)p[k] << (8 * k);
-  uint32_t w[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const uint32_t b = (v >> (8 * k)) & 0xFFu;  // rows 16g + 4k .. +3
-    w[k] = (b & 3u) | ((b & 0xCu) << 6) | ((b & 0x30u) << 12) | ((b & 0xC0u) << 18);
-  }
+  // word k = rows 16g + 4k .. +3: the codes of rows 4k + i (i = 0..3, one per
+  // byte k) masked out, then a 4 x 4 byte transpose by byte permutes
+  const uint32_t v0 = v & 0x03030303u, v1 = (v >> 2) & 0x03030303u;
+  const uint32_t v2 = (v >> 4) & 0x03030303u, v3 = (v >> 6) & 0x03030303u;
+  const uint32_t t0 = __byte_perm(v0, v1, 0x5140), t1 = __byte_perm(v2, v3, 0x5140);
+  const uint32_t t2 = __byte_perm(v0, v1, 0x7362), t3 = __byte_perm(v2, v3, 0x7362);
+  uint32_t w[4] = {__byte_perm(t0, t1, 0x5410), __byte_perm(t0, t1, 0x7632), __byte_perm(t2, t3, 0x5410),
+                   __byte_perm(t2, t3, 0x7632)};
   if (16 * g + 16 > n)  // rows past n as 0, whatever bits the packed padding holds
     for (int i = 0; i < 16; ++i)
       if (16 * g + i >= n) w[i >> 2] &= ~(0xFFu << (8 * (i & 3)));

@@ -75,15 +75,16 @@ __device__ __forceinline__ void store_cast16(void* xc, int64_t off, const float 
 }
 
 // 16 rows of a 2-bit packed column (4 bytes, row 4k + i in bits 2i .. 2i+1 of
-// byte k) as the 16 int8 values of an int4.
+// byte k) as the 16 int8 values of an int4: v_i = the codes of rows 4k + i
+// (one per byte k), then a 4 x 4 byte transpose by byte permutes, so that
+// word k holds rows 4k .. 4k+3 (13 operations for the 16 values).
 __device__ __forceinline__ int4 unpack16(uint32_t p) {
-  uint32_t w[4];
-#pragma unroll
-  for (int k = 0; k < 4; ++k) {
-    const uint32_t b = (p >> (8 * k)) & 0xFFu;
-    w[k] = (b & 3u) | ((b & 0xCu) << 6) | ((b & 0x30u) << 12) | ((b & 0xC0u) << 18);
-  }
-  return make_int4((int)w[0], (int)w[1], (int)w[2], (int)w[3]);
+  const uint32_t v0 = p & 0x03030303u, v1 = (p >> 2) & 0x03030303u;
+  const uint32_t v2 = (p >> 4) & 0x03030303u, v3 = (p >> 6) & 0x03030303u;
+  const uint32_t t0 = __byte_perm(v0, v1, 0x5140), t1 = __byte_perm(v2, v3, 0x5140);  // bytes 0, 1
+  const uint32_t t2 = __byte_perm(v0, v1, 0x7362), t3 = __byte_perm(v2, v3, 0x7362);  // bytes 2, 3
+  return make_int4((int)__byte_perm(t0, t1, 0x5410), (int)__byte_perm(t0, t1, 0x7632),
+                   (int)__byte_perm(t2, t3, 0x5410), (int)__byte_perm(t2, t3, 0x7632));
 }
 
 // The same in one read of the column: for n <= 512 * NV each lane holds its
