@@ -201,9 +201,10 @@ FULL_CASES = [("fp64", "auto"), ("sliced64", "auto")] + [(p, t) for p in SPLITS 
                                                           if p != "f16x2" or t in ("auto", "inverse")]
 
 
-@pytest.mark.parametrize("prec,tiles", [("fp64", "auto"), ("f16x2", "auto"), ("bf16x3", "auto"),
-                                        ("bf16x3", "pair_mma"), ("sliced64", "auto")])
-def test_stream_host_packing(prec, tiles):
+@pytest.mark.parametrize("prec,tiles,ring", [("fp64", "auto", 3), ("f16x2", "auto", 3), ("bf16x3", "auto", 3),
+                                             ("bf16x3", "pair_mma", 3), ("sliced64", "auto", 3),
+                                             ("f16x2", "auto", 2)])
+def test_stream_host_packing(prec, tiles, ring):
     """gwas_solve_stream with stream_pack = 1: int8 host blocks whose values lie
     in 0..3 are packed by the host threads and cross the link as 2-bit codes
     (the split inverse form reads them in its cast, the others unpack them);
@@ -219,7 +220,7 @@ def test_stream_host_packing(prec, tiles):
     outs, moved = {}, {}
     for mode in (0, 1):
         with gw.GLS(s["Phi"], s["XL"], s["y"], 0.6, 1.0, precision=prec, bs=bs, tiles=tiles,
-                    stream_pack=mode) as g:
+                    ring_depth=ring, stream_pack=mode) as g:
             h0 = g.h2d_bytes
             outs[mode] = g.solve_stream(X)
             moved[mode] = g.h2d_bytes - h0
