@@ -28,9 +28,9 @@
 // leave ~4e-9 (a CPU emulation of this scheme at n = 300..3000).  A slice times
 // the integer dosages, accumulated by the tensor cores in FP32, is exact while
 // every partial sum stays at most 2^24 in magnitude: one TMEM partial takes at
-// most 2^24 / (2^(B-1) max|x'| 64) operand stages of 64 K (dosages, |x'| <= 2:
-// 256 stages of 10-bit slices, 128 of 11-bit ones; any int8 values: at least
-// one), and the epilogue adds the partials as int32.  The products leave as
+// most 2^24 / (2^(B-1) max|x'| 32) sub-chunks of 32 K (dosages, |x'| <= 2:
+// 512 sub-chunks of 10-bit slices, 256 of 11-bit ones; any int8 values: at
+// least two), and the epilogue adds the partials as int32.  The products leave as
 // int32 and are combined per SNP in FP64 and int64, so the only error left is
 // the slices' representation.
 //
@@ -61,13 +61,15 @@ using tc::TRING;
 
 namespace ex3 {
 constexpr int KCH = 32;                              // FP16 K per sub-chunk: one 64-byte swizzle row
-constexpr int SUB = 2;                               // sub-chunks per stage (64 K a stage, four MMAs)
+constexpr int SUB = 4;                               // sub-chunks per stage (128 K a stage, eight MMAs)
 constexpr int KMMA = 16;                             // K per tcgen05.mma (kind::f16)
 constexpr int CPB = TB / (KCH * SUB);                // stages per 128-wide K-block
 constexpr int A_BYTES = TB * 64;                     // this CTA's 128 rows of a slice, one sub-chunk: 8 KB
 constexpr int B_BYTES = (TN / 2) * 64;               // this CTA's 128 SNP columns, one sub-chunk: 8 KB
-constexpr int STAGE_BYTES = SUB * (A_BYTES + B_BYTES);  // 32 KB: [A_0 | A_1 | B_0 | B_1]
-constexpr int STAGES = 6;
+constexpr int STAGE_BYTES = SUB * (A_BYTES + B_BYTES);  // 64 KB: [A_0 .. A_3 | B_0 .. B_3]
+// Three stages of eight MMAs: the single issuing thread waits on a stage and
+// commits it once per eight MMAs (six stages of four ran 7 % slower).
+constexpr int STAGES = 3;
 constexpr int CHUNK_BYTES = 2048;                    // epilogue store chunk: 32 rows x 16 int32
 constexpr int ST_COLS = 16;
 constexpr int STG_OFF = STAGES * STAGE_BYTES;
@@ -107,13 +109,14 @@ struct Params {
   int ldx;
 };
 
-// Operand stages (64 K each) per TMEM partial so that every partial sum is an
-// integer of magnitude at most 2^24: amax * xmax * 64 * G <= 2^24 (G >= 1 for
-// every int8 block: |x'| <= 255 and amax <= 1024).  `stages`: a unit's most.
-__device__ __forceinline__ int partial_stages(int xmax, int amax, int stages) {
-  if (xmax <= 0) return stages;
-  const long long g = (1LL << 24) / ((long long)amax * xmax * (KCH * SUB));
-  return g < 1 ? 1 : (g > stages ? stages : (int)g);
+// Sub-chunks (32 K each) per TMEM partial so that every partial sum is an
+// integer of magnitude at most 2^24: amax * xmax * 32 * G <= 2^24 (G >= 2 for
+// every int8 block: |x'| <= 255 and amax <= 1024).  `chunks`: a unit's most.
+// A partial may end inside an operand stage.
+__device__ __forceinline__ int partial_chunks(int xmax, int amax, int chunks) {
+  if (xmax <= 0) return chunks;
+  const long long g = (1LL << 24) / ((long long)amax * xmax * KCH);
+  return g < 1 ? 1 : (g > chunks ? chunks : (int)g);
 }
 
 // The int32 totals hold amax * xmax * n_pad at most: beyond 2^31 the block is refused.
@@ -178,7 +181,7 @@ __global__ void __launch_bounds__(THREADS, 1) exact_product_kernel(const __grid_
   const bool ok_range = in_range(xmax, b.amax, b.P);
   if (!ok_range && blockIdx.x == 0 && threadIdx.x == 0) atomicCAS(&st->err, DEV_OK, DEV_ERR_RANGE);
   const int ntiles = ok_range ? b.ntiles : 0;
-  const int G = partial_stages(xmax, b.amax, b.P * CPB);  // operand stages per TMEM partial
+  const int G = partial_chunks(xmax, b.amax, b.P * CPB * SUB);  // sub-chunks per TMEM partial
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -274,25 +277,25 @@ __global__ void __launch_bounds__(THREADS, 1) exact_product_kernel(const __grid_
         if (!leader) continue;
         const int nst = unit_of(b, t).kend * CPB;  // the unit's operand stages
         bool ok = true;
-        int a = 0, left = 0;  // stages left for the current partial (a counter: no division per stage)
+        int a = 0, left = 0;  // sub-chunks left for the current partial (a counter: no division)
         uint32_t d = 0, accumulate = 0;
-        for (int g = 0; g < nst; ++g, ++cnt) {
-          if (left == 0) {  // a fresh partial every G stages, alternating between the two buffers
-            a = kb & 1;
-            if (!ptx::mbar_wait(&part_empty[a], ((kb >> 1) & 1) ^ 1, st)) { ok = false; break; }
-            ++kb;
-            ptx::tc_fence_after();
-            d = tmem_base + a * TN;
-            accumulate = 0;
-            left = G;
-          }
+        for (int g = 0; g < nst && ok; ++g, ++cnt) {
           const int s = cnt % STAGES;
           const uint32_t r = cnt / STAGES;
           if (!ptx::mbar_wait(&full[s], r & 1, st)) { ok = false; break; }
           ptx::tc_fence_after();
           const uint32_t base = ptx::smem_u32(smem + s * STAGE_BYTES);
 #pragma unroll
-          for (int u2 = 0; u2 < SUB; ++u2)
+          for (int u2 = 0; u2 < SUB; ++u2) {
+            if (left == 0) {  // a fresh partial every G sub-chunks, alternating between the two buffers
+              a = kb & 1;
+              if (!ptx::mbar_wait(&part_empty[a], ((kb >> 1) & 1) ^ 1, st)) { ok = false; break; }
+              ++kb;
+              ptx::tc_fence_after();
+              d = tmem_base + a * TN;
+              accumulate = 0;
+              left = G;
+            }
 #pragma unroll
             for (int kk = 0; kk < KCH / KMMA; ++kk) {
               const uint32_t off = kk * KMMA * 2;
@@ -300,10 +303,12 @@ __global__ void __launch_bounds__(THREADS, 1) exact_product_kernel(const __grid_
                                    ptx::sdesc_k64(base + SUB * A_BYTES + u2 * B_BYTES + off), idesc, accumulate);
               accumulate = 1;
             }
-          ptx::mma_commit_pair(&empty[s], BOTH);
-          if (--left == 0 || g == nst - 1) ptx::mma_commit_pair(&part_full[a], BOTH);
+            if (--left == 0) ptx::mma_commit_pair(&part_full[a], BOTH);
+          }
+          if (ok) ptx::mma_commit_pair(&empty[s], BOTH);
         }
         if (!ok) break;
+        if (left != 0) ptx::mma_commit_pair(&part_full[a], BOTH);  // the unit's last partial
       }
     }
   } else if (warp >= 4) {
@@ -324,7 +329,7 @@ __global__ void __launch_bounds__(THREADS, 1) exact_product_kernel(const __grid_
       if (lane == 0) ptx::mbar_arrive(&tile_empty[slot]);
       if (t >= ntiles) break;
       const Unit un = unit_of(b, t);
-      const int nparts = (un.kend * CPB + G - 1) / G;
+      const int nparts = (un.kend * CPB * SUB + G - 1) / G;
 #pragma unroll
       for (int i = 0; i < EPI_COLS; ++i) master[i] = 0;
       bool ok = true;

@@ -1077,18 +1077,22 @@ __device__ __forceinline__ void tile_sums(const float (&master)[EPI_COLS], float
   }
 }
 
-// NST operand stages (8, the most that fit beside the epilogue staging, or 6:
-// a batch's autotuner picks one)
+// NST 64-byte K-steps of operands in flight (8, the most that fit beside the
+// epilogue staging, or 6: a batch's autotuner picks one), two to a stage: the
+// single MMA-issuing thread waits on a stage and commits it once per eight
+// MMAs (one step a stage, four MMAs, ran 4 % slower in BF16/FP16, 10 % in TF32)
 template <bool TF32, int NST = 8>
 struct Cfg {
-  static constexpr int STAGES = NST;
+  static constexpr int SUB = 2;  // K-steps per stage
+  static constexpr int STAGES = NST / SUB;
   static constexpr int ESZ = TF32 ? 4 : 2;
-  static constexpr int KCH = 64 / ESZ;
+  static constexpr int KCH = 64 / ESZ;  // K per step
   static constexpr int KMMA = TF32 ? 8 : 16;
-  static constexpr int CPB = TB / KCH;
+  static constexpr int CPB = TB / (KCH * SUB);  // stages per TB-wide K-block
   static constexpr int A_BYTES = TB * 64;                    // one piece of this CTA's L^-1 rows: 8 KB
   static constexpr int B_BYTES = (TN / 2) * 64;              // this CTA's half of the SNP columns: 8 KB
-  static constexpr int STAGE_BYTES = 2 * A_BYTES + B_BYTES;  // 24 KB
+  static constexpr int STEP_BYTES = 2 * A_BYTES + B_BYTES;   // 24 KB: [hi | lo | x]
+  static constexpr int STAGE_BYTES = SUB * STEP_BYTES;       // 48 KB
   static constexpr int CHUNK_BYTES = 2048;
   static constexpr int STG_OFF = STAGES * STAGE_BYTES;
   static constexpr int BAR_OFF = STG_OFF + EPI_WARPS * 2 * CHUNK_BYTES;
@@ -1211,15 +1215,19 @@ __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_co
             const uint32_t r = cnt / ST;
             if (!ptx::mbar_wait(&empty[s], (r & 1) ^ 1, st)) { ok = false; break; }
             uint8_t* sb = smem + s * K::STAGE_BYTES;
-            const int kx = j * TB + h * K::KCH;
+            const int kx = j * TB + h * K::KCH * K::SUB;
             const uint32_t fb = lead_addr(&full[s]);
             if (leader)
               ptx::mbar_arrive_expect_tx(&full[s], 2 * K::STAGE_BYTES);
             else
               ptx::mbar_arrive_peer_count(fb);
-            ptx::tma_load_2d_pair(sb, &M.Ahi, fb, kx, ay);
-            ptx::tma_load_2d_pair(sb + K::A_BYTES, &M.Alo, fb, kx, ay);
-            ptx::tma_load_2d_pair(sb + 2 * K::A_BYTES, &M.XcH, fb, kx, ycol);
+#pragma unroll
+            for (int u2 = 0; u2 < K::SUB; ++u2) {
+              uint8_t* sp = sb + u2 * K::STEP_BYTES;
+              ptx::tma_load_2d_pair(sp, &M.Ahi, fb, kx + u2 * K::KCH, ay);
+              ptx::tma_load_2d_pair(sp + K::A_BYTES, &M.Alo, fb, kx + u2 * K::KCH, ay);
+              ptx::tma_load_2d_pair(sp + 2 * K::A_BYTES, &M.XcH, fb, kx + u2 * K::KCH, ycol);
+            }
           }
         }
         if (!ok) break;
@@ -1263,16 +1271,20 @@ __global__ void __launch_bounds__(THREADS, 1) trsm_tc_inv_kernel(const __grid_co
             const uint32_t r = cnt / ST;
             if (!ptx::mbar_wait(&full[s], r & 1, st)) { ok = false; break; }
             ptx::tc_fence_after();
-            const uint32_t base = ptx::smem_u32(smem + s * K::STAGE_BYTES);
+            const uint32_t base0 = ptx::smem_u32(smem + s * K::STAGE_BYTES);
 #pragma unroll
-            for (int kk = 0; kk < K::KCH / K::KMMA; ++kk) {
-              const uint32_t off = kk * K::KMMA * K::ESZ;
-              const uint64_t ahi = ptx::sdesc_k64(base + off);
-              const uint64_t alo = ptx::sdesc_k64(base + K::A_BYTES + off);
-              const uint64_t bx = ptx::sdesc_k64(base + 2 * K::A_BYTES + off);
-              ptx::mma_pair<TF32>(d, alo, bx, idesc, accumulate);
-              accumulate = 1;
-              ptx::mma_pair<TF32>(d, ahi, bx, idesc, 1);
+            for (int u2 = 0; u2 < K::SUB; ++u2) {
+              const uint32_t base = base0 + u2 * K::STEP_BYTES;
+#pragma unroll
+              for (int kk = 0; kk < K::KCH / K::KMMA; ++kk) {
+                const uint32_t off = kk * K::KMMA * K::ESZ;
+                const uint64_t ahi = ptx::sdesc_k64(base + off);
+                const uint64_t alo = ptx::sdesc_k64(base + K::A_BYTES + off);
+                const uint64_t bx = ptx::sdesc_k64(base + 2 * K::A_BYTES + off);
+                ptx::mma_pair<TF32>(d, alo, bx, idesc, accumulate);
+                accumulate = 1;
+                ptx::mma_pair<TF32>(d, ahi, bx, idesc, 1);
+              }
             }
             ptx::mma_commit_pair(&empty[s], BOTH);
           }
