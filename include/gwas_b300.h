@@ -331,7 +331,8 @@ int gwas_batch_solve_k(gwas_batch *B, int k, const int8_t *const *XR, const int6
  * to the smallest bs); the tile mode -- the studies' own and, for BF16x3 and
  * TF32x3 batches, the other of GWAS_TILES_INVERSE and GWAS_TILES_PAIR_MMA
  * (their operators are built once for the trial, kept if chosen); the
- * inverse form's operand stages (8 or 6); the substitution's tile order
+ * inverse form's operand depth in 64-byte K-steps (8 or 6, two steps to a
+ * shared-memory stage); the substitution's tile order
  * (interleaved, or study after study over all strips or groups of 8 or 4).
  * Each candidate is timed (CUDA events; one warm-up, then reps) as whole
  * gwas_batch_solve steps with device arrays on seeded dosage blocks
@@ -341,7 +342,7 @@ int gwas_batch_solve_k(gwas_batch *B, int k, const int8_t *const *XR, const int6
 typedef struct {
   int cols;           /* SNP columns per study per launch */
   int tile_mode;      /* GWAS_TILES_INVERSE or GWAS_TILES_PAIR_MMA */
-  int stages;         /* operand stages of the inverse-form kernel */
+  int stages;         /* operand depth of the inverse-form kernel in K-steps (8 or 6; two a stage) */
   int order;          /* 0 interleaved, 1 study after study */
   int strip_group;    /* 0 = all strips */
   double snps_per_s;  /* the chosen candidate's rate over all studies */
